@@ -1,0 +1,802 @@
+/*
+ * FP64 CPU oracle of the focused-transport particle pusher.
+ *
+ * TEST INFRASTRUCTURE ONLY: called by tests/, by __graft_entry__.smoke() (as the
+ * checker) and by the cpu_baseline / reference legs of bench.py.  It shares no
+ * code, header, table or constant with the CUDA library.
+ *
+ * Every function below restates one part of the method of Husidic et al. (2024),
+ * Sec. 2.1-2.4, in plain double precision, in the order the method states it:
+ *
+ *   - Eq. 2  dx/dt  = V_sw + V_d + mu v b, with V_d = 0 (Sec. 2.1)
+ *   - Eq. 3  dmu/dt = (1-mu^2)/2 (v div b + mu div V - 3 mu bb:grad V - (2/v) b.dV/dt)
+ *   - Eq. 4  dp/dt  = [(1-3mu^2)/2 bb:grad V - (1-mu^2)/2 div V - (mu/v) b.dV/dt] p
+ *   - Eq. 5  D_mumu = D0 (|mu|/(1+|mu|) + eps)(1-mu^2), plus the quasi-linear form
+ *            (nu/2)(1-mu^2)(|mu|^(q-1) + H) and the isotropic form D(1-mu^2)
+ *   - Sec. 2.1: Eqs. 1-4 are integrated as Ito SDEs forward in time; here by
+ *            Euler-Maruyama, with the Ito drift dD_mumu/dmu in mu, reflection at
+ *            mu = +-1, and cross-field diffusion kappa_perp = (v lambda_perp/3)(I-bb)
+ *            with its Ito drift div(kappa_perp)
+ *   - Sec. 2.4: locate the particle on the grid, read the surrounding cell
+ *            values and interpolate them trilinearly at every step; snapshots
+ *            are interpolated linearly in time
+ *   - Eq. 7: injection uniform in volume over the div V < 0 region with weight
+ *            1/r^2, mono-energetic or a power law in energy
+ *   - Sec. 2.3 / Figs. 5-8: intensities from weighted occupancy tallies
+ *
+ * Readings where the paper is silent (normalisation of D0 from lambda_par,
+ * the mu floor of the quasi-linear drift, the momentum update, the cross-field
+ * drift form, the counter-based random numbers) are stated at each function.
+ *
+ * Parity pins: tests/test_oracle_*.py check this file against closed forms,
+ * invariants and library routines (the <mu> decay, stationary isotropy, the
+ * diffusion-limit kappa_par, the Hubble-flow exact solution, the magnetic-moment
+ * invariant, the diffusive-shock-acceleration index, the weight ledger,
+ * interpolation of affine data, Philox known-answer vectors).  The paper's own
+ * figures print no numbers, so agreement with its results is "parity unpinned".
+ */
+#include "fte_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* ---- units (own definitions) ---------------------------------------------- */
+static const double OR_PI = 3.14159265358979323846;
+static const double OR_AU_M = 1.495978707e11;
+static const double OR_C_MS = 299792458.0;
+static const double OR_MC2 = 938.27208816;   /* MeV */
+
+static double c_au(void) { return OR_C_MS / OR_AU_M; }
+
+/* ---- Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) --------------------- */
+/* A Philox round: two 32x32->64 multiplications by the round multipliers,
+   the high halves xored with the other counter words and the round key.  The
+   key is advanced by the Weyl constants between rounds. */
+void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c0;
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* Counter (c0, id, tag, 0), key (seed, set_id).  tag 0: transport step c0;
+   tag 1: injection draw (c0 = 0); tag 2: injection position attempt c0.
+   A 32-bit word x becomes u = ((x >> 8) + 1/2) 2^-24, in (0, 1). */
+void or_uniforms(uint32_t seed, uint32_t set_id, uint32_t c0, uint32_t id, uint32_t tag,
+                 double u[4])
+{
+    uint32_t ctr[4] = {c0, id, tag, 0u}, key[2] = {seed, set_id}, x[4];
+    or_philox4x32_10(ctr, key, x);
+    for (int i = 0; i < 4; ++i) u[i] = ((double)(x[i] >> 8) + 0.5) * (1.0 / 16777216.0);
+}
+
+/* Box-Muller: (u0, u1) -> z_mu, z_perp1; (u2, u3) -> z_perp2. */
+void or_normals(uint32_t seed, uint32_t set_id, uint32_t n, uint32_t id, double z[3])
+{
+    double u[4];
+    or_uniforms(seed, set_id, n, id, 0u, u);
+    double a = sqrt(-2.0 * log(u[0]));
+    double b = sqrt(-2.0 * log(u[2]));
+    z[0] = a * cos(2.0 * OR_PI * u[1]);
+    z[1] = a * sin(2.0 * OR_PI * u[1]);
+    z[2] = b * cos(2.0 * OR_PI * u[3]);
+}
+
+/* ---- Gauss-Legendre rule (Newton iteration on P_n) ----------------------- */
+#define OR_GL_N 1000
+static double gl_x[OR_GL_N], gl_w[OR_GL_N];
+static int gl_ready = 0;
+
+static void gl_init(void)
+{
+    if (gl_ready) return;
+    const int n = OR_GL_N;
+    for (int i = 0; i < (n + 1) / 2; ++i) {
+        double x = cos(OR_PI * (i + 0.75) / (n + 0.5));
+        double dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = x;
+            for (int k = 2; k <= n; ++k) {
+                double pk = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+                p0 = p1; p1 = pk;
+            }
+            dp = n * (x * p1 - p0) / (x * x - 1.0);
+            double dx = p1 / dp;
+            x -= dx;
+            if (fabs(dx) < 1e-16) break;
+        }
+        {   /* recompute derivative at the converged root */
+            double p0 = 1.0, p1 = x;
+            for (int k = 2; k <= n; ++k) {
+                double pk = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+                p0 = p1; p1 = pk;
+            }
+            dp = n * (x * p1 - p0) / (x * x - 1.0);
+        }
+        double w = 2.0 / ((1.0 - x * x) * dp * dp);
+        gl_x[i] = -x; gl_w[i] = w;
+        gl_x[n - 1 - i] = x; gl_w[n - 1 - i] = w;
+    }
+    gl_ready = 1;
+}
+
+/* Normalisation of the pitch-angle coefficient from lambda_par (Sec. 2.1: D0 is
+   fixed by the rigidity and a prescribed lambda_par).  Reading: the standard
+   relation lambda_par = (3v/8) int_{-1}^{1} (1-mu^2)^2 / D_mumu dmu.
+     QLT:   D = (nu/2)(1-mu^2)(|mu|^(q-1)+H)  -> nu = 3 v I / (2 lambda),
+            I = int_0^1 (1-mu^2)/(mu^(q-1)+H) dmu
+     Eq. 5: D = D0 (|mu|/(1+|mu|)+eps)(1-mu^2) -> D0 = 3 v J / (4 lambda),
+            J = int_0^1 (1-mu^2)/(mu/(1+mu)+eps) dmu
+     iso:   D = D(1-mu^2) -> D = v / (2 lambda)   (returns 1)
+   Integrals by Gauss-Legendre after mu = s^3 (removes the cusp at mu = 0). */
+double or_norm_integral(int model, double q, double H, double eps)
+{
+    if (model == OR_DMUMU_ISO) return 1.0;
+    gl_init();
+    double sum = 0.0;
+    for (int i = 0; i < OR_GL_N; ++i) {
+        double s = 0.5 * (gl_x[i] + 1.0);
+        double mu = s * s * s;
+        double jac = 3.0 * s * s * 0.5;
+        double den = (model == OR_DMUMU_QLT) ? (pow(mu, q - 1.0) + H) : (mu / (1.0 + mu) + eps);
+        sum += gl_w[i] * jac * (1.0 - mu * mu) / den;
+    }
+    return sum;
+}
+
+static double lambda_of_p(const or_params* prm, double p)
+{
+    if (prm->p_ref > 0.0 && prm->alpha != 0.0) return prm->lambda_par * pow(p / prm->p_ref, prm->alpha);
+    return prm->lambda_par;
+}
+
+/* D_mumu and dD_mumu/dmu (Eq. 5 and the alternatives of Sec. 2.1).  For the
+   quasi-linear form the factor |mu|^(q-2) of the derivative is evaluated with
+   |mu| floored at mu_floor (the derivative diverges at mu = 0 for q < 2).
+   sgn(0) = 0.  out = {D, dD/dmu, scale (nu, D0 or D)}. */
+static void dmumu_eval(const or_params* prm, double I, double mu, double v, double p,
+                       double* D, double* dD, double* scale)
+{
+    double lam = lambda_of_p(prm, p);
+    double am = fabs(mu);
+    double sg = (mu > 0.0) ? 1.0 : ((mu < 0.0) ? -1.0 : 0.0);
+    double omm = 1.0 - mu * mu;
+    if (prm->dmumu == OR_DMUMU_QLT) {
+        double nu = 3.0 * v * I / (2.0 * lam);
+        double g = pow(am, prm->q - 1.0) + prm->H;
+        double amf = am > prm->mu_floor ? am : prm->mu_floor;
+        double dg = (prm->q - 1.0) * pow(amf, prm->q - 2.0) * sg;
+        *D = 0.5 * nu * omm * g;
+        *dD = 0.5 * nu * (-2.0 * mu * g + omm * dg);
+        *scale = nu;
+    } else if (prm->dmumu == OR_DMUMU_PAPER) {
+        double D0 = 3.0 * v * I / (4.0 * lam);
+        double h = am / (1.0 + am) + prm->eps;
+        double dh = sg / ((1.0 + am) * (1.0 + am));
+        *D = D0 * h * omm;
+        *dD = D0 * (dh * omm - 2.0 * mu * h);
+        *scale = D0;
+    } else {
+        double Dc = v / (2.0 * lam);
+        *D = Dc * omm;
+        *dD = -2.0 * mu * Dc;
+        *scale = Dc;
+    }
+}
+
+void or_dmumu(const or_params* prm, double mu, double v, double p, double out[3])
+{
+    double I = or_norm_integral(prm->dmumu, prm->q, prm->H, prm->eps);
+    dmumu_eval(prm, I, mu, v, p, &out[0], &out[1], &out[2]);
+}
+
+/* ---- background evaluation (Sec. 2.4) ------------------------------------- */
+typedef struct {
+    double B[3], V[3], G[9], gB[3], dVdt[3], dB[9];
+    double divv;
+} fields_t;
+
+typedef struct { int i0; double f; double dfdx; } axis_t;
+
+static double r_centre(const or_background* g, int i)
+{
+    if (g->radial == 1) return g->r_min * exp((i + 0.5) * log(g->r_max / g->r_min) / g->nr);
+    return g->r_min + (i + 0.5) * (g->r_max - g->r_min) / g->nr;
+}
+
+/* Bracketing cell centres along one axis and the weight in the physical
+   coordinate; outside the outermost centres the value is held constant. */
+static void grid_axes(const or_background* g, double r, double th, double ph,
+                      axis_t* ar, axis_t* at, axis_t* ap, int* k1)
+{
+    double xi;
+    if (g->radial == 1) xi = log(r / g->r_min) / (log(g->r_max / g->r_min) / g->nr) - 0.5;
+    else xi = (r - g->r_min) / ((g->r_max - g->r_min) / g->nr) - 0.5;
+    if (xi < 0.0) { ar->i0 = 0; ar->f = 0.0; ar->dfdx = 0.0; }
+    else if (xi >= g->nr - 1) { ar->i0 = g->nr - 2; ar->f = 1.0; ar->dfdx = 0.0; }
+    else {
+        ar->i0 = (int)floor(xi);
+        double c0 = r_centre(g, ar->i0), c1 = r_centre(g, ar->i0 + 1);
+        ar->f = (r - c0) / (c1 - c0);
+        ar->dfdx = 1.0 / (c1 - c0);
+    }
+    double dth = (g->th_max - g->th_min) / g->nth;
+    xi = (th - g->th_min) / dth - 0.5;
+    if (xi < 0.0) { at->i0 = 0; at->f = 0.0; at->dfdx = 0.0; }
+    else if (xi >= g->nth - 1) { at->i0 = g->nth - 2; at->f = 1.0; at->dfdx = 0.0; }
+    else {
+        at->i0 = (int)floor(xi);
+        double c0 = g->th_min + (at->i0 + 0.5) * dth;
+        at->f = (th - c0) / dth;
+        at->dfdx = 1.0 / dth;
+    }
+    double dph = 2.0 * OR_PI / g->nph;
+    xi = ph / dph - 0.5;
+    int k0 = (int)floor(xi);
+    ap->f = xi - k0;
+    ap->dfdx = 1.0 / dph;
+    k0 = ((k0 % g->nph) + g->nph) % g->nph;
+    ap->i0 = k0;
+    *k1 = (k0 + 1) % g->nph;
+}
+
+static void grid_fields(const or_background* g, double x, double y, double z, double t,
+                        fields_t* F)
+{
+    memset(F, 0, sizeof(*F));
+    double r = sqrt(x * x + y * y + z * z);
+    double rho = sqrt(x * x + y * y);
+    double th = atan2(rho, z);
+    double ph = atan2(y, x);
+    if (ph < 0.0) ph += 2.0 * OR_PI;
+    axis_t ar, at, ap;
+    int k1;
+    grid_axes(g, r, th, ph, &ar, &at, &ap, &k1);
+
+    /* time bracket (linear interpolation between snapshots) */
+    int s0 = 0, s1 = 0, two = 0;
+    double wt = 0.0;
+    if (g->n_snap > 1) {
+        double tau = (t - g->t_snap0) / g->dt_snap;
+        if (g->periodic) {
+            double kf = floor(tau);
+            wt = tau - kf;
+            long long k = (long long)kf;
+            s0 = (int)(((k % g->n_snap) + g->n_snap) % g->n_snap);
+            s1 = (s0 + 1) % g->n_snap;
+            two = 1;
+        } else if (tau < 0.0) {
+            s0 = s1 = 0;
+        } else if (tau >= g->n_snap - 1) {
+            s0 = s1 = g->n_snap - 1;
+        } else {
+            double kf = floor(tau);
+            s0 = (int)kf; s1 = s0 + 1; wt = tau - kf; two = 1;
+        }
+    }
+    double dBax[3][3] = {{0}};   /* dB_i / d(r, theta, phi) */
+    const size_t rec = (size_t)g->rec;
+    for (int s = 0; s < (two ? 2 : 1); ++s) {
+        int snap = (s == 0) ? s0 : s1;
+        double ws = two ? ((s == 0) ? 1.0 - wt : wt) : 1.0;
+        for (int c = 0; c < 8; ++c) {
+            int cr = c & 1, ct = (c >> 1) & 1, cp = (c >> 2) & 1;
+            int i = ar.i0 + cr, j = at.i0 + ct, k = cp ? k1 : ap.i0;
+            double wr = cr ? ar.f : 1.0 - ar.f;
+            double wth = ct ? at.f : 1.0 - at.f;
+            double wp = cp ? ap.f : 1.0 - ap.f;
+            double wc = wr * wth * wp;
+            const float* q = g->fields + ((((size_t)snap * g->nph + k) * g->nth + j) * g->nr + i) * rec;
+            for (int m = 0; m < 3; ++m) F->B[m] += ws * wc * q[m];
+            for (int m = 0; m < 3; ++m) F->V[m] += ws * wc * q[3 + m];
+            for (int m = 0; m < 9; ++m) F->G[m] += ws * wc * q[6 + m];
+            for (int m = 0; m < 3; ++m) F->gB[m] += ws * wc * q[15 + m];
+            if (two)
+                for (int m = 0; m < 3; ++m)
+                    F->dVdt[m] += (s == 0 ? -1.0 : 1.0) * wc * q[3 + m] / g->dt_snap;
+            double er = (cr ? 1.0 : -1.0) * ar.dfdx * wth * wp;
+            double et = wr * (ct ? 1.0 : -1.0) * at.dfdx * wp;
+            double ep = wr * wth * (cp ? 1.0 : -1.0) * ap.dfdx;
+            for (int m = 0; m < 3; ++m) {
+                dBax[m][0] += ws * er * q[m];
+                dBax[m][1] += ws * et * q[m];
+                dBax[m][2] += ws * ep * q[m];
+            }
+        }
+    }
+    /* d/dx_j = r_hat_j d/dr + theta_hat_j / r d/dtheta + phi_hat_j / (r sin theta) d/dphi */
+    double st = sin(th), ctt = cos(th), sp = sin(ph), cpp = cos(ph);
+    double rh[3] = {st * cpp, st * sp, ctt};
+    double thh[3] = {ctt * cpp, ctt * sp, -st};
+    double phh[3] = {-sp, cpp, 0.0};
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            F->dB[3 * i + j] = dBax[i][0] * rh[j] + dBax[i][1] * thh[j] / r
+                             + dBax[i][2] * phh[j] / (r * st);
+    F->divv = F->G[0] + F->G[4] + F->G[8];
+}
+
+/* Analytic backgrounds used by the physics pins (all static):
+   UNIFORM_B    a0 = B0: B = B0 z_hat, V = 0
+   HUBBLE       a0 = alpha, a1 = B0: V = alpha x (grad V = alpha I), B = B0 z_hat
+   MONOPOLE     a0 = B0: B = B0 r_hat / r^2, V = 0
+   RADIAL_WIND  a0 = V0, a1 = B0: V = V0 r_hat, B = B0 r_hat / r^2
+   PLANAR_SHOCK a0 = V1, a1 = V2, a2 = width w, a3 = B0, a4 = field angle from x_hat (x-y plane):
+                V = V(x) x_hat, V(x) = V1 + (V2 - V1)(1 + tanh(x/w))/2, B uniform */
+static void analytic_fields(const or_background* g, double x, double y, double z, fields_t* F)
+{
+    memset(F, 0, sizeof(*F));
+    const double* a = g->a;
+    double r = sqrt(x * x + y * y + z * z);
+    double rh[3] = {x / r, y / r, z / r};
+    switch (g->kind) {
+    case OR_BG_UNIFORM_B:
+        F->B[2] = a[0];
+        break;
+    case OR_BG_HUBBLE:
+        F->V[0] = a[0] * x; F->V[1] = a[0] * y; F->V[2] = a[0] * z;
+        F->G[0] = F->G[4] = F->G[8] = a[0];
+        F->B[2] = a[1];
+        break;
+    case OR_BG_MONOPOLE:
+    case OR_BG_RADIAL_WIND: {
+        double B0 = (g->kind == OR_BG_MONOPOLE) ? a[0] : a[1];
+        double Bm = B0 / (r * r);
+        for (int i = 0; i < 3; ++i) {
+            F->B[i] = Bm * rh[i];
+            F->gB[i] = -2.0 * Bm / r * rh[i];
+            for (int j = 0; j < 3; ++j)
+                F->dB[3 * i + j] = Bm / r * ((i == j ? 1.0 : 0.0) - 3.0 * rh[i] * rh[j]);
+        }
+        if (g->kind == OR_BG_RADIAL_WIND) {
+            for (int i = 0; i < 3; ++i) {
+                F->V[i] = a[0] * rh[i];
+                for (int j = 0; j < 3; ++j)
+                    F->G[3 * i + j] = a[0] / r * ((i == j ? 1.0 : 0.0) - rh[i] * rh[j]);
+            }
+        }
+        break;
+    }
+    case OR_BG_PLANAR_SHOCK: {
+        double V1 = a[0], V2 = a[1], w = a[2];
+        double th = tanh(x / w);
+        F->V[0] = V1 + (V2 - V1) * 0.5 * (1.0 + th);
+        F->G[0] = (V2 - V1) * 0.5 * (1.0 - th * th) / w;
+        F->B[0] = a[3] * cos(a[4]);
+        F->B[1] = a[3] * sin(a[4]);
+        break;
+    }
+    default:
+        break;
+    }
+    F->divv = F->G[0] + F->G[4] + F->G[8];
+}
+
+static void eval_fields(const or_background* g, double x, double y, double z, double t,
+                        fields_t* F)
+{
+    if (g->kind == OR_BG_GRID) grid_fields(g, x, y, z, t, F);
+    else analytic_fields(g, x, y, z, F);
+}
+
+int or_eval_fields(const or_background* bg, double x, double y, double z, double t,
+                   double out[40])
+{
+    fields_t F;
+    eval_fields(bg, x, y, z, t, &F);
+    memset(out, 0, 40 * sizeof(double));
+    memcpy(out + 0, F.B, 3 * sizeof(double));
+    memcpy(out + 3, F.V, 3 * sizeof(double));
+    memcpy(out + 6, F.G, 9 * sizeof(double));
+    memcpy(out + 15, F.gB, 3 * sizeof(double));
+    memcpy(out + 18, F.dVdt, 3 * sizeof(double));
+    memcpy(out + 21, F.dB, 9 * sizeof(double));
+    out[30] = F.divv;
+    return 0;
+}
+
+/* ---- kinematics ------------------------------------------------------------ */
+/* p in m_p c: gamma = sqrt(1 + p^2), v = c p / gamma, E = m c^2 (gamma - 1)
+   evaluated as m c^2 p^2 / (gamma + 1). */
+static double speed(double p) { return c_au() * p / sqrt(1.0 + p * p); }
+static double kinetic(double p) { return OR_MC2 * p * p / (sqrt(1.0 + p * p) + 1.0); }
+static double momentum(double e) { double T = e / OR_MC2; return sqrt(T * (T + 2.0)); }
+
+/* ---- injection (Sec. 2.3, Eq. 7) ------------------------------------------- */
+static int near_integer(double xi, double tol)
+{
+    double d = xi - floor(xi);
+    return d < tol || d > 1.0 - tol;
+}
+
+int or_inject(const or_background* bg, const or_inject_spec* sp, const uint32_t* ids,
+              int64_t n, or_particle* out, double ledger_w[8], uint64_t ledger_n[8])
+{
+    for (int64_t i = 0; i < n; ++i) {
+        or_particle* P = &out[i];
+        memset(P, 0, sizeof(*P));
+        P->id = ids[i];
+        P->n_div = -1;
+        P->status = OR_ALIVE;
+        double u[4];
+        or_uniforms(sp->seed, sp->set_id, 0u, P->id, 1u, u);
+        P->mu = (sp->mu_mode == 1) ? sp->mu0 : 2.0 * u[0] - 1.0;
+        double E;
+        if (sp->energy == 0) {
+            E = sp->e0;
+        } else if (fabs(sp->gamma - 1.0) < 1e-12) {
+            E = sp->e1 * pow(sp->e2 / sp->e1, u[1]);
+        } else {
+            double g1 = 1.0 - sp->gamma;
+            double a = pow(sp->e1, g1), b = pow(sp->e2, g1);
+            E = pow(a + u[1] * (b - a), 1.0 / g1);
+        }
+        P->p = momentum(E);
+        double r = sp->r, th = sp->th, ph = sp->ph;
+        int ok = 1;
+        if (sp->region == 1) {
+            ok = 0;
+            for (int a = 0; a < sp->max_tries && !ok; ++a) {
+                double v[4];
+                or_uniforms(sp->seed, sp->set_id, (uint32_t)a, P->id, 2u, v);
+                double r13 = sp->r1 * sp->r1 * sp->r1, r23 = sp->r2 * sp->r2 * sp->r2;
+                r = cbrt(r13 + v[0] * (r23 - r13));
+                double c1 = cos(sp->th1), c2 = cos(sp->th2);
+                th = acos(c1 + v[1] * (c2 - c1));
+                ph = sp->ph1 + v[2] * (sp->ph2 - sp->ph1);
+                if (!sp->use_divv || bg->kind != OR_BG_GRID) { ok = 1; break; }
+                /* acceptance decided on the stored cell value of the containing
+                   cell, summed in float like the device does */
+                const or_background* g = bg;
+                double xr = (g->radial == 1) ? log(r / g->r_min) / (log(g->r_max / g->r_min) / g->nr)
+                                             : (r - g->r_min) / ((g->r_max - g->r_min) / g->nr);
+                double xt = (th - g->th_min) / ((g->th_max - g->th_min) / g->nth);
+                double phw = fmod(ph, 2.0 * OR_PI); if (phw < 0) phw += 2.0 * OR_PI;
+                double xp = phw / (2.0 * OR_PI / g->nph);
+                if (near_integer(xr, 2e-4) || near_integer(xt, 1e-4) || near_integer(xp, 1e-4))
+                    P->flags |= 1;
+                int ci = (int)floor(xr), cj = (int)floor(xt), ck = (int)floor(xp);
+                if (ci < 0) ci = 0;
+                if (ci > g->nr - 1) ci = g->nr - 1;
+                if (cj < 0) cj = 0;
+                if (cj > g->nth - 1) cj = g->nth - 1;
+                ck = ((ck % g->nph) + g->nph) % g->nph;
+                int sn = sp->divv_snap;
+                const float* q = g->fields + ((((size_t)sn * g->nph + ck) * g->nth + cj) * g->nr + ci) * (size_t)g->rec;
+                float s01 = q[6] + q[10];
+                float tr = s01 + q[14];
+                if (tr < (float)sp->divv_max) ok = 1;
+            }
+        }
+        P->x = r * sin(th) * cos(ph);
+        P->y = r * sin(th) * sin(ph);
+        P->z = r * cos(th);
+        P->w = (sp->weight == 1) ? 1.0 / (r * r) : 1.0;
+        if (!ok) {
+            P->status = OR_INJ_FAIL;
+            P->w = 0.0;
+            ledger_n[5] += 1;
+            continue;
+        }
+        ledger_w[0] += P->w;
+        ledger_n[0] += 1;
+    }
+    return 0;
+}
+
+/* ---- one transport step ----------------------------------------------------- */
+typedef struct {
+    const or_observer* obs;
+    int n_obs;
+    const int64_t* off;
+    double *S, *S2;
+    uint64_t *C, *A;
+    double lw[8];
+    uint64_t ln[8];
+} tally_t;
+
+static double wrap_pi(double a)
+{
+    a = fmod(a + OR_PI, 2.0 * OR_PI);
+    if (a < 0) a += 2.0 * OR_PI;
+    return a - OR_PI;
+}
+
+/* Occupancy tally of the start-of-step state: in observer o, bin (E, t) gains
+   w dt (and (w dt)^2, and one count).  Events within 1e-4 (relative) of an
+   energy-bin edge or of the observer's boundary are also counted in A. */
+static void tally_state(tally_t* T, double x, double y, double z, double p, double w,
+                        double t, double dt)
+{
+    if (!T || T->n_obs == 0) return;
+    double r = sqrt(x * x + y * y + z * z);
+    double th = atan2(sqrt(x * x + y * y), z);
+    double ph = atan2(y, x);
+    if (ph < 0.0) ph += 2.0 * OR_PI;
+    double E = kinetic(p);
+    for (int o = 0; o < T->n_obs; ++o) {
+        const or_observer* ob = &T->obs[o];
+        int inside, amb = 0;
+        if (ob->kind == 2) {
+            double d = fabs(x - ob->r);
+            inside = d <= ob->dr;
+            if (fabs(d - ob->dr) < 1e-4 * (ob->dr > 1.0 ? ob->dr : 1.0)) amb = 1;
+        } else {
+            double d = fabs(r - ob->r);
+            inside = d <= ob->dr;
+            if (fabs(d - ob->dr) < 1e-4 * ob->r) amb = 1;
+            if (ob->kind == 1) {
+                double dt_ = fabs(th - ob->th), dp_ = fabs(wrap_pi(ph - ob->ph));
+                inside = inside && dt_ <= ob->dth && dp_ <= ob->dph;
+                if (fabs(dt_ - ob->dth) < 1e-4 || fabs(dp_ - ob->dph) < 1e-4) amb = 1;
+            }
+        }
+        if (!inside && !amb) continue;
+        double le = log(E / ob->e_lo) / log(ob->e_hi / ob->e_lo) * ob->ne;
+        double ie_f = floor(le);
+        double it_f = floor(((t - ob->t_lo) * ob->nt) / (ob->t_hi - ob->t_lo));
+        if (ie_f < 0 || ie_f >= ob->ne || it_f < 0 || it_f >= ob->nt) {
+            if (inside) T->ln[7] += 1;
+            continue;
+        }
+        double step_le = log(ob->e_hi / ob->e_lo) / ob->ne;
+        double fr = le - ie_f;
+        if (fr * step_le < 1e-4 || (1.0 - fr) * step_le < 1e-4) amb = 1;
+        int64_t b = T->off[o] + (int64_t)ie_f * ob->nt + (int64_t)it_f;
+        if (inside) {
+            double wd = w * dt;
+            T->S[b] += wd;
+            T->S2[b] += wd * wd;
+            T->C[b] += 1;
+        }
+        if (amb) T->A[b] += 1;
+    }
+}
+
+/* Advance particle P by one step from step index n.  Returns the new status. */
+static int step_one(const or_background* bg, const or_params* prm, double I,
+                    or_particle* P, int64_t n, tally_t* T, double* terms)
+{
+    const double dt = prm->dt;
+    const double t = prm->t0 + (double)n * dt;
+    double x = P->x, y = P->y, z = P->z, mu = P->mu, p = P->p;
+    fields_t F;
+    eval_fields(bg, x, y, z, t, &F);
+
+    /* derived background quantities (Eqs. 3, 4) */
+    double Bm = sqrt(F.B[0] * F.B[0] + F.B[1] * F.B[1] + F.B[2] * F.B[2]);
+    double b[3] = {F.B[0] / Bm, F.B[1] / Bm, F.B[2] / Bm};
+    double divb = -(b[0] * F.gB[0] + b[1] * F.gB[1] + b[2] * F.gB[2]) / Bm;  /* = 1/L */
+    double divv = F.G[0] + F.G[4] + F.G[8];
+    double bbgv = 0.0;
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) bbgv += b[i] * b[j] * F.G[3 * i + j];
+    double dvdt[3];
+    for (int i = 0; i < 3; ++i) {
+        dvdt[i] = F.dVdt[i];
+        for (int j = 0; j < 3; ++j) dvdt[i] += F.V[j] * F.G[3 * i + j];  /* (V.grad)V */
+    }
+    double bdvdt = prm->dvdt_term ? (b[0] * dvdt[0] + b[1] * dvdt[1] + b[2] * dvdt[2]) : 0.0;
+
+    double v = speed(p);
+    double D, dD, scale;
+    dmumu_eval(prm, I, mu, v, p, &D, &dD, &scale);
+    double zn[3];
+    or_normals(prm->seed, prm->set_id, (uint32_t)n, P->id, zn);
+
+    /* Eq. 3 and the Ito pitch-angle step */
+    double omm = 1.0 - mu * mu;
+    double mudot = 0.5 * omm * (v * divb + mu * divv - 3.0 * mu * bbgv - (2.0 / v) * bdvdt);
+    double mu_new = mu + (mudot + dD) * dt + sqrt(2.0 * D * dt) * zn[0];
+    int ev = 0;
+    if (mu_new > 1.0 || mu_new < -1.0) ev = 1;           /* reflection */
+    if (mu_new > 1.0) mu_new = 2.0 - mu_new;
+    if (mu_new < -1.0) mu_new = -2.0 - mu_new;
+    if (mu_new > 1.0) mu_new = 1.0;
+    if (mu_new < -1.0) mu_new = -1.0;
+    if (mu * mu_new <= 0.0) ev = 1;                      /* mu changes sign */
+    if (prm->shock_divv > 0.0 && fabs(divv) > prm->shock_divv) ev = 1;
+
+    /* Eq. 2 with cross-field diffusion kappa_perp = (v lambda_perp / 3)(I - bb) */
+    double kap = v * prm->lambda_perp / 3.0;
+    double u_perp[3] = {0, 0, 0}, noise[3] = {0, 0, 0};
+    if (kap > 0.0) {
+        if (prm->kappa_drift) {
+            /* div(kappa_perp) = -kappa [(div b) b + (b.grad) b], with
+               (b.grad) b = [(b.grad)B - b (b.(b.grad)B)] / |B| */
+            double bgB[3];
+            for (int i = 0; i < 3; ++i)
+                bgB[i] = F.dB[3 * i + 0] * b[0] + F.dB[3 * i + 1] * b[1] + F.dB[3 * i + 2] * b[2];
+            double par = b[0] * bgB[0] + b[1] * bgB[1] + b[2] * bgB[2];
+            for (int i = 0; i < 3; ++i) {
+                double curv = (bgB[i] - b[i] * par) / Bm;
+                u_perp[i] = -kap * (divb * b[i] + curv);
+            }
+        }
+        double e1[3], e2[3];
+        double cz = sqrt(b[1] * b[1] + b[0] * b[0]);      /* |b x z_hat| */
+        if (fabs(cz - 0.1) < 1e-5) ev = 1;
+        if (cz >= 0.1) { e1[0] = b[1] / cz; e1[1] = -b[0] / cz; e1[2] = 0.0; }
+        else {
+            double cx = sqrt(b[2] * b[2] + b[1] * b[1]);  /* |b x x_hat| */
+            e1[0] = 0.0; e1[1] = b[2] / cx; e1[2] = -b[1] / cx;
+        }
+        e2[0] = b[1] * e1[2] - b[2] * e1[1];
+        e2[1] = b[2] * e1[0] - b[0] * e1[2];
+        e2[2] = b[0] * e1[1] - b[1] * e1[0];
+        double amp = sqrt(2.0 * kap * dt);
+        for (int i = 0; i < 3; ++i) noise[i] = amp * (zn[1] * e1[i] + zn[2] * e2[i]);
+    }
+    double xn[3];
+    double xo[3] = {x, y, z};
+    for (int i = 0; i < 3; ++i)
+        xn[i] = xo[i] + (F.V[i] + mu * v * b[i] + u_perp[i]) * dt + noise[i];
+
+    /* Eq. 4 */
+    double pdot_p = 0.5 * (1.0 - 3.0 * mu * mu) * bbgv - 0.5 * omm * divv - (mu / v) * bdvdt;
+    double p_new = prm->p_update == 0 ? p * exp(pdot_p * dt) : p * (1.0 + pdot_p * dt);
+
+    if (terms) {
+        double* o = terms;
+        o[0] = v; o[1] = sqrt(1.0 + p * p); o[2] = D; o[3] = dD; o[4] = mudot; o[5] = pdot_p;
+        o[6] = divb; o[7] = divv; o[8] = bbgv; o[9] = bdvdt;
+        o[10] = b[0]; o[11] = b[1]; o[12] = b[2];
+        o[13] = F.V[0]; o[14] = F.V[1]; o[15] = F.V[2];
+        o[16] = zn[0]; o[17] = zn[1]; o[18] = zn[2];
+        o[19] = kap; o[20] = u_perp[0]; o[21] = u_perp[1]; o[22] = u_perp[2];
+        o[23] = xn[0]; o[24] = xn[1]; o[25] = xn[2];
+        o[26] = mu_new; o[27] = p_new; o[28] = kinetic(p); o[29] = scale;
+        o[30] = t; o[31] = ev;
+        return P->status;
+    }
+
+    /* tally the start-of-step state */
+    tally_state(T, x, y, z, p, P->w, t, dt);
+
+    P->x = xn[0]; P->y = xn[1]; P->z = xn[2];
+    P->mu = mu_new; P->p = p_new;
+
+    int st = OR_ALIVE;
+    if (!isfinite(xn[0]) || !isfinite(xn[1]) || !isfinite(xn[2]) || !isfinite(mu_new) ||
+        !isfinite(p_new)) {
+        st = OR_NAN; ev = 1;
+    } else if (bg->domain == OR_DOM_SPHERE) {
+        double rmin = bg->dom[0], rmax = bg->dom[1], tmin = bg->dom[2], tmax = bg->dom[3];
+        double rn = sqrt(xn[0] * xn[0] + xn[1] * xn[1] + xn[2] * xn[2]);
+        double thn = atan2(sqrt(xn[0] * xn[0] + xn[1] * xn[1]), xn[2]);
+        if (fabs(rn - rmin) < 1e-5 * rmin || fabs(rn - rmax) < 1e-5 * rmax ||
+            fabs(thn - tmin) < 1e-5 || fabs(thn - tmax) < 1e-5) ev = 1;
+        if (rn < rmin) st = OR_ABS_INNER;
+        else if (rn > rmax) st = OR_ABS_OUTER;
+        else if (thn < tmin || thn > tmax) st = OR_ABS_THETA;
+    } else if (bg->domain == OR_DOM_SLAB_X) {
+        double a = bg->dom[0], c = bg->dom[1];
+        if (fabs(xn[0] - a) < 1e-5 * (fabs(a) > 1 ? fabs(a) : 1) ||
+            fabs(xn[0] - c) < 1e-5 * (fabs(c) > 1 ? fabs(c) : 1)) ev = 1;
+        if (xn[0] < a) st = OR_ABS_INNER;
+        else if (xn[0] > c) st = OR_ABS_OUTER;
+    }
+    if (ev && P->n_div < 0) P->n_div = n;
+    P->status = st;
+    if (st != OR_ALIVE && T) {
+        T->lw[st] += P->w;
+        T->ln[st] += 1;
+    }
+    return st;
+}
+
+int or_step_terms(const or_background* bg, const or_params* prm, const or_particle* p,
+                  int64_t n, double out[32])
+{
+    or_particle q = *p;
+    double I = or_norm_integral(prm->dmumu, prm->q, prm->H, prm->eps);
+    step_one(bg, prm, I, &q, n, NULL, out);
+    return 0;
+}
+
+int or_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+int or_advance(const or_background* bg, const or_params* prm, const or_observer* obs,
+               int n_obs, or_particle* P, int64_t n, int64_t n_start, int64_t n_end,
+               double* S, double* S2, uint64_t* C, uint64_t* A, double ledger_w[8],
+               uint64_t ledger_n[8], int n_threads)
+{
+    if (n_threads < 1) n_threads = 1;
+    int64_t off[64 + 1];
+    if (n_obs > 64) return -1;
+    off[0] = 0;
+    for (int o = 0; o < n_obs; ++o) off[o + 1] = off[o] + (int64_t)obs[o].ne * obs[o].nt;
+    const int64_t nb = off[n_obs];
+    const double I = or_norm_integral(prm->dmumu, prm->q, prm->H, prm->eps);
+
+    double* tS = (double*)calloc((size_t)n_threads * (nb > 0 ? nb : 1), sizeof(double));
+    double* tS2 = (double*)calloc((size_t)n_threads * (nb > 0 ? nb : 1), sizeof(double));
+    uint64_t* tC = (uint64_t*)calloc((size_t)n_threads * (nb > 0 ? nb : 1), sizeof(uint64_t));
+    uint64_t* tA = (uint64_t*)calloc((size_t)n_threads * (nb > 0 ? nb : 1), sizeof(uint64_t));
+    tally_t* tt = (tally_t*)calloc((size_t)n_threads, sizeof(tally_t));
+    if (!tS || !tS2 || !tC || !tA || !tt) return -2;
+    for (int k = 0; k < n_threads; ++k) {
+        tt[k].obs = obs; tt[k].n_obs = n_obs; tt[k].off = off;
+        tt[k].S = tS + (size_t)k * nb; tt[k].S2 = tS2 + (size_t)k * nb;
+        tt[k].C = tC + (size_t)k * nb; tt[k].A = tA + (size_t)k * nb;
+    }
+#ifdef _OPENMP
+#pragma omp parallel num_threads(n_threads)
+#endif
+    {
+        int tid = 0;
+#ifdef _OPENMP
+        tid = omp_get_thread_num();
+#endif
+        tally_t* T = &tt[tid];
+#ifdef _OPENMP
+#pragma omp for schedule(static)
+#endif
+        for (int64_t i = 0; i < n; ++i) {
+            or_particle* q = &P[i];
+            if (q->status != OR_ALIVE) continue;
+            for (int64_t s = n_start; s < n_end; ++s) {
+                T->ln[6] += 1;
+                if (step_one(bg, prm, I, q, s, T, NULL) != OR_ALIVE) break;
+            }
+        }
+    }
+    for (int k = 0; k < n_threads; ++k) {
+        for (int64_t b = 0; b < nb; ++b) {
+            S[b] += tt[k].S[b]; S2[b] += tt[k].S2[b]; C[b] += tt[k].C[b]; A[b] += tt[k].A[b];
+        }
+        for (int m = 0; m < 8; ++m) { ledger_w[m] += tt[k].lw[m]; ledger_n[m] += tt[k].ln[m]; }
+    }
+    free(tS); free(tS2); free(tC); free(tA); free(tt);
+    return 0;
+}
+
+/* Intensity from the occupancy sum (Eq. 7 with j = p^2 f): S / dt_bin is the
+   mean weight inside the observer volume during the bin; per unit volume and
+   energy, times v / (4 pi), gives the differential intensity
+   j = S v(E_c) / (4 pi V_obs dt_bin dE), E_c the geometric bin centre. */
+void or_intensity(const or_observer* ob, const double* S, double* J)
+{
+    double vol;
+    if (ob->kind == 0) {
+        double a = ob->r - ob->dr, b = ob->r + ob->dr;
+        vol = 4.0 * OR_PI / 3.0 * (b * b * b - a * a * a);
+    } else if (ob->kind == 1) {
+        double a = ob->r - ob->dr, b = ob->r + ob->dr;
+        vol = (b * b * b - a * a * a) / 3.0 * (cos(ob->th - ob->dth) - cos(ob->th + ob->dth))
+              * 2.0 * ob->dph;
+    } else {
+        vol = 2.0 * ob->dr;
+    }
+    double dtb = (ob->t_hi - ob->t_lo) / ob->nt;
+    for (int e = 0; e < ob->ne; ++e) {
+        double e0 = ob->e_lo * pow(ob->e_hi / ob->e_lo, (double)e / ob->ne);
+        double e1 = ob->e_lo * pow(ob->e_hi / ob->e_lo, (double)(e + 1) / ob->ne);
+        double ec = sqrt(e0 * e1);
+        double v = speed(momentum(ec));
+        for (int k = 0; k < ob->nt; ++k)
+            J[e * ob->nt + k] = S[e * ob->nt + k] * v / (4.0 * OR_PI * vol * dtb * (e1 - e0));
+    }
+}
