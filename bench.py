@@ -1,0 +1,344 @@
+"""Throughput benchmark of the focused-transport pusher on GB300.
+
+Workload (one bench step = one full pass of the hot path over one batch):
+  synthetic CIR in the corotating frame on a 512 r x 60 theta x 180 phi grid,
+  24 hourly snapshots (periodic), 1e6 protons injected at 50 keV uniformly over
+  the div V < 0 cells of one CIR between 1 and 2 au at theta = 90 +- 2 deg with
+  weight 1/r^2, quasi-linear D_mumu (q = 5/3, H = 0.05, lambda_par = 0.1 au),
+  dt = 10 s for 4 days (34,560 steps), occupancy tally at a 1 au observer box
+  (16 log energy bins x 144 time bins).  Per step: inject, advance, read the tally.
+
+Metric: alive particle-steps per second (whole job, all ranks).
+`value` times the device work with the inputs resident in HBM; `e2e` times the
+same step through the C ABI starting from host buffers (background upload from
+page-locked memory, tally download).
+
+Multi-GPU: every rank runs its own batch of 1e6 particles (distinct particle
+ids, weak scaling) and the tallies are summed over ranks after each step.
+
+`--impl reference` times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from fte_inputs import configs  # noqa: E402
+
+METRIC = "FTE particle-steps/s on 1 GB300 at stated tally error; % gather roofline; adj/fwd"
+UNIT = "particle-steps/s"
+ALG_BYTES = 2 * 8 * 18 * 4          # 2 snapshots x 8 corners x 18 fields x 4 B per particle-step
+CHUNK = 1024                        # steps per advance launch
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        load = [s for s in sm if s > 0.5 * max(sm)] if sm else []
+        return {"sm_mhz": statistics.median(load) if load else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def build_workload():
+    w = configs.cir_uniform_1e6()
+    cache = os.environ.get("FTE_BG_CACHE")
+    path = os.path.join(cache, "cir_uniform_512x60x180x24.npy") if cache else None
+    if path and os.path.exists(path):
+        return w, np.load(path, mmap_mode="r")
+    f = configs.build_background(w)
+    if path:
+        os.makedirs(cache, exist_ok=True)
+        np.save(path, f)
+    return w, f
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2404_12164_gb300 import api, build
+    from paper_2404_12164_gb300 import _abi as A
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    build.build()
+    w, fields = build_workload()
+    n_part, n_steps = w.n_particles, w.n_steps
+    stream = torch.cuda.current_stream()
+
+    host = torch.from_numpy(np.ascontiguousarray(fields)).pin_memory()
+    bg = api.Background(w.grid)
+    pool = api.Particles(n_part)
+    tally = api.Tally(w.observers)
+    wsp = api.Workspace()
+    wsp.ensure(api.fte_workspace_bytes(tally, CHUNK))
+    id_base = rank * n_part
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def one_step(timed_launches=None):
+        """inject + advance (chunked launches) + tally reduction over ranks."""
+        pool.c.count = 0
+        api.fte_tally_reset(tally)
+        api.fte_inject(pool, bg, w.inject, n_part, tally, id_base=id_base, check_failed=False)
+        for c in range(0, n_steps, CHUNK):
+            e = min(c + CHUNK, n_steps)
+            if timed_launches is not None:
+                ev0 = torch.cuda.Event(enable_timing=True)
+                ev1 = torch.cuda.Event(enable_timing=True)
+                ev0.record(stream)
+            api.fte_advance(pool, bg, w.params, tally, c, e, wsp)
+            if timed_launches is not None:
+                ev1.record(stream)
+                timed_launches.append((ev0, ev1))
+        if ws > 1:
+            for t_ in (tally.S, tally.S2, tally.C, tally.ledger_n):
+                dist.all_reduce(t_)
+
+    # device-resident arm ------------------------------------------------------
+    api.fte_load_background(bg, host)
+    torch.cuda.synchronize()
+    for _ in range(args.warmup):
+        one_step()
+    clocks = Clocks(local)
+    launches = []
+    steps_total = 0
+    barrier()
+    clocks.start()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.steps):
+        one_step(launches)
+        lw, ln = api.fte_ledger(tally) if ws == 1 else (None, tally.ledger_n.cpu().numpy())
+        steps_total += int(ln[6]) // (ws if ws > 1 else 1)
+    t1.record(stream)
+    barrier()
+    cl = clocks.stop()
+    ms = t0.elapsed_time(t1)
+    k_ms = sum(a.elapsed_time(b) for a, b in launches)
+    n_launch = len(launches)
+    ms_t = torch.tensor([ms, k_ms], dtype=torch.float64, device="cuda")
+    if ws > 1:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms, k_ms = ms_t.tolist()
+    total_steps = steps_total * ws
+    value = total_steps / (ms / 1e3)
+
+    # tally error: relative standard error of the observer's total occupancy
+    S = api.fte_tally(tally, 0, A.FTE_TALLY_S)
+    S2 = api.fte_tally(tally, 0, A.FTE_TALLY_S2)
+    rel_err = math.sqrt(S2.sum()) / S.sum() if S.sum() > 0 else None
+
+    # end-to-end arm: host buffers through the C ABI ---------------------------
+    out_host = np.zeros((w.observers[0].ne, w.observers[0].nt))
+
+    def e2e_step():
+        api.fte_load_background(bg, host)
+        one_step()
+        h = api.fte_tally(tally, 0, A.FTE_TALLY_S)
+        out_host[:] = h
+        return api.fte_ledger(tally)
+
+    for _ in range(1):
+        e2e_step()
+    barrier()
+    e0 = time.perf_counter()
+    e_steps = 0
+    for _ in range(args.steps):
+        lw, ln = e2e_step()
+        e_steps += int(ln[6]) // (ws if ws > 1 else 1)
+    barrier()
+    e_s = time.perf_counter() - e0
+    e_t = torch.tensor([e_s], dtype=torch.float64, device="cuda")
+    if ws > 1:
+        dist.all_reduce(e_t, op=dist.ReduceOp.MAX)
+    e2e_value = e_steps * ws / e_t.item()
+
+    peak, peak_kind = _peaks()
+    achieved = total_steps / ws * ALG_BYTES / (k_ms / 1e3) / 1e9
+    # kernels per step: inject, per launch (norm, step table, step kernel, reduce), 3 tally reads
+    launches_per_step = 1 + 4 * math.ceil(n_steps / CHUNK)
+    result = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "cir_uniform_1e6: synthetic CIR 512x60x180 grid, 24 hourly snapshots, "
+                               "1e6 protons at 50 keV in div V<0 cells (1-2 au, 90+-2 deg, w=1/r^2), "
+                               "QLT D_mumu q=5/3 H=0.05 lambda_par=0.1 au, dt=10 s x 34560 (4 days), "
+                               "1 au box tally 16x144",
+                   "particles_per_gpu": n_part, "steps_per_particle": n_steps,
+                   "background_bytes": int(bg.nbytes), "l2": "inputs larger than L2 (background 10.6 GB)",
+                   "tally_rel_err": rel_err},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(bg.nbytes),
+                "d2h_bytes_per_step": int(out_host.nbytes + 2 * 8 * A.FTE_LEDGER)},
+        "gpu_launches": launches_per_step * args.steps,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)",
+                     "kernel": "advance_kernel", "alg_bytes_per_particle_step": ALG_BYTES,
+                     "kernel_ms_total": k_ms, "kernel_launches": n_launch},
+        "clocks": cl,
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline(w, fields, budget_s=args.cpu_budget)
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# oracle arms (host cores)
+# ---------------------------------------------------------------------------
+def _oracle_sample(w, fields, n_sample, n_steps=None, threads=None):
+    from oracle import oracle as O
+    bg = O.grid_background(w.grid, fields)
+    ids = np.arange(n_sample, dtype=np.uint32)
+    P, led = O.inject(bg, w.inject, ids)
+    T = O.Tally(w.observers)
+    t = time.perf_counter()
+    O.advance(bg, w.params, P, 0, n_steps or w.n_steps, tally=T, ledger=led, threads=threads)
+    el = time.perf_counter() - t
+    return int(led.as_dict()["n"][6]), el
+
+
+def cpu_baseline(w, fields, budget_s=20.0):
+    from oracle import oracle as O
+    threads = O.lib().or_max_threads()
+    # calibrate on a tiny sample, then size the sample to ~budget_s of CPU work
+    s0, e0 = _oracle_sample(w, fields, 200, threads=threads)
+    rate = s0 / max(e0, 1e-6)
+    n = int(max(200, min(200_000, 200 * budget_s / max(e0, 1e-3))))
+    steps, el = _oracle_sample(w, fields, n, threads=threads)
+    return {"value": steps / el, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"first {n} of the workload's 1e6 particles over the full 4 days "
+                      f"({steps} alive particle-steps, {el:.1f} s)"}
+
+
+def run_reference(args):
+    ws, rank, local = _dist()
+    if rank != 0:
+        return
+    from oracle import build as ob
+    from oracle import oracle as O
+    ob.build()
+    w, fields = build_workload()
+    threads = O.lib().or_max_threads()
+    n_sample = int(os.environ.get("FTE_REF_SAMPLE", "5000"))
+    for _ in range(args.warmup):
+        _oracle_sample(w, fields, max(50, n_sample // 20), threads=threads)
+    total, el = 0, 0.0
+    for _ in range(args.steps):
+        s, e = _oracle_sample(w, fields, n_sample, threads=threads)
+        total += s
+        el += e
+    v = total / el
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "cir_uniform_1e6 (sampled: first %d particles per step, full 4 days)" % n_sample},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"{n_sample} particles x 4 days per step"},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

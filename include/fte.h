@@ -1,0 +1,239 @@
+/*
+ * fte.h - C ABI of the GB300 focused-transport particle pusher.
+ *
+ * The library integrates the focused transport equation (Husidic et al. 2024,
+ * Sec. 2.1, Eq. 1) for independent pseudo-particles as Ito stochastic
+ * differential equations forward in time, with the coefficients of Eq. 2 (dx/dt),
+ * Eq. 3 (dmu/dt) and Eq. 4 (dp/dt), pitch-angle diffusion D_mumu (Eq. 5 or the
+ * quasi-linear form of Sec. 2.1), optional cross-field diffusion (lambda_perp,
+ * Sec. 2.1), through gridded solar-wind snapshots that are located, read and
+ * interpolated trilinearly at every step (Sec. 2.4), with injection per Eq. 7
+ * and occupancy tallies of the intensity (Sec. 3, Figs. 5-8).
+ *
+ * Conventions
+ *   - Units: lengths au, times s, speeds au/s, B nT, energies MeV, momentum
+ *     p in units of m_p c.  Cartesian frame: z = rotation axis, theta
+ *     colatitude, phi longitude in [0, 2 pi).
+ *   - Memory: every pointer named "dev" / documented DEVICE is device memory
+ *     owned by the caller (the Python binding allocates it with PyTorch).  The
+ *     library allocates no device memory and keeps no state between calls.
+ *     Pointers documented HOST are host memory owned by the caller.
+ *   - Streams: `stream` is a cudaStream_t (NULL = legacy default stream).  All
+ *     work is enqueued asynchronously on it unless the call says it synchronises.
+ *   - Errors: every call returns an fte_status; on failure nothing was enqueued
+ *     unless stated, and fte_last_error() returns a message (thread-local, valid
+ *     until the next call on the same thread).  No C++ exception crosses the ABI.
+ *   - Random numbers: one Philox4x32-10 block (Salmon et al. 2011) per particle
+ *     and step, key (seed, set_id), counter (step, particle id, tag, 0); tag 0
+ *     transport, tag 1 injection draw, tag 2 injection position attempt.
+ *   - Time: step n is at t_n = t0 + n dt.  Time bin of an event at t:
+ *     floor(((t - t_lo) * nt) / (t_hi - t_lo)), evaluated in double precision.
+ */
+#ifndef FTE_H
+#define FTE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FTE_ABI_VERSION 1
+#define FTE_NFIELD 18          /* stored fields per cell */
+#define FTE_REC 20             /* floats per stored cell record (80 bytes) */
+#define FTE_MAX_OBS 8          /* observers per tally */
+#define FTE_LEDGER 8           /* ledger slots */
+
+typedef enum fte_status {
+    FTE_OK = 0,
+    FTE_EINVAL = 1,    /* invalid argument (null pointer, bad size, bad range) */
+    FTE_ENOMEM = 2,    /* a caller buffer is too small */
+    FTE_ECUDA = 3,     /* a CUDA runtime call failed */
+    FTE_ERANGE = 4,    /* injection found no acceptable position for some particles */
+    FTE_ENOTSUP = 5    /* configuration outside what this build supports */
+} fte_status;
+
+/* particle status codes (uint8 per particle) */
+enum { FTE_ALIVE = 0, FTE_ABS_INNER = 1, FTE_ABS_OUTER = 2, FTE_ABS_THETA = 3,
+       FTE_DEAD_NAN = 4, FTE_INJ_FAIL = 5 };
+/* ledger slots: weight (double) and count (uint64) per slot
+   0 injected; 1 absorbed at r_min; 2 absorbed at r_max; 3 absorbed at a theta
+   face; 4 non-finite state; 5 failed injections (count); 6 alive particle-steps
+   (count); 7 tally events inside an observer but outside its E/t range (count) */
+
+/* ---------------------------------------------------------------------------
+ * Background: spherical grid of cell-centred snapshots (Sec. 2.2-2.4).
+ * Cell k along an axis spans faces edge_k .. edge_{k+1}; r faces are uniform
+ * (radial = 0) or geometric (radial = 1, the radially stretched grid of Sec. 4);
+ * theta faces uniform on [th_min, th_max]; phi uniform and periodic on [0, 2 pi).
+ * Record layout (20 floats): 0-2 B, 3-5 V, 6-14 dV_i/dx_j (row i = component),
+ * 15-17 d|B|/dx_j, 18-19 unused.  Array order [snap][phi][theta][r][FTE_REC].
+ * Snapshot s holds the fields at t_snap0 + s dt_snap; between snapshots the
+ * fields are interpolated linearly in time and dV/dt gains (V_{s+1}-V_s)/dt_snap;
+ * periodic != 0 wraps the sequence; otherwise the fields are frozen (and
+ * dV/dt = 0) before the first and from the last snapshot on.
+ * ------------------------------------------------------------------------- */
+typedef struct fte_grid {
+    int32_t nr, nth, nph;      /* cells per axis, each >= 2 */
+    int32_t radial;            /* 0 linear, 1 logarithmic */
+    double r_min, r_max;       /* au, 0 < r_min < r_max; absorbing faces */
+    double th_min, th_max;     /* rad, 0 <= th_min < th_max <= pi; absorbing faces */
+    int32_t n_snap;            /* >= 1 */
+    int32_t periodic;
+    double t_snap0, dt_snap;   /* s; dt_snap > 0 when n_snap > 1 */
+} fte_grid;
+
+typedef struct fte_background {
+    fte_grid grid;
+    const float* fields;       /* DEVICE, fte_background_bytes(&grid) bytes, 16-byte aligned */
+} fte_background;
+
+/* Bytes of the device array holding all snapshots of `g` (0 if g is invalid). */
+size_t fte_background_bytes(const fte_grid* g);
+
+/* Validate `g` and copy `host_fields` (HOST, fte_background_bytes(g) bytes, in
+   the record layout above; page-locked memory makes the copy asynchronous) to
+   `dev_fields` (DEVICE, at least that many bytes).  EINVAL on an invalid grid or
+   null pointer, ENOMEM if dev_bytes is too small, ECUDA if the copy fails. */
+fte_status fte_load_background(const fte_grid* g, const float* host_fields, void* dev_fields,
+                               size_t dev_bytes, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Particle pool: structure of arrays in DEVICE memory, `capacity` entries each.
+ * `count` (host field) is the number of entries in use; fte_inject appends.
+ * ------------------------------------------------------------------------- */
+typedef struct fte_particles {
+    float *x, *y, *z;          /* position, au (inertial or snapshot frame) */
+    float *mu;                 /* pitch-angle cosine in the wind frame */
+    float *p;                  /* momentum, m_p c */
+    float *w;                  /* statistical weight */
+    uint32_t* id;              /* Philox counter word 1 */
+    uint8_t* status;           /* FTE_ALIVE ... */
+    uint64_t capacity;
+    uint64_t count;
+} fte_particles;
+
+/* ---------------------------------------------------------------------------
+ * Injection (Sec. 2.3, Eq. 7).  region 0: all at the point (r, th, ph); region 1:
+ * uniform in volume over r in [r1, r2], cos(theta) between cos th1 and cos th2,
+ * phi in [ph1, ph2], optionally accepting only positions whose containing cell
+ * of snapshot `divv_snap` has stored div V (dV_x/dx + dV_y/dy + dV_z/dz, summed in
+ * float in that order) < divv_max, with at most max_tries attempts per particle.
+ * energy 0: e0; energy 1: dN/dE ~ E^-gamma on [e1, e2] by inverse CDF.
+ * weight 0: 1; weight 1: 1/r^2 (r in au).  mu_mode 0: mu uniform in [-1, 1];
+ * 1: mu = mu0.  Particle ids are id_base + index within this call.
+ * ------------------------------------------------------------------------- */
+typedef struct fte_inject_spec {
+    int32_t region, energy, weight, mu_mode;
+    double r, th, ph;
+    double r1, r2, th1, th2, ph1, ph2;
+    int32_t use_divv, divv_snap, max_tries, pad0;
+    double divv_max;
+    double e0, e1, e2, gamma, mu0;
+    uint32_t seed, set_id;
+    uint32_t id_base, pad1;
+} fte_inject_spec;
+
+/* ---------------------------------------------------------------------------
+ * Transport parameters (Sec. 2.1).
+ * dmumu 0 quasi-linear: D = (nu/2)(1-mu^2)(|mu|^(q-1) + H), nu = 3 v I / (2 lambda),
+ *         I = int_0^1 (1-mu^2)/(mu^(q-1)+H) dmu; the factor |mu|^(q-2) of dD/dmu
+ *         uses max(|mu|, mu_floor)
+ *       1 Eq. 5: D = D0 (|mu|/(1+|mu|) + eps)(1-mu^2), D0 = 3 v J / (4 lambda),
+ *         J = int_0^1 (1-mu^2)/(mu/(1+mu)+eps) dmu
+ *       2 isotropic: D = (v / (2 lambda)) (1-mu^2)
+ * lambda = lambda_par (p / p_ref)^alpha when p_ref > 0 and alpha != 0, else lambda_par.
+ * Cross-field diffusion kappa_perp = (v lambda_perp / 3)(I - bb) when lambda_perp > 0,
+ * with Ito drift div(kappa_perp) when kappa_drift != 0.
+ * dvdt_term != 0 keeps the b.dV/dt terms of Eqs. 3-4.
+ * p_update 0: p' = p exp(pdot/p dt); 1: p' = p (1 + pdot/p dt).
+ * ------------------------------------------------------------------------- */
+typedef struct fte_params {
+    int32_t dmumu, p_update, kappa_drift, dvdt_term;
+    double lambda_par, p_ref, alpha, q, H, eps, mu_floor, lambda_perp;
+    double dt, t0;
+    uint32_t seed, set_id;
+} fte_params;
+
+/* ---------------------------------------------------------------------------
+ * Tallies.  An observer is kind 0 shell |r - r_o| <= dr; kind 1 box additionally
+ * |theta - th| <= dth and |phi - ph| <= dph (phi difference wrapped to [-pi, pi]);
+ * kind 2 slab |x - r| <= dr.  Bins: ne logarithmic energy bins on [e_lo, e_hi]
+ * (i_E = floor(ne ln(E/e_lo) / ln(e_hi/e_lo))) times nt time bins on [t_lo, t_hi).
+ * At every step, the start-of-step state of every alive particle inside an
+ * observer adds w dt to S, (w dt)^2 to S2 and 1 to C of its bin (occupancy
+ * estimator).  Accumulators are DEVICE arrays over all observers' bins,
+ * observer o starting at offset sum_{o' < o} ne*nt, bin index i_E * nt + i_t.
+ * ------------------------------------------------------------------------- */
+typedef struct fte_observer {
+    int32_t kind, ne, nt, pad;
+    double r, dr, th, dth, ph, dph;
+    double e_lo, e_hi, t_lo, t_hi;
+} fte_observer;
+
+typedef struct fte_tally_buf {
+    int32_t n_obs, pad;
+    fte_observer obs[FTE_MAX_OBS];
+    double* S;                        /* DEVICE, fte_tally_bins() doubles */
+    double* S2;                       /* DEVICE, fte_tally_bins() doubles */
+    unsigned long long* C;            /* DEVICE, fte_tally_bins() counts */
+    double* ledger_w;                 /* DEVICE, FTE_LEDGER doubles */
+    unsigned long long* ledger_n;     /* DEVICE, FTE_LEDGER counts */
+} fte_tally_buf;
+
+/* Total bins over all observers (0 if the tally description is invalid). */
+size_t fte_tally_bins(const fte_tally_buf* t);
+
+/* Zero S, S2, C and the ledger (asynchronous). */
+fte_status fte_tally_reset(const fte_tally_buf* t, void* stream);
+
+/* Scratch (DEVICE) needed by fte_advance for `t` and `n_steps` steps per call on
+   `device`: per-block partial histograms, launch counters, the per-step time
+   table and the normalisation constants.  0 on error. */
+size_t fte_workspace_bytes(int device, const fte_tally_buf* t, int64_t n_steps);
+
+/* Append n particles to P (requires P->count + n <= P->capacity) drawn per `spec`
+   on the device (Sec. 2.3, Eq. 7), positions in the frame of `bg`.  Adds the
+   injected weight to ledger slot 0 and failed injections to slot 5 of t.  On
+   success P->count += n.  If n_failed (HOST) is non-NULL the call synchronises
+   `stream`, stores the number of particles that found no acceptable position
+   (status FTE_INJ_FAIL, weight 0) and returns FTE_ERANGE if it is non-zero. */
+fte_status fte_inject(fte_particles* P, const fte_background* bg, const fte_inject_spec* spec,
+                      uint64_t n, const fte_tally_buf* t, uint64_t* n_failed, void* stream);
+
+/* Advance every alive particle of P from step n_start to step n_end (Sec. 2.1:
+   Euler-Maruyama steps of Eqs. 2-4 with the Ito drift of D_mumu, reflection at
+   mu = +-1, exponential momentum update; Sec. 2.4: trilinear interpolation of
+   the bracketing snapshots), tallying the start-of-step state of each step into
+   t and absorbing particles that leave [r_min, r_max] x [th_min, th_max] (ledger
+   slots 1-3).  ws (DEVICE, ws_bytes >= fte_workspace_bytes(device, t,
+   n_end - n_start)) is scratch; its contents on return are unspecified.
+   Asynchronous on `stream`. */
+fte_status fte_advance(fte_particles* P, const fte_background* bg, const fte_params* prm,
+                       const fte_tally_buf* t, int64_t n_start, int64_t n_end, void* ws,
+                       size_t ws_bytes, void* stream);
+
+/* Tally output kinds for fte_tally(). */
+enum { FTE_TALLY_S = 0, FTE_TALLY_S2 = 1, FTE_TALLY_C = 2, FTE_TALLY_INTENSITY = 3 };
+
+/* Write observer `obs`'s [ne][nt] array of `kind` as doubles to dev_out (DEVICE,
+   ne*nt doubles).  INTENSITY is j = S v(E_c) / (4 pi V_obs dt_bin dE) with E_c
+   the geometric bin centre and V_obs the observer volume (au^3; 2 dr for a slab):
+   particles / (au^2 s sr MeV) per unit weight.  If host_out (HOST, `bytes` >=
+   ne*nt*8) is non-NULL the array is also copied there and the call synchronises
+   `stream`. */
+fte_status fte_tally(const fte_tally_buf* t, int obs, int kind, double* dev_out, void* host_out,
+                     size_t bytes, void* stream);
+
+/* Copy the ledger to HOST arrays (FTE_LEDGER entries each); synchronises `stream`. */
+fte_status fte_ledger(const fte_tally_buf* t, double* host_w, uint64_t* host_n, void* stream);
+
+const char* fte_last_error(void);
+const char* fte_status_string(int status);
+int fte_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

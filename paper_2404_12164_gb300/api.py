@@ -1,0 +1,223 @@
+"""Python binding of the C ABI (argument marshalling only).
+
+Device memory is allocated with PyTorch and handed to the library as raw
+pointers; the CUDA stream is torch's current stream unless one is given.  The
+function names are those of include/fte.h; every computation runs in the
+library's kernels.
+"""
+import ctypes as C
+import math
+
+import numpy as np
+import torch
+
+from . import _abi as A
+from ._abi import check
+
+DEG = math.pi / 180.0
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+# ---------------------------------------------------------------------------
+# plain-data -> C struct conversions (fields follow fte_inputs.configs)
+# ---------------------------------------------------------------------------
+def grid_c(g):
+    c = A.fte_grid()
+    c.nr, c.nth, c.nph = g.nr, g.nth, g.nph
+    c.radial = 1 if g.radial == "log" else 0
+    c.r_min, c.r_max, c.th_min, c.th_max = g.r_min, g.r_max, g.th_min, g.th_max
+    c.n_snap, c.periodic = g.n_snap, int(bool(g.periodic))
+    c.t_snap0, c.dt_snap = g.t_snap0, g.dt_snap
+    return c
+
+
+def inject_c(s, id_base=0):
+    c = A.fte_inject_spec()
+    c.region = {"point": 0, "box": 1}[s.region]
+    c.energy = {"mono": 0, "powerlaw": 1}[s.energy]
+    c.weight = {"unit": 0, "r-2": 1}[s.weight]
+    c.mu_mode = {"isotropic": 0, "fixed": 1}[s.mu]
+    c.r, c.th, c.ph = s.r, s.th, s.ph
+    c.r1, c.r2, c.th1, c.th2, c.ph1, c.ph2 = s.r1, s.r2, s.th1, s.th2, s.ph1, s.ph2
+    c.use_divv = 0 if s.divv_max is None else 1
+    c.divv_snap, c.max_tries = s.divv_snap, s.max_tries
+    c.divv_max = 0.0 if s.divv_max is None else s.divv_max
+    c.e0, c.e1, c.e2, c.gamma, c.mu0 = s.e0, s.e1, s.e2, s.gamma, s.mu0
+    c.seed, c.set_id = s.seed & 0xFFFFFFFF, s.set_id & 0xFFFFFFFF
+    c.id_base = id_base
+    return c
+
+
+def params_c(p):
+    c = A.fte_params()
+    c.dmumu = {"qlt": 0, "paper": 1, "iso": 2}[p.dmumu]
+    c.p_update = 0 if p.p_update == "exp" else 1
+    c.kappa_drift, c.dvdt_term = int(p.kappa_drift), int(p.dvdt_term)
+    c.lambda_par, c.p_ref, c.alpha = p.lambda_par, p.p_ref, p.alpha
+    c.q, c.H, c.eps, c.mu_floor, c.lambda_perp = p.q, p.H, p.eps, p.mu_floor, p.lambda_perp
+    c.dt, c.t0 = p.dt, p.t0
+    c.seed, c.set_id = p.seed & 0xFFFFFFFF, p.set_id & 0xFFFFFFFF
+    return c
+
+
+def observer_c(o):
+    c = A.fte_observer()
+    c.kind = {"shell": 0, "box": 1, "slab": 2}[o.kind]
+    c.ne, c.nt = o.ne, o.nt
+    c.r, c.dr, c.th, c.dth, c.ph, c.dph = o.r, o.dr, o.th, o.dth, o.ph, o.dph
+    c.e_lo, c.e_hi, c.t_lo, c.t_hi = o.e_lo, o.e_hi, o.t_lo, o.t_hi
+    return c
+
+
+# ---------------------------------------------------------------------------
+# device-memory holders
+# ---------------------------------------------------------------------------
+class Background:
+    """Device copy of a snapshot sequence (fte_background)."""
+
+    def __init__(self, grid, device="cuda"):
+        self.grid = grid
+        self.gc = grid_c(grid)
+        nbytes = A.lib().fte_background_bytes(C.byref(self.gc))
+        if nbytes == 0:
+            raise ValueError("invalid grid")
+        self.nbytes = nbytes
+        self.dev = torch.empty(nbytes // 4, dtype=torch.float32, device=device)
+        self.c = A.fte_background(self.gc, self.dev.data_ptr())
+
+
+def fte_load_background(bg, host_fields, stream=None):
+    """Copy host snapshot data (numpy float32 or CPU tensor, record layout) into bg."""
+    if isinstance(host_fields, np.ndarray):
+        host = np.ascontiguousarray(host_fields, dtype=np.float32)
+        ptr, n = host.ctypes.data, host.nbytes
+    else:
+        assert host_fields.dtype == torch.float32 and host_fields.device.type == "cpu"
+        host = host_fields.contiguous()
+        ptr, n = host.data_ptr(), host.numel() * 4
+    if n != bg.nbytes:
+        raise ValueError(f"host data has {n} bytes, the grid needs {bg.nbytes}")
+    check(A.lib().fte_load_background(C.byref(bg.gc), C.c_void_p(ptr), C.c_void_p(bg.dev.data_ptr()),
+                                      bg.nbytes, _stream(stream)), "fte_load_background")
+    return host
+
+
+class Particles:
+    """Device particle pool (fte_particles, structure of arrays)."""
+
+    def __init__(self, capacity, device="cuda"):
+        f = lambda: torch.zeros(capacity, dtype=torch.float32, device=device)
+        self.x, self.y, self.z, self.mu, self.p, self.w = f(), f(), f(), f(), f(), f()
+        self.id = torch.zeros(capacity, dtype=torch.int32, device=device)
+        self.status = torch.full((capacity,), A.FTE_INJ_FAIL, dtype=torch.uint8, device=device)
+        self.c = A.fte_particles(self.x.data_ptr(), self.y.data_ptr(), self.z.data_ptr(),
+                                 self.mu.data_ptr(), self.p.data_ptr(), self.w.data_ptr(),
+                                 self.id.data_ptr(), self.status.data_ptr(), capacity, 0)
+
+    @property
+    def count(self):
+        return self.c.count
+
+    def state(self):
+        """Host copy of the used part of the pool as a dict of numpy arrays."""
+        n = self.count
+        out = {k: getattr(self, k)[:n].cpu().numpy() for k in ("x", "y", "z", "mu", "p", "w")}
+        out["id"] = self.id[:n].cpu().numpy().view(np.uint32)
+        out["status"] = self.status[:n].cpu().numpy()
+        return out
+
+
+class Tally:
+    """Device tally accumulators and ledger (fte_tally_buf)."""
+
+    def __init__(self, observers, device="cuda"):
+        self.observers = list(observers)
+        if len(self.observers) > A.FTE_MAX_OBS:
+            raise ValueError("too many observers")
+        self.nb = [o.ne * o.nt for o in self.observers]
+        n = max(sum(self.nb), 1)
+        self.S = torch.zeros(n, dtype=torch.float64, device=device)
+        self.S2 = torch.zeros(n, dtype=torch.float64, device=device)
+        self.C = torch.zeros(n, dtype=torch.int64, device=device)
+        self.ledger_w = torch.zeros(A.FTE_LEDGER, dtype=torch.float64, device=device)
+        self.ledger_n = torch.zeros(A.FTE_LEDGER, dtype=torch.int64, device=device)
+        self.out = torch.zeros(max(self.nb + [1]), dtype=torch.float64, device=device)
+        c = A.fte_tally_buf()
+        c.n_obs = len(self.observers)
+        for i, o in enumerate(self.observers):
+            c.obs[i] = observer_c(o)
+        c.S, c.S2, c.C = self.S.data_ptr(), self.S2.data_ptr(), self.C.data_ptr()
+        c.ledger_w, c.ledger_n = self.ledger_w.data_ptr(), self.ledger_n.data_ptr()
+        self.c = c
+
+
+class Workspace:
+    """Device scratch for fte_advance, grown on demand."""
+
+    def __init__(self, device="cuda"):
+        self.device = device
+        self.buf = torch.empty(0, dtype=torch.uint8, device=device)
+
+    def ensure(self, nbytes):
+        if self.buf.numel() < nbytes:
+            self.buf = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        return self.buf
+
+
+# ---------------------------------------------------------------------------
+# the C ABI, one wrapper per entry point
+# ---------------------------------------------------------------------------
+def fte_workspace_bytes(tally, n_steps, device=None):
+    dev = torch.cuda.current_device() if device is None else device
+    n = A.lib().fte_workspace_bytes(dev, C.byref(tally.c), int(n_steps))
+    if n == 0:
+        raise RuntimeError("fte_workspace_bytes: " + A.lib().fte_last_error().decode())
+    return n
+
+
+def fte_tally_reset(tally, stream=None):
+    check(A.lib().fte_tally_reset(C.byref(tally.c), _stream(stream)), "fte_tally_reset")
+
+
+def fte_inject(pool, bg, spec, n, tally, id_base=None, check_failed=True, stream=None):
+    """Append n particles drawn per `spec`; returns the number of failed injections
+    (None if check_failed is False, in which case the call does not synchronise)."""
+    base = pool.count if id_base is None else id_base
+    sc = inject_c(spec, base)
+    nf = C.c_uint64(0)
+    st = A.lib().fte_inject(C.byref(pool.c), C.byref(bg.c), C.byref(sc), int(n), C.byref(tally.c),
+                            C.byref(nf) if check_failed else None, _stream(stream))
+    if st == A.FTE_ERANGE:
+        return nf.value
+    check(st, "fte_inject")
+    return nf.value if check_failed else None
+
+
+def fte_advance(pool, bg, params, tally, n_start, n_end, ws=None, stream=None):
+    ws = ws if ws is not None else Workspace(bg.dev.device)
+    buf = ws.ensure(fte_workspace_bytes(tally, n_end - n_start, bg.dev.device.index))
+    pc = params_c(params)
+    check(A.lib().fte_advance(C.byref(pool.c), C.byref(bg.c), C.byref(pc), C.byref(tally.c),
+                              int(n_start), int(n_end), C.c_void_p(buf.data_ptr()), buf.numel(),
+                              _stream(stream)), "fte_advance")
+    return ws
+
+
+def fte_tally(tally, obs, kind=A.FTE_TALLY_S, stream=None):
+    """Observer `obs`'s [ne, nt] array of `kind` (S, S2, C or INTENSITY) on the host."""
+    ob = tally.observers[obs]
+    host = np.zeros((ob.ne, ob.nt), dtype=np.float64)
+    check(A.lib().fte_tally(C.byref(tally.c), int(obs), int(kind), C.c_void_p(tally.out.data_ptr()),
+                            C.c_void_p(host.ctypes.data), host.nbytes, _stream(stream)), "fte_tally")
+    return host
+
+
+def fte_ledger(tally, stream=None):
+    w = (C.c_double * A.FTE_LEDGER)()
+    n = (C.c_uint64 * A.FTE_LEDGER)()
+    check(A.lib().fte_ledger(C.byref(tally.c), w, n, _stream(stream)), "fte_ledger")
+    return np.array(w), np.array(n, dtype=np.uint64)

@@ -1,0 +1,436 @@
+// C ABI of the focused-transport pusher: argument validation, workspace
+// layout and kernel launches.  No device memory is allocated here; every
+// buffer comes from the caller.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include "fte_kernels.cuh"
+
+using namespace fte;
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+fte_status fail(fte_status s, const char* fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return s;
+}
+
+fte_status cuda_fail(cudaError_t e, const char* what)
+{
+    return fail(FTE_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define FTE_CUDA(call, what)                      \
+    do {                                          \
+        cudaError_t e_ = (call);                  \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+const double kPiD = 3.141592653589793;
+
+fte_status check_grid(const fte_grid* g)
+{
+    if (!g) return fail(FTE_EINVAL, "grid is NULL");
+    if (g->nr < 2 || g->nth < 2 || g->nph < 2) return fail(FTE_EINVAL, "grid needs >= 2 cells per axis");
+    if (g->radial != 0 && g->radial != 1) return fail(FTE_EINVAL, "radial must be 0 or 1");
+    if (!(g->r_min > 0.0 && g->r_max > g->r_min)) return fail(FTE_EINVAL, "need 0 < r_min < r_max");
+    if (!(g->th_min >= 0.0 && g->th_max > g->th_min && g->th_max <= kPiD + 1e-12))
+        return fail(FTE_EINVAL, "need 0 <= th_min < th_max <= pi");
+    if (g->n_snap < 1) return fail(FTE_EINVAL, "n_snap must be >= 1");
+    if (g->n_snap > 1 && !(g->dt_snap > 0.0)) return fail(FTE_EINVAL, "dt_snap must be > 0");
+    const double cells = (double)g->nr * g->nth * g->nph * g->n_snap;
+    if (cells * FTE_REC > 9.0e18 / 4.0) return fail(FTE_EINVAL, "grid too large");
+    return FTE_OK;
+}
+
+size_t grid_bytes(const fte_grid* g)
+{
+    return (size_t)g->nr * g->nth * g->nph * (size_t)g->n_snap * FTE_REC * sizeof(float);
+}
+
+GridK make_gridk(const fte_background* bg)
+{
+    const fte_grid& g = bg->grid;
+    GridK k;
+    k.fields = reinterpret_cast<const float4*>(bg->fields);
+    k.snap_recs = (long long)g.nr * g.nth * g.nph;
+    k.nr = g.nr; k.nth = g.nth; k.nph = g.nph; k.radial = g.radial;
+    k.r_min = (float)g.r_min; k.r_max = (float)g.r_max;
+    k.th_min = (float)g.th_min; k.th_max = (float)g.th_max;
+    if (g.radial) {
+        const double dl = log(g.r_max / g.r_min) / g.nr;
+        k.dr = (float)dl;
+        k.inv_dr = (float)(1.0 / dl);
+    } else {
+        k.dr = (float)((g.r_max - g.r_min) / g.nr);
+        k.inv_dr = (float)(g.nr / (g.r_max - g.r_min));
+    }
+    k.dth = (float)((g.th_max - g.th_min) / g.nth);
+    k.inv_dth = (float)(g.nth / (g.th_max - g.th_min));
+    k.inv_dph = (float)(g.nph / (2.0 * kPiD));
+    k.inv_dt_snap = g.n_snap > 1 ? (float)(1.0 / g.dt_snap) : 0.f;
+    return k;
+}
+
+fte_status check_background(const fte_background* bg)
+{
+    if (!bg) return fail(FTE_EINVAL, "background is NULL");
+    fte_status s = check_grid(&bg->grid);
+    if (s != FTE_OK) return s;
+    if (!bg->fields) return fail(FTE_EINVAL, "background fields pointer is NULL");
+    if ((uintptr_t)bg->fields % 16) return fail(FTE_EINVAL, "background fields must be 16-byte aligned");
+    return FTE_OK;
+}
+
+fte_status check_tally(const fte_tally_buf* t, size_t* nbins)
+{
+    if (!t) return fail(FTE_EINVAL, "tally is NULL");
+    if (t->n_obs < 0 || t->n_obs > FTE_MAX_OBS) return fail(FTE_EINVAL, "n_obs must be in [0, %d]", FTE_MAX_OBS);
+    size_t nb = 0;
+    for (int o = 0; o < t->n_obs; ++o) {
+        const fte_observer& ob = t->obs[o];
+        if (ob.kind < 0 || ob.kind > 2) return fail(FTE_EINVAL, "observer %d: bad kind", o);
+        if (ob.ne < 1 || ob.nt < 1 || ob.nt > 32767) return fail(FTE_EINVAL, "observer %d: bad bin counts", o);
+        if (!(ob.e_lo > 0.0 && ob.e_hi > ob.e_lo)) return fail(FTE_EINVAL, "observer %d: need 0 < e_lo < e_hi", o);
+        if (!(ob.t_hi > ob.t_lo)) return fail(FTE_EINVAL, "observer %d: need t_lo < t_hi", o);
+        if (!(ob.dr >= 0.0)) return fail(FTE_EINVAL, "observer %d: dr < 0", o);
+        nb += (size_t)ob.ne * ob.nt;
+    }
+    if (!t->ledger_w || !t->ledger_n) return fail(FTE_EINVAL, "ledger pointers are NULL");
+    if (nb && (!t->S || !t->S2 || !t->C)) return fail(FTE_EINVAL, "tally accumulator pointers are NULL");
+    *nbins = nb;
+    return FTE_OK;
+}
+
+// Layout of the fte_advance workspace.
+struct WsLayout {
+    size_t off_fetch, off_norm, off_table, off_part, total;
+    int blocks;
+};
+
+constexpr int kMaxSmemBins = 16384;    // 3 x 4 B per bin in shared memory
+constexpr long long kChunkSteps = 1024;
+
+int device_sms(int device)
+{
+    static int cache[64];
+    if (device < 0 || device >= 64) return 0;
+    if (!cache[device]) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return 0;
+        cache[device] = v;
+    }
+    return cache[device];
+}
+
+fte_status layout(int device, int kperp, size_t nbins, long long n_steps, WsLayout* L)
+{
+    const int sms = device_sms(device);
+    if (sms <= 0) return fail(FTE_ECUDA, "cannot query device %d", device);
+    const size_t smem = 3 * sizeof(float) * (nbins ? nbins : 1);
+    int per_sm = 0;
+    int cur = 0;
+    FTE_CUDA(cudaGetDevice(&cur), "cudaGetDevice");
+    if (cur != device) FTE_CUDA(cudaSetDevice(device), "cudaSetDevice");
+    cudaError_t e = advance_occupancy(kperp, smem, &per_sm);
+    if (cur != device) cudaSetDevice(cur);
+    if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
+    if (per_sm < 1) return fail(FTE_ENOTSUP, "step kernel does not fit on an SM with %zu bytes of tally", smem);
+    L->blocks = sms * per_sm;
+    size_t off = 0;
+    L->off_fetch = off; off += 64;
+    L->off_norm = off; off += 64;
+    L->off_table = off; off += (size_t)(n_steps > 0 ? n_steps : 1) * sizeof(StepEntry);
+    off = (off + 255) & ~(size_t)255;
+    L->off_part = off; off += (size_t)L->blocks * 3 * (nbins ? nbins : 1) * sizeof(float);
+    L->total = off;
+    return FTE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* fte_last_error(void) { return g_err; }
+
+const char* fte_status_string(int s)
+{
+    switch (s) {
+    case FTE_OK: return "ok";
+    case FTE_EINVAL: return "invalid argument";
+    case FTE_ENOMEM: return "buffer too small";
+    case FTE_ECUDA: return "CUDA error";
+    case FTE_ERANGE: return "injection region has no acceptable position";
+    case FTE_ENOTSUP: return "not supported";
+    default: return "unknown status";
+    }
+}
+
+int fte_abi_version(void) { return FTE_ABI_VERSION; }
+
+size_t fte_background_bytes(const fte_grid* g)
+{
+    if (check_grid(g) != FTE_OK) return 0;
+    return grid_bytes(g);
+}
+
+fte_status fte_load_background(const fte_grid* g, const float* host_fields, void* dev_fields,
+                               size_t dev_bytes, void* stream)
+{
+    fte_status s = check_grid(g);
+    if (s != FTE_OK) return s;
+    if (!host_fields || !dev_fields) return fail(FTE_EINVAL, "NULL field pointer");
+    if ((uintptr_t)dev_fields % 16) return fail(FTE_EINVAL, "device fields must be 16-byte aligned");
+    const size_t need = grid_bytes(g);
+    if (dev_bytes < need) return fail(FTE_ENOMEM, "device buffer has %zu bytes, needs %zu", dev_bytes, need);
+    FTE_CUDA(cudaMemcpyAsync(dev_fields, host_fields, need, cudaMemcpyHostToDevice, (cudaStream_t)stream),
+             "background copy");
+    return FTE_OK;
+}
+
+size_t fte_tally_bins(const fte_tally_buf* t)
+{
+    size_t nb = 0;
+    if (!t || t->n_obs < 0 || t->n_obs > FTE_MAX_OBS) return 0;
+    for (int o = 0; o < t->n_obs; ++o) {
+        if (t->obs[o].ne < 1 || t->obs[o].nt < 1) return 0;
+        nb += (size_t)t->obs[o].ne * t->obs[o].nt;
+    }
+    return nb;
+}
+
+fte_status fte_tally_reset(const fte_tally_buf* t, void* stream)
+{
+    size_t nb = 0;
+    fte_status s = check_tally(t, &nb);
+    if (s != FTE_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (nb) {
+        FTE_CUDA(cudaMemsetAsync(t->S, 0, nb * sizeof(double), st), "memset S");
+        FTE_CUDA(cudaMemsetAsync(t->S2, 0, nb * sizeof(double), st), "memset S2");
+        FTE_CUDA(cudaMemsetAsync(t->C, 0, nb * sizeof(unsigned long long), st), "memset C");
+    }
+    FTE_CUDA(cudaMemsetAsync(t->ledger_w, 0, FTE_LEDGER * sizeof(double), st), "memset ledger");
+    FTE_CUDA(cudaMemsetAsync(t->ledger_n, 0, FTE_LEDGER * sizeof(unsigned long long), st), "memset ledger");
+    return FTE_OK;
+}
+
+size_t fte_workspace_bytes(int device, const fte_tally_buf* t, int64_t n_steps)
+{
+    size_t nb = 0;
+    if (check_tally(t, &nb) != FTE_OK || n_steps < 0) return 0;
+    if (nb > (size_t)kMaxSmemBins) return 0;
+    WsLayout L0, L1;
+    if (layout(device, 0, nb, n_steps, &L0) != FTE_OK) return 0;
+    if (layout(device, 1, nb, n_steps, &L1) != FTE_OK) return 0;
+    return L0.total > L1.total ? L0.total : L1.total;
+}
+
+fte_status fte_inject(fte_particles* P, const fte_background* bg, const fte_inject_spec* spec,
+                      uint64_t n, const fte_tally_buf* t, uint64_t* n_failed, void* stream)
+{
+    if (!P || !spec) return fail(FTE_EINVAL, "NULL particles or spec");
+    fte_status s = check_background(bg);
+    if (s != FTE_OK) return s;
+    size_t nb = 0;
+    s = check_tally(t, &nb);
+    if (s != FTE_OK) return s;
+    if (!P->x || !P->y || !P->z || !P->mu || !P->p || !P->w || !P->id || !P->status)
+        return fail(FTE_EINVAL, "NULL particle array");
+    if (P->count + n > P->capacity) return fail(FTE_ENOMEM, "pool capacity %llu < %llu", (unsigned long long)P->capacity,
+                                                (unsigned long long)(P->count + n));
+    if (spec->region != 0 && spec->region != 1) return fail(FTE_EINVAL, "bad region");
+    if (spec->energy != 0 && spec->energy != 1) return fail(FTE_EINVAL, "bad energy mode");
+    if (spec->energy == 0 && !(spec->e0 > 0)) return fail(FTE_EINVAL, "e0 must be > 0");
+    if (spec->energy == 1 && !(spec->e1 > 0 && spec->e2 > spec->e1)) return fail(FTE_EINVAL, "need 0 < e1 < e2");
+    if (spec->region == 1) {
+        if (!(spec->r2 > spec->r1 && spec->r1 > 0)) return fail(FTE_EINVAL, "need 0 < r1 < r2");
+        if (spec->max_tries < 1) return fail(FTE_EINVAL, "max_tries must be >= 1");
+        if (spec->use_divv && (spec->divv_snap < 0 || spec->divv_snap >= bg->grid.n_snap))
+            return fail(FTE_EINVAL, "divv_snap out of range");
+    }
+    if (spec->mu_mode == 1 && !(spec->mu0 >= -1.0 && spec->mu0 <= 1.0)) return fail(FTE_EINVAL, "mu0 outside [-1, 1]");
+    if ((uint64_t)spec->id_base + n > 0x100000000ull) return fail(FTE_EINVAL, "particle ids exceed 32 bits");
+    if (n == 0) {
+        if (n_failed) *n_failed = 0;
+        return FTE_OK;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned long long before = 0;
+    if (n_failed) FTE_CUDA(cudaMemcpyAsync(&before, t->ledger_n + 5, sizeof(before), cudaMemcpyDeviceToHost, st), "ledger read");
+    InjectArgs a;
+    memset(&a, 0, sizeof(a));
+    a.g = make_gridk(bg);
+    a.n_snap = bg->grid.n_snap;
+    a.region = spec->region; a.energy = spec->energy; a.weight = spec->weight; a.mu_mode = spec->mu_mode;
+    a.use_divv = spec->use_divv; a.divv_snap = spec->divv_snap; a.max_tries = spec->max_tries;
+    a.r = (float)spec->r; a.th = (float)spec->th; a.ph = (float)spec->ph;
+    a.r1 = (float)spec->r1; a.r2 = (float)spec->r2; a.th1 = (float)spec->th1; a.th2 = (float)spec->th2;
+    a.ph1 = (float)spec->ph1; a.ph2 = (float)spec->ph2; a.divv_max = (float)spec->divv_max;
+    a.e0 = (float)spec->e0; a.e1 = (float)spec->e1; a.e2 = (float)spec->e2; a.gamma = (float)spec->gamma;
+    a.mu0 = (float)spec->mu0;
+    a.seed = spec->seed; a.set_id = spec->set_id; a.id_base = spec->id_base;
+    a.offset = P->count; a.n = n;
+    a.x = P->x; a.y = P->y; a.z = P->z; a.mu = P->mu; a.p = P->p; a.w = P->w; a.id = P->id; a.status = P->status;
+    a.ledger_w = t->ledger_w; a.ledger_n = t->ledger_n;
+    FTE_CUDA(launch_inject(a, st), "inject launch");
+    P->count += n;
+    if (n_failed) {
+        unsigned long long after = 0;
+        FTE_CUDA(cudaMemcpyAsync(&after, t->ledger_n + 5, sizeof(after), cudaMemcpyDeviceToHost, st), "ledger read");
+        FTE_CUDA(cudaStreamSynchronize(st), "stream sync");
+        *n_failed = after - before;
+        if (after != before) return fail(FTE_ERANGE, "%llu particles found no acceptable position", after - before);
+    }
+    return FTE_OK;
+}
+
+fte_status fte_advance(fte_particles* P, const fte_background* bg, const fte_params* prm,
+                       const fte_tally_buf* t, int64_t n_start, int64_t n_end, void* ws,
+                       size_t ws_bytes, void* stream)
+{
+    if (!P || !prm) return fail(FTE_EINVAL, "NULL particles or params");
+    fte_status s = check_background(bg);
+    if (s != FTE_OK) return s;
+    size_t nb = 0;
+    s = check_tally(t, &nb);
+    if (s != FTE_OK) return s;
+    if (nb > (size_t)kMaxSmemBins) return fail(FTE_ENOTSUP, "%zu tally bins exceed %d", nb, kMaxSmemBins);
+    if (n_end < n_start || n_start < 0) return fail(FTE_EINVAL, "need 0 <= n_start <= n_end");
+    if (n_end > 0xFFFFFFFFll) return fail(FTE_EINVAL, "step index exceeds 32 bits");
+    if (!(prm->dt > 0.0)) return fail(FTE_EINVAL, "dt must be > 0");
+    if (!(prm->lambda_par > 0.0)) return fail(FTE_EINVAL, "lambda_par must be > 0");
+    if (prm->dmumu < 0 || prm->dmumu > 2) return fail(FTE_EINVAL, "bad dmumu model");
+    if (prm->dmumu == 0 && !(prm->q > 1.0 && prm->q <= 2.0 && prm->H >= 0.0)) return fail(FTE_EINVAL, "need 1 < q <= 2, H >= 0");
+    if (prm->dmumu == 1 && !(prm->eps > 0.0)) return fail(FTE_EINVAL, "eps must be > 0");
+    if (prm->lambda_perp < 0.0) return fail(FTE_EINVAL, "lambda_perp must be >= 0");
+    if (!ws) return fail(FTE_EINVAL, "NULL workspace");
+    if (!P->x || !P->y || !P->z || !P->mu || !P->p || !P->w || !P->id || !P->status)
+        return fail(FTE_EINVAL, "NULL particle array");
+    if (n_end == n_start || P->count == 0) return FTE_OK;
+
+    int device = 0;
+    FTE_CUDA(cudaGetDevice(&device), "cudaGetDevice");
+    const int kperp = prm->lambda_perp > 0.0 ? 1 : 0;
+    const long long nsteps = n_end - n_start;
+    WsLayout L;
+    s = layout(device, kperp, nb, nsteps, &L);
+    if (s != FTE_OK) return s;
+    if (ws_bytes < L.total) return fail(FTE_ENOMEM, "workspace has %zu bytes, needs %zu", ws_bytes, L.total);
+    char* w = (char*)ws;
+    cudaStream_t st = (cudaStream_t)stream;
+
+    double* norm = (double*)(w + L.off_norm);
+    FTE_CUDA(launch_norm(prm->dmumu, prm->q, prm->H, prm->eps, norm, st), "norm launch");
+
+    StepTableArgs ta;
+    memset(&ta, 0, sizeof(ta));
+    ta.tab = (StepEntry*)(w + L.off_table);
+    ta.n0 = n_start; ta.count = nsteps; ta.t0 = prm->t0; ta.dt = prm->dt;
+    ta.n_snap = bg->grid.n_snap; ta.periodic = bg->grid.periodic;
+    ta.t_snap0 = bg->grid.t_snap0; ta.dt_snap = bg->grid.dt_snap;
+    ta.n_obs = t->n_obs;
+    for (int o = 0; o < t->n_obs; ++o) {
+        ta.ot[o].t_lo = t->obs[o].t_lo; ta.ot[o].t_hi = t->obs[o].t_hi; ta.ot[o].nt = t->obs[o].nt;
+    }
+    FTE_CUDA(launch_step_table(ta, st), "step table launch");
+
+    AdvanceArgs a;
+    memset(&a, 0, sizeof(a));
+    a.g = make_gridk(bg);
+    a.prm.dmumu = prm->dmumu; a.prm.p_update = prm->p_update; a.prm.kappa_drift = prm->kappa_drift;
+    a.prm.dvdt_term = prm->dvdt_term;
+    a.prm.use_rig = (prm->p_ref > 0.0 && prm->alpha != 0.0) ? 1 : 0;
+    a.prm.lambda_par = (float)prm->lambda_par; a.prm.p_ref = (float)prm->p_ref; a.prm.alpha = (float)prm->alpha;
+    a.prm.q = (float)prm->q; a.prm.H = (float)prm->H; a.prm.eps = (float)prm->eps;
+    a.prm.mu_floor = (float)prm->mu_floor; a.prm.lambda_perp = (float)prm->lambda_perp;
+    a.prm.dt = (float)prm->dt; a.prm.seed = prm->seed; a.prm.set_id = prm->set_id;
+    size_t off = 0;
+    for (int o = 0; o < t->n_obs; ++o) {
+        const fte_observer& ob = t->obs[o];
+        ObsK& k = a.obs[o];
+        k.kind = ob.kind; k.ne = ob.ne; k.nt = ob.nt; k.off = (int)off;
+        k.r = (float)ob.r; k.dr = (float)ob.dr; k.th = (float)ob.th; k.dth = (float)ob.dth;
+        k.ph = (float)ob.ph; k.dph = (float)ob.dph;
+        k.e_lo = (float)ob.e_lo; k.ne_over_lnratio = (float)(ob.ne / log(ob.e_hi / ob.e_lo));
+        off += (size_t)ob.ne * ob.nt;
+    }
+    a.n_obs = t->n_obs;
+    a.nbins = (int)(nb ? nb : 1);
+    a.x = P->x; a.y = P->y; a.z = P->z; a.mu = P->mu; a.p = P->p; a.w = P->w; a.id = P->id; a.status = P->status;
+    a.n_particles = P->count;
+    a.n_table0 = n_start;
+    a.table = ta.tab;
+    a.norm = norm;
+    a.part = (float*)(w + L.off_part);
+    a.fetch = (unsigned long long*)(w + L.off_fetch);
+    a.ledger_w = t->ledger_w; a.ledger_n = t->ledger_n;
+
+    // Grid: an equal number of particles per thread (no partial last wave).
+    const unsigned long long lanes = (unsigned long long)L.blocks * kThreads;
+    const unsigned long long per = (P->count + lanes - 1) / lanes;
+    const unsigned long long threads = (P->count + per - 1) / per;
+    int blocks = (int)((threads + kThreads - 1) / kThreads);
+    if (blocks > L.blocks) blocks = L.blocks;
+    if (blocks < 1) blocks = 1;
+    const size_t smem = 3 * sizeof(float) * (size_t)a.nbins;
+    int per_sm = 0;
+    FTE_CUDA(advance_occupancy(kperp, smem, &per_sm), "occupancy");
+
+    for (long long c0 = n_start; c0 < n_end; c0 += kChunkSteps) {
+        a.n_start = c0;
+        a.n_end = (c0 + kChunkSteps < n_end) ? c0 + kChunkSteps : n_end;
+        FTE_CUDA(cudaMemsetAsync(a.fetch, 0, sizeof(unsigned long long), st), "fetch reset");
+        FTE_CUDA(launch_advance(a, kperp, blocks, smem, st), "step kernel launch");
+        if (nb) FTE_CUDA(launch_reduce(a.part, blocks, (int)nb, t->S, t->S2, t->C, st), "reduce launch");
+    }
+    return FTE_OK;
+}
+
+fte_status fte_tally(const fte_tally_buf* t, int obs, int kind, double* dev_out, void* host_out,
+                     size_t bytes, void* stream)
+{
+    size_t nb = 0;
+    fte_status s = check_tally(t, &nb);
+    if (s != FTE_OK) return s;
+    if (obs < 0 || obs >= t->n_obs) return fail(FTE_EINVAL, "observer %d out of range", obs);
+    if (kind < FTE_TALLY_S || kind > FTE_TALLY_INTENSITY) return fail(FTE_EINVAL, "bad tally kind");
+    if (!dev_out) return fail(FTE_EINVAL, "NULL device output");
+    const fte_observer& ob = t->obs[obs];
+    const size_t n = (size_t)ob.ne * ob.nt;
+    if (host_out && bytes < n * sizeof(double)) return fail(FTE_ENOMEM, "host buffer too small");
+    ObsOut o;
+    o.kind = ob.kind; o.ne = ob.ne; o.nt = ob.nt;
+    size_t off = 0;
+    for (int k = 0; k < obs; ++k) off += (size_t)t->obs[k].ne * t->obs[k].nt;
+    o.off = (int)off;
+    o.r = ob.r; o.dr = ob.dr; o.th = ob.th; o.dth = ob.dth; o.dph = ob.dph;
+    o.e_lo = ob.e_lo; o.e_hi = ob.e_hi; o.t_lo = ob.t_lo; o.t_hi = ob.t_hi;
+    cudaStream_t st = (cudaStream_t)stream;
+    FTE_CUDA(launch_tally_out(t->S, t->S2, t->C, o, kind, dev_out, st), "tally output launch");
+    if (host_out) {
+        FTE_CUDA(cudaMemcpyAsync(host_out, dev_out, n * sizeof(double), cudaMemcpyDeviceToHost, st), "tally copy");
+        FTE_CUDA(cudaStreamSynchronize(st), "stream sync");
+    }
+    return FTE_OK;
+}
+
+fte_status fte_ledger(const fte_tally_buf* t, double* host_w, uint64_t* host_n, void* stream)
+{
+    if (!t || !t->ledger_w || !t->ledger_n || !host_w || !host_n) return fail(FTE_EINVAL, "NULL pointer");
+    cudaStream_t st = (cudaStream_t)stream;
+    FTE_CUDA(cudaMemcpyAsync(host_w, t->ledger_w, FTE_LEDGER * sizeof(double), cudaMemcpyDeviceToHost, st), "ledger copy");
+    FTE_CUDA(cudaMemcpyAsync(host_n, t->ledger_n, FTE_LEDGER * sizeof(uint64_t), cudaMemcpyDeviceToHost, st), "ledger copy");
+    FTE_CUDA(cudaStreamSynchronize(st), "stream sync");
+    return FTE_OK;
+}
+
+}  // extern "C"

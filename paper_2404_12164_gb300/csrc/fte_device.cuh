@@ -1,0 +1,242 @@
+// Device-side building blocks of the focused-transport pusher (sm_103a).
+//
+// One thread owns one pseudo-particle and keeps its state in registers for
+// every step of a launch.  Per step it locates the particle on the spherical
+// grid, gathers the 8 surrounding cell records of the two bracketing snapshots
+// (Sec. 2.4: trilinear interpolation of the surrounding grid values; linear in
+// time between snapshots), forms the coefficients of Eqs. 3-4, draws one
+// Philox4x32-10 block and applies one Euler-Maruyama step of the Ito SDEs
+// (Sec. 2.1).  All arithmetic is FP32 except the per-step time table, which is
+// built in FP64 by a separate kernel.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fte.h"
+
+namespace fte {
+
+constexpr float kPi = 3.14159265358979f;
+constexpr float kTwoPi = 6.28318530717959f;
+constexpr float kCau = 2.003988804e-3f;      // speed of light, au/s
+constexpr float kMc2 = 938.27208816f;        // proton rest energy, MeV
+constexpr int kThreads = 256;                // threads per block of the step kernel
+
+// ---------------------------------------------------------------------------
+// Kernel-side descriptions (passed by value in the kernel parameter space)
+// ---------------------------------------------------------------------------
+struct GridK {
+    const float4* fields;    // record r of snapshot s at fields[(s * snap_recs + r) * 5]
+    long long snap_recs;     // records per snapshot
+    int nr, nth, nph, radial;
+    float r_min, r_max, th_min, th_max;
+    float inv_dr;            // linear: nr / (r_max - r_min); log: nr / ln(r_max / r_min)
+    float dr;                // linear: (r_max - r_min) / nr; log: ln(r_max / r_min) / nr
+    float inv_dth, dth, inv_dph;
+    float inv_dt_snap;
+};
+
+struct ParamsK {
+    int dmumu, p_update, kappa_drift, dvdt_term;
+    int use_rig;
+    float lambda_par, p_ref, alpha, q, H, eps, mu_floor, lambda_perp, dt;
+    uint32_t seed, set_id;
+};
+
+struct ObsK {
+    int kind, ne, nt, off;
+    float r, dr, th, dth, ph, dph;
+    float e_lo, ne_over_lnratio;   // i_E = floor(ln(E / e_lo) * ne / ln(e_hi / e_lo))
+};
+
+// Per-step entry of the time table (built in FP64 by step_table_kernel).
+struct StepEntry {
+    int s0, s1;              // bracketing snapshots
+    float wt;                // weight of s1
+    int two;                 // 1: two snapshots and dV/dt from their difference
+    short it[FTE_MAX_OBS];   // time bin per observer, -1 outside [t_lo, t_hi)
+};
+static_assert(sizeof(StepEntry) == 32, "StepEntry layout");
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two 32x32
+// multiplications (high words mixed into the other lanes with the round key),
+// the key advanced by the Weyl increments between rounds.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k)
+{
+#pragma unroll
+    for (int i = 0; i < 10; ++i) {
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+        k.x += 0x9E3779B9u;
+        k.y += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// 32-bit word -> uniform in (0, 1): ((x >> 8) + 1/2) 2^-24, exact in FP32.
+__device__ __forceinline__ float u01(uint32_t x)
+{
+    return (float)(x >> 8) * (1.0f / 16777216.0f) + (0.5f / 16777216.0f);
+}
+
+// ---------------------------------------------------------------------------
+// Kinematics: p in m_p c; v = c p / gamma; E = m c^2 p^2 / (gamma + 1).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float speed_of(float p) { return kCau * p * rsqrtf(fmaf(p, p, 1.0f)); }
+__device__ __forceinline__ float energy_of(float p)
+{
+    const float g = sqrtf(fmaf(p, p, 1.0f));
+    return kMc2 * p * p / (g + 1.0f);
+}
+
+// ---------------------------------------------------------------------------
+// Pitch-angle diffusion coefficient and its mu derivative (Eq. 5 and the
+// quasi-linear / isotropic alternatives).  `I` is the normalisation integral.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void dmumu(const ParamsK& P, float I, float mu, float v, float p,
+                                      float& D, float& dD)
+{
+    const float lam = P.use_rig ? P.lambda_par * powf(p / P.p_ref, P.alpha) : P.lambda_par;
+    const float am = fabsf(mu);
+    const float sg = (mu > 0.f) ? 1.f : ((mu < 0.f) ? -1.f : 0.f);
+    const float omm = 1.f - mu * mu;
+    if (P.dmumu == 0) {
+        const float nu = 3.f * v * I / (2.f * lam);
+        const float g = powf(am, P.q - 1.f) + P.H;
+        const float dg = (P.q - 1.f) * powf(fmaxf(am, P.mu_floor), P.q - 2.f) * sg;
+        D = 0.5f * nu * omm * g;
+        dD = 0.5f * nu * (-2.f * mu * g + omm * dg);
+    } else if (P.dmumu == 1) {
+        const float D0 = 3.f * v * I / (4.f * lam);
+        const float h = am / (1.f + am) + P.eps;
+        const float dh = sg / ((1.f + am) * (1.f + am));
+        D = D0 * h * omm;
+        dD = D0 * (dh * omm - 2.f * mu * h);
+    } else {
+        const float Dc = v / (2.f * lam);
+        D = Dc * omm;
+        dD = -2.f * mu * Dc;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Grid location: bracketing cell centres and weights along each axis.
+// Beyond the outermost centres in r and theta the field is held constant.
+// ---------------------------------------------------------------------------
+struct Loc {
+    int i0, j0, k0, k1;
+    float fr, ft, fp;        // weights of the upper neighbour
+    float dfr, dft, dfp;     // d(weight)/d(coordinate); 0 where clamped
+};
+
+__device__ __forceinline__ void locate(const GridK& g, float r, float th, float ph, Loc& L)
+{
+    float xi = g.radial ? logf(r / g.r_min) * g.inv_dr - 0.5f : (r - g.r_min) * g.inv_dr - 0.5f;
+    if (xi < 0.f) {
+        L.i0 = 0; L.fr = 0.f; L.dfr = 0.f;
+    } else if (xi >= (float)(g.nr - 1)) {
+        L.i0 = g.nr - 2; L.fr = 1.f; L.dfr = 0.f;
+    } else {
+        L.i0 = (int)xi;
+        if (g.radial) {
+            const float c0 = g.r_min * expf(((float)L.i0 + 0.5f) * g.dr);
+            const float c1 = g.r_min * expf(((float)L.i0 + 1.5f) * g.dr);
+            L.dfr = 1.f / (c1 - c0);
+            L.fr = (r - c0) * L.dfr;
+        } else {
+            L.fr = xi - (float)L.i0;
+            L.dfr = g.inv_dr;
+        }
+    }
+    xi = (th - g.th_min) * g.inv_dth - 0.5f;
+    if (xi < 0.f) {
+        L.j0 = 0; L.ft = 0.f; L.dft = 0.f;
+    } else if (xi >= (float)(g.nth - 1)) {
+        L.j0 = g.nth - 2; L.ft = 1.f; L.dft = 0.f;
+    } else {
+        L.j0 = (int)xi;
+        L.ft = xi - (float)L.j0;
+        L.dft = g.inv_dth;
+    }
+    xi = ph * g.inv_dph - 0.5f;
+    const float kf = floorf(xi);
+    L.fp = xi - kf;
+    L.dfp = g.inv_dph;
+    int k0 = (int)kf;
+    if (k0 < 0) k0 += g.nph;
+    if (k0 >= g.nph) k0 -= g.nph;
+    L.k0 = k0;
+    L.k1 = (k0 + 1 == g.nph) ? 0 : k0 + 1;
+}
+
+// Interpolated background at the particle (18 fields, dV/dt partial, and the
+// axis derivatives of B when the cross-field drift is on).
+template <bool KPERP>
+struct Fields {
+    float f[FTE_NFIELD];
+    float dv[3];             // sum_c w_c (V_s1 - V_s0): times 1/dt_snap gives dV/dt
+    float dBa[KPERP ? 9 : 1];  // dB_i / d(weight axis a), a = r, theta, phi
+};
+
+template <bool KPERP>
+__device__ __forceinline__ void gather(const GridK& g, const StepEntry& e, const Loc& L,
+                                       Fields<KPERP>& F)
+{
+#pragma unroll
+    for (int m = 0; m < FTE_NFIELD; ++m) F.f[m] = 0.f;
+#pragma unroll
+    for (int m = 0; m < 3; ++m) F.dv[m] = 0.f;
+    if (KPERP) {
+#pragma unroll
+        for (int m = 0; m < 9; ++m) F.dBa[m] = 0.f;
+    }
+    const int ns = e.two ? 2 : 1;
+    for (int s = 0; s < ns; ++s) {
+        const int snap = s ? e.s1 : e.s0;
+        const float ws = e.two ? (s ? e.wt : 1.f - e.wt) : 1.f;
+        const float sgn = s ? 1.f : -1.f;
+        const float4* base = g.fields + (long long)snap * g.snap_recs * 5;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int ct = c & 1, cp = c >> 1;
+            const int j = L.j0 + ct;
+            const int k = cp ? L.k1 : L.k0;
+            const float wt_ = ct ? L.ft : 1.f - L.ft;
+            const float wp_ = cp ? L.fp : 1.f - L.fp;
+            const float wjk = wt_ * wp_;
+            const float4* q = base + (((long long)k * g.nth + j) * g.nr + L.i0) * 5;
+            float a[40];
+#pragma unroll
+            for (int m = 0; m < 10; ++m) {
+                const float4 v = __ldg(q + m);
+                a[4 * m + 0] = v.x; a[4 * m + 1] = v.y; a[4 * m + 2] = v.z; a[4 * m + 3] = v.w;
+            }
+            const float w0 = (1.f - L.fr) * wjk, w1 = L.fr * wjk;
+#pragma unroll
+            for (int m = 0; m < FTE_NFIELD; ++m) F.f[m] += ws * (w0 * a[m] + w1 * a[FTE_REC + m]);
+            if (e.two) {
+#pragma unroll
+                for (int m = 0; m < 3; ++m) F.dv[m] += sgn * (w0 * a[3 + m] + w1 * a[FTE_REC + 3 + m]);
+            }
+            if (KPERP) {
+                const float er = L.dfr * wjk;                          // d w / d r
+                const float et = (ct ? 1.f : -1.f) * L.dft * wp_;      // d w / d theta (x w_r)
+                const float ep = (cp ? 1.f : -1.f) * L.dfp * wt_;      // d w / d phi   (x w_r)
+#pragma unroll
+                for (int m = 0; m < 3; ++m) {
+                    const float lo = a[m], hi = a[FTE_REC + m];
+                    const float mix = (1.f - L.fr) * lo + L.fr * hi;
+                    F.dBa[3 * m + 0] += ws * er * (hi - lo);
+                    F.dBa[3 * m + 1] += ws * et * mix;
+                    F.dBa[3 * m + 2] += ws * ep * mix;
+                }
+            }
+        }
+    }
+}
+
+}  // namespace fte

@@ -1,0 +1,72 @@
+// Kernel declarations and launch arguments shared by the API and kernel files.
+#pragma once
+
+#include "fte_device.cuh"
+
+namespace fte {
+
+struct AdvanceArgs {
+    GridK g;
+    ParamsK prm;
+    ObsK obs[FTE_MAX_OBS];
+    int n_obs, nbins;
+    float *x, *y, *z, *mu, *p, *w;
+    const uint32_t* id;
+    uint8_t* status;
+    unsigned long long n_particles;
+    long long n_start, n_end;     // steps advanced by this launch
+    long long n_table0;           // step index of table[0]
+    const StepEntry* table;
+    const double* norm;           // normalisation integral of D_mumu
+    float* part;                  // per-block partial histograms [grid][3][nbins]
+    unsigned long long* fetch;    // particle counter for dynamic assignment
+    double* ledger_w;
+    unsigned long long* ledger_n;
+};
+
+struct ObsTime {
+    double t_lo, t_hi;
+    int nt, pad;
+};
+
+struct StepTableArgs {
+    StepEntry* tab;
+    long long n0, count;
+    double t0, dt;
+    int n_snap, periodic;
+    double t_snap0, dt_snap;
+    int n_obs, pad;
+    ObsTime ot[FTE_MAX_OBS];
+};
+
+struct ObsOut {
+    int kind, ne, nt, off;
+    double r, dr, th, dth, dph;
+    double e_lo, e_hi, t_lo, t_hi;
+};
+
+struct InjectArgs {
+    GridK g;
+    int n_snap, region, energy, weight, mu_mode, use_divv, divv_snap, max_tries;
+    float r, th, ph, r1, r2, th1, th2, ph1, ph2, divv_max, e0, e1, e2, gamma, mu0;
+    uint32_t seed, set_id, id_base;
+    unsigned long long offset, n;
+    float *x, *y, *z, *mu, *p, *w;
+    uint32_t* id;
+    uint8_t* status;
+    double* ledger_w;
+    unsigned long long* ledger_n;
+};
+
+// launchers (return cudaGetLastError())
+cudaError_t launch_advance(const AdvanceArgs& a, int kperp, int blocks, size_t smem, cudaStream_t s);
+cudaError_t launch_reduce(const float* part, int nblk, int nbins, double* S, double* S2,
+                          unsigned long long* C, cudaStream_t s);
+cudaError_t launch_step_table(const StepTableArgs& a, cudaStream_t s);
+cudaError_t launch_norm(int model, double q, double H, double eps, double* out, cudaStream_t s);
+cudaError_t launch_tally_out(const double* S, const double* S2, const unsigned long long* C,
+                             const ObsOut& ob, int kind, double* out, cudaStream_t s);
+cudaError_t launch_inject(const InjectArgs& a, cudaStream_t s);
+cudaError_t advance_occupancy(int kperp, size_t smem, int* blocks_per_sm);
+
+}  // namespace fte

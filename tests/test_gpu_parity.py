@@ -1,0 +1,246 @@
+"""GPU (C ABI) vs FP64 oracle parity on identical seeded inputs.
+
+Tolerances (FP32 device arithmetic against the FP64 oracle):
+* per trajectory, up to the first divergence event the oracle records
+  (reflection, mu sign change, a boundary or acceptance decision within
+  rounding): position within 1e-4 of r, mu within 1e-4, p within 1e-4 relative;
+* injection: mu bit-exact (one Philox draw, exact FP32 uniform), positions 1e-5;
+* tally counts: exact for deterministic trajectories except events the oracle
+  flags within 1e-4 of a bin or observer edge;
+* tally sums: every bin within 3 sigma (sigma^2 = S2_gpu + S2_oracle).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from fte_inputs import configs
+from fte_inputs.configs import InjectSpec, Observer, Params
+from tests._parity import gpu_run, oracle_run, trajectory_errors
+
+pytestmark = pytest.mark.gpu
+
+DEG = math.pi / 180
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2404_12164_gb300 import build
+    build.build()
+    from oracle import build as ob
+    ob.build()
+
+
+@pytest.fixture(scope="module")
+def parker():
+    w = configs.scaled(configs.parker_1e4(), n_particles=6000)
+    return w, configs.build_background(w)
+
+
+@pytest.fixture(scope="module")
+def cir_small():
+    w = configs.scaled(configs.cir_uniform_1e6(), nr=128, nth=30, nph=90, n_particles=4000)
+    return w, configs.build_background(w)
+
+
+def _assert_traj(g, o, step, tol=1e-4, min_matched=200):
+    ok, e = trajectory_errors(g, o, step)
+    assert ok.sum() >= min_matched, f"only {ok.sum()} matched trajectories at step {step}"
+    for k in ("pos", "mu", "p", "w"):
+        assert e[k].max() <= tol, (step, k, float(e[k].max()), float(np.percentile(e[k], 99)))
+    assert e["status"].sum() == 0, (step, "status")
+
+
+def test_injection_point_mu_bitexact(parker):
+    w, f = parker
+    g = gpu_run(w, f, 0, chunks=[])["states"][0]
+    o = oracle_run(w, f, 0, chunks=[])["states"][0]
+    assert np.array_equal(g["mu"], o["mu"].astype(np.float32))
+    assert np.array_equal(g["id"], o["id"])
+    assert np.allclose(g["p"], o["p"], rtol=1e-6)
+    assert np.allclose(g["x"], o["x"], rtol=1e-6, atol=1e-7)
+    assert np.abs(g["y"]).max() < 1e-7 and np.abs(g["z"]).max() < 1e-7
+    assert np.all(g["status"] == 0) and np.all(g["w"] == 1.0)
+
+
+def test_injection_box_divv(cir_small):
+    w, f = cir_small
+    gr = gpu_run(w, f, 0, chunks=[])
+    orr = oracle_run(w, f, 0, chunks=[])
+    g, o = gr["states"][0], orr["states"][0]
+    assert gr["failed"] == 0
+    clean = (o["flags"] & 1) == 0
+    assert clean.mean() > 0.9
+    r_o = np.sqrt(o["x"] ** 2 + o["y"] ** 2 + o["z"] ** 2)
+    dx = np.sqrt((g["x"] - o["x"]) ** 2 + (g["y"] - o["y"]) ** 2 + (g["z"] - o["z"]) ** 2) / r_o
+    assert dx[clean].max() < 1e-5
+    assert np.abs(g["w"] - o["w"])[clean].max() / o["w"].max() < 1e-5
+    assert np.array_equal(g["mu"], o["mu"].astype(np.float32))
+    assert np.array_equal(g["status"], o["status"].astype(np.uint8))
+    # injected weight in the ledger
+    assert gr["ledger_w"][0] == pytest.approx(g["w"].astype(np.float64).sum(), rel=1e-12)
+    assert gr["ledger_w"][0] == pytest.approx(orr["ledger_w"][0], rel=1e-5)
+
+
+def test_trajectories_parker_qlt(parker):
+    w, f = parker
+    chunks = [1, 10, 60, 250, 700]
+    g = gpu_run(w, f, 0, chunks=chunks)["states"]
+    o = oracle_run(w, f, 0, chunks=chunks)["states"]
+    for c in chunks:
+        _assert_traj(g[c], o[c], c)
+
+
+def test_trajectories_cir_time_interpolated(cir_small):
+    w, f = cir_small
+    chunks = [1, 37, 400, 800]          # crosses the first snapshot boundary (360 steps)
+    g = gpu_run(w, f, 0, chunks=chunks)["states"]
+    o = oracle_run(w, f, 0, chunks=chunks)["states"]
+    for c in chunks:
+        _assert_traj(g[c], o[c], c)
+
+
+@pytest.mark.parametrize("model", ["paper", "iso"])
+def test_trajectories_other_dmumu_log_grid(model):
+    w = configs.scaled(configs.parker_1e4(), n_particles=3000)
+    w.grid.radial = "log"
+    w.params = Params(dmumu=model, lambda_par=0.3, dt=10.0, seed=7)
+    f = configs.build_background(w)
+    chunks = [5, 120, 400]
+    g = gpu_run(w, f, 0, chunks=chunks)["states"]
+    o = oracle_run(w, f, 0, chunks=chunks)["states"]
+    for c in chunks:
+        _assert_traj(g[c], o[c], c)
+
+
+def test_trajectories_cross_field_diffusion(parker):
+    w, f = parker
+    prm = Params(dmumu="qlt", lambda_par=0.3, lambda_perp=3e-4, kappa_drift=1, dt=10.0, seed=3)
+    chunks = [3, 100, 400]
+    g = gpu_run(w, f, 0, chunks=chunks, params=prm)["states"]
+    o = oracle_run(w, f, 0, chunks=chunks, params=prm)["states"]
+    for c in chunks:
+        _assert_traj(g[c], o[c], c)
+
+
+def test_counts_exact_for_deterministic_trajectories():
+    """No scattering (D = 0): trajectories never diverge, so every tally count must match
+    except events the oracle flags within 1e-4 of an energy-bin or observer edge."""
+    w = configs.scaled(configs.parker_1e4(), n_particles=4000)
+    w.inject = InjectSpec(region="box", r1=0.8, r2=1.2, th1=80 * DEG, th2=100 * DEG, ph1=0.0,
+                          ph2=2 * math.pi, energy="powerlaw", e1=0.02, e2=0.8, gamma=1.5, seed=5)
+    w.params = Params(dmumu="iso", lambda_par=1e30, dt=10.0)
+    obs = [Observer(kind="shell", r=1.0, dr=0.05, e_lo=0.01, e_hi=1.0, ne=16, t_lo=0.0,
+                    t_hi=20000.0, nt=40),
+           Observer(kind="box", r=1.1, dr=0.05, th=90 * DEG, dth=8 * DEG, ph=1.0, dph=20 * DEG,
+                    e_lo=0.01, e_hi=1.0, ne=8, t_lo=0.0, t_hi=20000.0, nt=20)]
+    f = configs.build_background(w)
+    g = gpu_run(w, f, 2000, observers=obs)
+    o = oracle_run(w, f, 2000, observers=obs)
+    for k in range(len(obs)):
+        Cg = g["tallies"][k]["C"].astype(np.int64)
+        Co = o["tallies"][k]["C"].astype(np.int64)
+        A = o["tallies"][k]["A"].astype(np.int64)
+        assert Co.sum() > 1000
+        amb = A.copy()
+        amb[1:] += A[:-1]
+        amb[:-1] += A[1:]
+        assert np.all(np.abs(Cg - Co) <= amb), np.abs(Cg - Co).max()
+        assert np.array_equal(Cg[amb == 0], Co[amb == 0])
+        assert np.abs(Cg - Co).sum() <= 2 * A.sum()
+
+
+def test_tallies_within_three_sigma(parker):
+    w, f = parker
+    obs = [Observer(kind="shell", r=0.5, dr=0.05, e_lo=0.01, e_hi=1.0, ne=16, t_lo=0.0,
+                    t_hi=30000.0, nt=30)]
+    g = gpu_run(w, f, 3000, observers=obs)
+    o = oracle_run(w, f, 3000, observers=obs)
+    tg, to = g["tallies"][0], o["tallies"][0]
+    assert to["C"].sum() > 10000
+    sig = np.sqrt(tg["S2"] + to["S2"])
+    assert np.all(np.abs(tg["S"] - to["S"]) <= 3 * sig + 1e-9 * to["S"].max())
+    # intensity normalisation is the same function of S on both sides
+    nz = to["S"] > 0
+    assert np.allclose(tg["J"][nz] / tg["S"][nz], to["J"][nz] / to["S"][nz], rtol=1e-12)
+    # total occupancy agrees to a few per cent of its own statistical error
+    tot_sig = math.sqrt(tg["S2"].sum() + to["S2"].sum())
+    assert abs(tg["S"].sum() - to["S"].sum()) < 3 * tot_sig
+
+
+def test_ledger_conservation(cir_small):
+    w, f = cir_small
+    g = gpu_run(w, f, 1500)
+    st = g["states"][1500]
+    lw, ln = g["ledger_w"], g["ledger_n"]
+    alive = st["status"] == 0
+    assert int(ln[0]) == w.n_particles
+    assert int(ln[0]) == alive.sum() + int(ln[1:5].sum())
+    for k in (1, 2, 3):
+        assert int(ln[k]) == (st["status"] == k).sum()
+    total = st["w"][alive].astype(np.float64).sum() + lw[1:5].sum()
+    assert total == pytest.approx(lw[0], rel=1e-12)
+    assert 0 < int(ln[6]) <= w.n_particles * 1500
+
+
+def test_chunking_is_bitwise_invariant(parker):
+    w, f = parker
+    a = gpu_run(w, f, 300, chunks=[300])["states"][300]
+    b = gpu_run(w, f, 300, chunks=[17, 100, 300])["states"][300]
+    for k in ("x", "y", "z", "mu", "p", "w", "status"):
+        assert np.array_equal(a[k], b[k]), k
+
+
+@pytest.mark.parametrize("n", [1, 31, 257, 1000])
+def test_ragged_particle_counts(parker, n):
+    w, f = parker
+    g = gpu_run(w, f, 50, n_particles=n)["states"][50]
+    o = oracle_run(w, f, 50, n_particles=n)["states"][50]
+    ok, e = trajectory_errors(g, o, 50)
+    assert ok.sum() >= 1 or n == 1
+    for k in ("pos", "mu", "p"):
+        assert (e[k].max() if e[k].size else 0) <= 1e-4
+
+
+def test_empty_and_zero_step_calls(parker):
+    import torch
+    from paper_2404_12164_gb300 import api
+    w, f = parker
+    bg = api.Background(w.grid)
+    api.fte_load_background(bg, f)
+    pool = api.Particles(16)
+    tally = api.Tally(w.observers)
+    api.fte_tally_reset(tally)
+    api.fte_advance(pool, bg, w.params, tally, 0, 100)       # empty pool
+    assert api.fte_inject(pool, bg, w.inject, 0, tally) == 0
+    api.fte_inject(pool, bg, w.inject, 16, tally)
+    before = pool.state()
+    api.fte_advance(pool, bg, w.params, tally, 5, 5)         # zero steps
+    after = pool.state()
+    for k in ("x", "mu", "p"):
+        assert np.array_equal(before[k], after[k])
+    lw, ln = api.fte_ledger(tally)
+    assert int(ln[6]) == 0 and int(ln[0]) == 16
+    torch.cuda.synchronize()
+
+
+def test_failed_injection_reported():
+    from paper_2404_12164_gb300 import api
+    w = configs.scaled(configs.parker_1e4(), n_particles=64)
+    w.inject = InjectSpec(region="box", r1=0.5, r2=1.0, th1=80 * DEG, th2=100 * DEG,
+                          divv_max=0.0, max_tries=8)        # Parker: div V > 0 everywhere
+    f = configs.build_background(w)
+    bg = api.Background(w.grid)
+    api.fte_load_background(bg, f)
+    pool = api.Particles(64)
+    tally = api.Tally(w.observers)
+    api.fte_tally_reset(tally)
+    assert api.fte_inject(pool, bg, w.inject, 64, tally) == 64
+    st = pool.state()
+    assert np.all(st["status"] == 5) and np.all(st["w"] == 0)
+    api.fte_advance(pool, bg, w.params, tally, 0, 10)        # nothing alive to advance
+    lw, ln = api.fte_ledger(tally)
+    assert int(ln[5]) == 64 and int(ln[0]) == 0 and int(ln[6]) == 0
