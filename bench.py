@@ -325,8 +325,34 @@ def run_reference(args):
     }), flush=True)
 
 
+def run_profile_case(args):
+    """Small case of the same kernels for ncu captures: the full-resolution CIR grid with two
+    snapshots (884 MB, larger than L2), 2^18 particles, a few launches of 256 steps."""
+    import torch
+    from paper_2404_12164_gb300 import api, build
+    build.build()
+    torch.cuda.set_device(0)
+    w = configs.scaled(configs.cir_uniform_1e6(), n_snap=2, n_particles=1 << 18)
+    fields = configs.build_background(w)
+    bg = api.Background(w.grid)
+    api.fte_load_background(bg, fields)
+    pool = api.Particles(w.n_particles)
+    tally = api.Tally(w.observers)
+    api.fte_tally_reset(tally)
+    api.fte_inject(pool, bg, w.inject, w.n_particles, tally)
+    wsp = api.Workspace()
+    for c in range(args.launches):
+        api.fte_advance(pool, bg, w.params, tally, 256 * c, 256 * (c + 1), wsp)
+    lw, ln = api.fte_ledger(tally)
+    torch.cuda.synchronize()
+    print(json.dumps({"case": "profile", "launches": args.launches, "particle_steps": int(ln[6]),
+                      "alg_bytes": int(ln[6]) * ALG_BYTES}))
+
+
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--case", default="bench", choices=["bench", "profile"])
+    ap.add_argument("--launches", type=int, default=3)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
@@ -334,7 +360,9 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.case == "profile":
+        run_profile_case(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_gpu(args)

@@ -77,10 +77,17 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k)
     return c;
 }
 
-// 32-bit word -> uniform in (0, 1): ((x >> 8) + 1/2) 2^-24, exact in FP32.
+// 32-bit word -> uniform in (0, 1): ((x >> 8) + 1/2) 2^-24 (25 significant bits,
+// rounded to nearest in FP32).
 __device__ __forceinline__ float u01(uint32_t x)
 {
     return (float)(x >> 8) * (1.0f / 16777216.0f) + (0.5f / 16777216.0f);
+}
+
+// 2 u - 1 for the same word, exactly: (2 (x >> 8) + 1 - 2^24) 2^-24 has at most 24 bits.
+__device__ __forceinline__ float u11(uint32_t x)
+{
+    return (float)((int)((x >> 8) << 1) + 1 - (1 << 24)) * (1.0f / 16777216.0f);
 }
 
 // ---------------------------------------------------------------------------

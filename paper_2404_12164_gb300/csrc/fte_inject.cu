@@ -30,7 +30,7 @@ __global__ void __launch_bounds__(256) inject_kernel(const InjectArgs a)
         const uint32_t pid = a.id_base + (uint32_t)i;
         const uint2 key = make_uint2(a.seed, a.set_id);
         const uint4 d = philox4x32_10(make_uint4(0u, pid, 1u, 0u), key);
-        const float mu = a.mu_mode ? a.mu0 : 2.f * u01(d.x) - 1.f;
+        const float mu = a.mu_mode ? a.mu0 : u11(d.x);
         float E;
         if (a.energy == 0) {
             E = a.e0;
