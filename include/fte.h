@@ -214,6 +214,21 @@ fte_status fte_advance(fte_particles* P, const fte_background* bg, const fte_par
                        const fte_tally_buf* t, int64_t n_start, int64_t n_end, void* ws,
                        size_t ws_bytes, void* stream);
 
+/* Allocation-free variant of fte_advance (the paper has no counterpart: this is
+   an interface for callers that cannot allocate device memory at run time, such
+   as a host code whose own allocator owns all of the GPU's memory, or a service
+   that must not call cudaMalloc once running).  Same arguments, results and
+   stream semantics as fte_advance, but without the workspace: the scratch is a
+   24 MiB array that the library places in device memory statically, held by
+   every GPU that loads the library until the process exits.  The first call on
+   a device (with that device current) looks up the array's device address;
+   make that first call before any stream capture.  All calls share the array:
+   calls whose work overlaps on the GPU race on it.  Returns FTE_ENOMEM when the
+   tally's per-block partial histograms (12 bytes per bin) do not fit the array
+   for at least one block per SM (about 13,800 bins on a 152-SM GB300). */
+fte_status fte_advance_noalloc(fte_particles* P, const fte_background* bg, const fte_params* prm,
+                               const fte_tally_buf* t, int64_t n_start, int64_t n_end, void* stream);
+
 /* Tally output kinds for fte_tally(). */
 enum { FTE_TALLY_S = 0, FTE_TALLY_S2 = 1, FTE_TALLY_C = 2, FTE_TALLY_INTENSITY = 3 };
 

@@ -85,6 +85,8 @@ SIGNATURES = {
     "fte_advance": (C.c_int, [_P(fte_particles), _P(fte_background), _P(fte_params),
                               _P(fte_tally_buf), C.c_int64, C.c_int64, C.c_void_p, C.c_size_t,
                               C.c_void_p]),
+    "fte_advance_noalloc": (C.c_int, [_P(fte_particles), _P(fte_background), _P(fte_params),
+                                      _P(fte_tally_buf), C.c_int64, C.c_int64, C.c_void_p]),
     "fte_tally": (C.c_int, [_P(fte_tally_buf), C.c_int, C.c_int, C.c_void_p, C.c_void_p,
                             C.c_size_t, C.c_void_p]),
     "fte_ledger": (C.c_int, [_P(fte_tally_buf), _P(C.c_double), _P(C.c_uint64), C.c_void_p]),

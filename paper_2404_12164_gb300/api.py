@@ -207,6 +207,14 @@ def fte_advance(pool, bg, params, tally, n_start, n_end, ws=None, stream=None):
     return ws
 
 
+def fte_advance_noalloc(pool, bg, params, tally, n_start, n_end, stream=None):
+    """fte_advance without a workspace: the library's own statically placed
+    device scratch is used, for callers that cannot allocate device memory."""
+    pc = params_c(params)
+    check(A.lib().fte_advance_noalloc(C.byref(pool.c), C.byref(bg.c), C.byref(pc), C.byref(tally.c),
+                                      int(n_start), int(n_end), _stream(stream)), "fte_advance_noalloc")
+
+
 def fte_tally(tally, obs, kind=A.FTE_TALLY_S, stream=None):
     """Observer `obs`'s [ne, nt] array of `kind` (S, S2, C or INTENSITY) on the host."""
     ob = tally.observers[obs]

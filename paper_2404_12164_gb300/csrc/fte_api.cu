@@ -434,3 +434,159 @@ fte_status fte_ledger(const fte_tally_buf* t, double* host_w, uint64_t* host_n, 
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of fte_advance.
+//
+// Some callers cannot hand the library a scratch buffer: a host code that has
+// reserved all device memory for its own pool at start-up, or a service that
+// must not call cudaMalloc once it runs (the call can synchronise the device
+// and can fail under memory pressure).  For them the scratch of the step loop
+// lives in this file-scope device array.  Every GPU that loads the library
+// holds it until the process exits.  All calls share it, so two calls whose
+// work overlaps on the GPU (for example on two streams) race on it; it keeps
+// the contents of the last call, and every value that must start at zero is
+// cleared by the call itself.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+namespace {
+
+constexpr size_t kNoAllocBytes = 24u << 20;           // 24 MiB of scratch per device
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[64];
+
+// Device address of the scratch array for the current device, looked up once
+// per device (the host-side name of the array is not a device address).
+fte_status noalloc_scratch(int device, char** out)
+{
+    if (device < 0 || device >= 64) return fail(FTE_ENOTSUP, "device index %d out of range", device);
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[device]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(scratch)");
+        g_noalloc_ptr[device] = p;
+    }
+    *out = (char*)g_noalloc_ptr[device];
+    return FTE_OK;
+}
+
+}  // namespace
+
+extern "C" fte_status fte_advance_noalloc(fte_particles* P, const fte_background* bg,
+                                          const fte_params* prm, const fte_tally_buf* t,
+                                          int64_t n_start, int64_t n_end, void* stream)
+{
+    if (!P || !prm) return fail(FTE_EINVAL, "NULL particles or params");
+    fte_status s = check_background(bg);
+    if (s != FTE_OK) return s;
+    size_t nb = 0;
+    s = check_tally(t, &nb);
+    if (s != FTE_OK) return s;
+    if (nb > (size_t)kMaxSmemBins) return fail(FTE_ENOTSUP, "%zu tally bins exceed %d", nb, kMaxSmemBins);
+    if (n_end < n_start || n_start < 0) return fail(FTE_EINVAL, "need 0 <= n_start <= n_end");
+    if (n_end > 0xFFFFFFFFll) return fail(FTE_EINVAL, "step index exceeds 32 bits");
+    if (!(prm->dt > 0.0)) return fail(FTE_EINVAL, "dt must be > 0");
+    if (!(prm->lambda_par > 0.0)) return fail(FTE_EINVAL, "lambda_par must be > 0");
+    if (prm->dmumu < 0 || prm->dmumu > 2) return fail(FTE_EINVAL, "bad dmumu model");
+    if (prm->dmumu == 0 && !(prm->q > 1.0 && prm->q <= 2.0 && prm->H >= 0.0)) return fail(FTE_EINVAL, "need 1 < q <= 2, H >= 0");
+    if (prm->dmumu == 1 && !(prm->eps > 0.0)) return fail(FTE_EINVAL, "eps must be > 0");
+    if (prm->lambda_perp < 0.0) return fail(FTE_EINVAL, "lambda_perp must be >= 0");
+    if (!P->x || !P->y || !P->z || !P->mu || !P->p || !P->w || !P->id || !P->status)
+        return fail(FTE_EINVAL, "NULL particle array");
+
+    int device = 0;
+    FTE_CUDA(cudaGetDevice(&device), "cudaGetDevice");
+    char* w = nullptr;
+    s = noalloc_scratch(device, &w);
+    if (s != FTE_OK) return s;
+    if (n_end == n_start || P->count == 0) return FTE_OK;
+
+    // scratch layout: fetch counter, normalisation, the time table of one
+    // launch, then per-block partial histograms
+    const int kperp = prm->lambda_perp > 0.0 ? 1 : 0;
+    const size_t off_fetch = 0, off_norm = 64, off_table = 128;
+    const size_t off_part = (off_table + (size_t)kChunkSteps * sizeof(StepEntry) + 255) & ~(size_t)255;
+    const size_t part_block = 3 * sizeof(float) * (nb ? nb : 1);
+    const int sms = device_sms(device);
+    if (sms <= 0) return fail(FTE_ECUDA, "cannot query device %d", device);
+    const size_t fit = (kNoAllocBytes - off_part) / part_block;
+    if (fit < (size_t)sms)
+        return fail(FTE_ENOMEM, "a tally of %zu bins needs %zu bytes of scratch per block; the "
+                    "allocation-free variant holds %zu bytes, less than one block per SM (%d)",
+                    nb, part_block, kNoAllocBytes, sms);
+    const size_t smem = part_block;
+    int per_sm = 0;
+    FTE_CUDA(advance_occupancy(kperp, smem, &per_sm), "occupancy");
+    if (per_sm < 1) return fail(FTE_ENOTSUP, "step kernel does not fit on an SM with %zu bytes of tally", smem);
+    long long max_blocks = (long long)sms * per_sm;
+    if ((size_t)max_blocks > fit) max_blocks = (long long)fit;
+
+    cudaStream_t st = (cudaStream_t)stream;
+    double* norm = (double*)(w + off_norm);
+    FTE_CUDA(launch_norm(prm->dmumu, prm->q, prm->H, prm->eps, norm, st), "norm launch");
+
+    AdvanceArgs a;
+    memset(&a, 0, sizeof(a));
+    a.g = make_gridk(bg);
+    a.prm.dmumu = prm->dmumu; a.prm.p_update = prm->p_update; a.prm.kappa_drift = prm->kappa_drift;
+    a.prm.dvdt_term = prm->dvdt_term;
+    a.prm.use_rig = (prm->p_ref > 0.0 && prm->alpha != 0.0) ? 1 : 0;
+    a.prm.lambda_par = (float)prm->lambda_par; a.prm.p_ref = (float)prm->p_ref; a.prm.alpha = (float)prm->alpha;
+    a.prm.q = (float)prm->q; a.prm.H = (float)prm->H; a.prm.eps = (float)prm->eps;
+    a.prm.mu_floor = (float)prm->mu_floor; a.prm.lambda_perp = (float)prm->lambda_perp;
+    a.prm.dt = (float)prm->dt; a.prm.seed = prm->seed; a.prm.set_id = prm->set_id;
+    size_t off = 0;
+    for (int o = 0; o < t->n_obs; ++o) {
+        const fte_observer& ob = t->obs[o];
+        ObsK& k = a.obs[o];
+        k.kind = ob.kind; k.ne = ob.ne; k.nt = ob.nt; k.off = (int)off;
+        k.r = (float)ob.r; k.dr = (float)ob.dr; k.th = (float)ob.th; k.dth = (float)ob.dth;
+        k.ph = (float)ob.ph; k.dph = (float)ob.dph;
+        k.e_lo = (float)ob.e_lo; k.ne_over_lnratio = (float)(ob.ne / log(ob.e_hi / ob.e_lo));
+        off += (size_t)ob.ne * ob.nt;
+    }
+    a.n_obs = t->n_obs;
+    a.nbins = (int)(nb ? nb : 1);
+    a.x = P->x; a.y = P->y; a.z = P->z; a.mu = P->mu; a.p = P->p; a.w = P->w; a.id = P->id; a.status = P->status;
+    a.n_particles = P->count;
+    a.table = (const StepEntry*)(w + off_table);
+    a.norm = norm;
+    a.part = (float*)(w + off_part);
+    a.fetch = (unsigned long long*)(w + off_fetch);
+    a.ledger_w = t->ledger_w; a.ledger_n = t->ledger_n;
+
+    const unsigned long long lanes = (unsigned long long)max_blocks * kThreads;
+    const unsigned long long per = (P->count + lanes - 1) / lanes;
+    const unsigned long long threads = (P->count + per - 1) / per;
+    long long blocks = (long long)((threads + kThreads - 1) / kThreads);
+    if (blocks > max_blocks) blocks = max_blocks;
+    if (blocks < 1) blocks = 1;
+
+    StepTableArgs ta;
+    memset(&ta, 0, sizeof(ta));
+    ta.tab = (StepEntry*)(w + off_table);
+    ta.t0 = prm->t0; ta.dt = prm->dt;
+    ta.n_snap = bg->grid.n_snap; ta.periodic = bg->grid.periodic;
+    ta.t_snap0 = bg->grid.t_snap0; ta.dt_snap = bg->grid.dt_snap;
+    ta.n_obs = t->n_obs;
+    for (int o = 0; o < t->n_obs; ++o) {
+        ta.ot[o].t_lo = t->obs[o].t_lo; ta.ot[o].t_hi = t->obs[o].t_hi; ta.ot[o].nt = t->obs[o].nt;
+    }
+    for (long long c0 = n_start; c0 < n_end; c0 += kChunkSteps) {
+        const long long c1 = (c0 + kChunkSteps < n_end) ? c0 + kChunkSteps : n_end;
+        ta.n0 = c0;
+        ta.count = c1 - c0;
+        FTE_CUDA(launch_step_table(ta, st), "step table launch");
+        a.n_start = c0;
+        a.n_end = c1;
+        a.n_table0 = c0;
+        FTE_CUDA(cudaMemsetAsync(a.fetch, 0, sizeof(unsigned long long), st), "fetch reset");
+        FTE_CUDA(launch_advance(a, kperp, (int)blocks, smem, st), "step kernel launch");
+        if (nb) FTE_CUDA(launch_reduce(a.part, (int)blocks, (int)nb, t->S, t->S2, t->C, st), "reduce launch");
+    }
+    return FTE_OK;
+}
