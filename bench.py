@@ -147,7 +147,7 @@ def run_gpu(args):
     pool = api.Particles(n_part)
     tally = api.Tally(w.observers)
     wsp = api.Workspace()
-    wsp.ensure(api.fte_workspace_bytes(tally, CHUNK))
+    wsp.ensure(api.fte_workspace_bytes(bg, tally, n_part, CHUNK))
     id_base = rank * n_part
 
     def barrier():
@@ -177,32 +177,43 @@ def run_gpu(args):
     # device-resident arm ------------------------------------------------------
     api.fte_load_background(bg, host)
     torch.cuda.synchronize()
-    for _ in range(args.warmup):
-        one_step()
+
+    def measure(background, steps, warmup, clocks=None):
+        """W warm-up + K timed steps on `background`; returns (ms, kernel ms, launches, steps)."""
+        nonlocal bg
+        saved, bg = bg, background
+        for _ in range(warmup):
+            one_step()
+        launches = []
+        done = 0
+        barrier()
+        if clocks:
+            clocks.start()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(steps):
+            one_step(launches)
+            ln = tally.ledger_n.cpu().numpy()
+            done += int(ln[6]) // ws
+        t1.record(stream)
+        barrier()
+        if clocks:
+            clocks.result = clocks.stop()
+        bg = saved
+        ms = t0.elapsed_time(t1)
+        k_ms = sum(a_.elapsed_time(b_) for a_, b_ in launches)
+        ms_t = torch.tensor([ms, k_ms], dtype=torch.float64, device="cuda")
+        if ws > 1:
+            dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+        return ms_t[0].item(), ms_t[1].item(), len(launches), done
+
     clocks = Clocks(local)
-    launches = []
-    steps_total = 0
-    barrier()
-    clocks.start()
-    t0 = torch.cuda.Event(enable_timing=True)
-    t1 = torch.cuda.Event(enable_timing=True)
-    t0.record(stream)
-    for _ in range(args.steps):
-        one_step(launches)
-        lw, ln = api.fte_ledger(tally) if ws == 1 else (None, tally.ledger_n.cpu().numpy())
-        steps_total += int(ln[6]) // (ws if ws > 1 else 1)
-    t1.record(stream)
-    barrier()
-    cl = clocks.stop()
-    ms = t0.elapsed_time(t1)
-    k_ms = sum(a.elapsed_time(b) for a, b in launches)
-    n_launch = len(launches)
-    ms_t = torch.tensor([ms, k_ms], dtype=torch.float64, device="cuda")
-    if ws > 1:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms, k_ms = ms_t.tolist()
+    ms, k_ms, n_launch, steps_total = measure(bg, args.steps, args.warmup, clocks)
+    cl = clocks.result
     total_steps = steps_total * ws
     value = total_steps / (ms / 1e3)
+    S_f32 = api.fte_tally(tally, 0, A.FTE_TALLY_S)
 
     # tally error: relative standard error of the observer's total occupancy
     S = api.fte_tally(tally, 0, A.FTE_TALLY_S)
@@ -234,10 +245,30 @@ def run_gpu(args):
         dist.all_reduce(e_t, op=dist.ReduceOp.MAX)
     e2e_value = e_steps * ws / e_t.item()
 
+    # reduced-precision storage forms (same workload, background quantized on the device)
     peak, peak_kind = _peaks()
+    forms = {}
+    if not args.no_forms:
+        for dt in ("bf16", "f16"):
+            bh = api.Background(w.grid, dtype=dt)
+            api.fte_quantize_background(bh, bg)
+            f_ms, f_kms, _, f_steps = measure(bh, args.steps, max(1, args.warmup // 3))
+            Sh = api.fte_tally(tally, 0, A.FTE_TALLY_S)
+            f_alg = f_steps * (ALG_BYTES // 2) / (f_kms / 1e3) / 1e9
+            forms[dt] = {"value": f_steps * ws / (f_ms / 1e3), "unit": UNIT,
+                         "speedup_vs_f32": (f_steps / f_ms) / (steps_total / ms),
+                         "roofline": {"achieved": f_alg, "peak": peak, "unit": "GB/s",
+                                      "frac": f_alg / peak,
+                                      "alg_bytes_per_particle_step": ALG_BYTES // 2},
+                         "tally_total_rel_diff_vs_f32": float(abs(Sh.sum() - S_f32.sum()) / S_f32.sum()),
+                         "background_bytes": int(bh.nbytes)}
+            del bh
+            torch.cuda.empty_cache()
+
     achieved = total_steps / ws * ALG_BYTES / (k_ms / 1e3) / 1e9
-    # kernels per step: inject, per launch (norm, step table, step kernel, reduce), 3 tally reads
-    launches_per_step = 1 + 4 * math.ceil(n_steps / CHUNK)
+    # our kernels per timed step: inject, and per advance call the two normalisation
+    # kernels, the step table, the step kernel and the partial-histogram reduction
+    launches_per_step = 1 + 5 * math.ceil(n_steps / CHUNK)
     result = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -247,7 +278,7 @@ def run_gpu(args):
                                "QLT D_mumu q=5/3 H=0.05 lambda_par=0.1 au, dt=10 s x 34560 (4 days), "
                                "1 au box tally 16x144",
                    "particles_per_gpu": n_part, "steps_per_particle": n_steps,
-                   "background_bytes": int(bg.nbytes), "l2": "inputs larger than L2 (background 10.6 GB)",
+                   "background_bytes": int(bg.nbytes), "l2": "inputs larger than L2 (background %.1f GB)" % (bg.nbytes / 1e9),
                    "tally_rel_err": rel_err},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(bg.nbytes),
                 "d2h_bytes_per_step": int(out_host.nbytes + 2 * 8 * A.FTE_LEDGER)},
@@ -258,6 +289,7 @@ def run_gpu(args):
                      "kernel": "advance_kernel", "alg_bytes_per_particle_step": ALG_BYTES,
                      "kernel_ms_total": k_ms, "kernel_launches": n_launch},
         "clocks": cl,
+        "forms": forms,
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(w, fields, budget_s=args.cpu_budget)
@@ -359,6 +391,7 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true")
     args = ap.parse_args()
     if args.case == "profile":
         run_profile_case(args)

@@ -71,6 +71,7 @@ class Params:
     t0: float = 0.0                  # s, time of step 0
     seed: int = 0
     set_id: int = 0
+    sort_every: int = 0              # steps between spatial reorderings (performance only)
 
 
 @dataclass

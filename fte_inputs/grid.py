@@ -8,7 +8,8 @@ one record of REC float32 values:
     3..5   V  (Cartesian, au/s), in the frame the snapshot is given in
     6..14  dV_i/dx_j, row-major i (component) then j (direction), 1/s
     15..17 d|B|/dx_j (nT/au)
-    18..19 padding (zero), so that records are 16-byte aligned (80 B)
+    18..23 padding (zero): 96-byte records, so that two r-neighbours form one
+           32-byte aligned 192-byte block
 
 Array order is [snap][phi][theta][r][REC] (r fastest).  Cell k along an axis
 spans faces edge_k .. edge_{k+1}; phi covers [0, 2 pi) periodically.  With
@@ -19,7 +20,7 @@ import math
 import numpy as np
 
 NFIELD = 18
-REC = 20
+REC = 24
 
 
 @dataclass

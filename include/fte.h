@@ -41,7 +41,9 @@ extern "C" {
 
 #define FTE_ABI_VERSION 1
 #define FTE_NFIELD 18          /* stored fields per cell */
-#define FTE_REC 20             /* floats per stored cell record (80 bytes) */
+#define FTE_REC 24             /* floats per stored cell record (96 bytes) */
+#define FTE_HREC 32            /* 16-bit values per reduced-precision cell record (64 bytes) */
+#define FTE_HHDR 32            /* floats of the per-field scale header of a reduced-precision background */
 #define FTE_MAX_OBS 8          /* observers per tally */
 #define FTE_LEDGER 8           /* ledger slots */
 
@@ -67,13 +69,23 @@ enum { FTE_ALIVE = 0, FTE_ABS_INNER = 1, FTE_ABS_OUTER = 2, FTE_ABS_THETA = 3,
  * Cell k along an axis spans faces edge_k .. edge_{k+1}; r faces are uniform
  * (radial = 0) or geometric (radial = 1, the radially stretched grid of Sec. 4);
  * theta faces uniform on [th_min, th_max]; phi uniform and periodic on [0, 2 pi).
- * Record layout (20 floats): 0-2 B, 3-5 V, 6-14 dV_i/dx_j (row i = component),
- * 15-17 d|B|/dx_j, 18-19 unused.  Array order [snap][phi][theta][r][FTE_REC].
+ * Record layout (24 floats, 96 bytes): 0-2 B, 3-5 V, 6-14 dV_i/dx_j (row i =
+ * component), 15-17 d|B|/dx_j, 18-23 unused.  Array order [snap][phi][theta][r][FTE_REC],
+ * so the two r-neighbours of a cell are one contiguous, 32-byte aligned 192-byte read.
  * Snapshot s holds the fields at t_snap0 + s dt_snap; between snapshots the
  * fields are interpolated linearly in time and dV/dt gains (V_{s+1}-V_s)/dt_snap;
  * periodic != 0 wraps the sequence; otherwise the fields are frozen (and
  * dV/dt = 0) before the first and from the last snapshot on.
+ *
+ * Reduced precision (dtype FTE_BF16 / FTE_F16): the device array starts with a
+ * header of FTE_HHDR floats whose first 18 are per-field scales s_f (the largest
+ * |value| of field f over all cells and snapshots, 1 for an all-zero field),
+ * followed by records of FTE_HREC 16-bit values holding round-to-nearest-even
+ * (v_f / s_f) (the quotient rounded to float first), slots 18-31 zero.  The
+ * field used by the transport is the stored value times s_f.  Such arrays are
+ * produced on the device by fte_quantize_background (or copied in ready-made).
  * ------------------------------------------------------------------------- */
+enum { FTE_F32 = 0, FTE_BF16 = 1, FTE_F16 = 2 };
 typedef struct fte_grid {
     int32_t nr, nth, nph;      /* cells per axis, each >= 2 */
     int32_t radial;            /* 0 linear, 1 logarithmic */
@@ -82,11 +94,13 @@ typedef struct fte_grid {
     int32_t n_snap;            /* >= 1 */
     int32_t periodic;
     double t_snap0, dt_snap;   /* s; dt_snap > 0 when n_snap > 1 */
+    int32_t dtype;             /* FTE_F32, FTE_BF16 or FTE_F16 */
+    int32_t pad;
 } fte_grid;
 
 typedef struct fte_background {
     fte_grid grid;
-    const float* fields;       /* DEVICE, fte_background_bytes(&grid) bytes, 16-byte aligned */
+    const float* fields;       /* DEVICE, fte_background_bytes(&grid) bytes, 32-byte aligned */
 } fte_background;
 
 /* Bytes of the device array holding all snapshots of `g` (0 if g is invalid). */
@@ -94,10 +108,18 @@ size_t fte_background_bytes(const fte_grid* g);
 
 /* Validate `g` and copy `host_fields` (HOST, fte_background_bytes(g) bytes, in
    the record layout above; page-locked memory makes the copy asynchronous) to
-   `dev_fields` (DEVICE, at least that many bytes).  EINVAL on an invalid grid or
+   `dev_fields` (DEVICE, 32-byte aligned, at least that many bytes).  EINVAL on an invalid grid or
    null pointer, ENOMEM if dev_bytes is too small, ECUDA if the copy fails. */
 fte_status fte_load_background(const fte_grid* g, const float* host_fields, void* dev_fields,
                                size_t dev_bytes, void* stream);
+
+/* Quantize an FP32 background to the reduced-precision format of `g_half`
+   (dtype FTE_BF16 or FTE_F16; the other fields give the geometry of both
+   arrays): `dev_f32` (DEVICE, the FP32 array of the same geometry) is read and
+   `dev_out` (DEVICE, 32-byte aligned, out_bytes >= fte_background_bytes(g_half))
+   receives the scale header and the records.  Asynchronous on `stream`. */
+fte_status fte_quantize_background(const fte_grid* g_half, const float* dev_f32, void* dev_out,
+                                   size_t out_bytes, void* stream);
 
 /* ---------------------------------------------------------------------------
  * Particle pool: structure of arrays in DEVICE memory, `capacity` entries each.
@@ -148,12 +170,17 @@ typedef struct fte_inject_spec {
  * with Ito drift div(kappa_perp) when kappa_drift != 0.
  * dvdt_term != 0 keeps the b.dV/dt terms of Eqs. 3-4.
  * p_update 0: p' = p exp(pdot/p dt); 1: p' = p (1 + pdot/p dt).
+ * sort_every: see the field; it only changes which thread advances which particle.
  * ------------------------------------------------------------------------- */
 typedef struct fte_params {
     int32_t dmumu, p_update, kappa_drift, dvdt_term;
     double lambda_par, p_ref, alpha, q, H, eps, mu_floor, lambda_perp;
     double dt, t0;
     uint32_t seed, set_id;
+    int32_t sort_every;        /* > 0: reorder the alive particles by grid cell every
+                                  sort_every steps (performance only: results do not
+                                  depend on it); 0: no reordering */
+    int32_t pad;
 } fte_params;
 
 /* ---------------------------------------------------------------------------
@@ -188,10 +215,12 @@ size_t fte_tally_bins(const fte_tally_buf* t);
 /* Zero S, S2, C and the ledger (asynchronous). */
 fte_status fte_tally_reset(const fte_tally_buf* t, void* stream);
 
-/* Scratch (DEVICE) needed by fte_advance for `t` and `n_steps` steps per call on
-   `device`: per-block partial histograms, launch counters, the per-step time
-   table and the normalisation constants.  0 on error. */
-size_t fte_workspace_bytes(int device, const fte_tally_buf* t, int64_t n_steps);
+/* Scratch (DEVICE) needed by fte_advance on `device` for grid `g`, tally `t`, a
+   pool of `n_particles` entries and `n_steps` steps per call: per-block partial
+   histograms, launch counters, the per-step time table, the normalisation
+   constants and the particle-ordering buffers.  0 on error. */
+size_t fte_workspace_bytes(int device, const fte_grid* g, const fte_tally_buf* t,
+                           uint64_t n_particles, int64_t n_steps);
 
 /* Append n particles to P (requires P->count + n <= P->capacity) drawn per `spec`
    on the device (Sec. 2.3, Eq. 7), positions in the frame of `bg`.  Adds the
@@ -207,8 +236,8 @@ fte_status fte_inject(fte_particles* P, const fte_background* bg, const fte_inje
    mu = +-1, exponential momentum update; Sec. 2.4: trilinear interpolation of
    the bracketing snapshots), tallying the start-of-step state of each step into
    t and absorbing particles that leave [r_min, r_max] x [th_min, th_max] (ledger
-   slots 1-3).  ws (DEVICE, ws_bytes >= fte_workspace_bytes(device, t,
-   n_end - n_start)) is scratch; its contents on return are unspecified.
+   slots 1-3).  ws (DEVICE, ws_bytes >= fte_workspace_bytes(device, &bg->grid, t,
+   P->count, n_end - n_start)) is scratch; its contents on return are unspecified.
    Asynchronous on `stream`. */
 fte_status fte_advance(fte_particles* P, const fte_background* bg, const fte_params* prm,
                        const fte_tally_buf* t, int64_t n_start, int64_t n_end, void* ws,

@@ -10,7 +10,10 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libfte_gb300.so")
 
 FTE_NFIELD = 18
-FTE_REC = 20
+FTE_REC = 24
+FTE_HREC = 32
+FTE_HHDR = 32
+FTE_F32, FTE_BF16, FTE_F16 = range(3)
 FTE_MAX_OBS = 8
 FTE_LEDGER = 8
 FTE_OK, FTE_EINVAL, FTE_ENOMEM, FTE_ECUDA, FTE_ERANGE, FTE_ENOTSUP = range(6)
@@ -23,7 +26,8 @@ class fte_grid(C.Structure):
                 ("r_min", C.c_double), ("r_max", C.c_double),
                 ("th_min", C.c_double), ("th_max", C.c_double),
                 ("n_snap", C.c_int32), ("periodic", C.c_int32),
-                ("t_snap0", C.c_double), ("dt_snap", C.c_double)]
+                ("t_snap0", C.c_double), ("dt_snap", C.c_double),
+                ("dtype", C.c_int32), ("pad", C.c_int32)]
 
 
 class fte_background(C.Structure):
@@ -56,7 +60,8 @@ class fte_params(C.Structure):
                 ("q", C.c_double), ("H", C.c_double), ("eps", C.c_double),
                 ("mu_floor", C.c_double), ("lambda_perp", C.c_double),
                 ("dt", C.c_double), ("t0", C.c_double),
-                ("seed", C.c_uint32), ("set_id", C.c_uint32)]
+                ("seed", C.c_uint32), ("set_id", C.c_uint32),
+                ("sort_every", C.c_int32), ("pad", C.c_int32)]
 
 
 class fte_observer(C.Structure):
@@ -77,9 +82,10 @@ _P = C.POINTER
 SIGNATURES = {
     "fte_background_bytes": (C.c_size_t, [_P(fte_grid)]),
     "fte_load_background": (C.c_int, [_P(fte_grid), C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]),
+    "fte_quantize_background": (C.c_int, [_P(fte_grid), C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]),
     "fte_tally_bins": (C.c_size_t, [_P(fte_tally_buf)]),
     "fte_tally_reset": (C.c_int, [_P(fte_tally_buf), C.c_void_p]),
-    "fte_workspace_bytes": (C.c_size_t, [C.c_int, _P(fte_tally_buf), C.c_int64]),
+    "fte_workspace_bytes": (C.c_size_t, [C.c_int, _P(fte_grid), _P(fte_tally_buf), C.c_uint64, C.c_int64]),
     "fte_inject": (C.c_int, [_P(fte_particles), _P(fte_background), _P(fte_inject_spec), C.c_uint64,
                              _P(fte_tally_buf), _P(C.c_uint64), C.c_void_p]),
     "fte_advance": (C.c_int, [_P(fte_particles), _P(fte_background), _P(fte_params),

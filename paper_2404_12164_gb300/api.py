@@ -25,8 +25,12 @@ def _stream(stream=None):
 # ---------------------------------------------------------------------------
 # plain-data -> C struct conversions (fields follow fte_inputs.configs)
 # ---------------------------------------------------------------------------
-def grid_c(g):
+DTYPES = {"f32": A.FTE_F32, "bf16": A.FTE_BF16, "f16": A.FTE_F16}
+
+
+def grid_c(g, dtype="f32"):
     c = A.fte_grid()
+    c.dtype = DTYPES[dtype]
     c.nr, c.nth, c.nph = g.nr, g.nth, g.nph
     c.radial = 1 if g.radial == "log" else 0
     c.r_min, c.r_max, c.th_min, c.th_max = g.r_min, g.r_max, g.th_min, g.th_max
@@ -61,6 +65,7 @@ def params_c(p):
     c.q, c.H, c.eps, c.mu_floor, c.lambda_perp = p.q, p.H, p.eps, p.mu_floor, p.lambda_perp
     c.dt, c.t0 = p.dt, p.t0
     c.seed, c.set_id = p.seed & 0xFFFFFFFF, p.set_id & 0xFFFFFFFF
+    c.sort_every = int(getattr(p, "sort_every", 0))
     return c
 
 
@@ -77,11 +82,12 @@ def observer_c(o):
 # device-memory holders
 # ---------------------------------------------------------------------------
 class Background:
-    """Device copy of a snapshot sequence (fte_background)."""
+    """Device copy of a snapshot sequence (fte_background); dtype 'f32', 'bf16' or 'f16'."""
 
-    def __init__(self, grid, device="cuda"):
+    def __init__(self, grid, device="cuda", dtype="f32"):
         self.grid = grid
-        self.gc = grid_c(grid)
+        self.dtype = dtype
+        self.gc = grid_c(grid, dtype)
         nbytes = A.lib().fte_background_bytes(C.byref(self.gc))
         if nbytes == 0:
             raise ValueError("invalid grid")
@@ -104,6 +110,20 @@ def fte_load_background(bg, host_fields, stream=None):
     check(A.lib().fte_load_background(C.byref(bg.gc), C.c_void_p(ptr), C.c_void_p(bg.dev.data_ptr()),
                                       bg.nbytes, _stream(stream)), "fte_load_background")
     return host
+
+
+def fte_quantize_background(bg_half, bg_f32, stream=None):
+    """Fill the 16-bit background bg_half from the FP32 background bg_f32 (same geometry)."""
+    if bg_f32.dtype != "f32" or bg_half.dtype == "f32":
+        raise ValueError("quantize from an f32 background into a bf16/f16 background")
+    check(A.lib().fte_quantize_background(C.byref(bg_half.gc), C.c_void_p(bg_f32.dev.data_ptr()),
+                                          C.c_void_p(bg_half.dev.data_ptr()), bg_half.nbytes,
+                                          _stream(stream)), "fte_quantize_background")
+
+
+def device_bytes(bg):
+    """Host copy of a background's device array as raw bytes."""
+    return bg.dev.view(torch.uint8)[: bg.nbytes].cpu().numpy()
 
 
 class Particles:
@@ -171,9 +191,9 @@ class Workspace:
 # ---------------------------------------------------------------------------
 # the C ABI, one wrapper per entry point
 # ---------------------------------------------------------------------------
-def fte_workspace_bytes(tally, n_steps, device=None):
+def fte_workspace_bytes(bg, tally, n_particles, n_steps, device=None):
     dev = torch.cuda.current_device() if device is None else device
-    n = A.lib().fte_workspace_bytes(dev, C.byref(tally.c), int(n_steps))
+    n = A.lib().fte_workspace_bytes(dev, C.byref(bg.gc), C.byref(tally.c), int(n_particles), int(n_steps))
     if n == 0:
         raise RuntimeError("fte_workspace_bytes: " + A.lib().fte_last_error().decode())
     return n
@@ -199,7 +219,7 @@ def fte_inject(pool, bg, spec, n, tally, id_base=None, check_failed=True, stream
 
 def fte_advance(pool, bg, params, tally, n_start, n_end, ws=None, stream=None):
     ws = ws if ws is not None else Workspace(bg.dev.device)
-    buf = ws.ensure(fte_workspace_bytes(tally, n_end - n_start, bg.dev.device.index))
+    buf = ws.ensure(fte_workspace_bytes(bg, tally, pool.count, n_end - n_start, bg.dev.device.index))
     pc = params_c(params)
     check(A.lib().fte_advance(C.byref(pool.c), C.byref(bg.c), C.byref(pc), C.byref(tally.c),
                               int(n_start), int(n_end), C.c_void_p(buf.data_ptr()), buf.numel(),

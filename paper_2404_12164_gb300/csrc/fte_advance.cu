@@ -35,13 +35,18 @@ __device__ __forceinline__ void warp_tally(float* shS, float* shS2, unsigned* sh
 
 // One Euler-Maruyama step of Eqs. 2-4 for one particle (Sec. 2.1), with the
 // background interpolated at the start-of-step position and time (Sec. 2.4).
-template <bool KPERP>
+template <bool KPERP, int DT>
 __device__ __forceinline__ int step(const AdvanceArgs& a, float I, long long n, uint32_t pid,
                                     float& x, float& y, float& z, float& mu, float& p, float w,
-                                    float* shS, float* shS2, unsigned* shC,
+                                    float* shS, float* shS2, unsigned* shC, const float* sc,
                                     unsigned long long& noor)
 {
-    const StepEntry e = a.table[n - a.n_table0];
+    const StepEntry* ep = a.table + (n - a.n_table0);
+    StepEntry e;
+    {
+        const int4 h = __ldg(reinterpret_cast<const int4*>(ep));   // s0, s1, wt, two
+        e.s0 = h.x; e.s1 = h.y; e.wt = __int_as_float(h.z); e.two = h.w;
+    }
     const float rho2 = x * x + y * y;
     const float r = sqrtf(rho2 + z * z);
     const float rho = sqrtf(rho2);
@@ -52,7 +57,7 @@ __device__ __forceinline__ int step(const AdvanceArgs& a, float I, long long n, 
     Loc L;
     locate(a.g, r, th, ph, L);
     Fields<KPERP> F;
-    gather<KPERP>(a.g, e, L, F);
+    gather<KPERP, DT>(a.g, e, L, sc, F);
     const float* B = F.f;
     const float* V = F.f + 3;
     const float* G = F.f + 6;
@@ -157,7 +162,7 @@ __device__ __forceinline__ int step(const AdvanceArgs& a, float I, long long n, 
             int bin = -1;
             if (in) {
                 const float le = logf(E / ob.e_lo) * ob.ne_over_lnratio;
-                const int it = e.it[o];
+                const int it = __ldg(&ep->it[o]);
                 if (le >= 0.f && le < (float)ob.ne && it >= 0)
                     bin = ob.off + (int)le * ob.nt + it;
                 else
@@ -173,8 +178,8 @@ __device__ __forceinline__ int step(const AdvanceArgs& a, float I, long long n, 
     const float rn = sqrtf(xn * xn + yn * yn + zn * zn);
     if (rn < a.g.r_min) return FTE_ABS_INNER;
     if (rn > a.g.r_max) return FTE_ABS_OUTER;
-    const float thn = atan2f(sqrtf(xn * xn + yn * yn), zn);
-    if (thn < a.g.th_min || thn > a.g.th_max) return FTE_ABS_THETA;
+    // theta < th_min  <=>  z > r cos(th_min); theta > th_max  <=>  z < r cos(th_max)
+    if (zn > rn * a.g.cos_th_min || zn < rn * a.g.cos_th_max) return FTE_ABS_THETA;
     return FTE_ALIVE;
 }
 
@@ -187,29 +192,33 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
 
 // Persistent step kernel: each thread takes particles from a shared counter and
 // keeps each one in registers for all steps [n_start, n_end) of the launch.
-template <bool KPERP>
+template <bool KPERP, int DT>
 __global__ void __launch_bounds__(kThreads) advance_kernel(const AdvanceArgs a)
 {
     extern __shared__ float sh[];
     float* shS = sh;
     float* shS2 = sh + a.nbins;
     unsigned* shC = reinterpret_cast<unsigned*>(sh + 2 * a.nbins);
+    __shared__ float sc[FTE_NFIELD];      // per-field scales of 16-bit storage
     for (int b = threadIdx.x; b < 3 * a.nbins; b += blockDim.x) sh[b] = 0.f;
+    if (DT != FTE_F32 && threadIdx.x < FTE_NFIELD) sc[threadIdx.x] = __ldg(a.g.scale + threadIdx.x);
     __syncthreads();
 
     const float I = (float)__ldg(a.norm);
+    const unsigned long long n_work = a.order ? (unsigned long long)__ldg(a.n_order) : a.n_particles;
     unsigned long long nsteps = 0, noor = 0;
     for (;;) {
-        const unsigned long long i = atomicAdd(a.fetch, 1ULL);
-        if (i >= a.n_particles) break;
-        if (a.status[i] != FTE_ALIVE) continue;
+        const unsigned long long f = atomicAdd(a.fetch, 1ULL);
+        if (f >= n_work) break;
+        const unsigned long long i = a.order ? (unsigned long long)__ldg(a.order + f) : f;
+        if (!a.order && a.status[i] != FTE_ALIVE) continue;
         float x = a.x[i], y = a.y[i], z = a.z[i], mu = a.mu[i], p = a.p[i];
         const float w = a.w[i];
         const uint32_t pid = a.id[i];
         int st = FTE_ALIVE;
         for (long long n = a.n_start; n < a.n_end; ++n) {
             ++nsteps;
-            st = step<KPERP>(a, I, n, pid, x, y, z, mu, p, w, shS, shS2, shC, noor);
+            st = step<KPERP, DT>(a, I, n, pid, x, y, z, mu, p, w, shS, shS2, shC, sc, noor);
             if (st != FTE_ALIVE) break;
         }
         a.x[i] = x; a.y[i] = y; a.z[i] = z; a.mu[i] = mu; a.p[i] = p;
@@ -231,9 +240,18 @@ __global__ void __launch_bounds__(kThreads) advance_kernel(const AdvanceArgs a)
     }
 }
 
-cudaError_t advance_occupancy(int kperp, size_t smem, int* blocks_per_sm)
+static const void* advance_fn(int kperp, int dtype)
 {
-    const void* fn = kperp ? (const void*)advance_kernel<true> : (const void*)advance_kernel<false>;
+    if (dtype == FTE_BF16)
+        return kperp ? (const void*)advance_kernel<true, FTE_BF16> : (const void*)advance_kernel<false, FTE_BF16>;
+    if (dtype == FTE_F16)
+        return kperp ? (const void*)advance_kernel<true, FTE_F16> : (const void*)advance_kernel<false, FTE_F16>;
+    return kperp ? (const void*)advance_kernel<true, FTE_F32> : (const void*)advance_kernel<false, FTE_F32>;
+}
+
+cudaError_t advance_occupancy(int kperp, int dtype, size_t smem, int* blocks_per_sm)
+{
+    const void* fn = advance_fn(kperp, dtype);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, kThreads, smem);
@@ -241,8 +259,90 @@ cudaError_t advance_occupancy(int kperp, size_t smem, int* blocks_per_sm)
 
 cudaError_t launch_advance(const AdvanceArgs& a, int kperp, int blocks, size_t smem, cudaStream_t s)
 {
-    if (kperp) advance_kernel<true><<<blocks, kThreads, smem, s>>>(a);
-    else advance_kernel<false><<<blocks, kThreads, smem, s>>>(a);
+    const int dt = a.g.dtype;
+#define FTE_LAUNCH(K, D) advance_kernel<K, D><<<blocks, kThreads, smem, s>>>(a)
+    if (dt == FTE_BF16) { if (kperp) FTE_LAUNCH(true, FTE_BF16); else FTE_LAUNCH(false, FTE_BF16); }
+    else if (dt == FTE_F16) { if (kperp) FTE_LAUNCH(true, FTE_F16); else FTE_LAUNCH(false, FTE_F16); }
+    else { if (kperp) FTE_LAUNCH(true, FTE_F32); else FTE_LAUNCH(false, FTE_F32); }
+#undef FTE_LAUNCH
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Quantization of an FP32 background to 16-bit storage with per-field scales:
+// (1) largest |value| per field (atomic max of the non-negative float bits),
+// (2) zero scales become 1, (3) each record is encoded as the round-to-nearest-
+// even of (value / scale), the quotient correctly rounded in FP32.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) maxabs_kernel(const float* __restrict__ f, long long nrec,
+                                                     unsigned* hdr)
+{
+    float m[FTE_NFIELD];
+#pragma unroll
+    for (int k = 0; k < FTE_NFIELD; ++k) m[k] = 0.f;
+    for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < nrec;
+         r += (long long)gridDim.x * blockDim.x) {
+        float a[FTE_REC];
+#pragma unroll
+        for (int q = 0; q < FTE_REC / 8; ++q) ldg8(f + r * FTE_REC + 8 * q, a + 8 * q);
+#pragma unroll
+        for (int k = 0; k < FTE_NFIELD; ++k) m[k] = fmaxf(m[k], fabsf(a[k]));
+    }
+#pragma unroll
+    for (int k = 0; k < FTE_NFIELD; ++k) {
+        float v = m[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_down_sync(0xffffffffu, v, o));
+        if ((threadIdx.x & 31) == 0 && v > 0.f) atomicMax(hdr + k, __float_as_uint(v));
+    }
+}
+
+__global__ void scale_final_kernel(float* hdr)
+{
+    const int k = threadIdx.x;
+    if (k < FTE_HHDR) hdr[k] = (k < FTE_NFIELD) ? (hdr[k] > 0.f ? hdr[k] : 1.f) : 0.f;
+}
+
+template <int DT>
+__device__ __forceinline__ uint32_t encode16(float v)
+{
+    if (DT == FTE_BF16) return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(v));
+    return (uint32_t)__half_as_ushort(__float2half_rn(v));
+}
+
+template <int DT>
+__global__ void __launch_bounds__(256) encode_kernel(const float* __restrict__ f, long long nrec,
+                                                     const float* __restrict__ hdr, uint32_t* out)
+{
+    const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nrec) return;
+    float a[FTE_REC];
+#pragma unroll
+    for (int q = 0; q < FTE_REC / 8; ++q) ldg8(f + r * FTE_REC + 8 * q, a + 8 * q);
+    uint32_t w[FTE_HREC / 2];
+#pragma unroll
+    for (int k = 0; k < FTE_HREC / 2; ++k) w[k] = 0u;
+#pragma unroll
+    for (int k = 0; k < FTE_NFIELD; ++k) {
+        const uint32_t h = encode16<DT>(__fdiv_rn(a[k], __ldg(hdr + k)));
+        w[k >> 1] |= (k & 1) ? (h << 16) : h;
+    }
+    uint4* o = reinterpret_cast<uint4*>(out + r * (FTE_HREC / 2));
+#pragma unroll
+    for (int q = 0; q < FTE_HREC / 8; ++q) o[q] = make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
+}
+
+cudaError_t launch_quantize(const float* f32, long long nrec, int dtype, void* out, cudaStream_t s)
+{
+    float* hdr = reinterpret_cast<float*>(out);
+    uint32_t* recs = reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(out) + FTE_HHDR * sizeof(float));
+    cudaError_t e = cudaMemsetAsync(hdr, 0, FTE_HHDR * sizeof(float), s);
+    if (e != cudaSuccess) return e;
+    maxabs_kernel<<<1216, 256, 0, s>>>(f32, nrec, reinterpret_cast<unsigned*>(hdr));
+    scale_final_kernel<<<1, 32, 0, s>>>(hdr);
+    const long long blocks = (nrec + 255) / 256;
+    if (dtype == FTE_BF16) encode_kernel<FTE_BF16><<<(unsigned)blocks, 256, 0, s>>>(f32, nrec, hdr, recs);
+    else encode_kernel<FTE_F16><<<(unsigned)blocks, 256, 0, s>>>(f32, nrec, hdr, recs);
     return cudaGetLastError();
 }
 
@@ -344,31 +444,50 @@ cudaError_t launch_step_table(const StepTableArgs& a, cudaStream_t s)
 
 // ---------------------------------------------------------------------------
 // Normalisation of D_mumu from lambda_par: I (quasi-linear) or J (Eq. 5), by
-// composite Simpson in FP64 after mu = s^3; 1 for the isotropic form.
+// composite Simpson in FP64 after mu = s^3; 1 for the isotropic form.  Stage 1:
+// one node per thread, block sums in a fixed tree order; stage 2: one thread adds
+// the block sums in order.
 // ---------------------------------------------------------------------------
-__global__ void norm_kernel(int model, double q, double H, double eps, double* out)
+constexpr int kNormIntervals = 16384;
+constexpr int kNormThreads = 256;
+constexpr int kNormBlocks = kNormIntervals / kNormThreads + 1;   // nodes 0 .. kNormIntervals
+static_assert(kNormBlocks <= kNormPartials, "norm partials");
+
+__global__ void __launch_bounds__(kNormThreads) norm_partial_kernel(int model, double q, double H,
+                                                                    double eps, double* part)
 {
-    const int N = 16384;
-    const double h = 1.0 / N;
-    double acc = 0.0;
-    if (model != 2) {
-        for (int i = threadIdx.x; i <= N; i += 32) {
-            const double s = i * h;
-            const double m = s * s * s;
-            const double den = (model == 0) ? pow(m, q - 1.0) + H : m / (1.0 + m) + eps;
-            const double f = 3.0 * s * s * (1.0 - m * m) / den;
-            const double wgt = (i == 0 || i == N) ? 1.0 : ((i & 1) ? 4.0 : 2.0);
-            acc += wgt * f;
-        }
+    __shared__ double sh[kNormThreads];
+    const int i = blockIdx.x * kNormThreads + threadIdx.x;
+    double f = 0.0;
+    if (model != 2 && i <= kNormIntervals) {
+        const double h = 1.0 / kNormIntervals;
+        const double s = i * h;
+        const double m = s * s * s;
+        const double den = (model == 0) ? pow(m, q - 1.0) + H : m / (1.0 + m) + eps;
+        const double wgt = (i == 0 || i == kNormIntervals) ? 1.0 : ((i & 1) ? 4.0 : 2.0);
+        f = wgt * 3.0 * s * s * (1.0 - m * m) / den;
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-    if (threadIdx.x == 0) out[0] = (model == 2) ? 1.0 : acc * h / 3.0;
+    sh[threadIdx.x] = f;
+    __syncthreads();
+    for (int o = kNormThreads / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
 }
 
-cudaError_t launch_norm(int model, double q, double H, double eps, double* out, cudaStream_t s)
+__global__ void norm_final_kernel(int model, const double* part, double* out)
 {
-    norm_kernel<<<1, 32, 0, s>>>(model, q, H, eps, out);
+    double acc = 0.0;
+    for (int b = 0; b < kNormBlocks; ++b) acc += part[b];
+    out[0] = (model == 2) ? 1.0 : acc / (3.0 * kNormIntervals);
+}
+
+cudaError_t launch_norm(int model, double q, double H, double eps, double* out, double* part,
+                        cudaStream_t s)
+{
+    norm_partial_kernel<<<kNormBlocks, kNormThreads, 0, s>>>(model, q, H, eps, part);
+    norm_final_kernel<<<1, 1, 0, s>>>(model, part, out);
     return cudaGetLastError();
 }
 

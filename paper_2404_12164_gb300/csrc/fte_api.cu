@@ -46,25 +46,37 @@ fte_status check_grid(const fte_grid* g)
         return fail(FTE_EINVAL, "need 0 <= th_min < th_max <= pi");
     if (g->n_snap < 1) return fail(FTE_EINVAL, "n_snap must be >= 1");
     if (g->n_snap > 1 && !(g->dt_snap > 0.0)) return fail(FTE_EINVAL, "dt_snap must be > 0");
+    if (g->dtype != FTE_F32 && g->dtype != FTE_BF16 && g->dtype != FTE_F16)
+        return fail(FTE_EINVAL, "dtype must be FTE_F32, FTE_BF16 or FTE_F16");
     const double cells = (double)g->nr * g->nth * g->nph * g->n_snap;
     if (cells * FTE_REC > 9.0e18 / 4.0) return fail(FTE_EINVAL, "grid too large");
     return FTE_OK;
 }
 
+size_t grid_records(const fte_grid* g)
+{
+    return (size_t)g->nr * g->nth * g->nph * (size_t)g->n_snap;
+}
+
 size_t grid_bytes(const fte_grid* g)
 {
-    return (size_t)g->nr * g->nth * g->nph * (size_t)g->n_snap * FTE_REC * sizeof(float);
+    if (g->dtype == FTE_F32) return grid_records(g) * FTE_REC * sizeof(float);
+    return FTE_HHDR * sizeof(float) + grid_records(g) * FTE_HREC * sizeof(uint16_t);
 }
 
 GridK make_gridk(const fte_background* bg)
 {
     const fte_grid& g = bg->grid;
     GridK k;
-    k.fields = reinterpret_cast<const float4*>(bg->fields);
+    k.dtype = g.dtype;
+    k.fields = bg->fields;
+    k.scale = bg->fields;
+    k.hfields = reinterpret_cast<const uint32_t*>(bg->fields + FTE_HHDR);
     k.snap_recs = (long long)g.nr * g.nth * g.nph;
     k.nr = g.nr; k.nth = g.nth; k.nph = g.nph; k.radial = g.radial;
     k.r_min = (float)g.r_min; k.r_max = (float)g.r_max;
     k.th_min = (float)g.th_min; k.th_max = (float)g.th_max;
+    k.cos_th_min = (float)cos(g.th_min); k.cos_th_max = (float)cos(g.th_max);
     if (g.radial) {
         const double dl = log(g.r_max / g.r_min) / g.nr;
         k.dr = (float)dl;
@@ -86,7 +98,7 @@ fte_status check_background(const fte_background* bg)
     fte_status s = check_grid(&bg->grid);
     if (s != FTE_OK) return s;
     if (!bg->fields) return fail(FTE_EINVAL, "background fields pointer is NULL");
-    if ((uintptr_t)bg->fields % 16) return fail(FTE_EINVAL, "background fields must be 16-byte aligned");
+    if ((uintptr_t)bg->fields % 32) return fail(FTE_EINVAL, "background fields must be 32-byte aligned");
     return FTE_OK;
 }
 
@@ -112,7 +124,7 @@ fte_status check_tally(const fte_tally_buf* t, size_t* nbins)
 
 // Layout of the fte_advance workspace.
 struct WsLayout {
-    size_t off_fetch, off_norm, off_table, off_part, total;
+    size_t off_fetch, off_norm, off_npart, off_table, off_part, off_sort, total;
     int blocks;
 };
 
@@ -131,7 +143,8 @@ int device_sms(int device)
     return cache[device];
 }
 
-fte_status layout(int device, int kperp, size_t nbins, long long n_steps, WsLayout* L)
+fte_status layout(int device, int kperp, int dtype, size_t nbins, long long n_steps,
+                  size_t sort_bytes, WsLayout* L)
 {
     const int sms = device_sms(device);
     if (sms <= 0) return fail(FTE_ECUDA, "cannot query device %d", device);
@@ -140,7 +153,7 @@ fte_status layout(int device, int kperp, size_t nbins, long long n_steps, WsLayo
     int cur = 0;
     FTE_CUDA(cudaGetDevice(&cur), "cudaGetDevice");
     if (cur != device) FTE_CUDA(cudaSetDevice(device), "cudaSetDevice");
-    cudaError_t e = advance_occupancy(kperp, smem, &per_sm);
+    cudaError_t e = advance_occupancy(kperp, dtype, smem, &per_sm);
     if (cur != device) cudaSetDevice(cur);
     if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
     if (per_sm < 1) return fail(FTE_ENOTSUP, "step kernel does not fit on an SM with %zu bytes of tally", smem);
@@ -148,9 +161,12 @@ fte_status layout(int device, int kperp, size_t nbins, long long n_steps, WsLayo
     size_t off = 0;
     L->off_fetch = off; off += 64;
     L->off_norm = off; off += 64;
+    L->off_npart = off; off += kNormPartials * sizeof(double);
     L->off_table = off; off += (size_t)(n_steps > 0 ? n_steps : 1) * sizeof(StepEntry);
     off = (off + 255) & ~(size_t)255;
     L->off_part = off; off += (size_t)L->blocks * 3 * (nbins ? nbins : 1) * sizeof(float);
+    off = (off + 255) & ~(size_t)255;
+    L->off_sort = off; off += sort_bytes;
     L->total = off;
     return FTE_OK;
 }
@@ -188,11 +204,27 @@ fte_status fte_load_background(const fte_grid* g, const float* host_fields, void
     fte_status s = check_grid(g);
     if (s != FTE_OK) return s;
     if (!host_fields || !dev_fields) return fail(FTE_EINVAL, "NULL field pointer");
-    if ((uintptr_t)dev_fields % 16) return fail(FTE_EINVAL, "device fields must be 16-byte aligned");
+    if ((uintptr_t)dev_fields % 32) return fail(FTE_EINVAL, "device fields must be 32-byte aligned");
     const size_t need = grid_bytes(g);
     if (dev_bytes < need) return fail(FTE_ENOMEM, "device buffer has %zu bytes, needs %zu", dev_bytes, need);
     FTE_CUDA(cudaMemcpyAsync(dev_fields, host_fields, need, cudaMemcpyHostToDevice, (cudaStream_t)stream),
              "background copy");
+    return FTE_OK;
+}
+
+fte_status fte_quantize_background(const fte_grid* g_half, const float* dev_f32, void* dev_out,
+                                   size_t out_bytes, void* stream)
+{
+    fte_status s = check_grid(g_half);
+    if (s != FTE_OK) return s;
+    if (g_half->dtype != FTE_BF16 && g_half->dtype != FTE_F16)
+        return fail(FTE_EINVAL, "quantization target must be FTE_BF16 or FTE_F16");
+    if (!dev_f32 || !dev_out) return fail(FTE_EINVAL, "NULL field pointer");
+    if ((uintptr_t)dev_f32 % 32 || (uintptr_t)dev_out % 32) return fail(FTE_EINVAL, "arrays must be 32-byte aligned");
+    const size_t need = grid_bytes(g_half);
+    if (out_bytes < need) return fail(FTE_ENOMEM, "output buffer has %zu bytes, needs %zu", out_bytes, need);
+    FTE_CUDA(launch_quantize(dev_f32, (long long)grid_records(g_half), g_half->dtype, dev_out,
+                             (cudaStream_t)stream), "quantize launch");
     return FTE_OK;
 }
 
@@ -223,15 +255,25 @@ fte_status fte_tally_reset(const fte_tally_buf* t, void* stream)
     return FTE_OK;
 }
 
-size_t fte_workspace_bytes(int device, const fte_tally_buf* t, int64_t n_steps)
+size_t fte_workspace_bytes(int device, const fte_grid* g, const fte_tally_buf* t,
+                           uint64_t n_particles, int64_t n_steps)
 {
     size_t nb = 0;
+    if (check_grid(g) != FTE_OK) return 0;
     if (check_tally(t, &nb) != FTE_OK || n_steps < 0) return 0;
     if (nb > (size_t)kMaxSmemBins) return 0;
-    WsLayout L0, L1;
-    if (layout(device, 0, nb, n_steps, &L0) != FTE_OK) return 0;
-    if (layout(device, 1, nb, n_steps, &L1) != FTE_OK) return 0;
-    return L0.total > L1.total ? L0.total : L1.total;
+    fte_background tmp;
+    tmp.grid = *g;
+    tmp.fields = nullptr;
+    const size_t sort_bytes = sort_scratch_bytes(make_gridk(&tmp), n_particles);
+    size_t best = 0;
+    for (int dtype = FTE_F32; dtype <= FTE_F16; ++dtype)
+        for (int kperp = 0; kperp < 2; ++kperp) {
+            WsLayout L;
+            if (layout(device, kperp, dtype, nb, n_steps, sort_bytes, &L) != FTE_OK) return 0;
+            if (L.total > best) best = L.total;
+        }
+    return best;
 }
 
 fte_status fte_inject(fte_particles* P, const fte_background* bg, const fte_inject_spec* spec,
@@ -321,15 +363,18 @@ fte_status fte_advance(fte_particles* P, const fte_background* bg, const fte_par
     FTE_CUDA(cudaGetDevice(&device), "cudaGetDevice");
     const int kperp = prm->lambda_perp > 0.0 ? 1 : 0;
     const long long nsteps = n_end - n_start;
+    const GridK gk = make_gridk(bg);
+    const int sorting = prm->sort_every > 0;
     WsLayout L;
-    s = layout(device, kperp, nb, nsteps, &L);
+    s = layout(device, kperp, bg->grid.dtype, nb, nsteps, sorting ? sort_scratch_bytes(gk, P->count) : 0, &L);
     if (s != FTE_OK) return s;
     if (ws_bytes < L.total) return fail(FTE_ENOMEM, "workspace has %zu bytes, needs %zu", ws_bytes, L.total);
     char* w = (char*)ws;
     cudaStream_t st = (cudaStream_t)stream;
 
     double* norm = (double*)(w + L.off_norm);
-    FTE_CUDA(launch_norm(prm->dmumu, prm->q, prm->H, prm->eps, norm, st), "norm launch");
+    FTE_CUDA(launch_norm(prm->dmumu, prm->q, prm->H, prm->eps, norm, (double*)(w + L.off_npart), st),
+             "norm launch");
 
     StepTableArgs ta;
     memset(&ta, 0, sizeof(ta));
@@ -345,7 +390,7 @@ fte_status fte_advance(fte_particles* P, const fte_background* bg, const fte_par
 
     AdvanceArgs a;
     memset(&a, 0, sizeof(a));
-    a.g = make_gridk(bg);
+    a.g = gk;
     a.prm.dmumu = prm->dmumu; a.prm.p_update = prm->p_update; a.prm.kappa_drift = prm->kappa_drift;
     a.prm.dvdt_term = prm->dvdt_term;
     a.prm.use_rig = (prm->p_ref > 0.0 && prm->alpha != 0.0) ? 1 : 0;
@@ -353,6 +398,15 @@ fte_status fte_advance(fte_particles* P, const fte_background* bg, const fte_par
     a.prm.q = (float)prm->q; a.prm.H = (float)prm->H; a.prm.eps = (float)prm->eps;
     a.prm.mu_floor = (float)prm->mu_floor; a.prm.lambda_perp = (float)prm->lambda_perp;
     a.prm.dt = (float)prm->dt; a.prm.seed = prm->seed; a.prm.set_id = prm->set_id;
+    SortArgs sa;
+    memset(&sa, 0, sizeof(sa));
+    if (sorting) {
+        sort_carve(gk, P->count, w + L.off_sort, &sa);
+        sa.g = gk;
+        sa.x = P->x; sa.y = P->y; sa.z = P->z; sa.status = P->status; sa.n = P->count;
+        a.order = sa.order;
+        a.n_order = sa.hist + sa.nb;
+    }
     size_t off = 0;
     for (int o = 0; o < t->n_obs; ++o) {
         const fte_observer& ob = t->obs[o];
@@ -374,20 +428,24 @@ fte_status fte_advance(fte_particles* P, const fte_background* bg, const fte_par
     a.fetch = (unsigned long long*)(w + L.off_fetch);
     a.ledger_w = t->ledger_w; a.ledger_n = t->ledger_n;
 
-    // Grid: an equal number of particles per thread (no partial last wave).
+    // Grid: an equal number of particles per thread (no partial last wave); with
+    // reordering the alive count is only known on the device, so all resident
+    // blocks are launched.
     const unsigned long long lanes = (unsigned long long)L.blocks * kThreads;
     const unsigned long long per = (P->count + lanes - 1) / lanes;
     const unsigned long long threads = (P->count + per - 1) / per;
     int blocks = (int)((threads + kThreads - 1) / kThreads);
-    if (blocks > L.blocks) blocks = L.blocks;
+    if (blocks > L.blocks || sorting) blocks = L.blocks;
     if (blocks < 1) blocks = 1;
+    const long long chunk = sorting ? (prm->sort_every < kChunkSteps ? prm->sort_every : kChunkSteps) : kChunkSteps;
     const size_t smem = 3 * sizeof(float) * (size_t)a.nbins;
     int per_sm = 0;
-    FTE_CUDA(advance_occupancy(kperp, smem, &per_sm), "occupancy");
+    FTE_CUDA(advance_occupancy(kperp, bg->grid.dtype, smem, &per_sm), "occupancy");
 
-    for (long long c0 = n_start; c0 < n_end; c0 += kChunkSteps) {
+    for (long long c0 = n_start; c0 < n_end; c0 += chunk) {
         a.n_start = c0;
-        a.n_end = (c0 + kChunkSteps < n_end) ? c0 + kChunkSteps : n_end;
+        a.n_end = (c0 + chunk < n_end) ? c0 + chunk : n_end;
+        if (sorting) FTE_CUDA(launch_sort(sa, st), "sort launch");
         FTE_CUDA(cudaMemsetAsync(a.fetch, 0, sizeof(unsigned long long), st), "fetch reset");
         FTE_CUDA(launch_advance(a, kperp, blocks, smem, st), "step kernel launch");
         if (nb) FTE_CUDA(launch_reduce(a.part, blocks, (int)nb, t->S, t->S2, t->C, st), "reduce launch");
@@ -508,7 +566,8 @@ extern "C" fte_status fte_advance_noalloc(fte_particles* P, const fte_background
     // scratch layout: fetch counter, normalisation, the time table of one
     // launch, then per-block partial histograms
     const int kperp = prm->lambda_perp > 0.0 ? 1 : 0;
-    const size_t off_fetch = 0, off_norm = 64, off_table = 128;
+    const size_t off_fetch = 0, off_norm = 64, off_npart = 128;
+    const size_t off_table = off_npart + kNormPartials * sizeof(double);
     const size_t off_part = (off_table + (size_t)kChunkSteps * sizeof(StepEntry) + 255) & ~(size_t)255;
     const size_t part_block = 3 * sizeof(float) * (nb ? nb : 1);
     const int sms = device_sms(device);
@@ -520,14 +579,15 @@ extern "C" fte_status fte_advance_noalloc(fte_particles* P, const fte_background
                     nb, part_block, kNoAllocBytes, sms);
     const size_t smem = part_block;
     int per_sm = 0;
-    FTE_CUDA(advance_occupancy(kperp, smem, &per_sm), "occupancy");
+    FTE_CUDA(advance_occupancy(kperp, bg->grid.dtype, smem, &per_sm), "occupancy");
     if (per_sm < 1) return fail(FTE_ENOTSUP, "step kernel does not fit on an SM with %zu bytes of tally", smem);
     long long max_blocks = (long long)sms * per_sm;
     if ((size_t)max_blocks > fit) max_blocks = (long long)fit;
 
     cudaStream_t st = (cudaStream_t)stream;
     double* norm = (double*)(w + off_norm);
-    FTE_CUDA(launch_norm(prm->dmumu, prm->q, prm->H, prm->eps, norm, st), "norm launch");
+    FTE_CUDA(launch_norm(prm->dmumu, prm->q, prm->H, prm->eps, norm, (double*)(w + off_npart), st),
+             "norm launch");
 
     AdvanceArgs a;
     memset(&a, 0, sizeof(a));

@@ -10,6 +10,8 @@
 // built in FP64 by a separate kernel.
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -27,10 +29,14 @@ constexpr int kThreads = 256;                // threads per block of the step ke
 // Kernel-side descriptions (passed by value in the kernel parameter space)
 // ---------------------------------------------------------------------------
 struct GridK {
-    const float4* fields;    // record r of snapshot s at fields[(s * snap_recs + r) * 5]
+    const float* fields;     // FP32: record r of snapshot s at fields[(s * snap_recs + r) * FTE_REC]
+    const uint32_t* hfields; // 16-bit: record r of snapshot s at hfields[(s * snap_recs + r) * FTE_HREC / 2]
+    const float* scale;      // 16-bit: per-field scales (FTE_HHDR floats)
     long long snap_recs;     // records per snapshot
+    int dtype;
     int nr, nth, nph, radial;
     float r_min, r_max, th_min, th_max;
+    float cos_th_min, cos_th_max;
     float inv_dr;            // linear: nr / (r_max - r_min); log: nr / ln(r_max / r_min)
     float dr;                // linear: (r_max - r_min) / nr; log: ln(r_max / r_min) / nr
     float inv_dth, dth, inv_dph;
@@ -180,6 +186,42 @@ __device__ __forceinline__ void locate(const GridK& g, float r, float th, float 
     L.k1 = (k0 + 1 == g.nph) ? 0 : k0 + 1;
 }
 
+// 32-byte read-only loads (one sector each); the address must be 32-byte aligned.
+__device__ __forceinline__ void ldg8(const float* q, float* v)
+{
+    asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]),
+          "=f"(v[7])
+        : "l"(q));
+}
+
+__device__ __forceinline__ void ldg8u(const uint32_t* q, uint32_t* v)
+{
+    asm("ld.global.nc.v8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+          "=r"(v[7])
+        : "l"(q));
+}
+
+// 16-bit storage formats: value k of a record is half k & 1 of 32-bit word k >> 1.
+template <int DT>
+__device__ __forceinline__ float h_lo(uint32_t w)
+{
+    if (DT == FTE_BF16) return __uint_as_float(w << 16);
+    return __half2float(__ushort_as_half((unsigned short)(w & 0xFFFFu)));
+}
+template <int DT>
+__device__ __forceinline__ float h_hi(uint32_t w)
+{
+    if (DT == FTE_BF16) return __uint_as_float(w & 0xFFFF0000u);
+    return __half2float(__ushort_as_half((unsigned short)(w >> 16)));
+}
+template <int DT>
+__device__ __forceinline__ float h_get(const uint32_t* words, int k)
+{
+    return (k & 1) ? h_hi<DT>(words[k >> 1]) : h_lo<DT>(words[k >> 1]);
+}
+
 // Interpolated background at the particle (18 fields, dV/dt partial, and the
 // axis derivatives of B when the cross-field drift is on).
 template <bool KPERP>
@@ -189,9 +231,14 @@ struct Fields {
     float dBa[KPERP ? 9 : 1];  // dB_i / d(weight axis a), a = r, theta, phi
 };
 
-template <bool KPERP>
+// Trilinear (space) x linear (time) interpolation: for each snapshot and each
+// of the 4 (theta, phi) corners, the two r-neighbours are one contiguous block
+// (FP32: 192 bytes = six 32-byte loads; 16-bit: 128 bytes = four).  For 16-bit
+// storage the sums run over the stored values and the per-field scales `sc`
+// are applied once at the end.
+template <bool KPERP, int DT>
 __device__ __forceinline__ void gather(const GridK& g, const StepEntry& e, const Loc& L,
-                                       Fields<KPERP>& F)
+                                       const float* sc, Fields<KPERP>& F)
 {
 #pragma unroll
     for (int m = 0; m < FTE_NFIELD; ++m) F.f[m] = 0.f;
@@ -206,7 +253,6 @@ __device__ __forceinline__ void gather(const GridK& g, const StepEntry& e, const
         const int snap = s ? e.s1 : e.s0;
         const float ws = e.two ? (s ? e.wt : 1.f - e.wt) : 1.f;
         const float sgn = s ? 1.f : -1.f;
-        const float4* base = g.fields + (long long)snap * g.snap_recs * 5;
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
             const int ct = c & 1, cp = c >> 1;
@@ -215,19 +261,35 @@ __device__ __forceinline__ void gather(const GridK& g, const StepEntry& e, const
             const float wt_ = ct ? L.ft : 1.f - L.ft;
             const float wp_ = cp ? L.fp : 1.f - L.fp;
             const float wjk = wt_ * wp_;
-            const float4* q = base + (((long long)k * g.nth + j) * g.nr + L.i0) * 5;
-            float a[40];
+            const long long rec = ((long long)snap * g.snap_recs + ((long long)k * g.nth + j) * g.nr + L.i0);
+            float lo[FTE_NFIELD], hi[FTE_NFIELD];
+            if (DT == FTE_F32) {
+                float a[2 * FTE_REC];
+                const float* q = g.fields + rec * FTE_REC;
 #pragma unroll
-            for (int m = 0; m < 10; ++m) {
-                const float4 v = __ldg(q + m);
-                a[4 * m + 0] = v.x; a[4 * m + 1] = v.y; a[4 * m + 2] = v.z; a[4 * m + 3] = v.w;
+                for (int m = 0; m < 2 * FTE_REC / 8; ++m) ldg8(q + 8 * m, a + 8 * m);
+#pragma unroll
+                for (int m = 0; m < FTE_NFIELD; ++m) { lo[m] = a[m]; hi[m] = a[FTE_REC + m]; }
+            } else {
+                uint32_t u[FTE_HREC];      // two records of FTE_HREC / 2 words
+                const uint32_t* q = g.hfields + rec * (FTE_HREC / 2);
+#pragma unroll
+                for (int m = 0; m < FTE_HREC / 8; ++m) ldg8u(q + 8 * m, u + 8 * m);
+#pragma unroll
+                for (int m = 0; m < FTE_NFIELD; ++m) {
+                    lo[m] = h_get<DT>(u, m);
+                    hi[m] = h_get<DT>(u + FTE_HREC / 2, m);
+                }
             }
-            const float w0 = (1.f - L.fr) * wjk, w1 = L.fr * wjk;
+            const float c0 = (1.f - L.fr) * wjk, c1 = L.fr * wjk;
+            const float w0 = ws * c0, w1 = ws * c1;
 #pragma unroll
-            for (int m = 0; m < FTE_NFIELD; ++m) F.f[m] += ws * (w0 * a[m] + w1 * a[FTE_REC + m]);
+            for (int m = 0; m < FTE_NFIELD; ++m) F.f[m] = fmaf(w0, lo[m], fmaf(w1, hi[m], F.f[m]));
             if (e.two) {
+                const float d0 = sgn * c0, d1 = sgn * c1;
 #pragma unroll
-                for (int m = 0; m < 3; ++m) F.dv[m] += sgn * (w0 * a[3 + m] + w1 * a[FTE_REC + 3 + m]);
+                for (int m = 0; m < 3; ++m)
+                    F.dv[m] = fmaf(d0, lo[3 + m], fmaf(d1, hi[3 + m], F.dv[m]));
             }
             if (KPERP) {
                 const float er = L.dfr * wjk;                          // d w / d r
@@ -235,13 +297,22 @@ __device__ __forceinline__ void gather(const GridK& g, const StepEntry& e, const
                 const float ep = (cp ? 1.f : -1.f) * L.dfp * wt_;      // d w / d phi   (x w_r)
 #pragma unroll
                 for (int m = 0; m < 3; ++m) {
-                    const float lo = a[m], hi = a[FTE_REC + m];
-                    const float mix = (1.f - L.fr) * lo + L.fr * hi;
-                    F.dBa[3 * m + 0] += ws * er * (hi - lo);
+                    const float mix = (1.f - L.fr) * lo[m] + L.fr * hi[m];
+                    F.dBa[3 * m + 0] += ws * er * (hi[m] - lo[m]);
                     F.dBa[3 * m + 1] += ws * et * mix;
                     F.dBa[3 * m + 2] += ws * ep * mix;
                 }
             }
+        }
+    }
+    if (DT != FTE_F32) {
+#pragma unroll
+        for (int m = 0; m < FTE_NFIELD; ++m) F.f[m] *= sc[m];
+#pragma unroll
+        for (int m = 0; m < 3; ++m) F.dv[m] *= sc[3 + m];
+        if (KPERP) {
+#pragma unroll
+            for (int m = 0; m < 9; ++m) F.dBa[m] *= sc[m / 3];
         }
     }
 }

@@ -65,10 +65,22 @@ __global__ void __launch_bounds__(256) inject_kernel(const InjectArgs a)
                 const int cj = min(max((int)floorf(xt), 0), g.nth - 1);
                 int ck = (int)floorf(xp) % g.nph;
                 if (ck < 0) ck += g.nph;
-                const float* rec = reinterpret_cast<const float*>(
-                    g.fields + ((((long long)a.divv_snap * g.nph + ck) * g.nth + cj) * g.nr + ci) * 5);
-                const float s01 = __fadd_rn(__ldg(rec + 6), __ldg(rec + 10));
-                const float tr = __fadd_rn(s01, __ldg(rec + 14));
+                const long long ri = (((long long)a.divv_snap * g.nph + ck) * g.nth + cj) * g.nr + ci;
+                float g00, g11, g22;
+                if (g.dtype == FTE_F32) {
+                    const float* rec = g.fields + ri * FTE_REC;
+                    g00 = __ldg(rec + 6); g11 = __ldg(rec + 10); g22 = __ldg(rec + 14);
+                } else {
+                    // stored value times its field scale, rounded once
+                    const uint32_t* rec = g.hfields + ri * (FTE_HREC / 2);
+                    const uint32_t w3 = __ldg(rec + 3), w5 = __ldg(rec + 5), w7 = __ldg(rec + 7);
+                    const bool bf = g.dtype == FTE_BF16;
+                    g00 = __fmul_rn(bf ? h_lo<FTE_BF16>(w3) : h_lo<FTE_F16>(w3), __ldg(g.scale + 6));
+                    g11 = __fmul_rn(bf ? h_lo<FTE_BF16>(w5) : h_lo<FTE_F16>(w5), __ldg(g.scale + 10));
+                    g22 = __fmul_rn(bf ? h_lo<FTE_BF16>(w7) : h_lo<FTE_F16>(w7), __ldg(g.scale + 14));
+                }
+                const float s01 = __fadd_rn(g00, g11);
+                const float tr = __fadd_rn(s01, g22);
                 if (tr < a.divv_max) ok = true;
             }
         }

@@ -18,10 +18,25 @@ struct AdvanceArgs {
     long long n_table0;           // step index of table[0]
     const StepEntry* table;
     const double* norm;           // normalisation integral of D_mumu
+    const uint32_t* order;        // alive particles in spatial order (NULL: all, by index)
+    const unsigned* n_order;      // number of entries of `order` (device)
     float* part;                  // per-block partial histograms [grid][3][nbins]
     unsigned long long* fetch;    // particle counter for dynamic assignment
     double* ledger_w;
     unsigned long long* ledger_n;
+};
+
+struct SortArgs {
+    GridK g;
+    const float *x, *y, *z;
+    const uint8_t* status;
+    unsigned long long n;
+    unsigned* hist;               // bucket counts, then exclusive offsets; total at hist[nb]
+    unsigned* tiles;
+    int* key;
+    int* rank;
+    uint32_t* order;
+    int nb, ntiles;
 };
 
 struct ObsTime {
@@ -63,10 +78,19 @@ cudaError_t launch_advance(const AdvanceArgs& a, int kperp, int blocks, size_t s
 cudaError_t launch_reduce(const float* part, int nblk, int nbins, double* S, double* S2,
                           unsigned long long* C, cudaStream_t s);
 cudaError_t launch_step_table(const StepTableArgs& a, cudaStream_t s);
-cudaError_t launch_norm(int model, double q, double H, double eps, double* out, cudaStream_t s);
+// normalisation integral; `part` holds kNormPartials doubles of scratch
+constexpr int kNormPartials = 128;
+cudaError_t launch_norm(int model, double q, double H, double eps, double* out, double* part,
+                        cudaStream_t s);
 cudaError_t launch_tally_out(const double* S, const double* S2, const unsigned long long* C,
                              const ObsOut& ob, int kind, double* out, cudaStream_t s);
 cudaError_t launch_inject(const InjectArgs& a, cudaStream_t s);
-cudaError_t advance_occupancy(int kperp, size_t smem, int* blocks_per_sm);
+cudaError_t advance_occupancy(int kperp, int dtype, size_t smem, int* blocks_per_sm);
+// spatial ordering of the alive particles (fte_sort.cu)
+size_t sort_scratch_bytes(const GridK& g, unsigned long long n);
+void sort_carve(const GridK& g, unsigned long long n, char* p, SortArgs* a);
+cudaError_t launch_sort(const SortArgs& a, cudaStream_t s);
+// 16-bit storage: scale header + records of `nrec` FP32 records into `out`
+cudaError_t launch_quantize(const float* f32, long long nrec, int dtype, void* out, cudaStream_t s);
 
 }  // namespace fte

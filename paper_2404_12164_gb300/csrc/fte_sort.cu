@@ -1,0 +1,172 @@
+// Spatial ordering of the alive particles: a counting sort by grid bucket (two
+// r-cells of one (theta, phi) column), so that consecutive entries of the order
+// list - and so the lanes of a warp - read the same cache lines of the
+// background.  Dead particles are left out, which also compacts the work list.
+// Performance only: each particle's trajectory does not depend on the order.
+#include "fte_kernels.cuh"
+
+namespace fte {
+
+__device__ __forceinline__ int bucket_of(const GridK& g, float x, float y, float z)
+{
+    const float rho2 = x * x + y * y;
+    const float r = sqrtf(rho2 + z * z);
+    const float th = atan2f(sqrtf(rho2), z);
+    float ph = atan2f(y, x);
+    if (ph < 0.f) ph += kTwoPi;
+    const float xr = g.radial ? logf(r / g.r_min) * g.inv_dr : (r - g.r_min) * g.inv_dr;
+    const int i = min(max((int)xr, 0), g.nr - 1);
+    const int j = min(max((int)((th - g.th_min) * g.inv_dth), 0), g.nth - 1);
+    int k = (int)(ph * g.inv_dph);
+    k = min(max(k, 0), g.nph - 1);
+    const int nrb = (g.nr + 1) >> 1;
+    return (k * g.nth + j) * nrb + (i >> 1);
+}
+
+__global__ void __launch_bounds__(256) key_kernel(const SortArgs a)
+{
+    const unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    int key = -1, rank = 0;
+    if (a.status[i] == FTE_ALIVE) {
+        key = bucket_of(a.g, a.x[i], a.y[i], a.z[i]);
+        rank = (int)atomicAdd(a.hist + key, 1u);
+    }
+    a.key[i] = key;
+    a.rank[i] = rank;
+}
+
+// three-phase exclusive scan of hist[0..nb) into hist, total into hist[nb]
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 4;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+__device__ __forceinline__ unsigned block_exclusive_scan(unsigned v, unsigned* sh, unsigned* total)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    unsigned x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sh[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        unsigned s = (lane < (int)(blockDim.x >> 5)) ? sh[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        sh[lane] = s;
+    }
+    __syncthreads();
+    const unsigned warp_off = wid ? sh[wid - 1] : 0u;
+    *total = sh[(blockDim.x >> 5) - 1];
+    __syncthreads();
+    return warp_off + x - v;
+}
+
+__global__ void __launch_bounds__(kScanThreads) tile_sum_kernel(const unsigned* hist, int nb, unsigned* tiles)
+{
+    __shared__ unsigned sh[32];
+    const long long base = (long long)blockIdx.x * kScanTile + threadIdx.x * kScanItems;
+    unsigned s = 0;
+#pragma unroll
+    for (int q = 0; q < kScanItems; ++q)
+        if (base + q < nb) s += hist[base + q];
+    unsigned total;
+    block_exclusive_scan(s, sh, &total);
+    if (threadIdx.x == 0) tiles[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(kScanThreads) tile_offsets_kernel(unsigned* tiles, int ntiles)
+{
+    // one block: exclusive scan of the tile sums, in chunks of blockDim.x
+    __shared__ unsigned sh[32];
+    unsigned carry = 0;
+    for (int b0 = 0; b0 < ntiles; b0 += kScanThreads) {
+        const int t = b0 + threadIdx.x;
+        const unsigned v = t < ntiles ? tiles[t] : 0u;
+        unsigned total;
+        const unsigned ex = block_exclusive_scan(v, sh, &total);
+        if (t < ntiles) tiles[t] = carry + ex;
+        carry += total;
+    }
+    if (threadIdx.x == 0) tiles[ntiles] = carry;
+}
+
+__global__ void __launch_bounds__(kScanThreads) tile_scan_kernel(unsigned* hist, int nb, const unsigned* tiles,
+                                                                 int ntiles)
+{
+    __shared__ unsigned sh[32];
+    const long long base = (long long)blockIdx.x * kScanTile + threadIdx.x * kScanItems;
+    unsigned v[kScanItems];
+    unsigned s = 0;
+#pragma unroll
+    for (int q = 0; q < kScanItems; ++q) {
+        v[q] = (base + q < nb) ? hist[base + q] : 0u;
+        s += v[q];
+    }
+    unsigned total;
+    unsigned run = tiles[blockIdx.x] + block_exclusive_scan(s, sh, &total);
+#pragma unroll
+    for (int q = 0; q < kScanItems; ++q) {
+        if (base + q < nb) hist[base + q] = run;
+        run += v[q];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) hist[nb] = tiles[ntiles];
+}
+
+__global__ void __launch_bounds__(256) scatter_kernel(const SortArgs a)
+{
+    const unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    const int key = a.key[i];
+    if (key >= 0) a.order[a.hist[key] + (unsigned)a.rank[i]] = (uint32_t)i;
+}
+
+int sort_buckets(const GridK& g)
+{
+    return g.nph * g.nth * ((g.nr + 1) >> 1);
+}
+
+size_t sort_scratch_bytes(const GridK& g, unsigned long long n)
+{
+    const long long nb = sort_buckets(g);
+    const long long ntiles = (nb + kScanTile - 1) / kScanTile;
+    size_t b = 0;
+    b += ((size_t)(nb + 1) * 4 + 255) & ~(size_t)255;        // hist / offsets
+    b += ((size_t)(ntiles + 1) * 4 + 255) & ~(size_t)255;    // tile sums
+    b += 3 * (((size_t)n * 4 + 255) & ~(size_t)255);         // key, rank, order
+    return b;
+}
+
+void sort_carve(const GridK& g, unsigned long long n, char* p, SortArgs* a)
+{
+    const long long nb = sort_buckets(g);
+    const long long ntiles = (nb + kScanTile - 1) / kScanTile;
+    a->hist = (unsigned*)p; p += ((size_t)(nb + 1) * 4 + 255) & ~(size_t)255;
+    a->tiles = (unsigned*)p; p += ((size_t)(ntiles + 1) * 4 + 255) & ~(size_t)255;
+    a->key = (int*)p; p += ((size_t)n * 4 + 255) & ~(size_t)255;
+    a->rank = (int*)p; p += ((size_t)n * 4 + 255) & ~(size_t)255;
+    a->order = (uint32_t*)p;
+    a->nb = (int)nb;
+    a->ntiles = (int)ntiles;
+}
+
+cudaError_t launch_sort(const SortArgs& a, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(a.hist, 0, (size_t)(a.nb + 1) * 4, s);
+    if (e != cudaSuccess) return e;
+    const unsigned blocks = (unsigned)((a.n + 255) / 256);
+    if (blocks) key_kernel<<<blocks, 256, 0, s>>>(a);
+    tile_sum_kernel<<<a.ntiles, kScanThreads, 0, s>>>(a.hist, a.nb, a.tiles);
+    tile_offsets_kernel<<<1, kScanThreads, 0, s>>>(a.tiles, a.ntiles);
+    tile_scan_kernel<<<a.ntiles, kScanThreads, 0, s>>>(a.hist, a.nb, a.tiles, a.ntiles);
+    if (blocks) scatter_kernel<<<blocks, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace fte

@@ -43,9 +43,9 @@ def test_version_and_status_strings(L):
 
 def test_struct_sizes_match_header_layout():
     from paper_2404_12164_gb300 import _abi as A
-    assert C.sizeof(A.fte_grid) == 4 * 4 + 4 * 8 + 2 * 4 + 2 * 8
+    assert C.sizeof(A.fte_grid) == 4 * 4 + 4 * 8 + 2 * 4 + 2 * 8 + 2 * 4
     assert C.sizeof(A.fte_observer) == 4 * 4 + 10 * 8
-    assert C.sizeof(A.fte_params) == 4 * 4 + 10 * 8 + 2 * 4
+    assert C.sizeof(A.fte_params) == 4 * 4 + 10 * 8 + 4 * 4
     assert C.sizeof(A.fte_inject_spec) == 4 * 4 + 9 * 8 + 4 * 4 + 6 * 8 + 4 * 4
 
 
@@ -54,7 +54,7 @@ def test_background_bytes_and_grid_validation(L):
     from paper_2404_12164_gb300 import api, _abi as A
     g = GridSpec(nr=512, nth=60, nph=180, n_snap=24, periodic=True)
     gc = api.grid_c(g)
-    assert L.fte_background_bytes(C.byref(gc)) == 512 * 60 * 180 * 24 * 80
+    assert L.fte_background_bytes(C.byref(gc)) == 512 * 60 * 180 * 24 * 96
     for bad in (dict(nr=1), dict(r_min=0.0), dict(r_max=0.05), dict(th_max=4.0), dict(n_snap=0)):
         kw = dict(nr=8, nth=8, nph=8)
         kw.update(bad)
@@ -65,8 +65,8 @@ def test_background_bytes_and_grid_validation(L):
         assert len(L.fte_last_error()) > 0
     # undersized device buffer and misaligned pointer are refused before any copy
     gc = api.grid_c(GridSpec(nr=8, nth=8, nph=8))
-    assert L.fte_load_background(C.byref(gc), C.c_void_p(16), C.c_void_p(16), 100, None) == A.FTE_ENOMEM
-    assert L.fte_load_background(C.byref(gc), C.c_void_p(16), C.c_void_p(8), 1 << 30, None) == A.FTE_EINVAL
+    assert L.fte_load_background(C.byref(gc), C.c_void_p(16), C.c_void_p(64), 100, None) == A.FTE_ENOMEM
+    assert L.fte_load_background(C.byref(gc), C.c_void_p(16), C.c_void_p(16), 1 << 30, None) == A.FTE_EINVAL
     assert L.fte_load_background(None, C.c_void_p(16), C.c_void_p(16), 1 << 30, None) == A.FTE_EINVAL
 
 

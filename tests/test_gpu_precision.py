@@ -1,0 +1,100 @@
+"""Reduced-precision snapshot storage on the GPU (BF16 / FP16 with per-field scales).
+
+* the device quantizer reproduces the oracle's storage image bit for bit
+  (integer/byte work: exact);
+* trajectories advanced on the 16-bit background match the oracle evaluated on
+  the decoded values to the FP32 parity tolerance;
+* the storage error itself (16-bit vs FP32 background) is stated: tally totals
+  of the BF16 run against the FP32 oracle.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from fte_inputs import configs
+from oracle.quantize import quantize
+from tests._parity import oracle_run, trajectory_errors
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2404_12164_gb300 import build
+    build.build()
+
+
+@pytest.fixture(scope="module")
+def cir_small():
+    w = configs.scaled(configs.cir_uniform_1e6(), nr=128, nth=30, nph=90, n_particles=8000)
+    return w, configs.build_background(w)
+
+
+def _gpu_half(w, fields, dtype, chunks, n=None):
+    import torch
+    from paper_2404_12164_gb300 import api, _abi as A
+    n = n or w.n_particles
+    b32 = api.Background(w.grid)
+    api.fte_load_background(b32, fields)
+    bh = api.Background(w.grid, dtype=dtype)
+    api.fte_quantize_background(bh, b32)
+    image = api.device_bytes(bh)
+    del b32
+    pool = api.Particles(n)
+    tally = api.Tally(w.observers)
+    api.fte_tally_reset(tally)
+    api.fte_inject(pool, bh, w.inject, n, tally)
+    states = {0: pool.state()}
+    ws = api.Workspace()
+    prev = 0
+    for c in chunks:
+        api.fte_advance(pool, bh, w.params, tally, prev, c, ws)
+        prev = c
+        states[c] = pool.state()
+    S = api.fte_tally(tally, 0, A.FTE_TALLY_S)
+    S2 = api.fte_tally(tally, 0, A.FTE_TALLY_S2)
+    torch.cuda.synchronize()
+    return image, states, S, S2
+
+
+@pytest.mark.parametrize("dtype", ["bf16", "f16"])
+def test_quantizer_bit_exact(cir_small, dtype):
+    w, f = cir_small
+    image, _, _, _ = _gpu_half(w, f, dtype, [], n=1)
+    _, _, _, ref = quantize(f, dtype)
+    assert image.size == ref.size
+    assert np.array_equal(image, ref)
+
+
+@pytest.mark.parametrize("dtype", ["bf16", "f16"])
+def test_trajectories_on_16bit_background(cir_small, dtype):
+    w, f = cir_small
+    _, _, dec, _ = quantize(f, dtype)
+    chunks = [1, 50, 400]
+    _, g, _, _ = _gpu_half(w, f, dtype, chunks)
+    o = oracle_run(w, dec, 0, chunks=chunks)["states"]
+    for c in [0] + chunks:
+        ok, e = trajectory_errors(g[c], o[c], max(c, 1))
+        assert ok.sum() >= 500, c
+        for k in ("pos", "mu", "p"):
+            assert e[k].max() <= 1e-4, (dtype, c, k, float(e[k].max()))
+        assert e["status"].sum() == 0
+
+
+def test_bf16_storage_error_on_tallies(cir_small):
+    """Stated error of the storage form: BF16-background tallies vs the FP32 oracle.
+    Totals agree within 3 combined standard errors plus 2 % (the storage error)."""
+    w, f = cir_small
+    w.observers = [configs.Observer(kind="shell", r=1.5, dr=0.05, e_lo=0.01, e_hi=10.0, ne=16,
+                                    t_lo=0.0, t_hi=30000.0, nt=30)]
+    _, _, S, S2 = _gpu_half(w, f, "bf16", [3000])
+    o = oracle_run(w, f, 3000)["tallies"][0]
+    sig = math.sqrt(S2.sum() + o["S2"].sum())
+    diff = abs(S.sum() - o["S"].sum())
+    print(f"bf16 vs fp32 oracle: total S {S.sum():.6g} vs {o['S'].sum():.6g}, "
+          f"rel diff {diff / o['S'].sum():.3e}, sigma {sig / o['S'].sum():.3e}")
+    assert diff <= 3 * sig + 0.02 * o["S"].sum()
