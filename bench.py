@@ -139,6 +139,7 @@ def run_gpu(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     build.build()
     w, fields = build_workload()
+    w.params.sort_every = args.sort_every
     n_part, n_steps = w.n_particles, w.n_steps
     stream = torch.cuda.current_stream()
 
@@ -266,9 +267,14 @@ def run_gpu(args):
             torch.cuda.empty_cache()
 
     achieved = total_steps / ws * ALG_BYTES / (k_ms / 1e3) / 1e9
+    l2_gbs = l2_probe()
     # our kernels per timed step: inject, and per advance call the two normalisation
-    # kernels, the step table, the step kernel and the partial-histogram reduction
-    launches_per_step = 1 + 5 * math.ceil(n_steps / CHUNK)
+    # kernels and the step table, then per launch chunk the step kernel, the
+    # partial-histogram reduction and (with reordering) the five sort kernels
+    def kernels_per_call(s):
+        chunk = min(w.params.sort_every, CHUNK) if w.params.sort_every > 0 else CHUNK
+        return 3 + math.ceil(s / chunk) * (2 + (5 if w.params.sort_every > 0 else 0))
+    launches_per_step = 1 + sum(kernels_per_call(min(CHUNK, n_steps - c)) for c in range(0, n_steps, CHUNK))
     result = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -287,7 +293,8 @@ def run_gpu(args):
                      "frac": achieved / peak, "traffic": None,
                      "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)",
                      "kernel": "advance_kernel", "alg_bytes_per_particle_step": ALG_BYTES,
-                     "kernel_ms_total": k_ms, "kernel_launches": n_launch},
+                     "kernel_ms_total": k_ms, "kernel_launches": n_launch,
+                     "l2_random_sector_gbs": l2_gbs, "frac_of_l2": achieved / l2_gbs},
         "clocks": cl,
         "forms": forms,
     }
@@ -365,6 +372,7 @@ def run_profile_case(args):
     build.build()
     torch.cuda.set_device(0)
     w = configs.scaled(configs.cir_uniform_1e6(), n_snap=2, n_particles=1 << 18)
+    w.params.sort_every = args.sort_every
     fields = configs.build_background(w)
     bg = api.Background(w.grid)
     api.fte_load_background(bg, fields)
@@ -381,6 +389,25 @@ def run_profile_case(args):
                       "alg_bytes": int(ln[6]) * ALG_BYTES}))
 
 
+def l2_probe(mib=64, threads=152 * 2048, loads=256, reps=5):
+    """Random 32-byte sector read bandwidth of an L2-resident buffer (GB/s), best of reps."""
+    import torch
+    from paper_2404_12164_gb300 import api
+    buf = torch.ones(mib * (1 << 20) // 4, dtype=torch.float32, device="cuda")
+    out = torch.empty(threads, dtype=torch.float32, device="cuda")
+    api.fte_probe_sectors(buf, threads, 8, out)
+    best = 0.0
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        api.fte_probe_sectors(buf, threads, loads, out)
+        e1.record()
+        torch.cuda.synchronize()
+        best = max(best, threads * loads * 32 / (e0.elapsed_time(e1) / 1e3) / 1e9)
+    return best
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--case", default="bench", choices=["bench", "profile"])
@@ -392,6 +419,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true")
+    ap.add_argument("--sort-every", type=int, default=64,
+                    help="steps between spatial reorderings of the alive particles (0: off)")
     args = ap.parse_args()
     if args.case == "profile":
         run_profile_case(args)

@@ -124,7 +124,7 @@ def cir_uniform_1e6():
     inj = InjectSpec(region="box", r1=1.0, r2=2.0, th1=88 * DEG, th2=92 * DEG,
                      ph1=math.pi, ph2=2 * math.pi, divv_max=0.0, divv_snap=0,
                      energy="mono", e0=0.05, weight="r-2", seed=0)
-    prm = Params(dmumu="qlt", lambda_par=0.1, q=5.0 / 3.0, H=0.05, dt=10.0, seed=0)
+    prm = Params(dmumu="qlt", lambda_par=0.1, q=5.0 / 3.0, H=0.05, dt=10.0, seed=0, sort_every=64)
     four_days = 4 * 86400.0
     obs = [Observer(kind="box", r=1.0, dr=0.02, th=90 * DEG, dth=2 * DEG,
                     ph=cir_observer_phi(1.0), dph=2 * DEG, e_lo=0.01, e_hi=10.0, ne=16,

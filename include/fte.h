@@ -273,6 +273,15 @@ fte_status fte_tally(const fte_tally_buf* t, int obs, int kind, double* dev_out,
 /* Copy the ledger to HOST arrays (FTE_LEDGER entries each); synchronises `stream`. */
 fte_status fte_ledger(const fte_tally_buf* t, double* host_w, uint64_t* host_n, void* stream);
 
+/* Measurement helper (the paper has no counterpart): `threads` threads (a
+   multiple of 256) each read `loads` pseudo-random 32-byte sectors of `buf`
+   (DEVICE, 32-byte aligned, `bytes` >= 32) bypassing L1, and write one float
+   each to dev_out (DEVICE, `threads` floats).  Timing it gives the random-sector
+   read bandwidth of the level holding `buf` (L2 when `bytes` fits in L2), the
+   ceiling of a gather served from L2.  Asynchronous on `stream`. */
+fte_status fte_probe_sectors(const void* buf, size_t bytes, int threads, int loads, float* dev_out,
+                             void* stream);
+
 const char* fte_last_error(void);
 const char* fte_status_string(int status);
 int fte_abi_version(void);

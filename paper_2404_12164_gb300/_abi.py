@@ -96,6 +96,7 @@ SIGNATURES = {
     "fte_tally": (C.c_int, [_P(fte_tally_buf), C.c_int, C.c_int, C.c_void_p, C.c_void_p,
                             C.c_size_t, C.c_void_p]),
     "fte_ledger": (C.c_int, [_P(fte_tally_buf), _P(C.c_double), _P(C.c_uint64), C.c_void_p]),
+    "fte_probe_sectors": (C.c_int, [C.c_void_p, C.c_size_t, C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
     "fte_last_error": (C.c_char_p, []),
     "fte_status_string": (C.c_char_p, [C.c_int]),
     "fte_abi_version": (C.c_int, []),

@@ -244,6 +244,13 @@ def fte_tally(tally, obs, kind=A.FTE_TALLY_S, stream=None):
     return host
 
 
+def fte_probe_sectors(buf, threads, loads, out, stream=None):
+    """Random 32-byte sector reads of the device tensor `buf` (see include/fte.h)."""
+    check(A.lib().fte_probe_sectors(C.c_void_p(buf.data_ptr()), buf.numel() * buf.element_size(),
+                                    int(threads), int(loads), C.c_void_p(out.data_ptr()),
+                                    _stream(stream)), "fte_probe_sectors")
+
+
 def fte_ledger(tally, stream=None):
     w = (C.c_double * A.FTE_LEDGER)()
     n = (C.c_uint64 * A.FTE_LEDGER)()

@@ -481,6 +481,17 @@ fte_status fte_tally(const fte_tally_buf* t, int obs, int kind, double* dev_out,
     return FTE_OK;
 }
 
+fte_status fte_probe_sectors(const void* buf, size_t bytes, int threads, int loads, float* dev_out,
+                             void* stream)
+{
+    if (!buf || !dev_out) return fail(FTE_EINVAL, "NULL pointer");
+    if ((uintptr_t)buf % 32 || bytes < 32) return fail(FTE_EINVAL, "buffer must be 32-byte aligned, >= 32 bytes");
+    if (threads < 256 || threads % 256 || loads < 1) return fail(FTE_EINVAL, "threads must be a multiple of 256, loads >= 1");
+    FTE_CUDA(launch_probe((const float*)buf, bytes / 32, threads, loads, dev_out, (cudaStream_t)stream),
+             "probe launch");
+    return FTE_OK;
+}
+
 fte_status fte_ledger(const fte_tally_buf* t, double* host_w, uint64_t* host_n, void* stream)
 {
     if (!t || !t->ledger_w || !t->ledger_n || !host_w || !host_n) return fail(FTE_EINVAL, "NULL pointer");

@@ -90,6 +90,9 @@ cudaError_t advance_occupancy(int kperp, int dtype, size_t smem, int* blocks_per
 size_t sort_scratch_bytes(const GridK& g, unsigned long long n);
 void sort_carve(const GridK& g, unsigned long long n, char* p, SortArgs* a);
 cudaError_t launch_sort(const SortArgs& a, cudaStream_t s);
+// random-sector read probe (fte_probe.cu)
+cudaError_t launch_probe(const float* buf, unsigned long long nsec, int threads, int loads, float* out,
+                         cudaStream_t s);
 // 16-bit storage: scale header + records of `nrec` FP32 records into `out`
 cudaError_t launch_quantize(const float* f32, long long nrec, int dtype, void* out, cudaStream_t s);
 
