@@ -171,9 +171,10 @@ def _pack_leaf(rec, B_, V_, r, th, ph):
     R = torch.as_tensor(r, dtype=_F64)[None, None, :]
     TH = torch.as_tensor(th, dtype=_F64)[None, :, None]
     PH = torch.as_tensor(ph, dtype=_F64)[:, None, None]
+    P = len(r)
     basis = bgm._basis(TH, PH)
     ST = torch.sin(TH)
-    rhat, that, phat = basis
+    rhat, that, phat = [[torch.broadcast_to(c, (P, P, P)) for c in v] for v in basis]
     Rt = torch.as_tensor(r, dtype=_F64)
     Tt = torch.as_tensor(th, dtype=_F64)
     dph = float(ph[1] - ph[0])
@@ -265,3 +266,24 @@ def divv_refiner(spec, threshold, model="cir", t=0.0, r_from=0.0, **kw):
         dv = rec[1:-1, 1:-1, 1:-1, 6] + rec[1:-1, 1:-1, 1:-1, 10] + rec[1:-1, 1:-1, 1:-1, 14]
         return bool(np.abs(dv).max() > threshold)
     return refine
+
+
+def affine(spec, leaves, seed=0, phi_ref=math.pi):
+    """Every field affine in (r, theta, phi - phi_ref) (phi unwrapped to [0, 2 pi)), per
+    snapshot s plus a term linear in s; returns (fields, coef) like backgrounds.affine."""
+    rng = np.random.default_rng(seed)
+    coef = rng.normal(size=(18, 5))
+    B = spec.bsize
+    P = B + 2
+    out = np.zeros((spec.n_snap, len(leaves), P, P, P, REC), dtype=np.float32)
+    for n, (lv, bi, bj, bk) in enumerate(leaves):
+        idx = np.arange(B)
+        r = centres_1d(spec, lv, 0, bi * B + idx)
+        th = centres_1d(spec, lv, 1, bj * B + idx)
+        ph = centres_1d(spec, lv, 2, bk * B + idx) - phi_ref
+        for s in range(spec.n_snap):
+            for f in range(18):
+                c = coef[f]
+                out[s, n, 1:-1, 1:-1, 1:-1, f] = (c[0] + c[1] * r[None, None, :] + c[2] * th[None, :, None]
+                                                   + c[3] * ph[:, None, None] + c[4] * s)
+    return out, coef

@@ -255,20 +255,11 @@ static void grid_axes(const or_background* g, double r, double th, double ph,
     *k1 = (k0 + 1) % g->nph;
 }
 
-static void grid_fields(const or_background* g, double x, double y, double z, double t,
-                        fields_t* F)
+/* Bracketing snapshots and the weight of the later one (linear in time); `two`
+   says whether dV/dt gains the difference of the pair. */
+static void time_bracket(const or_background* g, double t, int* s0_, int* s1_, double* wt_,
+                         int* two_)
 {
-    memset(F, 0, sizeof(*F));
-    double r = sqrt(x * x + y * y + z * z);
-    double rho = sqrt(x * x + y * y);
-    double th = atan2(rho, z);
-    double ph = atan2(y, x);
-    if (ph < 0.0) ph += 2.0 * OR_PI;
-    axis_t ar, at, ap;
-    int k1;
-    grid_axes(g, r, th, ph, &ar, &at, &ap, &k1);
-
-    /* time bracket (linear interpolation between snapshots) */
     int s0 = 0, s1 = 0, two = 0;
     double wt = 0.0;
     if (g->n_snap > 1) {
@@ -289,6 +280,267 @@ static void grid_fields(const or_background* g, double x, double y, double z, do
             s0 = (int)kf; s1 = s0 + 1; wt = tau - kf; two = 1;
         }
     }
+    *s0_ = s0; *s1_ = s1; *wt_ = wt; *two_ = two;
+}
+
+/* ---- block AMR (Sec. 2.4) --------------------------------------------------
+   Leaves of 2:1-balanced blocks of B^3 cells.  The value at a point is the
+   trilinear interpolation (physical weights) of the containing leaf's cell
+   lattice extended by one ghost cell.  The paper fetches the neighbour data a
+   point near a block edge needs from the neighbouring blocks instead of storing
+   ghost cells (Sec. 2.4); here each ghost value is computed on demand from the
+   neighbours' interior cells:
+     same level   -> the neighbour's cell;
+     finer (L+1)  -> interpolation of the level-(L+1) lattice at the ghost centre;
+     coarser (L-1)-> interpolation of the level-(L-1) lattice at the ghost centre;
+   where a level-m lattice cell covered by finer leaves takes the interpolation of
+   the level-(m+1) lattice at its centre (recursively), and one inside a coarser
+   leaf takes that leaf's cell.  Outside the domain in r and theta a ghost takes
+   the nearest interior cell (constant beyond the outermost centres); phi wraps. */
+static int amr_L(const or_background* g) { return g->amr_levels - 1; }
+
+static void amr_ncells(const or_background* g, int m, long n[3])
+{
+    n[0] = (long)g->nr << m; n[1] = (long)g->nth << m; n[2] = (long)g->nph << m;
+}
+
+static double amr_centre(const or_background* g, int m, int a, long i)
+{
+    long n[3];
+    amr_ncells(g, m, n);
+    if (a == 0) {
+        if (g->radial == 1) return g->r_min * exp((i + 0.5) * log(g->r_max / g->r_min) / n[0]);
+        return g->r_min + (i + 0.5) * (g->r_max - g->r_min) / n[0];
+    }
+    if (a == 1) return g->th_min + (i + 0.5) * (g->th_max - g->th_min) / n[1];
+    return (i + 0.5) * (2.0 * OR_PI / n[2]);
+}
+
+static void amr_wrap(const or_background* g, int m, long X[3])
+{
+    long n[3];
+    amr_ncells(g, m, n);
+    if (X[0] < 0) X[0] = 0;
+    if (X[0] > n[0] - 1) X[0] = n[0] - 1;
+    if (X[1] < 0) X[1] = 0;
+    if (X[1] > n[1] - 1) X[1] = n[1] - 1;
+    X[2] = ((X[2] % n[2]) + n[2]) % n[2];
+}
+
+static int amr_cover(const or_background* g, int m, const long X[3])
+{
+    const int L = amr_L(g), B = g->amr_bsize;
+    const long nf0 = (long)(g->nr / B) << L, nf1 = (long)(g->nth / B) << L;
+    const long f0 = (X[0] << (L - m)) / B, f1 = (X[1] << (L - m)) / B, f2 = (X[2] << (L - m)) / B;
+    return g->table[(f2 * nf1 + f1) * nf0 + f0];
+}
+
+static const float* amr_rec(const or_background* g, int snap, int leaf, const long X[3])
+{
+    const int B = g->amr_bsize, P = B + 2;
+    const int32_t* lf = g->leaves + 4 * leaf;
+    const long li = X[0] - (long)lf[1] * B + 1, lj = X[1] - (long)lf[2] * B + 1;
+    const long lk = X[2] - (long)lf[3] * B + 1;
+    const size_t idx = ((((size_t)snap * g->n_leaves + leaf) * P + lk) * P + lj) * P + li;
+    return g->fields + idx * (size_t)g->rec;
+}
+
+static void amr_interp(const or_background* g, int snap, int m, const double c[3], double out[18]);
+
+static void amr_composite(const or_background* g, int snap, int m, const long Xin[3], double out[18])
+{
+    long X[3] = {Xin[0], Xin[1], Xin[2]};
+    amr_wrap(g, m, X);
+    const int leaf = amr_cover(g, m, X);
+    const int lv = g->leaves[4 * leaf];
+    if (lv == m) {
+        const float* q = amr_rec(g, snap, leaf, X);
+        for (int f = 0; f < 18; ++f) out[f] = q[f];
+    } else if (lv > m) {
+        const double c[3] = {amr_centre(g, m, 0, X[0]), amr_centre(g, m, 1, X[1]), amr_centre(g, m, 2, X[2])};
+        amr_interp(g, snap, m + 1, c, out);
+    } else {
+        const long Y[3] = {X[0] >> (m - lv), X[1] >> (m - lv), X[2] >> (m - lv)};
+        const float* q = amr_rec(g, snap, leaf, Y);
+        for (int f = 0; f < 18; ++f) out[f] = q[f];
+    }
+}
+
+static void amr_interp(const or_background* g, int snap, int m, const double c[3], double out[18])
+{
+    long n[3];
+    amr_ncells(g, m, n);
+    long i0[3];
+    double f[3];
+    for (int a = 0; a < 3; ++a) {
+        double x;
+        if (a == 0) x = (g->radial == 1) ? log(c[0] / g->r_min) / (log(g->r_max / g->r_min) / n[0]) - 0.5
+                                         : (c[0] - g->r_min) / ((g->r_max - g->r_min) / n[0]) - 0.5;
+        else if (a == 1) x = (c[1] - g->th_min) / ((g->th_max - g->th_min) / n[1]) - 0.5;
+        else x = c[2] / (2.0 * OR_PI / n[2]) - 0.5;
+        if (a < 2 && x < 0.0) { i0[a] = 0; f[a] = 0.0; }
+        else if (a < 2 && x >= n[a] - 1) { i0[a] = n[a] - 2; f[a] = 1.0; }
+        else {
+            i0[a] = (long)floor(x);
+            if (a == 0) {
+                const double c0 = amr_centre(g, m, 0, i0[0]), c1 = amr_centre(g, m, 0, i0[0] + 1);
+                f[a] = (c[0] - c0) / (c1 - c0);
+            } else {
+                f[a] = x - i0[a];
+            }
+        }
+    }
+    for (int k = 0; k < 18; ++k) out[k] = 0.0;
+    for (int cc = 0; cc < 8; ++cc) {
+        const int d0 = cc & 1, d1 = (cc >> 1) & 1, d2 = (cc >> 2) & 1;
+        const double w = (d0 ? f[0] : 1.0 - f[0]) * (d1 ? f[1] : 1.0 - f[1]) * (d2 ? f[2] : 1.0 - f[2]);
+        const long X[3] = {i0[0] + d0, i0[1] + d1, i0[2] + d2};
+        double v[18];
+        amr_composite(g, snap, m, X, v);
+        for (int k = 0; k < 18; ++k) out[k] += w * v[k];
+    }
+}
+
+/* value of the ghost cell G (global level-lv index) of a level-lv leaf */
+static void amr_ghost(const or_background* g, int snap, int lv, const long Gin[3], double out[18])
+{
+    long G[3] = {Gin[0], Gin[1], Gin[2]};
+    amr_wrap(g, lv, G);
+    const int leaf = amr_cover(g, lv, G);
+    const int lc = g->leaves[4 * leaf];
+    if (lc == lv) {
+        const float* q = amr_rec(g, snap, leaf, G);
+        for (int f = 0; f < 18; ++f) out[f] = q[f];
+        return;
+    }
+    const double c[3] = {amr_centre(g, lv, 0, G[0]), amr_centre(g, lv, 1, G[1]), amr_centre(g, lv, 2, G[2])};
+    amr_interp(g, snap, lc > lv ? lv + 1 : lv - 1, c, out);
+}
+
+/* leaf containing the point and its level-lv cell coordinates x[a] = u n - 1/2 */
+static int amr_locate(const or_background* g, double r, double th, double ph, long i0[3], double f[3],
+                      double dfdx[3], int* lv_out)
+{
+    const int L = amr_L(g), B = g->amr_bsize;
+    const long nf[3] = {(long)(g->nr / B) << L, (long)(g->nth / B) << L, (long)(g->nph / B) << L};
+    double u[3];
+    u[0] = (g->radial == 1) ? log(r / g->r_min) / log(g->r_max / g->r_min) : (r - g->r_min) / (g->r_max - g->r_min);
+    u[1] = (th - g->th_min) / (g->th_max - g->th_min);
+    u[2] = ph / (2.0 * OR_PI);
+    long fb[3];
+    for (int a = 0; a < 3; ++a) {
+        fb[a] = (long)floor(u[a] * nf[a]);
+        if (fb[a] < 0) fb[a] = (a == 2) ? fb[a] + nf[a] : 0;
+        if (fb[a] > nf[a] - 1) fb[a] = (a == 2) ? fb[a] - nf[a] : nf[a] - 1;
+    }
+    const int leaf = g->table[(fb[2] * nf[1] + fb[1]) * nf[0] + fb[0]];
+    const int lv = g->leaves[4 * leaf];
+    long n[3];
+    amr_ncells(g, lv, n);
+    for (int a = 0; a < 3; ++a) {
+        double x;
+        if (a == 0) x = (g->radial == 1) ? log(r / g->r_min) / (log(g->r_max / g->r_min) / n[0]) - 0.5
+                                         : (r - g->r_min) / ((g->r_max - g->r_min) / n[0]) - 0.5;
+        else if (a == 1) x = (th - g->th_min) / ((g->th_max - g->th_min) / n[1]) - 0.5;
+        else x = ph / (2.0 * OR_PI / n[2]) - 0.5;
+        long lo = (long)g->leaves[4 * leaf + 1 + a] * B - 1;       /* first padded index */
+        long k = (long)floor(x);
+        if (k < lo) k = lo;                                           /* rounding at the leaf edge */
+        if (k > lo + B) k = lo + B;
+        i0[a] = k;
+        if (a == 0) {
+            const double c0 = amr_centre(g, lv, 0, k), c1 = amr_centre(g, lv, 0, k + 1);
+            f[a] = (r - c0) / (c1 - c0);
+            dfdx[a] = 1.0 / (c1 - c0);
+        } else {
+            f[a] = x - k;
+            dfdx[a] = (a == 1) ? n[1] / (g->th_max - g->th_min) : n[2] / (2.0 * OR_PI);
+        }
+    }
+    *lv_out = lv;
+    return leaf;
+}
+
+static void amr_fields(const or_background* g, double x, double y, double z, double t, fields_t* F)
+{
+    memset(F, 0, sizeof(*F));
+    const double r = sqrt(x * x + y * y + z * z);
+    const double rho = sqrt(x * x + y * y);
+    const double th = atan2(rho, z);
+    double ph = atan2(y, x);
+    if (ph < 0.0) ph += 2.0 * OR_PI;
+    long i0[3];
+    double f[3], dfdx[3];
+    int lv;
+    const int leaf = amr_locate(g, r, th, ph, i0, f, dfdx, &lv);
+    const int B = g->amr_bsize;
+    int s0, s1, two;
+    double wt;
+    time_bracket(g, t, &s0, &s1, &wt, &two);
+    double dBax[3][3] = {{0}};
+    for (int s = 0; s < (two ? 2 : 1); ++s) {
+        const int snap = (s == 0) ? s0 : s1;
+        const double ws = two ? ((s == 0) ? 1.0 - wt : wt) : 1.0;
+        for (int c = 0; c < 8; ++c) {
+            const int cr = c & 1, ct = (c >> 1) & 1, cp = (c >> 2) & 1;
+            const long X[3] = {i0[0] + cr, i0[1] + ct, i0[2] + cp};
+            double q[18];
+            int interior = 1;
+            for (int a = 0; a < 3; ++a) {
+                const long loc = X[a] - (long)g->leaves[4 * leaf + 1 + a] * B;
+                if (loc < 0 || loc > B - 1) interior = 0;
+            }
+            if (interior) {
+                const float* p = amr_rec(g, snap, leaf, X);
+                for (int k = 0; k < 18; ++k) q[k] = p[k];
+            } else {
+                amr_ghost(g, snap, lv, X, q);
+            }
+            const double wr = cr ? f[0] : 1.0 - f[0];
+            const double wth = ct ? f[1] : 1.0 - f[1];
+            const double wp = cp ? f[2] : 1.0 - f[2];
+            const double wc = wr * wth * wp;
+            for (int m = 0; m < 3; ++m) F->B[m] += ws * wc * q[m];
+            for (int m = 0; m < 3; ++m) F->V[m] += ws * wc * q[3 + m];
+            for (int m = 0; m < 9; ++m) F->G[m] += ws * wc * q[6 + m];
+            for (int m = 0; m < 3; ++m) F->gB[m] += ws * wc * q[15 + m];
+            if (two)
+                for (int m = 0; m < 3; ++m) F->dVdt[m] += (s == 0 ? -1.0 : 1.0) * wc * q[3 + m] / g->dt_snap;
+            const double er = (cr ? 1.0 : -1.0) * dfdx[0] * wth * wp;
+            const double et = wr * (ct ? 1.0 : -1.0) * dfdx[1] * wp;
+            const double ep = wr * wth * (cp ? 1.0 : -1.0) * dfdx[2];
+            for (int m = 0; m < 3; ++m) {
+                dBax[m][0] += ws * er * q[m];
+                dBax[m][1] += ws * et * q[m];
+                dBax[m][2] += ws * ep * q[m];
+            }
+        }
+    }
+    const double st = sin(th), ctt = cos(th), sp = sin(ph), cpp = cos(ph);
+    const double rh[3] = {st * cpp, st * sp, ctt};
+    const double thh[3] = {ctt * cpp, ctt * sp, -st};
+    const double phh[3] = {-sp, cpp, 0.0};
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            F->dB[3 * i + j] = dBax[i][0] * rh[j] + dBax[i][1] * thh[j] / r + dBax[i][2] * phh[j] / (r * st);
+    F->divv = F->G[0] + F->G[4] + F->G[8];
+}
+
+static void grid_fields(const or_background* g, double x, double y, double z, double t,
+                        fields_t* F)
+{
+    memset(F, 0, sizeof(*F));
+    double r = sqrt(x * x + y * y + z * z);
+    double rho = sqrt(x * x + y * y);
+    double th = atan2(rho, z);
+    double ph = atan2(y, x);
+    if (ph < 0.0) ph += 2.0 * OR_PI;
+    axis_t ar, at, ap;
+    int k1;
+    grid_axes(g, r, th, ph, &ar, &at, &ap, &k1);
+    int s0, s1, two;
+    double wt;
+    time_bracket(g, t, &s0, &s1, &wt, &two);
     double dBax[3][3] = {{0}};   /* dB_i / d(r, theta, phi) */
     const size_t rec = (size_t)g->rec;
     for (int s = 0; s < (two ? 2 : 1); ++s) {
@@ -390,7 +642,8 @@ static void analytic_fields(const or_background* g, double x, double y, double z
 static void eval_fields(const or_background* g, double x, double y, double z, double t,
                         fields_t* F)
 {
-    if (g->kind == OR_BG_GRID) grid_fields(g, x, y, z, t, F);
+    if (g->kind == OR_BG_GRID && g->amr_levels > 0) amr_fields(g, x, y, z, t, F);
+    else if (g->kind == OR_BG_GRID) grid_fields(g, x, y, z, t, F);
     else analytic_fields(g, x, y, z, F);
 }
 
@@ -463,6 +716,41 @@ int or_inject(const or_background* bg, const or_inject_spec* sp, const uint32_t*
                 /* acceptance decided on the stored cell value of the containing
                    cell, summed in float like the device does */
                 const or_background* g = bg;
+                if (g->amr_levels > 0) {
+                    const int L = amr_L(g), B = g->amr_bsize;
+                    const long nf[3] = {(long)(g->nr / B) << L, (long)(g->nth / B) << L, (long)(g->nph / B) << L};
+                    double phw = fmod(ph, 2.0 * OR_PI);
+                    if (phw < 0) phw += 2.0 * OR_PI;
+                    double uu[3];
+                    uu[0] = (g->radial == 1) ? log(r / g->r_min) / log(g->r_max / g->r_min)
+                                             : (r - g->r_min) / (g->r_max - g->r_min);
+                    uu[1] = (th - g->th_min) / (g->th_max - g->th_min);
+                    uu[2] = phw / (2.0 * OR_PI);
+                    long fb[3];
+                    for (int k = 0; k < 3; ++k) {
+                        fb[k] = (long)floor(uu[k] * nf[k]);
+                        if (fb[k] < 0) fb[k] = 0;
+                        if (fb[k] > nf[k] - 1) fb[k] = nf[k] - 1;
+                    }
+                    const int leaf = g->table[(fb[2] * nf[1] + fb[1]) * nf[0] + fb[0]];
+                    const int lv = g->leaves[4 * leaf];
+                    long nl[3];
+                    amr_ncells(g, lv, nl);
+                    long X[3];
+                    for (int k = 0; k < 3; ++k) {
+                        const double xc = uu[k] * nl[k];
+                        if (near_integer(xc, k == 0 ? 2e-4 : 1e-4)) P->flags |= 1;
+                        const long lo = (long)g->leaves[4 * leaf + 1 + k] * B;
+                        X[k] = (long)floor(xc);
+                        if (X[k] < lo) X[k] = lo;
+                        if (X[k] > lo + B - 1) X[k] = lo + B - 1;
+                    }
+                    const float* q = amr_rec(g, sp->divv_snap, leaf, X);
+                    float s01 = q[6] + q[10];
+                    float tr = s01 + q[14];
+                    if (tr < (float)sp->divv_max) ok = 1;
+                    continue;
+                }
                 double xr = (g->radial == 1) ? log(r / g->r_min) / (log(g->r_max / g->r_min) / g->nr)
                                              : (r - g->r_min) / ((g->r_max - g->r_min) / g->nr);
                 double xt = (th - g->th_min) / ((g->th_max - g->th_min) / g->nth);

@@ -40,7 +40,12 @@ typedef struct {
     int32_t nr, nth, nph, radial;     /* GRID: cells; radial 0 linear, 1 log */
     int32_t n_snap, periodic, rec, pad;
     double r_min, r_max, th_min, th_max, t_snap0, dt_snap;
-    const float* fields;         /* [n_snap][nph][nth][nr][rec] */
+    const float* fields;         /* uniform: [n_snap][nph][nth][nr][rec];
+                                    AMR: [n_snap][n_leaves][B+2][B+2][B+2][rec], ghosts unused */
+    /* block AMR (amr_levels > 0): nr, nth, nph are the base-level cell counts */
+    int32_t amr_levels, amr_bsize, n_leaves, pad2;
+    const int32_t* leaves;       /* [n_leaves][4]: level, bi, bj, bk (block index at its level) */
+    const int32_t* table;        /* [nph/B 2^L][nth/B 2^L][nr/B 2^L]: leaf covering each finest block */
 } or_background;
 
 typedef struct {

@@ -27,7 +27,9 @@ class Background(C.Structure):
                 ("pad", C.c_int32),
                 ("r_min", C.c_double), ("r_max", C.c_double), ("th_min", C.c_double),
                 ("th_max", C.c_double), ("t_snap0", C.c_double), ("dt_snap", C.c_double),
-                ("fields", C.c_void_p)]
+                ("fields", C.c_void_p),
+                ("amr_levels", C.c_int32), ("amr_bsize", C.c_int32), ("n_leaves", C.c_int32),
+                ("pad2", C.c_int32), ("leaves", C.c_void_p), ("table", C.c_void_p)]
 
 
 class ParamsC(C.Structure):
@@ -121,6 +123,30 @@ def grid_background(grid, fields):
     c.t_snap0, c.dt_snap = grid.t_snap0, grid.dt_snap
     c.fields = f.ctypes.data
     return Bg(c, f)
+
+
+def amr_background(spec, leaves, fields):
+    """Background from an fte_inputs.amr.AmrSpec, its Morton-sorted leaves and padded fields
+    [n_snap, n_leaf, B+2, B+2, B+2, REC] (ghost layer ignored)."""
+    from fte_inputs import amr as amr_mod
+    f = np.ascontiguousarray(fields, dtype=np.float32)
+    lv = np.ascontiguousarray(leaves, dtype=np.int32)
+    tab = np.ascontiguousarray(amr_mod.finest_table(spec, lv), dtype=np.int32)
+    B = spec.bsize
+    c = Background()
+    c.kind = OR_BG["grid"]
+    c.domain = OR_DOM["sphere"]
+    c.dom[:] = [spec.r_min, spec.r_max, spec.th_min, spec.th_max]
+    c.nr, c.nth, c.nph = spec.nbr * B, spec.nbt * B, spec.nbp * B
+    c.radial = 1 if spec.radial == "log" else 0
+    c.n_snap, c.periodic, c.rec = spec.n_snap, int(spec.periodic), f.shape[-1]
+    c.r_min, c.r_max, c.th_min, c.th_max = spec.r_min, spec.r_max, spec.th_min, spec.th_max
+    c.t_snap0, c.dt_snap = spec.t_snap0, spec.dt_snap
+    c.fields = f.ctypes.data
+    c.amr_levels, c.amr_bsize, c.n_leaves = spec.levels, B, len(lv)
+    c.leaves = lv.ctypes.data
+    c.table = tab.ctypes.data
+    return Bg(c, (f, lv, tab))
 
 
 def analytic_background(kind, a=(), domain="none", dom=()):
