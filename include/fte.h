@@ -95,12 +95,29 @@ typedef struct fte_grid {
     int32_t periodic;
     double t_snap0, dt_snap;   /* s; dt_snap > 0 when n_snap > 1 */
     int32_t dtype;             /* FTE_F32, FTE_BF16 or FTE_F16 */
-    int32_t pad;
+    int32_t amr_levels;        /* 0: uniform grid; 1..4: block AMR with this many levels */
+    int32_t amr_bsize;         /* AMR: cells per block edge B (nr, nth, nph multiples of B) */
+    int32_t n_leaves;          /* AMR: number of leaf blocks */
 } fte_grid;
 
+/* Block AMR (Sec. 2.4, Fig. 4): nr x nth x nph are the base-level (level 0) cells,
+   split into blocks of B^3 cells; a block of level l is halved in every direction
+   to give 8 blocks of level l+1; touching leaves (faces, edges, corners) differ by
+   at most one level.  Leaf n is (level, bi, bj, bk): block indices at its own
+   level.  Fields: [snap][leaf][B+2][B+2][B+2] records (phi, theta, r order) - the
+   leaf's cells with a one-cell ghost layer that fte_amr_prepare fills from the
+   neighbours (same level: copy; finer: trilinear interpolation of the finer
+   lattice at the ghost centre; coarser: of the coarser lattice, where a coarser
+   lattice cell covered by finer leaves takes the interpolation of the finer
+   lattice at its centre; outside the domain in r and theta: the nearest
+   interior cell; phi periodic), so that every point of a leaf interpolates
+   trilinearly on the leaf's padded lattice. */
 typedef struct fte_background {
     fte_grid grid;
     const float* fields;       /* DEVICE, fte_background_bytes(&grid) bytes, 32-byte aligned */
+    const int32_t* leaves;     /* AMR: DEVICE [n_leaves][4] (level, bi, bj, bk) */
+    int32_t* table;            /* AMR: DEVICE, fte_amr_table_bytes(&grid) bytes: the leaf
+                                  covering each finest-level block, built by fte_amr_prepare */
 } fte_background;
 
 /* Bytes of the device array holding all snapshots of `g` (0 if g is invalid). */
@@ -112,6 +129,16 @@ size_t fte_background_bytes(const fte_grid* g);
    null pointer, ENOMEM if dev_bytes is too small, ECUDA if the copy fails. */
 fte_status fte_load_background(const fte_grid* g, const float* host_fields, void* dev_fields,
                                size_t dev_bytes, void* stream);
+
+/* Bytes of the finest-level lookup table of an AMR grid (0 if not AMR or invalid). */
+size_t fte_amr_table_bytes(const fte_grid* g);
+
+/* AMR set-up, once per background after its interior cells and leaves are on the
+   device (FP32 fields): builds bg->table, checks that the leaves tile the domain
+   without overlap and with 2:1 nesting (EINVAL otherwise; this check
+   synchronises `stream`), then fills the ghost layer of every leaf and snapshot
+   in bg->fields.  A 16-bit copy is then made with fte_quantize_background. */
+fte_status fte_amr_prepare(const fte_background* bg, void* stream);
 
 /* Quantize an FP32 background to the reduced-precision format of `g_half`
    (dtype FTE_BF16 or FTE_F16; the other fields give the geometry of both

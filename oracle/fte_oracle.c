@@ -417,6 +417,19 @@ static void amr_ghost(const or_background* g, int snap, int lv, const long Gin[3
     amr_interp(g, snap, lc > lv ? lv + 1 : lv - 1, c, out);
 }
 
+void or_amr_cell(const or_background* g, int snap, int leaf, int li, int lj, int lk, double out[18])
+{
+    const int B = g->amr_bsize;
+    const int32_t* lf = g->leaves + 4 * leaf;
+    const long X[3] = {(long)lf[1] * B + li - 1, (long)lf[2] * B + lj - 1, (long)lf[3] * B + lk - 1};
+    if (li >= 1 && li <= B && lj >= 1 && lj <= B && lk >= 1 && lk <= B) {
+        const float* q = amr_rec(g, snap, leaf, X);
+        for (int k = 0; k < 18; ++k) out[k] = q[k];
+        return;
+    }
+    amr_ghost(g, snap, lf[0], X, out);
+}
+
 /* leaf containing the point and its level-lv cell coordinates x[a] = u n - 1/2 */
 static int amr_locate(const or_background* g, double r, double th, double ph, long i0[3], double f[3],
                       double dfdx[3], int* lv_out)

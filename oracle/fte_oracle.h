@@ -98,6 +98,9 @@ int or_advance(const or_background* bg, const or_params* prm, const or_observer*
 int or_step_terms(const or_background* bg, const or_params* prm, const or_particle* p,
                   int64_t n, double out[32]);
 void or_intensity(const or_observer* obs, const double* S, double* J);
+/* value of padded cell (li, lj, lk) of an AMR leaf (interior cells: the stored record;
+   ghost cells: the neighbour value the method defines), fields 0..17 */
+void or_amr_cell(const or_background* bg, int snap, int leaf, int li, int lj, int lk, double out[18]);
 int or_max_threads(void);
 
 #ifdef __cplusplus

@@ -93,6 +93,8 @@ def lib():
                                     P(C.c_double)]
         L.or_intensity.argtypes = [P(ObserverC), C.c_void_p, C.c_void_p]
         L.or_max_threads.restype = C.c_int
+        L.or_amr_cell.argtypes = [P(Background), C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
+                                  P(C.c_double)]
         _lib = L
     return _lib
 
@@ -147,6 +149,12 @@ def amr_background(spec, leaves, fields):
     c.leaves = lv.ctypes.data
     c.table = tab.ctypes.data
     return Bg(c, (f, lv, tab))
+
+
+def amr_cell(bg, snap, leaf, li, lj, lk):
+    o = (C.c_double * 18)()
+    lib().or_amr_cell(C.byref(bg.c), snap, leaf, li, lj, lk, o)
+    return np.array(o)
 
 
 def analytic_background(kind, a=(), domain="none", dom=()):

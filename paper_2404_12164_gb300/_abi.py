@@ -27,11 +27,13 @@ class fte_grid(C.Structure):
                 ("th_min", C.c_double), ("th_max", C.c_double),
                 ("n_snap", C.c_int32), ("periodic", C.c_int32),
                 ("t_snap0", C.c_double), ("dt_snap", C.c_double),
-                ("dtype", C.c_int32), ("pad", C.c_int32)]
+                ("dtype", C.c_int32), ("amr_levels", C.c_int32), ("amr_bsize", C.c_int32),
+                ("n_leaves", C.c_int32)]
 
 
 class fte_background(C.Structure):
-    _fields_ = [("grid", fte_grid), ("fields", C.c_void_p)]
+    _fields_ = [("grid", fte_grid), ("fields", C.c_void_p), ("leaves", C.c_void_p),
+                ("table", C.c_void_p)]
 
 
 class fte_particles(C.Structure):
@@ -83,6 +85,8 @@ SIGNATURES = {
     "fte_background_bytes": (C.c_size_t, [_P(fte_grid)]),
     "fte_load_background": (C.c_int, [_P(fte_grid), C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]),
     "fte_quantize_background": (C.c_int, [_P(fte_grid), C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]),
+    "fte_amr_table_bytes": (C.c_size_t, [_P(fte_grid)]),
+    "fte_amr_prepare": (C.c_int, [_P(fte_background), C.c_void_p]),
     "fte_tally_bins": (C.c_size_t, [_P(fte_tally_buf)]),
     "fte_tally_reset": (C.c_int, [_P(fte_tally_buf), C.c_void_p]),
     "fte_workspace_bytes": (C.c_size_t, [C.c_int, _P(fte_grid), _P(fte_tally_buf), C.c_uint64, C.c_int64]),

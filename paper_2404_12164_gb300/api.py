@@ -93,7 +93,48 @@ class Background:
             raise ValueError("invalid grid")
         self.nbytes = nbytes
         self.dev = torch.empty(nbytes // 4, dtype=torch.float32, device=device)
-        self.c = A.fte_background(self.gc, self.dev.data_ptr())
+        self.c = A.fte_background(self.gc, self.dev.data_ptr(), None, None)
+
+
+def amr_grid_c(spec, n_leaves, dtype="f32"):
+    """fte_grid of an fte_inputs.amr.AmrSpec with n_leaves leaves."""
+    c = A.fte_grid()
+    B = spec.bsize
+    c.nr, c.nth, c.nph = spec.nbr * B, spec.nbt * B, spec.nbp * B
+    c.radial = 1 if spec.radial == "log" else 0
+    c.r_min, c.r_max, c.th_min, c.th_max = spec.r_min, spec.r_max, spec.th_min, spec.th_max
+    c.n_snap, c.periodic = spec.n_snap, int(bool(spec.periodic))
+    c.t_snap0, c.dt_snap = spec.t_snap0, spec.dt_snap
+    c.dtype = DTYPES[dtype]
+    c.amr_levels, c.amr_bsize, c.n_leaves = spec.levels, B, int(n_leaves)
+    return c
+
+
+class AmrBackground(Background):
+    """Device block-AMR background: padded leaf fields, leaves and finest-level table.
+    A 16-bit copy shares the leaves and table of the FP32 background it is quantized from."""
+
+    def __init__(self, spec, leaves, device="cuda", dtype="f32", share=None):
+        self.grid = spec
+        self.dtype = dtype
+        self.gc = amr_grid_c(spec, len(leaves), dtype)
+        nbytes = A.lib().fte_background_bytes(C.byref(self.gc))
+        if nbytes == 0:
+            raise ValueError("invalid AMR grid: " + A.lib().fte_last_error().decode())
+        self.nbytes = nbytes
+        self.dev = torch.empty(nbytes // 4, dtype=torch.float32, device=device)
+        if share is not None:
+            self.leaves_dev, self.table_dev = share.leaves_dev, share.table_dev
+        else:
+            self.leaves_dev = torch.as_tensor(np.ascontiguousarray(leaves, dtype=np.int32)).to(device)
+            tb = A.lib().fte_amr_table_bytes(C.byref(self.gc))
+            self.table_dev = torch.empty(tb // 4, dtype=torch.int32, device=device)
+        self.c = A.fte_background(self.gc, self.dev.data_ptr(), self.leaves_dev.data_ptr(),
+                                  self.table_dev.data_ptr())
+
+
+def fte_amr_prepare(bg, stream=None):
+    check(A.lib().fte_amr_prepare(C.byref(bg.c), _stream(stream)), "fte_amr_prepare")
 
 
 def fte_load_background(bg, host_fields, stream=None):
@@ -116,6 +157,8 @@ def fte_quantize_background(bg_half, bg_f32, stream=None):
     """Fill the 16-bit background bg_half from the FP32 background bg_f32 (same geometry)."""
     if bg_f32.dtype != "f32" or bg_half.dtype == "f32":
         raise ValueError("quantize from an f32 background into a bf16/f16 background")
+    if bg_half.gc.amr_levels != bg_f32.gc.amr_levels:
+        raise ValueError("quantize between backgrounds of the same kind")
     check(A.lib().fte_quantize_background(C.byref(bg_half.gc), C.c_void_p(bg_f32.dev.data_ptr()),
                                           C.c_void_p(bg_half.dev.data_ptr()), bg_half.nbytes,
                                           _stream(stream)), "fte_quantize_background")

@@ -48,14 +48,36 @@ fte_status check_grid(const fte_grid* g)
     if (g->n_snap > 1 && !(g->dt_snap > 0.0)) return fail(FTE_EINVAL, "dt_snap must be > 0");
     if (g->dtype != FTE_F32 && g->dtype != FTE_BF16 && g->dtype != FTE_F16)
         return fail(FTE_EINVAL, "dtype must be FTE_F32, FTE_BF16 or FTE_F16");
+    if (g->amr_levels < 0 || g->amr_levels > 4) return fail(FTE_EINVAL, "amr_levels must be in [0, 4]");
+    if (g->amr_levels > 0) {
+        const int B = g->amr_bsize;
+        if (B < 2 || g->nr % B || g->nth % B || g->nph % B)
+            return fail(FTE_EINVAL, "AMR: block size must be >= 2 and divide nr, nth, nph");
+        if (g->n_leaves < 1) return fail(FTE_EINVAL, "AMR: n_leaves must be >= 1");
+        const double P = B + 2.0;
+        if ((double)g->n_leaves * P * P * P > 2.0e9) return fail(FTE_EINVAL, "AMR: too many records per snapshot");
+        const double nf = (double)(g->nr / B) * (g->nth / B) * (g->nph / B) * pow(8.0, g->amr_levels - 1);
+        if (nf > 2.0e9) return fail(FTE_EINVAL, "AMR: finest-level table too large");
+    } else if ((double)g->nr * g->nth * g->nph > 2.0e9) {
+        return fail(FTE_EINVAL, "too many cells per snapshot");
+    }
     const double cells = (double)g->nr * g->nth * g->nph * g->n_snap;
     if (cells * FTE_REC > 9.0e18 / 4.0) return fail(FTE_EINVAL, "grid too large");
     return FTE_OK;
 }
 
+size_t snapshot_records(const fte_grid* g)
+{
+    if (g->amr_levels > 0) {
+        const size_t P = (size_t)g->amr_bsize + 2;
+        return (size_t)g->n_leaves * P * P * P;
+    }
+    return (size_t)g->nr * g->nth * g->nph;
+}
+
 size_t grid_records(const fte_grid* g)
 {
-    return (size_t)g->nr * g->nth * g->nph * (size_t)g->n_snap;
+    return snapshot_records(g) * (size_t)g->n_snap;
 }
 
 size_t grid_bytes(const fte_grid* g)
@@ -72,7 +94,7 @@ GridK make_gridk(const fte_background* bg)
     k.fields = bg->fields;
     k.scale = bg->fields;
     k.hfields = reinterpret_cast<const uint32_t*>(bg->fields + FTE_HHDR);
-    k.snap_recs = (long long)g.nr * g.nth * g.nph;
+    k.snap_recs = (long long)snapshot_records(&g);
     k.nr = g.nr; k.nth = g.nth; k.nph = g.nph; k.radial = g.radial;
     k.r_min = (float)g.r_min; k.r_max = (float)g.r_max;
     k.th_min = (float)g.th_min; k.th_max = (float)g.th_max;
@@ -89,6 +111,22 @@ GridK make_gridk(const fte_background* bg)
     k.inv_dth = (float)(g.nth / (g.th_max - g.th_min));
     k.inv_dph = (float)(g.nph / (2.0 * kPiD));
     k.inv_dt_snap = g.n_snap > 1 ? (float)(1.0 / g.dt_snap) : 0.f;
+    k.amr = g.amr_levels;
+    k.B = g.amr_bsize;
+    k.P = g.amr_bsize + 2;
+    k.L = g.amr_levels > 0 ? g.amr_levels - 1 : 0;
+    k.amr_leaves = g.n_leaves;
+    if (g.amr_levels > 0) {
+        k.nf0 = (g.nr / g.amr_bsize) << k.L;
+        k.nf1 = (g.nth / g.amr_bsize) << k.L;
+        k.nf2 = (g.nph / g.amr_bsize) << k.L;
+    } else {
+        k.nf0 = k.nf1 = k.nf2 = 0;
+    }
+    k.leaves = reinterpret_cast<const int4*>(bg->leaves);
+    k.table = bg->table;
+    k.inv_lnr = (float)(g.radial ? 1.0 / log(g.r_max / g.r_min) : 1.0 / (g.r_max - g.r_min));
+    k.inv_thspan = (float)(1.0 / (g.th_max - g.th_min));
     return k;
 }
 
@@ -99,6 +137,8 @@ fte_status check_background(const fte_background* bg)
     if (s != FTE_OK) return s;
     if (!bg->fields) return fail(FTE_EINVAL, "background fields pointer is NULL");
     if ((uintptr_t)bg->fields % 32) return fail(FTE_EINVAL, "background fields must be 32-byte aligned");
+    if (bg->grid.amr_levels > 0 && (!bg->leaves || !bg->table || (uintptr_t)bg->leaves % 16))
+        return fail(FTE_EINVAL, "AMR background needs 16-byte aligned leaves and a table");
     return FTE_OK;
 }
 
@@ -209,6 +249,37 @@ fte_status fte_load_background(const fte_grid* g, const float* host_fields, void
     if (dev_bytes < need) return fail(FTE_ENOMEM, "device buffer has %zu bytes, needs %zu", dev_bytes, need);
     FTE_CUDA(cudaMemcpyAsync(dev_fields, host_fields, need, cudaMemcpyHostToDevice, (cudaStream_t)stream),
              "background copy");
+    return FTE_OK;
+}
+
+size_t fte_amr_table_bytes(const fte_grid* g)
+{
+    if (check_grid(g) != FTE_OK || g->amr_levels < 1) return 0;
+    const int L = g->amr_levels - 1;
+    const size_t nf = ((size_t)(g->nr / g->amr_bsize) << L) * ((size_t)(g->nth / g->amr_bsize) << L) *
+                      ((size_t)(g->nph / g->amr_bsize) << L);
+    return nf * sizeof(int32_t) + 64;   // table, then four status counters
+}
+
+fte_status fte_amr_prepare(const fte_background* bg, void* stream)
+{
+    fte_status s = check_background(bg);
+    if (s != FTE_OK) return s;
+    if (bg->grid.amr_levels < 1) return fail(FTE_EINVAL, "not an AMR background");
+    if (bg->grid.dtype != FTE_F32) return fail(FTE_EINVAL, "prepare the FP32 background, then quantize it");
+    const GridK g = make_gridk(bg);
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t nt = (size_t)g.nf0 * g.nf1 * g.nf2;
+    unsigned* status = reinterpret_cast<unsigned*>(bg->table + nt);
+    FTE_CUDA(launch_amr_table(g, bg->table, status, st), "AMR table launch");
+    unsigned h[4] = {0, 0, 0, 0};
+    FTE_CUDA(cudaMemcpyAsync(h, status, sizeof(h), cudaMemcpyDeviceToHost, st), "AMR status copy");
+    FTE_CUDA(cudaStreamSynchronize(st), "stream sync");
+    if (h[0] || h[1] || h[2] || h[3])
+        return fail(FTE_EINVAL, "AMR leaves: %u malformed, %u overlapping finest blocks, %u uncovered, "
+                    "%u nesting violations", h[0], h[1], h[2], h[3]);
+    FTE_CUDA(launch_amr_ghosts(g, bg->grid.n_snap, bg->grid.r_min, bg->grid.r_max, bg->grid.th_min,
+                               bg->grid.th_max, st), "AMR ghost launch");
     return FTE_OK;
 }
 

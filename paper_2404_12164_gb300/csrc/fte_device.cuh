@@ -41,6 +41,13 @@ struct GridK {
     float dr;                // linear: (r_max - r_min) / nr; log: ln(r_max / r_min) / nr
     float inv_dth, dth, inv_dph;
     float inv_dt_snap;
+    // block AMR (amr > 0: number of levels); nr, nth, nph are base-level cells
+    int amr, B, P, L, amr_leaves;
+    int nf0, nf1, nf2;                // finest-level blocks per axis
+    const int4* leaves;               // (level, bi, bj, bk)
+    const int* table;                 // [nf2][nf1][nf0] leaf ids
+    float inv_lnr;                    // 1 / ln(r_max / r_min) (log) or 1 / (r_max - r_min)
+    float inv_thspan;
 };
 
 struct ParamsK {
@@ -142,12 +149,95 @@ __device__ __forceinline__ void dmumu(const ParamsK& P, float I, float mu, float
 // ---------------------------------------------------------------------------
 struct Loc {
     int i0, j0, k0, k1;
+    int base[4];             // record (within a snapshot) of the lower r-neighbour of corner
+                             // c = ct + 2 cp, ct/cp the upper theta/phi neighbour flags
     float fr, ft, fp;        // weights of the upper neighbour
     float dfr, dft, dfp;     // d(weight)/d(coordinate); 0 where clamped
 };
 
+// Block AMR: the leaf holding a point and the point's cell within it (interior
+// indices 0..B-1 along r, theta, phi).
+__device__ __forceinline__ int amr_containing(const GridK& g, float r, float th, float ph, int& ci, int& cj,
+                                              int& ck)
+{
+    const float ur = g.radial ? logf(r / g.r_min) * g.inv_lnr : (r - g.r_min) * g.inv_lnr;
+    const float ut = (th - g.th_min) * g.inv_thspan;
+    const float up = ph * (1.f / kTwoPi);
+    const int f0 = min(max((int)floorf(ur * (float)g.nf0), 0), g.nf0 - 1);
+    const int f1 = min(max((int)floorf(ut * (float)g.nf1), 0), g.nf1 - 1);
+    int f2 = (int)floorf(up * (float)g.nf2);
+    if (f2 < 0) f2 += g.nf2;
+    if (f2 >= g.nf2) f2 -= g.nf2;
+    // the clamp keeps every address inside the arrays even for a table that was never prepared
+    const int leaf = min(max(__ldg(g.table + ((long long)f2 * g.nf1 + f1) * g.nf0 + f0), 0), g.amr_leaves - 1);
+    const int4 lf = __ldg(g.leaves + leaf);
+    const float s = (float)(1 << lf.x);
+    const float xr = (g.radial ? logf(r / g.r_min) * g.inv_dr : (r - g.r_min) * g.inv_dr) * s;
+    ci = min(max((int)floorf(xr) - lf.y * g.B, 0), g.B - 1);
+    cj = min(max((int)floorf((th - g.th_min) * g.inv_dth * s) - lf.z * g.B, 0), g.B - 1);
+    ck = min(max((int)floorf(ph * g.inv_dph * s) - lf.w * g.B, 0), g.B - 1);
+    return leaf;
+}
+
+// Block AMR: leaf from the finest-level table, then the bracketing cells on the
+// leaf's padded lattice (level-l cell coordinate x = u n_l - 1/2, weights in the
+// physical coordinate).  The ghost layer supplies the neighbours' values.
+__device__ __forceinline__ void locate_amr(const GridK& g, float r, float th, float ph, Loc& L)
+{
+    const float ur = g.radial ? logf(r / g.r_min) * g.inv_lnr : (r - g.r_min) * g.inv_lnr;
+    const float ut = (th - g.th_min) * g.inv_thspan;
+    const float up = ph * (1.f / kTwoPi);
+    const int f0 = min(max((int)floorf(ur * (float)g.nf0), 0), g.nf0 - 1);
+    const int f1 = min(max((int)floorf(ut * (float)g.nf1), 0), g.nf1 - 1);
+    int f2 = (int)floorf(up * (float)g.nf2);
+    if (f2 < 0) f2 += g.nf2;
+    if (f2 >= g.nf2) f2 -= g.nf2;
+    // the clamp keeps every address inside the arrays even for a table that was never prepared
+    const int leaf = min(max(__ldg(g.table + ((long long)f2 * g.nf1 + f1) * g.nf0 + f0), 0), g.amr_leaves - 1);
+    const int4 lf = __ldg(g.leaves + leaf);
+    const float s = (float)(1 << lf.x);
+    const int B = g.B, P = g.P;
+    // r
+    float x = (g.radial ? logf(r / g.r_min) * g.inv_dr : (r - g.r_min) * g.inv_dr) * s - 0.5f;
+    int lo = lf.y * B - 1;
+    int i = min(max((int)floorf(x), lo), lo + B);
+    if (g.radial) {
+        const float c0 = g.r_min * expf(((float)i + 0.5f) * g.dr / s);
+        const float c1 = g.r_min * expf(((float)i + 1.5f) * g.dr / s);
+        L.dfr = 1.f / (c1 - c0);
+        L.fr = (r - c0) * L.dfr;
+    } else {
+        L.fr = x - (float)i;
+        L.dfr = g.inv_dr * s;
+    }
+    const int ii = i - lo;
+    // theta
+    x = (th - g.th_min) * g.inv_dth * s - 0.5f;
+    lo = lf.z * B - 1;
+    i = min(max((int)floorf(x), lo), lo + B);
+    L.ft = x - (float)i;
+    L.dft = g.inv_dth * s;
+    const int jj = i - lo;
+    // phi
+    x = ph * g.inv_dph * s - 0.5f;
+    lo = lf.w * B - 1;
+    i = min(max((int)floorf(x), lo), lo + B);
+    L.fp = x - (float)i;
+    L.dfp = g.inv_dph * s;
+    const int kk = i - lo;
+    const int b0 = ((leaf * P + kk) * P + jj) * P + ii;
+    L.base[0] = b0;
+    L.base[1] = b0 + P;
+    L.base[2] = b0 + P * P;
+    L.base[3] = b0 + P * P + P;
+}
+
 __device__ __forceinline__ void locate(const GridK& g, float r, float th, float ph, Loc& L)
 {
+    if (g.amr) {
+        locate_amr(g, r, th, ph, L);
+        return;
+    }
     float xi = g.radial ? logf(r / g.r_min) * g.inv_dr - 0.5f : (r - g.r_min) * g.inv_dr - 0.5f;
     if (xi < 0.f) {
         L.i0 = 0; L.fr = 0.f; L.dfr = 0.f;
@@ -184,6 +274,10 @@ __device__ __forceinline__ void locate(const GridK& g, float r, float th, float 
     if (k0 >= g.nph) k0 -= g.nph;
     L.k0 = k0;
     L.k1 = (k0 + 1 == g.nph) ? 0 : k0 + 1;
+    L.base[0] = (L.k0 * g.nth + L.j0) * g.nr + L.i0;
+    L.base[1] = L.base[0] + g.nr;
+    L.base[2] = (L.k1 * g.nth + L.j0) * g.nr + L.i0;
+    L.base[3] = L.base[2] + g.nr;
 }
 
 // 32-byte read-only loads (one sector each); the address must be 32-byte aligned.
@@ -256,12 +350,10 @@ __device__ __forceinline__ void gather(const GridK& g, const StepEntry& e, const
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
             const int ct = c & 1, cp = c >> 1;
-            const int j = L.j0 + ct;
-            const int k = cp ? L.k1 : L.k0;
             const float wt_ = ct ? L.ft : 1.f - L.ft;
             const float wp_ = cp ? L.fp : 1.f - L.fp;
             const float wjk = wt_ * wp_;
-            const long long rec = ((long long)snap * g.snap_recs + ((long long)k * g.nth + j) * g.nr + L.i0);
+            const long long rec = (long long)snap * g.snap_recs + L.base[c];
             float lo[FTE_NFIELD], hi[FTE_NFIELD];
             if (DT == FTE_F32) {
                 float a[2 * FTE_REC];

@@ -56,16 +56,24 @@ __global__ void __launch_bounds__(256) inject_kernel(const InjectArgs a)
                 ph = a.ph1 + u01(q.z) * (a.ph2 - a.ph1);
                 if (!a.use_divv) { ok = true; break; }
                 const GridK& g = a.g;
-                const float xr = g.radial ? logf(r / g.r_min) * g.inv_dr : (r - g.r_min) * g.inv_dr;
-                const float xt = (th - g.th_min) * g.inv_dth;
                 float phw = fmodf(ph, kTwoPi);
                 if (phw < 0.f) phw += kTwoPi;
-                const float xp = phw * g.inv_dph;
-                const int ci = min(max((int)floorf(xr), 0), g.nr - 1);
-                const int cj = min(max((int)floorf(xt), 0), g.nth - 1);
-                int ck = (int)floorf(xp) % g.nph;
-                if (ck < 0) ck += g.nph;
-                const long long ri = (((long long)a.divv_snap * g.nph + ck) * g.nth + cj) * g.nr + ci;
+                long long ri;
+                if (g.amr) {
+                    int ci, cj, ck;
+                    const int leaf = amr_containing(g, r, th, phw, ci, cj, ck);
+                    ri = (long long)a.divv_snap * g.snap_recs +
+                         (((long long)leaf * g.P + ck + 1) * g.P + cj + 1) * g.P + ci + 1;
+                } else {
+                    const float xr = g.radial ? logf(r / g.r_min) * g.inv_dr : (r - g.r_min) * g.inv_dr;
+                    const float xt = (th - g.th_min) * g.inv_dth;
+                    const float xp = phw * g.inv_dph;
+                    const int ci = min(max((int)floorf(xr), 0), g.nr - 1);
+                    const int cj = min(max((int)floorf(xt), 0), g.nth - 1);
+                    int ck = (int)floorf(xp) % g.nph;
+                    if (ck < 0) ck += g.nph;
+                    ri = (long long)a.divv_snap * g.snap_recs + ((long long)ck * g.nth + cj) * g.nr + ci;
+                }
                 float g00, g11, g22;
                 if (g.dtype == FTE_F32) {
                     const float* rec = g.fields + ri * FTE_REC;

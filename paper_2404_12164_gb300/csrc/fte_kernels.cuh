@@ -90,6 +90,11 @@ cudaError_t advance_occupancy(int kperp, int dtype, size_t smem, int* blocks_per
 size_t sort_scratch_bytes(const GridK& g, unsigned long long n);
 void sort_carve(const GridK& g, unsigned long long n, char* p, SortArgs* a);
 cudaError_t launch_sort(const SortArgs& a, cudaStream_t s);
+// block AMR set-up (fte_amr.cu): status[0] malformed leaves, [1] overlaps,
+// [2] uncovered finest blocks, [3] 2:1 nesting violations
+cudaError_t launch_amr_table(const GridK& g, int* table, unsigned* status, cudaStream_t s);
+cudaError_t launch_amr_ghosts(const GridK& g, int n_snap, double r_min, double r_max, double th_min,
+                              double th_max, cudaStream_t s);
 // random-sector read probe (fte_probe.cu)
 cudaError_t launch_probe(const float* buf, unsigned long long nsec, int threads, int loads, float* out,
                          cudaStream_t s);

@@ -7,6 +7,8 @@
 
 namespace fte {
 
+__device__ __forceinline__ int amr_sub(const GridK& g) { return g.B >= 4 ? g.B / 4 : 1; }
+
 __device__ __forceinline__ int bucket_of(const GridK& g, float x, float y, float z)
 {
     const float rho2 = x * x + y * y;
@@ -14,6 +16,12 @@ __device__ __forceinline__ int bucket_of(const GridK& g, float x, float y, float
     const float th = atan2f(sqrtf(rho2), z);
     float ph = atan2f(y, x);
     if (ph < 0.f) ph += kTwoPi;
+    if (g.amr) {      // AMR: leaf, then sub-blocks of (B/4)^3 cells
+        int ci, cj, ck;
+        const int leaf = amr_containing(g, r, th, ph, ci, cj, ck);
+        const int sb = amr_sub(g), ns = g.B / sb;
+        return ((leaf * ns + ck / sb) * ns + cj / sb) * ns + ci / sb;
+    }
     const float xr = g.radial ? logf(r / g.r_min) * g.inv_dr : (r - g.r_min) * g.inv_dr;
     const int i = min(max((int)xr, 0), g.nr - 1);
     const int j = min(max((int)((th - g.th_min) * g.inv_dth), 0), g.nth - 1);
@@ -129,6 +137,10 @@ __global__ void __launch_bounds__(256) scatter_kernel(const SortArgs a)
 
 int sort_buckets(const GridK& g)
 {
+    if (g.amr) {
+        const int sb = g.B >= 4 ? g.B / 4 : 1, ns = g.B / sb;
+        return g.amr_leaves * ns * ns * ns;
+    }
     return g.nph * g.nth * ((g.nr + 1) >> 1);
 }
 

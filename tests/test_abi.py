@@ -43,7 +43,7 @@ def test_version_and_status_strings(L):
 
 def test_struct_sizes_match_header_layout():
     from paper_2404_12164_gb300 import _abi as A
-    assert C.sizeof(A.fte_grid) == 4 * 4 + 4 * 8 + 2 * 4 + 2 * 8 + 2 * 4
+    assert C.sizeof(A.fte_grid) == 4 * 4 + 4 * 8 + 2 * 4 + 2 * 8 + 4 * 4
     assert C.sizeof(A.fte_observer) == 4 * 4 + 10 * 8
     assert C.sizeof(A.fte_params) == 4 * 4 + 10 * 8 + 4 * 4
     assert C.sizeof(A.fte_inject_spec) == 4 * 4 + 9 * 8 + 4 * 4 + 6 * 8 + 4 * 4

@@ -1,0 +1,220 @@
+"""Block-AMR backgrounds on the GPU vs the FP64 oracle (Sec. 2.4, Fig. 4).
+
+* the finest-level lookup table built on the device equals the host table
+  (integer work: exact);
+* every ghost value the device fills equals the oracle's on-demand neighbour
+  value (FP64 on both sides, stored in FP32: within FP32 rounding);
+* malformed trees are refused;
+* trajectories on a refined CIR background match the oracle per trajectory;
+  an unrefined AMR background gives the uniform-grid trajectories;
+* tallies within 3 sigma, ledger conserved, reordering changes nothing;
+* the BF16 storage form on AMR: tally total within the stated storage error.
+"""
+import dataclasses
+import math
+
+import numpy as np
+import pytest
+
+from fte_inputs import amr, backgrounds, configs
+from fte_inputs.configs import InjectSpec, Observer, Params
+from fte_inputs.grid import GridSpec
+from oracle import oracle as O
+from tests._parity import trajectory_errors
+
+pytestmark = pytest.mark.gpu
+DEG = math.pi / 180
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2404_12164_gb300 import build
+    build.build()
+
+
+@pytest.fixture(scope="module")
+def cir_amr():
+    spec = amr.AmrSpec(nbr=4, nbt=2, nbp=4, bsize=8, levels=3, n_snap=3, periodic=False, dt_snap=3600.0)
+    leaves = amr.build_leaves(spec, amr.divv_refiner(spec, threshold=8e-6, r_from=0.9))
+    return spec, leaves, amr.fields(spec, leaves)
+
+
+def _inject_spec():
+    return InjectSpec(region="box", r1=1.0, r2=2.0, th1=88 * DEG, th2=92 * DEG, ph1=math.pi,
+                      ph2=2 * math.pi, divv_max=0.0, divv_snap=0, max_tries=4096, energy="mono",
+                      e0=0.05, weight="r-2", seed=0)
+
+
+def _device_bg(spec, leaves, f):
+    from paper_2404_12164_gb300 import api
+    bg = api.AmrBackground(spec, leaves)
+    api.fte_load_background(bg, f)
+    api.fte_amr_prepare(bg)
+    return bg
+
+
+def _gpu_advance(bg, inj, prm, n, chunks, observers):
+    import torch
+    from paper_2404_12164_gb300 import api, _abi as A
+    pool = api.Particles(n)
+    tally = api.Tally(observers)
+    api.fte_tally_reset(tally)
+    failed = api.fte_inject(pool, bg, inj, n, tally)
+    states = {0: pool.state()}
+    ws = api.Workspace()
+    prev = 0
+    for c in chunks:
+        api.fte_advance(pool, bg, prm, tally, prev, c, ws)
+        prev = c
+        states[c] = pool.state()
+    tallies = [{k: api.fte_tally(tally, o, kind) for k, kind in
+                (("S", A.FTE_TALLY_S), ("S2", A.FTE_TALLY_S2), ("C", A.FTE_TALLY_C))}
+               for o in range(len(observers))]
+    lw, ln = api.fte_ledger(tally)
+    torch.cuda.synchronize()
+    return dict(states=states, tallies=tallies, ledger_w=lw, ledger_n=ln, failed=failed)
+
+
+def _oracle_advance(obg, inj, prm, n, chunks, observers):
+    P, led = O.inject(obg, inj, np.arange(n))
+    T = O.Tally(observers)
+    states = {0: P.copy()}
+    prev = 0
+    for c in chunks:
+        O.advance(obg, prm, P, prev, c, tally=T, ledger=led)
+        prev = c
+        states[c] = P.copy()
+    tallies = [dict(S=T.obs_view(o, T.S), S2=T.obs_view(o, T.S2), C=T.obs_view(o, T.C))
+               for o in range(len(observers))]
+    return dict(states=states, tallies=tallies, ledger=led.as_dict())
+
+
+def test_table_and_ghost_layer(cir_amr):
+    spec, leaves, f = cir_amr
+    bg = _device_bg(spec, leaves, f)
+    tab = bg.table_dev.cpu().numpy()
+    host = amr.finest_table(spec, leaves).ravel()
+    assert np.array_equal(tab[:host.size], host)
+    P = spec.bsize + 2
+    dev = bg.dev.cpu().numpy().reshape(spec.n_snap, len(leaves), P, P, P, -1)
+    # interior untouched
+    assert np.array_equal(dev[:, :, 1:-1, 1:-1, 1:-1], f[:, :, 1:-1, 1:-1, 1:-1])
+    obg = O.amr_background(spec, leaves, f)
+    scale = np.abs(f[..., :18]).max(axis=(0, 1, 2, 3, 4))
+    rng = np.random.default_rng(0)
+    lv = leaves[:, 0]
+    seen = set()
+    for _ in range(6000):
+        s = int(rng.integers(0, spec.n_snap))
+        n = int(rng.integers(0, len(leaves)))
+        face = rng.integers(0, 3)
+        idx = list(rng.integers(0, P, 3))
+        idx[face] = int(rng.choice([0, P - 1]))
+        lk, lj, li = idx
+        ref = O.amr_cell(obg, s, n, li, lj, lk)
+        got = dev[s, n, lk, lj, li, :18].astype(np.float64)
+        assert np.all(np.abs(got - ref) <= 2e-6 * scale + 1e-30), (s, n, li, lj, lk)
+        seen.add(int(lv[n]))
+    assert seen == {0, 1, 2}
+
+
+def test_prepare_refuses_malformed_trees(cir_amr):
+    from paper_2404_12164_gb300 import api, _abi as A
+    spec, leaves, f = cir_amr
+    bad_sets = [leaves[1:],                                          # a hole
+                np.concatenate([leaves, leaves[:1]]),                 # an overlap
+                np.concatenate([leaves[:-1], [[7, 0, 0, 0]]])]        # a level out of range
+    for bad in bad_sets:
+        fb = np.zeros((spec.n_snap, len(bad)) + f.shape[2:], np.float32)
+        bg = api.AmrBackground(spec, bad)
+        api.fte_load_background(bg, fb)
+        with pytest.raises(A.FteError) as e:
+            api.fte_amr_prepare(bg)
+        assert e.value.status == A.FTE_EINVAL
+
+
+def test_trajectories_on_refined_amr(cir_amr):
+    spec, leaves, f = cir_amr
+    bg = _device_bg(spec, leaves, f)
+    obg = O.amr_background(spec, leaves, f)
+    prm = Params(dmumu="qlt", lambda_par=0.1, dt=10.0)
+    inj = _inject_spec()
+    chunks = [1, 60, 500]
+    obs = [Observer(kind="shell", r=1.5, dr=0.05, e_lo=0.01, e_hi=10.0, ne=16, t_lo=0.0, t_hi=5000.0, nt=10)]
+    g = _gpu_advance(bg, inj, prm, 6000, chunks, obs)
+    o = _oracle_advance(obg, inj, prm, 6000, chunks, obs)
+    assert g["failed"] == 0
+    for c in [0] + chunks:
+        ok, e = trajectory_errors(g["states"][c], o["states"][c], max(c, 1))
+        assert ok.sum() >= 500, (c, ok.sum())
+        for k in ("pos", "mu", "p", "w"):
+            assert e[k].max() <= 1e-4, (c, k, float(e[k].max()))
+        assert e["status"].sum() == 0
+    # particles sit on every level during the run
+    st = o["states"][500]
+    r = np.sqrt(st["x"] ** 2 + st["y"] ** 2 + st["z"] ** 2)
+    assert r.min() < 1.0 < r.max()
+    tg, to = g["tallies"][0], o["tallies"][0]
+    sig = np.sqrt(tg["S2"] + to["S2"])
+    assert np.all(np.abs(tg["S"] - to["S"]) <= 3 * sig + 1e-9 * max(to["S"].max(), 1e-30))
+    assert int(g["ledger_n"][0]) == 6000
+    alive = g["states"][500]["status"] == 0
+    total = g["states"][500]["w"][alive].astype(np.float64).sum() + g["ledger_w"][1:5].sum()
+    assert total == pytest.approx(g["ledger_w"][0], rel=1e-12)
+
+
+def test_unrefined_amr_matches_uniform_grid():
+    from paper_2404_12164_gb300 import api
+    spec = amr.AmrSpec(nbr=8, nbt=4, nbp=12, bsize=8, levels=2, n_snap=2, periodic=True, dt_snap=3600.0)
+    g = GridSpec(nr=64, nth=32, nph=96, n_snap=2, periodic=True, dt_snap=3600.0)
+    uni = backgrounds.cir(g)
+    leaves, f = amr.from_uniform(spec, uni)
+    ba = _device_bg(spec, leaves, f)
+    bu = api.Background(g)
+    api.fte_load_background(bu, uni)
+    prm = Params(dmumu="qlt", lambda_par=0.1, dt=10.0)
+    inj = _inject_spec()
+    obs = [Observer(kind="shell", r=1.5, dr=0.05, e_lo=0.01, e_hi=10.0, ne=16, t_lo=0.0, t_hi=5000.0, nt=10)]
+    a = _gpu_advance(ba, inj, prm, 4000, [300], obs)["states"][300]
+    u = _gpu_advance(bu, inj, prm, 4000, [300], obs)["states"][300]
+    same = (a["status"] == u["status"])
+    assert same.mean() > 0.99
+    r = np.sqrt(u["x"] ** 2 + u["y"] ** 2 + u["z"] ** 2)
+    dx = np.sqrt((a["x"] - u["x"]) ** 2 + (a["y"] - u["y"]) ** 2 + (a["z"] - u["z"]) ** 2) / r
+    # identical up to FP32 rounding until chaotic events; most trajectories stay together
+    assert np.median(dx[same]) < 1e-6
+    assert np.mean(dx[same] < 1e-4) > 0.5
+
+
+def test_reordering_on_amr_changes_nothing(cir_amr):
+    spec, leaves, f = cir_amr
+    bg = _device_bg(spec, leaves, f)
+    inj = _inject_spec()
+    obs = [Observer(kind="shell", r=1.5, dr=0.05, e_lo=0.01, e_hi=10.0, ne=16, t_lo=0.0, t_hi=5000.0, nt=10)]
+    p0 = Params(dmumu="qlt", lambda_par=0.1, dt=10.0)
+    p1 = dataclasses.replace(p0, sort_every=32)
+    a = _gpu_advance(bg, inj, p0, 3000, [200], obs)
+    b = _gpu_advance(bg, inj, p1, 3000, [200], obs)
+    for k in ("x", "y", "z", "mu", "p", "status"):
+        assert np.array_equal(a["states"][200][k], b["states"][200][k]), k
+    assert np.array_equal(a["tallies"][0]["C"], b["tallies"][0]["C"])
+
+
+def test_bf16_on_amr_tally_error(cir_amr):
+    from paper_2404_12164_gb300 import api
+    spec, leaves, f = cir_amr
+    bg = _device_bg(spec, leaves, f)
+    bh = api.AmrBackground(spec, leaves, dtype="bf16", share=bg)
+    api.fte_quantize_background(bh, bg)
+    prm = Params(dmumu="qlt", lambda_par=0.1, dt=10.0)
+    inj = _inject_spec()
+    obs = [Observer(kind="shell", r=1.5, dr=0.05, e_lo=0.01, e_hi=10.0, ne=16, t_lo=0.0, t_hi=20000.0, nt=10)]
+    g = _gpu_advance(bh, inj, prm, 6000, [2000], obs)
+    o = _oracle_advance(O.amr_background(spec, leaves, f), inj, prm, 6000, [2000], obs)
+    S, So = g["tallies"][0]["S"].sum(), o["tallies"][0]["S"].sum()
+    sig = math.sqrt(g["tallies"][0]["S2"].sum() + o["tallies"][0]["S2"].sum())
+    print(f"AMR bf16 vs fp32 oracle: total S rel diff {abs(S - So) / So:.3e}, sigma {sig / So:.3e}")
+    assert abs(S - So) <= 3 * sig + 0.02 * So
