@@ -20,6 +20,7 @@ ids, weak scaling) and the tallies are summed over ranks after each step.
 sample of the same workload.
 """
 import argparse
+import dataclasses
 import json
 import math
 import os
@@ -371,11 +372,20 @@ def run_profile_case(args):
     from paper_2404_12164_gb300 import api, build
     build.build()
     torch.cuda.set_device(0)
-    w = configs.scaled(configs.cir_uniform_1e6(), n_snap=2, n_particles=1 << 18)
-    w.params.sort_every = args.sort_every
-    fields = configs.build_background(w)
-    bg = api.Background(w.grid)
-    api.fte_load_background(bg, fields)
+    if args.grid == "amr":
+        # block-AMR form of the same: base 16x4x8 blocks of 16^3 cells, 3 levels (3,872 leaves,
+        # 4.3 GB for two snapshots)
+        from fte_inputs.amr import AmrSpec
+        spec = AmrSpec(nbr=16, nbt=4, nbp=8, bsize=16, levels=3, n_snap=2, dt_snap=3600.0)
+        w = configs.cir_amr_1e7(n_particles=1 << 18, n_steps=256 * args.launches, spec=spec)
+        w.params.sort_every = args.sort_every
+        bg, _ = build_amr_background(w, api)
+    else:
+        w = configs.scaled(configs.cir_uniform_1e6(), n_snap=2, n_particles=1 << 18)
+        w.params.sort_every = args.sort_every
+        fields = configs.build_background(w)
+        bg = api.Background(w.grid)
+        api.fte_load_background(bg, fields)
     pool = api.Particles(w.n_particles)
     tally = api.Tally(w.observers)
     api.fte_tally_reset(tally)
@@ -387,6 +397,229 @@ def run_profile_case(args):
     torch.cuda.synchronize()
     print(json.dumps({"case": "profile", "launches": args.launches, "particle_steps": int(ln[6]),
                       "alg_bytes": int(ln[6]) * ALG_BYTES}))
+
+
+def build_amr_background(w, api, device="cuda"):
+    """Leaves and FP32 fields of a block-AMR workload, generated on the device straight into
+    the background buffer; then the lookup table and ghost layers (fte_amr_prepare)."""
+    import torch
+    from fte_inputs import amr
+    from fte_inputs.grid import REC
+    spec = w.grid
+    leaves = amr.build_leaves(spec, amr.divv_refiner_batched(spec, w.amr_divv, device=device))
+    bg = api.AmrBackground(spec, leaves, device=device)
+    P = spec.bsize + 2
+    view = bg.dev.view(spec.n_snap, len(leaves), P, P, P, REC)
+    view.zero_()
+    amr.fields_batched(spec, leaves, device=device, out=view)
+    api.fte_amr_prepare(bg)
+    torch.cuda.synchronize()
+    return bg, leaves
+
+
+def run_amr_case(args):
+    """Block-AMR workload (cir_amr_1e7): FP32, BF16 and FP16 storage, one line of JSON."""
+    import torch
+    from paper_2404_12164_gb300 import api, build
+    from paper_2404_12164_gb300 import _abi as A
+    build.build()
+    torch.cuda.set_device(0)
+    w = configs.cir_amr_1e7(n_particles=args.amr_particles, n_steps=args.amr_steps)
+    t_gen = time.perf_counter()
+    bg, leaves = build_amr_background(w, api)
+    t_gen = time.perf_counter() - t_gen
+    n_part, n_steps = w.n_particles, w.n_steps
+    stream = torch.cuda.current_stream()
+    pool = api.Particles(n_part)
+    tally = api.Tally(w.observers)
+    wsp = api.Workspace()
+    wsp.ensure(api.fte_workspace_bytes(bg, tally, n_part, CHUNK))
+    alg = ALG_BYTES + 4                  # + the 4-byte finest-level table entry
+
+    def one_step(b, launches=None):
+        pool.c.count = 0
+        api.fte_tally_reset(tally)
+        api.fte_inject(pool, b, w.inject, n_part, tally, check_failed=False)
+        for c in range(0, n_steps, CHUNK):
+            e = min(c + CHUNK, n_steps)
+            if launches is not None:
+                ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                ev[0].record(stream)
+            api.fte_advance(pool, b, w.params, tally, c, e, wsp)
+            if launches is not None:
+                ev[1].record(stream)
+                launches.append(ev)
+
+    def measure(b, steps, warmup, clocks=None):
+        for _ in range(warmup):
+            one_step(b)
+        torch.cuda.synchronize()
+        if clocks:
+            clocks.start()
+        launches, done = [], 0
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(steps):
+            one_step(b, launches)
+            done += int(tally.ledger_n.cpu().numpy()[6])
+        t1.record(stream)
+        torch.cuda.synchronize()
+        if clocks:
+            clocks.result = clocks.stop()
+        ms = t0.elapsed_time(t1)
+        k_ms = sum(a_.elapsed_time(b_) for a_, b_ in launches)
+        S = np.array([api.fte_tally(tally, o, A.FTE_TALLY_S).sum() for o in range(len(w.observers))])
+        S2 = np.array([api.fte_tally(tally, o, A.FTE_TALLY_S2).sum() for o in range(len(w.observers))])
+        return ms, k_ms, done, S, S2
+
+    peak, peak_kind = _peaks()
+    clocks = Clocks(0)
+    ms, k_ms, done, S, S2 = measure(bg, args.steps, args.warmup, clocks)
+    achieved = done * alg / (k_ms / 1e3) / 1e9
+    forms = {}
+    if not args.no_forms:
+        for dt in ("bf16", "f16"):
+            bh = api.AmrBackground(w.grid, leaves, dtype=dt, share=bg)
+            api.fte_quantize_background(bh, bg)
+            f_ms, f_kms, f_done, Sh, S2h = measure(bh, args.steps, max(1, args.warmup // 3))
+            f_alg = f_done * (ALG_BYTES // 2 + 4) / (f_kms / 1e3) / 1e9
+            forms[dt] = {"value": f_done / (f_ms / 1e3), "unit": UNIT,
+                         "speedup_vs_f32": (f_done / f_ms) / (done / ms),
+                         "roofline": {"achieved": f_alg, "peak": peak, "unit": "GB/s", "frac": f_alg / peak,
+                                      "alg_bytes_per_particle_step": ALG_BYTES // 2 + 4},
+                         "tally_total_rel_diff_vs_f32": [float(abs(a - b) / b) if b > 0 else None
+                                                         for a, b in zip(Sh, S)],
+                         "background_bytes": int(bh.nbytes)}
+            del bh
+            torch.cuda.empty_cache()
+    lv = np.bincount(leaves[:, 0], minlength=w.grid.levels)
+    print(json.dumps({
+        "case": "amr", "metric": METRIC, "value": done / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "cir_amr_1e7: synthetic CIR on a log-r 3-level block-AMR grid (16^3 blocks, "
+                               "base 32x8x24, refined where |div V| > 6e-5/s), 2 hourly snapshots, "
+                               f"{n_part:.0e} protons E^-3 over 50 keV-5 MeV (1-2 au, 90+-2 deg, w=1/r^2), "
+                               f"QLT q=5/3 H=0.05 lambda_par=0.1 au, dt=2 s x {n_steps}, "
+                               "4 observer boxes 16x144",
+                   "leaves": int(len(leaves)), "leaves_per_level": lv.tolist(),
+                   "background_bytes": int(bg.nbytes), "generate_s": t_gen,
+                   "tally_rel_err": [float(math.sqrt(b) / a) if a > 0 else None for a, b in zip(S, S2)]},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)",
+                     "kernel": "advance_kernel", "alg_bytes_per_particle_step": alg,
+                     "kernel_ms_total": k_ms},
+        "clocks": clocks.result,
+        "forms": forms,
+    }), flush=True)
+
+
+def run_ensemble_case(args):
+    """Ensemble workload (cir_ensemble_64): 64 parameter sets with uneven counts.  Three arms on
+    the same particles: the single-set kernel run set after set; the ensemble kernel with the
+    default launch configuration; the autotuned configuration replayed as one CUDA graph."""
+    import torch
+    from paper_2404_12164_gb300 import api, build
+    from paper_2404_12164_gb300 import _abi as A
+    build.build()
+    torch.cuda.set_device(0)
+    w0, fields = build_workload()
+    w = configs.cir_ensemble_64(n_steps=args.ens_steps)
+    w.params.sort_every = args.sort_every
+    sets, n_steps, n_tot = w.sets, w.n_steps, w.n_particles
+    bg = api.Background(w.grid)
+    api.fte_load_background(bg, torch.from_numpy(np.ascontiguousarray(fields)))
+    del fields
+    side = torch.cuda.Stream()
+    pool = api.Particles(n_tot)
+    tally = api.Tally(w.observers, n_sets=len(sets))
+    ws = api.Workspace()
+    ws.ensure(max(api.fte_workspace_bytes_batched(bg, tally, n_tot, n_steps),
+                  api.fte_workspace_bytes(bg, api.Tally(w.observers), n_tot, n_steps)))
+    torch.cuda.synchronize()
+
+    def timed(fn, steps, warmup):
+        for _ in range(warmup):
+            fn()
+        side.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        done = 0
+        with torch.cuda.stream(side):
+            e0.record(side)
+            for _ in range(steps):
+                fn()
+                done += int(tally.ledger_n.cpu().numpy()[6]) if fn is not plain_step else plain_done[0]
+            e1.record(side)
+        side.synchronize()
+        return done / (e0.elapsed_time(e1) / 1e3), e0.elapsed_time(e1) / steps
+
+    # arm 1: the single-set kernel, set after set (each set its own pool slice and tally)
+    one_tally = api.Tally(w.observers)
+    plain_done = [0]
+
+    def plain_step():
+        plain_done[0] = 0
+        for s in sets:
+            sub = api.Particles(s.count) if s.count not in sub_pools else sub_pools[s.count]
+            sub_pools[s.count] = sub
+            sub.c.count = 0
+            api.fte_tally_reset(one_tally, stream=side)
+            api.fte_inject(sub, bg, s.inject, s.count, one_tally, id_base=0, check_failed=False, stream=side)
+            prm = dataclasses.replace(w.params, lambda_par=s.lambda_par, q=s.q, H=s.H, eps=s.eps,
+                                      seed=s.seed, set_id=s.set_id)
+            api.fte_advance(sub, bg, prm, one_tally, 0, n_steps, ws, stream=side)
+            plain_done[0] += int(one_tally.ledger_n.cpu().numpy()[6])
+    sub_pools = {}
+    with torch.cuda.stream(side):
+        plain_rate, plain_ms = timed(plain_step, args.ens_timed, 1)
+    sub_pools.clear()
+    torch.cuda.empty_cache()
+
+    # arm 2: ensemble kernel, default configuration, eager calls
+    def batched_step(cfg=None):
+        pool.c.count = 0
+        api.fte_tally_reset(tally, stream=side)
+        api.fte_inject_batched(pool, bg, sets, tally, stream=side)
+        api.fte_advance_batched(pool, bg, w.params, sets, tally, 0, n_steps, ws, config=cfg, stream=side)
+    with torch.cuda.stream(side):
+        eager_rate, eager_ms = timed(batched_step, args.ens_timed, 1)
+
+    # arm 3: autotune on one pass, then capture one pass into a graph and replay it
+    with torch.cuda.stream(side):
+        pool.c.count = 0
+        api.fte_tally_reset(tally, stream=side)
+        api.fte_inject_batched(pool, bg, sets, tally, stream=side)
+        best, tried = api.fte_autotune_batched(pool, bg, w.params, sets, tally, 0, n_steps, ws, stream=side)
+        side.synchronize()
+        g = api.Graph()
+        with g.capture(side):
+            batched_step(best)
+        graph_rate, graph_ms = timed(lambda: g.launch(side), args.ens_timed, 1)
+    S = np.array([api.fte_tally_set(tally, k, 0, A.FTE_TALLY_S).sum() for k in range(len(sets))])
+    S2 = np.array([api.fte_tally_set(tally, k, 0, A.FTE_TALLY_S2).sum() for k in range(len(sets))])
+    rel = [float(math.sqrt(b) / a) for a, b in zip(S, S2) if a > 0]
+    counts = [s.count for s in sets]
+    print(json.dumps({
+        "case": "ensemble", "metric": METRIC, "value": graph_rate, "unit": UNIT, "n_gpus": 1,
+        "steps": args.ens_timed, "warmup": 1, "ms_per_step": graph_ms, "higher_is_better": True,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"cir_ensemble_64: cir_uniform_1e6 background, {len(sets)} parameter sets "
+                               "(lambda_par log-U[0.05,1] au, H U[0.01,0.2], E_inj log-U[20,200] keV), "
+                               f"{n_tot:.0e} protons (counts {min(counts)}-{max(counts)}), dt=10 s x {n_steps}, "
+                               "per-set 1 au box tallies 16x144",
+                   "sort_every": w.params.sort_every,
+                   "tally_rel_err_median": float(np.median(rel)) if rel else None,
+                   "sets_with_hits": len(rel)},
+        "arms": {"single_set_kernel_set_after_set": {"value": plain_rate, "ms_per_step": plain_ms},
+                 "ensemble_kernel_default_config": {"value": eager_rate, "ms_per_step": eager_ms},
+                 "ensemble_kernel_autotuned_graph": {"value": graph_rate, "ms_per_step": graph_ms,
+                                                     "config": best}},
+        "speedup_vs_single_set_kernel": graph_rate / plain_rate,
+        "autotune": [{"config": c, "rate": r} for c, r in tried],
+    }), flush=True)
 
 
 def l2_probe(mib=64, threads=152 * 2048, loads=256, reps=5):
@@ -410,8 +643,13 @@ def l2_probe(mib=64, threads=152 * 2048, loads=256, reps=5):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--case", default="bench", choices=["bench", "profile"])
+    ap.add_argument("--case", default="bench", choices=["bench", "profile", "amr", "ensemble"])
+    ap.add_argument("--ens-steps", type=int, default=2160)
+    ap.add_argument("--ens-timed", type=int, default=2)
+    ap.add_argument("--amr-particles", type=int, default=10_000_000)
+    ap.add_argument("--amr-steps", type=int, default=1800)
     ap.add_argument("--launches", type=int, default=3)
+    ap.add_argument("--grid", default="uniform", choices=["uniform", "amr"], help="grid of --case profile")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
@@ -424,6 +662,10 @@ def main():
     args = ap.parse_args()
     if args.case == "profile":
         run_profile_case(args)
+    elif args.case == "amr":
+        run_amr_case(args)
+    elif args.case == "ensemble":
+        run_ensemble_case(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -113,9 +113,14 @@ def build_leaves(spec, refine):
     from scipy import ndimage
     leaves = [(0, i, j, k) for k in range(spec.nbp) for j in range(spec.nbt) for i in range(spec.nbr)]
     for lv in range(spec.L):
+        if getattr(refine, "batched", False):      # refine(blocks) -> bool per block
+            cand = [leaf for leaf in leaves if leaf[0] == lv]
+            hit = set(map(tuple, np.asarray(cand)[refine(cand)].tolist())) if cand else set()
+        else:
+            hit = {leaf for leaf in leaves if leaf[0] == lv and refine(*leaf)}
         nxt = []
         for leaf in leaves:
-            if leaf[0] == lv and refine(*leaf):
+            if tuple(leaf) in hit:
                 nxt.extend(_split(*leaf))
             else:
                 nxt.append(leaf)
@@ -287,3 +292,93 @@ def affine(spec, leaves, seed=0, phi_ref=math.pi):
                 out[s, n, 1:-1, 1:-1, 1:-1, f] = (c[0] + c[1] * r[None, None, :] + c[2] * th[None, :, None]
                                                    + c[3] * ph[:, None, None] + c[4] * s)
     return out, coef
+
+
+def fields_batched(spec, leaves, model="cir", device="cpu", batch=1024, snaps=None, out=None, t=None, **kw):
+    """Same values as `fields`, evaluated for many leaves at once (torch, on `device`).
+    Returns (or fills `out`) a float32 tensor [n_snap, n_leaf, B+2, B+2, B+2, REC] on
+    `device`; ghost cells are left as they are.  `t` overrides the snapshot times."""
+    B = spec.bsize
+    P = B + 2
+    snaps = range(spec.n_snap) if snaps is None else snaps
+    if out is None:
+        out = torch.zeros((len(snaps), len(leaves), P, P, P, REC), dtype=torch.float32, device=device)
+    lv_all = np.asarray(leaves)
+    idx = np.arange(-1, B + 1)
+    for si, s in enumerate(snaps):
+        ts = spec.t_snap0 + s * spec.dt_snap if t is None else t
+        for a in range(0, len(lv_all), batch):
+            chunk = lv_all[a:a + batch]
+            n = len(chunk)
+            r = np.stack([centres_1d(spec, int(l[0]), 0, int(l[1]) * B + idx) for l in chunk])
+            th = np.stack([centres_1d(spec, int(l[0]), 1, int(l[2]) * B + idx) for l in chunk])
+            ph = np.stack([centres_1d(spec, int(l[0]), 2, int(l[3]) * B + idx) for l in chunk])
+            Rt = torch.as_tensor(r, dtype=_F64, device=device)          # [n, P]
+            Tt = torch.as_tensor(th, dtype=_F64, device=device)
+            Pt = torch.as_tensor(ph, dtype=_F64, device=device)
+            R = Rt[:, None, None, :]
+            TH = Tt[:, None, :, None]
+            PH = Pt[:, :, None, None]
+            if model == "cir":
+                B_, V_ = bgm.cir_fields(R, TH, PH, ts, **kw)
+            else:
+                B_, V_ = bgm.parker_fields(R, TH, PH, **kw)
+            shape = (n, P, P, P)
+            B_ = [torch.broadcast_to(b, shape) for b in B_]
+            V_ = [torch.broadcast_to(v, shape) for v in V_]
+            basis = bgm._basis(TH, PH)
+            rhat, that, phat = [[torch.broadcast_to(c, shape)[:, 1:-1, 1:-1, 1:-1] for c in v] for v in basis]
+            Ri = R[:, :, :, 1:-1]
+            Si = torch.sin(TH)[:, :, 1:-1, :]
+            h1 = (Rt[:, 1:-1] - Rt[:, :-2])[:, None, None, :]
+            h2 = (Rt[:, 2:] - Rt[:, 1:-1])[:, None, None, :]
+            dth = (Tt[:, 1] - Tt[:, 0])[:, None, None, None]
+            dph = (Pt[:, 1] - Pt[:, 0])[:, None, None, None]
+
+            def grad(f):
+                fr = (-h2 / (h1 * (h1 + h2)) * f[:, 1:-1, 1:-1, :-2] + (h2 - h1) / (h1 * h2) * f[:, 1:-1, 1:-1, 1:-1]
+                      + h1 / (h2 * (h1 + h2)) * f[:, 1:-1, 1:-1, 2:])
+                ft = (f[:, 1:-1, 2:, 1:-1] - f[:, 1:-1, :-2, 1:-1]) / (2 * dth)
+                fp = (f[:, 2:, 1:-1, 1:-1] - f[:, :-2, 1:-1, 1:-1]) / (2 * dph)
+                return [fr * rhat[j] + ft * that[j] / Ri + fp * phat[j] / (Ri * Si) for j in range(3)]
+
+            o = out[si, a:a + n]
+            inner = (slice(None),) + (slice(1, -1),) * 3
+            for i in range(3):
+                o[inner + (i,)] = B_[i][inner].float()
+                o[inner + (3 + i,)] = V_[i][inner].float()
+                gi = grad(V_[i])
+                for j in range(3):
+                    o[inner + (6 + 3 * i + j,)] = gi[j].float()
+            Bm = torch.sqrt(B_[0] ** 2 + B_[1] ** 2 + B_[2] ** 2)
+            gB = grad(Bm)
+            for j in range(3):
+                o[inner + (15 + j,)] = gB[j].float()
+    return out
+
+
+def divv_marks(spec, blocks, threshold, model="cir", t=0.0, r_from=0.0, device="cpu", batch=512, **kw):
+    """Batched form of `divv_refiner`: one bool per block (level, bi, bj, bk)."""
+    blocks = np.asarray(blocks, dtype=np.int64).reshape(-1, 4)
+    marks = np.zeros(len(blocks), dtype=bool)
+    one = AmrSpec(**{**spec.__dict__, "n_snap": 1})
+    for a in range(0, len(blocks), batch):
+        chunk = blocks[a:a + batch]
+        f = fields_batched(one, chunk, model=model, device=device, batch=batch, t=t, **kw)[0]
+        inner = f[:, 1:-1, 1:-1, 1:-1]
+        dv = (inner[..., 6] + inner[..., 10]) + inner[..., 14]
+        m = (dv.abs().reshape(len(chunk), -1).amax(dim=1) > threshold).cpu().numpy()
+        for n, (lv, bi, bj, bk) in enumerate(chunk):
+            r_last = centres_1d(spec, int(lv), 0, np.array([(int(bi) + 1) * spec.bsize]))[0]
+            if r_last < r_from:
+                m[n] = False
+        marks[a:a + len(chunk)] = m
+    return marks
+
+
+def divv_refiner_batched(spec, threshold, model="cir", t=0.0, r_from=0.0, device="cpu", **kw):
+    """`divv_refiner` for `build_leaves` that tests many blocks at once."""
+    def refine(blocks):
+        return divv_marks(spec, blocks, threshold, model=model, t=t, r_from=r_from, device=device, **kw)
+    refine.batched = True
+    return refine

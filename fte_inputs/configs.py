@@ -15,10 +15,24 @@ Workloads (the three that run on one spherical grid; names say what they are):
                          the div V < 0 region of one CIR between 1 and 2 au at
                          theta = 90 +- 2 deg with weight 1/r^2 (Eq. 7),
                          lambda_par = 0.1 au, dt = 10 s for four days.
+* ``cir_amr_1e7``     - the same CIR on a log-r block-AMR grid (16^3-cell blocks,
+                         base 32x8x24 blocks, 3 levels, refined where |div V|
+                         exceeds 6e-5 /s: about 40k leaves), two hourly
+                         snapshots, 1e7 protons with an E^-3 spectrum over
+                         50 keV - 5 MeV, dt = 2 s for one simulated hour,
+                         four observer boxes at 0.5, 1, 1.5 and 1.8 au.
+* ``cir_ensemble_64`` - the cir_uniform_1e6 background and transport with 64
+                         parameter sets (lambda_par log-uniform in 0.05-1 au,
+                         H uniform in 0.01-0.2, injection energy log-uniform
+                         in 20-200 keV, particle counts log-uniform in
+                         1e4-1e6 rescaled to 2e7 in total), six simulated
+                         hours, per-set tallies at the 1 au box.
 """
 from dataclasses import dataclass, field, replace
 import math
 from typing import List, Optional
+
+import numpy as np
 
 from .grid import GridSpec
 from .units import OMEGA_SUN, KMS
@@ -101,6 +115,8 @@ class Workload:
     params: Params
     observers: List[Observer] = field(default_factory=list)
     n_steps: int = 0
+    amr_divv: Optional[float] = None   # block-AMR grids: refinement threshold on |div V| (1/s)
+    sets: Optional[list] = None        # ensembles: EnsembleSet per parameter set
 
 
 def cir_observer_phi(r_obs=1.0, psi_c=1.5 * math.pi, u_kms=500.0, r_b=0.1):
@@ -130,6 +146,62 @@ def cir_uniform_1e6():
                     ph=cir_observer_phi(1.0), dph=2 * DEG, e_lo=0.01, e_hi=10.0, ne=16,
                     t_lo=0.0, t_hi=four_days, nt=144)]
     return Workload("cir_uniform_1e6", g, "cir", inj, 1_000_000, prm, obs, n_steps=34_560)
+
+
+def cir_amr_1e7(n_particles=10_000_000, n_steps=1800, spec=None):
+    from .amr import AmrSpec
+    g = spec or AmrSpec(nbr=32, nbt=8, nbp=24, bsize=16, levels=3, radial="log", n_snap=2,
+                        periodic=False, t_snap0=0.0, dt_snap=3600.0)
+    inj = InjectSpec(region="box", r1=1.0, r2=2.0, th1=88 * DEG, th2=92 * DEG,
+                     ph1=math.pi, ph2=2 * math.pi, divv_max=0.0, divv_snap=0,
+                     energy="powerlaw", e1=0.05, e2=5.0, gamma=3.0, weight="r-2", seed=0)
+    prm = Params(dmumu="qlt", lambda_par=0.1, q=5.0 / 3.0, H=0.05, dt=2.0, seed=0, sort_every=64)
+    t_end = n_steps * prm.dt
+    obs = [Observer(kind="box", r=r, dr=0.02, th=90 * DEG, dth=2 * DEG, ph=cir_observer_phi(r),
+                    dph=2 * DEG, e_lo=0.01, e_hi=10.0, ne=16, t_lo=0.0, t_hi=t_end, nt=144)
+           for r in (0.5, 1.0, 1.5, 1.8)]
+    return Workload("cir_amr_1e7", g, "cir", inj, n_particles, prm, obs, n_steps=n_steps, amr_divv=6e-5)
+
+
+@dataclass
+class EnsembleSet:
+    """One parameter set of an ensemble: its transport parameters, Philox key,
+    particle count and injection."""
+    lambda_par: float
+    q: float
+    H: float
+    eps: float
+    seed: int
+    set_id: int
+    count: int
+    inject: InjectSpec
+
+
+def ensemble_sets(n_sets=64, total=20_000_000, lo=10_000, hi=1_000_000, base_inject=None,
+                  q=5.0 / 3.0, eps=0.048, rng_seed=2024):
+    """Seeded parameter sets: lambda_par log-uniform on [0.05, 1] au, H uniform on
+    [0.01, 0.2], mono injection energy log-uniform on [20, 200] keV, counts
+    log-uniform on [lo, hi] rescaled to add up to `total`; set s has Philox key
+    (seed s, set_id s)."""
+    rng = np.random.default_rng(rng_seed)
+    lam = np.exp(rng.uniform(math.log(0.05), math.log(1.0), n_sets))
+    H = rng.uniform(0.01, 0.2, n_sets)
+    e0 = np.exp(rng.uniform(math.log(0.02), math.log(0.2), n_sets))
+    raw = np.exp(rng.uniform(math.log(lo), math.log(hi), n_sets))
+    counts = np.floor(raw * total / raw.sum()).astype(np.int64)
+    counts[np.argmax(counts)] += total - counts.sum()
+    base = base_inject or InjectSpec()
+    return [EnsembleSet(float(lam[s]), q, float(H[s]), eps, s, s, int(counts[s]),
+                        replace(base, energy="mono", e0=float(e0[s]), seed=s, set_id=s))
+            for s in range(n_sets)]
+
+
+def cir_ensemble_64(n_sets=64, total=20_000_000, n_steps=2160):
+    w = cir_uniform_1e6()
+    t_end = n_steps * w.params.dt
+    obs = [replace(w.observers[0], t_hi=t_end)]
+    sets = ensemble_sets(n_sets, total, base_inject=w.inject)
+    return replace(w, name="cir_ensemble_64", n_particles=total, observers=obs, n_steps=n_steps, sets=sets)
 
 
 def scaled(w: Workload, nr=None, nth=None, nph=None, n_particles=None, n_steps=None,

@@ -46,6 +46,7 @@ extern "C" {
 #define FTE_HHDR 32            /* floats of the per-field scale header of a reduced-precision background */
 #define FTE_MAX_OBS 8          /* observers per tally */
 #define FTE_LEDGER 8           /* ledger slots */
+#define FTE_MAX_SETS 64        /* parameter sets per ensemble call */
 
 typedef enum fte_status {
     FTE_OK = 0,
@@ -227,19 +228,21 @@ typedef struct fte_observer {
 } fte_observer;
 
 typedef struct fte_tally_buf {
-    int32_t n_obs, pad;
+    int32_t n_obs;
+    int32_t n_sets;                   /* ensembles: one block of bins per parameter set
+                                         (0 or 1: a single block); at most FTE_MAX_SETS */
     fte_observer obs[FTE_MAX_OBS];
-    double* S;                        /* DEVICE, fte_tally_bins() doubles */
-    double* S2;                       /* DEVICE, fte_tally_bins() doubles */
-    unsigned long long* C;            /* DEVICE, fte_tally_bins() counts */
+    double* S;                        /* DEVICE, max(n_sets, 1) * fte_tally_bins() doubles */
+    double* S2;                       /* DEVICE, max(n_sets, 1) * fte_tally_bins() doubles */
+    unsigned long long* C;            /* DEVICE, max(n_sets, 1) * fte_tally_bins() counts */
     double* ledger_w;                 /* DEVICE, FTE_LEDGER doubles */
     unsigned long long* ledger_n;     /* DEVICE, FTE_LEDGER counts */
 } fte_tally_buf;
 
-/* Total bins over all observers (0 if the tally description is invalid). */
+/* Total bins over all observers of one set (0 if the tally description is invalid). */
 size_t fte_tally_bins(const fte_tally_buf* t);
 
-/* Zero S, S2, C and the ledger (asynchronous). */
+/* Zero S, S2, C of every set and the ledger (asynchronous). */
 fte_status fte_tally_reset(const fte_tally_buf* t, void* stream);
 
 /* Scratch (DEVICE) needed by fte_advance on `device` for grid `g`, tally `t`, a
@@ -285,6 +288,93 @@ fte_status fte_advance(fte_particles* P, const fte_background* bg, const fte_par
 fte_status fte_advance_noalloc(fte_particles* P, const fte_background* bg, const fte_params* prm,
                                const fte_tally_buf* t, int64_t n_start, int64_t n_end, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Ensembles: many parameter sets advanced together (the paper runs one set per
+ * simulation; this is a batching of independent runs, Sec. 2.1 per set).
+ * The pool holds the sets one after another: set s is the counts[s] entries
+ * starting at counts[0] + ... + counts[s-1] (fte_set.count), and the counts
+ * add up to P->count.  Set s replaces lambda_par, q, H, eps, seed and set_id of
+ * the shared fte_params by its own; the D_mumu model, dt, t0, lambda_perp,
+ * p_ref/alpha, toggles and sort_every are shared.  Set s tallies into block s
+ * of the accumulators (bin b of set s at s * fte_tally_bins(t) + b; t->n_sets
+ * >= n_sets).  A particle of set s follows exactly the trajectory fte_advance
+ * gives it with prm carrying set s's values.
+ * ------------------------------------------------------------------------- */
+typedef struct fte_set {
+    double lambda_par, q, H, eps;
+    uint32_t seed, set_id;
+    uint64_t count;            /* particles of this set in the pool */
+} fte_set;
+
+/* Launch configuration of the ensemble step kernel (results do not depend on it). */
+enum { FTE_LAYOUT_SHARED = 1, FTE_LAYOUT_GLOBAL = 2 };
+typedef struct fte_launch_config {
+    int32_t threads;           /* threads per block: 128 or 256 */
+    int32_t steps_per_launch;  /* 1 .. 1024 steps per step-kernel launch; with prm->sort_every > 0
+                                  the alive particles are reordered before every launch */
+    int32_t tally_layout;      /* FTE_LAYOUT_SHARED: every block keeps all sets' bins in shared
+                                  memory (n_sets * bins <= 16384 and the block must fit on an SM),
+                                  reduced into t after each launch; FTE_LAYOUT_GLOBAL: lanes of a
+                                  warp in the same bin are merged and added to t with FP64 atomics */
+    int32_t pad;
+} fte_launch_config;
+
+/* Scratch (DEVICE) for fte_advance_batched / fte_autotune_batched with any
+   launch configuration: grid g, tally t (t->n_sets sets), n_particles pool
+   entries, n_steps steps per call.  0 on error. */
+size_t fte_workspace_bytes_batched(int device, const fte_grid* g, const fte_tally_buf* t,
+                                   uint64_t n_particles, int64_t n_steps);
+
+/* Inject every set of an ensemble: for s = 0 .. n_sets-1, append counts[s]
+   particles drawn per specs[s] (HOST arrays) exactly as fte_inject would, with
+   ids specs[s].id_base + index within the set.  Asynchronous (failed
+   injections are in ledger slot 5).  EINVAL if n_sets is outside
+   1..FTE_MAX_SETS, ENOMEM if the pool cannot hold them all. */
+fte_status fte_inject_batched(fte_particles* P, const fte_background* bg, const fte_inject_spec* specs,
+                              const uint64_t* counts, int n_sets, const fte_tally_buf* t, void* stream);
+
+/* Advance every set of an ensemble from step n_start to n_end in the same
+   launches (sets: HOST array of n_sets entries; cfg: HOST, NULL for 256
+   threads, prm->sort_every (or 1024) steps per launch and the shared layout
+   when it fits, else the global one).  ws (DEVICE, ws_bytes >=
+   fte_workspace_bytes_batched(...)) is scratch.  Asynchronous; makes no
+   synchronising CUDA call, so it can be captured into a graph. */
+fte_status fte_advance_batched(fte_particles* P, const fte_background* bg, const fte_params* prm,
+                               const fte_set* sets, int n_sets, const fte_tally_buf* t, int64_t n_start,
+                               int64_t n_end, const fte_launch_config* cfg, void* ws, size_t ws_bytes,
+                               void* stream);
+
+/* Autotuner of the ensemble launch configuration: advances steps n_start ..
+   n_end exactly as fte_advance_batched would (the trajectories and tallies do
+   not depend on the configuration), trying in turn every configuration of
+   {128, 256 threads} x {32, 64, 128, 256 steps per launch (1024 when
+   prm->sort_every == 0)} x {shared layout where it fits, global layout} on
+   consecutive slices of the steps, twice (forward, then backward order), and
+   stores in *best (HOST) the one with the highest rate of alive particle-steps
+   per second (CUDA events on `stream`, which it synchronises).  tried/rates
+   (HOST, optional, room for 16 entries) receive every configuration and its
+   rate, *n_tried their number.  n_end - n_start must allow at least
+   two launches per trial: ENOTSUP otherwise. */
+fte_status fte_autotune_batched(fte_particles* P, const fte_background* bg, const fte_params* prm,
+                                const fte_set* sets, int n_sets, const fte_tally_buf* t, int64_t n_start,
+                                int64_t n_end, void* ws, size_t ws_bytes, fte_launch_config* best,
+                                fte_launch_config* tried, double* rates, int* n_tried, void* stream);
+
+/* CUDA graphs of library calls (the paper has no counterpart): fte_graph_begin
+   starts capturing `stream` (not the legacy NULL stream; thread-local capture
+   mode), every asynchronous fte_* call enqueued on it until fte_graph_end is
+   recorded instead of run, and fte_graph_end instantiates the graph into *out
+   (a handle the caller owns until fte_graph_destroy).  fte_graph_launch runs
+   it on `stream`; it reuses the pointers and sizes of the capture, so every
+   buffer the captured calls used must stay allocated and unchanged in size.
+   Calls that synchronise (fte_tally with a host buffer, fte_ledger,
+   fte_inject with n_failed, fte_autotune_batched) must not be captured. */
+typedef struct fte_graph fte_graph;
+fte_status fte_graph_begin(void* stream);
+fte_status fte_graph_end(void* stream, fte_graph** out);
+fte_status fte_graph_launch(const fte_graph* g, void* stream);
+fte_status fte_graph_destroy(fte_graph* g);
+
 /* Tally output kinds for fte_tally(). */
 enum { FTE_TALLY_S = 0, FTE_TALLY_S2 = 1, FTE_TALLY_C = 2, FTE_TALLY_INTENSITY = 3 };
 
@@ -296,6 +386,10 @@ enum { FTE_TALLY_S = 0, FTE_TALLY_S2 = 1, FTE_TALLY_C = 2, FTE_TALLY_INTENSITY =
    `stream`. */
 fte_status fte_tally(const fte_tally_buf* t, int obs, int kind, double* dev_out, void* host_out,
                      size_t bytes, void* stream);
+
+/* fte_tally for parameter set `set` of an ensemble tally (0 <= set < max(t->n_sets, 1)). */
+fte_status fte_tally_set(const fte_tally_buf* t, int set, int obs, int kind, double* dev_out, void* host_out,
+                         size_t bytes, void* stream);
 
 /* Copy the ledger to HOST arrays (FTE_LEDGER entries each); synchronises `stream`. */
 fte_status fte_ledger(const fte_tally_buf* t, double* host_w, uint64_t* host_n, void* stream);

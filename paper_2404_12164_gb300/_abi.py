@@ -16,6 +16,8 @@ FTE_HHDR = 32
 FTE_F32, FTE_BF16, FTE_F16 = range(3)
 FTE_MAX_OBS = 8
 FTE_LEDGER = 8
+FTE_MAX_SETS = 64
+FTE_LAYOUT_SHARED, FTE_LAYOUT_GLOBAL = 1, 2
 FTE_OK, FTE_EINVAL, FTE_ENOMEM, FTE_ECUDA, FTE_ERANGE, FTE_ENOTSUP = range(6)
 FTE_ALIVE, FTE_ABS_INNER, FTE_ABS_OUTER, FTE_ABS_THETA, FTE_DEAD_NAN, FTE_INJ_FAIL = range(6)
 FTE_TALLY_S, FTE_TALLY_S2, FTE_TALLY_C, FTE_TALLY_INTENSITY = range(4)
@@ -74,9 +76,19 @@ class fte_observer(C.Structure):
 
 
 class fte_tally_buf(C.Structure):
-    _fields_ = [("n_obs", C.c_int32), ("pad", C.c_int32), ("obs", fte_observer * FTE_MAX_OBS),
+    _fields_ = [("n_obs", C.c_int32), ("n_sets", C.c_int32), ("obs", fte_observer * FTE_MAX_OBS),
                 ("S", C.c_void_p), ("S2", C.c_void_p), ("C", C.c_void_p),
                 ("ledger_w", C.c_void_p), ("ledger_n", C.c_void_p)]
+
+
+class fte_set(C.Structure):
+    _fields_ = [("lambda_par", C.c_double), ("q", C.c_double), ("H", C.c_double), ("eps", C.c_double),
+                ("seed", C.c_uint32), ("set_id", C.c_uint32), ("count", C.c_uint64)]
+
+
+class fte_launch_config(C.Structure):
+    _fields_ = [("threads", C.c_int32), ("steps_per_launch", C.c_int32), ("tally_layout", C.c_int32),
+                ("pad", C.c_int32)]
 
 
 # every symbol include/fte.h declares, with its ctypes signature
@@ -99,6 +111,23 @@ SIGNATURES = {
                                       _P(fte_tally_buf), C.c_int64, C.c_int64, C.c_void_p]),
     "fte_tally": (C.c_int, [_P(fte_tally_buf), C.c_int, C.c_int, C.c_void_p, C.c_void_p,
                             C.c_size_t, C.c_void_p]),
+    "fte_tally_set": (C.c_int, [_P(fte_tally_buf), C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
+                                C.c_size_t, C.c_void_p]),
+    "fte_workspace_bytes_batched": (C.c_size_t, [C.c_int, _P(fte_grid), _P(fte_tally_buf), C.c_uint64,
+                                                 C.c_int64]),
+    "fte_inject_batched": (C.c_int, [_P(fte_particles), _P(fte_background), _P(fte_inject_spec),
+                                     _P(C.c_uint64), C.c_int, _P(fte_tally_buf), C.c_void_p]),
+    "fte_advance_batched": (C.c_int, [_P(fte_particles), _P(fte_background), _P(fte_params), _P(fte_set),
+                                      C.c_int, _P(fte_tally_buf), C.c_int64, C.c_int64,
+                                      _P(fte_launch_config), C.c_void_p, C.c_size_t, C.c_void_p]),
+    "fte_autotune_batched": (C.c_int, [_P(fte_particles), _P(fte_background), _P(fte_params), _P(fte_set),
+                                       C.c_int, _P(fte_tally_buf), C.c_int64, C.c_int64, C.c_void_p,
+                                       C.c_size_t, _P(fte_launch_config), _P(fte_launch_config),
+                                       _P(C.c_double), _P(C.c_int), C.c_void_p]),
+    "fte_graph_begin": (C.c_int, [C.c_void_p]),
+    "fte_graph_end": (C.c_int, [C.c_void_p, _P(C.c_void_p)]),
+    "fte_graph_launch": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "fte_graph_destroy": (C.c_int, [C.c_void_p]),
     "fte_ledger": (C.c_int, [_P(fte_tally_buf), _P(C.c_double), _P(C.c_uint64), C.c_void_p]),
     "fte_probe_sectors": (C.c_int, [C.c_void_p, C.c_size_t, C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
     "fte_last_error": (C.c_char_p, []),

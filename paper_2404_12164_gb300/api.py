@@ -195,14 +195,16 @@ class Particles:
 
 
 class Tally:
-    """Device tally accumulators and ledger (fte_tally_buf)."""
+    """Device tally accumulators and ledger (fte_tally_buf); n_sets blocks of bins
+    for an ensemble."""
 
-    def __init__(self, observers, device="cuda"):
+    def __init__(self, observers, device="cuda", n_sets=1):
         self.observers = list(observers)
         if len(self.observers) > A.FTE_MAX_OBS:
             raise ValueError("too many observers")
         self.nb = [o.ne * o.nt for o in self.observers]
-        n = max(sum(self.nb), 1)
+        self.n_sets = int(n_sets)
+        n = max(sum(self.nb), 1) * max(self.n_sets, 1)
         self.S = torch.zeros(n, dtype=torch.float64, device=device)
         self.S2 = torch.zeros(n, dtype=torch.float64, device=device)
         self.C = torch.zeros(n, dtype=torch.int64, device=device)
@@ -211,6 +213,7 @@ class Tally:
         self.out = torch.zeros(max(self.nb + [1]), dtype=torch.float64, device=device)
         c = A.fte_tally_buf()
         c.n_obs = len(self.observers)
+        c.n_sets = self.n_sets
         for i, o in enumerate(self.observers):
             c.obs[i] = observer_c(o)
         c.S, c.S2, c.C = self.S.data_ptr(), self.S2.data_ptr(), self.C.data_ptr()
@@ -299,3 +302,127 @@ def fte_ledger(tally, stream=None):
     n = (C.c_uint64 * A.FTE_LEDGER)()
     check(A.lib().fte_ledger(C.byref(tally.c), w, n, _stream(stream)), "fte_ledger")
     return np.array(w), np.array(n, dtype=np.uint64)
+
+
+# ---------------------------------------------------------------------------
+# ensembles, the launch-configuration autotuner and CUDA graphs
+# ---------------------------------------------------------------------------
+LAYOUTS = {"shared": A.FTE_LAYOUT_SHARED, "global": A.FTE_LAYOUT_GLOBAL}
+LAYOUT_NAMES = {v: k for k, v in LAYOUTS.items()}
+
+
+def sets_c(sets):
+    """fte_set array of fte_inputs.configs.EnsembleSet entries."""
+    arr = (A.fte_set * len(sets))()
+    for i, e in enumerate(sets):
+        arr[i] = A.fte_set(e.lambda_par, e.q, e.H, e.eps, e.seed & 0xFFFFFFFF, e.set_id & 0xFFFFFFFF, int(e.count))
+    return arr
+
+
+def config_c(cfg):
+    """fte_launch_config of a dict {threads, steps_per_launch, tally_layout} (None: library default)."""
+    if cfg is None:
+        return None
+    return A.fte_launch_config(int(cfg["threads"]), int(cfg["steps_per_launch"]),
+                               LAYOUTS[cfg["tally_layout"]], 0)
+
+
+def _config_dict(c):
+    return {"threads": c.threads, "steps_per_launch": c.steps_per_launch,
+            "tally_layout": LAYOUT_NAMES.get(c.tally_layout, str(c.tally_layout))}
+
+
+def fte_workspace_bytes_batched(bg, tally, n_particles, n_steps, device=None):
+    dev = torch.cuda.current_device() if device is None else device
+    n = A.lib().fte_workspace_bytes_batched(dev, C.byref(bg.gc), C.byref(tally.c), int(n_particles), int(n_steps))
+    if n == 0:
+        raise RuntimeError("fte_workspace_bytes_batched: " + A.lib().fte_last_error().decode())
+    return n
+
+
+def fte_inject_batched(pool, bg, sets, tally, stream=None):
+    """Inject every set (EnsembleSet.inject, EnsembleSet.count) one after another; ids restart
+    at 0 in every set.  Asynchronous."""
+    specs = (A.fte_inject_spec * len(sets))()
+    for i, e in enumerate(sets):
+        specs[i] = inject_c(e.inject, 0)
+    counts = (C.c_uint64 * len(sets))(*[int(e.count) for e in sets])
+    check(A.lib().fte_inject_batched(C.byref(pool.c), C.byref(bg.c), specs, counts, len(sets),
+                                     C.byref(tally.c), _stream(stream)), "fte_inject_batched")
+
+
+def fte_advance_batched(pool, bg, params, sets, tally, n_start, n_end, ws=None, config=None, stream=None):
+    ws = ws if ws is not None else Workspace(bg.dev.device)
+    buf = ws.ensure(fte_workspace_bytes_batched(bg, tally, pool.count, n_end - n_start, bg.dev.device.index))
+    pc = params_c(params)
+    sc = sets_c(sets)
+    cc = config_c(config)
+    check(A.lib().fte_advance_batched(C.byref(pool.c), C.byref(bg.c), C.byref(pc), sc, len(sets),
+                                      C.byref(tally.c), int(n_start), int(n_end),
+                                      C.byref(cc) if cc is not None else None,
+                                      C.c_void_p(buf.data_ptr()), buf.numel(), _stream(stream)),
+          "fte_advance_batched")
+    return ws
+
+
+def fte_autotune_batched(pool, bg, params, sets, tally, n_start, n_end, ws=None, stream=None):
+    """Advance steps n_start..n_end while timing every launch configuration on a slice of them;
+    returns (best configuration, [(configuration, alive particle-steps per second), ...])."""
+    ws = ws if ws is not None else Workspace(bg.dev.device)
+    buf = ws.ensure(fte_workspace_bytes_batched(bg, tally, pool.count, n_end - n_start, bg.dev.device.index))
+    pc = params_c(params)
+    sc = sets_c(sets)
+    best = A.fte_launch_config()
+    tried = (A.fte_launch_config * 16)()
+    rates = (C.c_double * 16)()
+    n_tried = C.c_int(0)
+    check(A.lib().fte_autotune_batched(C.byref(pool.c), C.byref(bg.c), C.byref(pc), sc, len(sets),
+                                       C.byref(tally.c), int(n_start), int(n_end),
+                                       C.c_void_p(buf.data_ptr()), buf.numel(), C.byref(best), tried, rates,
+                                       C.byref(n_tried), _stream(stream)), "fte_autotune_batched")
+    return _config_dict(best), [(_config_dict(tried[k]), rates[k]) for k in range(n_tried.value)]
+
+
+def fte_tally_set(tally, set_index, obs, kind=A.FTE_TALLY_S, stream=None):
+    """fte_tally for parameter set `set_index` of an ensemble tally."""
+    ob = tally.observers[obs]
+    host = np.zeros((ob.ne, ob.nt), dtype=np.float64)
+    check(A.lib().fte_tally_set(C.byref(tally.c), int(set_index), int(obs), int(kind),
+                                C.c_void_p(tally.out.data_ptr()), C.c_void_p(host.ctypes.data), host.nbytes,
+                                _stream(stream)), "fte_tally_set")
+    return host
+
+
+class Graph:
+    """A CUDA graph of library calls: `with g.capture(stream): ...` records the asynchronous
+    fte_* calls made on `stream` (not torch's default stream); g.launch(stream) replays them."""
+
+    def __init__(self):
+        self.h = C.c_void_p(0)
+
+    def capture(self, stream):
+        graph = self
+
+        class _Cap:
+            def __enter__(self):
+                check(A.lib().fte_graph_begin(_stream(stream)), "fte_graph_begin")
+                return graph
+
+            def __exit__(self, *exc):
+                h = C.c_void_p(0)
+                st = A.lib().fte_graph_end(_stream(stream), C.byref(h))
+                if exc[0] is None:
+                    check(st, "fte_graph_end")
+                graph.h = h
+                return False
+        return _Cap()
+
+    def launch(self, stream=None):
+        check(A.lib().fte_graph_launch(self.h, _stream(stream)), "fte_graph_launch")
+
+    def __del__(self):
+        try:
+            if self.h and self.h.value:
+                A.lib().fte_graph_destroy(self.h)
+        except Exception:
+            pass

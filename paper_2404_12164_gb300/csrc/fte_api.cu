@@ -6,6 +6,8 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <new>
+
 #include "fte_kernels.cuh"
 
 using namespace fte;
@@ -146,6 +148,7 @@ fte_status check_tally(const fte_tally_buf* t, size_t* nbins)
 {
     if (!t) return fail(FTE_EINVAL, "tally is NULL");
     if (t->n_obs < 0 || t->n_obs > FTE_MAX_OBS) return fail(FTE_EINVAL, "n_obs must be in [0, %d]", FTE_MAX_OBS);
+    if (t->n_sets < 0 || t->n_sets > FTE_MAX_SETS) return fail(FTE_EINVAL, "n_sets must be in [0, %d]", FTE_MAX_SETS);
     size_t nb = 0;
     for (int o = 0; o < t->n_obs; ++o) {
         const fte_observer& ob = t->obs[o];
@@ -161,6 +164,8 @@ fte_status check_tally(const fte_tally_buf* t, size_t* nbins)
     *nbins = nb;
     return FTE_OK;
 }
+
+const BatchArgs g_no_batch = {};    // the single-set kernels ignore their ensemble argument
 
 // Layout of the fte_advance workspace.
 struct WsLayout {
@@ -193,7 +198,7 @@ fte_status layout(int device, int kperp, int dtype, size_t nbins, long long n_st
     int cur = 0;
     FTE_CUDA(cudaGetDevice(&cur), "cudaGetDevice");
     if (cur != device) FTE_CUDA(cudaSetDevice(device), "cudaSetDevice");
-    cudaError_t e = advance_occupancy(kperp, dtype, smem, &per_sm);
+    cudaError_t e = advance_occupancy(kperp, dtype, kModeSingle, kThreads, smem, &per_sm);
     if (cur != device) cudaSetDevice(cur);
     if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
     if (per_sm < 1) return fail(FTE_ENOTSUP, "step kernel does not fit on an SM with %zu bytes of tally", smem);
@@ -302,7 +307,7 @@ fte_status fte_quantize_background(const fte_grid* g_half, const float* dev_f32,
 size_t fte_tally_bins(const fte_tally_buf* t)
 {
     size_t nb = 0;
-    if (!t || t->n_obs < 0 || t->n_obs > FTE_MAX_OBS) return 0;
+    if (!t || t->n_obs < 0 || t->n_obs > FTE_MAX_OBS || t->n_sets < 0 || t->n_sets > FTE_MAX_SETS) return 0;
     for (int o = 0; o < t->n_obs; ++o) {
         if (t->obs[o].ne < 1 || t->obs[o].nt < 1) return 0;
         nb += (size_t)t->obs[o].ne * t->obs[o].nt;
@@ -316,6 +321,7 @@ fte_status fte_tally_reset(const fte_tally_buf* t, void* stream)
     fte_status s = check_tally(t, &nb);
     if (s != FTE_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
+    nb *= (size_t)(t->n_sets > 1 ? t->n_sets : 1);
     if (nb) {
         FTE_CUDA(cudaMemsetAsync(t->S, 0, nb * sizeof(double), st), "memset S");
         FTE_CUDA(cudaMemsetAsync(t->S2, 0, nb * sizeof(double), st), "memset S2");
@@ -511,14 +517,14 @@ fte_status fte_advance(fte_particles* P, const fte_background* bg, const fte_par
     const long long chunk = sorting ? (prm->sort_every < kChunkSteps ? prm->sort_every : kChunkSteps) : kChunkSteps;
     const size_t smem = 3 * sizeof(float) * (size_t)a.nbins;
     int per_sm = 0;
-    FTE_CUDA(advance_occupancy(kperp, bg->grid.dtype, smem, &per_sm), "occupancy");
+    FTE_CUDA(advance_occupancy(kperp, bg->grid.dtype, kModeSingle, kThreads, smem, &per_sm), "occupancy");
 
     for (long long c0 = n_start; c0 < n_end; c0 += chunk) {
         a.n_start = c0;
         a.n_end = (c0 + chunk < n_end) ? c0 + chunk : n_end;
         if (sorting) FTE_CUDA(launch_sort(sa, st), "sort launch");
         FTE_CUDA(cudaMemsetAsync(a.fetch, 0, sizeof(unsigned long long), st), "fetch reset");
-        FTE_CUDA(launch_advance(a, kperp, blocks, smem, st), "step kernel launch");
+        FTE_CUDA(launch_advance(a, g_no_batch, kperp, kModeSingle, kThreads, blocks, smem, st), "step kernel launch");
         if (nb) FTE_CUDA(launch_reduce(a.part, blocks, (int)nb, t->S, t->S2, t->C, st), "reduce launch");
     }
     return FTE_OK;
@@ -527,9 +533,16 @@ fte_status fte_advance(fte_particles* P, const fte_background* bg, const fte_par
 fte_status fte_tally(const fte_tally_buf* t, int obs, int kind, double* dev_out, void* host_out,
                      size_t bytes, void* stream)
 {
+    return fte_tally_set(t, 0, obs, kind, dev_out, host_out, bytes, stream);
+}
+
+fte_status fte_tally_set(const fte_tally_buf* t, int set, int obs, int kind, double* dev_out, void* host_out,
+                         size_t bytes, void* stream)
+{
     size_t nb = 0;
     fte_status s = check_tally(t, &nb);
     if (s != FTE_OK) return s;
+    if (set < 0 || set >= (t->n_sets > 1 ? t->n_sets : 1)) return fail(FTE_EINVAL, "set %d out of range", set);
     if (obs < 0 || obs >= t->n_obs) return fail(FTE_EINVAL, "observer %d out of range", obs);
     if (kind < FTE_TALLY_S || kind > FTE_TALLY_INTENSITY) return fail(FTE_EINVAL, "bad tally kind");
     if (!dev_out) return fail(FTE_EINVAL, "NULL device output");
@@ -538,7 +551,7 @@ fte_status fte_tally(const fte_tally_buf* t, int obs, int kind, double* dev_out,
     if (host_out && bytes < n * sizeof(double)) return fail(FTE_ENOMEM, "host buffer too small");
     ObsOut o;
     o.kind = ob.kind; o.ne = ob.ne; o.nt = ob.nt;
-    size_t off = 0;
+    size_t off = (size_t)set * nb;
     for (int k = 0; k < obs; ++k) off += (size_t)t->obs[k].ne * t->obs[k].nt;
     o.off = (int)off;
     o.r = ob.r; o.dr = ob.dr; o.th = ob.th; o.dth = ob.dth; o.dph = ob.dph;
@@ -661,7 +674,7 @@ extern "C" fte_status fte_advance_noalloc(fte_particles* P, const fte_background
                     nb, part_block, kNoAllocBytes, sms);
     const size_t smem = part_block;
     int per_sm = 0;
-    FTE_CUDA(advance_occupancy(kperp, bg->grid.dtype, smem, &per_sm), "occupancy");
+    FTE_CUDA(advance_occupancy(kperp, bg->grid.dtype, kModeSingle, kThreads, smem, &per_sm), "occupancy");
     if (per_sm < 1) return fail(FTE_ENOTSUP, "step kernel does not fit on an SM with %zu bytes of tally", smem);
     long long max_blocks = (long long)sms * per_sm;
     if ((size_t)max_blocks > fit) max_blocks = (long long)fit;
@@ -727,8 +740,435 @@ extern "C" fte_status fte_advance_noalloc(fte_particles* P, const fte_background
         a.n_end = c1;
         a.n_table0 = c0;
         FTE_CUDA(cudaMemsetAsync(a.fetch, 0, sizeof(unsigned long long), st), "fetch reset");
-        FTE_CUDA(launch_advance(a, kperp, (int)blocks, smem, st), "step kernel launch");
+        FTE_CUDA(launch_advance(a, g_no_batch, kperp, kModeSingle, kThreads, (int)blocks, smem, st), "step kernel launch");
         if (nb) FTE_CUDA(launch_reduce(a.part, (int)blocks, (int)nb, t->S, t->S2, t->C, st), "reduce launch");
     }
     return FTE_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Ensembles: many parameter sets per launch, the launch-configuration
+// autotuner and CUDA graphs of library calls.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct EnsLayout {
+    size_t off_fetch, off_norm, off_npart, off_table, off_part, off_sort, total;
+    int blocks;     // resident blocks (SMs x blocks per SM)
+};
+
+size_t shared_bins(int n_sets, size_t nb) { return (size_t)n_sets * nb; }
+
+bool shared_fits(int n_sets, size_t nb) { return nb > 0 && shared_bins(n_sets, nb) <= (size_t)kMaxSmemBins; }
+
+size_t ens_smem(int mode, int n_sets, size_t nb)
+{
+    return mode == kModeShared ? 3 * sizeof(float) * shared_bins(n_sets, nb) : 0;
+}
+
+fte_status ens_layout(int device, int kperp, int dtype, int mode, int nt, int n_sets, size_t nb,
+                      long long n_steps, size_t sort_bytes, EnsLayout* L)
+{
+    const int sms = device_sms(device);
+    if (sms <= 0) return fail(FTE_ECUDA, "cannot query device %d", device);
+    const size_t smem = ens_smem(mode, n_sets, nb);
+    int per_sm = 0, cur = 0;
+    FTE_CUDA(cudaGetDevice(&cur), "cudaGetDevice");
+    if (cur != device) FTE_CUDA(cudaSetDevice(device), "cudaSetDevice");
+    cudaError_t e = advance_occupancy(kperp, dtype, mode, nt, smem, &per_sm);
+    if (cur != device) cudaSetDevice(cur);
+    if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
+    if (per_sm < 1) return fail(FTE_ENOTSUP, "ensemble step kernel does not fit on an SM with %zu bytes of tally", smem);
+    L->blocks = sms * per_sm;
+    size_t off = 0;
+    L->off_fetch = off; off += 64;
+    L->off_norm = off; off += FTE_MAX_SETS * sizeof(double);
+    L->off_npart = off; off += (size_t)FTE_MAX_SETS * kNormPartials * sizeof(double);
+    L->off_table = off; off += (size_t)(n_steps > 0 ? n_steps : 1) * sizeof(StepEntry);
+    off = (off + 255) & ~(size_t)255;
+    L->off_part = off;
+    if (mode == kModeShared) off += (size_t)L->blocks * 3 * shared_bins(n_sets, nb) * sizeof(float);
+    off = (off + 255) & ~(size_t)255;
+    L->off_sort = off; off += sort_bytes;
+    L->total = off;
+    return FTE_OK;
+}
+
+fte_status check_params(const fte_params* prm)
+{
+    if (!(prm->dt > 0.0)) return fail(FTE_EINVAL, "dt must be > 0");
+    if (prm->dmumu < 0 || prm->dmumu > 2) return fail(FTE_EINVAL, "bad dmumu model");
+    if (prm->lambda_perp < 0.0) return fail(FTE_EINVAL, "lambda_perp must be >= 0");
+    return FTE_OK;
+}
+
+fte_status check_sets(const fte_params* prm, const fte_set* sets, int n_sets, const fte_particles* P,
+                      const fte_tally_buf* t)
+{
+    if (!sets) return fail(FTE_EINVAL, "NULL sets");
+    if (n_sets < 1 || n_sets > FTE_MAX_SETS) return fail(FTE_EINVAL, "n_sets must be in [1, %d]", FTE_MAX_SETS);
+    if ((t->n_sets > 1 ? t->n_sets : 1) < n_sets) return fail(FTE_EINVAL, "tally holds fewer than %d sets", n_sets);
+    unsigned long long total = 0;
+    for (int s = 0; s < n_sets; ++s) {
+        const fte_set& k = sets[s];
+        if (!(k.lambda_par > 0.0)) return fail(FTE_EINVAL, "set %d: lambda_par must be > 0", s);
+        if (prm->dmumu == 0 && !(k.q > 1.0 && k.q <= 2.0 && k.H >= 0.0))
+            return fail(FTE_EINVAL, "set %d: need 1 < q <= 2, H >= 0", s);
+        if (prm->dmumu == 1 && !(k.eps > 0.0)) return fail(FTE_EINVAL, "set %d: eps must be > 0", s);
+        total += k.count;
+    }
+    if (total != P->count) return fail(FTE_EINVAL, "set counts add up to %llu, the pool holds %llu", total,
+                                       (unsigned long long)P->count);
+    return FTE_OK;
+}
+
+struct EnsConfig {
+    int nt, steps, mode;
+};
+
+// The ensemble advance of steps [n_start, n_end) with one launch configuration.
+// Validation is done by the callers.
+fte_status ens_run(fte_particles* P, const fte_background* bg, const fte_params* prm, const fte_set* sets,
+                   int n_sets, const fte_tally_buf* t, size_t nb, int64_t n_start, int64_t n_end,
+                   const EnsConfig& cfg, void* ws, size_t ws_bytes, cudaStream_t st)
+{
+    int device = 0;
+    FTE_CUDA(cudaGetDevice(&device), "cudaGetDevice");
+    const int kperp = prm->lambda_perp > 0.0 ? 1 : 0;
+    const long long nsteps = n_end - n_start;
+    const GridK gk = make_gridk(bg);
+    const int sorting = prm->sort_every > 0;
+    EnsLayout L;
+    fte_status s = ens_layout(device, kperp, bg->grid.dtype, cfg.mode, cfg.nt, n_sets, nb, nsteps,
+                              sorting ? sort_scratch_bytes(gk, P->count) : 0, &L);
+    if (s != FTE_OK) return s;
+    if (ws_bytes < L.total) return fail(FTE_ENOMEM, "workspace has %zu bytes, needs %zu", ws_bytes, L.total);
+    char* w = (char*)ws;
+
+    NormSets ns;
+    memset(&ns, 0, sizeof(ns));
+    for (int k = 0; k < n_sets; ++k) { ns.q[k] = sets[k].q; ns.H[k] = sets[k].H; ns.eps[k] = sets[k].eps; }
+    double* norm = (double*)(w + L.off_norm);
+    FTE_CUDA(launch_norm_sets(prm->dmumu, ns, n_sets, norm, (double*)(w + L.off_npart), st), "norm launch");
+
+    StepTableArgs ta;
+    memset(&ta, 0, sizeof(ta));
+    ta.tab = (StepEntry*)(w + L.off_table);
+    ta.n0 = n_start; ta.count = nsteps; ta.t0 = prm->t0; ta.dt = prm->dt;
+    ta.n_snap = bg->grid.n_snap; ta.periodic = bg->grid.periodic;
+    ta.t_snap0 = bg->grid.t_snap0; ta.dt_snap = bg->grid.dt_snap;
+    ta.n_obs = t->n_obs;
+    for (int o = 0; o < t->n_obs; ++o) {
+        ta.ot[o].t_lo = t->obs[o].t_lo; ta.ot[o].t_hi = t->obs[o].t_hi; ta.ot[o].nt = t->obs[o].nt;
+    }
+    FTE_CUDA(launch_step_table(ta, st), "step table launch");
+
+    AdvanceArgs a;
+    memset(&a, 0, sizeof(a));
+    a.g = gk;
+    a.prm.dmumu = prm->dmumu; a.prm.p_update = prm->p_update; a.prm.kappa_drift = prm->kappa_drift;
+    a.prm.dvdt_term = prm->dvdt_term;
+    a.prm.use_rig = (prm->p_ref > 0.0 && prm->alpha != 0.0) ? 1 : 0;
+    a.prm.p_ref = (float)prm->p_ref; a.prm.alpha = (float)prm->alpha;
+    a.prm.mu_floor = (float)prm->mu_floor; a.prm.lambda_perp = (float)prm->lambda_perp;
+    a.prm.dt = (float)prm->dt;
+    BatchArgs b;
+    memset(&b, 0, sizeof(b));
+    b.n_sets = n_sets;
+    unsigned long long end = 0;
+    for (int k = 0; k < n_sets; ++k) {
+        end += sets[k].count;
+        b.end[k] = end;
+        b.set[k].lambda_par = (float)sets[k].lambda_par; b.set[k].q = (float)sets[k].q;
+        b.set[k].H = (float)sets[k].H; b.set[k].eps = (float)sets[k].eps;
+        b.set[k].seed = sets[k].seed; b.set[k].set_id = sets[k].set_id;
+    }
+    SortArgs sa;
+    memset(&sa, 0, sizeof(sa));
+    if (sorting) {
+        sort_carve(gk, P->count, w + L.off_sort, &sa);
+        sa.g = gk;
+        sa.x = P->x; sa.y = P->y; sa.z = P->z; sa.status = P->status; sa.n = P->count;
+        a.order = sa.order;
+        a.n_order = sa.hist + sa.nb;
+    }
+    size_t off = 0;
+    for (int o = 0; o < t->n_obs; ++o) {
+        const fte_observer& ob = t->obs[o];
+        ObsK& k = a.obs[o];
+        k.kind = ob.kind; k.ne = ob.ne; k.nt = ob.nt; k.off = (int)off;
+        k.r = (float)ob.r; k.dr = (float)ob.dr; k.th = (float)ob.th; k.dth = (float)ob.dth;
+        k.ph = (float)ob.ph; k.dph = (float)ob.dph;
+        k.e_lo = (float)ob.e_lo; k.ne_over_lnratio = (float)(ob.ne / log(ob.e_hi / ob.e_lo));
+        off += (size_t)ob.ne * ob.nt;
+    }
+    a.n_obs = t->n_obs;
+    a.nbins = (int)(nb ? nb : 1);
+    a.x = P->x; a.y = P->y; a.z = P->z; a.mu = P->mu; a.p = P->p; a.w = P->w; a.id = P->id; a.status = P->status;
+    a.n_particles = P->count;
+    a.n_table0 = n_start;
+    a.table = ta.tab;
+    a.norm = norm;
+    a.gS = t->S; a.gS2 = t->S2; a.gC = t->C;
+    a.part = (float*)(w + L.off_part);
+    a.fetch = (unsigned long long*)(w + L.off_fetch);
+    a.ledger_w = t->ledger_w; a.ledger_n = t->ledger_n;
+
+    const unsigned long long lanes = (unsigned long long)L.blocks * cfg.nt;
+    const unsigned long long per = (P->count + lanes - 1) / lanes;
+    const unsigned long long threads = (P->count + per - 1) / per;
+    int blocks = (int)((threads + cfg.nt - 1) / cfg.nt);
+    if (blocks > L.blocks || sorting) blocks = L.blocks;
+    if (blocks < 1) blocks = 1;
+    const size_t smem = ens_smem(cfg.mode, n_sets, nb);
+    const int reduce_bins = (int)shared_bins(n_sets, nb);
+    for (long long c0 = n_start; c0 < n_end; c0 += cfg.steps) {
+        a.n_start = c0;
+        a.n_end = (c0 + cfg.steps < n_end) ? c0 + cfg.steps : n_end;
+        if (sorting) FTE_CUDA(launch_sort(sa, st), "sort launch");
+        FTE_CUDA(cudaMemsetAsync(a.fetch, 0, sizeof(unsigned long long), st), "fetch reset");
+        FTE_CUDA(launch_advance(a, b, kperp, cfg.mode, cfg.nt, blocks, smem, st), "step kernel launch");
+        if (cfg.mode == kModeShared && nb)
+            FTE_CUDA(launch_reduce(a.part, blocks, reduce_bins, t->S, t->S2, t->C, st), "reduce launch");
+    }
+    return FTE_OK;
+}
+
+fte_status ens_check(fte_particles* P, const fte_background* bg, const fte_params* prm, const fte_set* sets,
+                     int n_sets, const fte_tally_buf* t, int64_t n_start, int64_t n_end, void* ws, size_t* nb)
+{
+    if (!P || !prm) return fail(FTE_EINVAL, "NULL particles or params");
+    fte_status s = check_background(bg);
+    if (s != FTE_OK) return s;
+    s = check_tally(t, nb);
+    if (s != FTE_OK) return s;
+    s = check_params(prm);
+    if (s != FTE_OK) return s;
+    s = check_sets(prm, sets, n_sets, P, t);
+    if (s != FTE_OK) return s;
+    if (n_end < n_start || n_start < 0) return fail(FTE_EINVAL, "need 0 <= n_start <= n_end");
+    if (n_end > 0xFFFFFFFFll) return fail(FTE_EINVAL, "step index exceeds 32 bits");
+    if (!ws) return fail(FTE_EINVAL, "NULL workspace");
+    if (!P->x || !P->y || !P->z || !P->mu || !P->p || !P->w || !P->id || !P->status)
+        return fail(FTE_EINVAL, "NULL particle array");
+    return FTE_OK;
+}
+
+fte_status to_config(const fte_launch_config* c, const fte_params* prm, int n_sets, size_t nb, EnsConfig* out)
+{
+    const long long def_steps = prm->sort_every > 0 ? (prm->sort_every < kChunkSteps ? prm->sort_every : kChunkSteps)
+                                                    : kChunkSteps;
+    out->nt = c && c->threads ? c->threads : 256;
+    out->steps = (int)(c && c->steps_per_launch ? c->steps_per_launch : def_steps);
+    const int layout = c && c->tally_layout ? c->tally_layout
+                                            : (shared_fits(n_sets, nb) ? FTE_LAYOUT_SHARED : FTE_LAYOUT_GLOBAL);
+    if (out->nt != 128 && out->nt != 256) return fail(FTE_EINVAL, "threads must be 128 or 256");
+    if (out->steps < 1 || out->steps > kChunkSteps) return fail(FTE_EINVAL, "steps_per_launch must be in [1, %lld]", kChunkSteps);
+    if (layout == FTE_LAYOUT_SHARED) {
+        if (!shared_fits(n_sets, nb)) return fail(FTE_ENOTSUP, "%d sets x %zu bins do not fit the shared layout", n_sets, nb);
+        out->mode = kModeShared;
+    } else if (layout == FTE_LAYOUT_GLOBAL) {
+        out->mode = kModeGlobal;
+    } else {
+        return fail(FTE_EINVAL, "bad tally layout");
+    }
+    return FTE_OK;
+}
+
+}  // namespace
+
+struct fte_graph {
+    cudaGraphExec_t exec;
+};
+
+extern "C" {
+
+size_t fte_workspace_bytes_batched(int device, const fte_grid* g, const fte_tally_buf* t,
+                                   uint64_t n_particles, int64_t n_steps)
+{
+    size_t nb = 0;
+    if (check_grid(g) != FTE_OK) return 0;
+    if (check_tally(t, &nb) != FTE_OK || n_steps < 0) return 0;
+    const int n_sets = t->n_sets > 1 ? t->n_sets : 1;
+    fte_background tmp;
+    memset(&tmp, 0, sizeof(tmp));
+    tmp.grid = *g;
+    const size_t sort_bytes = sort_scratch_bytes(make_gridk(&tmp), n_particles);
+    size_t best = 0;
+    for (int dtype = FTE_F32; dtype <= FTE_F16; ++dtype)
+        for (int kperp = 0; kperp < 2; ++kperp)
+            for (int mode = kModeShared; mode <= kModeGlobal; ++mode)
+                for (int nt = 128; nt <= 256; nt *= 2) {
+                    if (mode == kModeShared && !shared_fits(n_sets, nb)) continue;
+                    EnsLayout L;
+                    const fte_status s = ens_layout(device, kperp, dtype, mode, nt, n_sets, nb, n_steps, sort_bytes, &L);
+                    if (s == FTE_ENOTSUP) continue;
+                    if (s != FTE_OK) return 0;
+                    if (L.total > best) best = L.total;
+                }
+    return best;
+}
+
+fte_status fte_inject_batched(fte_particles* P, const fte_background* bg, const fte_inject_spec* specs,
+                              const uint64_t* counts, int n_sets, const fte_tally_buf* t, void* stream)
+{
+    if (!P || !specs || !counts) return fail(FTE_EINVAL, "NULL particles, specs or counts");
+    if (n_sets < 1 || n_sets > FTE_MAX_SETS) return fail(FTE_EINVAL, "n_sets must be in [1, %d]", FTE_MAX_SETS);
+    unsigned long long total = 0;
+    for (int s = 0; s < n_sets; ++s) total += counts[s];
+    if (P->count + total > P->capacity) return fail(FTE_ENOMEM, "pool capacity %llu < %llu",
+                                                    (unsigned long long)P->capacity,
+                                                    (unsigned long long)(P->count + total));
+    for (int s = 0; s < n_sets; ++s) {
+        const fte_status st = fte_inject(P, bg, specs + s, counts[s], t, nullptr, stream);
+        if (st != FTE_OK) return st;
+    }
+    return FTE_OK;
+}
+
+fte_status fte_advance_batched(fte_particles* P, const fte_background* bg, const fte_params* prm,
+                               const fte_set* sets, int n_sets, const fte_tally_buf* t, int64_t n_start,
+                               int64_t n_end, const fte_launch_config* cfg, void* ws, size_t ws_bytes,
+                               void* stream)
+{
+    size_t nb = 0;
+    fte_status s = ens_check(P, bg, prm, sets, n_sets, t, n_start, n_end, ws, &nb);
+    if (s != FTE_OK) return s;
+    EnsConfig c;
+    s = to_config(cfg, prm, n_sets, nb, &c);
+    if (s != FTE_OK) return s;
+    if (n_end == n_start || P->count == 0) return FTE_OK;
+    return ens_run(P, bg, prm, sets, n_sets, t, nb, n_start, n_end, c, ws, ws_bytes, (cudaStream_t)stream);
+}
+
+fte_status fte_autotune_batched(fte_particles* P, const fte_background* bg, const fte_params* prm,
+                                const fte_set* sets, int n_sets, const fte_tally_buf* t, int64_t n_start,
+                                int64_t n_end, void* ws, size_t ws_bytes, fte_launch_config* best,
+                                fte_launch_config* tried, double* rates, int* n_tried, void* stream)
+{
+    size_t nb = 0;
+    fte_status s = ens_check(P, bg, prm, sets, n_sets, t, n_start, n_end, ws, &nb);
+    if (s != FTE_OK) return s;
+    if (!best) return fail(FTE_EINVAL, "NULL best");
+    cudaStream_t st = (cudaStream_t)stream;
+    // candidates
+    fte_launch_config cand[16];
+    int nc = 0;
+    const int steps_sorted[4] = {32, 64, 128, 256};
+    const int n_steps_opts = prm->sort_every > 0 ? 4 : 1;
+    for (int ti = 0; ti < 2; ++ti)
+        for (int si = 0; si < n_steps_opts; ++si)
+            for (int li = 0; li < 2; ++li) {
+                const int layout = li == 0 ? FTE_LAYOUT_SHARED : FTE_LAYOUT_GLOBAL;
+                if (layout == FTE_LAYOUT_SHARED && !shared_fits(n_sets, nb)) continue;
+                fte_launch_config& c = cand[nc++];
+                c.threads = ti == 0 ? 128 : 256;
+                c.steps_per_launch = prm->sort_every > 0 ? steps_sorted[si] : (int)kChunkSteps;
+                c.tally_layout = layout;
+                c.pad = 0;
+            }
+    double secs[16] = {0}, done[16] = {0};
+    int ran[16] = {0};
+    const long long trial = prm->sort_every > 0 ? 256 : kChunkSteps;   // steps per trial
+    long long n = n_start;
+    cudaEvent_t e0, e1;
+    FTE_CUDA(cudaEventCreate(&e0), "event create");
+    FTE_CUDA(cudaEventCreate(&e1), "event create");
+    fte_status result = FTE_OK;
+    for (int round = 0; round < 2 && result == FTE_OK; ++round)
+        for (int q = 0; q < nc && result == FTE_OK; ++q) {
+            const int k = round == 0 ? q : nc - 1 - q;
+            if (n + trial > n_end || P->count == 0) break;
+            EnsConfig c;
+            result = to_config(&cand[k], prm, n_sets, nb, &c);
+            if (result != FTE_OK) break;
+            unsigned long long before = 0, after = 0;
+            if (cudaMemcpyAsync(&before, t->ledger_n + 6, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                cudaEventRecord(e0, st) != cudaSuccess) { result = cuda_fail(cudaGetLastError(), "trial start"); break; }
+            result = ens_run(P, bg, prm, sets, n_sets, t, nb, n, n + trial, c, ws, ws_bytes, st);
+            if (result != FTE_OK) break;
+            if (cudaEventRecord(e1, st) != cudaSuccess ||
+                cudaMemcpyAsync(&after, t->ledger_n + 6, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                cudaStreamSynchronize(st) != cudaSuccess) { result = cuda_fail(cudaGetLastError(), "trial end"); break; }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            secs[k] += ms * 1e-3;
+            done[k] += (double)(after - before);
+            ran[k] = 1;
+            n += trial;
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (result != FTE_OK) return result;
+    int bi = -1;
+    double brate = -1.0;
+    for (int k = 0; k < nc; ++k) {
+        const double r = (ran[k] && secs[k] > 0) ? done[k] / secs[k] : 0.0;
+        if (tried) tried[k] = cand[k];
+        if (rates) rates[k] = r;
+        if (ran[k] && r > brate) { brate = r; bi = k; }
+    }
+    if (n_tried) *n_tried = nc;
+    if (bi < 0) {   // no trial ran: the default configuration
+        EnsConfig c;
+        s = to_config(nullptr, prm, n_sets, nb, &c);
+        if (s != FTE_OK) return s;
+        best->threads = c.nt; best->steps_per_launch = c.steps;
+        best->tally_layout = c.mode == kModeShared ? FTE_LAYOUT_SHARED : FTE_LAYOUT_GLOBAL;
+        best->pad = 0;
+    } else {
+        *best = cand[bi];
+    }
+    if (n < n_end && P->count) {
+        EnsConfig c;
+        s = to_config(best, prm, n_sets, nb, &c);
+        if (s != FTE_OK) return s;
+        return ens_run(P, bg, prm, sets, n_sets, t, nb, n, n_end, c, ws, ws_bytes, st);
+    }
+    return FTE_OK;
+}
+
+fte_status fte_graph_begin(void* stream)
+{
+    if (!stream) return fail(FTE_EINVAL, "the legacy NULL stream cannot be captured");
+    FTE_CUDA(cudaStreamBeginCapture((cudaStream_t)stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+    return FTE_OK;
+}
+
+fte_status fte_graph_end(void* stream, fte_graph** out)
+{
+    if (!stream || !out) return fail(FTE_EINVAL, "NULL stream or output");
+    *out = nullptr;
+    cudaGraph_t g = nullptr;
+    FTE_CUDA(cudaStreamEndCapture((cudaStream_t)stream, &g), "end capture");
+    cudaGraphExec_t ex = nullptr;
+    const cudaError_t e = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(e, "graph instantiate");
+    fte_graph* h = new (std::nothrow) fte_graph;
+    if (!h) {
+        cudaGraphExecDestroy(ex);
+        return fail(FTE_ENOMEM, "out of host memory");
+    }
+    h->exec = ex;
+    *out = h;
+    return FTE_OK;
+}
+
+fte_status fte_graph_launch(const fte_graph* g, void* stream)
+{
+    if (!g) return fail(FTE_EINVAL, "NULL graph");
+    FTE_CUDA(cudaGraphLaunch(g->exec, (cudaStream_t)stream), "graph launch");
+    return FTE_OK;
+}
+
+fte_status fte_graph_destroy(fte_graph* g)
+{
+    if (!g) return FTE_OK;
+    const cudaError_t e = cudaGraphExecDestroy(g->exec);
+    delete g;
+    if (e != cudaSuccess) return cuda_fail(e, "graph destroy");
+    return FTE_OK;
+}
+
+}  // extern "C"

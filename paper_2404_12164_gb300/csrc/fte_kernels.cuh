@@ -5,6 +5,24 @@
 
 namespace fte {
 
+// Step-kernel modes: one parameter set; an ensemble with all sets' tallies in
+// shared memory; an ensemble with FP64 atomics into the global tally.
+constexpr int kModeSingle = 0;
+constexpr int kModeShared = 1;
+constexpr int kModeGlobal = 2;
+
+// Per-set transport parameters of an ensemble (everything else is shared).
+struct SetK {
+    float lambda_par, q, H, eps;
+    uint32_t seed, set_id;
+};
+
+struct BatchArgs {
+    int n_sets, pad;
+    unsigned long long end[FTE_MAX_SETS];   // pool entries [end[s-1], end[s]) belong to set s
+    SetK set[FTE_MAX_SETS];
+};
+
 struct AdvanceArgs {
     GridK g;
     ParamsK prm;
@@ -17,7 +35,10 @@ struct AdvanceArgs {
     long long n_start, n_end;     // steps advanced by this launch
     long long n_table0;           // step index of table[0]
     const StepEntry* table;
-    const double* norm;           // normalisation integral of D_mumu
+    const double* norm;           // normalisation integral of D_mumu (one per set)
+    double* gS;                   // kModeGlobal: FP64 accumulators [set][bin]
+    double* gS2;
+    unsigned long long* gC;
     const uint32_t* order;        // alive particles in spatial order (NULL: all, by index)
     const unsigned* n_order;      // number of entries of `order` (device)
     float* part;                  // per-block partial histograms [grid][3][nbins]
@@ -73,8 +94,22 @@ struct InjectArgs {
     unsigned long long* ledger_n;
 };
 
+static_assert(sizeof(AdvanceArgs) + sizeof(BatchArgs) <= 4096, "step kernel parameters exceed 4 KB");
+
+// Per-set inputs of the D_mumu normalisation integral.
+struct NormSets {
+    double q[FTE_MAX_SETS], H[FTE_MAX_SETS], eps[FTE_MAX_SETS];
+};
+
 // launchers (return cudaGetLastError())
-cudaError_t launch_advance(const AdvanceArgs& a, int kperp, int blocks, size_t smem, cudaStream_t s);
+// step kernel of (kperp, dtype, mode, threads per block); nt is 256 for kModeSingle
+cudaError_t launch_advance(const AdvanceArgs& a, const BatchArgs& b, int kperp, int mode, int nt, int blocks,
+                           size_t smem, cudaStream_t s);
+cudaError_t advance_occupancy(int kperp, int dtype, int mode, int nt, size_t smem, int* blocks_per_sm);
+// the ensemble variants live in their own translation unit (fte_batched.cu)
+const void* advance_fn_batched(int kperp, int dtype, int mode, int nt);
+cudaError_t launch_advance_batched(const AdvanceArgs& a, const BatchArgs& b, int kperp, int mode, int nt,
+                                   int blocks, size_t smem, cudaStream_t s);
 cudaError_t launch_reduce(const float* part, int nblk, int nbins, double* S, double* S2,
                           unsigned long long* C, cudaStream_t s);
 cudaError_t launch_step_table(const StepTableArgs& a, cudaStream_t s);
@@ -82,10 +117,12 @@ cudaError_t launch_step_table(const StepTableArgs& a, cudaStream_t s);
 constexpr int kNormPartials = 128;
 cudaError_t launch_norm(int model, double q, double H, double eps, double* out, double* part,
                         cudaStream_t s);
+// the same for n_sets sets at once: out[s], scratch part[n_sets][kNormPartials]
+cudaError_t launch_norm_sets(int model, const NormSets& ns, int n_sets, double* out, double* part,
+                             cudaStream_t s);
 cudaError_t launch_tally_out(const double* S, const double* S2, const unsigned long long* C,
                              const ObsOut& ob, int kind, double* out, cudaStream_t s);
 cudaError_t launch_inject(const InjectArgs& a, cudaStream_t s);
-cudaError_t advance_occupancy(int kperp, int dtype, size_t smem, int* blocks_per_sm);
 // spatial ordering of the alive particles (fte_sort.cu)
 size_t sort_scratch_bytes(const GridK& g, unsigned long long n);
 void sort_carve(const GridK& g, unsigned long long n, char* p, SortArgs* a);

@@ -1,0 +1,317 @@
+// The per-particle step loop of the transport kernels (Sec. 2.1, 2.4) with the
+// fused occupancy tally, shared by the single-set and the ensemble kernels.
+#pragma once
+
+#include "fte_kernels.cuh"
+
+namespace fte {
+
+// ---------------------------------------------------------------------------
+// Occupancy tally (start-of-step state, w dt per step).  Lanes of a warp that
+// hit the same bin are merged first (__match_any_sync), then one lane per bin
+// adds the merged sums to the block's shared-memory histogram.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void warp_tally(float* shS, float* shS2, unsigned* shC, int bin,
+                                           float val)
+{
+    const unsigned m = __activemask();
+    if (!__any_sync(m, bin >= 0)) return;
+    const unsigned grp = __match_any_sync(m, bin);
+    if (bin < 0) return;
+    float s = 0.f, s2 = 0.f;
+    unsigned mm = grp;
+    while (mm) {
+        const int src = __ffs(mm) - 1;
+        mm &= mm - 1;
+        const float v = __shfl_sync(grp, val, src);
+        s += v;
+        s2 += v * v;
+    }
+    if ((int)(threadIdx.x & 31) == __ffs(grp) - 1) {
+        atomicAdd(&shS[bin], s);
+        atomicAdd(&shS2[bin], s2);
+        atomicAdd(&shC[bin], (unsigned)__popc(grp));
+    }
+}
+
+// The same merge for tallies too large for shared memory (ensembles): one lane
+// per bin adds the merged sums to the FP64 accumulators in global memory.
+__device__ __forceinline__ void warp_tally_global(double* S, double* S2, unsigned long long* C,
+                                                  int bin, float val)
+{
+    const unsigned m = __activemask();
+    if (!__any_sync(m, bin >= 0)) return;
+    const unsigned grp = __match_any_sync(m, bin);
+    if (bin < 0) return;
+    float s = 0.f, s2 = 0.f;
+    unsigned mm = grp;
+    while (mm) {
+        const int src = __ffs(mm) - 1;
+        mm &= mm - 1;
+        const float v = __shfl_sync(grp, val, src);
+        s += v;
+        s2 += v * v;
+    }
+    if ((int)(threadIdx.x & 31) == __ffs(grp) - 1) {
+        atomicAdd(&S[bin], (double)s);
+        atomicAdd(&S2[bin], (double)s2);
+        atomicAdd(&C[bin], (unsigned long long)__popc(grp));
+    }
+}
+
+// One Euler-Maruyama step of Eqs. 2-4 for one particle (Sec. 2.1), with the
+// background interpolated at the start-of-step position and time (Sec. 2.4).
+template <bool KPERP, int DT, int MODE>
+__device__ __forceinline__ int step(const AdvanceArgs& a, const ParamsK& prm, float I, int sbin,
+                                    long long n, uint32_t pid,
+                                    float& x, float& y, float& z, float& mu, float& p, float w,
+                                    float* shS, float* shS2, unsigned* shC, const float* sc,
+                                    unsigned long long& noor)
+{
+    const StepEntry* ep = a.table + (n - a.n_table0);
+    StepEntry e;
+    {
+        const int4 h = __ldg(reinterpret_cast<const int4*>(ep));   // s0, s1, wt, two
+        e.s0 = h.x; e.s1 = h.y; e.wt = __int_as_float(h.z); e.two = h.w;
+    }
+    const float rho2 = x * x + y * y;
+    const float r = sqrtf(rho2 + z * z);
+    const float rho = sqrtf(rho2);
+    const float th = atan2f(rho, z);
+    float ph = atan2f(y, x);
+    if (ph < 0.f) ph += kTwoPi;
+
+    Loc L;
+    locate(a.g, r, th, ph, L);
+    Fields<KPERP> F;
+    gather<KPERP, DT>(a.g, e, L, sc, F);
+    const float* B = F.f;
+    const float* V = F.f + 3;
+    const float* G = F.f + 6;
+    const float* gB = F.f + 15;
+
+    // derived background quantities
+    const float invB = rsqrtf(B[0] * B[0] + B[1] * B[1] + B[2] * B[2]);
+    const float b0 = B[0] * invB, b1 = B[1] * invB, b2 = B[2] * invB;
+    const float divb = -(b0 * gB[0] + b1 * gB[1] + b2 * gB[2]) * invB;   // 1 / L
+    const float divv = G[0] + G[4] + G[8];
+    const float bbgv = b0 * (G[0] * b0 + G[1] * b1 + G[2] * b2)
+                     + b1 * (G[3] * b0 + G[4] * b1 + G[5] * b2)
+                     + b2 * (G[6] * b0 + G[7] * b1 + G[8] * b2);
+    float bdvdt = 0.f;
+    if (prm.dvdt_term) {
+        const float s = e.two ? a.g.inv_dt_snap : 0.f;   // dV/dt = dV/dt|_x + (V.grad) V
+        const float a0 = F.dv[0] * s + G[0] * V[0] + G[1] * V[1] + G[2] * V[2];
+        const float a1 = F.dv[1] * s + G[3] * V[0] + G[4] * V[1] + G[5] * V[2];
+        const float a2 = F.dv[2] * s + G[6] * V[0] + G[7] * V[1] + G[8] * V[2];
+        bdvdt = b0 * a0 + b1 * a1 + b2 * a2;
+    }
+
+    const float v = speed_of(p);
+    float D, dD;
+    dmumu(prm, I, mu, v, p, D, dD);
+
+    const uint4 rb = philox4x32_10(make_uint4((uint32_t)n, pid, 0u, 0u),
+                                   make_uint2(prm.seed, prm.set_id));
+    const float amp0 = sqrtf(-2.f * logf(u01(rb.x)));
+    float s1, c1;
+    sincospif(2.f * u01(rb.y), &s1, &c1);
+    const float dt = prm.dt;
+
+    // Eq. 3 + Ito pitch-angle diffusion, reflecting at mu = +-1
+    const float omm = 1.f - mu * mu;
+    const float mudot = 0.5f * omm * (v * divb + mu * divv - 3.f * mu * bbgv - (2.f / v) * bdvdt);
+    float mun = mu + (mudot + dD) * dt + sqrtf(2.f * D * dt) * (amp0 * c1);
+    if (mun > 1.f) mun = 2.f - mun;
+    if (mun < -1.f) mun = -2.f - mun;
+    mun = fminf(fmaxf(mun, -1.f), 1.f);
+
+    // Eq. 2 (V_d = 0) + cross-field diffusion kappa_perp = (v lambda_perp / 3)(I - bb)
+    float ux = V[0] + mu * v * b0, uy = V[1] + mu * v * b1, uz = V[2] + mu * v * b2;
+    float nx = 0.f, ny = 0.f, nz = 0.f;
+    if (KPERP) {
+        const float kap = v * prm.lambda_perp * (1.f / 3.f);
+        if (prm.kappa_drift) {
+            const float cth = z / r, sth = rho / r;
+            const float cph = rho > 0.f ? x / rho : 1.f, sph = rho > 0.f ? y / rho : 0.f;
+            const float br = (b0 * cph + b1 * sph) * sth + b2 * cth;        // b . r_hat
+            const float bt = ((b0 * cph + b1 * sph) * cth - b2 * sth) / r;  // b . theta_hat / r
+            const float bp = (-b0 * sph + b1 * cph) / rho;                  // b . phi_hat / (r sin th)
+            float g3[3];
+#pragma unroll
+            for (int m = 0; m < 3; ++m)
+                g3[m] = F.dBa[3 * m + 0] * br + F.dBa[3 * m + 1] * bt + F.dBa[3 * m + 2] * bp;
+            const float par = b0 * g3[0] + b1 * g3[1] + b2 * g3[2];
+            // div(kappa_perp) = -kappa [(div b) b + (b.grad) b]
+            ux -= kap * (divb * b0 + (g3[0] - b0 * par) * invB);
+            uy -= kap * (divb * b1 + (g3[1] - b1 * par) * invB);
+            uz -= kap * (divb * b2 + (g3[2] - b2 * par) * invB);
+        }
+        float e10, e11, e12;
+        const float cz = sqrtf(b0 * b0 + b1 * b1);       // |b x z_hat|
+        if (cz >= 0.1f) {
+            e10 = b1 / cz; e11 = -b0 / cz; e12 = 0.f;
+        } else {
+            const float cx = sqrtf(b1 * b1 + b2 * b2);   // |b x x_hat|
+            e10 = 0.f; e11 = b2 / cx; e12 = -b1 / cx;
+        }
+        const float e20 = b1 * e12 - b2 * e11, e21 = b2 * e10 - b0 * e12, e22 = b0 * e11 - b1 * e10;
+        const float z1 = amp0 * s1;
+        const float z2 = sqrtf(-2.f * logf(u01(rb.z))) * cospif(2.f * u01(rb.w));
+        const float amp = sqrtf(2.f * kap * dt);
+        nx = amp * (z1 * e10 + z2 * e20);
+        ny = amp * (z1 * e11 + z2 * e21);
+        nz = amp * (z1 * e12 + z2 * e22);
+    }
+    const float xn = x + ux * dt + nx, yn = y + uy * dt + ny, zn = z + uz * dt + nz;
+
+    // Eq. 4
+    const float pdot = 0.5f * (1.f - 3.f * mu * mu) * bbgv - 0.5f * omm * divv - (mu / v) * bdvdt;
+    const float pn = (prm.p_update == 0) ? p * expf(pdot * dt) : p * (1.f + pdot * dt);
+
+    // occupancy tally of the start-of-step state
+    if (a.n_obs) {
+        const float E = energy_of(p);
+        for (int o = 0; o < a.n_obs; ++o) {
+            const ObsK& ob = a.obs[o];
+            bool in;
+            if (ob.kind == 2) {
+                in = fabsf(x - ob.r) <= ob.dr;
+            } else {
+                in = fabsf(r - ob.r) <= ob.dr;
+                if (ob.kind == 1) {
+                    float d = ph - ob.ph;
+                    if (d > kPi) d -= kTwoPi;
+                    if (d < -kPi) d += kTwoPi;
+                    in = in && fabsf(th - ob.th) <= ob.dth && fabsf(d) <= ob.dph;
+                }
+            }
+            int bin = -1;
+            if (in) {
+                const float le = logf(E / ob.e_lo) * ob.ne_over_lnratio;
+                const int it = __ldg(&ep->it[o]);
+                if (le >= 0.f && le < (float)ob.ne && it >= 0)
+                    bin = sbin + ob.off + (int)le * ob.nt + it;
+                else
+                    ++noor;
+            }
+            if (MODE == kModeGlobal) warp_tally_global(a.gS, a.gS2, a.gC, bin, w * dt);
+            else warp_tally(shS, shS2, shC, bin, w * dt);
+        }
+    }
+
+    x = xn; y = yn; z = zn; mu = mun; p = pn;
+    if (!(isfinite(xn) && isfinite(yn) && isfinite(zn) && isfinite(mun) && isfinite(pn)))
+        return FTE_DEAD_NAN;
+    const float rn = sqrtf(xn * xn + yn * yn + zn * zn);
+    if (rn < a.g.r_min) return FTE_ABS_INNER;
+    if (rn > a.g.r_max) return FTE_ABS_OUTER;
+    // theta < th_min  <=>  z > r cos(th_min); theta > th_max  <=>  z < r cos(th_max)
+    if (zn > rn * a.g.cos_th_min || zn < rn * a.g.cos_th_max) return FTE_ABS_THETA;
+    return FTE_ALIVE;
+}
+
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Set of pool entry i: the first s with i < end[s] (end holds running totals).
+__device__ __forceinline__ int set_of(const unsigned long long* end, int n_sets, unsigned long long i)
+{
+    int lo = 0, hi = n_sets - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (i < end[mid]) hi = mid; else lo = mid + 1;
+    }
+    return lo;
+}
+
+// Persistent step kernel: each thread takes particles from a shared counter and
+// keeps each one in registers for all steps [n_start, n_end) of the launch.
+// MODE kModeSingle: one parameter set, tally in shared memory; kModeShared: an
+// ensemble (per-set parameters and tallies, the tallies of all sets in shared
+// memory); kModeGlobal: an ensemble with warp-merged FP64 atomics to the tally.
+template <bool KPERP, int DT, int MODE, int NT>
+__global__ void __launch_bounds__(NT, MODE == kModeSingle ? 1 : 512 / NT) advance_kernel(const AdvanceArgs a, const BatchArgs b)
+{
+    extern __shared__ float sh[];
+    const int nsh = MODE == kModeGlobal ? 0 : (MODE == kModeShared ? b.n_sets : 1) * a.nbins;
+    float* shS = sh;
+    float* shS2 = sh + nsh;
+    unsigned* shC = reinterpret_cast<unsigned*>(sh + 2 * nsh);
+    __shared__ float sc[FTE_NFIELD];      // per-field scales of 16-bit storage
+    constexpr int kSets = MODE == kModeSingle ? 1 : FTE_MAX_SETS;
+    __shared__ unsigned long long s_end[kSets];
+    __shared__ SetK s_set[kSets];
+    __shared__ float s_I[kSets];
+    for (int q = threadIdx.x; q < 3 * nsh; q += NT) sh[q] = 0.f;
+    if (DT != FTE_F32 && threadIdx.x < FTE_NFIELD) sc[threadIdx.x] = __ldg(a.g.scale + threadIdx.x);
+    if (MODE != kModeSingle) {
+        for (int s = threadIdx.x; s < b.n_sets; s += NT) {
+            s_end[s] = b.end[s];
+            s_set[s] = b.set[s];
+            s_I[s] = (float)__ldg(a.norm + s);
+        }
+    }
+    __syncthreads();
+
+    const float I0 = MODE == kModeSingle ? (float)__ldg(a.norm) : 0.f;
+    const unsigned long long n_work = a.order ? (unsigned long long)__ldg(a.n_order) : a.n_particles;
+    unsigned long long nsteps = 0, noor = 0;
+    for (;;) {
+        const unsigned long long f = atomicAdd(a.fetch, 1ULL);
+        if (f >= n_work) break;
+        const unsigned long long i = a.order ? (unsigned long long)__ldg(a.order + f) : f;
+        if (!a.order && a.status[i] != FTE_ALIVE) continue;
+        float x = a.x[i], y = a.y[i], z = a.z[i], mu = a.mu[i], p = a.p[i];
+        const float w = a.w[i];
+        const uint32_t pid = a.id[i];
+        int st = FTE_ALIVE;
+        if (MODE == kModeSingle) {
+            for (long long n = a.n_start; n < a.n_end; ++n) {
+                ++nsteps;
+                st = step<KPERP, DT, MODE>(a, a.prm, I0, 0, n, pid, x, y, z, mu, p, w, shS, shS2, shC, sc, noor);
+                if (st != FTE_ALIVE) break;
+            }
+        } else {
+            const int s = set_of(s_end, b.n_sets, i);
+            ParamsK prm = a.prm;
+            prm.lambda_par = s_set[s].lambda_par;
+            prm.q = s_set[s].q;
+            prm.H = s_set[s].H;
+            prm.eps = s_set[s].eps;
+            prm.seed = s_set[s].seed;
+            prm.set_id = s_set[s].set_id;
+            const float I = s_I[s];
+            const int sbin = s * a.nbins;
+            for (long long n = a.n_start; n < a.n_end; ++n) {
+                ++nsteps;
+                st = step<KPERP, DT, MODE>(a, prm, I, sbin, n, pid, x, y, z, mu, p, w, shS, shS2, shC, sc, noor);
+                if (st != FTE_ALIVE) break;
+            }
+        }
+        a.x[i] = x; a.y[i] = y; a.z[i] = z; a.mu[i] = mu; a.p[i] = p;
+        if (st != FTE_ALIVE) {
+            a.status[i] = (uint8_t)st;
+            atomicAdd(&a.ledger_w[st], (double)w);
+            atomicAdd(&a.ledger_n[st], 1ULL);
+        }
+    }
+
+    __syncthreads();   // all tally updates of this block are in shared memory
+    if (MODE != kModeGlobal) {
+        float* out = a.part + (size_t)blockIdx.x * 3 * nsh;
+        for (int q = threadIdx.x; q < 3 * nsh; q += NT) out[q] = sh[q];
+    }
+    nsteps = warp_sum_u64(nsteps);
+    noor = warp_sum_u64(noor);
+    if ((threadIdx.x & 31) == 0) {
+        if (nsteps) atomicAdd(&a.ledger_n[6], nsteps);
+        if (noor) atomicAdd(&a.ledger_n[7], noor);
+    }
+}
+
+}  // namespace fte

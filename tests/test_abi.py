@@ -93,3 +93,37 @@ def test_missing_library_fails_loudly(tmp_path, monkeypatch):
     monkeypatch.setattr(_abi, "_lib", None)
     with pytest.raises(ImportError):
         _abi.lib()
+
+
+def test_ensemble_structs_and_host_checks(L):
+    from fte_inputs.configs import Observer
+    from paper_2404_12164_gb300 import api, _abi as A
+    assert C.sizeof(A.fte_set) == 4 * 8 + 2 * 4 + 8
+    assert C.sizeof(A.fte_launch_config) == 4 * 4
+    # n_sets of a tally is bounded
+    t = A.fte_tally_buf()
+    t.n_obs = 1
+    t.obs[0] = api.observer_c(Observer(ne=16, nt=144))
+    t.n_sets = A.FTE_MAX_SETS + 1
+    assert L.fte_tally_bins(C.byref(t)) == 0
+    t.n_sets = A.FTE_MAX_SETS
+    assert L.fte_tally_bins(C.byref(t)) == 16 * 144
+    # argument checks that return before any CUDA call
+    specs = (A.fte_inject_spec * 1)()
+    counts = (C.c_uint64 * 1)(10)
+    assert L.fte_inject_batched(None, None, specs, counts, 1, None, None) == A.FTE_EINVAL
+    P = A.fte_particles()
+    assert L.fte_inject_batched(C.byref(P), None, specs, counts, 0, None, None) == A.FTE_EINVAL
+    assert L.fte_inject_batched(C.byref(P), None, specs, counts, A.FTE_MAX_SETS + 1, None, None) == A.FTE_EINVAL
+    sets = (A.fte_set * 1)()
+    assert L.fte_advance_batched(None, None, None, sets, 1, None, 0, 1, None, None, 0, None) == A.FTE_EINVAL
+    best = A.fte_launch_config()
+    assert L.fte_autotune_batched(None, None, None, sets, 1, None, 0, 1, None, 0, C.byref(best), None, None,
+                                  None, None) == A.FTE_EINVAL
+    assert L.fte_graph_begin(None) == A.FTE_EINVAL
+    assert b"NULL stream" in L.fte_last_error()
+    h = C.c_void_p(0)
+    assert L.fte_graph_end(None, C.byref(h)) == A.FTE_EINVAL
+    assert L.fte_graph_launch(None, None) == A.FTE_EINVAL
+    assert L.fte_graph_destroy(None) == A.FTE_OK
+    assert L.fte_tally_set(None, 0, 0, 0, None, None, 0, None) == A.FTE_EINVAL

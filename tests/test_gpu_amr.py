@@ -169,7 +169,7 @@ def test_trajectories_on_refined_amr(cir_amr):
 def test_unrefined_amr_matches_uniform_grid():
     from paper_2404_12164_gb300 import api
     spec = amr.AmrSpec(nbr=8, nbt=4, nbp=12, bsize=8, levels=2, n_snap=2, periodic=True, dt_snap=3600.0)
-    g = GridSpec(nr=64, nth=32, nph=96, n_snap=2, periodic=True, dt_snap=3600.0)
+    g = GridSpec(nr=64, nth=32, nph=96, radial="log", n_snap=2, periodic=True, dt_snap=3600.0)
     uni = backgrounds.cir(g)
     leaves, f = amr.from_uniform(spec, uni)
     ba = _device_bg(spec, leaves, f)
