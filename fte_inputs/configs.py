@@ -90,7 +90,8 @@ class Params:
 
 @dataclass
 class Observer:
-    kind: str = "shell"              # 'shell' | 'box'
+    kind: str = "shell"              # 'shell' | 'box' | 'slab' | 'ring' (longitude profile:
+                                     # nt bins in phi over [0, 2 pi), time integrated)
     r: float = 1.0
     dr: float = 0.01
     th: float = 90 * DEG
@@ -103,6 +104,18 @@ class Observer:
     t_lo: float = 0.0                # s
     t_hi: float = 86400.0
     nt: int = 144
+
+
+@dataclass
+class SmoothObserver:
+    """Kernel-smoothed intensity for parameter gradients: every alive step adds
+    w dt exp(-(r-r_o)^2/(2 sigma_r^2)) exp(-ln(E/e_c)^2/(2 sigma_lnE^2)) exp(-(t-t_c)^2/(2 sigma_t^2))."""
+    r_o: float = 1.0                 # au
+    sigma_r: float = 0.02            # au
+    e_c: float = 0.1                 # MeV
+    sigma_lnE: float = 0.1           # natural log
+    t_c: float = 2 * 86400.0         # s
+    sigma_t: float = 3600.0          # s
 
 
 @dataclass

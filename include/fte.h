@@ -214,8 +214,10 @@ typedef struct fte_params {
 /* ---------------------------------------------------------------------------
  * Tallies.  An observer is kind 0 shell |r - r_o| <= dr; kind 1 box additionally
  * |theta - th| <= dth and |phi - ph| <= dph (phi difference wrapped to [-pi, pi]);
- * kind 2 slab |x - r| <= dr.  Bins: ne logarithmic energy bins on [e_lo, e_hi]
- * (i_E = floor(ne ln(E/e_lo) / ln(e_hi/e_lo))) times nt time bins on [t_lo, t_hi).
+ * kind 2 slab |x - r| <= dr; kind 3 ring |r - r_o| <= dr and |theta - th| <= dth,
+ * the longitude profile of Figs. 5-7.  Bins: ne logarithmic energy bins on [e_lo, e_hi]
+ * (i_E = floor(ne ln(E/e_lo) / ln(e_hi/e_lo))) times nt time bins on [t_lo, t_hi)
+ * (ring: nt longitude bins floor(phi nt / 2 pi), counting steps in [t_lo, t_hi)).
  * At every step, the start-of-step state of every alive particle inside an
  * observer adds w dt to S, (w dt)^2 to S2 and 1 to C of its bin (occupancy
  * estimator).  Accumulators are DEVICE arrays over all observers' bins,
@@ -375,12 +377,62 @@ fte_status fte_graph_end(void* stream, fte_graph** out);
 fte_status fte_graph_launch(const fte_graph* g, void* stream);
 fte_status fte_graph_destroy(fte_graph* g);
 
+/* ---------------------------------------------------------------------------
+ * Pathwise adjoint: gradients of a smooth observable with respect to the
+ * transport parameters, for fitting them to intensities (the paper runs
+ * forward simulations only; this differentiates the same Euler-Maruyama map of
+ * Sec. 2.1 with every step's Philox noise held fixed).
+ * Observable: J = sum_i w_i sum_n dt K(r_n, E_n, t_n) over the alive steps
+ * n = n_start .. n_end-1 of every particle (start-of-step state, t_n = t0 + n dt),
+ * K = exp(-(r - r_o)^2 / (2 sigma_r^2)) exp(-ln(E / e_c)^2 / (2 sigma_lnE^2))
+ *     exp(-(t - t_c)^2 / (2 sigma_t^2)).
+ * Gradients (FTE_NGRAD): dJ/dlambda_par, dJ/dq, dJ/dH, dJ/deps (pathwise, through
+ * D_mumu, its mu derivative and the normalisation integral), dJ/dgamma of the
+ * injected power law (likelihood ratio of each particle's injected energy).
+ * Discrete decisions along a path (cell, reflection, absorption) are held
+ * fixed, so the pathwise part is the derivative of the realised paths; paths
+ * crossing mu = 0 under the quasi-linear D_mumu see its |mu|^(q-2) drift.
+ * Supported: lambda_perp = 0, lambda independent of p (p_ref = 0 or alpha = 0).
+ * ------------------------------------------------------------------------- */
+#define FTE_NGRAD 5
+typedef struct fte_smooth_obs {
+    double r_o, sigma_r;       /* au */
+    double e_c, sigma_lnE;     /* MeV; natural log */
+    double t_c, sigma_t;       /* s */
+} fte_smooth_obs;
+
+/* Scratch (DEVICE) for fte_adjoint_forward/reverse: checkpoints every
+   `checkpoint_every` steps (20 bytes per particle each), per-particle step
+   counts and observables, the replay scratch of the reverse pass and the
+   time table.  0 on error. */
+size_t fte_adjoint_workspace_bytes(int device, const fte_grid* g, uint64_t n_particles, int64_t n_steps,
+                                   int checkpoint_every);
+
+/* Forward pass: advances P from n_start to n_end exactly as fte_advance would
+   (no tally, no ledger), storing checkpoints in ws, and writes J to dev_out[0]
+   (DEVICE, 1 + FTE_NGRAD doubles; the rest is zeroed).  Asynchronous. */
+fte_status fte_adjoint_forward(fte_particles* P, const fte_background* bg, const fte_params* prm,
+                               const fte_smooth_obs* obs, int64_t n_start, int64_t n_end, int checkpoint_every,
+                               double* dev_out, void* ws, size_t ws_bytes, void* stream);
+
+/* Reverse pass after fte_adjoint_forward with the same P, bg, prm, obs, steps,
+   checkpoint interval and ws: writes the FTE_NGRAD gradients to dev_out[1..].
+   spec (HOST, optional): the injection that produced P at n_start; with a power
+   law (energy 1) the dJ/dgamma entry is filled, otherwise it is 0.
+   dev_per_particle (DEVICE, optional, n x (1 + FTE_NGRAD) floats): each
+   particle's J_i and gradients.  Asynchronous. */
+fte_status fte_adjoint_reverse(const fte_particles* P, const fte_background* bg, const fte_params* prm,
+                               const fte_smooth_obs* obs, const fte_inject_spec* spec, int64_t n_start,
+                               int64_t n_end, int checkpoint_every, double* dev_out, float* dev_per_particle,
+                               void* ws, size_t ws_bytes, void* stream);
+
 /* Tally output kinds for fte_tally(). */
 enum { FTE_TALLY_S = 0, FTE_TALLY_S2 = 1, FTE_TALLY_C = 2, FTE_TALLY_INTENSITY = 3 };
 
 /* Write observer `obs`'s [ne][nt] array of `kind` as doubles to dev_out (DEVICE,
    ne*nt doubles).  INTENSITY is j = S v(E_c) / (4 pi V_obs dt_bin dE) with E_c
-   the geometric bin centre and V_obs the observer volume (au^3; 2 dr for a slab):
+   the geometric bin centre and V_obs the observer volume (au^3; 2 dr for a slab;
+   one longitude bin of a ring, whose dt_bin is the whole window t_hi - t_lo):
    particles / (au^2 s sr MeV) per unit weight.  If host_out (HOST, `bytes` >=
    ne*nt*8) is non-NULL the array is also copied there and the call synchronises
    `stream`. */
@@ -390,6 +442,19 @@ fte_status fte_tally(const fte_tally_buf* t, int obs, int kind, double* dev_out,
 /* fte_tally for parameter set `set` of an ensemble tally (0 <= set < max(t->n_sets, 1)). */
 fte_status fte_tally_set(const fte_tally_buf* t, int set, int obs, int kind, double* dev_out, void* host_out,
                          size_t bytes, void* stream);
+
+/* Green's function to time-dependent source (Sec. 2.3: the particles are all
+   injected at t = 0; the solution for a source with a given time profile is the
+   convolution of that Green's-function solution with the profile).  For
+   observer `obs` of set `set`, with time bins of width dt_b = (t_hi - t_lo)/nt:
+   out[e][k] = dt_b * sum_{m=0..k} src[m] X[e][k-m], X the observer's S or
+   INTENSITY array (`kind`) and src[m] the source rate (injected populations per
+   second) in time bin m (dev_src: DEVICE, nt doubles, or NULL for 1 in every
+   bin, so that out[e][k] accumulates towards the steady state of a constant
+   source).  dev_out (DEVICE, ne*nt doubles); host_out/bytes as in fte_tally.
+   EINVAL for ring observers (their bins are longitudes, not times). */
+fte_status fte_tally_convolve(const fte_tally_buf* t, int set, int obs, int kind, const double* dev_src,
+                              double* dev_out, void* host_out, size_t bytes, void* stream);
 
 /* Copy the ledger to HOST arrays (FTE_LEDGER entries each); synchronises `stream`. */
 fte_status fte_ledger(const fte_tally_buf* t, double* host_w, uint64_t* host_n, void* stream);

@@ -837,6 +837,13 @@ static void tally_state(tally_t* T, double x, double y, double z, double p, doub
             double d = fabs(x - ob->r);
             inside = d <= ob->dr;
             if (fabs(d - ob->dr) < 1e-4 * (ob->dr > 1.0 ? ob->dr : 1.0)) amb = 1;
+        } else if (ob->kind == 3) {
+            /* ring |r - r_o| <= dr, |theta - th_o| <= dth: longitudinal profile, second
+               bin axis = longitude (nt equal bins over [0, 2 pi)), time integrated over
+               [t_lo, t_hi) */
+            double d = fabs(r - ob->r), dth_ = fabs(th - ob->th);
+            inside = d <= ob->dr && dth_ <= ob->dth;
+            if (fabs(d - ob->dr) < 1e-4 * ob->r || fabs(dth_ - ob->dth) < 1e-4) amb = 1;
         } else {
             double d = fabs(r - ob->r);
             inside = d <= ob->dr;
@@ -858,6 +865,14 @@ static void tally_state(tally_t* T, double x, double y, double z, double p, doub
         double step_le = log(ob->e_hi / ob->e_lo) / ob->ne;
         double fr = le - ie_f;
         if (fr * step_le < 1e-4 || (1.0 - fr) * step_le < 1e-4) amb = 1;
+        if (ob->kind == 3) {            /* inside the time window: bin in longitude */
+            double lp = ph * ob->nt / (2.0 * OR_PI);
+            it_f = floor(lp);
+            if (it_f >= ob->nt) it_f = ob->nt - 1;
+            double fp = lp - it_f;
+            double wbin = 2.0 * OR_PI / ob->nt;
+            if (fp * wbin < 1e-4 || (1.0 - fp) * wbin < 1e-4) amb = 1;
+        }
         int64_t b = T->off[o] + (int64_t)ie_f * ob->nt + (int64_t)it_f;
         if (inside) {
             double wd = w * dt;
@@ -1074,6 +1089,40 @@ int or_advance(const or_background* bg, const or_params* prm, const or_observer*
     return 0;
 }
 
+/* Smooth observable whose parameter gradients fit transport parameters to
+   intensities: every alive step of particle i adds w dt K(start-of-step state)
+   to J[i], K = exp(-(r - r_o)^2 / (2 s_r^2)) exp(-ln(E / E_c)^2 / (2 s_E^2))
+   exp(-(t - t_c)^2 / (2 s_t^2)); the particles are advanced as by or_advance
+   (no tally, no ledger). */
+static double smooth_kernel(const or_smooth_obs* K, double x, double y, double z, double p, double t)
+{
+    const double r = sqrt(x * x + y * y + z * z);
+    const double le = log(kinetic(p) / K->e_c);
+    const double a = (r - K->r_o) / K->sigma_r, b = le / K->sigma_lnE, c = (t - K->t_c) / K->sigma_t;
+    return exp(-0.5 * a * a) * exp(-0.5 * b * b) * exp(-0.5 * c * c);
+}
+
+int or_observe(const or_background* bg, const or_params* prm, const or_smooth_obs* K, or_particle* P,
+               int64_t n, int64_t n_start, int64_t n_end, double* J, int n_threads)
+{
+    if (n_threads < 1) n_threads = 1;
+    const double I = or_norm_integral(prm->dmumu, prm->q, prm->H, prm->eps);
+#ifdef _OPENMP
+#pragma omp parallel for num_threads(n_threads) schedule(static)
+#endif
+    for (int64_t i = 0; i < n; ++i) {
+        or_particle* q = &P[i];
+        double acc = 0.0;
+        for (int64_t s = n_start; s < n_end && q->status == OR_ALIVE; ++s) {
+            const double t = prm->t0 + (double)s * prm->dt;
+            acc += q->w * prm->dt * smooth_kernel(K, q->x, q->y, q->z, q->p, t);
+            if (step_one(bg, prm, I, q, s, NULL, NULL) != OR_ALIVE) break;
+        }
+        J[i] = acc;
+    }
+    return 0;
+}
+
 /* Intensity from the occupancy sum (Eq. 7 with j = p^2 f): S / dt_bin is the
    mean weight inside the observer volume during the bin; per unit volume and
    energy, times v / (4 pi), gives the differential intensity
@@ -1088,10 +1137,15 @@ void or_intensity(const or_observer* ob, const double* S, double* J)
         double a = ob->r - ob->dr, b = ob->r + ob->dr;
         vol = (b * b * b - a * a * a) / 3.0 * (cos(ob->th - ob->dth) - cos(ob->th + ob->dth))
               * 2.0 * ob->dph;
+    } else if (ob->kind == 3) {
+        double a = ob->r - ob->dr, b = ob->r + ob->dr;
+        vol = (b * b * b - a * a * a) / 3.0 * (cos(ob->th - ob->dth) - cos(ob->th + ob->dth))
+              * 2.0 * OR_PI / ob->nt;
     } else {
         vol = 2.0 * ob->dr;
     }
-    double dtb = (ob->t_hi - ob->t_lo) / ob->nt;
+    /* ring: every longitude bin integrates the whole time window */
+    double dtb = ob->kind == 3 ? ob->t_hi - ob->t_lo : (ob->t_hi - ob->t_lo) / ob->nt;
     for (int e = 0; e < ob->ne; ++e) {
         double e0 = ob->e_lo * pow(ob->e_hi / ob->e_lo, (double)e / ob->ne);
         double e1 = ob->e_lo * pow(ob->e_hi / ob->e_lo, (double)(e + 1) / ob->ne);

@@ -68,7 +68,9 @@ typedef struct {
 } or_inject_spec;
 
 typedef struct {
-    int32_t kind, ne, nt, pad;   /* kind 0 shell, 1 box, 2 slab |x - r| <= dr */
+    int32_t kind, ne, nt, pad;   /* kind 0 shell, 1 box, 2 slab |x - r| <= dr, 3 ring
+                                    (|r - r_o| <= dr, |theta - th| <= dth; nt longitude bins,
+                                    time integrated over [t_lo, t_hi)) */
     double r, dr, th, dth, ph, dph, e_lo, e_hi, t_lo, t_hi;
 } or_observer;
 
@@ -98,6 +100,13 @@ int or_advance(const or_background* bg, const or_params* prm, const or_observer*
 int or_step_terms(const or_background* bg, const or_params* prm, const or_particle* p,
                   int64_t n, double out[32]);
 void or_intensity(const or_observer* obs, const double* S, double* J);
+/* smooth observable for parameter gradients: J[i] = sum over alive steps of
+   w dt exp(-(r-r_o)^2/(2 sigma_r^2)) exp(-ln(E/e_c)^2/(2 sigma_lnE^2)) exp(-(t-t_c)^2/(2 sigma_t^2)) */
+typedef struct {
+    double r_o, sigma_r, e_c, sigma_lnE, t_c, sigma_t;
+} or_smooth_obs;
+int or_observe(const or_background* bg, const or_params* prm, const or_smooth_obs* K, or_particle* P,
+               int64_t n, int64_t n_start, int64_t n_end, double* J, int n_threads);
 /* value of padded cell (li, lj, lk) of an AMR leaf (interior cells: the stored record;
    ghost cells: the neighbour value the method defines), fields 0..17 */
 void or_amr_cell(const or_background* bg, int snap, int leaf, int li, int lj, int lk, double out[18]);

@@ -92,6 +92,8 @@ def lib():
         L.or_step_terms.argtypes = [P(Background), P(ParamsC), C.c_void_p, C.c_int64,
                                     P(C.c_double)]
         L.or_intensity.argtypes = [P(ObserverC), C.c_void_p, C.c_void_p]
+        L.or_observe.argtypes = [P(Background), P(ParamsC), P(SmoothObsC), C.c_void_p, C.c_int64,
+                                 C.c_int64, C.c_int64, C.c_void_p, C.c_int]
         L.or_max_threads.restype = C.c_int
         L.or_amr_cell.argtypes = [P(Background), C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                                   P(C.c_double)]
@@ -199,7 +201,7 @@ def inject_c(s):
 
 def observer_c(o):
     c = ObserverC()
-    c.kind = {"shell": 0, "box": 1, "slab": 2}[o.kind]
+    c.kind = {"shell": 0, "box": 1, "slab": 2, "ring": 3}[o.kind]
     c.ne, c.nt = o.ne, o.nt
     c.r, c.dr, c.th, c.dth, c.ph, c.dph = o.r, o.dr, o.th, o.dth, o.ph, o.dph
     c.e_lo, c.e_hi, c.t_lo, c.t_hi = o.e_lo, o.e_hi, o.t_lo, o.t_hi
@@ -290,6 +292,46 @@ class Tally:
         J = np.zeros_like(S)
         lib().or_intensity(C.byref(self.oc[o]), S.ctypes.data, J.ctypes.data)
         return J
+
+
+class SmoothObsC(C.Structure):
+    _fields_ = [("r_o", C.c_double), ("sigma_r", C.c_double), ("e_c", C.c_double),
+                ("sigma_lnE", C.c_double), ("t_c", C.c_double), ("sigma_t", C.c_double)]
+
+
+def observe(bg, params, particles, n_start, n_end, obs, threads=None):
+    """Advance particles (in place, no tally) and return each one's smooth observable
+    J_i = sum over alive steps of w dt K(start-of-step state); `obs` has r_o, sigma_r,
+    e_c, sigma_lnE, t_c, sigma_t."""
+    assert particles.dtype == PARTICLE and particles.flags.c_contiguous
+    L = lib()
+    J = np.zeros(len(particles))
+    k = SmoothObsC(obs.r_o, obs.sigma_r, obs.e_c, obs.sigma_lnE, obs.t_c, obs.sigma_t)
+    nthreads = threads or int(os.environ.get("FTE_ORACLE_THREADS", "0")) or L.or_max_threads()
+    rc = L.or_observe(C.byref(bg.c), C.byref(params_c(params)), C.byref(k), particles.ctypes.data,
+                      len(particles), n_start, n_end, J.ctypes.data, nthreads)
+    if rc != 0:
+        raise RuntimeError(f"or_observe failed ({rc})")
+    return J
+
+
+def convolve(G, dt_bin, src=None):
+    """Time-dependent source from the Green's function tally (Sec. 2.3: all particles
+    injected at t = 0, then convolved with the source's time profile): for every
+    energy row e, out[e, k] = dt_bin * sum_{m=0..k} src[m] * G[e, k - m], src[m] the
+    source rate in time bin m (1 in every bin if None, which accumulates towards the
+    steady state).  G: [ne, nt] array (occupancy sums or intensities)."""
+    G = np.asarray(G, dtype=np.float64)
+    ne, nt = G.shape
+    src = np.ones(nt) if src is None else np.asarray(src, dtype=np.float64)
+    out = np.zeros((ne, nt))
+    for e in range(ne):
+        for k in range(nt):
+            acc = 0.0
+            for m in range(k + 1):
+                acc += src[m] * G[e, k - m]
+            out[e, k] = dt_bin * acc
+    return out
 
 
 def advance(bg, params, particles, n_start, n_end, tally=None, ledger=None, threads=None,

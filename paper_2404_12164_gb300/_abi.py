@@ -17,6 +17,7 @@ FTE_F32, FTE_BF16, FTE_F16 = range(3)
 FTE_MAX_OBS = 8
 FTE_LEDGER = 8
 FTE_MAX_SETS = 64
+FTE_NGRAD = 5
 FTE_LAYOUT_SHARED, FTE_LAYOUT_GLOBAL = 1, 2
 FTE_OK, FTE_EINVAL, FTE_ENOMEM, FTE_ECUDA, FTE_ERANGE, FTE_ENOTSUP = range(6)
 FTE_ALIVE, FTE_ABS_INNER, FTE_ABS_OUTER, FTE_ABS_THETA, FTE_DEAD_NAN, FTE_INJ_FAIL = range(6)
@@ -81,6 +82,11 @@ class fte_tally_buf(C.Structure):
                 ("ledger_w", C.c_void_p), ("ledger_n", C.c_void_p)]
 
 
+class fte_smooth_obs(C.Structure):
+    _fields_ = [("r_o", C.c_double), ("sigma_r", C.c_double), ("e_c", C.c_double), ("sigma_lnE", C.c_double),
+                ("t_c", C.c_double), ("sigma_t", C.c_double)]
+
+
 class fte_set(C.Structure):
     _fields_ = [("lambda_par", C.c_double), ("q", C.c_double), ("H", C.c_double), ("eps", C.c_double),
                 ("seed", C.c_uint32), ("set_id", C.c_uint32), ("count", C.c_uint64)]
@@ -111,6 +117,8 @@ SIGNATURES = {
                                       _P(fte_tally_buf), C.c_int64, C.c_int64, C.c_void_p]),
     "fte_tally": (C.c_int, [_P(fte_tally_buf), C.c_int, C.c_int, C.c_void_p, C.c_void_p,
                             C.c_size_t, C.c_void_p]),
+    "fte_tally_convolve": (C.c_int, [_P(fte_tally_buf), C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
+                                     C.c_void_p, C.c_size_t, C.c_void_p]),
     "fte_tally_set": (C.c_int, [_P(fte_tally_buf), C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
                                 C.c_size_t, C.c_void_p]),
     "fte_workspace_bytes_batched": (C.c_size_t, [C.c_int, _P(fte_grid), _P(fte_tally_buf), C.c_uint64,
@@ -124,6 +132,13 @@ SIGNATURES = {
                                        C.c_int, _P(fte_tally_buf), C.c_int64, C.c_int64, C.c_void_p,
                                        C.c_size_t, _P(fte_launch_config), _P(fte_launch_config),
                                        _P(C.c_double), _P(C.c_int), C.c_void_p]),
+    "fte_adjoint_workspace_bytes": (C.c_size_t, [C.c_int, _P(fte_grid), C.c_uint64, C.c_int64, C.c_int]),
+    "fte_adjoint_forward": (C.c_int, [_P(fte_particles), _P(fte_background), _P(fte_params), _P(fte_smooth_obs),
+                                      C.c_int64, C.c_int64, C.c_int, C.c_void_p, C.c_void_p, C.c_size_t,
+                                      C.c_void_p]),
+    "fte_adjoint_reverse": (C.c_int, [_P(fte_particles), _P(fte_background), _P(fte_params), _P(fte_smooth_obs),
+                                      _P(fte_inject_spec), C.c_int64, C.c_int64, C.c_int, C.c_void_p, C.c_void_p,
+                                      C.c_void_p, C.c_size_t, C.c_void_p]),
     "fte_graph_begin": (C.c_int, [C.c_void_p]),
     "fte_graph_end": (C.c_int, [C.c_void_p, _P(C.c_void_p)]),
     "fte_graph_launch": (C.c_int, [C.c_void_p, C.c_void_p]),

@@ -71,7 +71,7 @@ def params_c(p):
 
 def observer_c(o):
     c = A.fte_observer()
-    c.kind = {"shell": 0, "box": 1, "slab": 2}[o.kind]
+    c.kind = {"shell": 0, "box": 1, "slab": 2, "ring": 3}[o.kind]
     c.ne, c.nt = o.ne, o.nt
     c.r, c.dr, c.th, c.dth, c.ph, c.dph = o.r, o.dr, o.th, o.dth, o.ph, o.dph
     c.e_lo, c.e_hi, c.t_lo, c.t_hi = o.e_lo, o.e_hi, o.t_lo, o.t_hi
@@ -426,3 +426,15 @@ class Graph:
                 A.lib().fte_graph_destroy(self.h)
         except Exception:
             pass
+
+
+def fte_tally_convolve(tally, obs, kind=A.FTE_TALLY_INTENSITY, src=None, set_index=0, stream=None):
+    """Observer `obs`'s Green's-function tally convolved with the source rate per time bin
+    (`src`: device tensor of nt doubles, None for a constant unit source), on the host."""
+    ob = tally.observers[obs]
+    host = np.zeros((ob.ne, ob.nt), dtype=np.float64)
+    sp = C.c_void_p(src.data_ptr()) if src is not None else None
+    check(A.lib().fte_tally_convolve(C.byref(tally.c), int(set_index), int(obs), int(kind), sp,
+                                     C.c_void_p(tally.out.data_ptr()), C.c_void_p(host.ctypes.data), host.nbytes,
+                                     _stream(stream)), "fte_tally_convolve")
+    return host

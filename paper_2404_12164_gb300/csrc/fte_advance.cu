@@ -311,15 +311,10 @@ cudaError_t launch_norm(int model, double q, double H, double eps, double* out, 
 // Tally output for one observer: S, S2, C (as doubles) or the intensity
 // j = S v(E_c) / (4 pi V_obs dt_bin dE).
 // ---------------------------------------------------------------------------
-__global__ void tally_out_kernel(const double* S, const double* S2, const unsigned long long* C,
-                                 const ObsOut ob, int kind, double* out)
+// v(E_c) / (4 pi V dt dE) of energy row ie: the factor from the occupancy sum to the
+// intensity.  Ring observers: V of one longitude bin, dt the whole time window.
+__device__ double intensity_factor(const ObsOut& ob, int ie)
 {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= ob.ne * ob.nt) return;
-    const int b = ob.off + k;
-    if (kind == FTE_TALLY_S) { out[k] = S[b]; return; }
-    if (kind == FTE_TALLY_S2) { out[k] = S2[b]; return; }
-    if (kind == FTE_TALLY_C) { out[k] = (double)C[b]; return; }
     const double pi = 3.141592653589793;
     double vol;
     if (ob.kind == 0) {
@@ -329,18 +324,55 @@ __global__ void tally_out_kernel(const double* S, const double* S2, const unsign
         const double lo = ob.r - ob.dr, hi = ob.r + ob.dr;
         vol = (hi * hi * hi - lo * lo * lo) / 3.0 * (cos(ob.th - ob.dth) - cos(ob.th + ob.dth))
               * 2.0 * ob.dph;
+    } else if (ob.kind == 3) {
+        const double lo = ob.r - ob.dr, hi = ob.r + ob.dr;
+        vol = (hi * hi * hi - lo * lo * lo) / 3.0 * (cos(ob.th - ob.dth) - cos(ob.th + ob.dth))
+              * 2.0 * pi / ob.nt;
     } else {
         vol = 2.0 * ob.dr;
     }
-    const int ie = k / ob.nt;
     const double e0 = ob.e_lo * pow(ob.e_hi / ob.e_lo, (double)ie / ob.ne);
     const double e1 = ob.e_lo * pow(ob.e_hi / ob.e_lo, (double)(ie + 1) / ob.ne);
     const double ec = sqrt(e0 * e1);
     const double T = ec / 938.27208816;
     const double pm = sqrt(T * (T + 2.0));
     const double v = (299792458.0 / 1.495978707e11) * pm / sqrt(1.0 + pm * pm);
+    const double dtb = ob.kind == 3 ? ob.t_hi - ob.t_lo : (ob.t_hi - ob.t_lo) / ob.nt;
+    return v / (4.0 * pi * vol * dtb * (e1 - e0));
+}
+
+__global__ void tally_out_kernel(const double* S, const double* S2, const unsigned long long* C,
+                                 const ObsOut ob, int kind, double* out)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= ob.ne * ob.nt) return;
+    const int b = ob.off + k;
+    if (kind == FTE_TALLY_S) { out[k] = S[b]; return; }
+    if (kind == FTE_TALLY_S2) { out[k] = S2[b]; return; }
+    if (kind == FTE_TALLY_C) { out[k] = (double)C[b]; return; }
+    out[k] = S[b] * intensity_factor(ob, k / ob.nt);
+}
+
+// Green's function -> time-dependent source (Sec. 2.3): out[e][k] = dt_bin *
+// sum_{m <= k} src[m] X[e][k - m], X = S or the intensity; src NULL = 1.
+__global__ void convolve_kernel(const double* S, const ObsOut ob, int kind, const double* src, double* out)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= ob.ne * ob.nt) return;
+    const int ie = k / ob.nt, it = k - ie * ob.nt;
+    const double* row = S + ob.off + (size_t)ie * ob.nt;
+    double acc = 0.0;
+    for (int m = 0; m <= it; ++m) acc += (src ? src[m] : 1.0) * row[it - m];
     const double dtb = (ob.t_hi - ob.t_lo) / ob.nt;
-    out[k] = S[b] * v / (4.0 * pi * vol * dtb * (e1 - e0));
+    out[k] = dtb * acc * (kind == FTE_TALLY_INTENSITY ? intensity_factor(ob, ie) : 1.0);
+}
+
+cudaError_t launch_convolve(const double* S, const ObsOut& ob, int kind, const double* src, double* out,
+                            cudaStream_t s)
+{
+    const int n = ob.ne * ob.nt;
+    convolve_kernel<<<(n + 127) / 128, 128, 0, s>>>(S, ob, kind, src, out);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_tally_out(const double* S, const double* S2, const unsigned long long* C,

@@ -152,7 +152,7 @@ fte_status check_tally(const fte_tally_buf* t, size_t* nbins)
     size_t nb = 0;
     for (int o = 0; o < t->n_obs; ++o) {
         const fte_observer& ob = t->obs[o];
-        if (ob.kind < 0 || ob.kind > 2) return fail(FTE_EINVAL, "observer %d: bad kind", o);
+        if (ob.kind < 0 || ob.kind > 3) return fail(FTE_EINVAL, "observer %d: bad kind", o);
         if (ob.ne < 1 || ob.nt < 1 || ob.nt > 32767) return fail(FTE_EINVAL, "observer %d: bad bin counts", o);
         if (!(ob.e_lo > 0.0 && ob.e_hi > ob.e_lo)) return fail(FTE_EINVAL, "observer %d: need 0 < e_lo < e_hi", o);
         if (!(ob.t_hi > ob.t_lo)) return fail(FTE_EINVAL, "observer %d: need t_lo < t_hi", o);
@@ -166,6 +166,23 @@ fte_status check_tally(const fte_tally_buf* t, size_t* nbins)
 }
 
 const BatchArgs g_no_batch = {};    // the single-set kernels ignore their ensemble argument
+
+// Kernel-side observers: bins of observer o start at the sum of the earlier observers' bins.
+void fill_observers(const fte_tally_buf* t, AdvanceArgs* a)
+{
+    size_t off = 0;
+    for (int o = 0; o < t->n_obs; ++o) {
+        const fte_observer& ob = t->obs[o];
+        ObsK& k = a->obs[o];
+        k.kind = ob.kind; k.ne = ob.ne; k.nt = ob.nt; k.off = (int)off;
+        k.r = (float)ob.r; k.dr = (float)ob.dr; k.th = (float)ob.th; k.dth = (float)ob.dth;
+        k.ph = (float)ob.ph; k.dph = (float)ob.dph;
+        k.e_lo = (float)ob.e_lo; k.ne_over_lnratio = (float)(ob.ne / log(ob.e_hi / ob.e_lo));
+        k.phi_scale = (float)(ob.nt / (2.0 * 3.141592653589793));
+        off += (size_t)ob.ne * ob.nt;
+    }
+    a->n_obs = t->n_obs;
+}
 
 // Layout of the fte_advance workspace.
 struct WsLayout {
@@ -484,17 +501,7 @@ fte_status fte_advance(fte_particles* P, const fte_background* bg, const fte_par
         a.order = sa.order;
         a.n_order = sa.hist + sa.nb;
     }
-    size_t off = 0;
-    for (int o = 0; o < t->n_obs; ++o) {
-        const fte_observer& ob = t->obs[o];
-        ObsK& k = a.obs[o];
-        k.kind = ob.kind; k.ne = ob.ne; k.nt = ob.nt; k.off = (int)off;
-        k.r = (float)ob.r; k.dr = (float)ob.dr; k.th = (float)ob.th; k.dth = (float)ob.dth;
-        k.ph = (float)ob.ph; k.dph = (float)ob.dph;
-        k.e_lo = (float)ob.e_lo; k.ne_over_lnratio = (float)(ob.ne / log(ob.e_hi / ob.e_lo));
-        off += (size_t)ob.ne * ob.nt;
-    }
-    a.n_obs = t->n_obs;
+    fill_observers(t, &a);
     a.nbins = (int)(nb ? nb : 1);
     a.x = P->x; a.y = P->y; a.z = P->z; a.mu = P->mu; a.p = P->p; a.w = P->w; a.id = P->id; a.status = P->status;
     a.n_particles = P->count;
@@ -536,33 +543,71 @@ fte_status fte_tally(const fte_tally_buf* t, int obs, int kind, double* dev_out,
     return fte_tally_set(t, 0, obs, kind, dev_out, host_out, bytes, stream);
 }
 
-fte_status fte_tally_set(const fte_tally_buf* t, int set, int obs, int kind, double* dev_out, void* host_out,
-                         size_t bytes, void* stream)
+}  // extern "C"
+
+namespace {
+
+// Validated description of one observer's block of bins (set `set`) for the output kernels.
+fte_status obs_out(const fte_tally_buf* t, int set, int obs, ObsOut* o, size_t* n)
 {
     size_t nb = 0;
     fte_status s = check_tally(t, &nb);
     if (s != FTE_OK) return s;
     if (set < 0 || set >= (t->n_sets > 1 ? t->n_sets : 1)) return fail(FTE_EINVAL, "set %d out of range", set);
     if (obs < 0 || obs >= t->n_obs) return fail(FTE_EINVAL, "observer %d out of range", obs);
-    if (kind < FTE_TALLY_S || kind > FTE_TALLY_INTENSITY) return fail(FTE_EINVAL, "bad tally kind");
-    if (!dev_out) return fail(FTE_EINVAL, "NULL device output");
     const fte_observer& ob = t->obs[obs];
-    const size_t n = (size_t)ob.ne * ob.nt;
-    if (host_out && bytes < n * sizeof(double)) return fail(FTE_ENOMEM, "host buffer too small");
-    ObsOut o;
-    o.kind = ob.kind; o.ne = ob.ne; o.nt = ob.nt;
+    *n = (size_t)ob.ne * ob.nt;
+    o->kind = ob.kind; o->ne = ob.ne; o->nt = ob.nt;
     size_t off = (size_t)set * nb;
     for (int k = 0; k < obs; ++k) off += (size_t)t->obs[k].ne * t->obs[k].nt;
-    o.off = (int)off;
-    o.r = ob.r; o.dr = ob.dr; o.th = ob.th; o.dth = ob.dth; o.dph = ob.dph;
-    o.e_lo = ob.e_lo; o.e_hi = ob.e_hi; o.t_lo = ob.t_lo; o.t_hi = ob.t_hi;
-    cudaStream_t st = (cudaStream_t)stream;
-    FTE_CUDA(launch_tally_out(t->S, t->S2, t->C, o, kind, dev_out, st), "tally output launch");
+    o->off = (int)off;
+    o->r = ob.r; o->dr = ob.dr; o->th = ob.th; o->dth = ob.dth; o->dph = ob.dph;
+    o->e_lo = ob.e_lo; o->e_hi = ob.e_hi; o->t_lo = ob.t_lo; o->t_hi = ob.t_hi;
+    return FTE_OK;
+}
+
+fte_status copy_out(void* host_out, const double* dev_out, size_t n, cudaStream_t st)
+{
     if (host_out) {
         FTE_CUDA(cudaMemcpyAsync(host_out, dev_out, n * sizeof(double), cudaMemcpyDeviceToHost, st), "tally copy");
         FTE_CUDA(cudaStreamSynchronize(st), "stream sync");
     }
     return FTE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+fte_status fte_tally_set(const fte_tally_buf* t, int set, int obs, int kind, double* dev_out, void* host_out,
+                         size_t bytes, void* stream)
+{
+    ObsOut o;
+    size_t n = 0;
+    fte_status s = obs_out(t, set, obs, &o, &n);
+    if (s != FTE_OK) return s;
+    if (kind < FTE_TALLY_S || kind > FTE_TALLY_INTENSITY) return fail(FTE_EINVAL, "bad tally kind");
+    if (!dev_out) return fail(FTE_EINVAL, "NULL device output");
+    if (host_out && bytes < n * sizeof(double)) return fail(FTE_ENOMEM, "host buffer too small");
+    cudaStream_t st = (cudaStream_t)stream;
+    FTE_CUDA(launch_tally_out(t->S, t->S2, t->C, o, kind, dev_out, st), "tally output launch");
+    return copy_out(host_out, dev_out, n, st);
+}
+
+fte_status fte_tally_convolve(const fte_tally_buf* t, int set, int obs, int kind, const double* dev_src,
+                              double* dev_out, void* host_out, size_t bytes, void* stream)
+{
+    ObsOut o;
+    size_t n = 0;
+    fte_status s = obs_out(t, set, obs, &o, &n);
+    if (s != FTE_OK) return s;
+    if (kind != FTE_TALLY_S && kind != FTE_TALLY_INTENSITY) return fail(FTE_EINVAL, "kind must be S or INTENSITY");
+    if (o.kind == 3) return fail(FTE_EINVAL, "observer %d bins longitude, not time", obs);
+    if (!dev_out) return fail(FTE_EINVAL, "NULL device output");
+    if (host_out && bytes < n * sizeof(double)) return fail(FTE_ENOMEM, "host buffer too small");
+    cudaStream_t st = (cudaStream_t)stream;
+    FTE_CUDA(launch_convolve(t->S, o, kind, dev_src, dev_out, st), "convolution launch");
+    return copy_out(host_out, dev_out, n, st);
 }
 
 fte_status fte_probe_sectors(const void* buf, size_t bytes, int threads, int loads, float* dev_out,
@@ -694,17 +739,7 @@ extern "C" fte_status fte_advance_noalloc(fte_particles* P, const fte_background
     a.prm.q = (float)prm->q; a.prm.H = (float)prm->H; a.prm.eps = (float)prm->eps;
     a.prm.mu_floor = (float)prm->mu_floor; a.prm.lambda_perp = (float)prm->lambda_perp;
     a.prm.dt = (float)prm->dt; a.prm.seed = prm->seed; a.prm.set_id = prm->set_id;
-    size_t off = 0;
-    for (int o = 0; o < t->n_obs; ++o) {
-        const fte_observer& ob = t->obs[o];
-        ObsK& k = a.obs[o];
-        k.kind = ob.kind; k.ne = ob.ne; k.nt = ob.nt; k.off = (int)off;
-        k.r = (float)ob.r; k.dr = (float)ob.dr; k.th = (float)ob.th; k.dth = (float)ob.dth;
-        k.ph = (float)ob.ph; k.dph = (float)ob.dph;
-        k.e_lo = (float)ob.e_lo; k.ne_over_lnratio = (float)(ob.ne / log(ob.e_hi / ob.e_lo));
-        off += (size_t)ob.ne * ob.nt;
-    }
-    a.n_obs = t->n_obs;
+    fill_observers(t, &a);
     a.nbins = (int)(nb ? nb : 1);
     a.x = P->x; a.y = P->y; a.z = P->z; a.mu = P->mu; a.p = P->p; a.w = P->w; a.id = P->id; a.status = P->status;
     a.n_particles = P->count;
@@ -892,17 +927,7 @@ fte_status ens_run(fte_particles* P, const fte_background* bg, const fte_params*
         a.order = sa.order;
         a.n_order = sa.hist + sa.nb;
     }
-    size_t off = 0;
-    for (int o = 0; o < t->n_obs; ++o) {
-        const fte_observer& ob = t->obs[o];
-        ObsK& k = a.obs[o];
-        k.kind = ob.kind; k.ne = ob.ne; k.nt = ob.nt; k.off = (int)off;
-        k.r = (float)ob.r; k.dr = (float)ob.dr; k.th = (float)ob.th; k.dth = (float)ob.dth;
-        k.ph = (float)ob.ph; k.dph = (float)ob.dph;
-        k.e_lo = (float)ob.e_lo; k.ne_over_lnratio = (float)(ob.ne / log(ob.e_hi / ob.e_lo));
-        off += (size_t)ob.ne * ob.nt;
-    }
-    a.n_obs = t->n_obs;
+    fill_observers(t, &a);
     a.nbins = (int)(nb ? nb : 1);
     a.x = P->x; a.y = P->y; a.z = P->z; a.mu = P->mu; a.p = P->p; a.w = P->w; a.id = P->id; a.status = P->status;
     a.n_particles = P->count;
@@ -1168,6 +1193,204 @@ fte_status fte_graph_destroy(fte_graph* g)
     const cudaError_t e = cudaGraphExecDestroy(g->exec);
     delete g;
     if (e != cudaSuccess) return cuda_fail(e, "graph destroy");
+    return FTE_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Pathwise adjoint: workspace layout, argument checks, forward and reverse.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct AdjLayout {
+    size_t off_norm, off_npart, off_normd, off_ndpart, off_table, off_ckpt, off_ndead, off_jpart, off_scratch, total;
+    int fwd_blocks, rev_blocks;
+    long long nseg;
+};
+
+fte_status adj_layout(int device, int dtype, unsigned long long n, long long n_steps, int K, AdjLayout* L)
+{
+    const int sms = device_sms(device);
+    if (sms <= 0) return fail(FTE_ECUDA, "cannot query device %d", device);
+    int pf = 0, pr = 0, cur = 0;
+    FTE_CUDA(cudaGetDevice(&cur), "cudaGetDevice");
+    if (cur != device) FTE_CUDA(cudaSetDevice(device), "cudaSetDevice");
+    cudaError_t e = adjoint_blocks(dtype, 0, &pf);
+    if (e == cudaSuccess) e = adjoint_blocks(dtype, 1, &pr);
+    if (cur != device) cudaSetDevice(cur);
+    if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
+    if (pf < 1 || pr < 1) return fail(FTE_ENOTSUP, "adjoint kernels do not fit on an SM");
+    L->fwd_blocks = sms * pf;
+    L->rev_blocks = sms * pr;
+    L->nseg = n_steps > 0 ? (n_steps + K - 1) / K : 1;
+    const unsigned long long nthr = (unsigned long long)L->rev_blocks * 256;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { const size_t o = off; off = (off + bytes + 255) & ~(size_t)255; return o; };
+    L->off_norm = take(64);
+    L->off_npart = take(kNormPartials * sizeof(double));
+    L->off_normd = take(64);
+    L->off_ndpart = take(256 * sizeof(double));
+    L->off_table = take((size_t)(n_steps > 0 ? n_steps : 1) * sizeof(StepEntry));
+    L->off_ckpt = take((size_t)L->nseg * 5 * (n ? n : 1) * sizeof(float));
+    L->off_ndead = take((size_t)(n ? n : 1) * sizeof(int));
+    L->off_jpart = take((size_t)(n ? n : 1) * sizeof(double));
+    L->off_scratch = take((size_t)K * 5 * nthr * sizeof(float));
+    L->total = off;
+    return FTE_OK;
+}
+
+fte_status adj_check(const fte_particles* P, const fte_background* bg, const fte_params* prm,
+                     const fte_smooth_obs* obs, int64_t n_start, int64_t n_end, int K, const void* ws)
+{
+    if (!P || !prm || !obs) return fail(FTE_EINVAL, "NULL particles, params or observable");
+    fte_status s = check_background(bg);
+    if (s != FTE_OK) return s;
+    s = check_params(prm);
+    if (s != FTE_OK) return s;
+    if (!(prm->lambda_par > 0.0)) return fail(FTE_EINVAL, "lambda_par must be > 0");
+    if (prm->dmumu == 0 && !(prm->q > 1.0 && prm->q <= 2.0 && prm->H >= 0.0)) return fail(FTE_EINVAL, "need 1 < q <= 2, H >= 0");
+    if (prm->dmumu == 1 && !(prm->eps > 0.0)) return fail(FTE_EINVAL, "eps must be > 0");
+    if (prm->lambda_perp > 0.0) return fail(FTE_ENOTSUP, "the adjoint needs lambda_perp = 0");
+    if (prm->p_ref > 0.0 && prm->alpha != 0.0) return fail(FTE_ENOTSUP, "the adjoint needs lambda independent of p");
+    if (!(obs->sigma_r > 0.0 && obs->sigma_lnE > 0.0 && obs->sigma_t > 0.0 && obs->e_c > 0.0))
+        return fail(FTE_EINVAL, "observable widths and e_c must be > 0");
+    if (K < 1 || K > 65536) return fail(FTE_EINVAL, "checkpoint_every must be in [1, 65536]");
+    if (n_end < n_start || n_start < 0) return fail(FTE_EINVAL, "need 0 <= n_start <= n_end");
+    if (n_end > 0xFFFFFFFFll) return fail(FTE_EINVAL, "step index exceeds 32 bits");
+    if (!ws) return fail(FTE_EINVAL, "NULL workspace");
+    if (!P->x || !P->y || !P->z || !P->mu || !P->p || !P->w || !P->id || !P->status)
+        return fail(FTE_EINVAL, "NULL particle array");
+    return FTE_OK;
+}
+
+// Kernel arguments shared by both passes; fills the time table and the
+// normalisation integrals when `setup` is set.
+fte_status adj_args(const fte_particles* P, const fte_background* bg, const fte_params* prm,
+                    const fte_smooth_obs* obs, int64_t n_start, int64_t n_end, int K, char* w, const AdjLayout& L,
+                    double* dev_out, bool setup, cudaStream_t st, AdvanceArgs* a, AdjK* k)
+{
+    const long long nsteps = n_end - n_start;
+    double* norm = (double*)(w + L.off_norm);
+    double* normd = (double*)(w + L.off_normd);
+    StepTableArgs ta;
+    memset(&ta, 0, sizeof(ta));
+    ta.tab = (StepEntry*)(w + L.off_table);
+    ta.n0 = n_start; ta.count = nsteps; ta.t0 = prm->t0; ta.dt = prm->dt;
+    ta.n_snap = bg->grid.n_snap; ta.periodic = bg->grid.periodic;
+    ta.t_snap0 = bg->grid.t_snap0; ta.dt_snap = bg->grid.dt_snap;
+    if (setup) {
+        FTE_CUDA(launch_norm(prm->dmumu, prm->q, prm->H, prm->eps, norm, (double*)(w + L.off_npart), st), "norm launch");
+        FTE_CUDA(launch_norm_derivs(prm->dmumu, prm->q, prm->H, prm->eps, normd, (double*)(w + L.off_ndpart), st),
+                 "norm derivative launch");
+        if (nsteps > 0) FTE_CUDA(launch_step_table(ta, st), "step table launch");
+    }
+    memset(a, 0, sizeof(*a));
+    a->g = make_gridk(bg);
+    a->prm.dmumu = prm->dmumu; a->prm.p_update = prm->p_update; a->prm.kappa_drift = prm->kappa_drift;
+    a->prm.dvdt_term = prm->dvdt_term;
+    a->prm.lambda_par = (float)prm->lambda_par; a->prm.p_ref = (float)prm->p_ref; a->prm.alpha = (float)prm->alpha;
+    a->prm.q = (float)prm->q; a->prm.H = (float)prm->H; a->prm.eps = (float)prm->eps;
+    a->prm.mu_floor = (float)prm->mu_floor; a->prm.lambda_perp = 0.f;
+    a->prm.dt = (float)prm->dt; a->prm.seed = prm->seed; a->prm.set_id = prm->set_id;
+    a->x = P->x; a->y = P->y; a->z = P->z; a->mu = P->mu; a->p = P->p; a->w = P->w; a->id = P->id;
+    a->status = P->status;
+    a->n_particles = P->count;
+    a->n_start = n_start; a->n_end = n_end; a->n_table0 = n_start;
+    a->table = ta.tab;
+    a->norm = norm;
+    a->nbins = 1;
+    memset(k, 0, sizeof(*k));
+    k->K = K;
+    k->ckpt = (float*)(w + L.off_ckpt);
+    k->scratch = (float*)(w + L.off_scratch);
+    k->n_dead = (int*)(w + L.off_ndead);
+    k->J_part = (double*)(w + L.off_jpart);
+    k->out = dev_out;
+    k->normd = normd;
+    k->r_o = (float)obs->r_o; k->inv_sr = (float)(1.0 / obs->sigma_r);
+    k->inv_ec = (float)(1.0 / obs->e_c); k->inv_se = (float)(1.0 / obs->sigma_lnE);
+    k->t_c = obs->t_c; k->inv_st = 1.0 / obs->sigma_t; k->t0 = prm->t0; k->dt = prm->dt;
+    return FTE_OK;
+}
+
+// Mean ln E of dN/dE ~ E^-gamma on [e1, e2].
+double mean_ln_energy(double e1, double e2, double gamma)
+{
+    const double a = log(e1), b = log(e2);
+    if (fabs(gamma - 1.0) < 1e-12) return 0.5 * (a + b);
+    const double s = 1.0 - gamma;
+    const double Z = (exp(s * b) - exp(s * a)) / s;
+    const double F = exp(s * b) * (b / s - 1.0 / (s * s)) - exp(s * a) * (a / s - 1.0 / (s * s));
+    return F / Z;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t fte_adjoint_workspace_bytes(int device, const fte_grid* g, uint64_t n_particles, int64_t n_steps,
+                                   int checkpoint_every)
+{
+    if (check_grid(g) != FTE_OK || n_steps < 0 || checkpoint_every < 1) return 0;
+    AdjLayout L;
+    if (adj_layout(device, g->dtype, n_particles, n_steps, checkpoint_every, &L) != FTE_OK) return 0;
+    return L.total;
+}
+
+fte_status fte_adjoint_forward(fte_particles* P, const fte_background* bg, const fte_params* prm,
+                               const fte_smooth_obs* obs, int64_t n_start, int64_t n_end, int checkpoint_every,
+                               double* dev_out, void* ws, size_t ws_bytes, void* stream)
+{
+    fte_status s = adj_check(P, bg, prm, obs, n_start, n_end, checkpoint_every, ws);
+    if (s != FTE_OK) return s;
+    if (!dev_out) return fail(FTE_EINVAL, "NULL output");
+    int device = 0;
+    FTE_CUDA(cudaGetDevice(&device), "cudaGetDevice");
+    AdjLayout L;
+    s = adj_layout(device, bg->grid.dtype, P->count, n_end - n_start, checkpoint_every, &L);
+    if (s != FTE_OK) return s;
+    if (ws_bytes < L.total) return fail(FTE_ENOMEM, "workspace has %zu bytes, needs %zu", ws_bytes, L.total);
+    cudaStream_t st = (cudaStream_t)stream;
+    FTE_CUDA(cudaMemsetAsync(dev_out, 0, (1 + FTE_NGRAD) * sizeof(double), st), "output reset");
+    if (P->count == 0) return FTE_OK;
+    AdvanceArgs a;
+    AdjK k;
+    s = adj_args(P, bg, prm, obs, n_start, n_end, checkpoint_every, (char*)ws, L, dev_out, true, st, &a, &k);
+    if (s != FTE_OK) return s;
+    FTE_CUDA(launch_adjoint_forward(a, k, L.fwd_blocks, st), "adjoint forward launch");
+    return FTE_OK;
+}
+
+fte_status fte_adjoint_reverse(const fte_particles* P, const fte_background* bg, const fte_params* prm,
+                               const fte_smooth_obs* obs, const fte_inject_spec* spec, int64_t n_start,
+                               int64_t n_end, int checkpoint_every, double* dev_out, float* dev_per_particle,
+                               void* ws, size_t ws_bytes, void* stream)
+{
+    fte_status s = adj_check(P, bg, prm, obs, n_start, n_end, checkpoint_every, ws);
+    if (s != FTE_OK) return s;
+    if (!dev_out) return fail(FTE_EINVAL, "NULL output");
+    if (spec && spec->energy == 1 && !(spec->e1 > 0.0 && spec->e2 > spec->e1))
+        return fail(FTE_EINVAL, "need 0 < e1 < e2");
+    int device = 0;
+    FTE_CUDA(cudaGetDevice(&device), "cudaGetDevice");
+    AdjLayout L;
+    s = adj_layout(device, bg->grid.dtype, P->count, n_end - n_start, checkpoint_every, &L);
+    if (s != FTE_OK) return s;
+    if (ws_bytes < L.total) return fail(FTE_ENOMEM, "workspace has %zu bytes, needs %zu", ws_bytes, L.total);
+    cudaStream_t st = (cudaStream_t)stream;
+    FTE_CUDA(cudaMemsetAsync(dev_out + 1, 0, FTE_NGRAD * sizeof(double), st), "output reset");
+    if (P->count == 0) return FTE_OK;
+    AdvanceArgs a;
+    AdjK k;
+    s = adj_args(P, bg, prm, obs, n_start, n_end, checkpoint_every, (char*)ws, L, dev_out, false, st, &a, &k);
+    if (s != FTE_OK) return s;
+    k.per_particle = dev_per_particle;
+    if (spec && spec->energy == 1) {
+        k.score_on = 1;
+        k.mean_lnE = mean_ln_energy(spec->e1, spec->e2, spec->gamma);
+    }
+    FTE_CUDA(launch_adjoint_reverse(a, k, L.rev_blocks, st), "adjoint reverse launch");
     return FTE_OK;
 }
 

@@ -61,6 +61,7 @@ struct ObsK {
     int kind, ne, nt, off;
     float r, dr, th, dth, ph, dph;
     float e_lo, ne_over_lnratio;   // i_E = floor(ln(E / e_lo) * ne / ln(e_hi / e_lo))
+    float phi_scale;               // ring: longitude bin = floor(phi * nt / (2 pi))
 };
 
 // Per-step entry of the time table (built in FP64 by step_table_kernel).

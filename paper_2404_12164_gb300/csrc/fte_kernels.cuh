@@ -101,6 +101,22 @@ struct NormSets {
     double q[FTE_MAX_SETS], H[FTE_MAX_SETS], eps[FTE_MAX_SETS];
 };
 
+// Pathwise adjoint (fte_adjoint.cu): checkpoints, replay scratch and outputs.
+struct AdjK {
+    int K;                        // steps between checkpoints
+    int score_on;                 // injection-index gradient by the likelihood ratio
+    float* ckpt;                  // [segment][5][n]: x, y, z, mu, p at n_start + segment K
+    float* scratch;               // [K][5][threads]: replayed start-of-step states
+    int* n_dead;                  // [n]: steps each particle took (alive at their start)
+    double* J_part;               // [n]: each particle's observable
+    double* out;                  // [1 + FTE_NGRAD]: J, then the gradients
+    float* per_particle;          // optional [n][1 + FTE_NGRAD]
+    const double* normd;          // dI/dq and dI/dH (or dJ/deps) of the normalisation integral
+    float r_o, inv_sr, inv_ec, inv_se;
+    double t_c, inv_st, t0, dt;   // observable time centre and width; step times t0 + n dt
+    double mean_lnE;              // mean ln E of the injected spectrum
+};
+
 // launchers (return cudaGetLastError())
 // step kernel of (kperp, dtype, mode, threads per block); nt is 256 for kModeSingle
 cudaError_t launch_advance(const AdvanceArgs& a, const BatchArgs& b, int kperp, int mode, int nt, int blocks,
@@ -122,7 +138,15 @@ cudaError_t launch_norm_sets(int model, const NormSets& ns, int n_sets, double* 
                              cudaStream_t s);
 cudaError_t launch_tally_out(const double* S, const double* S2, const unsigned long long* C,
                              const ObsOut& ob, int kind, double* out, cudaStream_t s);
+cudaError_t launch_convolve(const double* S, const ObsOut& ob, int kind, const double* src, double* out,
+                            cudaStream_t s);
 cudaError_t launch_inject(const InjectArgs& a, cudaStream_t s);
+// adjoint (fte_adjoint.cu)
+cudaError_t adjoint_blocks(int dtype, int reverse, int* blocks_per_sm);
+cudaError_t launch_adjoint_forward(const AdvanceArgs& a, const AdjK& k, int blocks, cudaStream_t s);
+cudaError_t launch_adjoint_reverse(const AdvanceArgs& a, const AdjK& k, int blocks, cudaStream_t s);
+cudaError_t launch_norm_derivs(int model, double q, double H, double eps, double* out, double* part,
+                               cudaStream_t s);
 // spatial ordering of the alive particles (fte_sort.cu)
 size_t sort_scratch_bytes(const GridK& g, unsigned long long n);
 void sort_carve(const GridK& g, unsigned long long n, char* p, SortArgs* a);

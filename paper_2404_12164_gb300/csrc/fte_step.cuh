@@ -177,6 +177,8 @@ __device__ __forceinline__ int step(const AdvanceArgs& a, const ParamsK& prm, fl
             bool in;
             if (ob.kind == 2) {
                 in = fabsf(x - ob.r) <= ob.dr;
+            } else if (ob.kind == 3) {       // ring: longitude profile at fixed r, theta
+                in = fabsf(r - ob.r) <= ob.dr && fabsf(th - ob.th) <= ob.dth;
             } else {
                 in = fabsf(r - ob.r) <= ob.dr;
                 if (ob.kind == 1) {
@@ -189,7 +191,8 @@ __device__ __forceinline__ int step(const AdvanceArgs& a, const ParamsK& prm, fl
             int bin = -1;
             if (in) {
                 const float le = logf(E / ob.e_lo) * ob.ne_over_lnratio;
-                const int it = __ldg(&ep->it[o]);
+                int it = __ldg(&ep->it[o]);     // time bin, -1 outside [t_lo, t_hi)
+                if (ob.kind == 3 && it >= 0) it = min((int)(ph * ob.phi_scale), ob.nt - 1);
                 if (le >= 0.f && le < (float)ob.ne && it >= 0)
                     bin = sbin + ob.off + (int)le * ob.nt + it;
                 else
@@ -235,7 +238,7 @@ __device__ __forceinline__ int set_of(const unsigned long long* end, int n_sets,
 // ensemble (per-set parameters and tallies, the tallies of all sets in shared
 // memory); kModeGlobal: an ensemble with warp-merged FP64 atomics to the tally.
 template <bool KPERP, int DT, int MODE, int NT>
-__global__ void __launch_bounds__(NT, MODE == kModeSingle ? 1 : 512 / NT) advance_kernel(const AdvanceArgs a, const BatchArgs b)
+__global__ void __launch_bounds__(NT, MODE == kModeSingle ? 0 : 512 / NT) advance_kernel(const AdvanceArgs a, const BatchArgs b)
 {
     extern __shared__ float sh[];
     const int nsh = MODE == kModeGlobal ? 0 : (MODE == kModeShared ? b.n_sets : 1) * a.nbins;

@@ -102,7 +102,7 @@ def test_injection_failure_is_ledgered():
     assert L["n"][5] == 50 and L["n"][0] == 0
 
 
-@pytest.mark.parametrize("kind", ["shell", "box"])
+@pytest.mark.parametrize("kind", ["shell", "box", "ring"])
 def test_intensity_of_homogeneous_isotropic_population(kind):
     """n particles per au^3 with energies uniform in one bin: j = v n / (4 pi dE)."""
     bg = O.analytic_background("uniform_b", [5.0])
