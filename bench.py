@@ -622,6 +622,91 @@ def run_ensemble_case(args):
     }), flush=True)
 
 
+def run_adjoint_case(args):
+    """Adjoint workload: the cir_uniform_1e6 background and transport, 1e6 protons with an E^-3
+    spectrum over 50 keV - 5 MeV, gradients of the smoothed 1 au intensity (E_c = 100 keV,
+    sigma_lnE = 0.1, t_c = 2 d, sigma_t = 1 h, sigma_r = 0.02 au) with respect to lambda_par, q, H
+    and the injection index; checkpoints every 256 steps.  Reports the forward rate of the plain
+    step kernel, the adjoint's forward + reverse time, their ratio, and a central-difference check
+    of dJ/dlambda_par with common random numbers."""
+    import torch
+    from paper_2404_12164_gb300 import api, build
+    build.build()
+    torch.cuda.set_device(0)
+    w, fields = build_workload()
+    n_part, n_steps = args.adj_particles, args.adj_steps
+    inj = dataclasses.replace(w.inject, energy="powerlaw", e1=0.05, e2=5.0, gamma=3.0)
+    obs = configs.SmoothObserver(r_o=1.0, sigma_r=0.02, e_c=0.1, sigma_lnE=0.1, t_c=2 * 86400.0, sigma_t=3600.0)
+    prm = dataclasses.replace(w.params, sort_every=args.sort_every)
+    bg = api.Background(w.grid)
+    api.fte_load_background(bg, torch.from_numpy(np.ascontiguousarray(fields)))
+    del fields
+    pool = api.Particles(n_part)
+    tally = api.Tally(w.observers)
+    ws = api.Workspace()
+    adj = api.Adjoint(bg, prm, obs, 0, n_steps, args.checkpoint_every)
+    stream = torch.cuda.current_stream()
+
+    def inject():
+        pool.c.count = 0
+        api.fte_tally_reset(tally)
+        api.fte_inject(pool, bg, inj, n_part, tally, id_base=0, check_failed=False)
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps / 1e3
+
+    def plain():
+        inject()
+        for c in range(0, n_steps, CHUNK):
+            api.fte_advance(pool, bg, prm, tally, c, min(c + CHUNK, n_steps), ws)
+
+    t_plain = timed(plain, args.steps)
+    alive_steps = int(tally.ledger_n.cpu().numpy()[6])
+
+    def fwd():
+        inject()
+        adj.forward(pool)
+
+    def fwd_rev():
+        fwd()
+        adj.reverse(pool, inj)
+
+    t_fwd = timed(fwd, args.steps)
+    t_adj = timed(fwd_rev, args.steps)
+    J = float(adj.out[0])
+    grads = adj.out[1:].cpu().numpy()
+    # central difference of dJ/dlambda_par with the same particles and noise
+    h = 1e-3 * prm.lambda_par
+    Js = []
+    for lam in (prm.lambda_par + h, prm.lambda_par - h):
+        a2 = api.Adjoint(bg, dataclasses.replace(prm, lambda_par=lam), obs, 0, n_steps, args.checkpoint_every, ws=adj.ws)
+        inject()
+        Js.append(float(a2.forward(pool)))
+    fd = (Js[0] - Js[1]) / (2 * h)
+    print(json.dumps({
+        "case": "adjoint", "metric": METRIC, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": f"cir_uniform_1e6 background and transport, {n_part:.0e} protons E^-3 over 50 keV-5 MeV, "
+                               f"dt=10 s x {n_steps}, smoothed 1 au intensity (E_c 100 keV, sigma_lnE 0.1, "
+                               "t_c 2 d, sigma_t 1 h, sigma_r 0.02 au)", "checkpoint_every": args.checkpoint_every},
+        "forward_plain_kernel": {"value": alive_steps / t_plain, "s": t_plain},
+        "adjoint_forward_pass": {"value": alive_steps / t_fwd, "s": t_fwd},
+        "adjoint_forward_plus_reverse": {"value": alive_steps / t_adj, "s": t_adj},
+        "adj_over_fwd": t_adj / t_plain,
+        "J": J, "grad": dict(zip(api.GRAD_NAMES, grads.tolist())),
+        "fd_check": {"d_lambda_par_central_difference": fd, "adjoint": float(grads[0]),
+                     "rel_diff": abs(fd - grads[0]) / abs(fd) if fd else None},
+    }), flush=True)
+
+
 def l2_probe(mib=64, threads=152 * 2048, loads=256, reps=5):
     """Random 32-byte sector read bandwidth of an L2-resident buffer (GB/s), best of reps."""
     import torch
@@ -643,7 +728,10 @@ def l2_probe(mib=64, threads=152 * 2048, loads=256, reps=5):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--case", default="bench", choices=["bench", "profile", "amr", "ensemble"])
+    ap.add_argument("--case", default="bench", choices=["bench", "profile", "amr", "ensemble", "adjoint"])
+    ap.add_argument("--adj-particles", type=int, default=1_000_000)
+    ap.add_argument("--adj-steps", type=int, default=34_560)
+    ap.add_argument("--checkpoint-every", type=int, default=256)
     ap.add_argument("--ens-steps", type=int, default=2160)
     ap.add_argument("--ens-timed", type=int, default=2)
     ap.add_argument("--amr-particles", type=int, default=10_000_000)
@@ -666,6 +754,8 @@ def main():
         run_amr_case(args)
     elif args.case == "ensemble":
         run_ensemble_case(args)
+    elif args.case == "adjoint":
+        run_adjoint_case(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

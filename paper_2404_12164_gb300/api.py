@@ -438,3 +438,86 @@ def fte_tally_convolve(tally, obs, kind=A.FTE_TALLY_INTENSITY, src=None, set_ind
                                      C.c_void_p(tally.out.data_ptr()), C.c_void_p(host.ctypes.data), host.nbytes,
                                      _stream(stream)), "fte_tally_convolve")
     return host
+
+
+# ---------------------------------------------------------------------------
+# pathwise adjoint of a smooth observable, and its torch.autograd.Function
+# ---------------------------------------------------------------------------
+GRAD_NAMES = ("lambda_par", "q", "H", "eps", "gamma")
+
+
+def smooth_c(o):
+    return A.fte_smooth_obs(o.r_o, o.sigma_r, o.e_c, o.sigma_lnE, o.t_c, o.sigma_t)
+
+
+def fte_adjoint_workspace_bytes(bg, n_particles, n_steps, checkpoint_every, device=None):
+    dev = torch.cuda.current_device() if device is None else device
+    n = A.lib().fte_adjoint_workspace_bytes(dev, C.byref(bg.gc), int(n_particles), int(n_steps),
+                                             int(checkpoint_every))
+    if n == 0:
+        raise RuntimeError("fte_adjoint_workspace_bytes: " + A.lib().fte_last_error().decode())
+    return n
+
+
+class Adjoint:
+    """One checkpointed forward pass and its reverse pass (fte_adjoint_forward / _reverse) for a
+    particle pool, a background, transport parameters and a smooth observable."""
+
+    def __init__(self, bg, params, obs, n_start, n_end, checkpoint_every=256, ws=None, device="cuda"):
+        self.bg, self.params, self.obs = bg, params, obs
+        self.n_start, self.n_end, self.K = int(n_start), int(n_end), int(checkpoint_every)
+        self.ws = ws if ws is not None else Workspace(device)
+        self.out = torch.zeros(1 + A.FTE_NGRAD, dtype=torch.float64, device=device)
+
+    def forward(self, pool, stream=None):
+        """Advance `pool` and return J (a 0-d device tensor, valid once the stream reaches it)."""
+        buf = self.ws.ensure(fte_adjoint_workspace_bytes(self.bg, pool.count, self.n_end - self.n_start, self.K))
+        check(A.lib().fte_adjoint_forward(C.byref(pool.c), C.byref(self.bg.c), C.byref(params_c(self.params)),
+                                          C.byref(smooth_c(self.obs)), self.n_start, self.n_end, self.K,
+                                          C.c_void_p(self.out.data_ptr()), C.c_void_p(buf.data_ptr()),
+                                          buf.numel(), _stream(stream)), "fte_adjoint_forward")
+        self.n_particles = pool.count
+        return self.out[0]
+
+    def reverse(self, pool, inject=None, per_particle=False, stream=None):
+        """Gradients of J (device tensor of FTE_NGRAD doubles, in GRAD_NAMES order); with
+        per_particle also each particle's [J_i, gradients] (float32 [n, 1 + FTE_NGRAD])."""
+        buf = self.ws.buf
+        pp = torch.zeros((pool.count, 1 + A.FTE_NGRAD), dtype=torch.float32, device=buf.device) \
+            if per_particle else None
+        spec = inject_c(inject, 0) if inject is not None else None
+        check(A.lib().fte_adjoint_reverse(C.byref(pool.c), C.byref(self.bg.c), C.byref(params_c(self.params)),
+                                          C.byref(smooth_c(self.obs)), C.byref(spec) if spec is not None else None,
+                                          self.n_start, self.n_end, self.K, C.c_void_p(self.out.data_ptr()),
+                                          C.c_void_p(pp.data_ptr()) if pp is not None else None,
+                                          C.c_void_p(buf.data_ptr()), buf.numel(), _stream(stream)),
+              "fte_adjoint_reverse")
+        return (self.out[1:], pp) if per_particle else self.out[1:]
+
+
+class SmoothIntensity(torch.autograd.Function):
+    """J(theta) for theta = (lambda_par, q, H, eps, gamma): forward injects `run.n_particles`
+    particles per run.inject (power-law index gamma), advances them through the checkpointed
+    forward pass and returns J; backward runs the reverse pass.  `run` carries bg, params,
+    inject, obs, n_steps, n_particles and checkpoint_every (plain attributes)."""
+
+    @staticmethod
+    def forward(ctx, theta, run):
+        import dataclasses
+        th = [float(v) for v in theta.detach().cpu().tolist()]
+        prm = dataclasses.replace(run.params, lambda_par=th[0], q=th[1], H=th[2], eps=th[3])
+        inj = dataclasses.replace(run.inject, gamma=th[4])
+        pool = Particles(run.n_particles, device=run.bg.dev.device)
+        tally = Tally([], device=run.bg.dev.device)
+        fte_tally_reset(tally)
+        fte_inject(pool, run.bg, inj, run.n_particles, tally, id_base=0, check_failed=False)
+        adj = Adjoint(run.bg, prm, run.obs, 0, run.n_steps, run.checkpoint_every, device=run.bg.dev.device)
+        J = adj.forward(pool)
+        ctx.adj, ctx.pool, ctx.inj = adj, pool, inj
+        ctx.theta_device, ctx.theta_dtype = theta.device, theta.dtype
+        return J.detach().clone().to(theta.device, theta.dtype)
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        g = ctx.adj.reverse(ctx.pool, ctx.inj).to(ctx.theta_device, ctx.theta_dtype)
+        return grad_out * g, None
