@@ -5,12 +5,16 @@
 // injection spectral index through the likelihood ratio of the injected
 // energies.
 //
-// Forward: every particle runs its steps once, keeping its state every K steps
-// (checkpoints).  Reverse: per particle, segments are replayed from their
-// checkpoint (start-of-step states into per-thread scratch), then walked
-// backwards: lambda_n = (dF/ds_n)^T lambda_{n+1} + w dt grad K(s_n), and the
-// parameter adjoint gains (dF/dtheta)^T lambda_{n+1}.  Discrete decisions of a
-// step (cell, reflection, clamp, absorption) are those of the replayed path.
+// Forward: the run is cut into segments of K steps; every particle stores its
+// state at each segment start (checkpoints).  Reverse: segment by segment from
+// the last, every particle replays its segment from the checkpoint (start-of-
+// step states into per-thread scratch) and walks it backwards:
+// lambda_n = (dF/ds_n)^T lambda_{n+1} + w dt grad K(s_n), and the parameter
+// adjoint gains (dF/dtheta)^T lambda_{n+1}; the adjoints cross segment borders
+// through global memory.  Discrete decisions of a step (cell, reflection,
+// clamp, absorption) are those of the replayed path.  Each launch may take the
+// particles in spatial order (a counting sort by grid bucket of the positions
+// the launch starts from), which changes no result.
 #include "fte_step.cuh"
 
 namespace fte {
@@ -358,7 +362,9 @@ __device__ void step_vjp(const AdvanceArgs& a, float I, float rq, float rh, long
 }
 
 // ---------------------------------------------------------------------------
-// Forward pass with checkpoints and the per-particle observable.
+// Forward pass, one launch per segment of K steps: each alive particle (taken
+// in spatial order from a.order when reordering is on) stores its checkpoint,
+// runs the segment's steps and adds its observable to J_part.
 // ---------------------------------------------------------------------------
 template <int DT>
 __global__ void __launch_bounds__(256) adj_forward_kernel(const AdvanceArgs a, const AdjK k)
@@ -367,59 +373,55 @@ __global__ void __launch_bounds__(256) adj_forward_kernel(const AdvanceArgs a, c
     __shared__ double red[8];
     if (DT != FTE_F32 && threadIdx.x < FTE_NFIELD) sc[threadIdx.x] = __ldg(a.g.scale + threadIdx.x);
     __syncthreads();
-    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
     const float I = (float)__ldg(a.norm);
+    const unsigned long long n_work = a.order ? (unsigned long long)__ldg(a.n_order) : a.n_particles;
+    const size_t n = a.n_particles;
+    float* c = k.ckpt + (size_t)k.seg * 5 * n;
     double jsum = 0.0;
     unsigned long long noor = 0;
-    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < a.n_particles;
-         i += stride) {
+    for (;;) {
+        const unsigned long long f = atomicAdd(a.fetch, 1ULL);
+        if (f >= n_work) break;
+        const unsigned long long i = a.order ? (unsigned long long)__ldg(a.order + f) : f;
+        if (!a.order && a.status[i] != FTE_ALIVE) continue;
+        float x = a.x[i], y = a.y[i], z = a.z[i], mu = a.mu[i], p = a.p[i];
+        c[i] = x; c[n + i] = y; c[2 * n + i] = z; c[3 * n + i] = mu; c[4 * n + i] = p;
+        const float w = a.w[i];
+        const uint32_t pid = a.id[i];
         double J = 0.0;
-        long long nd = a.n_start;
-        if (a.status[i] == FTE_ALIVE) {
-            float x = a.x[i], y = a.y[i], z = a.z[i], mu = a.mu[i], p = a.p[i];
-            const float w = a.w[i];
-            const uint32_t pid = a.id[i];
-            int st = FTE_ALIVE;
-            long long n = a.n_start;
-            for (; n < a.n_end; ++n) {
-                const long long kk = n - a.n_start;
-                if (kk % k.K == 0) {
-                    float* c = k.ckpt + (size_t)(kk / k.K) * 5 * a.n_particles;
-                    c[i] = x;
-                    c[a.n_particles + i] = y;
-                    c[2 * a.n_particles + i] = z;
-                    c[3 * a.n_particles + i] = mu;
-                    c[4 * a.n_particles + i] = p;
-                }
-                const float r = sqrtf(x * x + y * y + z * z);
-                J += (double)(w * a.prm.dt * smooth_k(k, r, p, k.t0 + (double)n * k.dt, nullptr, nullptr));
-                st = step<false, DT, kModeSingle>(a, a.prm, I, 0, n, pid, x, y, z, mu, p, w, nullptr, nullptr,
-                                                  nullptr, sc, noor);
-                if (st != FTE_ALIVE) { ++n; break; }
-            }
-            nd = n;
-            a.x[i] = x; a.y[i] = y; a.z[i] = z; a.mu[i] = mu; a.p[i] = p;
-            if (st != FTE_ALIVE) a.status[i] = (uint8_t)st;
+        int st = FTE_ALIVE;
+        long long s = a.n_start;
+        for (; s < a.n_end; ++s) {
+            const float r = sqrtf(x * x + y * y + z * z);
+            J += (double)(w * a.prm.dt * smooth_k(k, r, p, k.t0 + (double)s * k.dt, nullptr, nullptr));
+            st = step<false, DT, kModeSingle>(a, a.prm, I, 0, s, pid, x, y, z, mu, p, w, nullptr, nullptr,
+                                              nullptr, sc, noor);
+            if (st != FTE_ALIVE) { ++s; break; }
         }
-        k.n_dead[i] = (int)(nd - a.n_start);
-        k.J_part[i] = J;
+        // steps taken since the start of the run (a.n_table0), counting the one that ended it
+        k.n_dead[i] = (int)(s - a.n_table0);
+        k.J_part[i] += J;
         jsum += J;
+        a.x[i] = x; a.y[i] = y; a.z[i] = z; a.mu[i] = mu; a.p[i] = p;
+        if (st != FTE_ALIVE) a.status[i] = (uint8_t)st;
     }
-    // block sum -> one FP64 atomic per block
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) jsum += __shfl_down_sync(0xffffffffu, jsum, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = jsum;
     __syncthreads();
     if (threadIdx.x == 0) {
-        double s = 0.0;
-        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) s += red[q];
-        atomicAdd(k.out, s);
+        double t = 0.0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[q];
+        if (t != 0.0) atomicAdd(k.out, t);
     }
 }
 
 // ---------------------------------------------------------------------------
-// Reverse pass.  Thread slot `tid` keeps the replayed states of its current
-// segment in scratch[(kk * 5 + c) * nthreads + tid].
+// Reverse pass, one launch per segment from the last to the first: each
+// particle alive at the segment's start (in spatial order of its checkpoint)
+// loads its adjoints, replays the segment into the thread's scratch
+// (scratch[(kk * 5 + c) * threads + tid]) and walks it backwards.  The launch
+// of the first segment adds the injection-index term and reduces the gradients.
 // ---------------------------------------------------------------------------
 template <int DT>
 __global__ void __launch_bounds__(256) adj_reverse_kernel(const AdvanceArgs a, const AdjK k)
@@ -433,58 +435,69 @@ __global__ void __launch_bounds__(256) adj_reverse_kernel(const AdvanceArgs a, c
     const double In = __ldg(a.norm);
     const float I = (float)In;
     const float rq = (float)(__ldg(k.normd) / In), rh = (float)(__ldg(k.normd + 1) / In);
+    const unsigned long long n_work = a.order ? (unsigned long long)__ldg(a.n_order) : a.n_particles;
+    const size_t n = a.n_particles;
+    const float* c = k.ckpt + (size_t)k.seg * 5 * n;
+    const long long seg0 = (long long)k.seg * k.K;          // steps before this segment
     double gsum[FTE_NGRAD];
 #pragma unroll
     for (int q = 0; q < FTE_NGRAD; ++q) gsum[q] = 0.0;
     unsigned long long noor = 0;
-    for (unsigned long long i = tid; i < a.n_particles; i += nthr) {
-        const long long nd = k.n_dead[i];     // alive steps of this particle
-        float gth[4] = {0.f, 0.f, 0.f, 0.f};
-        float lam[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    for (;;) {
+        const unsigned long long f = atomicAdd(a.fetch, 1ULL);
+        if (f >= n_work) break;
+        const unsigned long long i = a.order ? (unsigned long long)__ldg(a.order + f) : f;
+        const long long nd = k.n_dead[i];
+        if (nd <= seg0) continue;                            // not alive at this segment's start
+        float lam[5], gth[4];
+#pragma unroll
+        for (int q = 0; q < 5; ++q) lam[q] = k.adj[q * n + i];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) gth[q] = k.adj[(5 + q) * n + i];
         const float w = a.w[i];
         const uint32_t pid = a.id[i];
-        const long long nseg = (nd + k.K - 1) / k.K;
-        for (long long seg = nseg - 1; seg >= 0; --seg) {
-            const float* c = k.ckpt + (size_t)seg * 5 * a.n_particles;
-            float x = c[i], y = c[a.n_particles + i], z = c[2 * a.n_particles + i];
-            float mu = c[3 * a.n_particles + i], p = c[4 * a.n_particles + i];
-            const long long n0 = a.n_start + seg * k.K;
-            const long long n1 = min(n0 + (long long)k.K, a.n_start + nd);
-            for (long long n = n0; n < n1; ++n) {
-                float* sp = k.scratch + ((size_t)(n - n0) * 5) * nthr + tid;
-                sp[0] = x; sp[nthr] = y; sp[2 * nthr] = z; sp[3 * nthr] = mu; sp[4 * nthr] = p;
-                if (n + 1 < n1)
-                    step<false, DT, kModeSingle>(a, a.prm, I, 0, n, pid, x, y, z, mu, p, w, nullptr, nullptr,
-                                                 nullptr, sc, noor);
-            }
-            for (long long n = n1 - 1; n >= n0; --n) {
-                const float* sp = k.scratch + ((size_t)(n - n0) * 5) * nthr + tid;
-                const float sx = sp[0], sy = sp[nthr], sz = sp[2 * nthr], smu = sp[3 * nthr], spp = sp[4 * nthr];
-                step_vjp<DT>(a, I, rq, rh, n, pid, sx, sy, sz, smu, spp, sc, lam, gth);
-                // the observable's own term at the start-of-step state
-                const float r = sqrtf(sx * sx + sy * sy + sz * sz);
-                float dKdr, dKdp;
-                smooth_k(k, r, spp, k.t0 + (double)n * k.dt, &dKdr, &dKdp);
-                const float f = w * a.prm.dt;
-                lam[0] += f * dKdr * sx / r;
-                lam[1] += f * dKdr * sy / r;
-                lam[2] += f * dKdr * sz / r;
-                lam[4] += f * dKdp;
-            }
+        float x = c[i], y = c[n + i], z = c[2 * n + i], mu = c[3 * n + i], p = c[4 * n + i];
+        const long long n0 = a.n_table0 + seg0;
+        const long long n1 = min(n0 + (long long)k.K, a.n_table0 + nd);
+        for (long long s = n0; s < n1; ++s) {
+            float* sp = k.scratch + ((size_t)(s - n0) * 5) * nthr + tid;
+            sp[0] = x; sp[nthr] = y; sp[2 * nthr] = z; sp[3 * nthr] = mu; sp[4 * nthr] = p;
+            if (s + 1 < n1)
+                step<false, DT, kModeSingle>(a, a.prm, I, 0, s, pid, x, y, z, mu, p, w, nullptr, nullptr, nullptr,
+                                             sc, noor);
         }
-        // injection index: likelihood-ratio weight of the injected energy
+        for (long long s = n1 - 1; s >= n0; --s) {
+            const float* sp = k.scratch + ((size_t)(s - n0) * 5) * nthr + tid;
+            const float sx = sp[0], sy = sp[nthr], sz = sp[2 * nthr], smu = sp[3 * nthr], spp = sp[4 * nthr];
+            step_vjp<DT>(a, I, rq, rh, s, pid, sx, sy, sz, smu, spp, sc, lam, gth);
+            // the observable's own term at the start-of-step state
+            const float r = sqrtf(sx * sx + sy * sy + sz * sz);
+            float dKdr, dKdp;
+            smooth_k(k, r, spp, k.t0 + (double)s * k.dt, &dKdr, &dKdp);
+            const float fw = w * a.prm.dt;
+            lam[0] += fw * dKdr * sx / r;
+            lam[1] += fw * dKdr * sy / r;
+            lam[2] += fw * dKdr * sz / r;
+            lam[4] += fw * dKdp;
+        }
+        if (!k.last) {
+#pragma unroll
+            for (int q = 0; q < 5; ++q) k.adj[q * n + i] = lam[q];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) k.adj[(5 + q) * n + i] = gth[q];
+            continue;
+        }
+        // first segment: injection index by the likelihood ratio of the injected energy
         float gg = 0.f;
-        if (k.score_on && nd > 0) {
-            const float p0 = k.ckpt[4 * a.n_particles + i];
-            gg = (float)(-(log((double)energy_of(p0)) - k.mean_lnE) * k.J_part[i]);
-        }
+        if (k.score_on) gg = (float)(-(log((double)energy_of(c[4 * n + i])) - k.mean_lnE) * k.J_part[i]);
         if (k.per_particle) {
-            float* o = k.per_particle + (size_t)i * (1 + FTE_NGRAD);
+            float* o = k.per_particle + i * (1 + FTE_NGRAD);
             o[0] = (float)k.J_part[i];
             o[1] = gth[0]; o[2] = gth[1]; o[3] = gth[2]; o[4] = gth[3]; o[5] = gg;
         }
         gsum[0] += gth[0]; gsum[1] += gth[1]; gsum[2] += gth[2]; gsum[3] += gth[3]; gsum[4] += gg;
     }
+    if (!k.last) return;
 #pragma unroll
     for (int q = 0; q < FTE_NGRAD; ++q) {
         double v = gsum[q];
@@ -494,9 +507,9 @@ __global__ void __launch_bounds__(256) adj_reverse_kernel(const AdvanceArgs a, c
     }
     __syncthreads();
     if (threadIdx.x < FTE_NGRAD) {
-        double s = 0.0;
-        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) s += red[q][threadIdx.x];
-        atomicAdd(k.out + 1 + threadIdx.x, s);
+        double t = 0.0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[q][threadIdx.x];
+        atomicAdd(k.out + 1 + threadIdx.x, t);
     }
 }
 

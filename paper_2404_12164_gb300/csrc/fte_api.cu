@@ -1204,20 +1204,22 @@ fte_status fte_graph_destroy(fte_graph* g)
 namespace {
 
 struct AdjLayout {
-    size_t off_norm, off_npart, off_normd, off_ndpart, off_table, off_ckpt, off_ndead, off_jpart, off_scratch, total;
+    size_t off_fetch, off_norm, off_npart, off_normd, off_ndpart, off_table, off_ckpt, off_ndead, off_jpart,
+        off_adj, off_scratch, off_sort, total;
     int fwd_blocks, rev_blocks;
     long long nseg;
 };
 
-fte_status adj_layout(int device, int dtype, unsigned long long n, long long n_steps, int K, AdjLayout* L)
+fte_status adj_layout(int device, const fte_grid* g, unsigned long long n, long long n_steps, int K, bool sorting,
+                      AdjLayout* L)
 {
     const int sms = device_sms(device);
     if (sms <= 0) return fail(FTE_ECUDA, "cannot query device %d", device);
     int pf = 0, pr = 0, cur = 0;
     FTE_CUDA(cudaGetDevice(&cur), "cudaGetDevice");
     if (cur != device) FTE_CUDA(cudaSetDevice(device), "cudaSetDevice");
-    cudaError_t e = adjoint_blocks(dtype, 0, &pf);
-    if (e == cudaSuccess) e = adjoint_blocks(dtype, 1, &pr);
+    cudaError_t e = adjoint_blocks(g->dtype, 0, &pf);
+    if (e == cudaSuccess) e = adjoint_blocks(g->dtype, 1, &pr);
     if (cur != device) cudaSetDevice(cur);
     if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
     if (pf < 1 || pr < 1) return fail(FTE_ENOTSUP, "adjoint kernels do not fit on an SM");
@@ -1225,17 +1227,24 @@ fte_status adj_layout(int device, int dtype, unsigned long long n, long long n_s
     L->rev_blocks = sms * pr;
     L->nseg = n_steps > 0 ? (n_steps + K - 1) / K : 1;
     const unsigned long long nthr = (unsigned long long)L->rev_blocks * 256;
+    const size_t nn = n ? n : 1;
     size_t off = 0;
     auto take = [&](size_t bytes) { const size_t o = off; off = (off + bytes + 255) & ~(size_t)255; return o; };
+    L->off_fetch = take(64);
     L->off_norm = take(64);
     L->off_npart = take(kNormPartials * sizeof(double));
     L->off_normd = take(64);
     L->off_ndpart = take(256 * sizeof(double));
     L->off_table = take((size_t)(n_steps > 0 ? n_steps : 1) * sizeof(StepEntry));
-    L->off_ckpt = take((size_t)L->nseg * 5 * (n ? n : 1) * sizeof(float));
-    L->off_ndead = take((size_t)(n ? n : 1) * sizeof(int));
-    L->off_jpart = take((size_t)(n ? n : 1) * sizeof(double));
+    L->off_ckpt = take((size_t)L->nseg * 5 * nn * sizeof(float));
+    L->off_ndead = take(nn * sizeof(int));
+    L->off_jpart = take(nn * sizeof(double));
+    L->off_adj = take(9 * nn * sizeof(float));
     L->off_scratch = take((size_t)K * 5 * nthr * sizeof(float));
+    fte_background tmp;
+    memset(&tmp, 0, sizeof(tmp));
+    tmp.grid = *g;
+    L->off_sort = take(sorting ? sort_scratch_bytes(make_gridk(&tmp), nn) : 0);
     L->total = off;
     return FTE_OK;
 }
@@ -1257,6 +1266,7 @@ fte_status adj_check(const fte_particles* P, const fte_background* bg, const fte
         return fail(FTE_EINVAL, "observable widths and e_c must be > 0");
     if (K < 1 || K > 65536) return fail(FTE_EINVAL, "checkpoint_every must be in [1, 65536]");
     if (n_end < n_start || n_start < 0) return fail(FTE_EINVAL, "need 0 <= n_start <= n_end");
+    if (n_end - n_start > 0x7FFFFFFFll) return fail(FTE_EINVAL, "more than 2^31 - 1 steps");
     if (n_end > 0xFFFFFFFFll) return fail(FTE_EINVAL, "step index exceeds 32 bits");
     if (!ws) return fail(FTE_EINVAL, "NULL workspace");
     if (!P->x || !P->y || !P->z || !P->mu || !P->p || !P->w || !P->id || !P->status)
@@ -1264,7 +1274,7 @@ fte_status adj_check(const fte_particles* P, const fte_background* bg, const fte
     return FTE_OK;
 }
 
-// Kernel arguments shared by both passes; fills the time table and the
+// Kernel arguments shared by both passes; launches the time table and the
 // normalisation integrals when `setup` is set.
 fte_status adj_args(const fte_particles* P, const fte_background* bg, const fte_params* prm,
                     const fte_smooth_obs* obs, int64_t n_start, int64_t n_end, int K, char* w, const AdjLayout& L,
@@ -1300,10 +1310,12 @@ fte_status adj_args(const fte_particles* P, const fte_background* bg, const fte_
     a->table = ta.tab;
     a->norm = norm;
     a->nbins = 1;
+    a->fetch = (unsigned long long*)(w + L.off_fetch);
     memset(k, 0, sizeof(*k));
     k->K = K;
     k->ckpt = (float*)(w + L.off_ckpt);
     k->scratch = (float*)(w + L.off_scratch);
+    k->adj = (float*)(w + L.off_adj);
     k->n_dead = (int*)(w + L.off_ndead);
     k->J_part = (double*)(w + L.off_jpart);
     k->out = dev_out;
@@ -1334,7 +1346,7 @@ size_t fte_adjoint_workspace_bytes(int device, const fte_grid* g, uint64_t n_par
 {
     if (check_grid(g) != FTE_OK || n_steps < 0 || checkpoint_every < 1) return 0;
     AdjLayout L;
-    if (adj_layout(device, g->dtype, n_particles, n_steps, checkpoint_every, &L) != FTE_OK) return 0;
+    if (adj_layout(device, g, n_particles, n_steps, checkpoint_every, true, &L) != FTE_OK) return 0;
     return L.total;
 }
 
@@ -1347,18 +1359,38 @@ fte_status fte_adjoint_forward(fte_particles* P, const fte_background* bg, const
     if (!dev_out) return fail(FTE_EINVAL, "NULL output");
     int device = 0;
     FTE_CUDA(cudaGetDevice(&device), "cudaGetDevice");
+    const bool sorting = prm->sort_every > 0;
     AdjLayout L;
-    s = adj_layout(device, bg->grid.dtype, P->count, n_end - n_start, checkpoint_every, &L);
+    s = adj_layout(device, &bg->grid, P->count, n_end - n_start, checkpoint_every, sorting, &L);
     if (s != FTE_OK) return s;
     if (ws_bytes < L.total) return fail(FTE_ENOMEM, "workspace has %zu bytes, needs %zu", ws_bytes, L.total);
     cudaStream_t st = (cudaStream_t)stream;
     FTE_CUDA(cudaMemsetAsync(dev_out, 0, (1 + FTE_NGRAD) * sizeof(double), st), "output reset");
     if (P->count == 0) return FTE_OK;
+    char* w = (char*)ws;
     AdvanceArgs a;
     AdjK k;
-    s = adj_args(P, bg, prm, obs, n_start, n_end, checkpoint_every, (char*)ws, L, dev_out, true, st, &a, &k);
+    s = adj_args(P, bg, prm, obs, n_start, n_end, checkpoint_every, w, L, dev_out, true, st, &a, &k);
     if (s != FTE_OK) return s;
-    FTE_CUDA(launch_adjoint_forward(a, k, L.fwd_blocks, st), "adjoint forward launch");
+    FTE_CUDA(cudaMemsetAsync(k.n_dead, 0, P->count * sizeof(int), st), "step count reset");
+    FTE_CUDA(cudaMemsetAsync(k.J_part, 0, P->count * sizeof(double), st), "observable reset");
+    SortArgs sa;
+    memset(&sa, 0, sizeof(sa));
+    if (sorting) {
+        sort_carve(a.g, P->count, w + L.off_sort, &sa);
+        sa.g = a.g;
+        sa.x = P->x; sa.y = P->y; sa.z = P->z; sa.status = P->status; sa.n = P->count;
+        a.order = sa.order;
+        a.n_order = sa.hist + sa.nb;
+    }
+    for (long long seg = 0; seg < L.nseg && n_end > n_start; ++seg) {
+        k.seg = (int)seg;
+        a.n_start = n_start + seg * checkpoint_every;
+        a.n_end = a.n_start + checkpoint_every < n_end ? a.n_start + checkpoint_every : n_end;
+        if (sorting) FTE_CUDA(launch_sort(sa, st), "sort launch");
+        FTE_CUDA(cudaMemsetAsync(a.fetch, 0, sizeof(unsigned long long), st), "fetch reset");
+        FTE_CUDA(launch_adjoint_forward(a, k, L.fwd_blocks, st), "adjoint forward launch");
+    }
     return FTE_OK;
 }
 
@@ -1374,23 +1406,51 @@ fte_status fte_adjoint_reverse(const fte_particles* P, const fte_background* bg,
         return fail(FTE_EINVAL, "need 0 < e1 < e2");
     int device = 0;
     FTE_CUDA(cudaGetDevice(&device), "cudaGetDevice");
+    const bool sorting = prm->sort_every > 0;
     AdjLayout L;
-    s = adj_layout(device, bg->grid.dtype, P->count, n_end - n_start, checkpoint_every, &L);
+    s = adj_layout(device, &bg->grid, P->count, n_end - n_start, checkpoint_every, sorting, &L);
     if (s != FTE_OK) return s;
     if (ws_bytes < L.total) return fail(FTE_ENOMEM, "workspace has %zu bytes, needs %zu", ws_bytes, L.total);
     cudaStream_t st = (cudaStream_t)stream;
     FTE_CUDA(cudaMemsetAsync(dev_out + 1, 0, FTE_NGRAD * sizeof(double), st), "output reset");
     if (P->count == 0) return FTE_OK;
+    char* w = (char*)ws;
     AdvanceArgs a;
     AdjK k;
-    s = adj_args(P, bg, prm, obs, n_start, n_end, checkpoint_every, (char*)ws, L, dev_out, false, st, &a, &k);
+    s = adj_args(P, bg, prm, obs, n_start, n_end, checkpoint_every, w, L, dev_out, false, st, &a, &k);
     if (s != FTE_OK) return s;
     k.per_particle = dev_per_particle;
     if (spec && spec->energy == 1) {
         k.score_on = 1;
         k.mean_lnE = mean_ln_energy(spec->e1, spec->e2, spec->gamma);
     }
-    FTE_CUDA(launch_adjoint_reverse(a, k, L.rev_blocks, st), "adjoint reverse launch");
+    if (dev_per_particle)
+        FTE_CUDA(cudaMemsetAsync(dev_per_particle, 0, P->count * (1 + FTE_NGRAD) * sizeof(float), st),
+                 "per-particle reset");
+    FTE_CUDA(cudaMemsetAsync(k.adj, 0, 9 * P->count * sizeof(float), st), "adjoint reset");
+    const size_t n = P->count;
+    SortArgs sa;
+    memset(&sa, 0, sizeof(sa));
+    if (sorting) {
+        sort_carve(a.g, n, w + L.off_sort, &sa);
+        sa.g = a.g;
+        sa.steps = k.n_dead;
+        sa.n = n;
+        a.order = sa.order;
+        a.n_order = sa.hist + sa.nb;
+    }
+    for (long long seg = L.nseg - 1; seg >= 0; --seg) {
+        k.seg = (int)seg;
+        k.last = seg == 0;
+        if (sorting) {
+            const float* c = k.ckpt + (size_t)seg * 5 * n;
+            sa.x = c; sa.y = c + n; sa.z = c + 2 * n;
+            sa.steps_min = seg * (long long)checkpoint_every;
+            FTE_CUDA(launch_sort(sa, st), "sort launch");
+        }
+        FTE_CUDA(cudaMemsetAsync(a.fetch, 0, sizeof(unsigned long long), st), "fetch reset");
+        FTE_CUDA(launch_adjoint_reverse(a, k, L.rev_blocks, st), "adjoint reverse launch");
+    }
     return FTE_OK;
 }
 

@@ -50,7 +50,9 @@ struct AdvanceArgs {
 struct SortArgs {
     GridK g;
     const float *x, *y, *z;
-    const uint8_t* status;
+    const uint8_t* status;        // entries with status FTE_ALIVE are ordered ...
+    const int* steps;             // ... or, when set, entries with steps[i] > steps_min
+    long long steps_min;
     unsigned long long n;
     unsigned* hist;               // bucket counts, then exclusive offsets; total at hist[nb]
     unsigned* tiles;
@@ -105,8 +107,11 @@ struct NormSets {
 struct AdjK {
     int K;                        // steps between checkpoints
     int score_on;                 // injection-index gradient by the likelihood ratio
+    int seg;                      // segment of this launch: steps n_start + seg K ..
+    int last;                     // reverse: 1 for the first segment of the run (seg 0)
     float* ckpt;                  // [segment][5][n]: x, y, z, mu, p at n_start + segment K
     float* scratch;               // [K][5][threads]: replayed start-of-step states
+    float* adj;                   // [9][n]: state adjoint (5) and parameter adjoint (4) between segments
     int* n_dead;                  // [n]: steps each particle took (alive at their start)
     double* J_part;               // [n]: each particle's observable
     double* out;                  // [1 + FTE_NGRAD]: J, then the gradients

@@ -36,7 +36,7 @@ __global__ void __launch_bounds__(256) key_kernel(const SortArgs a)
     const unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.n) return;
     int key = -1, rank = 0;
-    if (a.status[i] == FTE_ALIVE) {
+    if (a.steps ? a.steps[i] > a.steps_min : a.status[i] == FTE_ALIVE) {
         key = bucket_of(a.g, a.x[i], a.y[i], a.z[i]);
         rank = (int)atomicAdd(a.hist + key, 1u);
     }

@@ -145,6 +145,19 @@ def test_checkpoint_interval_changes_nothing(cir_small, model):
         assert np.allclose(gx, g, rtol=1e-5, atol=1e-9 * np.abs(g).max())
 
 
+def test_spatial_ordering_changes_nothing(cir_small):
+    """Each launch may take the particles in spatial order; every particle's J_i and
+    gradients are the same."""
+    w, f = cir_small
+    prm = MODELS[0][1]
+    _, g0, pp0, s0 = _gpu(w, f, prm, 5000, 300, K=32)
+    _, g1, pp1, s1 = _gpu(w, f, dataclasses.replace(prm, sort_every=32), 5000, 300, K=32)
+    assert np.array_equal(pp0, pp1)
+    for key in ("x", "y", "z", "mu", "p", "status"):
+        assert np.array_equal(s0[key], s1[key]), key
+    assert np.allclose(g0, g1, rtol=1e-9, atol=0)
+
+
 def test_total_matches_gpu_finite_differences(cir_small):
     """Sum over many particles against central differences of the GPU forward pass with
     common random numbers, for the isotropic D_mumu, whose coefficients are smooth in mu.
