@@ -18,6 +18,14 @@ ids, weak scaling) and the tallies are summed over ranks after each step.
 
 `--impl reference` times the FP64 CPU oracle on the host cores on a bounded
 sample of the same workload.
+
+The default line also carries the 16-bit storage forms (`forms`) and the
+adjoint's cost on a slice of the workload (`adjoint`).  Other cases, each one
+JSON line: `--case amr` (the CIR on a 39,520-leaf block-AMR grid, 1e7 protons,
+FP32/BF16/FP16), `--case ensemble` (64 parameter sets, 2e7 protons: set after
+set, one ensemble launch, autotuned and graph-captured), `--case adjoint` (the
+full 4-day adjoint with a finite-difference check), `--case profile` (small
+cases for ncu captures).
 """
 import argparse
 import dataclasses
@@ -133,6 +141,7 @@ def run_gpu(args):
     import torch.distributed as dist
     from paper_2404_12164_gb300 import api, build
     from paper_2404_12164_gb300 import _abi as A
+    from paper_2404_12164_gb300 import dist as pdist
 
     ws, rank, local = _dist()
     torch.cuda.set_device(local)
@@ -150,7 +159,7 @@ def run_gpu(args):
     tally = api.Tally(w.observers)
     wsp = api.Workspace()
     wsp.ensure(api.fte_workspace_bytes(bg, tally, n_part, CHUNK))
-    id_base = rank * n_part
+    id_base = pdist.id_base(rank, n_part)
 
     def barrier():
         if ws > 1:
@@ -172,9 +181,7 @@ def run_gpu(args):
             if timed_launches is not None:
                 ev1.record(stream)
                 timed_launches.append((ev0, ev1))
-        if ws > 1:
-            for t_ in (tally.S, tally.S2, tally.C, tally.ledger_n):
-                dist.all_reduce(t_)
+        pdist.reduce_tally(tally)
 
     # device-resident arm ------------------------------------------------------
     api.fte_load_background(bg, host)
@@ -205,10 +212,8 @@ def run_gpu(args):
         bg = saved
         ms = t0.elapsed_time(t1)
         k_ms = sum(a_.elapsed_time(b_) for a_, b_ in launches)
-        ms_t = torch.tensor([ms, k_ms], dtype=torch.float64, device="cuda")
-        if ws > 1:
-            dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-        return ms_t[0].item(), ms_t[1].item(), len(launches), done
+        ms, k_ms = pdist.max_over_ranks([ms, k_ms], device="cuda")
+        return ms, k_ms, len(launches), done
 
     clocks = Clocks(local)
     ms, k_ms, n_launch, steps_total = measure(bg, args.steps, args.warmup, clocks)
@@ -242,10 +247,8 @@ def run_gpu(args):
         e_steps += int(ln[6]) // (ws if ws > 1 else 1)
     barrier()
     e_s = time.perf_counter() - e0
-    e_t = torch.tensor([e_s], dtype=torch.float64, device="cuda")
-    if ws > 1:
-        dist.all_reduce(e_t, op=dist.ReduceOp.MAX)
-    e2e_value = e_steps * ws / e_t.item()
+    (e_s,) = pdist.max_over_ranks([e_s], device="cuda")
+    e2e_value = e_steps * ws / e_s
 
     # reduced-precision storage forms (same workload, background quantized on the device)
     peak, peak_kind = _peaks()
@@ -266,6 +269,12 @@ def run_gpu(args):
                          "background_bytes": int(bh.nbytes)}
             del bh
             torch.cuda.empty_cache()
+
+    adjoint = None
+    if not args.no_adjoint:
+        adjoint = adjoint_times(api, bg, w, n_part, args.adj_slice, args.checkpoint_every, args.sort_every)
+        adjoint["note"] = ("first %d steps of the workload, E^-3 injection over 50 keV-5 MeV; bench.py --case "
+                           "adjoint runs the full 4 days" % args.adj_slice)
 
     achieved = total_steps / ws * ALG_BYTES / (k_ms / 1e3) / 1e9
     l2_gbs = l2_probe()
@@ -298,6 +307,7 @@ def run_gpu(args):
                      "l2_random_sector_gbs": l2_gbs, "frac_of_l2": achieved / l2_gbs},
         "clocks": cl,
         "forms": forms,
+        "adjoint": adjoint,
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(w, fields, budget_s=args.cpu_budget)
@@ -622,29 +632,21 @@ def run_ensemble_case(args):
     }), flush=True)
 
 
-def run_adjoint_case(args):
-    """Adjoint workload: the cir_uniform_1e6 background and transport, 1e6 protons with an E^-3
-    spectrum over 50 keV - 5 MeV, gradients of the smoothed 1 au intensity (E_c = 100 keV,
-    sigma_lnE = 0.1, t_c = 2 d, sigma_t = 1 h, sigma_r = 0.02 au) with respect to lambda_par, q, H
-    and the injection index; checkpoints every 256 steps.  Reports the forward rate of the plain
-    step kernel, the adjoint's forward + reverse time, their ratio, and a central-difference check
-    of dJ/dlambda_par with common random numbers."""
+ADJ_OBS = dict(r_o=1.0, sigma_r=0.02, e_c=0.1, sigma_lnE=0.1, t_c=2 * 86400.0, sigma_t=3600.0)
+
+
+def adjoint_times(api, bg, w, n_part, n_steps, K, sort_every, reps=1, fd=False):
+    """Times of the plain step kernel, of the adjoint's forward pass and of forward + reverse on
+    the same particles (1e6-style power-law injection of the CIR workload); optionally the
+    central difference of dJ/dlambda_par with common random numbers."""
     import torch
-    from paper_2404_12164_gb300 import api, build
-    build.build()
-    torch.cuda.set_device(0)
-    w, fields = build_workload()
-    n_part, n_steps = args.adj_particles, args.adj_steps
     inj = dataclasses.replace(w.inject, energy="powerlaw", e1=0.05, e2=5.0, gamma=3.0)
-    obs = configs.SmoothObserver(r_o=1.0, sigma_r=0.02, e_c=0.1, sigma_lnE=0.1, t_c=2 * 86400.0, sigma_t=3600.0)
-    prm = dataclasses.replace(w.params, sort_every=args.sort_every)
-    bg = api.Background(w.grid)
-    api.fte_load_background(bg, torch.from_numpy(np.ascontiguousarray(fields)))
-    del fields
+    obs = configs.SmoothObserver(**ADJ_OBS)
+    prm = dataclasses.replace(w.params, sort_every=sort_every)
     pool = api.Particles(n_part)
     tally = api.Tally(w.observers)
     ws = api.Workspace()
-    adj = api.Adjoint(bg, prm, obs, 0, n_steps, args.checkpoint_every)
+    adj = api.Adjoint(bg, prm, obs, 0, n_steps, K)
     stream = torch.cuda.current_stream()
 
     def inject():
@@ -652,7 +654,7 @@ def run_adjoint_case(args):
         api.fte_tally_reset(tally)
         api.fte_inject(pool, bg, inj, n_part, tally, id_base=0, check_failed=False)
 
-    def timed(fn, reps):
+    def timed(fn):
         fn()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -668,7 +670,7 @@ def run_adjoint_case(args):
         for c in range(0, n_steps, CHUNK):
             api.fte_advance(pool, bg, prm, tally, c, min(c + CHUNK, n_steps), ws)
 
-    t_plain = timed(plain, args.steps)
+    t_plain = timed(plain)
     alive_steps = int(tally.ledger_n.cpu().numpy()[6])
 
     def fwd():
@@ -679,31 +681,55 @@ def run_adjoint_case(args):
         fwd()
         adj.reverse(pool, inj)
 
-    t_fwd = timed(fwd, args.steps)
-    t_adj = timed(fwd_rev, args.steps)
-    J = float(adj.out[0])
-    grads = adj.out[1:].cpu().numpy()
-    # central difference of dJ/dlambda_par with the same particles and noise
-    h = 1e-3 * prm.lambda_par
-    Js = []
-    for lam in (prm.lambda_par + h, prm.lambda_par - h):
-        a2 = api.Adjoint(bg, dataclasses.replace(prm, lambda_par=lam), obs, 0, n_steps, args.checkpoint_every, ws=adj.ws)
-        inject()
-        Js.append(float(a2.forward(pool)))
-    fd = (Js[0] - Js[1]) / (2 * h)
+    t_fwd = timed(fwd)
+    t_adj = timed(fwd_rev)
+    out = {"particles": n_part, "steps": n_steps, "checkpoint_every": K, "alive_particle_steps": alive_steps,
+           "plain_s": t_plain, "adjoint_forward_s": t_fwd, "adjoint_forward_reverse_s": t_adj,
+           "adj_over_fwd": t_adj / t_plain, "J": float(adj.out[0]),
+           "grad": dict(zip(api.GRAD_NAMES, adj.out[1:].cpu().numpy().tolist()))}
+    if fd:
+        h = 1e-3 * prm.lambda_par
+        Js = []
+        for lam in (prm.lambda_par + h, prm.lambda_par - h):
+            a2 = api.Adjoint(bg, dataclasses.replace(prm, lambda_par=lam), obs, 0, n_steps, K, ws=adj.ws)
+            inject()
+            Js.append(float(a2.forward(pool)))
+        d = (Js[0] - Js[1]) / (2 * h)
+        g0 = out["grad"]["lambda_par"]
+        out["fd_check"] = {"d_lambda_par_central_difference": d, "adjoint": g0,
+                           "rel_diff": abs(d - g0) / abs(d) if d else None}
+    return out
+
+
+def run_adjoint_case(args):
+    """Adjoint workload: the cir_uniform_1e6 background and transport, 1e6 protons with an E^-3
+    spectrum over 50 keV - 5 MeV, gradients of the smoothed 1 au intensity (E_c = 100 keV,
+    sigma_lnE = 0.1, t_c = 2 d, sigma_t = 1 h, sigma_r = 0.02 au) with respect to lambda_par, q, H
+    and the injection index; checkpoints every 256 steps.  Reports the plain step kernel's time,
+    the adjoint's forward + reverse time, their ratio, and a central-difference check of
+    dJ/dlambda_par with common random numbers."""
+    import torch
+    from paper_2404_12164_gb300 import api, build
+    build.build()
+    torch.cuda.set_device(0)
+    w, fields = build_workload()
+    bg = api.Background(w.grid)
+    api.fte_load_background(bg, torch.from_numpy(np.ascontiguousarray(fields)))
+    del fields
+    res = adjoint_times(api, bg, w, args.adj_particles, args.adj_steps, args.checkpoint_every, args.sort_every,
+                        reps=args.steps, fd=True)
     print(json.dumps({
         "case": "adjoint", "metric": METRIC, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": f"cir_uniform_1e6 background and transport, {n_part:.0e} protons E^-3 over 50 keV-5 MeV, "
-                               f"dt=10 s x {n_steps}, smoothed 1 au intensity (E_c 100 keV, sigma_lnE 0.1, "
-                               "t_c 2 d, sigma_t 1 h, sigma_r 0.02 au)", "checkpoint_every": args.checkpoint_every},
-        "forward_plain_kernel": {"value": alive_steps / t_plain, "s": t_plain},
-        "adjoint_forward_pass": {"value": alive_steps / t_fwd, "s": t_fwd},
-        "adjoint_forward_plus_reverse": {"value": alive_steps / t_adj, "s": t_adj},
-        "adj_over_fwd": t_adj / t_plain,
-        "J": J, "grad": dict(zip(api.GRAD_NAMES, grads.tolist())),
-        "fd_check": {"d_lambda_par_central_difference": fd, "adjoint": float(grads[0]),
-                     "rel_diff": abs(fd - grads[0]) / abs(fd) if fd else None},
+        "config": {"workload": f"cir_uniform_1e6 background and transport, {args.adj_particles:.0e} protons E^-3 "
+                               f"over 50 keV-5 MeV, dt=10 s x {args.adj_steps}, smoothed 1 au intensity (E_c 100 keV, "
+                               "sigma_lnE 0.1, t_c 2 d, sigma_t 1 h, sigma_r 0.02 au)"},
+        "forward_plain_kernel": {"value": res["alive_particle_steps"] / res["plain_s"], "s": res["plain_s"]},
+        "adjoint_forward_pass": {"value": res["alive_particle_steps"] / res["adjoint_forward_s"],
+                                 "s": res["adjoint_forward_s"]},
+        "adjoint_forward_plus_reverse": {"value": res["alive_particle_steps"] / res["adjoint_forward_reverse_s"],
+                                         "s": res["adjoint_forward_reverse_s"]},
+        "adj_over_fwd": res["adj_over_fwd"], "J": res["J"], "grad": res["grad"], "fd_check": res["fd_check"],
     }), flush=True)
 
 
@@ -745,6 +771,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--adj-slice", type=int, default=4096, help="steps of the adjoint measurement in the default run")
     ap.add_argument("--sort-every", type=int, default=64,
                     help="steps between spatial reorderings of the alive particles (0: off)")
     args = ap.parse_args()
