@@ -1,6 +1,6 @@
 """Build the CUDA library libfte_gb300.so in-tree with nvcc for sm_103a.
 
-The three translation units are compiled in parallel and linked into one
+The translation units are compiled in parallel and linked into one
 shared library next to this file.  Rebuilds only when a source or header is
 newer than the library.
 """
