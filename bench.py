@@ -735,6 +735,75 @@ def run_adjoint_case(args):
     }), flush=True)
 
 
+def run_stream_case(args):
+    """The cir_uniform_1e6 workload with only `--ring` snapshot slots on the device: the 24 hourly
+    snapshots stay in page-locked host memory and are copied into their slots as the 4 days
+    advance (each copy overlapped with the previous interval's steps).  Reports the streamed and
+    the fully resident rates on the same particles."""
+    import torch
+    from paper_2404_12164_gb300 import api, build
+    build.build()
+    torch.cuda.set_device(0)
+    w, fields = build_workload()
+    w.params.sort_every = args.sort_every
+    host = torch.from_numpy(np.ascontiguousarray(fields)).pin_memory()
+    n_part, n_steps = w.n_particles, w.n_steps
+    pool = api.Particles(n_part)
+    tally = api.Tally(w.observers)
+    ws = api.Workspace()
+    stream = torch.cuda.current_stream()
+
+    def timed(step, reps, warmup):
+        for _ in range(warmup):
+            step()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        done = 0
+        for _ in range(reps):
+            step()
+            done += int(tally.ledger_n.cpu().numpy()[6])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return done / (e0.elapsed_time(e1) / 1e3), e0.elapsed_time(e1) / reps
+
+    ring_bg = api.Background(w.grid, ring=args.ring)
+    st = api.SnapshotStream(ring_bg, host)
+
+    def streamed():
+        pool.c.count = 0
+        api.fte_tally_reset(tally)
+        st.load(0)                     # the injection reads snapshot 0 (slot 0)
+        api.fte_inject(pool, ring_bg, w.inject, n_part, tally, check_failed=False)
+        api.fte_advance_streamed(pool, ring_bg, st, w.params, tally, 0, n_steps, ws)
+
+    v_str, ms_str = timed(streamed, args.steps, 1)
+    res_bg = api.Background(w.grid)
+    api.fte_load_background(res_bg, host)
+
+    def resident():
+        pool.c.count = 0
+        api.fte_tally_reset(tally)
+        api.fte_inject(pool, res_bg, w.inject, n_part, tally, check_failed=False)
+        for c in range(0, n_steps, CHUNK):
+            api.fte_advance(pool, res_bg, w.params, tally, c, min(c + CHUNK, n_steps), ws)
+
+    v_res, ms_res = timed(resident, args.steps, 1)
+    plan = api.fte_stream_plan(ring_bg, w.params, 0, n_steps)
+    uploads = len(plan) + 1
+    print(json.dumps({
+        "case": "stream", "metric": METRIC, "value": v_str, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "ms_per_step": ms_str, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "cir_uniform_1e6 with %d resident snapshot slots (24 hourly snapshots in "
+                               "page-locked host memory)" % args.ring,
+                   "device_background_bytes": int(ring_bg.nbytes), "resident_background_bytes": int(res_bg.nbytes),
+                   "snapshot_uploads_per_step": uploads,
+                   "h2d_bytes_per_step": int(uploads * api.fte_snapshot_bytes(ring_bg))},
+        "resident": {"value": v_res, "ms_per_step": ms_res},
+        "streamed_over_resident": v_str / v_res,
+    }), flush=True)
+
+
 def l2_probe(mib=64, threads=152 * 2048, loads=256, reps=5):
     """Random 32-byte sector read bandwidth of an L2-resident buffer (GB/s), best of reps."""
     import torch
@@ -756,7 +825,8 @@ def l2_probe(mib=64, threads=152 * 2048, loads=256, reps=5):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--case", default="bench", choices=["bench", "profile", "amr", "ensemble", "adjoint"])
+    ap.add_argument("--case", default="bench", choices=["bench", "profile", "amr", "ensemble", "adjoint", "stream"])
+    ap.add_argument("--ring", type=int, default=3, help="resident snapshot slots of --case stream")
     ap.add_argument("--adj-particles", type=int, default=1_000_000)
     ap.add_argument("--adj-steps", type=int, default=34_560)
     ap.add_argument("--checkpoint-every", type=int, default=256)
@@ -786,6 +856,8 @@ def main():
         run_ensemble_case(args)
     elif args.case == "adjoint":
         run_adjoint_case(args)
+    elif args.case == "stream":
+        run_stream_case(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -99,6 +99,11 @@ typedef struct fte_grid {
     int32_t amr_levels;        /* 0: uniform grid; 1..4: block AMR with this many levels */
     int32_t amr_bsize;         /* AMR: cells per block edge B (nr, nth, nph multiples of B) */
     int32_t n_leaves;          /* AMR: number of leaf blocks */
+    int32_t ring;              /* 0: all n_snap snapshots resident; 2 .. n_snap: the device
+                                  array holds `ring` snapshot slots, snapshot u (counted in
+                                  time order, periodic sequences unwrapped) in slot u mod ring,
+                                  filled on demand by fte_advance_streamed (FP32 only) */
+    int32_t pad;
 } fte_grid;
 
 /* Block AMR (Sec. 2.4, Fig. 4): nr x nth x nph are the base-level (level 0) cells,
@@ -168,7 +173,8 @@ typedef struct fte_particles {
  * Injection (Sec. 2.3, Eq. 7).  region 0: all at the point (r, th, ph); region 1:
  * uniform in volume over r in [r1, r2], cos(theta) between cos th1 and cos th2,
  * phi in [ph1, ph2], optionally accepting only positions whose containing cell
- * of snapshot `divv_snap` has stored div V (dV_x/dx + dV_y/dy + dV_z/dz, summed in
+ * of snapshot `divv_snap` (of a ring background: slot `divv_snap`, which the caller
+ * must have filled) has stored div V (dV_x/dx + dV_y/dy + dV_z/dz, summed in
  * float in that order) < divv_max, with at most max_tries attempts per particle.
  * energy 0: e0; energy 1: dN/dE ~ E^-gamma on [e1, e2] by inverse CDF.
  * weight 0: 1; weight 1: 1/r^2 (r in au).  mu_mode 0: mu uniform in [-1, 1];
@@ -274,6 +280,49 @@ fte_status fte_inject(fte_particles* P, const fte_background* bg, const fte_inje
 fte_status fte_advance(fte_particles* P, const fte_background* bg, const fte_params* prm,
                        const fte_tally_buf* t, int64_t n_start, int64_t n_end, void* ws,
                        size_t ws_bytes, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Snapshot streaming (Sec. 4 names loading only what is needed as the way to cut
+ * the cost of whole snapshot files): with grid.ring = R > 0 only R snapshots are
+ * resident and fte_advance_streamed moves snapshot files from host memory into
+ * their slots as the simulated time reaches them, on a copy stream, overlapped
+ * with the steps of the previous interval (R >= 3 prefetches one interval ahead).
+ * ------------------------------------------------------------------------- */
+
+/* Plan of a streamed advance: the steps n_start .. n_end-1 split into runs that
+   use the same snapshot pair.  out (HOST, 3 entries per run): first step, end
+   step, and the unwrapped index u of the earlier snapshot (the pair u, u+1), or
+   -1 - u when the fields are frozen at snapshot u (before the first or from the
+   last snapshot of a non-periodic sequence).  *count receives the number of
+   runs; ENOMEM if it exceeds max_runs (out then holds the first max_runs). */
+fte_status fte_stream_plan(const fte_grid* g, const fte_params* prm, int64_t n_start, int64_t n_end,
+                           int64_t* out, int64_t max_runs, int64_t* count);
+
+/* fte_advance over a ring background (grid.ring >= 2, FP32): for every run of
+   the plan, the snapshots it needs (and, with ring >= 3, the next one) are
+   copied from host_snapshots (HOST, page-locked for overlap: the n_snap
+   snapshots in order, each fte_snapshot_bytes(g) bytes of records; for AMR the
+   ghost cells of a copied snapshot are refilled on the device) into their
+   slots on copy_stream, and the run is advanced on
+   compute_stream once its slots are filled; a slot is overwritten only after
+   the steps using it are done.  slot_state (HOST, ring entries, caller-owned,
+   -1 = empty before the first call) records the unwrapped snapshot each slot
+   holds and is updated.  ws as for fte_advance with n_steps = the longest run.
+   Work of earlier calls on either stream is waited for.  Asynchronous. */
+fte_status fte_advance_streamed(fte_particles* P, const fte_background* bg, const void* host_snapshots,
+                                const fte_params* prm, const fte_tally_buf* t, int64_t n_start, int64_t n_end,
+                                int64_t* slot_state, void* ws, size_t ws_bytes, void* compute_stream,
+                                void* copy_stream);
+
+/* Copy unwrapped snapshot u (periodic sequences: any u, snapshot u mod n_snap;
+   otherwise 0 <= u < n_snap) from host_snapshots into slot u mod ring on
+   `stream` (AMR: and refill its ghost layer), and record it in slot_state, for
+   instance the injection snapshot before fte_inject.  Asynchronous. */
+fte_status fte_stream_load(const fte_background* bg, const void* host_snapshots, int64_t u, int64_t* slot_state,
+                           void* stream);
+
+/* Bytes of one snapshot's records (the unit fte_advance_streamed copies). */
+size_t fte_snapshot_bytes(const fte_grid* g);
 
 /* Allocation-free variant of fte_advance (the paper has no counterpart: this is
    an interface for callers that cannot allocate device memory at run time, such

@@ -28,9 +28,10 @@ def _stream(stream=None):
 DTYPES = {"f32": A.FTE_F32, "bf16": A.FTE_BF16, "f16": A.FTE_F16}
 
 
-def grid_c(g, dtype="f32"):
+def grid_c(g, dtype="f32", ring=0):
     c = A.fte_grid()
     c.dtype = DTYPES[dtype]
+    c.ring = int(ring)
     c.nr, c.nth, c.nph = g.nr, g.nth, g.nph
     c.radial = 1 if g.radial == "log" else 0
     c.r_min, c.r_max, c.th_min, c.th_max = g.r_min, g.r_max, g.th_min, g.th_max
@@ -84,10 +85,10 @@ def observer_c(o):
 class Background:
     """Device copy of a snapshot sequence (fte_background); dtype 'f32', 'bf16' or 'f16'."""
 
-    def __init__(self, grid, device="cuda", dtype="f32"):
+    def __init__(self, grid, device="cuda", dtype="f32", ring=0):
         self.grid = grid
         self.dtype = dtype
-        self.gc = grid_c(grid, dtype)
+        self.gc = grid_c(grid, dtype, ring)
         nbytes = A.lib().fte_background_bytes(C.byref(self.gc))
         if nbytes == 0:
             raise ValueError("invalid grid")
@@ -96,9 +97,10 @@ class Background:
         self.c = A.fte_background(self.gc, self.dev.data_ptr(), None, None)
 
 
-def amr_grid_c(spec, n_leaves, dtype="f32"):
+def amr_grid_c(spec, n_leaves, dtype="f32", ring=0):
     """fte_grid of an fte_inputs.amr.AmrSpec with n_leaves leaves."""
     c = A.fte_grid()
+    c.ring = int(ring)
     B = spec.bsize
     c.nr, c.nth, c.nph = spec.nbr * B, spec.nbt * B, spec.nbp * B
     c.radial = 1 if spec.radial == "log" else 0
@@ -114,10 +116,10 @@ class AmrBackground(Background):
     """Device block-AMR background: padded leaf fields, leaves and finest-level table.
     A 16-bit copy shares the leaves and table of the FP32 background it is quantized from."""
 
-    def __init__(self, spec, leaves, device="cuda", dtype="f32", share=None):
+    def __init__(self, spec, leaves, device="cuda", dtype="f32", share=None, ring=0):
         self.grid = spec
         self.dtype = dtype
-        self.gc = amr_grid_c(spec, len(leaves), dtype)
+        self.gc = amr_grid_c(spec, len(leaves), dtype, ring)
         nbytes = A.lib().fte_background_bytes(C.byref(self.gc))
         if nbytes == 0:
             raise ValueError("invalid AMR grid: " + A.lib().fte_last_error().decode())
@@ -521,3 +523,67 @@ class SmoothIntensity(torch.autograd.Function):
     def backward(ctx, grad_out):
         g = ctx.adj.reverse(ctx.pool, ctx.inj).to(ctx.theta_device, ctx.theta_dtype)
         return grad_out * g, None
+
+
+# ---------------------------------------------------------------------------
+# snapshot streaming through a ring of resident slots
+# ---------------------------------------------------------------------------
+def fte_snapshot_bytes(bg):
+    return A.lib().fte_snapshot_bytes(C.byref(bg.gc))
+
+
+def fte_stream_plan(bg, params, n_start, n_end):
+    """Runs of steps sharing a snapshot pair: int64 array [runs, 3] = (first, end, key); key >= 0 is
+    the unwrapped earlier snapshot of the pair, key < 0 freezes the fields at snapshot -1 - key."""
+    pc = params_c(params)
+    count = C.c_int64(0)
+    st = A.lib().fte_stream_plan(C.byref(bg.gc), C.byref(pc), int(n_start), int(n_end), None, 0, C.byref(count))
+    if st not in (A.FTE_OK, A.FTE_ENOMEM):
+        check(st, "fte_stream_plan")
+    out = np.zeros((max(count.value, 1), 3), dtype=np.int64)
+    check(A.lib().fte_stream_plan(C.byref(bg.gc), C.byref(pc), int(n_start), int(n_end),
+                                  C.c_void_p(out.ctypes.data), count.value, C.byref(count)), "fte_stream_plan")
+    return out[:count.value]
+
+
+class SnapshotStream:
+    """Host snapshots (page-locked, FP32 records) and the ring's slot bookkeeping for
+    fte_advance_streamed; `copy_stream` carries the uploads."""
+
+    def __init__(self, bg, host_fields, device="cuda"):
+        if bg.gc.ring < 2:
+            raise ValueError("the background has no ring")
+        t = host_fields if isinstance(host_fields, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(host_fields))
+        self.host = t if t.is_pinned() else t.pin_memory()
+        need = fte_snapshot_bytes(bg) * bg.gc.n_snap
+        if self.host.numel() * self.host.element_size() < need:
+            raise ValueError("host snapshots hold %d bytes, need %d" % (self.host.numel() * self.host.element_size(), need))
+        self.slots = np.full(bg.gc.ring, -1, dtype=np.int64)
+        self.copy_stream = torch.cuda.Stream(device=device)
+        self.bg = bg
+
+    def load(self, u, stream=None):
+        """Copy unwrapped snapshot u into its slot, e.g. the injection snapshot before fte_inject:
+        on the copy stream, after the work already on `stream` (torch's current stream by
+        default), which then waits for the copy."""
+        cur = stream if stream is not None else torch.cuda.current_stream()
+        self.copy_stream.wait_stream(cur)
+        check(A.lib().fte_stream_load(C.byref(self.bg.c), C.c_void_p(self.host.data_ptr()), int(u),
+                                      C.c_void_p(self.slots.ctypes.data), _stream(self.copy_stream)),
+              "fte_stream_load")
+        cur.wait_stream(self.copy_stream)
+
+
+def fte_advance_streamed(pool, bg, stream_state, params, tally, n_start, n_end, ws=None, stream=None):
+    """fte_advance over a ring background, uploading snapshots as the run reaches them."""
+    ws = ws if ws is not None else Workspace(bg.dev.device)
+    plan = fte_stream_plan(bg, params, n_start, n_end)
+    longest = int((plan[:, 1] - plan[:, 0]).max()) if len(plan) else 0
+    buf = ws.ensure(fte_workspace_bytes(bg, tally, pool.count, longest, bg.dev.device.index))
+    pc = params_c(params)
+    check(A.lib().fte_advance_streamed(C.byref(pool.c), C.byref(bg.c), C.c_void_p(stream_state.host.data_ptr()),
+                                       C.byref(pc), C.byref(tally.c), int(n_start), int(n_end),
+                                       C.c_void_p(stream_state.slots.ctypes.data), C.c_void_p(buf.data_ptr()),
+                                       buf.numel(), _stream(stream), _stream(stream_state.copy_stream)),
+          "fte_advance_streamed")
+    return ws

@@ -424,7 +424,7 @@ __global__ void __launch_bounds__(256) adj_forward_kernel(const AdvanceArgs a, c
 // of the first segment adds the injection-index term and reduces the gradients.
 // ---------------------------------------------------------------------------
 template <int DT>
-__global__ void __launch_bounds__(256) adj_reverse_kernel(const AdvanceArgs a, const AdjK k)
+__global__ void __launch_bounds__(256, 2) adj_reverse_kernel(const AdvanceArgs a, const AdjK k)
 {
     __shared__ float sc[FTE_NFIELD];
     __shared__ double red[8][FTE_NGRAD];

@@ -176,25 +176,29 @@ __global__ void step_table_kernel(const StepTableArgs a)
     e.s0 = 0; e.s1 = 0; e.wt = 0.f; e.two = 0;
     if (a.n_snap > 1) {
         const double tau = __ddiv_rn(__dsub_rn(t, a.t_snap0), a.dt_snap);
+        // u0, u1: the snapshots in time order (periodic sequences unwrapped)
+        long long u0 = 0, u1 = 0;
         if (a.periodic) {
             const double kf = floor(tau);
-            const long long kk = (long long)kf;
-            const int s0 = (int)(((kk % a.n_snap) + a.n_snap) % a.n_snap);
-            e.s0 = s0;
-            e.s1 = (s0 + 1) % a.n_snap;
+            u0 = (long long)kf;
+            u1 = u0 + 1;
             e.wt = (float)(tau - kf);
             e.two = 1;
         } else if (tau < 0.0) {
-            e.s0 = e.s1 = 0;
+            u0 = u1 = 0;
         } else if (tau >= (double)(a.n_snap - 1)) {
-            e.s0 = e.s1 = a.n_snap - 1;
+            u0 = u1 = a.n_snap - 1;
         } else {
             const double kf = floor(tau);
-            e.s0 = (int)kf;
-            e.s1 = e.s0 + 1;
+            u0 = (long long)kf;
+            u1 = u0 + 1;
             e.wt = (float)(tau - kf);
             e.two = 1;
         }
+        // storage slot: the snapshot itself, or its place in the ring
+        const long long m = a.ring > 0 ? a.ring : a.n_snap;
+        e.s0 = (int)(((u0 % m) + m) % m);
+        e.s1 = (int)(((u1 % m) + m) % m);
     }
     for (int o = 0; o < FTE_MAX_OBS; ++o) {
         short it = -1;

@@ -50,6 +50,8 @@ fte_status check_grid(const fte_grid* g)
     if (g->n_snap > 1 && !(g->dt_snap > 0.0)) return fail(FTE_EINVAL, "dt_snap must be > 0");
     if (g->dtype != FTE_F32 && g->dtype != FTE_BF16 && g->dtype != FTE_F16)
         return fail(FTE_EINVAL, "dtype must be FTE_F32, FTE_BF16 or FTE_F16");
+    if (g->ring != 0 && (g->ring < 2 || g->ring > g->n_snap))
+        return fail(FTE_EINVAL, "ring must be 0 or in [2, n_snap]");
     if (g->amr_levels < 0 || g->amr_levels > 4) return fail(FTE_EINVAL, "amr_levels must be in [0, 4]");
     if (g->amr_levels > 0) {
         const int B = g->amr_bsize;
@@ -77,9 +79,12 @@ size_t snapshot_records(const fte_grid* g)
     return (size_t)g->nr * g->nth * g->nph;
 }
 
+// snapshots held on the device: all of them, or the ring's slots
+int resident_snapshots(const fte_grid* g) { return g->ring > 0 ? g->ring : g->n_snap; }
+
 size_t grid_records(const fte_grid* g)
 {
-    return snapshot_records(g) * (size_t)g->n_snap;
+    return snapshot_records(g) * (size_t)resident_snapshots(g);
 }
 
 size_t grid_bytes(const fte_grid* g)
@@ -300,7 +305,7 @@ fte_status fte_amr_prepare(const fte_background* bg, void* stream)
     if (h[0] || h[1] || h[2] || h[3])
         return fail(FTE_EINVAL, "AMR leaves: %u malformed, %u overlapping finest blocks, %u uncovered, "
                     "%u nesting violations", h[0], h[1], h[2], h[3]);
-    FTE_CUDA(launch_amr_ghosts(g, bg->grid.n_snap, bg->grid.r_min, bg->grid.r_max, bg->grid.th_min,
+    FTE_CUDA(launch_amr_ghosts(g, resident_snapshots(&bg->grid), bg->grid.r_min, bg->grid.r_max, bg->grid.th_min,
                                bg->grid.th_max, st), "AMR ghost launch");
     return FTE_OK;
 }
@@ -357,8 +362,8 @@ size_t fte_workspace_bytes(int device, const fte_grid* g, const fte_tally_buf* t
     if (check_tally(t, &nb) != FTE_OK || n_steps < 0) return 0;
     if (nb > (size_t)kMaxSmemBins) return 0;
     fte_background tmp;
+    memset(&tmp, 0, sizeof(tmp));
     tmp.grid = *g;
-    tmp.fields = nullptr;
     const size_t sort_bytes = sort_scratch_bytes(make_gridk(&tmp), n_particles);
     size_t best = 0;
     for (int dtype = FTE_F32; dtype <= FTE_F16; ++dtype)
@@ -390,7 +395,7 @@ fte_status fte_inject(fte_particles* P, const fte_background* bg, const fte_inje
     if (spec->region == 1) {
         if (!(spec->r2 > spec->r1 && spec->r1 > 0)) return fail(FTE_EINVAL, "need 0 < r1 < r2");
         if (spec->max_tries < 1) return fail(FTE_EINVAL, "max_tries must be >= 1");
-        if (spec->use_divv && (spec->divv_snap < 0 || spec->divv_snap >= bg->grid.n_snap))
+        if (spec->use_divv && (spec->divv_snap < 0 || spec->divv_snap >= resident_snapshots(&bg->grid)))
             return fail(FTE_EINVAL, "divv_snap out of range");
     }
     if (spec->mu_mode == 1 && !(spec->mu0 >= -1.0 && spec->mu0 <= 1.0)) return fail(FTE_EINVAL, "mu0 outside [-1, 1]");
@@ -474,7 +479,7 @@ fte_status fte_advance(fte_particles* P, const fte_background* bg, const fte_par
     memset(&ta, 0, sizeof(ta));
     ta.tab = (StepEntry*)(w + L.off_table);
     ta.n0 = n_start; ta.count = nsteps; ta.t0 = prm->t0; ta.dt = prm->dt;
-    ta.n_snap = bg->grid.n_snap; ta.periodic = bg->grid.periodic;
+    ta.n_snap = bg->grid.n_snap; ta.periodic = bg->grid.periodic; ta.ring = bg->grid.ring;
     ta.t_snap0 = bg->grid.t_snap0; ta.dt_snap = bg->grid.dt_snap;
     ta.n_obs = t->n_obs;
     for (int o = 0; o < t->n_obs; ++o) {
@@ -760,7 +765,7 @@ extern "C" fte_status fte_advance_noalloc(fte_particles* P, const fte_background
     memset(&ta, 0, sizeof(ta));
     ta.tab = (StepEntry*)(w + off_table);
     ta.t0 = prm->t0; ta.dt = prm->dt;
-    ta.n_snap = bg->grid.n_snap; ta.periodic = bg->grid.periodic;
+    ta.n_snap = bg->grid.n_snap; ta.periodic = bg->grid.periodic; ta.ring = bg->grid.ring;
     ta.t_snap0 = bg->grid.t_snap0; ta.dt_snap = bg->grid.dt_snap;
     ta.n_obs = t->n_obs;
     for (int o = 0; o < t->n_obs; ++o) {
@@ -890,7 +895,7 @@ fte_status ens_run(fte_particles* P, const fte_background* bg, const fte_params*
     memset(&ta, 0, sizeof(ta));
     ta.tab = (StepEntry*)(w + L.off_table);
     ta.n0 = n_start; ta.count = nsteps; ta.t0 = prm->t0; ta.dt = prm->dt;
-    ta.n_snap = bg->grid.n_snap; ta.periodic = bg->grid.periodic;
+    ta.n_snap = bg->grid.n_snap; ta.periodic = bg->grid.periodic; ta.ring = bg->grid.ring;
     ta.t_snap0 = bg->grid.t_snap0; ta.dt_snap = bg->grid.dt_snap;
     ta.n_obs = t->n_obs;
     for (int o = 0; o < t->n_obs; ++o) {
@@ -1287,7 +1292,7 @@ fte_status adj_args(const fte_particles* P, const fte_background* bg, const fte_
     memset(&ta, 0, sizeof(ta));
     ta.tab = (StepEntry*)(w + L.off_table);
     ta.n0 = n_start; ta.count = nsteps; ta.t0 = prm->t0; ta.dt = prm->dt;
-    ta.n_snap = bg->grid.n_snap; ta.periodic = bg->grid.periodic;
+    ta.n_snap = bg->grid.n_snap; ta.periodic = bg->grid.periodic; ta.ring = bg->grid.ring;
     ta.t_snap0 = bg->grid.t_snap0; ta.dt_snap = bg->grid.dt_snap;
     if (setup) {
         FTE_CUDA(launch_norm(prm->dmumu, prm->q, prm->H, prm->eps, norm, (double*)(w + L.off_npart), st), "norm launch");
@@ -1452,6 +1457,201 @@ fte_status fte_adjoint_reverse(const fte_particles* P, const fte_background* bg,
         FTE_CUDA(launch_adjoint_reverse(a, k, L.rev_blocks, st), "adjoint reverse launch");
     }
     return FTE_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Snapshot streaming through a ring of resident slots.
+// ---------------------------------------------------------------------------
+#include <vector>
+
+namespace {
+
+struct Run {
+    int64_t a, b, key;     // steps [a, b); key >= 0: pair (key, key + 1); key < 0: frozen at -1 - key
+};
+
+// The snapshot pair of every step, by the step table's own rule (double
+// precision, each operation rounded: the host code is built without contraction).
+void stream_runs(const fte_grid* g, const fte_params* prm, int64_t n0, int64_t n1, std::vector<Run>& runs)
+{
+    runs.clear();
+    for (int64_t n = n0; n < n1; ++n) {
+        int64_t key = -1;
+        if (g->n_snap > 1) {
+            const double t = prm->t0 + (double)n * prm->dt;
+            const double tau = (t - g->t_snap0) / g->dt_snap;
+            if (g->periodic) key = (int64_t)floor(tau);
+            else if (tau < 0.0) key = -1;
+            else if (tau >= (double)(g->n_snap - 1)) key = -1 - (int64_t)(g->n_snap - 1);
+            else key = (int64_t)floor(tau);
+        }
+        if (!runs.empty() && runs.back().key == key && runs.back().b == n) runs.back().b = n + 1;
+        else runs.push_back(Run{n, n + 1, key});
+    }
+}
+
+int64_t pmod(int64_t u, int64_t m) { return ((u % m) + m) % m; }
+
+// Copy unwrapped snapshot u from host memory into its ring slot on stream `xs`
+// (AMR: and refill that slot's ghost layer).
+cudaError_t load_slot(const fte_background* bg, const void* host_snapshots, int64_t u, cudaStream_t xs)
+{
+    const fte_grid& g = bg->grid;
+    const size_t snap_bytes = snapshot_records(&g) * FTE_REC * sizeof(float);
+    const int64_t slot = pmod(u, g.ring);
+    const int64_t logical = g.periodic ? pmod(u, g.n_snap) : u;
+    float* dst = const_cast<float*>(bg->fields) + (size_t)slot * snapshot_records(&g) * FTE_REC;
+    cudaError_t e = cudaMemcpyAsync(dst, (const char*)host_snapshots + (size_t)logical * snap_bytes, snap_bytes,
+                                    cudaMemcpyHostToDevice, xs);
+    if (e == cudaSuccess && g.amr_levels > 0) {
+        GridK one = make_gridk(bg);
+        one.fields = dst;
+        e = launch_amr_ghosts(one, 1, g.r_min, g.r_max, g.th_min, g.th_max, xs);
+    }
+    return e;
+}
+
+fte_status check_stream(const fte_background* bg, const void* host_snapshots, const int64_t* slot_state)
+{
+    fte_status s = check_background(bg);
+    if (s != FTE_OK) return s;
+    if (bg->grid.ring < 2) return fail(FTE_EINVAL, "streaming needs a ring background (grid.ring >= 2)");
+    if (bg->grid.dtype != FTE_F32) return fail(FTE_ENOTSUP, "streaming supports FP32 snapshots");
+    if (!host_snapshots || !slot_state) return fail(FTE_EINVAL, "NULL argument");
+    return FTE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t fte_snapshot_bytes(const fte_grid* g)
+{
+    if (check_grid(g) != FTE_OK) return 0;
+    return snapshot_records(g) * (g->dtype == FTE_F32 ? FTE_REC * sizeof(float) : FTE_HREC * sizeof(uint16_t));
+}
+
+fte_status fte_stream_plan(const fte_grid* g, const fte_params* prm, int64_t n_start, int64_t n_end,
+                           int64_t* out, int64_t max_runs, int64_t* count)
+{
+    fte_status s = check_grid(g);
+    if (s != FTE_OK) return s;
+    if (!prm || !count || (max_runs > 0 && !out)) return fail(FTE_EINVAL, "NULL argument");
+    if (!(prm->dt > 0.0)) return fail(FTE_EINVAL, "dt must be > 0");
+    if (n_end < n_start || n_start < 0) return fail(FTE_EINVAL, "need 0 <= n_start <= n_end");
+    std::vector<Run> runs;
+    stream_runs(g, prm, n_start, n_end, runs);
+    *count = (int64_t)runs.size();
+    for (int64_t k = 0; k < (int64_t)runs.size() && k < max_runs; ++k) {
+        out[3 * k] = runs[k].a; out[3 * k + 1] = runs[k].b; out[3 * k + 2] = runs[k].key;
+    }
+    if ((int64_t)runs.size() > max_runs) return fail(FTE_ENOMEM, "%zu runs, room for %lld", runs.size(), (long long)max_runs);
+    return FTE_OK;
+}
+
+fte_status fte_stream_load(const fte_background* bg, const void* host_snapshots, int64_t u, int64_t* slot_state,
+                           void* stream)
+{
+    fte_status s = check_stream(bg, host_snapshots, slot_state);
+    if (s != FTE_OK) return s;
+    if (!bg->grid.periodic && (u < 0 || u >= bg->grid.n_snap)) return fail(FTE_EINVAL, "snapshot %lld out of range", (long long)u);
+    FTE_CUDA(load_slot(bg, host_snapshots, u, (cudaStream_t)stream), "snapshot copy");
+    slot_state[pmod(u, bg->grid.ring)] = u;
+    return FTE_OK;
+}
+
+fte_status fte_advance_streamed(fte_particles* P, const fte_background* bg, const void* host_snapshots,
+                                const fte_params* prm, const fte_tally_buf* t, int64_t n_start, int64_t n_end,
+                                int64_t* slot_state, void* ws, size_t ws_bytes, void* compute_stream,
+                                void* copy_stream)
+{
+    fte_status s = check_stream(bg, host_snapshots, slot_state);
+    if (s != FTE_OK) return s;
+    const fte_grid& g = bg->grid;
+    if (!prm) return fail(FTE_EINVAL, "NULL params");
+    if (!(prm->dt > 0.0)) return fail(FTE_EINVAL, "dt must be > 0");
+    if (n_end < n_start || n_start < 0) return fail(FTE_EINVAL, "need 0 <= n_start <= n_end");
+    std::vector<Run> runs;
+    stream_runs(&g, prm, n_start, n_end, runs);
+    const int R = g.ring;
+    cudaStream_t cs = (cudaStream_t)compute_stream, xs = (cudaStream_t)copy_stream;
+    std::vector<cudaEvent_t> ready(R, nullptr), freed(R, nullptr);
+    std::vector<char> has_ready(R, 0), has_freed(R, 0);
+    cudaEvent_t fence_c = nullptr, fence_x = nullptr;
+    fte_status result = FTE_OK;
+    auto fail_cuda = [&](cudaError_t e, const char* what) {
+        if (result == FTE_OK) result = cuda_fail(e, what);
+        return result;
+    };
+    auto mk = [&](cudaEvent_t* e) {
+        const cudaError_t r = cudaEventCreateWithFlags(e, cudaEventDisableTiming);
+        if (r != cudaSuccess) fail_cuda(r, "event create");
+    };
+    for (int k = 0; k < R && result == FTE_OK; ++k) { mk(&ready[k]); mk(&freed[k]); }
+    if (result == FTE_OK) mk(&fence_c);
+    if (result == FTE_OK) mk(&fence_x);
+    // order against earlier work: copies after earlier steps, steps after earlier copies
+    if (result == FTE_OK) {
+        cudaError_t e = cudaEventRecord(fence_c, cs);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(xs, fence_c, 0);
+        if (e == cudaSuccess) e = cudaEventRecord(fence_x, xs);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, fence_x, 0);
+        if (e != cudaSuccess) fail_cuda(e, "stream ordering");
+    }
+    // bring unwrapped snapshot u into its slot (unless already there or, for a
+    // prefetch, the slot is in use by the current run)
+    auto ensure = [&](int64_t u, int busy0, int busy1, bool prefetch) {
+        if (result != FTE_OK) return;
+        const int slot = (int)pmod(u, R);
+        if (slot_state[slot] == u) return;
+        if (prefetch && (slot == busy0 || slot == busy1)) return;
+        if (has_freed[slot]) {
+            const cudaError_t e = cudaStreamWaitEvent(xs, freed[slot], 0);
+            if (e != cudaSuccess) { fail_cuda(e, "copy wait"); return; }
+        }
+        cudaError_t e = load_slot(bg, host_snapshots, u, xs);
+        if (e == cudaSuccess) e = cudaEventRecord(ready[slot], xs);
+        if (e != cudaSuccess) { fail_cuda(e, "snapshot copy"); return; }
+        has_ready[slot] = 1;
+        slot_state[slot] = u;
+    };
+    for (size_t k = 0; k < runs.size() && result == FTE_OK; ++k) {
+        const Run& r = runs[k];
+        const bool pair = r.key >= 0;
+        const int64_t u0 = pair ? r.key : -1 - r.key;
+        const int64_t u1 = pair ? r.key + 1 : u0;
+        const int s0 = (int)pmod(u0, R), s1 = (int)pmod(u1, R);
+        ensure(u0, -1, -1, false);
+        ensure(u1, -1, -1, false);
+        if (R >= 3) {      // the snapshot after this pair, while this run computes
+            const int64_t nx = u1 + 1;
+            if (g.periodic || nx <= g.n_snap - 1) ensure(nx, s0, s1, true);
+        }
+        if (result != FTE_OK) break;
+        for (int sl : {s0, s1}) {
+            if (has_ready[sl]) {
+                const cudaError_t e = cudaStreamWaitEvent(cs, ready[sl], 0);
+                if (e != cudaSuccess) { fail_cuda(e, "compute wait"); break; }
+            }
+        }
+        if (result != FTE_OK) break;
+        const fte_status st = fte_advance(P, bg, prm, t, r.a, r.b, ws, ws_bytes, compute_stream);
+        if (st != FTE_OK) { result = st; break; }
+        for (int sl : {s0, s1}) {
+            const cudaError_t e = cudaEventRecord(freed[sl], cs);
+            if (e != cudaSuccess) { fail_cuda(e, "event record"); break; }
+            has_freed[sl] = 1;
+        }
+    }
+    for (int k = 0; k < R; ++k) {
+        if (ready[k]) cudaEventDestroy(ready[k]);
+        if (freed[k]) cudaEventDestroy(freed[k]);
+    }
+    if (fence_c) cudaEventDestroy(fence_c);
+    if (fence_x) cudaEventDestroy(fence_x);
+    return result;
 }
 
 }  // extern "C"

@@ -73,7 +73,8 @@ struct StepTableArgs {
     double t0, dt;
     int n_snap, periodic;
     double t_snap0, dt_snap;
-    int n_obs, pad;
+    int n_obs;
+    int ring;                     // > 0: snapshot u (unwrapped, in time order) is in slot u mod ring
     ObsTime ot[FTE_MAX_OBS];
 };
 

@@ -43,7 +43,7 @@ def test_version_and_status_strings(L):
 
 def test_struct_sizes_match_header_layout():
     from paper_2404_12164_gb300 import _abi as A
-    assert C.sizeof(A.fte_grid) == 4 * 4 + 4 * 8 + 2 * 4 + 2 * 8 + 4 * 4
+    assert C.sizeof(A.fte_grid) == 4 * 4 + 4 * 8 + 2 * 4 + 2 * 8 + 6 * 4
     assert C.sizeof(A.fte_observer) == 4 * 4 + 10 * 8
     assert C.sizeof(A.fte_params) == 4 * 4 + 10 * 8 + 4 * 4
     assert C.sizeof(A.fte_inject_spec) == 4 * 4 + 9 * 8 + 4 * 4 + 6 * 8 + 4 * 4
@@ -127,3 +127,37 @@ def test_ensemble_structs_and_host_checks(L):
     assert L.fte_graph_launch(None, None) == A.FTE_EINVAL
     assert L.fte_graph_destroy(None) == A.FTE_OK
     assert L.fte_tally_set(None, 0, 0, 0, None, None, 0, None) == A.FTE_EINVAL
+
+
+def test_stream_plan_and_ring_sizes(L):
+    """The snapshot-pair runs of a streamed advance (host-side plan) and the size of a ring
+    background; no GPU needed."""
+    from fte_inputs.configs import Params
+    from fte_inputs.grid import GridSpec
+    from paper_2404_12164_gb300 import api, _abi as A
+    g = GridSpec(nr=16, nth=8, nph=8, n_snap=24, periodic=True, dt_snap=3600.0)
+    snap = 16 * 8 * 8 * 96
+    assert L.fte_snapshot_bytes(C.byref(api.grid_c(g))) == snap
+    assert L.fte_background_bytes(C.byref(api.grid_c(g, ring=3))) == 3 * snap
+    for bad in (1, 25, -1):
+        assert L.fte_background_bytes(C.byref(api.grid_c(g, ring=bad))) == 0
+
+    def plan(grid, prm, a, b):
+        gc, pc = api.grid_c(grid, ring=2), api.params_c(prm)
+        cnt = C.c_int64(0)
+        out = (C.c_int64 * 3000)()
+        assert L.fte_stream_plan(C.byref(gc), C.byref(pc), a, b, out, 1000, C.byref(cnt)) == A.FTE_OK
+        return [tuple(out[3 * k:3 * k + 3]) for k in range(cnt.value)]
+    runs = plan(g, Params(dt=10.0), 0, 34560)
+    assert len(runs) == 96
+    assert all(r == (360 * k, 360 * (k + 1), k) for k, r in enumerate(runs))
+    # non-periodic, starting before the first snapshot: frozen, three pairs, frozen at the last
+    g2 = GridSpec(nr=16, nth=8, nph=8, n_snap=4, periodic=False, dt_snap=1000.0)
+    runs = plan(g2, Params(dt=10.0, t0=-500.0), 0, 400)
+    assert runs == [(0, 50, -1), (50, 150, 0), (150, 250, 1), (250, 350, 2), (350, 400, -4)]
+    # too little room is reported with the count
+    gc, pc = api.grid_c(g, ring=2), api.params_c(Params(dt=10.0))
+    cnt = C.c_int64(0)
+    out = (C.c_int64 * 3)()
+    assert L.fte_stream_plan(C.byref(gc), C.byref(pc), 0, 720, out, 1, C.byref(cnt)) == A.FTE_ENOMEM
+    assert cnt.value == 2 and tuple(out) == (0, 360, 0)

@@ -1,0 +1,119 @@
+"""Snapshot streaming through a ring of resident slots on the GPU: the same run
+with all snapshots resident and with 2 or 3 slots filled on demand from host
+memory gives the same trajectories (bit for bit) and the same tallies, for
+periodic and non-periodic sequences and for block-AMR backgrounds (whose ghost
+layers are refilled on the device after each upload)."""
+import math
+
+import numpy as np
+import pytest
+
+from fte_inputs import amr, configs
+from fte_inputs.configs import InjectSpec, Observer, Params
+
+pytestmark = pytest.mark.gpu
+DEG = math.pi / 180
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2404_12164_gb300 import build
+    build.build()
+
+
+OBS = [Observer(kind="shell", r=1.4, dr=0.05, e_lo=0.01, e_hi=1.0, ne=8, t_lo=0.0, t_hi=8000.0, nt=16)]
+
+
+def _run(bg, w, n, n_steps, stream_state=None, splits=(0,)):
+    import torch
+    from paper_2404_12164_gb300 import api, _abi as A
+    pool = api.Particles(n)
+    tally = api.Tally(OBS)
+    api.fte_tally_reset(tally)
+    api.fte_inject(pool, bg, w.inject, n, tally)
+    ws = api.Workspace()
+    bounds = list(splits) + [n_steps]
+    for a, b in zip(bounds[:-1], bounds[1:]):
+        if stream_state is None:
+            api.fte_advance(pool, bg, w.params, tally, a, b, ws)
+        else:
+            api.fte_advance_streamed(pool, bg, stream_state, w.params, tally, a, b, ws)
+    torch.cuda.synchronize()
+    return pool.state(), api.fte_tally(tally, 0, A.FTE_TALLY_C), api.fte_tally(tally, 0, A.FTE_TALLY_S)
+
+
+def _same(a, b):
+    sa, ca, Sa = a
+    sb, cb, Sb = b
+    for k in ("x", "y", "z", "mu", "p", "status"):
+        assert np.array_equal(sa[k], sb[k]), k
+    assert np.array_equal(ca, cb)
+    assert np.allclose(Sa, Sb, rtol=1e-5, atol=0)     # per-launch FP32 partial sums group differently
+
+
+@pytest.mark.parametrize("periodic", [True, False])
+@pytest.mark.parametrize("ring", [2, 3])
+def test_uniform_ring_equals_resident(periodic, ring):
+    from paper_2404_12164_gb300 import api
+    w = configs.scaled(configs.cir_uniform_1e6(), nr=96, nth=24, nph=72, n_snap=6, n_particles=3000)
+    w.grid.periodic = periodic
+    w.grid.dt_snap = 600.0
+    w.params.sort_every = 32
+    w.inject.divv_max = None           # injection reads no snapshot (ring slots fill on demand)
+    f = configs.build_background(w)
+    n_steps = 800                      # 8000 s: beyond the period (3600 s) / the last snapshot (3000 s)
+    res = api.Background(w.grid)
+    api.fte_load_background(res, f)
+    ref = _run(res, w, w.n_particles, n_steps)
+    bg = api.Background(w.grid, ring=ring)
+    st = api.SnapshotStream(bg, f)
+    got = _run(bg, w, w.n_particles, n_steps, st, splits=(0, 333))
+    _same(got, ref)
+    plan = api.fte_stream_plan(bg, w.params, 0, n_steps)
+    if periodic:
+        assert len(plan) == 14 and np.all(plan[:-1, 1] - plan[:-1, 0] == 60)
+    else:
+        assert plan[-1, 2] == -1 - 5 and plan[-1, 1] == n_steps
+
+
+def test_amr_ring_refills_ghosts():
+    from paper_2404_12164_gb300 import api
+    spec = amr.AmrSpec(nbr=4, nbt=2, nbp=4, bsize=8, levels=3, n_snap=4, periodic=False, dt_snap=1500.0)
+    leaves = amr.build_leaves(spec, amr.divv_refiner(spec, threshold=8e-6, r_from=0.9))
+    f = amr.fields(spec, leaves)
+    w = configs.cir_uniform_1e6()
+    w.inject = InjectSpec(region="box", r1=1.0, r2=1.8, th1=88 * DEG, th2=92 * DEG, ph1=math.pi, ph2=2 * math.pi,
+                          energy="mono", e0=0.05, weight="r-2", seed=2)
+    w.params = Params(dmumu="qlt", lambda_par=0.1, dt=10.0, sort_every=32)
+    res = api.AmrBackground(spec, leaves)
+    api.fte_load_background(res, f)
+    api.fte_amr_prepare(res)
+    ref = _run(res, w, 2000, 600)
+    bg = api.AmrBackground(spec, leaves, ring=2)
+    api.fte_amr_prepare(bg)                      # table; the slots are filled by the stream
+    st = api.SnapshotStream(bg, f)
+    got = _run(bg, w, 2000, 600, st)
+    _same(got, ref)
+
+
+def test_streaming_refusals():
+    from paper_2404_12164_gb300 import api, _abi as A
+    w = configs.scaled(configs.cir_uniform_1e6(), nr=32, nth=8, nph=16, n_snap=4, n_particles=10)
+    f = configs.build_background(w)
+    plain = api.Background(w.grid)
+    with pytest.raises(ValueError):
+        api.SnapshotStream(plain, f)
+    half = api.Background(w.grid, dtype="bf16", ring=2)
+    st = api.SnapshotStream.__new__(api.SnapshotStream)
+    st.host = __import__("torch").from_numpy(np.ascontiguousarray(f)).pin_memory()
+    st.slots = np.full(2, -1, dtype=np.int64)
+    st.copy_stream = __import__("torch").cuda.Stream()
+    pool = api.Particles(10)
+    tally = api.Tally(OBS)
+    api.fte_tally_reset(tally)
+    with pytest.raises(A.FteError) as e:
+        api.fte_advance_streamed(pool, half, st, w.params, tally, 0, 10)
+    assert e.value.status == A.FTE_ENOTSUP
