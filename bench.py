@@ -550,42 +550,45 @@ def run_ensemble_case(args):
                   api.fte_workspace_bytes(bg, api.Tally(w.observers), n_tot, n_steps)))
     torch.cuda.synchronize()
 
-    def timed(fn, steps, warmup):
+    def timed(fn, count, steps, warmup):
+        """Rate and time per step of `fn`; every step repeats the same work, so the alive
+        particle-steps of the last one (`count`, read after the timed region) times the
+        number of steps is the total."""
         for _ in range(warmup):
             fn()
         side.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
-        done = 0
         with torch.cuda.stream(side):
             e0.record(side)
             for _ in range(steps):
                 fn()
-                done += int(tally.ledger_n.cpu().numpy()[6]) if fn is not plain_step else plain_done[0]
             e1.record(side)
         side.synchronize()
+        done = count() * steps
         return done / (e0.elapsed_time(e1) / 1e3), e0.elapsed_time(e1) / steps
 
-    # arm 1: the single-set kernel, set after set (each set its own pool slice and tally)
-    one_tally = api.Tally(w.observers)
-    plain_done = [0]
+    def ensemble_count():
+        return int(tally.ledger_n.cpu().numpy()[6])
+
+    # arm 1: the single-set kernel, set after set (each set its own pool and tally)
+    sub_pools = [api.Particles(s.count) for s in sets]
+    sub_tallies = [api.Tally(w.observers) for _ in sets]
+    set_params = [dataclasses.replace(w.params, lambda_par=s.lambda_par, q=s.q, H=s.H, eps=s.eps, seed=s.seed,
+                                      set_id=s.set_id) for s in sets]
 
     def plain_step():
-        plain_done[0] = 0
-        for s in sets:
-            sub = api.Particles(s.count) if s.count not in sub_pools else sub_pools[s.count]
-            sub_pools[s.count] = sub
+        for s, sub, tl, prm in zip(sets, sub_pools, sub_tallies, set_params):
             sub.c.count = 0
-            api.fte_tally_reset(one_tally, stream=side)
-            api.fte_inject(sub, bg, s.inject, s.count, one_tally, id_base=0, check_failed=False, stream=side)
-            prm = dataclasses.replace(w.params, lambda_par=s.lambda_par, q=s.q, H=s.H, eps=s.eps,
-                                      seed=s.seed, set_id=s.set_id)
-            api.fte_advance(sub, bg, prm, one_tally, 0, n_steps, ws, stream=side)
-            plain_done[0] += int(one_tally.ledger_n.cpu().numpy()[6])
-    sub_pools = {}
+            api.fte_tally_reset(tl, stream=side)
+            api.fte_inject(sub, bg, s.inject, s.count, tl, id_base=0, check_failed=False, stream=side)
+            api.fte_advance(sub, bg, prm, tl, 0, n_steps, ws, stream=side)
+
+    def plain_count():
+        return sum(int(tl.ledger_n.cpu().numpy()[6]) for tl in sub_tallies)
     with torch.cuda.stream(side):
-        plain_rate, plain_ms = timed(plain_step, args.ens_timed, 1)
-    sub_pools.clear()
+        plain_rate, plain_ms = timed(plain_step, plain_count, args.ens_timed, 1)
+    del sub_pools, sub_tallies
     torch.cuda.empty_cache()
 
     # arm 2: ensemble kernel, default configuration, eager calls
@@ -595,7 +598,7 @@ def run_ensemble_case(args):
         api.fte_inject_batched(pool, bg, sets, tally, stream=side)
         api.fte_advance_batched(pool, bg, w.params, sets, tally, 0, n_steps, ws, config=cfg, stream=side)
     with torch.cuda.stream(side):
-        eager_rate, eager_ms = timed(batched_step, args.ens_timed, 1)
+        eager_rate, eager_ms = timed(batched_step, ensemble_count, args.ens_timed, 1)
 
     # arm 3: autotune on one pass, then capture one pass into a graph and replay it
     with torch.cuda.stream(side):
@@ -607,7 +610,7 @@ def run_ensemble_case(args):
         g = api.Graph()
         with g.capture(side):
             batched_step(best)
-        graph_rate, graph_ms = timed(lambda: g.launch(side), args.ens_timed, 1)
+        graph_rate, graph_ms = timed(lambda: g.launch(side), ensemble_count, args.ens_timed, 1)
     S = np.array([api.fte_tally_set(tally, k, 0, A.FTE_TALLY_S).sum() for k in range(len(sets))])
     S2 = np.array([api.fte_tally_set(tally, k, 0, A.FTE_TALLY_S2).sum() for k in range(len(sets))])
     rel = [float(math.sqrt(b) / a) for a, b in zip(S, S2) if a > 0]

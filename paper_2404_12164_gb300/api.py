@@ -195,6 +195,18 @@ class Particles:
         out["status"] = self.status[:n].cpu().numpy()
         return out
 
+    def load_state(self, st):
+        """Restore a pool saved with state() (a checkpoint): with the step index it is the whole
+        state of a run, since every random number is a function of (seed, set, step, id)."""
+        n = len(st["x"])
+        if n > self.c.capacity:
+            raise ValueError("pool capacity %d < %d" % (self.c.capacity, n))
+        for k in ("x", "y", "z", "mu", "p", "w"):
+            getattr(self, k)[:n].copy_(torch.from_numpy(np.ascontiguousarray(st[k], dtype=np.float32)))
+        self.id[:n].copy_(torch.from_numpy(np.ascontiguousarray(st["id"]).view(np.int32)))
+        self.status[:n].copy_(torch.from_numpy(np.ascontiguousarray(st["status"], dtype=np.uint8)))
+        self.c.count = n
+
 
 class Tally:
     """Device tally accumulators and ledger (fte_tally_buf); n_sets blocks of bins

@@ -1,13 +1,12 @@
 // Spatial ordering of the alive particles: a counting sort by grid bucket (two
-// r-cells of one (theta, phi) column), so that consecutive entries of the order
-// list - and so the lanes of a warp - read the same cache lines of the
-// background.  Dead particles are left out, which also compacts the work list.
-// Performance only: each particle's trajectory does not depend on the order.
+// r-cells of one (theta, phi) column, of the grid or of a block-AMR leaf), so
+// that consecutive entries of the order list - and so the lanes of a warp - read
+// the same cache lines of the background.  Dead particles are left out, which
+// also compacts the work list.  Performance only: each particle's trajectory does not depend on the order.
 #include "fte_kernels.cuh"
 
 namespace fte {
 
-__device__ __forceinline__ int amr_sub(const GridK& g) { return g.B >= 4 ? g.B / 4 : 1; }
 
 __device__ __forceinline__ int bucket_of(const GridK& g, float x, float y, float z)
 {
@@ -16,11 +15,10 @@ __device__ __forceinline__ int bucket_of(const GridK& g, float x, float y, float
     const float th = atan2f(sqrtf(rho2), z);
     float ph = atan2f(y, x);
     if (ph < 0.f) ph += kTwoPi;
-    if (g.amr) {      // AMR: leaf, then sub-blocks of (B/4)^3 cells
+    if (g.amr) {      // AMR: leaf, then two r-cells of one (theta, phi) column of it
         int ci, cj, ck;
         const int leaf = amr_containing(g, r, th, ph, ci, cj, ck);
-        const int sb = amr_sub(g), ns = g.B / sb;
-        return ((leaf * ns + ck / sb) * ns + cj / sb) * ns + ci / sb;
+        return ((leaf * g.B + ck) * g.B + cj) * ((g.B + 1) >> 1) + (ci >> 1);
     }
     const float xr = g.radial ? logf(r / g.r_min) * g.inv_dr : (r - g.r_min) * g.inv_dr;
     const int i = min(max((int)xr, 0), g.nr - 1);
@@ -137,10 +135,7 @@ __global__ void __launch_bounds__(256) scatter_kernel(const SortArgs a)
 
 int sort_buckets(const GridK& g)
 {
-    if (g.amr) {
-        const int sb = g.B >= 4 ? g.B / 4 : 1, ns = g.B / sb;
-        return g.amr_leaves * ns * ns * ns;
-    }
+    if (g.amr) return g.amr_leaves * g.B * g.B * ((g.B + 1) >> 1);
     return g.nph * g.nth * ((g.nr + 1) >> 1);
 }
 

@@ -260,3 +260,45 @@ def test_spatial_reordering_changes_nothing(cir_small):
     assert np.array_equal(a["tallies"][0]["C"], b["tallies"][0]["C"])
     assert np.allclose(a["tallies"][0]["S"], b["tallies"][0]["S"], rtol=1e-5, atol=1e-12)
     assert np.array_equal(a["ledger_n"], b["ledger_n"])
+
+
+def test_checkpoint_resume_is_bit_exact(tmp_path, parker):
+    """A run saved to disk after 150 steps and resumed in a fresh pool ends where the
+    uninterrupted run ends (every random number depends on (seed, set, step, id) only)."""
+    from paper_2404_12164_gb300 import api
+    w, f = parker
+    full = gpu_run(w, f, 300, chunks=[300])["states"][300]
+    bg = api.Background(w.grid)
+    api.fte_load_background(bg, f)
+    pool = api.Particles(w.n_particles)
+    tally = api.Tally(w.observers)
+    api.fte_tally_reset(tally)
+    api.fte_inject(pool, bg, w.inject, w.n_particles, tally)
+    api.fte_advance(pool, bg, w.params, tally, 0, 150)
+    np.savez(tmp_path / "ckpt.npz", **pool.state())
+    del pool
+    saved = dict(np.load(tmp_path / "ckpt.npz"))
+    resumed = api.Particles(w.n_particles)
+    resumed.load_state(saved)
+    api.fte_advance(resumed, bg, w.params, tally, 150, 300)
+    st = resumed.state()
+    for k in ("x", "y", "z", "mu", "p", "w", "id", "status"):
+        assert np.array_equal(st[k], full[k]), k
+
+
+def test_undersized_workspace_is_refused(parker):
+    import ctypes as C
+    import torch
+    from paper_2404_12164_gb300 import api, _abi as A
+    w, f = parker
+    bg = api.Background(w.grid)
+    api.fte_load_background(bg, f)
+    pool = api.Particles(100)
+    tally = api.Tally(w.observers)
+    api.fte_tally_reset(tally)
+    api.fte_inject(pool, bg, w.inject, 100, tally)
+    buf = torch.empty(1024, dtype=torch.uint8, device="cuda")     # far below the partial histograms
+    st = A.lib().fte_advance(C.byref(pool.c), C.byref(bg.c), C.byref(api.params_c(w.params)), C.byref(tally.c),
+                             0, 50, C.c_void_p(buf.data_ptr()), buf.numel(), None)
+    assert st == A.FTE_ENOMEM
+    assert b"workspace" in A.lib().fte_last_error()
