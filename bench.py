@@ -19,8 +19,11 @@ ids, weak scaling) and the tallies are summed over ranks after each step.
 `--impl reference` times the FP64 CPU oracle on the host cores on a bounded
 sample of the same workload.
 
-The default line also carries the 16-bit storage forms (`forms`) and the
-adjoint's cost on a slice of the workload (`adjoint`).  Other cases, each one
+The device background uses the pair record layout by default (each record
+holds a cell and its upper r-neighbour, converted on the device from the
+uploaded cell records; `--layout cell` measures the plain layout).  The default
+line also carries the 16-bit storage forms (`forms`) and the adjoint's cost on a
+slice of the workload (`adjoint`).  Other cases, each one
 JSON line: `--case amr` (the CIR on a 39,520-leaf block-AMR grid, 1e7 protons,
 FP32/BF16/FP16), `--case ensemble` (64 parameter sets, 2e7 protons: set after
 set, one ensemble launch, autotuned and graph-captured), `--case adjoint` (the
@@ -154,7 +157,8 @@ def run_gpu(args):
     stream = torch.cuda.current_stream()
 
     host = torch.from_numpy(np.ascontiguousarray(fields)).pin_memory()
-    bg = api.Background(w.grid)
+    src = api.Background(w.grid)               # FP32 cell records, as uploaded from the host
+    bg = src if args.layout == "cell" else api.Background(w.grid, layout=args.layout)
     pool = api.Particles(n_part)
     tally = api.Tally(w.observers)
     wsp = api.Workspace()
@@ -183,8 +187,14 @@ def run_gpu(args):
                 timed_launches.append((ev0, ev1))
         pdist.reduce_tally(tally)
 
+    def upload():
+        """host snapshots -> device, converted to the measured record layout"""
+        api.fte_load_background(src, host)
+        if bg is not src:
+            api.fte_quantize_background(bg, src)
+
     # device-resident arm ------------------------------------------------------
-    api.fte_load_background(bg, host)
+    upload()
     torch.cuda.synchronize()
 
     def measure(background, steps, warmup, clocks=None):
@@ -231,7 +241,7 @@ def run_gpu(args):
     out_host = np.zeros((w.observers[0].ne, w.observers[0].nt))
 
     def e2e_step():
-        api.fte_load_background(bg, host)
+        upload()
         one_step()
         h = api.fte_tally(tally, 0, A.FTE_TALLY_S)
         out_host[:] = h
@@ -255,8 +265,8 @@ def run_gpu(args):
     forms = {}
     if not args.no_forms:
         for dt in ("bf16", "f16"):
-            bh = api.Background(w.grid, dtype=dt)
-            api.fte_quantize_background(bh, bg)
+            bh = api.Background(w.grid, dtype=dt, layout=args.layout)
+            api.fte_quantize_background(bh, src)
             f_ms, f_kms, _, f_steps = measure(bh, args.steps, max(1, args.warmup // 3))
             Sh = api.fte_tally(tally, 0, A.FTE_TALLY_S)
             f_alg = f_steps * (ALG_BYTES // 2) / (f_kms / 1e3) / 1e9
@@ -293,10 +303,10 @@ def run_gpu(args):
                                "1e6 protons at 50 keV in div V<0 cells (1-2 au, 90+-2 deg, w=1/r^2), "
                                "QLT D_mumu q=5/3 H=0.05 lambda_par=0.1 au, dt=10 s x 34560 (4 days), "
                                "1 au box tally 16x144",
-                   "particles_per_gpu": n_part, "steps_per_particle": n_steps,
+                   "particles_per_gpu": n_part, "steps_per_particle": n_steps, "record_layout": args.layout,
                    "background_bytes": int(bg.nbytes), "l2": "inputs larger than L2 (background %.1f GB)" % (bg.nbytes / 1e9),
                    "tally_rel_err": rel_err},
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(bg.nbytes),
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(src.nbytes),
                 "d2h_bytes_per_step": int(out_host.nbytes + 2 * 8 * A.FTE_LEDGER)},
         "gpu_launches": launches_per_step * args.steps,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -485,12 +495,20 @@ def run_amr_case(args):
 
     peak, peak_kind = _peaks()
     clocks = Clocks(0)
-    ms, k_ms, done, S, S2 = measure(bg, args.steps, args.warmup, clocks)
+    layout = getattr(args, "layout", "cell")
+    bm = bg
+    if layout != "cell":
+        bm = api.AmrBackground(w.grid, leaves, share=bg, layout=layout)
+        api.fte_quantize_background(bm, bg)
+    ms, k_ms, done, S, S2 = measure(bm, args.steps, args.warmup, clocks)
+    if bm is not bg:
+        del bm
+        torch.cuda.empty_cache()
     achieved = done * alg / (k_ms / 1e3) / 1e9
     forms = {}
     if not args.no_forms:
         for dt in ("bf16", "f16"):
-            bh = api.AmrBackground(w.grid, leaves, dtype=dt, share=bg)
+            bh = api.AmrBackground(w.grid, leaves, dtype=dt, share=bg, layout=layout)
             api.fte_quantize_background(bh, bg)
             f_ms, f_kms, f_done, Sh, S2h = measure(bh, args.steps, max(1, args.warmup // 3))
             f_alg = f_done * (ALG_BYTES // 2 + 4) / (f_kms / 1e3) / 1e9
@@ -513,7 +531,7 @@ def run_amr_case(args):
                                f"{n_part:.0e} protons E^-3 over 50 keV-5 MeV (1-2 au, 90+-2 deg, w=1/r^2), "
                                f"QLT q=5/3 H=0.05 lambda_par=0.1 au, dt=2 s x {n_steps}, "
                                "4 observer boxes 16x144",
-                   "leaves": int(len(leaves)), "leaves_per_level": lv.tolist(),
+                   "leaves": int(len(leaves)), "leaves_per_level": lv.tolist(), "record_layout": layout,
                    "background_bytes": int(bg.nbytes), "generate_s": t_gen,
                    "tally_rel_err": [float(math.sqrt(b) / a) if a > 0 else None for a, b in zip(S, S2)]},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -846,6 +864,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true")
+    ap.add_argument("--layout", default="pair", choices=["pair", "cell"],
+                    help="record layout of the device background (pair: a cell and its r-neighbour per record)")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--adj-slice", type=int, default=4096, help="steps of the adjoint measurement in the default run")
     ap.add_argument("--sort-every", type=int, default=64,

@@ -87,6 +87,13 @@ enum { FTE_ALIVE = 0, FTE_ABS_INNER = 1, FTE_ABS_OUTER = 2, FTE_ABS_THETA = 3,
  * produced on the device by fte_quantize_background (or copied in ready-made).
  * ------------------------------------------------------------------------- */
 enum { FTE_F32 = 0, FTE_BF16 = 1, FTE_F16 = 2 };
+/* Record layout.  FTE_LAYOUT_CELL: one record per cell as above.  FTE_LAYOUT_PAIR:
+   record k holds the fields of cell k and of its upper r-neighbour k + 1 (zero
+   for the last cell of an r-row): FP32 40 floats (160 bytes: 0-17 cell k,
+   18-35 cell k + 1, 36-39 zero), 16-bit 48 values (96 bytes: 0-17, 18-35, then
+   zero), so that the two r-neighbours of a corner pair are one 32-byte aligned
+   read of five (FP32) or three (16-bit) sectors instead of six or four. */
+enum { FTE_LAYOUT_CELL = 0, FTE_LAYOUT_PAIR = 1 };
 typedef struct fte_grid {
     int32_t nr, nth, nph;      /* cells per axis, each >= 2 */
     int32_t radial;            /* 0 linear, 1 logarithmic */
@@ -103,7 +110,7 @@ typedef struct fte_grid {
                                   array holds `ring` snapshot slots, snapshot u (counted in
                                   time order, periodic sequences unwrapped) in slot u mod ring,
                                   filled on demand by fte_advance_streamed (FP32 only) */
-    int32_t pad;
+    int32_t layout;            /* FTE_LAYOUT_CELL or FTE_LAYOUT_PAIR (see below) */
 } fte_grid;
 
 /* Block AMR (Sec. 2.4, Fig. 4): nr x nth x nph are the base-level (level 0) cells,
@@ -146,11 +153,13 @@ size_t fte_amr_table_bytes(const fte_grid* g);
    in bg->fields.  A 16-bit copy is then made with fte_quantize_background. */
 fte_status fte_amr_prepare(const fte_background* bg, void* stream);
 
-/* Quantize an FP32 background to the reduced-precision format of `g_half`
-   (dtype FTE_BF16 or FTE_F16; the other fields give the geometry of both
-   arrays): `dev_f32` (DEVICE, the FP32 array of the same geometry) is read and
-   `dev_out` (DEVICE, 32-byte aligned, out_bytes >= fte_background_bytes(g_half))
-   receives the scale header and the records.  Asynchronous on `stream`. */
+/* Convert an FP32 cell-layout background to the storage form of `g_half`: a
+   16-bit dtype (FTE_BF16 or FTE_F16: per-field scales and rounded records) and/or
+   the pair layout; the other fields give the geometry of both arrays.
+   `dev_f32` (DEVICE, the FP32 cell-layout array of the same geometry; for AMR
+   after fte_amr_prepare) is read and `dev_out` (DEVICE, 32-byte aligned,
+   out_bytes >= fte_background_bytes(g_half)) receives the converted array.
+   EINVAL if g_half is FP32 with the cell layout.  Asynchronous on `stream`. */
 fte_status fte_quantize_background(const fte_grid* g_half, const float* dev_f32, void* dev_out,
                                    size_t out_bytes, void* stream);
 

@@ -14,6 +14,7 @@ FTE_REC = 24
 FTE_HREC = 32
 FTE_HHDR = 32
 FTE_F32, FTE_BF16, FTE_F16 = range(3)
+FTE_LAYOUT_CELL, FTE_LAYOUT_PAIR = 0, 1
 FTE_MAX_OBS = 8
 FTE_LEDGER = 8
 FTE_MAX_SETS = 64
@@ -31,7 +32,7 @@ class fte_grid(C.Structure):
                 ("n_snap", C.c_int32), ("periodic", C.c_int32),
                 ("t_snap0", C.c_double), ("dt_snap", C.c_double),
                 ("dtype", C.c_int32), ("amr_levels", C.c_int32), ("amr_bsize", C.c_int32),
-                ("n_leaves", C.c_int32), ("ring", C.c_int32), ("pad", C.c_int32)]
+                ("n_leaves", C.c_int32), ("ring", C.c_int32), ("layout", C.c_int32)]
 
 
 class fte_background(C.Structure):

@@ -28,10 +28,14 @@ def _stream(stream=None):
 DTYPES = {"f32": A.FTE_F32, "bf16": A.FTE_BF16, "f16": A.FTE_F16}
 
 
-def grid_c(g, dtype="f32", ring=0):
+LAYOUTS_REC = {"cell": A.FTE_LAYOUT_CELL, "pair": A.FTE_LAYOUT_PAIR}
+
+
+def grid_c(g, dtype="f32", ring=0, layout="cell"):
     c = A.fte_grid()
     c.dtype = DTYPES[dtype]
     c.ring = int(ring)
+    c.layout = LAYOUTS_REC[layout]
     c.nr, c.nth, c.nph = g.nr, g.nth, g.nph
     c.radial = 1 if g.radial == "log" else 0
     c.r_min, c.r_max, c.th_min, c.th_max = g.r_min, g.r_max, g.th_min, g.th_max
@@ -83,12 +87,14 @@ def observer_c(o):
 # device-memory holders
 # ---------------------------------------------------------------------------
 class Background:
-    """Device copy of a snapshot sequence (fte_background); dtype 'f32', 'bf16' or 'f16'."""
+    """Device copy of a snapshot sequence (fte_background); dtype 'f32', 'bf16' or 'f16';
+    record layout 'cell' or 'pair'."""
 
-    def __init__(self, grid, device="cuda", dtype="f32", ring=0):
+    def __init__(self, grid, device="cuda", dtype="f32", ring=0, layout="cell"):
         self.grid = grid
         self.dtype = dtype
-        self.gc = grid_c(grid, dtype, ring)
+        self.layout = layout
+        self.gc = grid_c(grid, dtype, ring, layout)
         nbytes = A.lib().fte_background_bytes(C.byref(self.gc))
         if nbytes == 0:
             raise ValueError("invalid grid")
@@ -97,10 +103,11 @@ class Background:
         self.c = A.fte_background(self.gc, self.dev.data_ptr(), None, None)
 
 
-def amr_grid_c(spec, n_leaves, dtype="f32", ring=0):
+def amr_grid_c(spec, n_leaves, dtype="f32", ring=0, layout="cell"):
     """fte_grid of an fte_inputs.amr.AmrSpec with n_leaves leaves."""
     c = A.fte_grid()
     c.ring = int(ring)
+    c.layout = LAYOUTS_REC[layout]
     B = spec.bsize
     c.nr, c.nth, c.nph = spec.nbr * B, spec.nbt * B, spec.nbp * B
     c.radial = 1 if spec.radial == "log" else 0
@@ -116,10 +123,11 @@ class AmrBackground(Background):
     """Device block-AMR background: padded leaf fields, leaves and finest-level table.
     A 16-bit copy shares the leaves and table of the FP32 background it is quantized from."""
 
-    def __init__(self, spec, leaves, device="cuda", dtype="f32", share=None, ring=0):
+    def __init__(self, spec, leaves, device="cuda", dtype="f32", share=None, ring=0, layout="cell"):
         self.grid = spec
         self.dtype = dtype
-        self.gc = amr_grid_c(spec, len(leaves), dtype, ring)
+        self.layout = layout
+        self.gc = amr_grid_c(spec, len(leaves), dtype, ring, layout)
         nbytes = A.lib().fte_background_bytes(C.byref(self.gc))
         if nbytes == 0:
             raise ValueError("invalid AMR grid: " + A.lib().fte_last_error().decode())
@@ -156,9 +164,12 @@ def fte_load_background(bg, host_fields, stream=None):
 
 
 def fte_quantize_background(bg_half, bg_f32, stream=None):
-    """Fill the 16-bit background bg_half from the FP32 background bg_f32 (same geometry)."""
-    if bg_f32.dtype != "f32" or bg_half.dtype == "f32":
-        raise ValueError("quantize from an f32 background into a bf16/f16 background")
+    """Fill bg_half (16-bit and/or pair layout) from the FP32 cell-layout background bg_f32
+    (same geometry)."""
+    if bg_f32.dtype != "f32" or getattr(bg_f32, "layout", "cell") != "cell":
+        raise ValueError("convert from an f32 cell-layout background")
+    if bg_half.dtype == "f32" and getattr(bg_half, "layout", "cell") == "cell":
+        raise ValueError("the target must be 16-bit or use the pair layout")
     if bg_half.gc.amr_levels != bg_f32.gc.amr_levels:
         raise ValueError("quantize between backgrounds of the same kind")
     check(A.lib().fte_quantize_background(C.byref(bg_half.gc), C.c_void_p(bg_f32.dev.data_ptr()),

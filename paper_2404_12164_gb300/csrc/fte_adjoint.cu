@@ -176,7 +176,7 @@ __device__ void step_vjp(const AdvanceArgs& a, float I, float rq, float rh, long
     Loc L;
     locate(g, r, th, ph, L);
     Fields<false> F;
-    gather<false, DT>(g, e, L, sc, F);
+    gather<false, DT, kLayAny>(g, e, L, sc, F);
     const float* B = F.f;
     const float* V = F.f + 3;
     const float* G = F.f + 6;
@@ -315,29 +315,13 @@ __device__ void step_vjp(const AdvanceArgs& a, float I, float rq, float rh, long
             const float wt_ = ct ? L.ft : 1.f - L.ft;
             const float wp_ = cp ? L.fp : 1.f - L.fp;
             const long long rec = (long long)snap * g.snap_recs + L.base[c];
+            float lo[FTE_NFIELD], hi[FTE_NFIELD];
+            corner_pair<DT, kLayAny>(g, rec, lo, hi);
             float dlo = 0.f, dhi = 0.f, vlo = 0.f, vhi = 0.f;
-            if (DT == FTE_F32) {
-                float q[2 * FTE_REC];
-                const float* src = g.fields + rec * FTE_REC;
 #pragma unroll
-                for (int m = 0; m < 2 * FTE_REC / 8; ++m) ldg8(src + 8 * m, q + 8 * m);
+            for (int m = 0; m < FTE_NFIELD; ++m) { dlo += Fb[m] * lo[m]; dhi += Fb[m] * hi[m]; }
 #pragma unroll
-                for (int m = 0; m < FTE_NFIELD; ++m) { dlo += Fb[m] * q[m]; dhi += Fb[m] * q[FTE_REC + m]; }
-#pragma unroll
-                for (int m = 0; m < 3; ++m) { vlo += dvb[m] * q[3 + m]; vhi += dvb[m] * q[FTE_REC + 3 + m]; }
-            } else {
-                uint32_t u[FTE_HREC];
-                const uint32_t* src = g.hfields + rec * (FTE_HREC / 2);
-#pragma unroll
-                for (int m = 0; m < FTE_HREC / 8; ++m) ldg8u(src + 8 * m, u + 8 * m);
-#pragma unroll
-                for (int m = 0; m < FTE_NFIELD; ++m) {
-                    const float lo = h_get<DT>(u, m), hi = h_get<DT>(u + FTE_HREC / 2, m);
-                    dlo += Fb[m] * lo;
-                    dhi += Fb[m] * hi;
-                    if (m >= 3 && m < 6) { vlo += dvb[m - 3] * lo; vhi += dvb[m - 3] * hi; }
-                }
-            }
+            for (int m = 0; m < 3; ++m) { vlo += dvb[m] * lo[3 + m]; vhi += dvb[m] * hi[3 + m]; }
             const float tlo = ws * dlo + (e.two ? sgn * vlo : 0.f);
             const float thi = ws * dhi + (e.two ? sgn * vhi : 0.f);
             frb += wt_ * wp_ * (thi - tlo);
@@ -394,7 +378,7 @@ __global__ void __launch_bounds__(256) adj_forward_kernel(const AdvanceArgs a, c
         for (; s < a.n_end; ++s) {
             const float r = sqrtf(x * x + y * y + z * z);
             J += (double)(w * a.prm.dt * smooth_k(k, r, p, k.t0 + (double)s * k.dt, nullptr, nullptr));
-            st = step<false, DT, kModeSingle>(a, a.prm, I, 0, s, pid, x, y, z, mu, p, w, nullptr, nullptr,
+            st = step<false, DT, kModeSingle, kLayAny>(a, a.prm, I, 0, s, pid, x, y, z, mu, p, w, nullptr, nullptr,
                                               nullptr, sc, noor);
             if (st != FTE_ALIVE) { ++s; break; }
         }
@@ -463,7 +447,7 @@ __global__ void __launch_bounds__(256, 2) adj_reverse_kernel(const AdvanceArgs a
             float* sp = k.scratch + ((size_t)(s - n0) * 5) * nthr + tid;
             sp[0] = x; sp[nthr] = y; sp[2 * nthr] = z; sp[3 * nthr] = mu; sp[4 * nthr] = p;
             if (s + 1 < n1)
-                step<false, DT, kModeSingle>(a, a.prm, I, 0, s, pid, x, y, z, mu, p, w, nullptr, nullptr, nullptr,
+                step<false, DT, kModeSingle, kLayAny>(a, a.prm, I, 0, s, pid, x, y, z, mu, p, w, nullptr, nullptr, nullptr,
                                              sc, noor);
         }
         for (long long s = n1 - 1; s >= n0; --s) {

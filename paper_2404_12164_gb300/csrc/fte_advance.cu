@@ -5,23 +5,30 @@
 
 namespace fte {
 
-static const void* advance_fn(int kperp, int dtype, int mode, int nt)
+template <int LAY>
+static const void* single_fn(int kperp, int dtype)
+{
+    if (dtype == FTE_BF16)
+        return kperp ? (const void*)advance_kernel<true, FTE_BF16, kModeSingle, kThreads, LAY>
+                     : (const void*)advance_kernel<false, FTE_BF16, kModeSingle, kThreads, LAY>;
+    if (dtype == FTE_F16)
+        return kperp ? (const void*)advance_kernel<true, FTE_F16, kModeSingle, kThreads, LAY>
+                     : (const void*)advance_kernel<false, FTE_F16, kModeSingle, kThreads, LAY>;
+    return kperp ? (const void*)advance_kernel<true, FTE_F32, kModeSingle, kThreads, LAY>
+                 : (const void*)advance_kernel<false, FTE_F32, kModeSingle, kThreads, LAY>;
+}
+
+// the single-set kernels come in one variant per record layout (pair: 1)
+static const void* advance_fn(int kperp, int dtype, int mode, int nt, int pair)
 {
     if (mode != kModeSingle) return advance_fn_batched(kperp, dtype, mode, nt);
     if (nt != kThreads) return nullptr;
-    if (dtype == FTE_BF16)
-        return kperp ? (const void*)advance_kernel<true, FTE_BF16, kModeSingle, kThreads>
-                     : (const void*)advance_kernel<false, FTE_BF16, kModeSingle, kThreads>;
-    if (dtype == FTE_F16)
-        return kperp ? (const void*)advance_kernel<true, FTE_F16, kModeSingle, kThreads>
-                     : (const void*)advance_kernel<false, FTE_F16, kModeSingle, kThreads>;
-    return kperp ? (const void*)advance_kernel<true, FTE_F32, kModeSingle, kThreads>
-                 : (const void*)advance_kernel<false, FTE_F32, kModeSingle, kThreads>;
+    return pair ? single_fn<kLayPair>(kperp, dtype) : single_fn<kLayCell>(kperp, dtype);
 }
 
-cudaError_t advance_occupancy(int kperp, int dtype, int mode, int nt, size_t smem, int* blocks_per_sm)
+cudaError_t advance_occupancy(int kperp, int dtype, int mode, int nt, int pair, size_t smem, int* blocks_per_sm)
 {
-    const void* fn = advance_fn(kperp, dtype, mode, nt);
+    const void* fn = advance_fn(kperp, dtype, mode, nt, pair);
     if (!fn) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -32,14 +39,10 @@ cudaError_t launch_advance(const AdvanceArgs& a, const BatchArgs& b, int kperp, 
                            size_t smem, cudaStream_t s)
 {
     if (mode != kModeSingle) return launch_advance_batched(a, b, kperp, mode, nt, blocks, smem, s);
-    if (nt != kThreads) return cudaErrorInvalidValue;
-    const int dt = a.g.dtype;
-#define FTE_LAUNCH(K, D) advance_kernel<K, D, kModeSingle, kThreads><<<blocks, kThreads, smem, s>>>(a, b)
-    if (dt == FTE_BF16) { if (kperp) FTE_LAUNCH(true, FTE_BF16); else FTE_LAUNCH(false, FTE_BF16); }
-    else if (dt == FTE_F16) { if (kperp) FTE_LAUNCH(true, FTE_F16); else FTE_LAUNCH(false, FTE_F16); }
-    else { if (kperp) FTE_LAUNCH(true, FTE_F32); else FTE_LAUNCH(false, FTE_F32); }
-#undef FTE_LAUNCH
-    return cudaGetLastError();
+    const void* fn = advance_fn(kperp, a.g.dtype, mode, nt, a.g.pair);
+    if (!fn) return cudaErrorInvalidValue;
+    void* args[] = {(void*)&a, (void*)&b};
+    return cudaLaunchKernel(fn, dim3(blocks), dim3(nt), args, smem, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -84,39 +87,82 @@ __device__ __forceinline__ uint32_t encode16(float v)
     return (uint32_t)__half_as_ushort(__float2half_rn(v));
 }
 
-template <int DT>
-__global__ void __launch_bounds__(256) encode_kernel(const float* __restrict__ f, long long nrec,
+// 16-bit records: cell layout (18 values, padded to FTE_HREC) or pair layout
+// (the cell's 18 values, then those of its upper r-neighbour - zero at the end of
+// an r-row of `row` cells - padded to kPairHRec).
+template <int DT, bool PAIR>
+__global__ void __launch_bounds__(256) encode_kernel(const float* __restrict__ f, long long nrec, int row,
                                                      const float* __restrict__ hdr, uint32_t* out)
+{
+    constexpr int kWords = (PAIR ? kPairHRec : FTE_HREC) / 2;
+    const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nrec) return;
+    uint32_t w[kWords];
+#pragma unroll
+    for (int k = 0; k < kWords; ++k) w[k] = 0u;
+    const bool hi_in_row = (r % row) != row - 1;
+#pragma unroll
+    for (int c = 0; c < (PAIR ? 2 : 1); ++c) {
+        if (c == 1 && !hi_in_row) break;
+        float a[FTE_REC];
+#pragma unroll
+        for (int q = 0; q < FTE_REC / 8; ++q) ldg8(f + (r + c) * FTE_REC + 8 * q, a + 8 * q);
+#pragma unroll
+        for (int k = 0; k < FTE_NFIELD; ++k) {
+            const uint32_t h = encode16<DT>(__fdiv_rn(a[k], __ldg(hdr + k)));
+            const int slot = c * FTE_NFIELD + k;
+            w[slot >> 1] |= (slot & 1) ? (h << 16) : h;
+        }
+    }
+    uint4* o = reinterpret_cast<uint4*>(out + r * kWords);
+#pragma unroll
+    for (int q = 0; q < kWords / 4; ++q) o[q] = make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
+}
+
+// FP32 pair records from FP32 cell records.
+__global__ void __launch_bounds__(256) pair_f32_kernel(const float* __restrict__ f, long long nrec, int row,
+                                                       float* out)
 {
     const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= nrec) return;
-    float a[FTE_REC];
+    float a[kPairRec];
 #pragma unroll
-    for (int q = 0; q < FTE_REC / 8; ++q) ldg8(f + r * FTE_REC + 8 * q, a + 8 * q);
-    uint32_t w[FTE_HREC / 2];
+    for (int k = 0; k < kPairRec; ++k) a[k] = 0.f;
+    float b[FTE_REC];
 #pragma unroll
-    for (int k = 0; k < FTE_HREC / 2; ++k) w[k] = 0u;
+    for (int q = 0; q < FTE_REC / 8; ++q) ldg8(f + r * FTE_REC + 8 * q, b + 8 * q);
 #pragma unroll
-    for (int k = 0; k < FTE_NFIELD; ++k) {
-        const uint32_t h = encode16<DT>(__fdiv_rn(a[k], __ldg(hdr + k)));
-        w[k >> 1] |= (k & 1) ? (h << 16) : h;
+    for (int k = 0; k < FTE_NFIELD; ++k) a[k] = b[k];
+    if ((r % row) != row - 1) {
+#pragma unroll
+        for (int q = 0; q < FTE_REC / 8; ++q) ldg8(f + (r + 1) * FTE_REC + 8 * q, b + 8 * q);
+#pragma unroll
+        for (int k = 0; k < FTE_NFIELD; ++k) a[FTE_NFIELD + k] = b[k];
     }
-    uint4* o = reinterpret_cast<uint4*>(out + r * (FTE_HREC / 2));
+    float4* o = reinterpret_cast<float4*>(out + r * kPairRec);
 #pragma unroll
-    for (int q = 0; q < FTE_HREC / 8; ++q) o[q] = make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
+    for (int q = 0; q < kPairRec / 4; ++q) o[q] = make_float4(a[4 * q], a[4 * q + 1], a[4 * q + 2], a[4 * q + 3]);
 }
 
-cudaError_t launch_quantize(const float* f32, long long nrec, int dtype, void* out, cudaStream_t s)
+cudaError_t launch_quantize(const float* f32, long long nrec, int row, int dtype, int pair, void* out,
+                            cudaStream_t s)
 {
+    const long long blocks = (nrec + 255) / 256;
+    if (dtype == FTE_F32) {
+        if (!pair) return cudaErrorInvalidValue;
+        pair_f32_kernel<<<(unsigned)blocks, 256, 0, s>>>(f32, nrec, row, reinterpret_cast<float*>(out));
+        return cudaGetLastError();
+    }
     float* hdr = reinterpret_cast<float*>(out);
     uint32_t* recs = reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(out) + FTE_HHDR * sizeof(float));
     cudaError_t e = cudaMemsetAsync(hdr, 0, FTE_HHDR * sizeof(float), s);
     if (e != cudaSuccess) return e;
     maxabs_kernel<<<1216, 256, 0, s>>>(f32, nrec, reinterpret_cast<unsigned*>(hdr));
     scale_final_kernel<<<1, 32, 0, s>>>(hdr);
-    const long long blocks = (nrec + 255) / 256;
-    if (dtype == FTE_BF16) encode_kernel<FTE_BF16><<<(unsigned)blocks, 256, 0, s>>>(f32, nrec, hdr, recs);
-    else encode_kernel<FTE_F16><<<(unsigned)blocks, 256, 0, s>>>(f32, nrec, hdr, recs);
+#define FTE_ENC(D, P) encode_kernel<D, P><<<(unsigned)blocks, 256, 0, s>>>(f32, nrec, row, hdr, recs)
+    if (dtype == FTE_BF16) { if (pair) FTE_ENC(FTE_BF16, true); else FTE_ENC(FTE_BF16, false); }
+    else { if (pair) FTE_ENC(FTE_F16, true); else FTE_ENC(FTE_F16, false); }
+#undef FTE_ENC
     return cudaGetLastError();
 }
 

@@ -52,6 +52,8 @@ fte_status check_grid(const fte_grid* g)
         return fail(FTE_EINVAL, "dtype must be FTE_F32, FTE_BF16 or FTE_F16");
     if (g->ring != 0 && (g->ring < 2 || g->ring > g->n_snap))
         return fail(FTE_EINVAL, "ring must be 0 or in [2, n_snap]");
+    if (g->layout != FTE_LAYOUT_CELL && g->layout != FTE_LAYOUT_PAIR)
+        return fail(FTE_EINVAL, "layout must be FTE_LAYOUT_CELL or FTE_LAYOUT_PAIR");
     if (g->amr_levels < 0 || g->amr_levels > 4) return fail(FTE_EINVAL, "amr_levels must be in [0, 4]");
     if (g->amr_levels > 0) {
         const int B = g->amr_bsize;
@@ -87,17 +89,29 @@ size_t grid_records(const fte_grid* g)
     return snapshot_records(g) * (size_t)resident_snapshots(g);
 }
 
+// bytes of one stored record for the grid's dtype and layout
+size_t record_bytes(const fte_grid* g)
+{
+    const bool pair = g->layout == FTE_LAYOUT_PAIR;
+    if (g->dtype == FTE_F32) return (pair ? kPairRec : FTE_REC) * sizeof(float);
+    return (pair ? kPairHRec : FTE_HREC) * sizeof(uint16_t);
+}
+
 size_t grid_bytes(const fte_grid* g)
 {
-    if (g->dtype == FTE_F32) return grid_records(g) * FTE_REC * sizeof(float);
-    return FTE_HHDR * sizeof(float) + grid_records(g) * FTE_HREC * sizeof(uint16_t);
+    const size_t head = g->dtype == FTE_F32 ? 0 : FTE_HHDR * sizeof(float);
+    return head + grid_records(g) * record_bytes(g);
 }
+
+// cells per r-row of the stored lattice (the pair layout pairs within a row)
+int row_cells(const fte_grid* g) { return g->amr_levels > 0 ? g->amr_bsize + 2 : g->nr; }
 
 GridK make_gridk(const fte_background* bg)
 {
     const fte_grid& g = bg->grid;
     GridK k;
     k.dtype = g.dtype;
+    k.pair = g.layout == FTE_LAYOUT_PAIR ? 1 : 0;
     k.fields = bg->fields;
     k.scale = bg->fields;
     k.hfields = reinterpret_cast<const uint32_t*>(bg->fields + FTE_HHDR);
@@ -210,7 +224,7 @@ int device_sms(int device)
     return cache[device];
 }
 
-fte_status layout(int device, int kperp, int dtype, size_t nbins, long long n_steps,
+fte_status layout(int device, int kperp, int dtype, int pair, size_t nbins, long long n_steps,
                   size_t sort_bytes, WsLayout* L)
 {
     const int sms = device_sms(device);
@@ -220,7 +234,7 @@ fte_status layout(int device, int kperp, int dtype, size_t nbins, long long n_st
     int cur = 0;
     FTE_CUDA(cudaGetDevice(&cur), "cudaGetDevice");
     if (cur != device) FTE_CUDA(cudaSetDevice(device), "cudaSetDevice");
-    cudaError_t e = advance_occupancy(kperp, dtype, kModeSingle, kThreads, smem, &per_sm);
+    cudaError_t e = advance_occupancy(kperp, dtype, kModeSingle, kThreads, pair, smem, &per_sm);
     if (cur != device) cudaSetDevice(cur);
     if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
     if (per_sm < 1) return fail(FTE_ENOTSUP, "step kernel does not fit on an SM with %zu bytes of tally", smem);
@@ -293,7 +307,8 @@ fte_status fte_amr_prepare(const fte_background* bg, void* stream)
     fte_status s = check_background(bg);
     if (s != FTE_OK) return s;
     if (bg->grid.amr_levels < 1) return fail(FTE_EINVAL, "not an AMR background");
-    if (bg->grid.dtype != FTE_F32) return fail(FTE_EINVAL, "prepare the FP32 background, then quantize it");
+    if (bg->grid.dtype != FTE_F32 || bg->grid.layout != FTE_LAYOUT_CELL)
+        return fail(FTE_EINVAL, "prepare the FP32 cell-layout background, then convert it");
     const GridK g = make_gridk(bg);
     cudaStream_t st = (cudaStream_t)stream;
     const size_t nt = (size_t)g.nf0 * g.nf1 * g.nf2;
@@ -315,14 +330,15 @@ fte_status fte_quantize_background(const fte_grid* g_half, const float* dev_f32,
 {
     fte_status s = check_grid(g_half);
     if (s != FTE_OK) return s;
-    if (g_half->dtype != FTE_BF16 && g_half->dtype != FTE_F16)
-        return fail(FTE_EINVAL, "quantization target must be FTE_BF16 or FTE_F16");
+    if (g_half->dtype == FTE_F32 && g_half->layout == FTE_LAYOUT_CELL)
+        return fail(FTE_EINVAL, "conversion target must be 16-bit or use the pair layout");
     if (!dev_f32 || !dev_out) return fail(FTE_EINVAL, "NULL field pointer");
     if ((uintptr_t)dev_f32 % 32 || (uintptr_t)dev_out % 32) return fail(FTE_EINVAL, "arrays must be 32-byte aligned");
     const size_t need = grid_bytes(g_half);
     if (out_bytes < need) return fail(FTE_ENOMEM, "output buffer has %zu bytes, needs %zu", out_bytes, need);
-    FTE_CUDA(launch_quantize(dev_f32, (long long)grid_records(g_half), g_half->dtype, dev_out,
-                             (cudaStream_t)stream), "quantize launch");
+    FTE_CUDA(launch_quantize(dev_f32, (long long)grid_records(g_half), row_cells(g_half), g_half->dtype,
+                             g_half->layout == FTE_LAYOUT_PAIR, dev_out, (cudaStream_t)stream),
+             "conversion launch");
     return FTE_OK;
 }
 
@@ -367,11 +383,12 @@ size_t fte_workspace_bytes(int device, const fte_grid* g, const fte_tally_buf* t
     const size_t sort_bytes = sort_scratch_bytes(make_gridk(&tmp), n_particles);
     size_t best = 0;
     for (int dtype = FTE_F32; dtype <= FTE_F16; ++dtype)
-        for (int kperp = 0; kperp < 2; ++kperp) {
-            WsLayout L;
-            if (layout(device, kperp, dtype, nb, n_steps, sort_bytes, &L) != FTE_OK) return 0;
-            if (L.total > best) best = L.total;
-        }
+        for (int kperp = 0; kperp < 2; ++kperp)
+            for (int pair = 0; pair < 2; ++pair) {
+                WsLayout L;
+                if (layout(device, kperp, dtype, pair, nb, n_steps, sort_bytes, &L) != FTE_OK) return 0;
+                if (L.total > best) best = L.total;
+            }
     return best;
 }
 
@@ -465,7 +482,7 @@ fte_status fte_advance(fte_particles* P, const fte_background* bg, const fte_par
     const GridK gk = make_gridk(bg);
     const int sorting = prm->sort_every > 0;
     WsLayout L;
-    s = layout(device, kperp, bg->grid.dtype, nb, nsteps, sorting ? sort_scratch_bytes(gk, P->count) : 0, &L);
+    s = layout(device, kperp, bg->grid.dtype, gk.pair, nb, nsteps, sorting ? sort_scratch_bytes(gk, P->count) : 0, &L);
     if (s != FTE_OK) return s;
     if (ws_bytes < L.total) return fail(FTE_ENOMEM, "workspace has %zu bytes, needs %zu", ws_bytes, L.total);
     char* w = (char*)ws;
@@ -529,7 +546,8 @@ fte_status fte_advance(fte_particles* P, const fte_background* bg, const fte_par
     const long long chunk = sorting ? (prm->sort_every < kChunkSteps ? prm->sort_every : kChunkSteps) : kChunkSteps;
     const size_t smem = 3 * sizeof(float) * (size_t)a.nbins;
     int per_sm = 0;
-    FTE_CUDA(advance_occupancy(kperp, bg->grid.dtype, kModeSingle, kThreads, smem, &per_sm), "occupancy");
+    FTE_CUDA(advance_occupancy(kperp, bg->grid.dtype, kModeSingle, kThreads, bg->grid.layout == FTE_LAYOUT_PAIR,
+                                smem, &per_sm), "occupancy");
 
     for (long long c0 = n_start; c0 < n_end; c0 += chunk) {
         a.n_start = c0;
@@ -724,7 +742,8 @@ extern "C" fte_status fte_advance_noalloc(fte_particles* P, const fte_background
                     nb, part_block, kNoAllocBytes, sms);
     const size_t smem = part_block;
     int per_sm = 0;
-    FTE_CUDA(advance_occupancy(kperp, bg->grid.dtype, kModeSingle, kThreads, smem, &per_sm), "occupancy");
+    FTE_CUDA(advance_occupancy(kperp, bg->grid.dtype, kModeSingle, kThreads, bg->grid.layout == FTE_LAYOUT_PAIR,
+                                smem, &per_sm), "occupancy");
     if (per_sm < 1) return fail(FTE_ENOTSUP, "step kernel does not fit on an SM with %zu bytes of tally", smem);
     long long max_blocks = (long long)sms * per_sm;
     if ((size_t)max_blocks > fit) max_blocks = (long long)fit;
@@ -815,7 +834,7 @@ fte_status ens_layout(int device, int kperp, int dtype, int mode, int nt, int n_
     int per_sm = 0, cur = 0;
     FTE_CUDA(cudaGetDevice(&cur), "cudaGetDevice");
     if (cur != device) FTE_CUDA(cudaSetDevice(device), "cudaSetDevice");
-    cudaError_t e = advance_occupancy(kperp, dtype, mode, nt, smem, &per_sm);
+    cudaError_t e = advance_occupancy(kperp, dtype, mode, nt, 0, smem, &per_sm);
     if (cur != device) cudaSetDevice(cur);
     if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
     if (per_sm < 1) return fail(FTE_ENOTSUP, "ensemble step kernel does not fit on an SM with %zu bytes of tally", smem);
@@ -1518,7 +1537,8 @@ fte_status check_stream(const fte_background* bg, const void* host_snapshots, co
     fte_status s = check_background(bg);
     if (s != FTE_OK) return s;
     if (bg->grid.ring < 2) return fail(FTE_EINVAL, "streaming needs a ring background (grid.ring >= 2)");
-    if (bg->grid.dtype != FTE_F32) return fail(FTE_ENOTSUP, "streaming supports FP32 snapshots");
+    if (bg->grid.dtype != FTE_F32 || bg->grid.layout != FTE_LAYOUT_CELL)
+        return fail(FTE_ENOTSUP, "streaming supports FP32 cell-layout snapshots");
     if (!host_snapshots || !slot_state) return fail(FTE_EINVAL, "NULL argument");
     return FTE_OK;
 }
@@ -1530,7 +1550,7 @@ extern "C" {
 size_t fte_snapshot_bytes(const fte_grid* g)
 {
     if (check_grid(g) != FTE_OK) return 0;
-    return snapshot_records(g) * (g->dtype == FTE_F32 ? FTE_REC * sizeof(float) : FTE_HREC * sizeof(uint16_t));
+    return snapshot_records(g) * record_bytes(g);
 }
 
 fte_status fte_stream_plan(const fte_grid* g, const fte_params* prm, int64_t n_start, int64_t n_end,

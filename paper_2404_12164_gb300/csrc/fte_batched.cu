@@ -10,13 +10,13 @@ template <int MODE, int NT>
 static const void* pick(int kperp, int dtype)
 {
     if (dtype == FTE_BF16)
-        return kperp ? (const void*)advance_kernel<true, FTE_BF16, MODE, NT>
-                     : (const void*)advance_kernel<false, FTE_BF16, MODE, NT>;
+        return kperp ? (const void*)advance_kernel<true, FTE_BF16, MODE, NT, kLayAny>
+                     : (const void*)advance_kernel<false, FTE_BF16, MODE, NT, kLayAny>;
     if (dtype == FTE_F16)
-        return kperp ? (const void*)advance_kernel<true, FTE_F16, MODE, NT>
-                     : (const void*)advance_kernel<false, FTE_F16, MODE, NT>;
-    return kperp ? (const void*)advance_kernel<true, FTE_F32, MODE, NT>
-                 : (const void*)advance_kernel<false, FTE_F32, MODE, NT>;
+        return kperp ? (const void*)advance_kernel<true, FTE_F16, MODE, NT, kLayAny>
+                     : (const void*)advance_kernel<false, FTE_F16, MODE, NT, kLayAny>;
+    return kperp ? (const void*)advance_kernel<true, FTE_F32, MODE, NT, kLayAny>
+                 : (const void*)advance_kernel<false, FTE_F32, MODE, NT, kLayAny>;
 }
 
 const void* advance_fn_batched(int kperp, int dtype, int mode, int nt)

@@ -24,6 +24,8 @@ constexpr float kTwoPi = 6.28318530717959f;
 constexpr float kCau = 2.003988804e-3f;      // speed of light, au/s
 constexpr float kMc2 = 938.27208816f;        // proton rest energy, MeV
 constexpr int kThreads = 256;                // threads per block of the step kernel
+constexpr int kPairRec = 40;                 // floats of an FP32 pair record
+constexpr int kPairHRec = 48;                // 16-bit values of a 16-bit pair record
 
 // ---------------------------------------------------------------------------
 // Kernel-side descriptions (passed by value in the kernel parameter space)
@@ -34,6 +36,7 @@ struct GridK {
     const float* scale;      // 16-bit: per-field scales (FTE_HHDR floats)
     long long snap_recs;     // records per snapshot
     int dtype;
+    int pair;                // 1: FTE_LAYOUT_PAIR records (cell k and k + 1 in one record)
     int nr, nth, nph, radial;
     float r_min, r_max, th_min, th_max;
     float cos_th_min, cos_th_max;
@@ -326,12 +329,61 @@ struct Fields {
     float dBa[KPERP ? 9 : 1];  // dB_i / d(weight axis a), a = r, theta, phi
 };
 
+// The stored fields of the two r-neighbours of one corner pair: record `rec` and
+// the next one (cell layout: six or four 32-byte loads) or the one pair record
+// (five or three); 16-bit values are returned unscaled.
+// Record layout of a kernel: fixed at compile time, or read from the grid.
+constexpr int kLayCell = 0, kLayPair = 1, kLayAny = 2;
+
+template <int DT, int LAY>
+__device__ __forceinline__ void corner_pair(const GridK& g, long long rec, float* lo, float* hi)
+{
+    const bool pair = LAY == kLayAny ? g.pair != 0 : LAY == kLayPair;
+    if (DT == FTE_F32) {
+        if (pair) {
+            float a[kPairRec];
+            const float* q = g.fields + rec * kPairRec;
+#pragma unroll
+            for (int m = 0; m < kPairRec / 8; ++m) ldg8(q + 8 * m, a + 8 * m);
+#pragma unroll
+            for (int m = 0; m < FTE_NFIELD; ++m) { lo[m] = a[m]; hi[m] = a[FTE_NFIELD + m]; }
+        } else {
+            float a[2 * FTE_REC];
+            const float* q = g.fields + rec * FTE_REC;
+#pragma unroll
+            for (int m = 0; m < 2 * FTE_REC / 8; ++m) ldg8(q + 8 * m, a + 8 * m);
+#pragma unroll
+            for (int m = 0; m < FTE_NFIELD; ++m) { lo[m] = a[m]; hi[m] = a[FTE_REC + m]; }
+        }
+    } else if (pair) {
+        uint32_t u[kPairHRec / 2];
+        const uint32_t* q = g.hfields + rec * (kPairHRec / 2);
+#pragma unroll
+        for (int m = 0; m < kPairHRec / 16; ++m) ldg8u(q + 8 * m, u + 8 * m);
+#pragma unroll
+        for (int m = 0; m < FTE_NFIELD; ++m) {
+            lo[m] = h_get<DT>(u, m);
+            hi[m] = h_get<DT>(u, FTE_NFIELD + m);
+        }
+    } else {
+        uint32_t u[FTE_HREC];      // two records of FTE_HREC / 2 words
+        const uint32_t* q = g.hfields + rec * (FTE_HREC / 2);
+#pragma unroll
+        for (int m = 0; m < FTE_HREC / 8; ++m) ldg8u(q + 8 * m, u + 8 * m);
+#pragma unroll
+        for (int m = 0; m < FTE_NFIELD; ++m) {
+            lo[m] = h_get<DT>(u, m);
+            hi[m] = h_get<DT>(u + FTE_HREC / 2, m);
+        }
+    }
+}
+
 // Trilinear (space) x linear (time) interpolation: for each snapshot and each
 // of the 4 (theta, phi) corners, the two r-neighbours are one contiguous block
 // (FP32: 192 bytes = six 32-byte loads; 16-bit: 128 bytes = four).  For 16-bit
 // storage the sums run over the stored values and the per-field scales `sc`
 // are applied once at the end.
-template <bool KPERP, int DT>
+template <bool KPERP, int DT, int LAY>
 __device__ __forceinline__ void gather(const GridK& g, const StepEntry& e, const Loc& L,
                                        const float* sc, Fields<KPERP>& F)
 {
@@ -356,24 +408,7 @@ __device__ __forceinline__ void gather(const GridK& g, const StepEntry& e, const
             const float wjk = wt_ * wp_;
             const long long rec = (long long)snap * g.snap_recs + L.base[c];
             float lo[FTE_NFIELD], hi[FTE_NFIELD];
-            if (DT == FTE_F32) {
-                float a[2 * FTE_REC];
-                const float* q = g.fields + rec * FTE_REC;
-#pragma unroll
-                for (int m = 0; m < 2 * FTE_REC / 8; ++m) ldg8(q + 8 * m, a + 8 * m);
-#pragma unroll
-                for (int m = 0; m < FTE_NFIELD; ++m) { lo[m] = a[m]; hi[m] = a[FTE_REC + m]; }
-            } else {
-                uint32_t u[FTE_HREC];      // two records of FTE_HREC / 2 words
-                const uint32_t* q = g.hfields + rec * (FTE_HREC / 2);
-#pragma unroll
-                for (int m = 0; m < FTE_HREC / 8; ++m) ldg8u(q + 8 * m, u + 8 * m);
-#pragma unroll
-                for (int m = 0; m < FTE_NFIELD; ++m) {
-                    lo[m] = h_get<DT>(u, m);
-                    hi[m] = h_get<DT>(u + FTE_HREC / 2, m);
-                }
-            }
+            corner_pair<DT, LAY>(g, rec, lo, hi);
             const float c0 = (1.f - L.fr) * wjk, c1 = L.fr * wjk;
             const float w0 = ws * c0, w1 = ws * c1;
 #pragma unroll

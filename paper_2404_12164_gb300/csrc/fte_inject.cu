@@ -75,12 +75,13 @@ __global__ void __launch_bounds__(256) inject_kernel(const InjectArgs a)
                     ri = (long long)a.divv_snap * g.snap_recs + ((long long)ck * g.nth + cj) * g.nr + ci;
                 }
                 float g00, g11, g22;
+                // the cell's own fields lead its record in either layout
                 if (g.dtype == FTE_F32) {
-                    const float* rec = g.fields + ri * FTE_REC;
+                    const float* rec = g.fields + ri * (g.pair ? kPairRec : FTE_REC);
                     g00 = __ldg(rec + 6); g11 = __ldg(rec + 10); g22 = __ldg(rec + 14);
                 } else {
                     // stored value times its field scale, rounded once
-                    const uint32_t* rec = g.hfields + ri * (FTE_HREC / 2);
+                    const uint32_t* rec = g.hfields + ri * ((g.pair ? kPairHRec : FTE_HREC) / 2);
                     const uint32_t w3 = __ldg(rec + 3), w5 = __ldg(rec + 5), w7 = __ldg(rec + 7);
                     const bool bf = g.dtype == FTE_BF16;
                     g00 = __fmul_rn(bf ? h_lo<FTE_BF16>(w3) : h_lo<FTE_F16>(w3), __ldg(g.scale + 6));

@@ -127,7 +127,8 @@ struct AdjK {
 // step kernel of (kperp, dtype, mode, threads per block); nt is 256 for kModeSingle
 cudaError_t launch_advance(const AdvanceArgs& a, const BatchArgs& b, int kperp, int mode, int nt, int blocks,
                            size_t smem, cudaStream_t s);
-cudaError_t advance_occupancy(int kperp, int dtype, int mode, int nt, size_t smem, int* blocks_per_sm);
+// resident blocks per SM of a step kernel (`pair`: record layout of a single-set kernel)
+cudaError_t advance_occupancy(int kperp, int dtype, int mode, int nt, int pair, size_t smem, int* blocks_per_sm);
 // the ensemble variants live in their own translation unit (fte_batched.cu)
 const void* advance_fn_batched(int kperp, int dtype, int mode, int nt);
 cudaError_t launch_advance_batched(const AdvanceArgs& a, const BatchArgs& b, int kperp, int mode, int nt,
@@ -165,7 +166,9 @@ cudaError_t launch_amr_ghosts(const GridK& g, int n_snap, double r_min, double r
 // random-sector read probe (fte_probe.cu)
 cudaError_t launch_probe(const float* buf, unsigned long long nsec, int threads, int loads, float* out,
                          cudaStream_t s);
-// 16-bit storage: scale header + records of `nrec` FP32 records into `out`
-cudaError_t launch_quantize(const float* f32, long long nrec, int dtype, void* out, cudaStream_t s);
+// storage conversion of `nrec` FP32 cell records (r-rows of `row` cells): 16-bit
+// (scale header + records) in the cell or pair layout, or FP32 pair records
+cudaError_t launch_quantize(const float* f32, long long nrec, int row, int dtype, int pair, void* out,
+                            cudaStream_t s);
 
 }  // namespace fte

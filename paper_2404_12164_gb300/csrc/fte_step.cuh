@@ -61,7 +61,7 @@ __device__ __forceinline__ void warp_tally_global(double* S, double* S2, unsigne
 
 // One Euler-Maruyama step of Eqs. 2-4 for one particle (Sec. 2.1), with the
 // background interpolated at the start-of-step position and time (Sec. 2.4).
-template <bool KPERP, int DT, int MODE>
+template <bool KPERP, int DT, int MODE, int LAY>
 __device__ __forceinline__ int step(const AdvanceArgs& a, const ParamsK& prm, float I, int sbin,
                                     long long n, uint32_t pid,
                                     float& x, float& y, float& z, float& mu, float& p, float w,
@@ -84,7 +84,7 @@ __device__ __forceinline__ int step(const AdvanceArgs& a, const ParamsK& prm, fl
     Loc L;
     locate(a.g, r, th, ph, L);
     Fields<KPERP> F;
-    gather<KPERP, DT>(a.g, e, L, sc, F);
+    gather<KPERP, DT, LAY>(a.g, e, L, sc, F);
     const float* B = F.f;
     const float* V = F.f + 3;
     const float* G = F.f + 6;
@@ -237,7 +237,9 @@ __device__ __forceinline__ int set_of(const unsigned long long* end, int n_sets,
 // MODE kModeSingle: one parameter set, tally in shared memory; kModeShared: an
 // ensemble (per-set parameters and tallies, the tallies of all sets in shared
 // memory); kModeGlobal: an ensemble with warp-merged FP64 atomics to the tally.
-template <bool KPERP, int DT, int MODE, int NT>
+// LAY: record layout, compile-time for the single-set kernels, read from the
+// grid (kLayAny) by the ensemble kernels.
+template <bool KPERP, int DT, int MODE, int NT, int LAY>
 __global__ void __launch_bounds__(NT, MODE == kModeSingle ? 0 : 512 / NT) advance_kernel(const AdvanceArgs a, const BatchArgs b)
 {
     extern __shared__ float sh[];
@@ -276,7 +278,7 @@ __global__ void __launch_bounds__(NT, MODE == kModeSingle ? 0 : 512 / NT) advanc
         if (MODE == kModeSingle) {
             for (long long n = a.n_start; n < a.n_end; ++n) {
                 ++nsteps;
-                st = step<KPERP, DT, MODE>(a, a.prm, I0, 0, n, pid, x, y, z, mu, p, w, shS, shS2, shC, sc, noor);
+                st = step<KPERP, DT, MODE, LAY>(a, a.prm, I0, 0, n, pid, x, y, z, mu, p, w, shS, shS2, shC, sc, noor);
                 if (st != FTE_ALIVE) break;
             }
         } else {
@@ -292,7 +294,7 @@ __global__ void __launch_bounds__(NT, MODE == kModeSingle ? 0 : 512 / NT) advanc
             const int sbin = s * a.nbins;
             for (long long n = a.n_start; n < a.n_end; ++n) {
                 ++nsteps;
-                st = step<KPERP, DT, MODE>(a, prm, I, sbin, n, pid, x, y, z, mu, p, w, shS, shS2, shC, sc, noor);
+                st = step<KPERP, DT, MODE, LAY>(a, prm, I, sbin, n, pid, x, y, z, mu, p, w, shS, shS2, shC, sc, noor);
                 if (st != FTE_ALIVE) break;
             }
         }
