@@ -61,6 +61,34 @@ def _dist():
     return ws, rank, local
 
 
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "advance_kernel_traffic.json")
+KERNEL_SOURCES = ("fte_advance.cu", "fte_device.cuh", "fte_kernels.cuh", "fte_step.cuh")
+
+
+def kernel_sources_hash():
+    """sha256 of the step kernel's sources: DRAM traffic measured by ncu is reported only while
+    the kernel it was measured on is unchanged."""
+    import hashlib
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2404_12164_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def measured_traffic(layout):
+    """DRAM bytes per step-kernel launch from the committed ncu summary, or None when the kernel
+    sources changed since, or the summary is for another record layout."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if d.get("sources_sha256") != kernel_sources_hash() or d.get("record_layout") != layout:
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -121,6 +149,22 @@ class Clocks:
         return {"sm_mhz": statistics.median(load) if load else None,
                 "sm_max_mhz": max(smax) if smax else None,
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def device_background(api, w, fields, layout):
+    """The workload's background on the device in the given record layout (converted on the
+    device from the FP32 cell records)."""
+    import torch
+    cell = api.Background(w.grid)
+    api.fte_load_background(cell, torch.from_numpy(np.ascontiguousarray(fields)))
+    if layout == "cell":
+        return cell
+    bg = api.Background(w.grid, layout=layout)
+    api.fte_quantize_background(bg, cell)
+    torch.cuda.synchronize()
+    del cell
+    torch.cuda.empty_cache()
+    return bg
 
 
 def build_workload():
@@ -310,7 +354,9 @@ def run_gpu(args):
                 "d2h_bytes_per_step": int(out_host.nbytes + 2 * 8 * A.FTE_LEDGER)},
         "gpu_launches": launches_per_step * args.steps,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak, "traffic": measured_traffic(args.layout),
+                     "traffic_source": "profiles/advance_kernel_traffic.json (ncu, same kernel sources)",
+                     "alg_bytes_per_launch": total_steps / ws * ALG_BYTES / n_launch,
                      "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)",
                      "kernel": "advance_kernel", "alg_bytes_per_particle_step": ALG_BYTES,
                      "kernel_ms_total": k_ms, "kernel_launches": n_launch,
@@ -557,8 +603,7 @@ def run_ensemble_case(args):
     w = configs.cir_ensemble_64(n_steps=args.ens_steps)
     w.params.sort_every = args.sort_every
     sets, n_steps, n_tot = w.sets, w.n_steps, w.n_particles
-    bg = api.Background(w.grid)
-    api.fte_load_background(bg, torch.from_numpy(np.ascontiguousarray(fields)))
+    bg = device_background(api, w, fields, args.layout)
     del fields
     side = torch.cuda.Stream()
     pool = api.Particles(n_tot)
@@ -641,7 +686,7 @@ def run_ensemble_case(args):
                                "(lambda_par log-U[0.05,1] au, H U[0.01,0.2], E_inj log-U[20,200] keV), "
                                f"{n_tot:.0e} protons (counts {min(counts)}-{max(counts)}), dt=10 s x {n_steps}, "
                                "per-set 1 au box tallies 16x144",
-                   "sort_every": w.params.sort_every,
+                   "sort_every": w.params.sort_every, "record_layout": args.layout,
                    "tally_rel_err_median": float(np.median(rel)) if rel else None,
                    "sets_with_hits": len(rel)},
         "arms": {"single_set_kernel_set_after_set": {"value": plain_rate, "ms_per_step": plain_ms},
@@ -736,8 +781,7 @@ def run_adjoint_case(args):
     build.build()
     torch.cuda.set_device(0)
     w, fields = build_workload()
-    bg = api.Background(w.grid)
-    api.fte_load_background(bg, torch.from_numpy(np.ascontiguousarray(fields)))
+    bg = device_background(api, w, fields, args.layout)
     del fields
     res = adjoint_times(api, bg, w, args.adj_particles, args.adj_steps, args.checkpoint_every, args.sort_every,
                         reps=args.steps, fd=True)
