@@ -333,11 +333,13 @@ def run_gpu(args):
     achieved = total_steps / ws * ALG_BYTES / (k_ms / 1e3) / 1e9
     l2_gbs = l2_probe()
     # our kernels per timed step: inject, and per advance call the two normalisation
-    # kernels and the step table, then per launch chunk the step kernel, the
-    # partial-histogram reduction and (with reordering) the five sort kernels
+    # kernels and the step table, then per launch chunk the step kernel, (with the
+    # shared-memory tally) the partial-histogram reduction and (with reordering) the
+    # five sort kernels
     def kernels_per_call(s):
         chunk = min(w.params.sort_every, CHUNK) if w.params.sort_every > 0 else CHUNK
-        return 3 + math.ceil(s / chunk) * (2 + (5 if w.params.sort_every > 0 else 0))
+        per_chunk = 1 + (1 if w.params.tally_layout == "shared" else 0) + (5 if w.params.sort_every > 0 else 0)
+        return 3 + math.ceil(s / chunk) * per_chunk
     launches_per_step = 1 + sum(kernels_per_call(min(CHUNK, n_steps - c)) for c in range(0, n_steps, CHUNK))
     result = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -433,7 +435,8 @@ def run_reference(args):
 
 def run_profile_case(args):
     """Small case of the same kernels for ncu captures: the full-resolution CIR grid with two
-    snapshots (884 MB, larger than L2), 2^18 particles, a few launches of 256 steps."""
+    snapshots (884 MB of cell records, 1.5 GB of pair records: larger than L2), 2^18 particles,
+    a few launches of 256 steps, in the record layout of --layout."""
     import torch
     from paper_2404_12164_gb300 import api, build
     build.build()
@@ -445,13 +448,17 @@ def run_profile_case(args):
         spec = AmrSpec(nbr=16, nbt=4, nbp=8, bsize=16, levels=3, n_snap=2, dt_snap=3600.0)
         w = configs.cir_amr_1e7(n_particles=1 << 18, n_steps=256 * args.launches, spec=spec)
         w.params.sort_every = args.sort_every
-        bg, _ = build_amr_background(w, api)
+        bg, leaves = build_amr_background(w, api)
+        if args.layout != "cell":
+            cell = bg
+            bg = api.AmrBackground(w.grid, leaves, share=cell, layout=args.layout)
+            api.fte_quantize_background(bg, cell)
+            torch.cuda.synchronize()
+            del cell
     else:
         w = configs.scaled(configs.cir_uniform_1e6(), n_snap=2, n_particles=1 << 18)
         w.params.sort_every = args.sort_every
-        fields = configs.build_background(w)
-        bg = api.Background(w.grid)
-        api.fte_load_background(bg, fields)
+        bg = device_background(api, w, configs.build_background(w), args.layout)
     pool = api.Particles(w.n_particles)
     tally = api.Tally(w.observers)
     api.fte_tally_reset(tally)

@@ -86,6 +86,7 @@ class Params:
     seed: int = 0
     set_id: int = 0
     sort_every: int = 0              # steps between spatial reorderings (performance only)
+    tally_layout: str = "global"     # 'global' (warp-merged FP64 atomics) | 'shared' (per-block histograms)
 
 
 @dataclass

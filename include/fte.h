@@ -223,7 +223,11 @@ typedef struct fte_params {
     int32_t sort_every;        /* > 0: reorder the alive particles by grid cell every
                                   sort_every steps (performance only: results do not
                                   depend on it); 0: no reordering */
-    int32_t pad;
+    int32_t tally_layout;      /* fte_advance: FTE_LAYOUT_GLOBAL (or 0): lanes of a warp in the
+                                  same bin are merged and added to the tally with FP64 atomics;
+                                  FTE_LAYOUT_SHARED: per-block histograms in shared memory
+                                  (at most 16384 bins), reduced after each launch.  The
+                                  counts are the same; the sums differ in rounding only */
 } fte_params;
 
 /* ---------------------------------------------------------------------------

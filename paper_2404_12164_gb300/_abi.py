@@ -67,7 +67,7 @@ class fte_params(C.Structure):
                 ("mu_floor", C.c_double), ("lambda_perp", C.c_double),
                 ("dt", C.c_double), ("t0", C.c_double),
                 ("seed", C.c_uint32), ("set_id", C.c_uint32),
-                ("sort_every", C.c_int32), ("pad", C.c_int32)]
+                ("sort_every", C.c_int32), ("tally_layout", C.c_int32)]
 
 
 class fte_observer(C.Structure):

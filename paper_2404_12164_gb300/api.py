@@ -71,6 +71,7 @@ def params_c(p):
     c.dt, c.t0 = p.dt, p.t0
     c.seed, c.set_id = p.seed & 0xFFFFFFFF, p.set_id & 0xFFFFFFFF
     c.sort_every = int(getattr(p, "sort_every", 0))
+    c.tally_layout = {"global": A.FTE_LAYOUT_GLOBAL, "shared": A.FTE_LAYOUT_SHARED}[getattr(p, "tally_layout", "global")]
     return c
 
 

@@ -5,25 +5,28 @@
 
 namespace fte {
 
-template <int LAY>
+template <int MODE, int LAY>
 static const void* single_fn(int kperp, int dtype)
 {
     if (dtype == FTE_BF16)
-        return kperp ? (const void*)advance_kernel<true, FTE_BF16, kModeSingle, kThreads, LAY>
-                     : (const void*)advance_kernel<false, FTE_BF16, kModeSingle, kThreads, LAY>;
+        return kperp ? (const void*)advance_kernel<true, FTE_BF16, MODE, kThreads, LAY>
+                     : (const void*)advance_kernel<false, FTE_BF16, MODE, kThreads, LAY>;
     if (dtype == FTE_F16)
-        return kperp ? (const void*)advance_kernel<true, FTE_F16, kModeSingle, kThreads, LAY>
-                     : (const void*)advance_kernel<false, FTE_F16, kModeSingle, kThreads, LAY>;
-    return kperp ? (const void*)advance_kernel<true, FTE_F32, kModeSingle, kThreads, LAY>
-                 : (const void*)advance_kernel<false, FTE_F32, kModeSingle, kThreads, LAY>;
+        return kperp ? (const void*)advance_kernel<true, FTE_F16, MODE, kThreads, LAY>
+                     : (const void*)advance_kernel<false, FTE_F16, MODE, kThreads, LAY>;
+    return kperp ? (const void*)advance_kernel<true, FTE_F32, MODE, kThreads, LAY>
+                 : (const void*)advance_kernel<false, FTE_F32, MODE, kThreads, LAY>;
 }
 
-// the single-set kernels come in one variant per record layout (pair: 1)
+// the single-set kernels come in one variant per record layout (pair: 1) and tally mode
 static const void* advance_fn(int kperp, int dtype, int mode, int nt, int pair)
 {
-    if (mode != kModeSingle) return advance_fn_batched(kperp, dtype, mode, nt);
+    if (!single_set(mode)) return advance_fn_batched(kperp, dtype, mode, nt);
     if (nt != kThreads) return nullptr;
-    return pair ? single_fn<kLayPair>(kperp, dtype) : single_fn<kLayCell>(kperp, dtype);
+    if (mode == kModeSingleGlobal)
+        return pair ? single_fn<kModeSingleGlobal, kLayPair>(kperp, dtype)
+                    : single_fn<kModeSingleGlobal, kLayCell>(kperp, dtype);
+    return pair ? single_fn<kModeSingle, kLayPair>(kperp, dtype) : single_fn<kModeSingle, kLayCell>(kperp, dtype);
 }
 
 cudaError_t advance_occupancy(int kperp, int dtype, int mode, int nt, int pair, size_t smem, int* blocks_per_sm)
@@ -38,7 +41,7 @@ cudaError_t advance_occupancy(int kperp, int dtype, int mode, int nt, int pair, 
 cudaError_t launch_advance(const AdvanceArgs& a, const BatchArgs& b, int kperp, int mode, int nt, int blocks,
                            size_t smem, cudaStream_t s)
 {
-    if (mode != kModeSingle) return launch_advance_batched(a, b, kperp, mode, nt, blocks, smem, s);
+    if (!single_set(mode)) return launch_advance_batched(a, b, kperp, mode, nt, blocks, smem, s);
     const void* fn = advance_fn(kperp, a.g.dtype, mode, nt, a.g.pair);
     if (!fn) return cudaErrorInvalidValue;
     void* args[] = {(void*)&a, (void*)&b};

@@ -224,17 +224,23 @@ int device_sms(int device)
     return cache[device];
 }
 
-fte_status layout(int device, int kperp, int dtype, int pair, size_t nbins, long long n_steps,
+// shared memory of a single-set step kernel: the partial histogram, or none
+size_t single_smem(int mode, size_t nbins)
+{
+    return mode == kModeSingle ? 3 * sizeof(float) * (nbins ? nbins : 1) : 0;
+}
+
+fte_status layout(int device, int kperp, int dtype, int pair, int mode, size_t nbins, long long n_steps,
                   size_t sort_bytes, WsLayout* L)
 {
     const int sms = device_sms(device);
     if (sms <= 0) return fail(FTE_ECUDA, "cannot query device %d", device);
-    const size_t smem = 3 * sizeof(float) * (nbins ? nbins : 1);
+    const size_t smem = single_smem(mode, nbins);
     int per_sm = 0;
     int cur = 0;
     FTE_CUDA(cudaGetDevice(&cur), "cudaGetDevice");
     if (cur != device) FTE_CUDA(cudaSetDevice(device), "cudaSetDevice");
-    cudaError_t e = advance_occupancy(kperp, dtype, kModeSingle, kThreads, pair, smem, &per_sm);
+    cudaError_t e = advance_occupancy(kperp, dtype, mode, kThreads, pair, smem, &per_sm);
     if (cur != device) cudaSetDevice(cur);
     if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
     if (per_sm < 1) return fail(FTE_ENOTSUP, "step kernel does not fit on an SM with %zu bytes of tally", smem);
@@ -245,7 +251,8 @@ fte_status layout(int device, int kperp, int dtype, int pair, size_t nbins, long
     L->off_npart = off; off += kNormPartials * sizeof(double);
     L->off_table = off; off += (size_t)(n_steps > 0 ? n_steps : 1) * sizeof(StepEntry);
     off = (off + 255) & ~(size_t)255;
-    L->off_part = off; off += (size_t)L->blocks * 3 * (nbins ? nbins : 1) * sizeof(float);
+    L->off_part = off;
+    if (mode == kModeSingle) off += (size_t)L->blocks * 3 * (nbins ? nbins : 1) * sizeof(float);
     off = (off + 255) & ~(size_t)255;
     L->off_sort = off; off += sort_bytes;
     L->total = off;
@@ -376,7 +383,6 @@ size_t fte_workspace_bytes(int device, const fte_grid* g, const fte_tally_buf* t
     size_t nb = 0;
     if (check_grid(g) != FTE_OK) return 0;
     if (check_tally(t, &nb) != FTE_OK || n_steps < 0) return 0;
-    if (nb > (size_t)kMaxSmemBins) return 0;
     fte_background tmp;
     memset(&tmp, 0, sizeof(tmp));
     tmp.grid = *g;
@@ -384,11 +390,13 @@ size_t fte_workspace_bytes(int device, const fte_grid* g, const fte_tally_buf* t
     size_t best = 0;
     for (int dtype = FTE_F32; dtype <= FTE_F16; ++dtype)
         for (int kperp = 0; kperp < 2; ++kperp)
-            for (int pair = 0; pair < 2; ++pair) {
-                WsLayout L;
-                if (layout(device, kperp, dtype, pair, nb, n_steps, sort_bytes, &L) != FTE_OK) return 0;
-                if (L.total > best) best = L.total;
-            }
+            for (int pair = 0; pair < 2; ++pair)
+                for (int mode : {kModeSingle, kModeSingleGlobal}) {
+                    if (mode == kModeSingle && nb > (size_t)kMaxSmemBins) continue;
+                    WsLayout L;
+                    if (layout(device, kperp, dtype, pair, mode, nb, n_steps, sort_bytes, &L) != FTE_OK) return 0;
+                    if (L.total > best) best = L.total;
+                }
     return best;
 }
 
@@ -461,7 +469,12 @@ fte_status fte_advance(fte_particles* P, const fte_background* bg, const fte_par
     size_t nb = 0;
     s = check_tally(t, &nb);
     if (s != FTE_OK) return s;
-    if (nb > (size_t)kMaxSmemBins) return fail(FTE_ENOTSUP, "%zu tally bins exceed %d", nb, kMaxSmemBins);
+    if (prm && prm->tally_layout != 0 && prm->tally_layout != FTE_LAYOUT_SHARED && prm->tally_layout != FTE_LAYOUT_GLOBAL)
+        return fail(FTE_EINVAL, "bad tally layout");
+    // the warp-merged FP64 atomics unless the shared-memory histogram is asked for
+    const int mode = (prm && prm->tally_layout == FTE_LAYOUT_SHARED) ? kModeSingle : kModeSingleGlobal;
+    if (mode == kModeSingle && nb > (size_t)kMaxSmemBins)
+        return fail(FTE_ENOTSUP, "%zu tally bins exceed %d", nb, kMaxSmemBins);
     if (n_end < n_start || n_start < 0) return fail(FTE_EINVAL, "need 0 <= n_start <= n_end");
     if (n_end > 0xFFFFFFFFll) return fail(FTE_EINVAL, "step index exceeds 32 bits");
     if (!(prm->dt > 0.0)) return fail(FTE_EINVAL, "dt must be > 0");
@@ -482,7 +495,8 @@ fte_status fte_advance(fte_particles* P, const fte_background* bg, const fte_par
     const GridK gk = make_gridk(bg);
     const int sorting = prm->sort_every > 0;
     WsLayout L;
-    s = layout(device, kperp, bg->grid.dtype, gk.pair, nb, nsteps, sorting ? sort_scratch_bytes(gk, P->count) : 0, &L);
+    s = layout(device, kperp, bg->grid.dtype, gk.pair, mode, nb, nsteps, sorting ? sort_scratch_bytes(gk, P->count) : 0,
+               &L);
     if (s != FTE_OK) return s;
     if (ws_bytes < L.total) return fail(FTE_ENOMEM, "workspace has %zu bytes, needs %zu", ws_bytes, L.total);
     char* w = (char*)ws;
@@ -531,6 +545,7 @@ fte_status fte_advance(fte_particles* P, const fte_background* bg, const fte_par
     a.table = ta.tab;
     a.norm = norm;
     a.part = (float*)(w + L.off_part);
+    a.gS = t->S; a.gS2 = t->S2; a.gC = t->C;
     a.fetch = (unsigned long long*)(w + L.off_fetch);
     a.ledger_w = t->ledger_w; a.ledger_n = t->ledger_n;
 
@@ -544,18 +559,19 @@ fte_status fte_advance(fte_particles* P, const fte_background* bg, const fte_par
     if (blocks > L.blocks || sorting) blocks = L.blocks;
     if (blocks < 1) blocks = 1;
     const long long chunk = sorting ? (prm->sort_every < kChunkSteps ? prm->sort_every : kChunkSteps) : kChunkSteps;
-    const size_t smem = 3 * sizeof(float) * (size_t)a.nbins;
+    const size_t smem = single_smem(mode, nb);
     int per_sm = 0;
-    FTE_CUDA(advance_occupancy(kperp, bg->grid.dtype, kModeSingle, kThreads, bg->grid.layout == FTE_LAYOUT_PAIR,
-                                smem, &per_sm), "occupancy");
+    FTE_CUDA(advance_occupancy(kperp, bg->grid.dtype, mode, kThreads, bg->grid.layout == FTE_LAYOUT_PAIR, smem,
+                               &per_sm), "occupancy");
 
     for (long long c0 = n_start; c0 < n_end; c0 += chunk) {
         a.n_start = c0;
         a.n_end = (c0 + chunk < n_end) ? c0 + chunk : n_end;
         if (sorting) FTE_CUDA(launch_sort(sa, st), "sort launch");
         FTE_CUDA(cudaMemsetAsync(a.fetch, 0, sizeof(unsigned long long), st), "fetch reset");
-        FTE_CUDA(launch_advance(a, g_no_batch, kperp, kModeSingle, kThreads, blocks, smem, st), "step kernel launch");
-        if (nb) FTE_CUDA(launch_reduce(a.part, blocks, (int)nb, t->S, t->S2, t->C, st), "reduce launch");
+        FTE_CUDA(launch_advance(a, g_no_batch, kperp, mode, kThreads, blocks, smem, st), "step kernel launch");
+        if (nb && mode == kModeSingle)
+            FTE_CUDA(launch_reduce(a.part, blocks, (int)nb, t->S, t->S2, t->C, st), "reduce launch");
     }
     return FTE_OK;
 }

@@ -10,6 +10,10 @@ namespace fte {
 constexpr int kModeSingle = 0;
 constexpr int kModeShared = 1;
 constexpr int kModeGlobal = 2;
+constexpr int kModeSingleGlobal = 3;   // one parameter set, warp-merged FP64 atomics to the tally
+
+__host__ __device__ constexpr bool single_set(int mode) { return mode == kModeSingle || mode == kModeSingleGlobal; }
+__host__ __device__ constexpr bool global_tally(int mode) { return mode == kModeGlobal || mode == kModeSingleGlobal; }
 
 // Per-set transport parameters of an ensemble (everything else is shared).
 struct SetK {
@@ -36,7 +40,7 @@ struct AdvanceArgs {
     long long n_table0;           // step index of table[0]
     const StepEntry* table;
     const double* norm;           // normalisation integral of D_mumu (one per set)
-    double* gS;                   // kModeGlobal: FP64 accumulators [set][bin]
+    double* gS;                   // global tally modes: FP64 accumulators [set][bin]
     double* gS2;
     unsigned long long* gC;
     const uint32_t* order;        // alive particles in spatial order (NULL: all, by index)
@@ -124,7 +128,7 @@ struct AdjK {
 };
 
 // launchers (return cudaGetLastError())
-// step kernel of (kperp, dtype, mode, threads per block); nt is 256 for kModeSingle
+// step kernel of (kperp, dtype, mode, threads per block); nt is 256 for the single-set modes
 cudaError_t launch_advance(const AdvanceArgs& a, const BatchArgs& b, int kperp, int mode, int nt, int blocks,
                            size_t smem, cudaStream_t s);
 // resident blocks per SM of a step kernel (`pair`: record layout of a single-set kernel)

@@ -198,7 +198,7 @@ __device__ __forceinline__ int step(const AdvanceArgs& a, const ParamsK& prm, fl
                 else
                     ++noor;
             }
-            if (MODE == kModeGlobal) warp_tally_global(a.gS, a.gS2, a.gC, bin, w * dt);
+            if (global_tally(MODE)) warp_tally_global(a.gS, a.gS2, a.gC, bin, w * dt);
             else warp_tally(shS, shS2, shC, bin, w * dt);
         }
     }
@@ -234,27 +234,29 @@ __device__ __forceinline__ int set_of(const unsigned long long* end, int n_sets,
 
 // Persistent step kernel: each thread takes particles from a shared counter and
 // keeps each one in registers for all steps [n_start, n_end) of the launch.
-// MODE kModeSingle: one parameter set, tally in shared memory; kModeShared: an
-// ensemble (per-set parameters and tallies, the tallies of all sets in shared
-// memory); kModeGlobal: an ensemble with warp-merged FP64 atomics to the tally.
+// MODE kModeSingle: one parameter set, tally in shared memory; kModeSingleGlobal:
+// one parameter set, warp-merged FP64 atomics to the tally (no shared memory, so
+// L1 keeps its whole capacity for the gather); kModeShared: an ensemble
+// (per-set parameters and tallies, the tallies of all sets in shared memory);
+// kModeGlobal: an ensemble with warp-merged FP64 atomics to the tally.
 // LAY: record layout, compile-time for the single-set kernels, read from the
 // grid (kLayAny) by the ensemble kernels.
 template <bool KPERP, int DT, int MODE, int NT, int LAY>
-__global__ void __launch_bounds__(NT, MODE == kModeSingle ? 0 : 512 / NT) advance_kernel(const AdvanceArgs a, const BatchArgs b)
+__global__ void __launch_bounds__(NT, single_set(MODE) ? 0 : 512 / NT) advance_kernel(const AdvanceArgs a, const BatchArgs b)
 {
     extern __shared__ float sh[];
-    const int nsh = MODE == kModeGlobal ? 0 : (MODE == kModeShared ? b.n_sets : 1) * a.nbins;
+    const int nsh = global_tally(MODE) ? 0 : (MODE == kModeShared ? b.n_sets : 1) * a.nbins;
     float* shS = sh;
     float* shS2 = sh + nsh;
     unsigned* shC = reinterpret_cast<unsigned*>(sh + 2 * nsh);
     __shared__ float sc[FTE_NFIELD];      // per-field scales of 16-bit storage
-    constexpr int kSets = MODE == kModeSingle ? 1 : FTE_MAX_SETS;
+    constexpr int kSets = single_set(MODE) ? 1 : FTE_MAX_SETS;
     __shared__ unsigned long long s_end[kSets];
     __shared__ SetK s_set[kSets];
     __shared__ float s_I[kSets];
     for (int q = threadIdx.x; q < 3 * nsh; q += NT) sh[q] = 0.f;
     if (DT != FTE_F32 && threadIdx.x < FTE_NFIELD) sc[threadIdx.x] = __ldg(a.g.scale + threadIdx.x);
-    if (MODE != kModeSingle) {
+    if (!single_set(MODE)) {
         for (int s = threadIdx.x; s < b.n_sets; s += NT) {
             s_end[s] = b.end[s];
             s_set[s] = b.set[s];
@@ -263,7 +265,7 @@ __global__ void __launch_bounds__(NT, MODE == kModeSingle ? 0 : 512 / NT) advanc
     }
     __syncthreads();
 
-    const float I0 = MODE == kModeSingle ? (float)__ldg(a.norm) : 0.f;
+    const float I0 = single_set(MODE) ? (float)__ldg(a.norm) : 0.f;
     const unsigned long long n_work = a.order ? (unsigned long long)__ldg(a.n_order) : a.n_particles;
     unsigned long long nsteps = 0, noor = 0;
     for (;;) {
@@ -275,7 +277,7 @@ __global__ void __launch_bounds__(NT, MODE == kModeSingle ? 0 : 512 / NT) advanc
         const float w = a.w[i];
         const uint32_t pid = a.id[i];
         int st = FTE_ALIVE;
-        if (MODE == kModeSingle) {
+        if (single_set(MODE)) {
             for (long long n = a.n_start; n < a.n_end; ++n) {
                 ++nsteps;
                 st = step<KPERP, DT, MODE, LAY>(a, a.prm, I0, 0, n, pid, x, y, z, mu, p, w, shS, shS2, shC, sc, noor);
@@ -307,7 +309,7 @@ __global__ void __launch_bounds__(NT, MODE == kModeSingle ? 0 : 512 / NT) advanc
     }
 
     __syncthreads();   // all tally updates of this block are in shared memory
-    if (MODE != kModeGlobal) {
+    if (!global_tally(MODE)) {
         float* out = a.part + (size_t)blockIdx.x * 3 * nsh;
         for (int q = threadIdx.x; q < 3 * nsh; q += NT) out[q] = sh[q];
     }

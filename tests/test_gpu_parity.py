@@ -302,3 +302,21 @@ def test_undersized_workspace_is_refused(parker):
                              0, 50, C.c_void_p(buf.data_ptr()), buf.numel(), None)
     assert st == A.FTE_ENOMEM
     assert b"workspace" in A.lib().fte_last_error()
+
+
+def test_tally_layouts_agree(cir_small):
+    """Warp-merged FP64 atomics (the default) and per-block shared-memory histograms tally the
+    same events: counts equal, sums to FP32 partial-sum rounding, trajectories identical."""
+    import dataclasses
+    w, f = cir_small
+    obs = w.observers + [Observer(kind="shell", r=1.5, dr=0.05, e_lo=0.01, e_hi=10.0, ne=16, t_lo=0.0,
+                                  t_hi=20000.0, nt=40)]
+    g = gpu_run(w, f, 1200, observers=obs)
+    s = gpu_run(w, f, 1200, observers=obs, params=dataclasses.replace(w.params, tally_layout="shared"))
+    for k in ("x", "y", "z", "mu", "p", "status"):
+        assert np.array_equal(g["states"][1200][k], s["states"][1200][k]), k
+    for o in range(len(obs)):
+        assert np.array_equal(g["tallies"][o]["C"], s["tallies"][o]["C"])
+        Sg, Ss = g["tallies"][o]["S"], s["tallies"][o]["S"]
+        assert np.allclose(Sg, Ss, rtol=1e-5, atol=1e-12 * max(Sg.max(), 1e-30))
+    assert np.array_equal(g["ledger_n"], s["ledger_n"])

@@ -6,6 +6,8 @@ middle of a run is not allowed); it keeps its scratch in a device array the
 library places statically.  This file is collected last so that a run that
 stops at the first failure has already run every other test.
 """
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -38,8 +40,10 @@ def test_noalloc_matches_fte_advance_on_two_calls():
     bg_a, pool_a, tally_a = _setup(api, w, fields, obs)
     bg_b, pool_b, tally_b = _setup(api, w, fields, obs)
     ws = api.Workspace()
+    # the allocation-free call keeps per-block histograms in shared memory: compare with the same layout
+    prm = dataclasses.replace(w.params, tally_layout="shared")
     for n0, n1 in ((0, 700), (700, 2300)):          # two calls in a row; the second spans 2 launches
-        api.fte_advance(pool_a, bg_a, w.params, tally_a, n0, n1, ws)
+        api.fte_advance(pool_a, bg_a, prm, tally_a, n0, n1, ws)
         api.fte_advance_noalloc(pool_b, bg_b, w.params, tally_b, n0, n1)
         a, b = pool_a.state(), pool_b.state()
         for k in ("x", "y", "z", "mu", "p", "w", "status", "id"):
