@@ -151,15 +151,16 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def device_background(api, w, fields, layout):
-    """The workload's background on the device in the given record layout (converted on the
-    device from the FP32 cell records)."""
+def device_background(api, w, fields, layout, dtype="f32"):
+    """The workload's background on the device in the given record layout and storage dtype
+    (converted on the device from the FP32 cell records)."""
     import torch
     cell = api.Background(w.grid)
-    api.fte_load_background(cell, torch.from_numpy(np.ascontiguousarray(fields)))
-    if layout == "cell":
+    src = fields if isinstance(fields, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(fields))
+    api.fte_load_background(cell, src)
+    if layout == "cell" and dtype == "f32":
         return cell
-    bg = api.Background(w.grid, layout=layout)
+    bg = api.Background(w.grid, dtype=dtype, layout=layout)
     api.fte_quantize_background(bg, cell)
     torch.cuda.synchronize()
     del cell
@@ -809,9 +810,11 @@ def run_adjoint_case(args):
 
 def run_stream_case(args):
     """The cir_uniform_1e6 workload with only `--ring` snapshot slots on the device: the 24 hourly
-    snapshots stay in page-locked host memory and are copied into their slots as the 4 days
-    advance (each copy overlapped with the previous interval's steps).  Reports the streamed and
-    the fully resident rates on the same particles."""
+    snapshots stay in page-locked host memory (FP32 cell records) and are copied into their slots
+    as the 4 days advance (each copy overlapped with the previous interval's steps; pair-layout
+    or 16-bit slots are filled through a staging snapshot converted on the device).  Reports the
+    streamed and the fully resident rates on the same particles in the same storage
+    (`--layout`, `--stream-dtype`), and the host-to-device copy bandwidth measured beside them."""
     import torch
     from paper_2404_12164_gb300 import api, build
     build.build()
@@ -820,6 +823,7 @@ def run_stream_case(args):
     w.params.sort_every = args.sort_every
     host = torch.from_numpy(np.ascontiguousarray(fields)).pin_memory()
     n_part, n_steps = w.n_particles, w.n_steps
+    dtype, layout = args.stream_dtype, args.layout
     pool = api.Particles(n_part)
     tally = api.Tally(w.observers)
     ws = api.Workspace()
@@ -839,8 +843,24 @@ def run_stream_case(args):
         torch.cuda.synchronize()
         return done / (e0.elapsed_time(e1) / 1e3), e0.elapsed_time(e1) / reps
 
-    ring_bg = api.Background(w.grid, ring=args.ring)
+    ring_bg = api.Background(w.grid, dtype=dtype, ring=args.ring, layout=layout)
     st = api.SnapshotStream(ring_bg, host)
+    snap = api.fte_snapshot_bytes(ring_bg)
+
+    # host-to-device bandwidth of whole-snapshot copies on the copy stream, into the staging
+    # buffer or a slot (nothing runs beside them)
+    flat = host.view(torch.uint8).view(-1)
+    dst = st.staging if st.staging is not None else ring_bg.dev.view(torch.uint8)[:snap]
+    torch.cuda.synchronize()
+    c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(st.copy_stream):
+        c0.record(st.copy_stream)
+        for k in range(8):
+            dst[:snap].copy_(flat[k * snap:(k + 1) * snap], non_blocking=True)
+        c1.record(st.copy_stream)
+    torch.cuda.synchronize()
+    h2d_gbs = 8 * snap / (c0.elapsed_time(c1) / 1e3) / 1e9
+    st.slots[:] = -1                   # the probe overwrote slot contents
 
     def streamed():
         pool.c.count = 0
@@ -850,8 +870,10 @@ def run_stream_case(args):
         api.fte_advance_streamed(pool, ring_bg, st, w.params, tally, 0, n_steps, ws)
 
     v_str, ms_str = timed(streamed, args.steps, 1)
-    res_bg = api.Background(w.grid)
-    api.fte_load_background(res_bg, host)
+    ring_bytes = int(ring_bg.nbytes) + (st.staging.numel() if st.staging is not None else 0)
+    del st, ring_bg
+    torch.cuda.empty_cache()
+    res_bg = device_background(api, w, host, layout, dtype)
 
     def resident():
         pool.c.count = 0
@@ -861,16 +883,16 @@ def run_stream_case(args):
             api.fte_advance(pool, res_bg, w.params, tally, c, min(c + CHUNK, n_steps), ws)
 
     v_res, ms_res = timed(resident, args.steps, 1)
-    plan = api.fte_stream_plan(ring_bg, w.params, 0, n_steps)
+    plan = api.fte_stream_plan(res_bg, w.params, 0, n_steps)
     uploads = len(plan) + 1
     print(json.dumps({
         "case": "stream", "metric": METRIC, "value": v_str, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-        "ms_per_step": ms_str, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+        "ms_per_step": ms_str, "higher_is_better": True, "dtype": dtype, "data": "synthetic",
         "config": {"workload": "cir_uniform_1e6 with %d resident snapshot slots (24 hourly snapshots in "
-                               "page-locked host memory)" % args.ring,
-                   "device_background_bytes": int(ring_bg.nbytes), "resident_background_bytes": int(res_bg.nbytes),
-                   "snapshot_uploads_per_step": uploads,
-                   "h2d_bytes_per_step": int(uploads * api.fte_snapshot_bytes(ring_bg))},
+                               "page-locked host memory), %s %s records" % (args.ring, dtype, layout),
+                   "device_background_bytes": ring_bytes, "resident_background_bytes": int(res_bg.nbytes),
+                   "snapshot_uploads_per_step": uploads, "h2d_bytes_per_step": int(uploads * snap)},
+        "h2d_gbs": h2d_gbs,
         "resident": {"value": v_res, "ms_per_step": ms_res},
         "streamed_over_resident": v_str / v_res,
     }), flush=True)
@@ -899,6 +921,8 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--case", default="bench", choices=["bench", "profile", "amr", "ensemble", "adjoint", "stream"])
     ap.add_argument("--ring", type=int, default=3, help="resident snapshot slots of --case stream")
+    ap.add_argument("--stream-dtype", default="f32", choices=["f32", "bf16", "f16"],
+                    help="storage of the slots (and of the resident comparison) of --case stream")
     ap.add_argument("--adj-particles", type=int, default=1_000_000)
     ap.add_argument("--adj-steps", type=int, default=34_560)
     ap.add_argument("--checkpoint-every", type=int, default=256)

@@ -39,7 +39,7 @@
 extern "C" {
 #endif
 
-#define FTE_ABI_VERSION 1
+#define FTE_ABI_VERSION 2
 #define FTE_NFIELD 18          /* stored fields per cell */
 #define FTE_REC 24             /* floats per stored cell record (96 bytes) */
 #define FTE_HREC 32            /* 16-bit values per reduced-precision cell record (64 bytes) */
@@ -109,7 +109,8 @@ typedef struct fte_grid {
     int32_t ring;              /* 0: all n_snap snapshots resident; 2 .. n_snap: the device
                                   array holds `ring` snapshot slots, snapshot u (counted in
                                   time order, periodic sequences unwrapped) in slot u mod ring,
-                                  filled on demand by fte_advance_streamed (FP32 only) */
+                                  filled on demand by fte_advance_streamed (any dtype and
+                                  layout: host snapshots are FP32 cell records) */
     int32_t layout;            /* FTE_LAYOUT_CELL or FTE_LAYOUT_PAIR (see below) */
 } fte_grid;
 
@@ -150,7 +151,9 @@ size_t fte_amr_table_bytes(const fte_grid* g);
    device (FP32 fields): builds bg->table, checks that the leaves tile the domain
    without overlap and with 2:1 nesting (EINVAL otherwise; this check
    synchronises `stream`), then fills the ghost layer of every leaf and snapshot
-   in bg->fields.  A 16-bit copy is then made with fte_quantize_background. */
+   in bg->fields.  A 16-bit copy is then made with fte_quantize_background.  For
+   a ring background in 16-bit or pair storage only the table is built (its
+   slots are filled, ghosts included, as snapshots stream in). */
 fte_status fte_amr_prepare(const fte_background* bg, void* stream);
 
 /* Convert an FP32 cell-layout background to the storage form of `g_half`: a
@@ -311,31 +314,53 @@ fte_status fte_advance(fte_particles* P, const fte_background* bg, const fte_par
 fte_status fte_stream_plan(const fte_grid* g, const fte_params* prm, int64_t n_start, int64_t n_end,
                            int64_t* out, int64_t max_runs, int64_t* count);
 
-/* fte_advance over a ring background (grid.ring >= 2, FP32): for every run of
-   the plan, the snapshots it needs (and, with ring >= 3, the next one) are
-   copied from host_snapshots (HOST, page-locked for overlap: the n_snap
-   snapshots in order, each fte_snapshot_bytes(g) bytes of records; for AMR the
-   ghost cells of a copied snapshot are refilled on the device) into their
-   slots on copy_stream, and the run is advanced on
+/* Bytes of one host snapshot: FP32 cell records (96 bytes per cell; AMR: the
+   padded leaf lattices, ghost values ignored), the unit fte_advance_streamed copies. */
+size_t fte_snapshot_bytes(const fte_grid* g);
+
+/* Bytes of the DEVICE staging buffer that streaming into a ring of `g` needs: 0
+   for FP32 cell-layout slots (a snapshot is copied straight into its slot);
+   otherwise one host snapshot (fte_snapshot_bytes), into which each snapshot is
+   copied and from which it is converted into its slot as fte_quantize_background
+   converts a resident background (0 if g is invalid). */
+size_t fte_stream_staging_bytes(const fte_grid* g);
+
+/* 16-bit ring backgrounds: set the per-field scale header of bg->fields from all
+   n_snap host snapshots (each copied into `staging`, AMR ghost layer refilled,
+   largest |value| per field; the scales fte_quantize_background computes for the
+   fully resident background of the same snapshots, so the stored values are
+   identical).  Once, before the first fte_stream_load or fte_advance_streamed;
+   AMR: after fte_amr_prepare.  EINVAL for FP32 backgrounds or a NULL argument,
+   ENOMEM if staging_bytes < fte_stream_staging_bytes.  Asynchronous on `stream`. */
+fte_status fte_stream_scales(const fte_background* bg, const void* host_snapshots, void* staging,
+                             size_t staging_bytes, void* stream);
+
+/* fte_advance over a ring background (grid.ring >= 2): for every run of the
+   plan, the snapshots it needs (and, with ring >= 3, the next one) are copied
+   from host_snapshots (HOST, page-locked for overlap: the n_snap snapshots in
+   order, each fte_snapshot_bytes(g) bytes of FP32 cell records) into their slots
+   on copy_stream - for a 16-bit or pair-layout ring through `staging` (DEVICE,
+   32-byte aligned, fte_stream_staging_bytes(g) bytes; may be NULL when that is
+   0) and a conversion into the slot; for AMR the ghost cells of a copied
+   snapshot are refilled on the device - and the run is advanced on
    compute_stream once its slots are filled; a slot is overwritten only after
    the steps using it are done.  slot_state (HOST, ring entries, caller-owned,
    -1 = empty before the first call) records the unwrapped snapshot each slot
    holds and is updated.  ws as for fte_advance with n_steps = the longest run.
-   Work of earlier calls on either stream is waited for.  Asynchronous. */
+   Work of earlier calls on either stream is waited for.  EINVAL/ENOMEM for a
+   missing or undersized staging buffer.  Asynchronous. */
 fte_status fte_advance_streamed(fte_particles* P, const fte_background* bg, const void* host_snapshots,
                                 const fte_params* prm, const fte_tally_buf* t, int64_t n_start, int64_t n_end,
-                                int64_t* slot_state, void* ws, size_t ws_bytes, void* compute_stream,
-                                void* copy_stream);
+                                int64_t* slot_state, void* staging, size_t staging_bytes, void* ws,
+                                size_t ws_bytes, void* compute_stream, void* copy_stream);
 
 /* Copy unwrapped snapshot u (periodic sequences: any u, snapshot u mod n_snap;
    otherwise 0 <= u < n_snap) from host_snapshots into slot u mod ring on
-   `stream` (AMR: and refill its ghost layer), and record it in slot_state, for
-   instance the injection snapshot before fte_inject.  Asynchronous. */
+   `stream` (through `staging` as above; AMR: and refill its ghost layer), and
+   record it in slot_state, for instance the injection snapshot before
+   fte_inject.  Asynchronous. */
 fte_status fte_stream_load(const fte_background* bg, const void* host_snapshots, int64_t u, int64_t* slot_state,
-                           void* stream);
-
-/* Bytes of one snapshot's records (the unit fte_advance_streamed copies). */
-size_t fte_snapshot_bytes(const fte_grid* g);
+                           void* staging, size_t staging_bytes, void* stream);
 
 /* Allocation-free variant of fte_advance (the paper has no counterpart: this is
    an interface for callers that cannot allocate device memory at run time, such

@@ -141,12 +141,15 @@ SIGNATURES = {
                                       _P(fte_inject_spec), C.c_int64, C.c_int64, C.c_int, C.c_void_p, C.c_void_p,
                                       C.c_void_p, C.c_size_t, C.c_void_p]),
     "fte_snapshot_bytes": (C.c_size_t, [_P(fte_grid)]),
-    "fte_stream_load": (C.c_int, [_P(fte_background), C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
+    "fte_stream_staging_bytes": (C.c_size_t, [_P(fte_grid)]),
+    "fte_stream_scales": (C.c_int, [_P(fte_background), C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]),
+    "fte_stream_load": (C.c_int, [_P(fte_background), C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_size_t,
+                                  C.c_void_p]),
     "fte_stream_plan": (C.c_int, [_P(fte_grid), _P(fte_params), C.c_int64, C.c_int64, C.c_void_p, C.c_int64,
                                   _P(C.c_int64)]),
     "fte_advance_streamed": (C.c_int, [_P(fte_particles), _P(fte_background), C.c_void_p, _P(fte_params),
                                        _P(fte_tally_buf), C.c_int64, C.c_int64, C.c_void_p, C.c_void_p, C.c_size_t,
-                                       C.c_void_p, C.c_void_p]),
+                                       C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p]),
     "fte_graph_begin": (C.c_int, [C.c_void_p]),
     "fte_graph_end": (C.c_int, [C.c_void_p, _P(C.c_void_p)]),
     "fte_graph_launch": (C.c_int, [C.c_void_p, C.c_void_p]),

@@ -571,8 +571,10 @@ def fte_stream_plan(bg, params, n_start, n_end):
 
 
 class SnapshotStream:
-    """Host snapshots (page-locked, FP32 records) and the ring's slot bookkeeping for
-    fte_advance_streamed; `copy_stream` carries the uploads."""
+    """Host snapshots (page-locked FP32 cell records) and the ring's slot bookkeeping for
+    fte_advance_streamed; `copy_stream` carries the uploads.  A 16-bit or pair-layout ring
+    also gets a device staging snapshot, and a 16-bit ring its per-field scales from all
+    host snapshots (fte_stream_scales) here, before any slot is filled."""
 
     def __init__(self, bg, host_fields, device="cuda"):
         if bg.gc.ring < 2:
@@ -585,6 +587,19 @@ class SnapshotStream:
         self.slots = np.full(bg.gc.ring, -1, dtype=np.int64)
         self.copy_stream = torch.cuda.Stream(device=device)
         self.bg = bg
+        nst = A.lib().fte_stream_staging_bytes(C.byref(bg.gc))
+        self.staging = torch.empty(nst, dtype=torch.uint8, device=bg.dev.device) if nst else None
+        if bg.gc.dtype != A.FTE_F32:
+            cur = torch.cuda.current_stream()
+            self.copy_stream.wait_stream(cur)
+            check(A.lib().fte_stream_scales(C.byref(bg.c), C.c_void_p(self.host.data_ptr()), *self._staging(),
+                                            _stream(self.copy_stream)), "fte_stream_scales")
+            cur.wait_stream(self.copy_stream)
+
+    def _staging(self):
+        if self.staging is None:
+            return C.c_void_p(None), 0
+        return C.c_void_p(self.staging.data_ptr()), self.staging.numel()
 
     def load(self, u, stream=None):
         """Copy unwrapped snapshot u into its slot, e.g. the injection snapshot before fte_inject:
@@ -593,7 +608,8 @@ class SnapshotStream:
         cur = stream if stream is not None else torch.cuda.current_stream()
         self.copy_stream.wait_stream(cur)
         check(A.lib().fte_stream_load(C.byref(self.bg.c), C.c_void_p(self.host.data_ptr()), int(u),
-                                      C.c_void_p(self.slots.ctypes.data), _stream(self.copy_stream)),
+                                      C.c_void_p(self.slots.ctypes.data), *self._staging(),
+                                      _stream(self.copy_stream)),
               "fte_stream_load")
         cur.wait_stream(self.copy_stream)
 
@@ -607,7 +623,8 @@ def fte_advance_streamed(pool, bg, stream_state, params, tally, n_start, n_end, 
     pc = params_c(params)
     check(A.lib().fte_advance_streamed(C.byref(pool.c), C.byref(bg.c), C.c_void_p(stream_state.host.data_ptr()),
                                        C.byref(pc), C.byref(tally.c), int(n_start), int(n_end),
-                                       C.c_void_p(stream_state.slots.ctypes.data), C.c_void_p(buf.data_ptr()),
-                                       buf.numel(), _stream(stream), _stream(stream_state.copy_stream)),
+                                       C.c_void_p(stream_state.slots.ctypes.data), *stream_state._staging(),
+                                       C.c_void_p(buf.data_ptr()), buf.numel(), _stream(stream),
+                                       _stream(stream_state.copy_stream)),
           "fte_advance_streamed")
     return ws

@@ -147,26 +147,47 @@ __global__ void __launch_bounds__(256) pair_f32_kernel(const float* __restrict__
     for (int q = 0; q < kPairRec / 4; ++q) o[q] = make_float4(a[4 * q], a[4 * q + 1], a[4 * q + 2], a[4 * q + 3]);
 }
 
-cudaError_t launch_quantize(const float* f32, long long nrec, int row, int dtype, int pair, void* out,
-                            cudaStream_t s)
+// Per-field scales of FP32 cell records: `first` zeroes the header, each call
+// folds nrec records into the running maxima, `last` turns them into scales.
+cudaError_t launch_scales(const float* f32, long long nrec, float* hdr, bool first, bool last, cudaStream_t s)
+{
+    if (first) {
+        const cudaError_t e = cudaMemsetAsync(hdr, 0, FTE_HHDR * sizeof(float), s);
+        if (e != cudaSuccess) return e;
+    }
+    if (nrec > 0) maxabs_kernel<<<1216, 256, 0, s>>>(f32, nrec, reinterpret_cast<unsigned*>(hdr));
+    if (last) scale_final_kernel<<<1, 32, 0, s>>>(hdr);
+    return cudaGetLastError();
+}
+
+// FP32 cell records into pair and/or 16-bit records (16-bit: with the scales
+// already in `hdr`), nrec records starting at `out_recs`.
+cudaError_t launch_convert(const float* f32, long long nrec, int row, int dtype, int pair, const float* hdr,
+                           void* out_recs, cudaStream_t s)
 {
     const long long blocks = (nrec + 255) / 256;
+    if (nrec <= 0) return cudaSuccess;
     if (dtype == FTE_F32) {
         if (!pair) return cudaErrorInvalidValue;
-        pair_f32_kernel<<<(unsigned)blocks, 256, 0, s>>>(f32, nrec, row, reinterpret_cast<float*>(out));
+        pair_f32_kernel<<<(unsigned)blocks, 256, 0, s>>>(f32, nrec, row, reinterpret_cast<float*>(out_recs));
         return cudaGetLastError();
     }
-    float* hdr = reinterpret_cast<float*>(out);
-    uint32_t* recs = reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(out) + FTE_HHDR * sizeof(float));
-    cudaError_t e = cudaMemsetAsync(hdr, 0, FTE_HHDR * sizeof(float), s);
-    if (e != cudaSuccess) return e;
-    maxabs_kernel<<<1216, 256, 0, s>>>(f32, nrec, reinterpret_cast<unsigned*>(hdr));
-    scale_final_kernel<<<1, 32, 0, s>>>(hdr);
+    uint32_t* recs = reinterpret_cast<uint32_t*>(out_recs);
 #define FTE_ENC(D, P) encode_kernel<D, P><<<(unsigned)blocks, 256, 0, s>>>(f32, nrec, row, hdr, recs)
     if (dtype == FTE_BF16) { if (pair) FTE_ENC(FTE_BF16, true); else FTE_ENC(FTE_BF16, false); }
     else { if (pair) FTE_ENC(FTE_F16, true); else FTE_ENC(FTE_F16, false); }
 #undef FTE_ENC
     return cudaGetLastError();
+}
+
+cudaError_t launch_quantize(const float* f32, long long nrec, int row, int dtype, int pair, void* out,
+                            cudaStream_t s)
+{
+    if (dtype == FTE_F32) return launch_convert(f32, nrec, row, dtype, pair, nullptr, out, s);
+    float* hdr = reinterpret_cast<float*>(out);
+    const cudaError_t e = launch_scales(f32, nrec, hdr, true, true, s);
+    if (e != cudaSuccess) return e;
+    return launch_convert(f32, nrec, row, dtype, pair, hdr, reinterpret_cast<char*>(out) + FTE_HHDR * sizeof(float), s);
 }
 
 // ---------------------------------------------------------------------------

@@ -314,7 +314,8 @@ fte_status fte_amr_prepare(const fte_background* bg, void* stream)
     fte_status s = check_background(bg);
     if (s != FTE_OK) return s;
     if (bg->grid.amr_levels < 1) return fail(FTE_EINVAL, "not an AMR background");
-    if (bg->grid.dtype != FTE_F32 || bg->grid.layout != FTE_LAYOUT_CELL)
+    const bool table_only = bg->grid.ring > 0 && (bg->grid.dtype != FTE_F32 || bg->grid.layout != FTE_LAYOUT_CELL);
+    if (!table_only && (bg->grid.dtype != FTE_F32 || bg->grid.layout != FTE_LAYOUT_CELL))
         return fail(FTE_EINVAL, "prepare the FP32 cell-layout background, then convert it");
     const GridK g = make_gridk(bg);
     cudaStream_t st = (cudaStream_t)stream;
@@ -327,6 +328,7 @@ fte_status fte_amr_prepare(const fte_background* bg, void* stream)
     if (h[0] || h[1] || h[2] || h[3])
         return fail(FTE_EINVAL, "AMR leaves: %u malformed, %u overlapping finest blocks, %u uncovered, "
                     "%u nesting violations", h[0], h[1], h[2], h[3]);
+    if (table_only) return FTE_OK;     // the slots are filled (ghosts included) as snapshots stream in
     FTE_CUDA(launch_amr_ghosts(g, resident_snapshots(&bg->grid), bg->grid.r_min, bg->grid.r_max, bg->grid.th_min,
                                bg->grid.th_max, st), "AMR ghost launch");
     return FTE_OK;
@@ -1529,33 +1531,65 @@ void stream_runs(const fte_grid* g, const fte_params* prm, int64_t n0, int64_t n
 
 int64_t pmod(int64_t u, int64_t m) { return ((u % m) + m) % m; }
 
-// Copy unwrapped snapshot u from host memory into its ring slot on stream `xs`
-// (AMR: and refill that slot's ghost layer).
-cudaError_t load_slot(const fte_background* bg, const void* host_snapshots, int64_t u, cudaStream_t xs)
+// A ring slot receives host snapshots (FP32 cell records) directly, or through
+// a staging snapshot converted into the slot's storage form.
+bool converts(const fte_grid& g) { return g.dtype != FTE_F32 || g.layout != FTE_LAYOUT_CELL; }
+
+size_t host_snapshot_bytes(const fte_grid& g) { return snapshot_records(&g) * FTE_REC * sizeof(float); }
+
+// Copy host snapshot `logical` into `dst` (FP32 cell records) on `xs` and, for
+// AMR, refill the ghost layer of that one snapshot.
+cudaError_t upload_f32(const fte_background* bg, const void* host_snapshots, int64_t logical, float* dst,
+                       cudaStream_t xs)
 {
     const fte_grid& g = bg->grid;
-    const size_t snap_bytes = snapshot_records(&g) * FTE_REC * sizeof(float);
-    const int64_t slot = pmod(u, g.ring);
-    const int64_t logical = g.periodic ? pmod(u, g.n_snap) : u;
-    float* dst = const_cast<float*>(bg->fields) + (size_t)slot * snapshot_records(&g) * FTE_REC;
-    cudaError_t e = cudaMemcpyAsync(dst, (const char*)host_snapshots + (size_t)logical * snap_bytes, snap_bytes,
+    const size_t bytes = host_snapshot_bytes(g);
+    cudaError_t e = cudaMemcpyAsync(dst, (const char*)host_snapshots + (size_t)logical * bytes, bytes,
                                     cudaMemcpyHostToDevice, xs);
     if (e == cudaSuccess && g.amr_levels > 0) {
         GridK one = make_gridk(bg);
+        one.dtype = FTE_F32;
+        one.pair = 0;
         one.fields = dst;
         e = launch_amr_ghosts(one, 1, g.r_min, g.r_max, g.th_min, g.th_max, xs);
     }
     return e;
 }
 
-fte_status check_stream(const fte_background* bg, const void* host_snapshots, const int64_t* slot_state)
+// Bring unwrapped snapshot u into its ring slot on stream `xs`: straight into an
+// FP32 cell-layout slot, otherwise into `staging` and converted from there
+// (16-bit: with the scales already in the header).
+cudaError_t load_slot(const fte_background* bg, const void* host_snapshots, int64_t u, float* staging,
+                      cudaStream_t xs)
+{
+    const fte_grid& g = bg->grid;
+    const size_t nrec = snapshot_records(&g);
+    const int64_t slot = pmod(u, g.ring);
+    const int64_t logical = g.periodic ? pmod(u, g.n_snap) : u;
+    const size_t head = g.dtype == FTE_F32 ? 0 : FTE_HHDR * sizeof(float);
+    char* slot_ptr = const_cast<char*>(reinterpret_cast<const char*>(bg->fields)) + head +
+                     (size_t)slot * nrec * record_bytes(&g);
+    if (!converts(g)) return upload_f32(bg, host_snapshots, logical, reinterpret_cast<float*>(slot_ptr), xs);
+    cudaError_t e = upload_f32(bg, host_snapshots, logical, staging, xs);
+    if (e != cudaSuccess) return e;
+    return launch_convert(staging, (long long)nrec, row_cells(&g), g.dtype, g.layout == FTE_LAYOUT_PAIR,
+                          bg->fields, slot_ptr, xs);
+}
+
+fte_status check_stream(const fte_background* bg, const void* host_snapshots, const int64_t* slot_state,
+                        const void* staging, size_t staging_bytes)
 {
     fte_status s = check_background(bg);
     if (s != FTE_OK) return s;
     if (bg->grid.ring < 2) return fail(FTE_EINVAL, "streaming needs a ring background (grid.ring >= 2)");
-    if (bg->grid.dtype != FTE_F32 || bg->grid.layout != FTE_LAYOUT_CELL)
-        return fail(FTE_ENOTSUP, "streaming supports FP32 cell-layout snapshots");
     if (!host_snapshots || !slot_state) return fail(FTE_EINVAL, "NULL argument");
+    if (converts(bg->grid)) {
+        if (!staging) return fail(FTE_EINVAL, "a 16-bit or pair-layout ring needs a staging buffer");
+        if ((uintptr_t)staging % 32) return fail(FTE_EINVAL, "staging buffer must be 32-byte aligned");
+        if (staging_bytes < host_snapshot_bytes(bg->grid))
+            return fail(FTE_ENOMEM, "staging buffer has %zu bytes, needs %zu", staging_bytes,
+                        host_snapshot_bytes(bg->grid));
+    }
     return FTE_OK;
 }
 
@@ -1566,7 +1600,32 @@ extern "C" {
 size_t fte_snapshot_bytes(const fte_grid* g)
 {
     if (check_grid(g) != FTE_OK) return 0;
-    return snapshot_records(g) * record_bytes(g);
+    return host_snapshot_bytes(*g);
+}
+
+size_t fte_stream_staging_bytes(const fte_grid* g)
+{
+    if (check_grid(g) != FTE_OK || !converts(*g)) return 0;
+    return host_snapshot_bytes(*g);
+}
+
+fte_status fte_stream_scales(const fte_background* bg, const void* host_snapshots, void* staging,
+                             size_t staging_bytes, void* stream)
+{
+    int64_t unused = -1;
+    fte_status s = check_stream(bg, host_snapshots, &unused, staging, staging_bytes);
+    if (s != FTE_OK) return s;
+    const fte_grid& g = bg->grid;
+    if (g.dtype == FTE_F32) return fail(FTE_EINVAL, "FP32 backgrounds have no scales");
+    cudaStream_t st = (cudaStream_t)stream;
+    float* hdr = const_cast<float*>(bg->fields);
+    float* stage = reinterpret_cast<float*>(staging);
+    for (int u = 0; u < g.n_snap; ++u) {
+        FTE_CUDA(upload_f32(bg, host_snapshots, u, stage, st), "snapshot copy");
+        FTE_CUDA(launch_scales(stage, (long long)snapshot_records(&g), hdr, u == 0, u == g.n_snap - 1, st),
+                 "scale launch");
+    }
+    return FTE_OK;
 }
 
 fte_status fte_stream_plan(const fte_grid* g, const fte_params* prm, int64_t n_start, int64_t n_end,
@@ -1588,22 +1647,23 @@ fte_status fte_stream_plan(const fte_grid* g, const fte_params* prm, int64_t n_s
 }
 
 fte_status fte_stream_load(const fte_background* bg, const void* host_snapshots, int64_t u, int64_t* slot_state,
-                           void* stream)
+                           void* staging, size_t staging_bytes, void* stream)
 {
-    fte_status s = check_stream(bg, host_snapshots, slot_state);
+    fte_status s = check_stream(bg, host_snapshots, slot_state, staging, staging_bytes);
     if (s != FTE_OK) return s;
     if (!bg->grid.periodic && (u < 0 || u >= bg->grid.n_snap)) return fail(FTE_EINVAL, "snapshot %lld out of range", (long long)u);
-    FTE_CUDA(load_slot(bg, host_snapshots, u, (cudaStream_t)stream), "snapshot copy");
+    FTE_CUDA(load_slot(bg, host_snapshots, u, reinterpret_cast<float*>(staging), (cudaStream_t)stream),
+             "snapshot copy");
     slot_state[pmod(u, bg->grid.ring)] = u;
     return FTE_OK;
 }
 
 fte_status fte_advance_streamed(fte_particles* P, const fte_background* bg, const void* host_snapshots,
                                 const fte_params* prm, const fte_tally_buf* t, int64_t n_start, int64_t n_end,
-                                int64_t* slot_state, void* ws, size_t ws_bytes, void* compute_stream,
-                                void* copy_stream)
+                                int64_t* slot_state, void* staging, size_t staging_bytes, void* ws,
+                                size_t ws_bytes, void* compute_stream, void* copy_stream)
 {
-    fte_status s = check_stream(bg, host_snapshots, slot_state);
+    fte_status s = check_stream(bg, host_snapshots, slot_state, staging, staging_bytes);
     if (s != FTE_OK) return s;
     const fte_grid& g = bg->grid;
     if (!prm) return fail(FTE_EINVAL, "NULL params");
@@ -1647,7 +1707,7 @@ fte_status fte_advance_streamed(fte_particles* P, const fte_background* bg, cons
             const cudaError_t e = cudaStreamWaitEvent(xs, freed[slot], 0);
             if (e != cudaSuccess) { fail_cuda(e, "copy wait"); return; }
         }
-        cudaError_t e = load_slot(bg, host_snapshots, u, xs);
+        cudaError_t e = load_slot(bg, host_snapshots, u, reinterpret_cast<float*>(staging), xs);
         if (e == cudaSuccess) e = cudaEventRecord(ready[slot], xs);
         if (e != cudaSuccess) { fail_cuda(e, "snapshot copy"); return; }
         has_ready[slot] = 1;

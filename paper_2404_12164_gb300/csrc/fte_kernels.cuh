@@ -174,5 +174,11 @@ cudaError_t launch_probe(const float* buf, unsigned long long nsec, int threads,
 // (scale header + records) in the cell or pair layout, or FP32 pair records
 cudaError_t launch_quantize(const float* f32, long long nrec, int row, int dtype, int pair, void* out,
                             cudaStream_t s);
+// the two halves of launch_quantize, for one snapshot at a time: per-field
+// scales folded over calls (first: zero the header; last: finalise), and the
+// conversion of nrec records into `out_recs` with the scales in `hdr`
+cudaError_t launch_scales(const float* f32, long long nrec, float* hdr, bool first, bool last, cudaStream_t s);
+cudaError_t launch_convert(const float* f32, long long nrec, int row, int dtype, int pair, const float* hdr,
+                           void* out_recs, cudaStream_t s);
 
 }  // namespace fte

@@ -36,7 +36,7 @@ def test_every_declared_symbol_is_exported(L):
 
 
 def test_version_and_status_strings(L):
-    assert L.fte_abi_version() == 1
+    assert L.fte_abi_version() == 2
     assert L.fte_status_string(0) == b"ok"
     assert L.fte_status_string(1) == b"invalid argument"
 
@@ -139,6 +139,15 @@ def test_stream_plan_and_ring_sizes(L):
     snap = 16 * 8 * 8 * 96
     assert L.fte_snapshot_bytes(C.byref(api.grid_c(g))) == snap
     assert L.fte_background_bytes(C.byref(api.grid_c(g, ring=3))) == 3 * snap
+    assert L.fte_stream_staging_bytes(C.byref(api.grid_c(g, ring=3))) == 0
+    # host snapshots stay FP32 cell records whatever the slots hold; converted slots need
+    # one staging snapshot
+    for dt, lay, rec in (("bf16", "cell", 64), ("f16", "pair", 96), ("f32", "pair", 160)):
+        gc = api.grid_c(g, dtype=dt, ring=3, layout=lay)
+        head = 0 if dt == "f32" else 128
+        assert L.fte_snapshot_bytes(C.byref(gc)) == snap
+        assert L.fte_stream_staging_bytes(C.byref(gc)) == snap
+        assert L.fte_background_bytes(C.byref(gc)) == head + 3 * 16 * 8 * 8 * rec
     for bad in (1, 25, -1):
         assert L.fte_background_bytes(C.byref(api.grid_c(g, ring=bad))) == 0
 

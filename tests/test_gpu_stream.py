@@ -2,7 +2,10 @@
 with all snapshots resident and with 2 or 3 slots filled on demand from host
 memory gives the same trajectories (bit for bit) and the same tallies, for
 periodic and non-periodic sequences and for block-AMR backgrounds (whose ghost
-layers are refilled on the device after each upload)."""
+layers are refilled on the device after each upload).  Rings in 16-bit or pair
+storage convert each FP32 host snapshot on the device through a staging buffer;
+their scales come from all host snapshots, so they equal the resident background
+converted by fte_quantize_background, and so do the trajectories."""
 import math
 
 import numpy as np
@@ -99,21 +102,78 @@ def test_amr_ring_refills_ghosts():
     _same(got, ref)
 
 
+def _uniform(n_snap=6, periodic=True):
+    w = configs.scaled(configs.cir_uniform_1e6(), nr=96, nth=24, nph=72, n_snap=n_snap, n_particles=3000)
+    w.grid.periodic = periodic
+    w.grid.dt_snap = 600.0
+    w.params.sort_every = 32
+    w.inject.divv_max = None
+    return w, configs.build_background(w)
+
+
+@pytest.mark.parametrize("dtype,layout", [("bf16", "cell"), ("f16", "pair"), ("f32", "pair"), ("bf16", "pair")])
+def test_converted_ring_equals_resident(dtype, layout):
+    from paper_2404_12164_gb300 import api
+    w, f = _uniform(periodic=(dtype != "f16"))
+    n_steps = 800
+    b32 = api.Background(w.grid)
+    api.fte_load_background(b32, f)
+    res = api.Background(w.grid, dtype=dtype, layout=layout)
+    api.fte_quantize_background(res, b32)
+    ref = _run(res, w, w.n_particles, n_steps)
+    bg = api.Background(w.grid, dtype=dtype, ring=3, layout=layout)
+    st = api.SnapshotStream(bg, f)
+    if dtype != "f32":                  # the scale header equals the resident one
+        assert np.array_equal(api.device_bytes(bg)[:128], api.device_bytes(res)[:128])
+    got = _run(bg, w, w.n_particles, n_steps, st, splits=(0, 333))
+    _same(got, ref)
+
+
+def test_converted_amr_ring():
+    from paper_2404_12164_gb300 import api
+    spec = amr.AmrSpec(nbr=4, nbt=2, nbp=4, bsize=8, levels=3, n_snap=4, periodic=False, dt_snap=1500.0)
+    leaves = amr.build_leaves(spec, amr.divv_refiner(spec, threshold=8e-6, r_from=0.9))
+    f = amr.fields(spec, leaves)
+    w = configs.cir_uniform_1e6()
+    w.inject = InjectSpec(region="box", r1=1.0, r2=1.8, th1=88 * DEG, th2=92 * DEG, ph1=math.pi, ph2=2 * math.pi,
+                          energy="mono", e0=0.05, weight="r-2", seed=2)
+    w.params = Params(dmumu="qlt", lambda_par=0.1, dt=10.0, sort_every=32)
+    cell = api.AmrBackground(spec, leaves)
+    api.fte_load_background(cell, f)
+    api.fte_amr_prepare(cell)
+    res = api.AmrBackground(spec, leaves, dtype="bf16", share=cell, layout="pair")
+    api.fte_quantize_background(res, cell)
+    ref = _run(res, w, 2000, 600)
+    bg = api.AmrBackground(spec, leaves, dtype="bf16", ring=2, layout="pair")
+    api.fte_amr_prepare(bg)                      # the table only: slots fill as snapshots stream in
+    st = api.SnapshotStream(bg, f)
+    got = _run(bg, w, 2000, 600, st)
+    _same(got, ref)
+
+
 def test_streaming_refusals():
+    import ctypes as C
+    import torch
     from paper_2404_12164_gb300 import api, _abi as A
     w = configs.scaled(configs.cir_uniform_1e6(), nr=32, nth=8, nph=16, n_snap=4, n_particles=10)
     f = configs.build_background(w)
     plain = api.Background(w.grid)
     with pytest.raises(ValueError):
         api.SnapshotStream(plain, f)
+    host = torch.from_numpy(np.ascontiguousarray(f)).pin_memory()
+    slots = np.full(2, -1, dtype=np.int64)
+    L = A.lib()
+    s = C.c_void_p(torch.cuda.current_stream().cuda_stream)
     half = api.Background(w.grid, dtype="bf16", ring=2)
-    st = api.SnapshotStream.__new__(api.SnapshotStream)
-    st.host = __import__("torch").from_numpy(np.ascontiguousarray(f)).pin_memory()
-    st.slots = np.full(2, -1, dtype=np.int64)
-    st.copy_stream = __import__("torch").cuda.Stream()
-    pool = api.Particles(10)
-    tally = api.Tally(OBS)
-    api.fte_tally_reset(tally)
-    with pytest.raises(A.FteError) as e:
-        api.fte_advance_streamed(pool, half, st, w.params, tally, 0, 10)
-    assert e.value.status == A.FTE_ENOTSUP
+    need = L.fte_stream_staging_bytes(C.byref(half.gc))
+    assert need == api.fte_snapshot_bytes(half) > 0
+    stage = torch.empty(need, dtype=torch.uint8, device="cuda")
+    hp, sp, stp = C.c_void_p(host.data_ptr()), C.c_void_p(slots.ctypes.data), C.c_void_p(stage.data_ptr())
+    assert L.fte_stream_load(C.byref(half.c), hp, 0, sp, None, 0, s) == A.FTE_EINVAL
+    assert L.fte_stream_load(C.byref(half.c), hp, 0, sp, stp, need - 32, s) == A.FTE_ENOMEM
+    assert L.fte_stream_scales(C.byref(half.c), hp, stp, need, s) == A.FTE_OK
+    assert L.fte_stream_load(C.byref(half.c), hp, 0, sp, stp, need, s) == A.FTE_OK
+    assert slots[0] == 0
+    ring32 = api.Background(w.grid, ring=2)
+    assert L.fte_stream_scales(C.byref(ring32.c), hp, stp, need, s) == A.FTE_EINVAL
+    torch.cuda.synchronize()
