@@ -62,12 +62,12 @@ def _dist():
 
 
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "advance_kernel_traffic.json")
-KERNEL_SOURCES = ("fte_advance.cu", "fte_device.cuh", "fte_kernels.cuh", "fte_step.cuh")
+KERNEL_SOURCES = ("fte_advance.cu", "fte_device.cuh", "fte_kernels.cuh", "fte_step.cuh", "fte_sort.cu")
 
 
 def kernel_sources_hash():
-    """sha256 of the step kernel's sources: DRAM traffic measured by ncu is reported only while
-    the kernel it was measured on is unchanged."""
+    """sha256 of the step kernel's sources and of the particle ordering that sets its access
+    pattern: DRAM traffic measured by ncu is reported only while both are unchanged."""
     import hashlib
     h = hashlib.sha256()
     for name in KERNEL_SOURCES:

@@ -1,5 +1,5 @@
-// Spatial ordering of the alive particles: a counting sort by grid bucket (two
-// r-cells of one (theta, phi) column, of the grid or of a block-AMR leaf), so
+// Spatial ordering of the alive particles: a counting sort by grid bucket (the
+// lower corner of the interpolation stencil, radial index in pairs), so
 // that consecutive entries of the order list - and so the lanes of a warp - read
 // the same cache lines of the background.  Dead particles are left out, which
 // also compacts the work list.  Performance only: each particle's trajectory does not depend on the order.
@@ -8,6 +8,11 @@
 namespace fte {
 
 
+// Bucket of a point: the lower corner (i0, j0, k0) of its interpolation stencil -
+// the first of the records the step gathers - with i0 taken in pairs, so that the
+// particles of one bucket read the same corner records (a bucket by the cell
+// holding the point would mix up to 3 x 2 x 2 different stencils).  The index
+// arithmetic follows locate / locate_amr.
 __device__ __forceinline__ int bucket_of(const GridK& g, float x, float y, float z)
 {
     const float rho2 = x * x + y * y;
@@ -15,15 +20,31 @@ __device__ __forceinline__ int bucket_of(const GridK& g, float x, float y, float
     const float th = atan2f(sqrtf(rho2), z);
     float ph = atan2f(y, x);
     if (ph < 0.f) ph += kTwoPi;
-    if (g.amr) {      // AMR: leaf, then two r-cells of one (theta, phi) column of it
-        int ci, cj, ck;
-        const int leaf = amr_containing(g, r, th, ph, ci, cj, ck);
-        return ((leaf * g.B + ck) * g.B + cj) * ((g.B + 1) >> 1) + (ci >> 1);
-    }
     const float xr = g.radial ? logf(r / g.r_min) * g.inv_dr : (r - g.r_min) * g.inv_dr;
-    const int i = min(max((int)xr, 0), g.nr - 1);
-    const int j = min(max((int)((th - g.th_min) * g.inv_dth), 0), g.nth - 1);
-    int k = (int)(ph * g.inv_dph);
+    const float xt = (th - g.th_min) * g.inv_dth;
+    const float xp = ph * g.inv_dph;
+    if (g.amr) {      // AMR: leaf, then the stencil corner on its padded lattice (0 .. B)
+        const float ur = g.radial ? logf(r / g.r_min) * g.inv_lnr : (r - g.r_min) * g.inv_lnr;
+        const float ut = (th - g.th_min) * g.inv_thspan;
+        const float up = ph * (1.f / kTwoPi);
+        const int f0 = min(max((int)floorf(ur * (float)g.nf0), 0), g.nf0 - 1);
+        const int f1 = min(max((int)floorf(ut * (float)g.nf1), 0), g.nf1 - 1);
+        int f2 = (int)floorf(up * (float)g.nf2);
+        if (f2 < 0) f2 += g.nf2;
+        if (f2 >= g.nf2) f2 -= g.nf2;
+        const int leaf = min(max(__ldg(g.table + ((long long)f2 * g.nf1 + f1) * g.nf0 + f0), 0), g.amr_leaves - 1);
+        const int4 lf = __ldg(g.leaves + leaf);
+        const float s = (float)(1 << lf.x);
+        const int B = g.B;
+        const int ii = min(max((int)floorf(xr * s - 0.5f) - (lf.y * B - 1), 0), B);
+        const int jj = min(max((int)floorf(xt * s - 0.5f) - (lf.z * B - 1), 0), B);
+        const int kk = min(max((int)floorf(xp * s - 0.5f) - (lf.w * B - 1), 0), B);
+        return ((leaf * (B + 1) + kk) * (B + 1) + jj) * ((B + 2) >> 1) + (ii >> 1);
+    }
+    const int i = min(max((int)floorf(xr - 0.5f), 0), g.nr - 2);
+    const int j = min(max((int)floorf(xt - 0.5f), 0), g.nth - 2);
+    int k = (int)floorf(xp - 0.5f);
+    if (k < 0) k += g.nph;
     k = min(max(k, 0), g.nph - 1);
     const int nrb = (g.nr + 1) >> 1;
     return (k * g.nth + j) * nrb + (i >> 1);
@@ -135,7 +156,7 @@ __global__ void __launch_bounds__(256) scatter_kernel(const SortArgs a)
 
 int sort_buckets(const GridK& g)
 {
-    if (g.amr) return g.amr_leaves * g.B * g.B * ((g.B + 1) >> 1);
+    if (g.amr) return g.amr_leaves * (g.B + 1) * (g.B + 1) * ((g.B + 2) >> 1);
     return g.nph * g.nth * ((g.nr + 1) >> 1);
 }
 
