@@ -18,20 +18,37 @@ static const void* single_fn(int kperp, int dtype)
                  : (const void*)advance_kernel<false, FTE_F32, MODE, kThreads, LAY>;
 }
 
-// the single-set kernels come in one variant per record layout (pair: 1) and tally mode
-static const void* advance_fn(int kperp, int dtype, int mode, int nt, int pair)
+// the 3-blocks-per-SM builds (global tally, no cross-field diffusion)
+template <int LAY>
+static const void* dense_fn(int dtype)
+{
+    if (dtype == FTE_BF16) return (const void*)advance_kernel<false, FTE_BF16, kModeSingleGlobal, kThreads, LAY, 3>;
+    if (dtype == FTE_F16) return (const void*)advance_kernel<false, FTE_F16, kModeSingleGlobal, kThreads, LAY, 3>;
+    return (const void*)advance_kernel<false, FTE_F32, kModeSingleGlobal, kThreads, LAY, 3>;
+}
+
+bool dense_variant(int kperp, int dtype, int mode, int amr)
+{
+    return mode == kModeSingleGlobal && !kperp && (amr || dtype != FTE_F32);
+}
+
+// the single-set kernels come in one variant per record layout (pair: 1) and tally
+// mode, and for dense_variant() in a 3-blocks-per-SM build
+static const void* advance_fn(int kperp, int dtype, int mode, int nt, int pair, int amr)
 {
     if (!single_set(mode)) return advance_fn_batched(kperp, dtype, mode, nt);
     if (nt != kThreads) return nullptr;
+    if (dense_variant(kperp, dtype, mode, amr)) return pair ? dense_fn<kLayPair>(dtype) : dense_fn<kLayCell>(dtype);
     if (mode == kModeSingleGlobal)
         return pair ? single_fn<kModeSingleGlobal, kLayPair>(kperp, dtype)
                     : single_fn<kModeSingleGlobal, kLayCell>(kperp, dtype);
     return pair ? single_fn<kModeSingle, kLayPair>(kperp, dtype) : single_fn<kModeSingle, kLayCell>(kperp, dtype);
 }
 
-cudaError_t advance_occupancy(int kperp, int dtype, int mode, int nt, int pair, size_t smem, int* blocks_per_sm)
+cudaError_t advance_occupancy(int kperp, int dtype, int mode, int nt, int pair, int amr, size_t smem,
+                              int* blocks_per_sm)
 {
-    const void* fn = advance_fn(kperp, dtype, mode, nt, pair);
+    const void* fn = advance_fn(kperp, dtype, mode, nt, pair, amr);
     if (!fn) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -42,7 +59,7 @@ cudaError_t launch_advance(const AdvanceArgs& a, const BatchArgs& b, int kperp, 
                            size_t smem, cudaStream_t s)
 {
     if (!single_set(mode)) return launch_advance_batched(a, b, kperp, mode, nt, blocks, smem, s);
-    const void* fn = advance_fn(kperp, a.g.dtype, mode, nt, a.g.pair);
+    const void* fn = advance_fn(kperp, a.g.dtype, mode, nt, a.g.pair, a.g.amr > 0);
     if (!fn) return cudaErrorInvalidValue;
     void* args[] = {(void*)&a, (void*)&b};
     return cudaLaunchKernel(fn, dim3(blocks), dim3(nt), args, smem, s);

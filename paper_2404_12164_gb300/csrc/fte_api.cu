@@ -230,7 +230,7 @@ size_t single_smem(int mode, size_t nbins)
     return mode == kModeSingle ? 3 * sizeof(float) * (nbins ? nbins : 1) : 0;
 }
 
-fte_status layout(int device, int kperp, int dtype, int pair, int mode, size_t nbins, long long n_steps,
+fte_status layout(int device, int kperp, int dtype, int pair, int amr, int mode, size_t nbins, long long n_steps,
                   size_t sort_bytes, WsLayout* L)
 {
     const int sms = device_sms(device);
@@ -240,7 +240,7 @@ fte_status layout(int device, int kperp, int dtype, int pair, int mode, size_t n
     int cur = 0;
     FTE_CUDA(cudaGetDevice(&cur), "cudaGetDevice");
     if (cur != device) FTE_CUDA(cudaSetDevice(device), "cudaSetDevice");
-    cudaError_t e = advance_occupancy(kperp, dtype, mode, kThreads, pair, smem, &per_sm);
+    cudaError_t e = advance_occupancy(kperp, dtype, mode, kThreads, pair, amr, smem, &per_sm);
     if (cur != device) cudaSetDevice(cur);
     if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
     if (per_sm < 1) return fail(FTE_ENOTSUP, "step kernel does not fit on an SM with %zu bytes of tally", smem);
@@ -396,7 +396,8 @@ size_t fte_workspace_bytes(int device, const fte_grid* g, const fte_tally_buf* t
                 for (int mode : {kModeSingle, kModeSingleGlobal}) {
                     if (mode == kModeSingle && nb > (size_t)kMaxSmemBins) continue;
                     WsLayout L;
-                    if (layout(device, kperp, dtype, pair, mode, nb, n_steps, sort_bytes, &L) != FTE_OK) return 0;
+                    if (layout(device, kperp, dtype, pair, g->amr_levels > 0, mode, nb, n_steps, sort_bytes, &L) != FTE_OK)
+                        return 0;
                     if (L.total > best) best = L.total;
                 }
     return best;
@@ -497,7 +498,8 @@ fte_status fte_advance(fte_particles* P, const fte_background* bg, const fte_par
     const GridK gk = make_gridk(bg);
     const int sorting = prm->sort_every > 0;
     WsLayout L;
-    s = layout(device, kperp, bg->grid.dtype, gk.pair, mode, nb, nsteps, sorting ? sort_scratch_bytes(gk, P->count) : 0,
+    s = layout(device, kperp, bg->grid.dtype, gk.pair, gk.amr > 0, mode, nb, nsteps,
+               sorting ? sort_scratch_bytes(gk, P->count) : 0,
                &L);
     if (s != FTE_OK) return s;
     if (ws_bytes < L.total) return fail(FTE_ENOMEM, "workspace has %zu bytes, needs %zu", ws_bytes, L.total);
@@ -563,8 +565,8 @@ fte_status fte_advance(fte_particles* P, const fte_background* bg, const fte_par
     const long long chunk = sorting ? (prm->sort_every < kChunkSteps ? prm->sort_every : kChunkSteps) : kChunkSteps;
     const size_t smem = single_smem(mode, nb);
     int per_sm = 0;
-    FTE_CUDA(advance_occupancy(kperp, bg->grid.dtype, mode, kThreads, bg->grid.layout == FTE_LAYOUT_PAIR, smem,
-                               &per_sm), "occupancy");
+    FTE_CUDA(advance_occupancy(kperp, bg->grid.dtype, mode, kThreads, bg->grid.layout == FTE_LAYOUT_PAIR, gk.amr > 0,
+                               smem, &per_sm), "occupancy");
 
     for (long long c0 = n_start; c0 < n_end; c0 += chunk) {
         a.n_start = c0;
@@ -761,7 +763,7 @@ extern "C" fte_status fte_advance_noalloc(fte_particles* P, const fte_background
     const size_t smem = part_block;
     int per_sm = 0;
     FTE_CUDA(advance_occupancy(kperp, bg->grid.dtype, kModeSingle, kThreads, bg->grid.layout == FTE_LAYOUT_PAIR,
-                                smem, &per_sm), "occupancy");
+                                bg->grid.amr_levels > 0, smem, &per_sm), "occupancy");
     if (per_sm < 1) return fail(FTE_ENOTSUP, "step kernel does not fit on an SM with %zu bytes of tally", smem);
     long long max_blocks = (long long)sms * per_sm;
     if ((size_t)max_blocks > fit) max_blocks = (long long)fit;
@@ -852,7 +854,7 @@ fte_status ens_layout(int device, int kperp, int dtype, int mode, int nt, int n_
     int per_sm = 0, cur = 0;
     FTE_CUDA(cudaGetDevice(&cur), "cudaGetDevice");
     if (cur != device) FTE_CUDA(cudaSetDevice(device), "cudaSetDevice");
-    cudaError_t e = advance_occupancy(kperp, dtype, mode, nt, 0, smem, &per_sm);
+    cudaError_t e = advance_occupancy(kperp, dtype, mode, nt, 0, 0, smem, &per_sm);
     if (cur != device) cudaSetDevice(cur);
     if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
     if (per_sm < 1) return fail(FTE_ENOTSUP, "ensemble step kernel does not fit on an SM with %zu bytes of tally", smem);

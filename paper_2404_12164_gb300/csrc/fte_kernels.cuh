@@ -132,7 +132,12 @@ struct AdjK {
 cudaError_t launch_advance(const AdvanceArgs& a, const BatchArgs& b, int kperp, int mode, int nt, int blocks,
                            size_t smem, cudaStream_t s);
 // resident blocks per SM of a step kernel (`pair`: record layout of a single-set kernel)
-cudaError_t advance_occupancy(int kperp, int dtype, int mode, int nt, int pair, size_t smem, int* blocks_per_sm);
+cudaError_t advance_occupancy(int kperp, int dtype, int mode, int nt, int pair, int amr, size_t smem,
+                              int* blocks_per_sm);
+// whether the single-set step kernel runs in its 3-blocks-per-SM build: block AMR
+// or 16-bit storage with the global tally and no cross-field diffusion (uniform
+// FP32 grids keep the unconstrained build, which spills under the tighter limit)
+bool dense_variant(int kperp, int dtype, int mode, int amr);
 // the ensemble variants live in their own translation unit (fte_batched.cu)
 const void* advance_fn_batched(int kperp, int dtype, int mode, int nt);
 cudaError_t launch_advance_batched(const AdvanceArgs& a, const BatchArgs& b, int kperp, int mode, int nt,

@@ -240,9 +240,11 @@ __device__ __forceinline__ int set_of(const unsigned long long* end, int n_sets,
 // (per-set parameters and tallies, the tallies of all sets in shared memory);
 // kModeGlobal: an ensemble with warp-merged FP64 atomics to the tally.
 // LAY: record layout, compile-time for the single-set kernels, read from the
-// grid (kLayAny) by the ensemble kernels.
-template <bool KPERP, int DT, int MODE, int NT, int LAY>
-__global__ void __launch_bounds__(NT, single_set(MODE) ? 0 : 512 / NT) advance_kernel(const AdvanceArgs a, const BatchArgs b)
+// grid (kLayAny) by the ensemble kernels.  MINB: blocks per SM the single-set
+// kernel is compiled for (0: the register count ptxas chooses; 3: at most 85
+// registers, 24 warps per SM, for the longer dependent-load chains of block AMR).
+template <bool KPERP, int DT, int MODE, int NT, int LAY, int MINB = 0>
+__global__ void __launch_bounds__(NT, single_set(MODE) ? MINB : 512 / NT) advance_kernel(const AdvanceArgs a, const BatchArgs b)
 {
     extern __shared__ float sh[];
     const int nsh = global_tally(MODE) ? 0 : (MODE == kModeShared ? b.n_sets : 1) * a.nbins;
