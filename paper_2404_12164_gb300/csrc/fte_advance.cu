@@ -18,13 +18,15 @@ static const void* single_fn(int kperp, int dtype)
                  : (const void*)advance_kernel<false, FTE_F32, MODE, kThreads, LAY>;
 }
 
-// the 3-blocks-per-SM builds (global tally, no cross-field diffusion)
+// the denser builds (768 threads per SM: at most 85 registers; global tally, no
+// cross-field diffusion)
+constexpr int kDenseBlocks = 768 / kThreads;
 template <int LAY>
 static const void* dense_fn(int dtype)
 {
-    if (dtype == FTE_BF16) return (const void*)advance_kernel<false, FTE_BF16, kModeSingleGlobal, kThreads, LAY, 3>;
-    if (dtype == FTE_F16) return (const void*)advance_kernel<false, FTE_F16, kModeSingleGlobal, kThreads, LAY, 3>;
-    return (const void*)advance_kernel<false, FTE_F32, kModeSingleGlobal, kThreads, LAY, 3>;
+    if (dtype == FTE_BF16) return (const void*)advance_kernel<false, FTE_BF16, kModeSingleGlobal, kThreads, LAY, kDenseBlocks>;
+    if (dtype == FTE_F16) return (const void*)advance_kernel<false, FTE_F16, kModeSingleGlobal, kThreads, LAY, kDenseBlocks>;
+    return (const void*)advance_kernel<false, FTE_F32, kModeSingleGlobal, kThreads, LAY, kDenseBlocks>;
 }
 
 bool dense_variant(int kperp, int dtype, int mode, int amr)
