@@ -223,9 +223,9 @@ typedef struct fte_params {
     double lambda_par, p_ref, alpha, q, H, eps, mu_floor, lambda_perp;
     double dt, t0;
     uint32_t seed, set_id;
-    int32_t sort_every;        /* > 0: reorder the alive particles by interpolation stencil every
-                                  sort_every steps (performance only: results do not
-                                  depend on it); 0: no reordering */
+    int32_t sort_every;        /* > 0: reorder the alive particles by interpolation stencil
+                                  (and sign of mu) every sort_every steps (performance
+                                  only: results do not depend on it); 0: no reordering */
     int32_t tally_layout;      /* fte_advance: FTE_LAYOUT_GLOBAL (or 0): lanes of a warp in the
                                   same bin are merged and added to the tally with FP64 atomics;
                                   FTE_LAYOUT_SHARED: per-block histograms in shared memory

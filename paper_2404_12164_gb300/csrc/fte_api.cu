@@ -537,7 +537,7 @@ fte_status fte_advance(fte_particles* P, const fte_background* bg, const fte_par
     if (sorting) {
         sort_carve(gk, P->count, w + L.off_sort, &sa);
         sa.g = gk;
-        sa.x = P->x; sa.y = P->y; sa.z = P->z; sa.status = P->status; sa.n = P->count;
+        sa.x = P->x; sa.y = P->y; sa.z = P->z; sa.mu = P->mu; sa.status = P->status; sa.n = P->count;
         a.order = sa.order;
         a.n_order = sa.hist + sa.nb;
     }
@@ -967,7 +967,7 @@ fte_status ens_run(fte_particles* P, const fte_background* bg, const fte_params*
     if (sorting) {
         sort_carve(gk, P->count, w + L.off_sort, &sa);
         sa.g = gk;
-        sa.x = P->x; sa.y = P->y; sa.z = P->z; sa.status = P->status; sa.n = P->count;
+        sa.x = P->x; sa.y = P->y; sa.z = P->z; sa.mu = P->mu; sa.status = P->status; sa.n = P->count;
         a.order = sa.order;
         a.n_order = sa.hist + sa.nb;
     }
@@ -1423,7 +1423,7 @@ fte_status fte_adjoint_forward(fte_particles* P, const fte_background* bg, const
     if (sorting) {
         sort_carve(a.g, P->count, w + L.off_sort, &sa);
         sa.g = a.g;
-        sa.x = P->x; sa.y = P->y; sa.z = P->z; sa.status = P->status; sa.n = P->count;
+        sa.x = P->x; sa.y = P->y; sa.z = P->z; sa.mu = P->mu; sa.status = P->status; sa.n = P->count;
         a.order = sa.order;
         a.n_order = sa.hist + sa.nb;
     }
@@ -1488,7 +1488,7 @@ fte_status fte_adjoint_reverse(const fte_particles* P, const fte_background* bg,
         k.last = seg == 0;
         if (sorting) {
             const float* c = k.ckpt + (size_t)seg * 5 * n;
-            sa.x = c; sa.y = c + n; sa.z = c + 2 * n;
+            sa.x = c; sa.y = c + n; sa.z = c + 2 * n; sa.mu = c + 3 * n;
             sa.steps_min = seg * (long long)checkpoint_every;
             FTE_CUDA(launch_sort(sa, st), "sort launch");
         }

@@ -54,6 +54,7 @@ struct AdvanceArgs {
 struct SortArgs {
     GridK g;
     const float *x, *y, *z;
+    const float* mu;              // pitch-angle cosine (NULL: ordered by position only)
     const uint8_t* status;        // entries with status FTE_ALIVE are ordered ...
     const int* steps;             // ... or, when set, entries with steps[i] > steps_min
     long long steps_min;

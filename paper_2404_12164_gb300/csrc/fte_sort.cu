@@ -1,5 +1,6 @@
 // Spatial ordering of the alive particles: a counting sort by grid bucket (the
-// lower corner of the interpolation stencil, radial index in pairs), so
+// lower corner of the interpolation stencil, radial index in pairs, and the sign
+// of mu), so
 // that consecutive entries of the order list - and so the lanes of a warp - read
 // the same cache lines of the background.  Dead particles are left out, which
 // also compacts the work list.  Performance only: each particle's trajectory does not depend on the order.
@@ -50,13 +51,22 @@ __device__ __forceinline__ int bucket_of(const GridK& g, float x, float y, float
     return (k * g.nth + j) * nrb + (i >> 1);
 }
 
+// Within a bucket the particles are grouped by the sign of the pitch-angle cosine
+// (kMuBins equal bins of mu): particles moving the same way along the field stay
+// together for longer (mu changes on the scattering time, many reorderings apart),
+// so the lanes of a warp keep sharing records through the launch.  Two bins
+// measured best: four halve the particles per bucket for a smaller gain.
+constexpr int kMuBins = 2;
+
 __global__ void __launch_bounds__(256) key_kernel(const SortArgs a)
 {
     const unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.n) return;
     int key = -1, rank = 0;
     if (a.steps ? a.steps[i] > a.steps_min : a.status[i] == FTE_ALIVE) {
-        key = bucket_of(a.g, a.x[i], a.y[i], a.z[i]);
+        int mb = 0;
+        if (a.mu) mb = min(max((int)((a.mu[i] + 1.f) * (0.5f * kMuBins)), 0), kMuBins - 1);
+        key = bucket_of(a.g, a.x[i], a.y[i], a.z[i]) * kMuBins + mb;
         rank = (int)atomicAdd(a.hist + key, 1u);
     }
     a.key[i] = key;
@@ -156,8 +166,8 @@ __global__ void __launch_bounds__(256) scatter_kernel(const SortArgs a)
 
 int sort_buckets(const GridK& g)
 {
-    if (g.amr) return g.amr_leaves * (g.B + 1) * (g.B + 1) * ((g.B + 2) >> 1);
-    return g.nph * g.nth * ((g.nr + 1) >> 1);
+    if (g.amr) return g.amr_leaves * (g.B + 1) * (g.B + 1) * ((g.B + 2) >> 1) * kMuBins;
+    return g.nph * g.nth * ((g.nr + 1) >> 1) * kMuBins;
 }
 
 size_t sort_scratch_bytes(const GridK& g, unsigned long long n)
