@@ -344,9 +344,11 @@ fte_status fte_stream_scales(const fte_background* bg, const void* host_snapshot
    0) and a conversion into the slot; for AMR the ghost cells of a copied
    snapshot are refilled on the device - and the run is advanced on
    compute_stream once its slots are filled; a slot is overwritten only after
-   the steps using it are done.  slot_state (HOST, ring entries, caller-owned,
-   -1 = empty before the first call) records the unwrapped snapshot each slot
-   holds and is updated.  ws as for fte_advance with n_steps = the longest run.
+   the steps using it are done; a slot already holding the snapshot (periodic
+   sequences: the same snapshot of another period) is not copied again, so a
+   ring of n_snap slots over a periodic sequence copies each snapshot once.
+   slot_state (HOST, ring entries, caller-owned, -1 = empty before the first
+   call) records the unwrapped snapshot each slot holds and is updated.  ws as for fte_advance with n_steps = the longest run.
    Work of earlier calls on either stream is waited for.  EINVAL/ENOMEM for a
    missing or undersized staging buffer.  Asynchronous. */
 fte_status fte_advance_streamed(fte_particles* P, const fte_background* bg, const void* host_snapshots,

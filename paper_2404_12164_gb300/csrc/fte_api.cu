@@ -1698,12 +1698,17 @@ fte_status fte_advance_streamed(fte_particles* P, const fte_background* bg, cons
         if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, fence_x, 0);
         if (e != cudaSuccess) fail_cuda(e, "stream ordering");
     }
-    // bring unwrapped snapshot u into its slot (unless already there or, for a
+    // bring unwrapped snapshot u into its slot (unless already there - for a
+    // periodic sequence, the same snapshot of an earlier period counts - or, for a
     // prefetch, the slot is in use by the current run)
     auto ensure = [&](int64_t u, int busy0, int busy1, bool prefetch) {
         if (result != FTE_OK) return;
         const int slot = (int)pmod(u, R);
         if (slot_state[slot] == u) return;
+        if (g.periodic && slot_state[slot] >= 0 && pmod(slot_state[slot], g.n_snap) == pmod(u, g.n_snap)) {
+            slot_state[slot] = u;
+            return;
+        }
         if (prefetch && (slot == busy0 || slot == busy1)) return;
         if (has_freed[slot]) {
             const cudaError_t e = cudaStreamWaitEvent(xs, freed[slot], 0);

@@ -58,7 +58,7 @@ def _same(a, b):
 
 
 @pytest.mark.parametrize("periodic", [True, False])
-@pytest.mark.parametrize("ring", [2, 3])
+@pytest.mark.parametrize("ring", [2, 3, 6])
 def test_uniform_ring_equals_resident(periodic, ring):
     from paper_2404_12164_gb300 import api
     w = configs.scaled(configs.cir_uniform_1e6(), nr=96, nth=24, nph=72, n_snap=6, n_particles=3000)
@@ -78,6 +78,8 @@ def test_uniform_ring_equals_resident(periodic, ring):
     plan = api.fte_stream_plan(bg, w.params, 0, n_steps)
     if periodic:
         assert len(plan) == 14 and np.all(plan[:-1, 1] - plan[:-1, 0] == 60)
+        if ring == 6:          # one slot per snapshot: the second period reuses the first one's
+            assert sorted(st.slots % 6) == list(range(6)) and st.slots.max() >= 6
     else:
         assert plan[-1, 2] == -1 - 5 and plan[-1, 1] == n_steps
 
