@@ -301,6 +301,29 @@ __device__ __forceinline__ void ldg8u(const uint32_t* q, uint32_t* v)
         : "l"(q));
 }
 
+// Narrower loads for the tail of a record: the L1 returns a warp's loaded bytes to
+// registers at 128 bytes per data-pipe wavefront, so bytes of padding loaded cost
+// as much as bytes used.  Alignment: 16 (v4), 8 (v2) or 4 bytes.
+__device__ __forceinline__ void ldg4(const float* q, float* v)
+{
+    asm("ld.global.nc.v4.f32 {%0,%1,%2,%3}, [%4];" : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]) : "l"(q));
+}
+
+__device__ __forceinline__ void ldg2(const float* q, float* v)
+{
+    asm("ld.global.nc.v2.f32 {%0,%1}, [%2];" : "=f"(v[0]), "=f"(v[1]) : "l"(q));
+}
+
+__device__ __forceinline__ void ldg2u(const uint32_t* q, uint32_t* v)
+{
+    asm("ld.global.nc.v2.b32 {%0,%1}, [%2];" : "=r"(v[0]), "=r"(v[1]) : "l"(q));
+}
+
+__device__ __forceinline__ void ldg1u(const uint32_t* q, uint32_t* v)
+{
+    asm("ld.global.nc.b32 %0, [%1];" : "=r"(v[0]) : "l"(q));
+}
+
 // 16-bit storage formats: value k of a record is half k & 1 of 32-bit word k >> 1.
 template <int DT>
 __device__ __forceinline__ float h_lo(uint32_t w)
@@ -330,46 +353,55 @@ struct Fields {
 };
 
 // The stored fields of the two r-neighbours of one corner pair: record `rec` and
-// the next one (cell layout: six or four 32-byte loads) or the one pair record
-// (five or three); 16-bit values are returned unscaled.
+// the next one (cell layout) or the one pair record; 16-bit values are returned
+// unscaled.
 // Record layout of a kernel: fixed at compile time, or read from the grid.
 constexpr int kLayCell = 0, kLayPair = 1, kLayAny = 2;
 
 template <int DT, int LAY>
 __device__ __forceinline__ void corner_pair(const GridK& g, long long rec, float* lo, float* hi)
 {
+    // Only the 18 stored fields of each cell are loaded, the last piece of a record
+    // with a narrower load (FP32 pair: 4 x 32 + 16 bytes of 160; FP32 cell: 2 x 32 +
+    // 8 of 96 per record; 16-bit pair: 2 x 32 + 8 of 96; 16-bit cell: 32 + 4 of 64).
     const bool pair = LAY == kLayAny ? g.pair != 0 : LAY == kLayPair;
+    static_assert(FTE_NFIELD == 18, "load pattern assumes 18 fields per cell");
     if (DT == FTE_F32) {
         if (pair) {
-            float a[kPairRec];
+            float a[2 * FTE_NFIELD];
             const float* q = g.fields + rec * kPairRec;
 #pragma unroll
-            for (int m = 0; m < kPairRec / 8; ++m) ldg8(q + 8 * m, a + 8 * m);
+            for (int m = 0; m < 4; ++m) ldg8(q + 8 * m, a + 8 * m);
+            ldg4(q + 32, a + 32);
 #pragma unroll
             for (int m = 0; m < FTE_NFIELD; ++m) { lo[m] = a[m]; hi[m] = a[FTE_NFIELD + m]; }
         } else {
-            float a[2 * FTE_REC];
             const float* q = g.fields + rec * FTE_REC;
-#pragma unroll
-            for (int m = 0; m < 2 * FTE_REC / 8; ++m) ldg8(q + 8 * m, a + 8 * m);
-#pragma unroll
-            for (int m = 0; m < FTE_NFIELD; ++m) { lo[m] = a[m]; hi[m] = a[FTE_REC + m]; }
+            ldg8(q, lo);
+            ldg8(q + 8, lo + 8);
+            ldg2(q + 16, lo + 16);
+            ldg8(q + FTE_REC, hi);
+            ldg8(q + FTE_REC + 8, hi + 8);
+            ldg2(q + FTE_REC + 16, hi + 16);
         }
     } else if (pair) {
-        uint32_t u[kPairHRec / 2];
+        uint32_t u[FTE_NFIELD];       // 36 values in 18 words
         const uint32_t* q = g.hfields + rec * (kPairHRec / 2);
-#pragma unroll
-        for (int m = 0; m < kPairHRec / 16; ++m) ldg8u(q + 8 * m, u + 8 * m);
+        ldg8u(q, u);
+        ldg8u(q + 8, u + 8);
+        ldg2u(q + 16, u + 16);
 #pragma unroll
         for (int m = 0; m < FTE_NFIELD; ++m) {
             lo[m] = h_get<DT>(u, m);
             hi[m] = h_get<DT>(u, FTE_NFIELD + m);
         }
     } else {
-        uint32_t u[FTE_HREC];      // two records of FTE_HREC / 2 words
+        uint32_t u[FTE_HREC];         // two records of FTE_HREC / 2 words; 9 words used of each
         const uint32_t* q = g.hfields + rec * (FTE_HREC / 2);
-#pragma unroll
-        for (int m = 0; m < FTE_HREC / 8; ++m) ldg8u(q + 8 * m, u + 8 * m);
+        ldg8u(q, u);
+        ldg1u(q + 8, u + 8);
+        ldg8u(q + FTE_HREC / 2, u + FTE_HREC / 2);
+        ldg1u(q + FTE_HREC / 2 + 8, u + FTE_HREC / 2 + 8);
 #pragma unroll
         for (int m = 0; m < FTE_NFIELD; ++m) {
             lo[m] = h_get<DT>(u, m);
@@ -380,7 +412,7 @@ __device__ __forceinline__ void corner_pair(const GridK& g, long long rec, float
 
 // Trilinear (space) x linear (time) interpolation: for each snapshot and each
 // of the 4 (theta, phi) corners, the two r-neighbours are one contiguous block
-// (FP32: 192 bytes = six 32-byte loads; 16-bit: 128 bytes = four).  For 16-bit
+// (pair layout: one record; 144 of its bytes loaded in FP32, 72 in 16-bit).  For 16-bit
 // storage the sums run over the stored values and the per-field scales `sc`
 // are applied once at the end.
 template <bool KPERP, int DT, int LAY>
