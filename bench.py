@@ -21,9 +21,9 @@ ids, weak scaling) and the tallies are summed over ranks after each step.
 `--impl reference` times the FP64 CPU oracle on the host cores on a bounded
 sample of the same workload.
 
-The device background uses the pair record layout by default (each record
-holds a cell and its upper r-neighbour, converted on the device from the
-uploaded cell records; `--layout cell` measures the plain layout).  The default
+The device background uses the cell record layout by default (`--layout pair`
+measures records that hold a cell and its upper r-neighbour, converted on the
+device from the uploaded cell records).  The default
 line also carries the 16-bit storage forms (`forms`) and the adjoint's cost on a
 slice of the workload (`adjoint`).  Other cases, each one
 JSON line: `--case amr` (the CIR on a 39,520-leaf block-AMR grid, 1e7 protons,
@@ -989,7 +989,7 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true")
-    ap.add_argument("--layout", default="pair", choices=["pair", "cell"],
+    ap.add_argument("--layout", default="cell", choices=["cell", "pair"],
                     help="record layout of the device background (pair: a cell and its r-neighbour per record)")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--adj-slice", type=int, default=4096, help="steps of the adjoint measurement in the default run")
