@@ -38,7 +38,7 @@ bool dense_variant(int kperp, int dtype, int mode, int amr)
 // mode, and for dense_variant() in a 3-blocks-per-SM build
 static const void* advance_fn(int kperp, int dtype, int mode, int nt, int pair, int amr)
 {
-    if (!single_set(mode)) return advance_fn_batched(kperp, dtype, mode, nt);
+    if (!single_set(mode)) return advance_fn_batched(kperp, dtype, mode, nt, pair);
     if (nt != kThreads) return nullptr;
     if (dense_variant(kperp, dtype, mode, amr)) return pair ? dense_fn<kLayPair>(dtype) : dense_fn<kLayCell>(dtype);
     if (mode == kModeSingleGlobal)

@@ -845,7 +845,7 @@ size_t ens_smem(int mode, int n_sets, size_t nb)
     return mode == kModeShared ? 3 * sizeof(float) * shared_bins(n_sets, nb) : 0;
 }
 
-fte_status ens_layout(int device, int kperp, int dtype, int mode, int nt, int n_sets, size_t nb,
+fte_status ens_layout(int device, int kperp, int dtype, int pair, int mode, int nt, int n_sets, size_t nb,
                       long long n_steps, size_t sort_bytes, EnsLayout* L)
 {
     const int sms = device_sms(device);
@@ -854,7 +854,7 @@ fte_status ens_layout(int device, int kperp, int dtype, int mode, int nt, int n_
     int per_sm = 0, cur = 0;
     FTE_CUDA(cudaGetDevice(&cur), "cudaGetDevice");
     if (cur != device) FTE_CUDA(cudaSetDevice(device), "cudaSetDevice");
-    cudaError_t e = advance_occupancy(kperp, dtype, mode, nt, 0, 0, smem, &per_sm);
+    cudaError_t e = advance_occupancy(kperp, dtype, mode, nt, pair, 0, smem, &per_sm);
     if (cur != device) cudaSetDevice(cur);
     if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
     if (per_sm < 1) return fail(FTE_ENOTSUP, "ensemble step kernel does not fit on an SM with %zu bytes of tally", smem);
@@ -918,7 +918,7 @@ fte_status ens_run(fte_particles* P, const fte_background* bg, const fte_params*
     const GridK gk = make_gridk(bg);
     const int sorting = prm->sort_every > 0;
     EnsLayout L;
-    fte_status s = ens_layout(device, kperp, bg->grid.dtype, cfg.mode, cfg.nt, n_sets, nb, nsteps,
+    fte_status s = ens_layout(device, kperp, bg->grid.dtype, gk.pair, cfg.mode, cfg.nt, n_sets, nb, nsteps,
                               sorting ? sort_scratch_bytes(gk, P->count) : 0, &L);
     if (s != FTE_OK) return s;
     if (ws_bytes < L.total) return fail(FTE_ENOMEM, "workspace has %zu bytes, needs %zu", ws_bytes, L.total);
@@ -1070,10 +1070,13 @@ size_t fte_workspace_bytes_batched(int device, const fte_grid* g, const fte_tall
                 for (int nt = 128; nt <= 256; nt *= 2) {
                     if (mode == kModeShared && !shared_fits(n_sets, nb)) continue;
                     EnsLayout L;
-                    const fte_status s = ens_layout(device, kperp, dtype, mode, nt, n_sets, nb, n_steps, sort_bytes, &L);
-                    if (s == FTE_ENOTSUP) continue;
-                    if (s != FTE_OK) return 0;
-                    if (L.total > best) best = L.total;
+                    for (int pair = 0; pair < 2; ++pair) {
+                        const fte_status s = ens_layout(device, kperp, dtype, pair, mode, nt, n_sets, nb, n_steps,
+                                                        sort_bytes, &L);
+                        if (s == FTE_ENOTSUP) continue;
+                        if (s != FTE_OK) return 0;
+                        if (L.total > best) best = L.total;
+                    }
                 }
     return best;
 }

@@ -140,7 +140,7 @@ cudaError_t advance_occupancy(int kperp, int dtype, int mode, int nt, int pair, 
 // FP32 grids keep the unconstrained build, which spills under the tighter limit)
 bool dense_variant(int kperp, int dtype, int mode, int amr);
 // the ensemble variants live in their own translation unit (fte_batched.cu)
-const void* advance_fn_batched(int kperp, int dtype, int mode, int nt);
+const void* advance_fn_batched(int kperp, int dtype, int mode, int nt, int pair);
 cudaError_t launch_advance_batched(const AdvanceArgs& a, const BatchArgs& b, int kperp, int mode, int nt,
                                    int blocks, size_t smem, cudaStream_t s);
 cudaError_t launch_reduce(const float* part, int nblk, int nbins, double* S, double* S2,
