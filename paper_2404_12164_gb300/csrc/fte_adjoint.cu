@@ -155,7 +155,7 @@ __device__ __forceinline__ void dmumu_vjp(const ParamsK& P, float I, float rq, f
 // Vector-Jacobian product of one step (lambda_perp = 0): lam holds the adjoint
 // of the state after step n on entry and of the state before it on return.
 // ---------------------------------------------------------------------------
-template <int DT>
+template <int DT, int LAY>
 __device__ void step_vjp(const AdvanceArgs& a, float I, float rq, float rh, long long n, uint32_t pid, float x,
                          float y, float z, float mu, float p, const float* sc, float* lam, float* gth)
 {
@@ -176,7 +176,7 @@ __device__ void step_vjp(const AdvanceArgs& a, float I, float rq, float rh, long
     Loc L;
     locate(g, r, th, ph, L);
     Fields<false> F;
-    gather<false, DT, kLayAny>(g, e, L, sc, F);
+    gather<false, DT, LAY>(g, e, L, sc, F);
     const float* B = F.f;
     const float* V = F.f + 3;
     const float* G = F.f + 6;
@@ -316,7 +316,7 @@ __device__ void step_vjp(const AdvanceArgs& a, float I, float rq, float rh, long
             const float wp_ = cp ? L.fp : 1.f - L.fp;
             const long long rec = (long long)snap * g.snap_recs + L.base[c];
             float lo[FTE_NFIELD], hi[FTE_NFIELD];
-            corner_pair<DT, kLayAny>(g, rec, lo, hi);
+            corner_pair<DT, LAY>(g, rec, lo, hi);
             float dlo = 0.f, dhi = 0.f, vlo = 0.f, vhi = 0.f;
 #pragma unroll
             for (int m = 0; m < FTE_NFIELD; ++m) { dlo += Fb[m] * lo[m]; dhi += Fb[m] * hi[m]; }
@@ -350,7 +350,7 @@ __device__ void step_vjp(const AdvanceArgs& a, float I, float rq, float rh, long
 // in spatial order from a.order when reordering is on) stores its checkpoint,
 // runs the segment's steps and adds its observable to J_part.
 // ---------------------------------------------------------------------------
-template <int DT>
+template <int DT, int LAY>
 __global__ void __launch_bounds__(256) adj_forward_kernel(const AdvanceArgs a, const AdjK k)
 {
     __shared__ float sc[FTE_NFIELD];
@@ -378,7 +378,7 @@ __global__ void __launch_bounds__(256) adj_forward_kernel(const AdvanceArgs a, c
         for (; s < a.n_end; ++s) {
             const float r = sqrtf(x * x + y * y + z * z);
             J += (double)(w * a.prm.dt * smooth_k(k, r, p, k.t0 + (double)s * k.dt, nullptr, nullptr));
-            st = step<false, DT, kModeSingle, kLayAny>(a, a.prm, I, 0, s, pid, x, y, z, mu, p, w, nullptr, nullptr,
+            st = step<false, DT, kModeSingle, LAY>(a, a.prm, I, 0, s, pid, x, y, z, mu, p, w, nullptr, nullptr,
                                               nullptr, sc, noor);
             if (st != FTE_ALIVE) { ++s; break; }
         }
@@ -407,7 +407,7 @@ __global__ void __launch_bounds__(256) adj_forward_kernel(const AdvanceArgs a, c
 // (scratch[(kk * 5 + c) * threads + tid]) and walks it backwards.  The launch
 // of the first segment adds the injection-index term and reduces the gradients.
 // ---------------------------------------------------------------------------
-template <int DT>
+template <int DT, int LAY>
 __global__ void __launch_bounds__(256, 2) adj_reverse_kernel(const AdvanceArgs a, const AdjK k)
 {
     __shared__ float sc[FTE_NFIELD];
@@ -447,13 +447,13 @@ __global__ void __launch_bounds__(256, 2) adj_reverse_kernel(const AdvanceArgs a
             float* sp = k.scratch + ((size_t)(s - n0) * 5) * nthr + tid;
             sp[0] = x; sp[nthr] = y; sp[2 * nthr] = z; sp[3 * nthr] = mu; sp[4 * nthr] = p;
             if (s + 1 < n1)
-                step<false, DT, kModeSingle, kLayAny>(a, a.prm, I, 0, s, pid, x, y, z, mu, p, w, nullptr, nullptr, nullptr,
+                step<false, DT, kModeSingle, LAY>(a, a.prm, I, 0, s, pid, x, y, z, mu, p, w, nullptr, nullptr, nullptr,
                                              sc, noor);
         }
         for (long long s = n1 - 1; s >= n0; --s) {
             const float* sp = k.scratch + ((size_t)(s - n0) * 5) * nthr + tid;
             const float sx = sp[0], sy = sp[nthr], sz = sp[2 * nthr], smu = sp[3 * nthr], spp = sp[4 * nthr];
-            step_vjp<DT>(a, I, rq, rh, s, pid, sx, sy, sz, smu, spp, sc, lam, gth);
+            step_vjp<DT, LAY>(a, I, rq, rh, s, pid, sx, sy, sz, smu, spp, sc, lam, gth);
             // the observable's own term at the start-of-step state
             const float r = sqrtf(sx * sx + sy * sy + sz * sz);
             float dKdr, dKdp;
@@ -497,36 +497,42 @@ __global__ void __launch_bounds__(256, 2) adj_reverse_kernel(const AdvanceArgs a
     }
 }
 
-static const void* fwd_fn(int dtype)
+template <int LAY>
+static const void* fwd_fn_lay(int dtype)
 {
-    if (dtype == FTE_BF16) return (const void*)adj_forward_kernel<FTE_BF16>;
-    if (dtype == FTE_F16) return (const void*)adj_forward_kernel<FTE_F16>;
-    return (const void*)adj_forward_kernel<FTE_F32>;
+    if (dtype == FTE_BF16) return (const void*)adj_forward_kernel<FTE_BF16, LAY>;
+    if (dtype == FTE_F16) return (const void*)adj_forward_kernel<FTE_F16, LAY>;
+    return (const void*)adj_forward_kernel<FTE_F32, LAY>;
 }
 
-static const void* rev_fn(int dtype)
+template <int LAY>
+static const void* rev_fn_lay(int dtype)
 {
-    if (dtype == FTE_BF16) return (const void*)adj_reverse_kernel<FTE_BF16>;
-    if (dtype == FTE_F16) return (const void*)adj_reverse_kernel<FTE_F16>;
-    return (const void*)adj_reverse_kernel<FTE_F32>;
+    if (dtype == FTE_BF16) return (const void*)adj_reverse_kernel<FTE_BF16, LAY>;
+    if (dtype == FTE_F16) return (const void*)adj_reverse_kernel<FTE_F16, LAY>;
+    return (const void*)adj_reverse_kernel<FTE_F32, LAY>;
 }
 
-cudaError_t adjoint_blocks(int dtype, int reverse, int* blocks_per_sm)
+// record layout fixed at compile time, as for the step kernels
+static const void* fwd_fn(int dtype, int pair) { return pair ? fwd_fn_lay<kLayPair>(dtype) : fwd_fn_lay<kLayCell>(dtype); }
+static const void* rev_fn(int dtype, int pair) { return pair ? rev_fn_lay<kLayPair>(dtype) : rev_fn_lay<kLayCell>(dtype); }
+
+cudaError_t adjoint_blocks(int dtype, int pair, int reverse, int* blocks_per_sm)
 {
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, reverse ? rev_fn(dtype) : fwd_fn(dtype),
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, reverse ? rev_fn(dtype, pair) : fwd_fn(dtype, pair),
                                                          256, 0);
 }
 
 cudaError_t launch_adjoint_forward(const AdvanceArgs& a, const AdjK& k, int blocks, cudaStream_t s)
 {
     void* args[] = {(void*)&a, (void*)&k};
-    return cudaLaunchKernel(fwd_fn(a.g.dtype), dim3(blocks), dim3(256), args, 0, s);
+    return cudaLaunchKernel(fwd_fn(a.g.dtype, a.g.pair), dim3(blocks), dim3(256), args, 0, s);
 }
 
 cudaError_t launch_adjoint_reverse(const AdvanceArgs& a, const AdjK& k, int blocks, cudaStream_t s)
 {
     void* args[] = {(void*)&a, (void*)&k};
-    return cudaLaunchKernel(rev_fn(a.g.dtype), dim3(blocks), dim3(256), args, 0, s);
+    return cudaLaunchKernel(rev_fn(a.g.dtype, a.g.pair), dim3(blocks), dim3(256), args, 0, s);
 }
 
 cudaError_t launch_norm_derivs(int model, double q, double H, double eps, double* out, double* part,

@@ -1265,8 +1265,9 @@ fte_status adj_layout(int device, const fte_grid* g, unsigned long long n, long 
     int pf = 0, pr = 0, cur = 0;
     FTE_CUDA(cudaGetDevice(&cur), "cudaGetDevice");
     if (cur != device) FTE_CUDA(cudaSetDevice(device), "cudaSetDevice");
-    cudaError_t e = adjoint_blocks(g->dtype, 0, &pf);
-    if (e == cudaSuccess) e = adjoint_blocks(g->dtype, 1, &pr);
+    const int pair = g->layout == FTE_LAYOUT_PAIR;
+    cudaError_t e = adjoint_blocks(g->dtype, pair, 0, &pf);
+    if (e == cudaSuccess) e = adjoint_blocks(g->dtype, pair, 1, &pr);
     if (cur != device) cudaSetDevice(cur);
     if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
     if (pf < 1 || pr < 1) return fail(FTE_ENOTSUP, "adjoint kernels do not fit on an SM");

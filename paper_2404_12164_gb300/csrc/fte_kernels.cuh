@@ -159,7 +159,7 @@ cudaError_t launch_convolve(const double* S, const ObsOut& ob, int kind, const d
                             cudaStream_t s);
 cudaError_t launch_inject(const InjectArgs& a, cudaStream_t s);
 // adjoint (fte_adjoint.cu)
-cudaError_t adjoint_blocks(int dtype, int reverse, int* blocks_per_sm);
+cudaError_t adjoint_blocks(int dtype, int pair, int reverse, int* blocks_per_sm);
 cudaError_t launch_adjoint_forward(const AdvanceArgs& a, const AdjK& k, int blocks, cudaStream_t s);
 cudaError_t launch_adjoint_reverse(const AdvanceArgs& a, const AdjK& k, int blocks, cudaStream_t s);
 cudaError_t launch_norm_derivs(int model, double q, double H, double eps, double* out, double* part,
