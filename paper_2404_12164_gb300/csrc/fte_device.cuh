@@ -432,6 +432,9 @@ __device__ __forceinline__ void gather(const GridK& g, const StepEntry& e, const
         const int snap = s ? e.s1 : e.s0;
         const float ws = e.two ? (s ? e.wt : 1.f - e.wt) : 1.f;
         const float sgn = s ? 1.f : -1.f;
+        // V of this snapshot, spatially interpolated: it enters F (weighted by ws) and
+        // the snapshot difference for dV/dt, from one set of accumulators
+        float vs[3] = {0.f, 0.f, 0.f};
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
             const int ct = c & 1, cp = c >> 1;
@@ -444,13 +447,12 @@ __device__ __forceinline__ void gather(const GridK& g, const StepEntry& e, const
             const float c0 = (1.f - L.fr) * wjk, c1 = L.fr * wjk;
             const float w0 = ws * c0, w1 = ws * c1;
 #pragma unroll
-            for (int m = 0; m < FTE_NFIELD; ++m) F.f[m] = fmaf(w0, lo[m], fmaf(w1, hi[m], F.f[m]));
-            if (e.two) {
-                const float d0 = sgn * c0, d1 = sgn * c1;
-#pragma unroll
-                for (int m = 0; m < 3; ++m)
-                    F.dv[m] = fmaf(d0, lo[3 + m], fmaf(d1, hi[3 + m], F.dv[m]));
+            for (int m = 0; m < FTE_NFIELD; ++m) {
+                if (m >= 3 && m < 6) continue;
+                F.f[m] = fmaf(w0, lo[m], fmaf(w1, hi[m], F.f[m]));
             }
+#pragma unroll
+            for (int m = 0; m < 3; ++m) vs[m] = fmaf(c0, lo[3 + m], fmaf(c1, hi[3 + m], vs[m]));
             if (KPERP) {
                 const float er = L.dfr * wjk;                          // d w / d r
                 const float et = (ct ? 1.f : -1.f) * L.dft * wp_;      // d w / d theta (x w_r)
@@ -463,6 +465,11 @@ __device__ __forceinline__ void gather(const GridK& g, const StepEntry& e, const
                     F.dBa[3 * m + 2] += ws * ep * mix;
                 }
             }
+        }
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+            F.f[3 + m] = fmaf(ws, vs[m], F.f[3 + m]);
+            if (e.two) F.dv[m] = fmaf(sgn, vs[m], F.dv[m]);
         }
     }
     if (DT != FTE_F32) {
