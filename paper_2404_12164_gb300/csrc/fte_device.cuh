@@ -130,8 +130,12 @@ __device__ __forceinline__ void dmumu(const ParamsK& P, float I, float mu, float
     const float omm = 1.f - mu * mu;
     if (P.dmumu == 0) {
         const float nu = 3.f * v * I / (2.f * lam);
-        const float g = powf(am, P.q - 1.f) + P.H;
-        const float dg = (P.q - 1.f) * powf(fmaxf(am, P.mu_floor), P.q - 2.f) * sg;
+        // |mu|^(q-1) and max(|mu|, mu_floor)^(q-2) from one logarithm: above the floor
+        // the first is the second times |mu| (two exp2/log2 instead of two powf)
+        const float pq2 = exp2f((P.q - 2.f) * log2f(fmaxf(am, P.mu_floor)));
+        const float pq1 = am >= P.mu_floor ? pq2 * am : exp2f((P.q - 1.f) * log2f(am));
+        const float g = pq1 + P.H;
+        const float dg = (P.q - 1.f) * pq2 * sg;
         D = 0.5f * nu * omm * g;
         dD = 0.5f * nu * (-2.f * mu * g + omm * dg);
     } else if (P.dmumu == 1) {
