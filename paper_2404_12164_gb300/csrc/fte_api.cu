@@ -529,6 +529,7 @@ fte_status fte_advance(fte_particles* P, const fte_background* bg, const fte_par
     a.prm.dvdt_term = prm->dvdt_term;
     a.prm.use_rig = (prm->p_ref > 0.0 && prm->alpha != 0.0) ? 1 : 0;
     a.prm.lambda_par = (float)prm->lambda_par; a.prm.p_ref = (float)prm->p_ref; a.prm.alpha = (float)prm->alpha;
+    a.prm.inv_lambda_par = (float)(1.0 / prm->lambda_par);
     a.prm.q = (float)prm->q; a.prm.H = (float)prm->H; a.prm.eps = (float)prm->eps;
     a.prm.mu_floor = (float)prm->mu_floor; a.prm.lambda_perp = (float)prm->lambda_perp;
     a.prm.dt = (float)prm->dt; a.prm.seed = prm->seed; a.prm.set_id = prm->set_id;
@@ -780,6 +781,7 @@ extern "C" fte_status fte_advance_noalloc(fte_particles* P, const fte_background
     a.prm.dvdt_term = prm->dvdt_term;
     a.prm.use_rig = (prm->p_ref > 0.0 && prm->alpha != 0.0) ? 1 : 0;
     a.prm.lambda_par = (float)prm->lambda_par; a.prm.p_ref = (float)prm->p_ref; a.prm.alpha = (float)prm->alpha;
+    a.prm.inv_lambda_par = (float)(1.0 / prm->lambda_par);
     a.prm.q = (float)prm->q; a.prm.H = (float)prm->H; a.prm.eps = (float)prm->eps;
     a.prm.mu_floor = (float)prm->mu_floor; a.prm.lambda_perp = (float)prm->lambda_perp;
     a.prm.dt = (float)prm->dt; a.prm.seed = prm->seed; a.prm.set_id = prm->set_id;
@@ -1348,6 +1350,7 @@ fte_status adj_args(const fte_particles* P, const fte_background* bg, const fte_
     a->prm.dmumu = prm->dmumu; a->prm.p_update = prm->p_update; a->prm.kappa_drift = prm->kappa_drift;
     a->prm.dvdt_term = prm->dvdt_term;
     a->prm.lambda_par = (float)prm->lambda_par; a->prm.p_ref = (float)prm->p_ref; a->prm.alpha = (float)prm->alpha;
+    a->prm.inv_lambda_par = (float)(1.0 / prm->lambda_par);
     a->prm.q = (float)prm->q; a->prm.H = (float)prm->H; a->prm.eps = (float)prm->eps;
     a->prm.mu_floor = (float)prm->mu_floor; a->prm.lambda_perp = 0.f;
     a->prm.dt = (float)prm->dt; a->prm.seed = prm->seed; a->prm.set_id = prm->set_id;

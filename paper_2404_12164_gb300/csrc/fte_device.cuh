@@ -58,6 +58,7 @@ struct ParamsK {
     int use_rig;
     float lambda_par, p_ref, alpha, q, H, eps, mu_floor, lambda_perp, dt;
     uint32_t seed, set_id;
+    float inv_lambda_par;      // 1 / lambda_par, so that a step divides by nothing constant
 };
 
 struct ObsK {
@@ -124,12 +125,12 @@ __device__ __forceinline__ float energy_of(float p)
 __device__ __forceinline__ void dmumu(const ParamsK& P, float I, float mu, float v, float p,
                                       float& D, float& dD)
 {
-    const float lam = P.use_rig ? P.lambda_par * powf(p / P.p_ref, P.alpha) : P.lambda_par;
+    const float ilam = P.use_rig ? 1.f / (P.lambda_par * powf(p / P.p_ref, P.alpha)) : P.inv_lambda_par;
     const float am = fabsf(mu);
     const float sg = (mu > 0.f) ? 1.f : ((mu < 0.f) ? -1.f : 0.f);
     const float omm = 1.f - mu * mu;
     if (P.dmumu == 0) {
-        const float nu = 3.f * v * I / (2.f * lam);
+        const float nu = 1.5f * v * I * ilam;
         // |mu|^(q-1) and max(|mu|, mu_floor)^(q-2) from one logarithm: above the floor
         // the first is the second times |mu| (two exp2/log2 instead of two powf)
         const float pq2 = exp2f((P.q - 2.f) * log2f(fmaxf(am, P.mu_floor)));
@@ -139,13 +140,13 @@ __device__ __forceinline__ void dmumu(const ParamsK& P, float I, float mu, float
         D = 0.5f * nu * omm * g;
         dD = 0.5f * nu * (-2.f * mu * g + omm * dg);
     } else if (P.dmumu == 1) {
-        const float D0 = 3.f * v * I / (4.f * lam);
+        const float D0 = 0.75f * v * I * ilam;
         const float h = am / (1.f + am) + P.eps;
         const float dh = sg / ((1.f + am) * (1.f + am));
         D = D0 * h * omm;
         dD = D0 * (dh * omm - 2.f * mu * h);
     } else {
-        const float Dc = v / (2.f * lam);
+        const float Dc = 0.5f * v * ilam;
         D = Dc * omm;
         dD = -2.f * mu * Dc;
     }

@@ -108,6 +108,7 @@ __device__ __forceinline__ int step(const AdvanceArgs& a, const ParamsK& prm, fl
     }
 
     const float v = speed_of(p);
+    const float inv_v = 1.f / v;
     float D, dD;
     dmumu(prm, I, mu, v, p, D, dD);
 
@@ -120,7 +121,7 @@ __device__ __forceinline__ int step(const AdvanceArgs& a, const ParamsK& prm, fl
 
     // Eq. 3 + Ito pitch-angle diffusion, reflecting at mu = +-1
     const float omm = 1.f - mu * mu;
-    const float mudot = 0.5f * omm * (v * divb + mu * divv - 3.f * mu * bbgv - (2.f / v) * bdvdt);
+    const float mudot = 0.5f * omm * (v * divb + mu * divv - 3.f * mu * bbgv - 2.f * inv_v * bdvdt);
     float mun = mu + (mudot + dD) * dt + sqrtf(2.f * D * dt) * (amp0 * c1);
     if (mun > 1.f) mun = 2.f - mun;
     if (mun < -1.f) mun = -2.f - mun;
@@ -166,12 +167,11 @@ __device__ __forceinline__ int step(const AdvanceArgs& a, const ParamsK& prm, fl
     const float xn = x + ux * dt + nx, yn = y + uy * dt + ny, zn = z + uz * dt + nz;
 
     // Eq. 4
-    const float pdot = 0.5f * (1.f - 3.f * mu * mu) * bbgv - 0.5f * omm * divv - (mu / v) * bdvdt;
+    const float pdot = 0.5f * (1.f - 3.f * mu * mu) * bbgv - 0.5f * omm * divv - mu * inv_v * bdvdt;
     const float pn = (prm.p_update == 0) ? p * expf(pdot * dt) : p * (1.f + pdot * dt);
 
     // occupancy tally of the start-of-step state
     if (a.n_obs) {
-        const float E = energy_of(p);
         for (int o = 0; o < a.n_obs; ++o) {
             const ObsK& ob = a.obs[o];
             bool in;
@@ -190,7 +190,7 @@ __device__ __forceinline__ int step(const AdvanceArgs& a, const ParamsK& prm, fl
             }
             int bin = -1;
             if (in) {
-                const float le = logf(E / ob.e_lo) * ob.ne_over_lnratio;
+                const float le = logf(energy_of(p) / ob.e_lo) * ob.ne_over_lnratio;
                 int it = __ldg(&ep->it[o]);     // time bin, -1 outside [t_lo, t_hi)
                 if (ob.kind == 3 && it >= 0) it = min((int)(ph * ob.phi_scale), ob.nt - 1);
                 if (le >= 0.f && le < (float)ob.ne && it >= 0)
@@ -289,6 +289,7 @@ __global__ void __launch_bounds__(NT, single_set(MODE) ? MINB : 512 / NT) advanc
             const int s = set_of(s_end, b.n_sets, i);
             ParamsK prm = a.prm;
             prm.lambda_par = s_set[s].lambda_par;
+            prm.inv_lambda_par = 1.f / s_set[s].lambda_par;
             prm.q = s_set[s].q;
             prm.H = s_set[s].H;
             prm.eps = s_set[s].eps;
