@@ -97,35 +97,41 @@ __device__ __forceinline__ float smooth_k(const AdjK& k, float r, float p, doubl
 // respect to mu, v and the parameters; gth gains Dbar dD/dtheta + dDbar ddD/dtheta
 // for theta = (lambda_par, q, H, eps).
 // ---------------------------------------------------------------------------
+constexpr float kLn2f = 0.693147180559945309f;
+
 __device__ __forceinline__ void dmumu_vjp(const ParamsK& P, float I, float rq, float rh, float mu, float v,
                                           float Db, float dDb, float& mub, float& vb, float* gth)
 {
-    const float lam = P.lambda_par;
     const float am = fabsf(mu);
     const float sg = (mu > 0.f) ? 1.f : ((mu < 0.f) ? -1.f : 0.f);
     const float omm = 1.f - mu * mu;
     float D, dD, D_mu, dD_mu, D_q = 0.f, dD_q = 0.f, D_h = 0.f, dD_h = 0.f, D_e = 0.f, dD_e = 0.f;
     if (P.dmumu == 0) {
-        const float nu = 3.f * v * I / (2.f * lam);
-        const float pq1 = powf(am, P.q - 1.f);
+        const float nu = 1.5f * v * I * P.inv_lambda_par;
+        // the powers of |mu| from one base-2 logarithm: |mu|^(q-1), then divided by |mu|
+        // (la = -inf and pq1 = 0 at mu = 0, where the terms that divide are not used)
+        const float la = log2f(am);
+        const float pq1 = exp2f((P.q - 1.f) * la);
+        const float ia = 1.f / am;
         const float g = pq1 + P.H;
         const float amf = fmaxf(am, P.mu_floor);
-        const float pf2 = powf(amf, P.q - 2.f);
+        const float laf = am >= P.mu_floor ? la : log2f(amf);
+        const float pf2 = am >= P.mu_floor ? pq1 * ia : exp2f((P.q - 2.f) * laf);
         const float gp = (P.q - 1.f) * pf2 * sg;
         D = 0.5f * nu * omm * g;
         dD = 0.5f * nu * (-2.f * mu * g + omm * gp);
-        const float gmu = am > 0.f ? (P.q - 1.f) * powf(am, P.q - 2.f) * sg : 0.f;
-        const float gpmu = am > P.mu_floor ? (P.q - 1.f) * (P.q - 2.f) * powf(am, P.q - 3.f) : 0.f;
+        const float gmu = am > 0.f ? (P.q - 1.f) * (pq1 * ia) * sg : 0.f;
+        const float gpmu = am > P.mu_floor ? (P.q - 1.f) * (P.q - 2.f) * (pq1 * ia * ia) : 0.f;
         D_mu = 0.5f * nu * (-2.f * mu * g + omm * gmu);
         dD_mu = 0.5f * nu * (-2.f * g - 2.f * mu * gmu - 2.f * mu * gp + omm * gpmu);
-        const float gq = am > 0.f ? pq1 * logf(am) : 0.f;
-        const float gpq = (pf2 + (P.q - 1.f) * pf2 * logf(amf)) * sg;
+        const float gq = am > 0.f ? pq1 * (la * kLn2f) : 0.f;
+        const float gpq = (pf2 + (P.q - 1.f) * pf2 * (laf * kLn2f)) * sg;
         D_q = 0.5f * nu * omm * gq + D * rq;
         dD_q = 0.5f * nu * (-2.f * mu * gq + omm * gpq) + dD * rq;
         D_h = 0.5f * nu * omm + D * rh;
         dD_h = 0.5f * nu * (-2.f * mu) + dD * rh;
     } else if (P.dmumu == 1) {
-        const float D0 = 3.f * v * I / (4.f * lam);
+        const float D0 = 0.75f * v * I * P.inv_lambda_par;
         const float opa = 1.f + am;
         const float h = am / opa + P.eps;
         const float dh = sg / (opa * opa);
@@ -137,7 +143,7 @@ __device__ __forceinline__ void dmumu_vjp(const ParamsK& P, float I, float rq, f
         D_e = D0 * omm + D * rh;
         dD_e = D0 * (-2.f * mu) + dD * rh;
     } else {
-        const float Dc = v / (2.f * lam);
+        const float Dc = 0.5f * v * P.inv_lambda_par;
         D = Dc * omm;
         dD = -2.f * mu * Dc;
         D_mu = dD;
@@ -145,7 +151,7 @@ __device__ __forceinline__ void dmumu_vjp(const ParamsK& P, float I, float rq, f
     }
     mub += Db * D_mu + dDb * dD_mu;
     vb += (Db * D + dDb * dD) / v;
-    gth[0] -= (Db * D + dDb * dD) / lam;
+    gth[0] -= (Db * D + dDb * dD) * P.inv_lambda_par;
     gth[1] += Db * D_q + dDb * dD_q;
     gth[2] += Db * D_h + dDb * dD_h;
     gth[3] += Db * D_e + dDb * dD_e;
