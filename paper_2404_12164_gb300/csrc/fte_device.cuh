@@ -360,8 +360,8 @@ struct Fields {
 // The stored fields of the two r-neighbours of one corner pair: record `rec` and
 // the next one (cell layout) or the one pair record; 16-bit values are returned
 // unscaled.
-// Record layout of a kernel: fixed at compile time, or read from the grid.
-constexpr int kLayCell = 0, kLayPair = 1, kLayAny = 2;
+// Record layout of a kernel, fixed at compile time (each kernel is built for both).
+constexpr int kLayCell = 0, kLayPair = 1;
 
 template <int DT, int LAY>
 __device__ __forceinline__ void corner_pair(const GridK& g, long long rec, float* lo, float* hi)
@@ -369,7 +369,7 @@ __device__ __forceinline__ void corner_pair(const GridK& g, long long rec, float
     // Only the 18 stored fields of each cell are loaded, the last piece of a record
     // with a narrower load (FP32 pair: 4 x 32 + 16 bytes of 160; FP32 cell: 2 x 32 +
     // 8 of 96 per record; 16-bit pair: 2 x 32 + 8 of 96; 16-bit cell: 32 + 4 of 64).
-    const bool pair = LAY == kLayAny ? g.pair != 0 : LAY == kLayPair;
+    constexpr bool pair = LAY == kLayPair;
     static_assert(FTE_NFIELD == 18, "load pattern assumes 18 fields per cell");
     if (DT == FTE_F32) {
         if (pair) {

@@ -239,8 +239,7 @@ __device__ __forceinline__ int set_of(const unsigned long long* end, int n_sets,
 // L1 keeps its whole capacity for the gather); kModeShared: an ensemble
 // (per-set parameters and tallies, the tallies of all sets in shared memory);
 // kModeGlobal: an ensemble with warp-merged FP64 atomics to the tally.
-// LAY: record layout, compile-time for the single-set kernels, read from the
-// grid (kLayAny) by the ensemble kernels.  MINB: blocks per SM the single-set
+// LAY: record layout (cell or pair), compile-time.  MINB: blocks per SM the single-set
 // kernel is compiled for (0: the register count ptxas chooses; 3: at most 85
 // registers, 24 warps per SM, for the longer dependent-load chains of block AMR).
 template <bool KPERP, int DT, int MODE, int NT, int LAY, int MINB = 0>
