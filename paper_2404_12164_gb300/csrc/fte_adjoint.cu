@@ -209,6 +209,7 @@ __device__ void step_vjp(const AdvanceArgs& a, float I, float rq, float rh, long
         bdvdt = b[0] * acc[0] + b[1] * acc[1] + b[2] * acc[2];
     }
     const float v = speed_of(p);
+    const float iv = 1.f / v;      // the step and its VJP divide by v only through iv
     float D, dD;
     dmumu(P, I, mu, v, p, D, dD);
     const uint4 rb = philox4x32_10(make_uint4((uint32_t)n, pid, 0u, 0u), make_uint2(P.seed, P.set_id));
@@ -218,14 +219,14 @@ __device__ void step_vjp(const AdvanceArgs& a, float I, float rq, float rh, long
     const float zmu = amp0 * c1;
     const float dt = P.dt;
     const float omm = 1.f - mu * mu;
-    const float Q = v * divb + mu * divv - 3.f * mu * bbgv - (2.f / v) * bdvdt;
+    const float Q = v * divb + mu * divv - 3.f * mu * bbgv - 2.f * iv * bdvdt;
     const float mudot = 0.5f * omm * Q;
     const float mu1 = mu + (mudot + dD) * dt + sqrtf(2.f * D * dt) * zmu;
     float fm = 1.f, m2 = mu1;
     if (m2 > 1.f) { m2 = 2.f - m2; fm = -fm; }
     if (m2 < -1.f) { m2 = -2.f - m2; fm = -fm; }
     if (m2 > 1.f || m2 < -1.f) fm = 0.f;
-    const float pdot = 0.5f * (1.f - 3.f * mu * mu) * bbgv - 0.5f * omm * divv - (mu / v) * bdvdt;
+    const float pdot = 0.5f * (1.f - 3.f * mu * mu) * bbgv - 0.5f * omm * divv - mu * iv * bdvdt;
     const float ep_ = (P.p_update == 0) ? expf(pdot * dt) : 1.f + pdot * dt;
 
     // ---- reverse ----
@@ -247,24 +248,24 @@ __device__ void step_vjp(const AdvanceArgs& a, float I, float rq, float rh, long
     float bb[3] = {mu * v * ub[0], mu * v * ub[1], mu * v * ub[2]};
     // pdot
     float bbgvb = 0.5f * (1.f - 3.f * mu * mu) * pdotb;
-    mub += pdotb * (-3.f * mu * bbgv + mu * divv - bdvdt / v);
+    mub += pdotb * (-3.f * mu * bbgv + mu * divv - bdvdt * iv);
     float divvb = -0.5f * omm * pdotb;
-    float bdvdtb = -(mu / v) * pdotb;
-    vb += (mu / (v * v)) * bdvdt * pdotb;
+    float bdvdtb = -(mu * iv) * pdotb;
+    vb += (mu * iv * iv) * bdvdt * pdotb;
     // mudot = omm Q / 2
     mub += mudotb * (-mu * Q + 0.5f * omm * (divv - 3.f * bbgv));
     const float Qb = 0.5f * omm * mudotb;
-    vb += Qb * (divb + 2.f * bdvdt / (v * v));
+    vb += Qb * (divb + 2.f * bdvdt * (iv * iv));
     const float divbb = Qb * v;
     divvb += Qb * mu;
     bbgvb += -3.f * mu * Qb;
-    bdvdtb += -(2.f / v) * Qb;
+    bdvdtb += -(2.f * iv) * Qb;
     // D, dD/dmu
     dmumu_vjp(P, I, rq, rh, mu, v, Db, dDb, mub, vb, gth);
     // v(p)
     {
-        const float op = fmaf(p, p, 1.f);
-        pb += vb * kCau * rsqrtf(op) / op;
+        const float ro = rsqrtf(fmaf(p, p, 1.f));
+        pb += vb * kCau * (ro * ro * ro);
     }
     // background quantities -> fields
     float Fb[FTE_NFIELD], dvb[3] = {0.f, 0.f, 0.f};
