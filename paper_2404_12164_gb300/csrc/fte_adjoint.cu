@@ -74,14 +74,14 @@ __global__ void normd_final_kernel(const double* part, double* out)
 }
 
 // ---------------------------------------------------------------------------
-// Smooth observable K(r, E, t) and its gradient with respect to (x, y, z, p).
+// Smooth observable K(r, E, t) and its gradient with respect to (x, y, z, p);
+// c = (t - t_c) / sigma_t is passed in (see time_arg).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float smooth_k(const AdjK& k, float r, float p, double t, float* dKdr, float* dKdp)
+__device__ __forceinline__ float smooth_k(const AdjK& k, float r, float p, float c, float* dKdr, float* dKdp)
 {
     const float E = energy_of(p);
     const float a = (r - k.r_o) * k.inv_sr;
     const float b = logf(E * k.inv_ec) * k.inv_se;
-    const float c = (float)((t - k.t_c) * k.inv_st);
     const float K = expf(-0.5f * (a * a + b * b + c * c));
     if (dKdr) {
         *dKdr = -K * a * k.inv_sr;
@@ -90,6 +90,14 @@ __device__ __forceinline__ float smooth_k(const AdjK& k, float r, float p, doubl
         *dKdp = -K * b * k.inv_se * dEdp / E;
     }
     return K;
+}
+
+// The observable's time argument at step s in FP32: c0 + s * cstep with c0 =
+// (t0 - t_c) / sigma_t (FP64, rounded once); it depends on s alone, not on how
+// the run is cut into launches.
+__device__ __forceinline__ float time_arg(const AdjK& k, long long s)
+{
+    return fmaf((float)s, k.cstep, k.c0);
 }
 
 // ---------------------------------------------------------------------------
@@ -384,7 +392,7 @@ __global__ void __launch_bounds__(256) adj_forward_kernel(const AdvanceArgs a, c
         long long s = a.n_start;
         for (; s < a.n_end; ++s) {
             const float r = sqrtf(x * x + y * y + z * z);
-            J += (double)(w * a.prm.dt * smooth_k(k, r, p, k.t0 + (double)s * k.dt, nullptr, nullptr));
+            J += (double)(w * a.prm.dt * smooth_k(k, r, p, time_arg(k, s), nullptr, nullptr));
             st = step<false, DT, kModeSingle, LAY>(a, a.prm, I, 0, s, pid, x, y, z, mu, p, w, nullptr, nullptr,
                                               nullptr, sc, noor);
             if (st != FTE_ALIVE) { ++s; break; }
@@ -464,7 +472,7 @@ __global__ void __launch_bounds__(256, 2) adj_reverse_kernel(const AdvanceArgs a
             // the observable's own term at the start-of-step state
             const float r = sqrtf(sx * sx + sy * sy + sz * sz);
             float dKdr, dKdp;
-            smooth_k(k, r, spp, k.t0 + (double)s * k.dt, &dKdr, &dKdp);
+            smooth_k(k, r, spp, time_arg(k, s), &dKdr, &dKdp);
             const float fw = w * a.prm.dt;
             lam[0] += fw * dKdr * sx / r;
             lam[1] += fw * dKdr * sy / r;

@@ -1374,6 +1374,8 @@ fte_status adj_args(const fte_particles* P, const fte_background* bg, const fte_
     k->r_o = (float)obs->r_o; k->inv_sr = (float)(1.0 / obs->sigma_r);
     k->inv_ec = (float)(1.0 / obs->e_c); k->inv_se = (float)(1.0 / obs->sigma_lnE);
     k->t_c = obs->t_c; k->inv_st = 1.0 / obs->sigma_t; k->t0 = prm->t0; k->dt = prm->dt;
+    k->c0 = (float)((prm->t0 - obs->t_c) / obs->sigma_t);
+    k->cstep = (float)(prm->dt / obs->sigma_t);
     return FTE_OK;
 }
 

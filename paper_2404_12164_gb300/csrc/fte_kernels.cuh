@@ -125,6 +125,7 @@ struct AdjK {
     const double* normd;          // dI/dq and dI/dH (or dJ/deps) of the normalisation integral
     float r_o, inv_sr, inv_ec, inv_se;
     double t_c, inv_st, t0, dt;   // observable time centre and width; step times t0 + n dt
+    float c0, cstep;              // (t0 - t_c) inv_st and dt inv_st: time argument c0 + n cstep
     double mean_lnE;              // mean ln E of the injected spectrum
 };
 
