@@ -384,7 +384,7 @@ __global__ void __launch_bounds__(256) adj_forward_kernel(const AdvanceArgs a, c
         const unsigned long long i = a.order ? (unsigned long long)__ldg(a.order + f) : f;
         if (!a.order && a.status[i] != FTE_ALIVE) continue;
         float x = a.x[i], y = a.y[i], z = a.z[i], mu = a.mu[i], p = a.p[i];
-        c[i] = x; c[n + i] = y; c[2 * n + i] = z; c[3 * n + i] = mu; c[4 * n + i] = p;
+        if (k.ckpt_on) { c[i] = x; c[n + i] = y; c[2 * n + i] = z; c[3 * n + i] = mu; c[4 * n + i] = p; }
         const float w = a.w[i];
         const uint32_t pid = a.id[i];
         double J = 0.0;

@@ -1436,13 +1436,22 @@ fte_status fte_adjoint_forward(fte_particles* P, const fte_background* bg, const
         a.order = sa.order;
         a.n_order = sa.hist + sa.nb;
     }
+    // each segment in launches of sort_every steps (reordered before each, as the plain
+    // step kernel is); the first launch of a segment stores its checkpoint
+    const long long sub = sorting ? (prm->sort_every < checkpoint_every ? prm->sort_every : checkpoint_every)
+                                  : checkpoint_every;
     for (long long seg = 0; seg < L.nseg && n_end > n_start; ++seg) {
         k.seg = (int)seg;
-        a.n_start = n_start + seg * checkpoint_every;
-        a.n_end = a.n_start + checkpoint_every < n_end ? a.n_start + checkpoint_every : n_end;
-        if (sorting) FTE_CUDA(launch_sort(sa, st), "sort launch");
-        FTE_CUDA(cudaMemsetAsync(a.fetch, 0, sizeof(unsigned long long), st), "fetch reset");
-        FTE_CUDA(launch_adjoint_forward(a, k, L.fwd_blocks, st), "adjoint forward launch");
+        const long long s0 = n_start + seg * checkpoint_every;
+        const long long s1 = s0 + checkpoint_every < n_end ? s0 + checkpoint_every : n_end;
+        for (long long c0 = s0; c0 < s1; c0 += sub) {
+            a.n_start = c0;
+            a.n_end = c0 + sub < s1 ? c0 + sub : s1;
+            k.ckpt_on = c0 == s0;
+            if (sorting) FTE_CUDA(launch_sort(sa, st), "sort launch");
+            FTE_CUDA(cudaMemsetAsync(a.fetch, 0, sizeof(unsigned long long), st), "fetch reset");
+            FTE_CUDA(launch_adjoint_forward(a, k, L.fwd_blocks, st), "adjoint forward launch");
+        }
     }
     return FTE_OK;
 }

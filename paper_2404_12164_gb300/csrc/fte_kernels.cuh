@@ -115,6 +115,7 @@ struct AdjK {
     int score_on;                 // injection-index gradient by the likelihood ratio
     int seg;                      // segment of this launch: steps n_start + seg K ..
     int last;                     // reverse: 1 for the first segment of the run (seg 0)
+    int ckpt_on;                  // forward: this launch starts a segment (stores its checkpoint)
     float* ckpt;                  // [segment][5][n]: x, y, z, mu, p at n_start + segment K
     float* scratch;               // [K][5][threads]: replayed start-of-step states
     float* adj;                   // [9][n]: state adjoint (5) and parameter adjoint (4) between segments
