@@ -492,8 +492,10 @@ typedef struct fte_smooth_obs {
 
 /* Scratch (DEVICE) for fte_adjoint_forward/reverse: checkpoints every
    `checkpoint_every` steps (20 bytes per particle each), per-particle step
-   counts and observables, the replay scratch of the reverse pass and the
-   time table.  0 on error. */
+   counts and observables, the replay scratch of the reverse pass (the states
+   of one segment: checkpoint_every x 20 bytes per particle, e.g. 5.1 GB for
+   1e6 particles and 256 steps), the particle orders of its 64-step chunks and
+   the time table.  0 on error. */
 size_t fte_adjoint_workspace_bytes(int device, const fte_grid* g, uint64_t n_particles, int64_t n_steps,
                                    int checkpoint_every);
 
@@ -506,6 +508,9 @@ fte_status fte_adjoint_forward(fte_particles* P, const fte_background* bg, const
 
 /* Reverse pass after fte_adjoint_forward with the same P, bg, prm, obs, steps,
    checkpoint interval and ws: writes the FTE_NGRAD gradients to dev_out[1..].
+   Segment by segment from the last, it replays the segment from its checkpoint
+   in chunks of 64 steps and then runs the step VJPs backwards over them, with
+   the particles reordered by position per chunk (prm->sort_every > 0).
    spec (HOST, optional): the injection that produced P at n_start; with a power
    law (energy 1) the dJ/dgamma entry is filled, otherwise it is 0.
    dev_per_particle (DEVICE, optional, n x (1 + FTE_NGRAD) floats): each

@@ -422,32 +422,78 @@ __global__ void __launch_bounds__(256) adj_forward_kernel(const AdvanceArgs a, c
 // (scratch[(kk * 5 + c) * threads + tid]) and walks it backwards.  The launch
 // of the first segment adds the injection-index term and reduces the gradients.
 // ---------------------------------------------------------------------------
+// Reverse pass, in two phases per checkpoint segment, each launched chunk by chunk
+// (chunk [k.c_start, k.c_end), the particles reordered before the chunk's replay):
+// the replay walks the chunk forwards from the checkpoint (or from the state the
+// previous chunk left in k.carry) and stores every start-of-step state at the
+// particle's position f in the chunk's order; the backward phase walks the chunks
+// from the last, in the same order as their replay, and runs the step VJPs over
+// the stored states, carrying the adjoints between launches in k.adj.
 template <int DT, int LAY>
-__global__ void __launch_bounds__(256, 2) adj_reverse_kernel(const AdvanceArgs a, const AdjK k)
+__global__ void __launch_bounds__(256) adj_replay_kernel(const AdvanceArgs a, const AdjK k)
 {
     __shared__ float sc[FTE_NFIELD];
-    __shared__ double red[8][FTE_NGRAD];
     if (DT != FTE_F32 && threadIdx.x < FTE_NFIELD) sc[threadIdx.x] = __ldg(a.g.scale + threadIdx.x);
     __syncthreads();
-    const unsigned long long nthr = (unsigned long long)gridDim.x * blockDim.x;
-    const unsigned long long tid = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const double In = __ldg(a.norm);
-    const float I = (float)In;
-    const float rq = (float)(__ldg(k.normd) / In), rh = (float)(__ldg(k.normd + 1) / In);
+    const float I = (float)__ldg(a.norm);
     const unsigned long long n_work = a.order ? (unsigned long long)__ldg(a.n_order) : a.n_particles;
     const size_t n = a.n_particles;
+    const long long n0 = a.n_table0 + (long long)k.seg * k.K;    // segment start
+    const long long cs = k.c_start, ce = k.c_end;
     const float* c = k.ckpt + (size_t)k.seg * 5 * n;
-    const long long seg0 = (long long)k.seg * k.K;          // steps before this segment
-    double gsum[FTE_NGRAD];
-#pragma unroll
-    for (int q = 0; q < FTE_NGRAD; ++q) gsum[q] = 0.0;
     unsigned long long noor = 0;
     for (;;) {
         const unsigned long long f = atomicAdd(a.fetch, 1ULL);
         if (f >= n_work) break;
         const unsigned long long i = a.order ? (unsigned long long)__ldg(a.order + f) : f;
         const long long nd = k.n_dead[i];
-        if (nd <= seg0) continue;                            // not alive at this segment's start
+        if (nd <= cs - a.n_table0) continue;                  // not alive at this chunk's start
+        const long long e = min(n0 + (long long)k.K, a.n_table0 + nd);   // end of its steps here
+        const float* src = cs == n0 ? c : k.carry;
+        float x = src[i], y = src[n + i], z = src[2 * n + i], mu = src[3 * n + i], p = src[4 * n + i];
+        const float w = a.w[i];
+        const uint32_t pid = a.id[i];
+        const long long hi = min(ce, e);
+        for (long long s = cs; s < hi; ++s) {
+            float* sp = k.scratch + (size_t)(s - n0) * 5 * n + f;
+            sp[0] = x; sp[n] = y; sp[2 * n] = z; sp[3 * n] = mu; sp[4 * n] = p;
+            if (s + 1 < e)
+                step<false, DT, kModeSingle, LAY>(a, a.prm, I, 0, s, pid, x, y, z, mu, p, w, nullptr, nullptr, nullptr,
+                                             sc, noor);
+        }
+        if (ce < e) {      // the start of the next chunk
+            float* cp = k.carry + i;
+            cp[0] = x; cp[n] = y; cp[2 * n] = z; cp[3 * n] = mu; cp[4 * n] = p;
+        }
+    }
+}
+
+template <int DT, int LAY>
+__global__ void __launch_bounds__(256, 2) adj_back_kernel(const AdvanceArgs a, const AdjK k)
+{
+    __shared__ float sc[FTE_NFIELD];
+    __shared__ double red[8][FTE_NGRAD];
+    if (DT != FTE_F32 && threadIdx.x < FTE_NFIELD) sc[threadIdx.x] = __ldg(a.g.scale + threadIdx.x);
+    __syncthreads();
+    const double In = __ldg(a.norm);
+    const float I = (float)In;
+    const float rq = (float)(__ldg(k.normd) / In), rh = (float)(__ldg(k.normd + 1) / In);
+    const unsigned long long n_work = a.order ? (unsigned long long)__ldg(a.n_order) : a.n_particles;
+    const size_t n = a.n_particles;
+    const long long n0 = a.n_table0 + (long long)k.seg * k.K;
+    const long long cs = k.c_start, ce = k.c_end;
+    const bool closing = k.last && cs == n0;                    // the first chunk of the run
+    const float* c = k.ckpt + (size_t)k.seg * 5 * n;
+    double gsum[FTE_NGRAD];
+#pragma unroll
+    for (int q = 0; q < FTE_NGRAD; ++q) gsum[q] = 0.0;
+    for (;;) {
+        const unsigned long long f = atomicAdd(a.fetch, 1ULL);
+        if (f >= n_work) break;
+        const unsigned long long i = a.order ? (unsigned long long)__ldg(a.order + f) : f;
+        const long long nd = k.n_dead[i];
+        if (nd <= cs - a.n_table0) continue;
+        const long long e = min(n0 + (long long)k.K, a.n_table0 + nd);
         float lam[5], gth[4];
 #pragma unroll
         for (int q = 0; q < 5; ++q) lam[q] = k.adj[q * n + i];
@@ -455,19 +501,9 @@ __global__ void __launch_bounds__(256, 2) adj_reverse_kernel(const AdvanceArgs a
         for (int q = 0; q < 4; ++q) gth[q] = k.adj[(5 + q) * n + i];
         const float w = a.w[i];
         const uint32_t pid = a.id[i];
-        float x = c[i], y = c[n + i], z = c[2 * n + i], mu = c[3 * n + i], p = c[4 * n + i];
-        const long long n0 = a.n_table0 + seg0;
-        const long long n1 = min(n0 + (long long)k.K, a.n_table0 + nd);
-        for (long long s = n0; s < n1; ++s) {
-            float* sp = k.scratch + ((size_t)(s - n0) * 5) * nthr + tid;
-            sp[0] = x; sp[nthr] = y; sp[2 * nthr] = z; sp[3 * nthr] = mu; sp[4 * nthr] = p;
-            if (s + 1 < n1)
-                step<false, DT, kModeSingle, LAY>(a, a.prm, I, 0, s, pid, x, y, z, mu, p, w, nullptr, nullptr, nullptr,
-                                             sc, noor);
-        }
-        for (long long s = n1 - 1; s >= n0; --s) {
-            const float* sp = k.scratch + ((size_t)(s - n0) * 5) * nthr + tid;
-            const float sx = sp[0], sy = sp[nthr], sz = sp[2 * nthr], smu = sp[3 * nthr], spp = sp[4 * nthr];
+        for (long long s = min(ce, e) - 1; s >= cs; --s) {
+            const float* sp = k.scratch + (size_t)(s - n0) * 5 * n + f;
+            const float sx = sp[0], sy = sp[n], sz = sp[2 * n], smu = sp[3 * n], spp = sp[4 * n];
             step_vjp<DT, LAY>(a, I, rq, rh, s, pid, sx, sy, sz, smu, spp, sc, lam, gth);
             // the observable's own term at the start-of-step state
             const float r = sqrtf(sx * sx + sy * sy + sz * sz);
@@ -479,14 +515,14 @@ __global__ void __launch_bounds__(256, 2) adj_reverse_kernel(const AdvanceArgs a
             lam[2] += fw * dKdr * sz / r;
             lam[4] += fw * dKdp;
         }
-        if (!k.last) {
+        if (!closing) {
 #pragma unroll
             for (int q = 0; q < 5; ++q) k.adj[q * n + i] = lam[q];
 #pragma unroll
             for (int q = 0; q < 4; ++q) k.adj[(5 + q) * n + i] = gth[q];
             continue;
         }
-        // first segment: injection index by the likelihood ratio of the injected energy
+        // first step of the run: injection index by the likelihood ratio of the injected energy
         float gg = 0.f;
         if (k.score_on) gg = (float)(-(log((double)energy_of(c[4 * n + i])) - k.mean_lnE) * k.J_part[i]);
         if (k.per_particle) {
@@ -496,7 +532,7 @@ __global__ void __launch_bounds__(256, 2) adj_reverse_kernel(const AdvanceArgs a
         }
         gsum[0] += gth[0]; gsum[1] += gth[1]; gsum[2] += gth[2]; gsum[3] += gth[3]; gsum[4] += gg;
     }
-    if (!k.last) return;
+    if (!closing) return;
 #pragma unroll
     for (int q = 0; q < FTE_NGRAD; ++q) {
         double v = gsum[q];
@@ -521,33 +557,54 @@ static const void* fwd_fn_lay(int dtype)
 }
 
 template <int LAY>
-static const void* rev_fn_lay(int dtype)
+static const void* rep_fn_lay(int dtype)
 {
-    if (dtype == FTE_BF16) return (const void*)adj_reverse_kernel<FTE_BF16, LAY>;
-    if (dtype == FTE_F16) return (const void*)adj_reverse_kernel<FTE_F16, LAY>;
-    return (const void*)adj_reverse_kernel<FTE_F32, LAY>;
+    if (dtype == FTE_BF16) return (const void*)adj_replay_kernel<FTE_BF16, LAY>;
+    if (dtype == FTE_F16) return (const void*)adj_replay_kernel<FTE_F16, LAY>;
+    return (const void*)adj_replay_kernel<FTE_F32, LAY>;
 }
 
-// record layout fixed at compile time, as for the step kernels
-static const void* fwd_fn(int dtype, int pair) { return pair ? fwd_fn_lay<kLayPair>(dtype) : fwd_fn_lay<kLayCell>(dtype); }
-static const void* rev_fn(int dtype, int pair) { return pair ? rev_fn_lay<kLayPair>(dtype) : rev_fn_lay<kLayCell>(dtype); }
-
-cudaError_t adjoint_blocks(int dtype, int pair, int reverse, int* blocks_per_sm)
+template <int LAY>
+static const void* back_fn_lay(int dtype)
 {
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, reverse ? rev_fn(dtype, pair) : fwd_fn(dtype, pair),
-                                                         256, 0);
+    if (dtype == FTE_BF16) return (const void*)adj_back_kernel<FTE_BF16, LAY>;
+    if (dtype == FTE_F16) return (const void*)adj_back_kernel<FTE_F16, LAY>;
+    return (const void*)adj_back_kernel<FTE_F32, LAY>;
+}
+
+// record layout fixed at compile time, as for the step kernels; kind 0 forward,
+// 1 backward VJP, 2 replay
+static const void* adj_fn(int kind, int dtype, int pair)
+{
+    if (kind == 1) return pair ? back_fn_lay<kLayPair>(dtype) : back_fn_lay<kLayCell>(dtype);
+    if (kind == 2) return pair ? rep_fn_lay<kLayPair>(dtype) : rep_fn_lay<kLayCell>(dtype);
+    return pair ? fwd_fn_lay<kLayPair>(dtype) : fwd_fn_lay<kLayCell>(dtype);
+}
+
+cudaError_t adjoint_blocks(int dtype, int pair, int kind, int* blocks_per_sm)
+{
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, adj_fn(kind, dtype, pair), 256, 0);
+}
+
+static cudaError_t launch_adj(int kind, const AdvanceArgs& a, const AdjK& k, int blocks, cudaStream_t s)
+{
+    void* args[] = {(void*)&a, (void*)&k};
+    return cudaLaunchKernel(adj_fn(kind, a.g.dtype, a.g.pair), dim3(blocks), dim3(256), args, 0, s);
 }
 
 cudaError_t launch_adjoint_forward(const AdvanceArgs& a, const AdjK& k, int blocks, cudaStream_t s)
 {
-    void* args[] = {(void*)&a, (void*)&k};
-    return cudaLaunchKernel(fwd_fn(a.g.dtype, a.g.pair), dim3(blocks), dim3(256), args, 0, s);
+    return launch_adj(0, a, k, blocks, s);
 }
 
-cudaError_t launch_adjoint_reverse(const AdvanceArgs& a, const AdjK& k, int blocks, cudaStream_t s)
+cudaError_t launch_adjoint_replay(const AdvanceArgs& a, const AdjK& k, int blocks, cudaStream_t s)
 {
-    void* args[] = {(void*)&a, (void*)&k};
-    return cudaLaunchKernel(rev_fn(a.g.dtype, a.g.pair), dim3(blocks), dim3(256), args, 0, s);
+    return launch_adj(2, a, k, blocks, s);
+}
+
+cudaError_t launch_adjoint_back(const AdvanceArgs& a, const AdjK& k, int blocks, cudaStream_t s)
+{
+    return launch_adj(1, a, k, blocks, s);
 }
 
 cudaError_t launch_norm_derivs(int model, double q, double H, double eps, double* out, double* part,

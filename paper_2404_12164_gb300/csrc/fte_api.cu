@@ -1252,10 +1252,13 @@ fte_status fte_graph_destroy(fte_graph* g)
 // ---------------------------------------------------------------------------
 namespace {
 
+// Steps per reverse-pass launch (the reordering interval of the reverse pass).
+constexpr long long kAdjChunk = 64;
+
 struct AdjLayout {
     size_t off_fetch, off_norm, off_npart, off_normd, off_ndpart, off_table, off_ckpt, off_ndead, off_jpart,
-        off_adj, off_scratch, off_sort, total;
-    int fwd_blocks, rev_blocks;
+        off_adj, off_scratch, off_carry, off_orders, off_counts, off_sort, total;
+    int fwd_blocks, rev_blocks, rep_blocks;
     long long nseg;
 };
 
@@ -1264,19 +1267,20 @@ fte_status adj_layout(int device, const fte_grid* g, unsigned long long n, long 
 {
     const int sms = device_sms(device);
     if (sms <= 0) return fail(FTE_ECUDA, "cannot query device %d", device);
-    int pf = 0, pr = 0, cur = 0;
+    int pf = 0, pr = 0, pp = 0, cur = 0;
     FTE_CUDA(cudaGetDevice(&cur), "cudaGetDevice");
     if (cur != device) FTE_CUDA(cudaSetDevice(device), "cudaSetDevice");
     const int pair = g->layout == FTE_LAYOUT_PAIR;
     cudaError_t e = adjoint_blocks(g->dtype, pair, 0, &pf);
     if (e == cudaSuccess) e = adjoint_blocks(g->dtype, pair, 1, &pr);
+    if (e == cudaSuccess) e = adjoint_blocks(g->dtype, pair, 2, &pp);
     if (cur != device) cudaSetDevice(cur);
     if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
-    if (pf < 1 || pr < 1) return fail(FTE_ENOTSUP, "adjoint kernels do not fit on an SM");
+    if (pf < 1 || pr < 1 || pp < 1) return fail(FTE_ENOTSUP, "adjoint kernels do not fit on an SM");
     L->fwd_blocks = sms * pf;
     L->rev_blocks = sms * pr;
+    L->rep_blocks = sms * pp;
     L->nseg = n_steps > 0 ? (n_steps + K - 1) / K : 1;
-    const unsigned long long nthr = (unsigned long long)L->rev_blocks * 256;
     const size_t nn = n ? n : 1;
     size_t off = 0;
     auto take = [&](size_t bytes) { const size_t o = off; off = (off + bytes + 255) & ~(size_t)255; return o; };
@@ -1290,7 +1294,11 @@ fte_status adj_layout(int device, const fte_grid* g, unsigned long long n, long 
     L->off_ndead = take(nn * sizeof(int));
     L->off_jpart = take(nn * sizeof(double));
     L->off_adj = take(9 * nn * sizeof(float));
-    L->off_scratch = take((size_t)K * 5 * nthr * sizeof(float));
+    L->off_scratch = take((size_t)K * 5 * nn * sizeof(float));    // a segment's states, per particle
+    L->off_carry = take(5 * nn * sizeof(float));
+    const long long nch = sorting ? (K + kAdjChunk - 1) / kAdjChunk : 1;
+    L->off_orders = take(sorting ? (size_t)nch * nn * sizeof(uint32_t) : 0);   // each chunk's order
+    L->off_counts = take((size_t)nch * sizeof(unsigned));
     fte_background tmp;
     memset(&tmp, 0, sizeof(tmp));
     tmp.grid = *g;
@@ -1366,6 +1374,7 @@ fte_status adj_args(const fte_particles* P, const fte_background* bg, const fte_
     k->K = K;
     k->ckpt = (float*)(w + L.off_ckpt);
     k->scratch = (float*)(w + L.off_scratch);
+    k->carry = (float*)(w + L.off_carry);
     k->adj = (float*)(w + L.off_adj);
     k->n_dead = (int*)(w + L.off_ndead);
     k->J_part = (double*)(w + L.off_jpart);
@@ -1501,17 +1510,45 @@ fte_status fte_adjoint_reverse(const fte_particles* P, const fte_background* bg,
         a.order = sa.order;
         a.n_order = sa.hist + sa.nb;
     }
+    // every segment from the last: replay its chunks forwards, then run the VJPs over
+    // its chunks backwards; each chunk's particles (those alive at its start) are
+    // reordered by their position there, and its backward launch reuses that order
+    const long long chunk = sorting ? (kAdjChunk < checkpoint_every ? kAdjChunk : checkpoint_every) : checkpoint_every;
+    uint32_t* orders = (uint32_t*)(w + L.off_orders);
+    unsigned* counts = (unsigned*)(w + L.off_counts);
     for (long long seg = L.nseg - 1; seg >= 0; --seg) {
         k.seg = (int)seg;
         k.last = seg == 0;
-        if (sorting) {
-            const float* c = k.ckpt + (size_t)seg * 5 * n;
-            sa.x = c; sa.y = c + n; sa.z = c + 2 * n; sa.mu = c + 3 * n;
-            sa.steps_min = seg * (long long)checkpoint_every;
-            FTE_CUDA(launch_sort(sa, st), "sort launch");
+        const long long n0 = n_start + seg * checkpoint_every;
+        const long long se = n0 + checkpoint_every < n_end ? n0 + checkpoint_every : n_end;
+        const long long nch = (se - n0 + chunk - 1) / chunk;
+        for (long long q = 0; q < nch; ++q) {
+            k.c_start = n0 + q * chunk;
+            k.c_end = k.c_start + chunk < se ? k.c_start + chunk : se;
+            if (sorting) {
+                const float* c = q == 0 ? k.ckpt + (size_t)seg * 5 * n : k.carry;
+                sa.x = c; sa.y = c + n; sa.z = c + 2 * n; sa.mu = c + 3 * n;
+                sa.steps_min = k.c_start - n_start;
+                sa.order = orders + (size_t)q * n;
+                FTE_CUDA(launch_sort(sa, st), "sort launch");
+                FTE_CUDA(cudaMemcpyAsync(counts + q, sa.hist + sa.nb, sizeof(unsigned), cudaMemcpyDeviceToDevice, st),
+                         "order count");
+                a.order = sa.order;
+                a.n_order = counts + q;
+            }
+            FTE_CUDA(cudaMemsetAsync(a.fetch, 0, sizeof(unsigned long long), st), "fetch reset");
+            FTE_CUDA(launch_adjoint_replay(a, k, L.rep_blocks, st), "adjoint replay launch");
         }
-        FTE_CUDA(cudaMemsetAsync(a.fetch, 0, sizeof(unsigned long long), st), "fetch reset");
-        FTE_CUDA(launch_adjoint_reverse(a, k, L.rev_blocks, st), "adjoint reverse launch");
+        for (long long q = nch - 1; q >= 0; --q) {
+            k.c_start = n0 + q * chunk;
+            k.c_end = k.c_start + chunk < se ? k.c_start + chunk : se;
+            if (sorting) {
+                a.order = orders + (size_t)q * n;
+                a.n_order = counts + q;
+            }
+            FTE_CUDA(cudaMemsetAsync(a.fetch, 0, sizeof(unsigned long long), st), "fetch reset");
+            FTE_CUDA(launch_adjoint_back(a, k, L.rev_blocks, st), "adjoint backward launch");
+        }
     }
     return FTE_OK;
 }

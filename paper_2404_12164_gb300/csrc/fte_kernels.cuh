@@ -116,8 +116,11 @@ struct AdjK {
     int seg;                      // segment of this launch: steps n_start + seg K ..
     int last;                     // reverse: 1 for the first segment of the run (seg 0)
     int ckpt_on;                  // forward: this launch starts a segment (stores its checkpoint)
+    long long c_start, c_end;     // reverse: steps of this launch's chunk of the segment
     float* ckpt;                  // [segment][5][n]: x, y, z, mu, p at n_start + segment K
-    float* scratch;               // [K][5][threads]: replayed start-of-step states
+    float* scratch;               // [K][5][n]: replayed start-of-step states of the segment, at
+                                  // each particle's position in its chunk's order (coalesced)
+    float* carry;                 // [5][n]: state at the start of the next chunk, by particle
     float* adj;                   // [9][n]: state adjoint (5) and parameter adjoint (4) between segments
     int* n_dead;                  // [n]: steps each particle took (alive at their start)
     double* J_part;               // [n]: each particle's observable
@@ -161,9 +164,11 @@ cudaError_t launch_convolve(const double* S, const ObsOut& ob, int kind, const d
                             cudaStream_t s);
 cudaError_t launch_inject(const InjectArgs& a, cudaStream_t s);
 // adjoint (fte_adjoint.cu)
-cudaError_t adjoint_blocks(int dtype, int pair, int reverse, int* blocks_per_sm);
+// resident blocks per SM of an adjoint kernel (kind 0 forward, 1 backward VJP, 2 replay)
+cudaError_t adjoint_blocks(int dtype, int pair, int kind, int* blocks_per_sm);
 cudaError_t launch_adjoint_forward(const AdvanceArgs& a, const AdjK& k, int blocks, cudaStream_t s);
-cudaError_t launch_adjoint_reverse(const AdvanceArgs& a, const AdjK& k, int blocks, cudaStream_t s);
+cudaError_t launch_adjoint_replay(const AdvanceArgs& a, const AdjK& k, int blocks, cudaStream_t s);
+cudaError_t launch_adjoint_back(const AdvanceArgs& a, const AdjK& k, int blocks, cudaStream_t s);
 cudaError_t launch_norm_derivs(int model, double q, double H, double eps, double* out, double* part,
                                cudaStream_t s);
 // spatial ordering of the alive particles (fte_sort.cu)
