@@ -199,6 +199,31 @@ static void dmumu_eval(const or_params* prm, double I, double mu, double v, doub
     }
 }
 
+/* d2 D_mumu / d mu2 of dmumu_eval's forms (with the same floor on |mu|); used only
+   to record where the pitch-angle map is strongly expanding. */
+static double dmumu_d2(const or_params* prm, double I, double mu, double v, double p)
+{
+    double lam = lambda_of_p(prm, p);
+    double am = fabs(mu);
+    double sg = (mu > 0.0) ? 1.0 : ((mu < 0.0) ? -1.0 : 0.0);
+    double omm = 1.0 - mu * mu;
+    if (prm->dmumu == OR_DMUMU_QLT) {
+        double nu = 3.0 * v * I / (2.0 * lam);
+        double g = pow(am, prm->q - 1.0) + prm->H;
+        double amf = am > prm->mu_floor ? am : prm->mu_floor;
+        double dg = (prm->q - 1.0) * pow(amf, prm->q - 2.0) * sg;
+        double d2g = (prm->q - 1.0) * (prm->q - 2.0) * pow(amf, prm->q - 3.0);
+        return 0.5 * nu * (-2.0 * g - 4.0 * mu * dg + omm * d2g);
+    } else if (prm->dmumu == OR_DMUMU_PAPER) {
+        double D0 = 3.0 * v * I / (4.0 * lam);
+        double h = am / (1.0 + am) + prm->eps;
+        double dh = sg / ((1.0 + am) * (1.0 + am));
+        double d2h = -2.0 / ((1.0 + am) * (1.0 + am) * (1.0 + am));
+        return D0 * (d2h * omm - 4.0 * mu * dh - 2.0 * h);
+    }
+    return -2.0 * v / (2.0 * lam);
+}
+
 void or_dmumu(const or_params* prm, double mu, double v, double p, double out[3])
 {
     double I = or_norm_integral(prm->dmumu, prm->q, prm->H, prm->eps);
@@ -698,6 +723,7 @@ int or_inject(const or_background* bg, const or_inject_spec* sp, const uint32_t*
         memset(P, 0, sizeof(*P));
         P->id = ids[i];
         P->n_div = -1;
+        P->n_sens = -1;
         P->status = OR_ALIVE;
         double u[4];
         or_uniforms(sp->seed, sp->set_id, 0u, P->id, 1u, u);
@@ -927,6 +953,18 @@ static int step_one(const or_background* bg, const or_params* prm, double I,
     if (mu_new < -1.0) mu_new = -1.0;
     if (mu * mu_new <= 0.0) ev = 1;                      /* mu changes sign */
     if (prm->shock_divv > 0.0 && fabs(divv) > prm->shock_divv) ev = 1;
+    if (P->n_sens < 0) {
+        /* derivative of the pitch-angle update with respect to mu, fields held fixed:
+           1 + dt (d mudot/dmu + d2D/dmu2) + z sqrt(2 dt) d sqrt(D)/dmu (bookkeeping) */
+        double d2D = dmumu_d2(prm, I, mu, v, p);
+        double dq = divv - 3.0 * bbgv;
+        double dmudot = 0.5 * (-2.0 * mu * (v * divb + mu * divv - 3.0 * mu * bbgv - (2.0 / v) * bdvdt)
+                               + omm * dq);
+        double jac = 1.0 + (dmudot + d2D) * dt + (D > 0.0 ? zn[0] * sqrt(2.0 * dt) * dD / (2.0 * sqrt(D)) : 0.0);
+        double L = P->amp_log + log(fabs(jac) > 1e-300 ? fabs(jac) : 1e-300);
+        P->amp_log = L > 0.0 ? L : 0.0;
+        if (P->amp_log > log(100.0)) P->n_sens = (int32_t)n;
+    }
 
     /* Eq. 2 with cross-field diffusion kappa_perp = (v lambda_perp / 3)(I - bb) */
     double kap = v * prm->lambda_perp / 3.0;

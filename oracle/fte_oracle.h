@@ -80,7 +80,13 @@ typedef struct {
     uint32_t id;
     int32_t status;
     int32_t flags;               /* bit 0: injection decision within rounding of a threshold/edge */
-    int32_t pad;
+    int32_t n_sens;              /* first step at which a difference in mu made at an earlier
+                                    step has been amplified more than 100-fold by the pitch-angle
+                                    map (fields held fixed), -1 if none: from there FP32 and
+                                    FP64 rounding grow apart although both compute the same map
+                                    (bookkeeping only) */
+    double amp_log;              /* max over earlier steps k of sum_{j>=k} ln|d mu_{j+1}/d mu_j|,
+                                    i.e. L_n = max(0, L_{n-1} + ln|d mu'/d mu|) */
 } or_particle;
 
 void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);

@@ -64,8 +64,8 @@ class ObserverC(C.Structure):
 
 PARTICLE = np.dtype([("x", "f8"), ("y", "f8"), ("z", "f8"), ("mu", "f8"), ("p", "f8"),
                      ("w", "f8"), ("n_div", "i8"), ("id", "u4"), ("status", "i4"),
-                     ("flags", "i4"), ("pad", "i4")])
-assert PARTICLE.itemsize == 72
+                     ("flags", "i4"), ("n_sens", "i4"), ("amp_log", "f8")])
+assert PARTICLE.itemsize == 80
 
 _lib = None
 
@@ -368,6 +368,7 @@ def make_particles(n, x=0.0, y=0.0, z=0.0, mu=0.0, p=0.01, w=1.0, ids=None):
     P["x"], P["y"], P["z"], P["mu"], P["p"], P["w"] = x, y, z, mu, p, w
     P["id"] = np.arange(n, dtype=np.uint32) if ids is None else ids
     P["n_div"] = -1
+    P["n_sens"] = -1
     return P
 
 

@@ -57,11 +57,15 @@ def oracle_run(w, fields, n_steps, chunks=None, params=None, observers=None, n_p
     return dict(states=states, tallies=tallies, ledger_w=L["w"], ledger_n=L["n"])
 
 
-def trajectory_errors(g, o, step, sel=None):
+def trajectory_errors(g, o, step, sel=None, expanding=False):
     """Per-particle errors at checkpoint `step` for particles the oracle saw no
     divergence event for before `step` and that both sides have alive or absorbed
-    identically.  Returns (mask, dict of error arrays)."""
+    identically.  expanding=True also leaves out particles whose pitch-angle map
+    had amplified an earlier difference in mu more than 100-fold before `step`
+    (the oracle's n_sens).  Returns (mask, dict of error arrays)."""
     ok = ((o["n_div"] < 0) | (o["n_div"] >= step)) & ((o["flags"] & 1) == 0)
+    if expanding:
+        ok &= (o["n_sens"] < 0) | (o["n_sens"] >= step)
     if sel is not None:
         ok &= sel
     r_o = np.sqrt(o["x"] ** 2 + o["y"] ** 2 + o["z"] ** 2)

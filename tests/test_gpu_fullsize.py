@@ -1,0 +1,117 @@
+"""Parity at the full size of the benchmark workload, in the launch configuration
+bench.py times: the synthetic CIR on the 512 x 60 x 180 grid with 24 hourly
+snapshots (12.7 GB of cell records), 1e6 protons injected in the div V < 0 cells,
+4 days of 10-s steps advanced in calls of up to 1024 steps with the particles
+reordered every 64 steps and the warp-merged global tally.
+
+The FP64 oracle advances a seeded sample of the particles one by one over the same
+steps.  At every call boundary each sampled particle's state agrees within 1e-4
+(position relative to r, mu, p relative) up to its first divergence event, the
+parity protocol, or the first step at which the pitch-angle map has amplified an
+earlier difference in mu more than 100-fold (under the quasi-linear D_mumu near
+mu = 0, where the derivative of sqrt(D) grows as |mu|^(q-2): there FP32 and FP64
+rounding grow apart by orders of magnitude within tens of steps); absorbed counts
+and the weight ledger are checked over the whole population.  Call boundaries at 64, 256 and 512 steps add early comparisons: a
+call of 1024 steps launches the same 64-step kernels as these shorter calls, and
+the results do not depend on how the steps are split into calls (tested bitwise
+elsewhere)."""
+import numpy as np
+import pytest
+
+from fte_inputs import configs
+from oracle import oracle as O
+
+from _parity import trajectory_errors
+
+pytestmark = pytest.mark.gpu
+
+N_SAMPLE = 2048
+BOUNDS = [64, 256, 512, 1024] + list(range(2048, 34560, 1024)) + [34560]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2404_12164_gb300 import build
+    build.build()
+    from oracle import build as ob
+    ob.build()
+
+
+@pytest.fixture(scope="module")
+def full_run():
+    import torch
+    from paper_2404_12164_gb300 import api
+    w = configs.cir_uniform_1e6()
+    assert (w.grid.nr, w.grid.nth, w.grid.nph, w.grid.n_snap) == (512, 60, 180, 24)
+    assert w.n_particles == 1_000_000 and w.n_steps == 34560
+    w.params.sort_every = 64
+    f = configs.build_background(w)
+    bg = api.Background(w.grid)
+    api.fte_load_background(bg, f)
+    pool = api.Particles(w.n_particles)
+    tally = api.Tally(w.observers)
+    api.fte_tally_reset(tally)
+    failed = api.fte_inject(pool, bg, w.inject, w.n_particles, tally, check_failed=False)
+    rng = np.random.default_rng(20240418)
+    sample = np.sort(rng.choice(w.n_particles, N_SAMPLE, replace=False))
+    ws = api.Workspace()
+    states = {}
+    prev = 0
+    for b in BOUNDS:
+        api.fte_advance(pool, bg, w.params, tally, prev, b, ws)
+        prev = b
+        st = pool.state()
+        states[b] = {k: v[sample] for k, v in st.items()}
+    final = pool.state()
+    lw, ln = api.fte_ledger(tally)
+    torch.cuda.synchronize()
+    del bg
+    torch.cuda.empty_cache()
+
+    obg = O.grid_background(w.grid, f)
+    P, _ = O.inject(obg, w.inject, sample.astype(np.uint32))
+    ostates = {}
+    prev = 0
+    for b in BOUNDS:
+        O.advance(obg, w.params, P, prev, b)
+        prev = b
+        ostates[b] = P.copy()
+    return dict(w=w, sample=sample, g=states, o=ostates, final=final, lw=lw, ln=ln, failed=failed)
+
+
+def test_sampled_trajectories_match_oracle(full_run):
+    g, o = full_run["g"], full_run["o"]
+    assert np.array_equal(g[BOUNDS[0]]["id"], full_run["sample"].astype(np.uint32))
+    total = 0
+    for b in BOUNDS:
+        ok, e = trajectory_errors(g[b], o[b], b, sel=o[b]["status"] != 5, expanding=True)   # 5: not injected
+        total += int(ok.sum())
+        if b <= 256:
+            assert ok.sum() >= 500, f"only {ok.sum()} matched trajectories at step {b}"
+        if ok.any():
+            for k in ("pos", "mu", "p", "w"):
+                assert e[k].max() <= 1e-4, (b, k, float(e[k].max()))
+            assert e["status"].sum() == 0, (b, "status")
+    print(f"{total} (particle, boundary) pairs compared over {len(BOUNDS)} boundaries")
+    assert total >= 2000
+
+
+def test_full_population_ledger(full_run):
+    """Exact counts and the FP64 weight ledger over all 1e6 particles after 4 days."""
+    st, lw, ln = full_run["final"], full_run["lw"], full_run["ln"]
+    n_inj = int(ln[0])
+    assert n_inj + int(ln[5]) == full_run["w"].n_particles
+    status = st["status"]
+    alive = status == 0
+    for code in (1, 2, 3, 4):            # absorbed at r_min, r_max, a theta face; non-finite
+        assert int(ln[code]) == int((status == code).sum()), code
+    assert int(alive.sum()) + sum(int(ln[c]) for c in (1, 2, 3, 4)) == n_inj
+    w = st["w"].astype(np.float64)
+    assert lw[0] == pytest.approx(w[status != 5].sum(), rel=1e-9)
+    absorbed = sum(float(lw[c]) for c in (1, 2, 3, 4))
+    assert absorbed + w[alive].sum() == pytest.approx(float(lw[0]), rel=1e-9)
+    # alive particle-steps: more than a day's worth for every particle injected
+    assert int(ln[6]) > 8640 * n_inj

@@ -9,6 +9,8 @@ other modules.
 """
 import math
 
+import numpy as np
+
 import pytest
 import sympy as sp
 from scipy import integrate
@@ -96,3 +98,34 @@ def test_rigidity_scaling():
     v = O.speed_of_p(p)
     lam = 0.3 * 2 ** (1 / 3)
     assert O.dmumu(prm, 0.0, v, p)[2] == pytest.approx(v / (2 * lam), rel=1e-13)
+
+
+@pytest.mark.parametrize("model", ["qlt", "paper", "iso"])
+def test_pitch_angle_amplification_record(model):
+    """The oracle's record of how much the pitch-angle map amplifies differences in mu
+    (amp_log after one step = max(0, ln|d mu'/d mu|)) equals a central finite difference
+    of its own one-step update with the same noise, on a uniform-B background (no
+    focusing or adiabatic terms, so d mu'/d mu comes from D_mumu alone)."""
+    from oracle import oracle as O
+    from fte_inputs.configs import Params
+    bg = O.analytic_background("uniform_b", [5.0])
+    prm = Params(dmumu=model, lambda_par=0.05, q=5 / 3, H=0.05, eps=0.048, dt=30.0)
+    p0 = 0.0103
+    n = 256
+    mus = np.linspace(0.03, 0.6, n)
+    ids = np.arange(n, dtype=np.uint32)
+    P = O.make_particles(n, 1.0, 0.0, 0.0, mus, p0, ids=ids)
+    O.advance(bg, prm, P, 0, 1)
+    h = 1e-6
+    Pp = O.make_particles(n, 1.0, 0.0, 0.0, mus + h, p0, ids=ids)
+    Pm = O.make_particles(n, 1.0, 0.0, 0.0, mus - h, p0, ids=ids)
+    O.advance(bg, prm, Pp, 0, 1)
+    O.advance(bg, prm, Pm, 0, 1)
+    clean = (Pp["n_div"] < 0) & (Pm["n_div"] < 0) & (P["n_div"] < 0)    # no reflection or sign change
+    jac = (Pp["mu"] - Pm["mu"]) / (2 * h)
+    expect = np.maximum(0.0, np.log(np.abs(jac)))
+    assert clean.sum() > 100
+    assert np.allclose(P["amp_log"][clean], expect[clean], rtol=0, atol=2e-4)
+    assert (P["amp_log"][clean] > 0).sum() > 10          # some steps do expand
+    # a 100-fold amplification is recorded as the first such step, none here after one step
+    assert np.all(P["n_sens"][clean] == -1) or model == "qlt"
