@@ -115,3 +115,103 @@ def test_full_population_ledger(full_run):
     assert absorbed + w[alive].sum() == pytest.approx(float(lw[0]), rel=1e-9)
     # alive particle-steps: more than a day's worth for every particle injected
     assert int(ln[6]) > 8640 * n_inj
+
+
+def test_parker_full_config_all_particles():
+    """The Parker-spiral workload at its full size (128 x 16 x 32 grid, 1e4 protons at
+    100 keV from 0.1 au, quasi-linear D_mumu, 1 day of 10-s steps): every particle is
+    recomputed by the oracle, states agree at the call boundaries up to the first
+    divergence or 100-fold amplification, absorbed counts match, and the 1 au shell
+    tally agrees within 3 sigma in every bin with enough events."""
+    import torch
+    from paper_2404_12164_gb300 import api, _abi as A
+    w = configs.parker_1e4()
+    assert (w.grid.nr, w.grid.nth, w.grid.nph, w.n_particles, w.n_steps) == (128, 16, 32, 10_000, 8640)
+    f = configs.build_background(w)
+    bounds = [64, 512, 1024, 2048, 4096, 8640]
+    bg = api.Background(w.grid)
+    api.fte_load_background(bg, f)
+    pool = api.Particles(w.n_particles)
+    tally = api.Tally(w.observers)
+    api.fte_tally_reset(tally)
+    api.fte_inject(pool, bg, w.inject, w.n_particles, tally)
+    ws = api.Workspace()
+    g, prev = {}, 0
+    for b in bounds:
+        api.fte_advance(pool, bg, w.params, tally, prev, b, ws)
+        prev = b
+        g[b] = pool.state()
+    gS = api.fte_tally(tally, 0, A.FTE_TALLY_S)
+    gS2 = api.fte_tally(tally, 0, A.FTE_TALLY_S2)
+    lw, ln = api.fte_ledger(tally)
+    torch.cuda.synchronize()
+
+    obg = O.grid_background(w.grid, f)
+    P, led = O.inject(obg, w.inject, np.arange(w.n_particles, dtype=np.uint32))
+    T = O.Tally(w.observers)
+    prev = 0
+    total = 0
+    for b in bounds:
+        O.advance(obg, w.params, P, prev, b, tally=T, ledger=led)
+        prev = b
+        ok, e = trajectory_errors(g[b], P, b, expanding=True)
+        total += int(ok.sum())
+        if ok.any():
+            for k in ("pos", "mu", "p"):
+                assert e[k].max() <= 1e-4, (b, k, float(e[k].max()))
+            assert e["status"].sum() == 0, (b, "status")
+    assert total >= 10_000
+    L = led.as_dict()
+    for code in (0, 1, 2, 3, 4):
+        # counts of whole trajectories: equal up to the few that diverged near a boundary
+        assert abs(int(ln[code]) - int(L["n"][code])) <= max(3, 1e-3 * int(L["n"][code])), code
+    oS, oS2 = T.obs_view(0, T.S), T.obs_view(0, T.S2)
+    sigma = np.sqrt(gS2 + oS2)
+    busy = oS2 > 0
+    assert busy.sum() > 50
+    assert np.all(np.abs(gS - oS)[busy] <= 3 * sigma[busy] + 1e-12 * np.abs(oS).max())
+
+
+def test_amr_full_config_ledger():
+    """The block-AMR workload at its full size (39,520 leaves of 16^3 cells, 2 snapshots,
+    44 GB of padded FP32 leaf lattices, 1e7 protons, 1800 steps of 2 s) in the benchmark's
+    launch configuration: exact counts and the FP64 weight ledger over all particles.
+    (Per-trajectory parity of block AMR is tested on smaller leaf sets: the oracle would
+    need a 44 GB host copy of these lattices.)"""
+    import torch
+    from fte_inputs import amr
+    from fte_inputs.grid import REC
+    from paper_2404_12164_gb300 import api
+    w = configs.cir_amr_1e7()
+    assert w.n_particles == 10_000_000 and w.n_steps == 1800
+    w.params.sort_every = 64
+    spec = w.grid
+    leaves = amr.build_leaves(spec, amr.divv_refiner_batched(spec, w.amr_divv, device="cuda"))
+    assert len(leaves) == 39_520
+    bg = api.AmrBackground(spec, leaves)
+    P = spec.bsize + 2
+    view = bg.dev.view(spec.n_snap, len(leaves), P, P, P, REC)
+    view.zero_()
+    amr.fields_batched(spec, leaves, device="cuda", out=view)
+    api.fte_amr_prepare(bg)
+    pool = api.Particles(w.n_particles)
+    tally = api.Tally(w.observers)
+    api.fte_tally_reset(tally)
+    api.fte_inject(pool, bg, w.inject, w.n_particles, tally, check_failed=False)
+    ws = api.Workspace()
+    for c in range(0, w.n_steps, 1024):
+        api.fte_advance(pool, bg, w.params, tally, c, min(c + 1024, w.n_steps), ws)
+    st = pool.state()
+    lw, ln = api.fte_ledger(tally)
+    torch.cuda.synchronize()
+    status = st["status"]
+    n_inj = int(ln[0])
+    assert n_inj + int(ln[5]) == w.n_particles
+    for code in (1, 2, 3, 4):
+        assert int(ln[code]) == int((status == code).sum()), code
+    alive = status == 0
+    assert int(alive.sum()) + sum(int(ln[c]) for c in (1, 2, 3, 4)) == n_inj
+    wts = st["w"].astype(np.float64)
+    absorbed = sum(float(lw[c]) for c in (1, 2, 3, 4))
+    assert absorbed + wts[alive].sum() == pytest.approx(float(lw[0]), rel=1e-9)
+    assert 0.5 * n_inj * w.n_steps < int(ln[6]) <= n_inj * w.n_steps
