@@ -415,6 +415,18 @@ __device__ __forceinline__ void corner_pair(const GridK& g, long long rec, float
     }
 }
 
+// d0 = a0 * b0 + d0 and d1 = a1 * b1 + d1 in one paired FP32 FMA (each lane a fused
+// multiply-add rounded once, so the results equal two fmaf calls).
+__device__ __forceinline__ void fma2(float& d0, float& d1, float a0, float a1, float b0, float b1)
+{
+    unsigned long long d, a, b, c;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(a) : "f"(a0), "f"(a1));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(b) : "f"(b0), "f"(b1));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(c) : "f"(d0), "f"(d1));
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(d0), "=f"(d1) : "l"(d));
+}
+
 // Trilinear (space) x linear (time) interpolation: for each snapshot and each
 // of the 4 (theta, phi) corners, the two r-neighbours are one contiguous block
 // (pair layout: one record; 144 of its bytes loaded in FP32, 72 in 16-bit).  For 16-bit
@@ -451,13 +463,20 @@ __device__ __forceinline__ void gather(const GridK& g, const StepEntry& e, const
             corner_pair<DT, LAY>(g, rec, lo, hi);
             const float c0 = (1.f - L.fr) * wjk, c1 = L.fr * wjk;
             const float w0 = ws * c0, w1 = ws * c1;
+            // acc = w0 lo + (w1 hi + acc) per field, two fields per paired FMA along the
+            // record's field pairs: (B_x, B_y), (B_z, V_x), (V_y, V_z), then the gradients;
+            // V goes to this snapshot's vs with the spatial weights c0, c1 alone
+            fma2(F.f[0], F.f[1], w1, w1, hi[0], hi[1]);
+            fma2(F.f[0], F.f[1], w0, w0, lo[0], lo[1]);
+            fma2(F.f[2], vs[0], w1, c1, hi[2], hi[3]);
+            fma2(F.f[2], vs[0], w0, c0, lo[2], lo[3]);
+            fma2(vs[1], vs[2], c1, c1, hi[4], hi[5]);
+            fma2(vs[1], vs[2], c0, c0, lo[4], lo[5]);
 #pragma unroll
-            for (int m = 0; m < FTE_NFIELD; ++m) {
-                if (m >= 3 && m < 6) continue;
-                F.f[m] = fmaf(w0, lo[m], fmaf(w1, hi[m], F.f[m]));
+            for (int m = 6; m < FTE_NFIELD; m += 2) {
+                fma2(F.f[m], F.f[m + 1], w1, w1, hi[m], hi[m + 1]);
+                fma2(F.f[m], F.f[m + 1], w0, w0, lo[m], lo[m + 1]);
             }
-#pragma unroll
-            for (int m = 0; m < 3; ++m) vs[m] = fmaf(c0, lo[3 + m], fmaf(c1, hi[3 + m], vs[m]));
             if (KPERP) {
                 const float er = L.dfr * wjk;                          // d w / d r
                 const float et = (ct ? 1.f : -1.f) * L.dft * wp_;      // d w / d theta (x w_r)
