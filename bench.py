@@ -830,8 +830,8 @@ def run_adjoint_case(args):
 def ring_uploads(plan, R, n_snap, periodic):
     """Snapshot copies of one streamed step: the injection snapshot, then the ring's own rule
     (a slot holding the snapshot - for a periodic sequence, the same snapshot of another
-    period - is not copied again; with R >= 3 the next snapshot is prefetched unless its slot
-    is in use)."""
+    period - is not copied again; with R >= 3 the next R - 2 snapshots are prefetched unless
+    their slots are in use)."""
     slots = [-1] * R
     n = 0
 
@@ -853,8 +853,10 @@ def ring_uploads(plan, R, n_snap, periodic):
         u1 = u0 + 1 if key >= 0 else u0
         ensure(u0)
         ensure(u1)
-        if R >= 3 and (periodic or u1 + 1 <= n_snap - 1):
-            ensure(u1 + 1, busy=(u0 % R, u1 % R), prefetch=True)
+        for nx in range(u1 + 1, u1 + R - 1):
+            if not periodic and nx > n_snap - 1:
+                break
+            ensure(nx, busy=(u0 % R, u1 % R), prefetch=True)
     return n
 
 

@@ -302,7 +302,7 @@ fte_status fte_advance(fte_particles* P, const fte_background* bg, const fte_par
  * the cost of whole snapshot files): with grid.ring = R > 0 only R snapshots are
  * resident and fte_advance_streamed moves snapshot files from host memory into
  * their slots as the simulated time reaches them, on a copy stream, overlapped
- * with the steps of the previous interval (R >= 3 prefetches one interval ahead).
+ * with the steps of earlier intervals (R >= 3 prefetches R - 2 snapshots ahead).
  * ------------------------------------------------------------------------- */
 
 /* Plan of a streamed advance: the steps n_start .. n_end-1 split into runs that
@@ -336,7 +336,7 @@ fte_status fte_stream_scales(const fte_background* bg, const void* host_snapshot
                              size_t staging_bytes, void* stream);
 
 /* fte_advance over a ring background (grid.ring >= 2): for every run of the
-   plan, the snapshots it needs (and, with ring >= 3, the next one) are copied
+   plan, the snapshots it needs (and, with ring >= 3, the next ring - 2) are copied
    from host_snapshots (HOST, page-locked for overlap: the n_snap snapshots in
    order, each fte_snapshot_bytes(g) bytes of FP32 cell records) into their slots
    on copy_stream - for a 16-bit or pair-layout ring through `staging` (DEVICE,

@@ -1783,9 +1783,11 @@ fte_status fte_advance_streamed(fte_particles* P, const fte_background* bg, cons
         const int s0 = (int)pmod(u0, R), s1 = (int)pmod(u1, R);
         ensure(u0, -1, -1, false);
         ensure(u1, -1, -1, false);
-        if (R >= 3) {      // the snapshot after this pair, while this run computes
-            const int64_t nx = u1 + 1;
-            if (g.periodic || nx <= g.n_snap - 1) ensure(nx, s0, s1, true);
+        // the snapshots after this pair, as far ahead as the slots that this run does not
+        // use allow (R - 2 of them), while this run computes
+        for (int64_t nx = u1 + 1; nx <= u1 + R - 2 && result == FTE_OK; ++nx) {
+            if (!g.periodic && nx > g.n_snap - 1) break;
+            ensure(nx, s0, s1, true);
         }
         if (result != FTE_OK) break;
         for (int sl : {s0, s1}) {

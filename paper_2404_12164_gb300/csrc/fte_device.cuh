@@ -432,7 +432,10 @@ __device__ __forceinline__ void fma2(float& d0, float& d1, float a0, float a1, f
 // (pair layout: one record; 144 of its bytes loaded in FP32, 72 in 16-bit).  For 16-bit
 // storage the sums run over the stored values and the per-field scales `sc`
 // are applied once at the end.
-template <bool KPERP, int DT, int LAY>
+// PAIRED: accumulate with paired FMAs (the step kernels with the global tally; the
+// adjoint kernels, at their register bound, measured faster with scalar FMAs; both
+// round identically).
+template <bool KPERP, int DT, int LAY, bool PAIRED = false>
 __device__ __forceinline__ void gather(const GridK& g, const StepEntry& e, const Loc& L,
                                        const float* sc, Fields<KPERP>& F)
 {
@@ -466,16 +469,26 @@ __device__ __forceinline__ void gather(const GridK& g, const StepEntry& e, const
             // acc = w0 lo + (w1 hi + acc) per field, two fields per paired FMA along the
             // record's field pairs: (B_x, B_y), (B_z, V_x), (V_y, V_z), then the gradients;
             // V goes to this snapshot's vs with the spatial weights c0, c1 alone
-            fma2(F.f[0], F.f[1], w1, w1, hi[0], hi[1]);
-            fma2(F.f[0], F.f[1], w0, w0, lo[0], lo[1]);
-            fma2(F.f[2], vs[0], w1, c1, hi[2], hi[3]);
-            fma2(F.f[2], vs[0], w0, c0, lo[2], lo[3]);
-            fma2(vs[1], vs[2], c1, c1, hi[4], hi[5]);
-            fma2(vs[1], vs[2], c0, c0, lo[4], lo[5]);
+            if (PAIRED) {
+                fma2(F.f[0], F.f[1], w1, w1, hi[0], hi[1]);
+                fma2(F.f[0], F.f[1], w0, w0, lo[0], lo[1]);
+                fma2(F.f[2], vs[0], w1, c1, hi[2], hi[3]);
+                fma2(F.f[2], vs[0], w0, c0, lo[2], lo[3]);
+                fma2(vs[1], vs[2], c1, c1, hi[4], hi[5]);
+                fma2(vs[1], vs[2], c0, c0, lo[4], lo[5]);
 #pragma unroll
-            for (int m = 6; m < FTE_NFIELD; m += 2) {
-                fma2(F.f[m], F.f[m + 1], w1, w1, hi[m], hi[m + 1]);
-                fma2(F.f[m], F.f[m + 1], w0, w0, lo[m], lo[m + 1]);
+                for (int m = 6; m < FTE_NFIELD; m += 2) {
+                    fma2(F.f[m], F.f[m + 1], w1, w1, hi[m], hi[m + 1]);
+                    fma2(F.f[m], F.f[m + 1], w0, w0, lo[m], lo[m + 1]);
+                }
+            } else {
+#pragma unroll
+                for (int m = 0; m < FTE_NFIELD; ++m) {
+                    if (m >= 3 && m < 6) continue;
+                    F.f[m] = fmaf(w0, lo[m], fmaf(w1, hi[m], F.f[m]));
+                }
+#pragma unroll
+                for (int m = 0; m < 3; ++m) vs[m] = fmaf(c0, lo[3 + m], fmaf(c1, hi[3 + m], vs[m]));
             }
             if (KPERP) {
                 const float er = L.dfr * wjk;                          // d w / d r

@@ -84,7 +84,7 @@ __device__ __forceinline__ int step(const AdvanceArgs& a, const ParamsK& prm, fl
     Loc L;
     locate(a.g, r, th, ph, L);
     Fields<KPERP> F;
-    gather<KPERP, DT, LAY>(a.g, e, L, sc, F);
+    gather<KPERP, DT, LAY, global_tally(MODE)>(a.g, e, L, sc, F);
     const float* B = F.f;
     const float* V = F.f + 3;
     const float* G = F.f + 6;
