@@ -172,12 +172,13 @@ def test_parker_full_config_all_particles():
     assert np.all(np.abs(gS - oS)[busy] <= 3 * sigma[busy] + 1e-12 * np.abs(oS).max())
 
 
-def test_amr_full_config_ledger():
+def test_amr_full_config():
     """The block-AMR workload at its full size (39,520 leaves of 16^3 cells, 2 snapshots,
     44 GB of padded FP32 leaf lattices, 1e7 protons, 1800 steps of 2 s) in the benchmark's
-    launch configuration: exact counts and the FP64 weight ledger over all particles.
-    (Per-trajectory parity of block AMR is tested on smaller leaf sets: the oracle would
-    need a 44 GB host copy of these lattices.)"""
+    launch configuration: exact counts and the FP64 weight ledger over all particles, and a
+    seeded sample of 1024 particles recomputed by the oracle (which interpolates across leaf
+    faces from the neighbours on each query, without the ghost layers) on a host copy of
+    the lattices, compared as above at the call boundaries."""
     import torch
     from fte_inputs import amr
     from fte_inputs.grid import REC
@@ -198,10 +199,16 @@ def test_amr_full_config_ledger():
     tally = api.Tally(w.observers)
     api.fte_tally_reset(tally)
     api.fte_inject(pool, bg, w.inject, w.n_particles, tally, check_failed=False)
+    rng = np.random.default_rng(20240419)
+    sample = np.sort(rng.choice(w.n_particles, 1024, replace=False))
+    bounds = [64, 256, 512, 1024, 1800]
     ws = api.Workspace()
-    for c in range(0, w.n_steps, 1024):
-        api.fte_advance(pool, bg, w.params, tally, c, min(c + 1024, w.n_steps), ws)
-    st = pool.state()
+    g, prev = {}, 0
+    for b in bounds:
+        api.fte_advance(pool, bg, w.params, tally, prev, b, ws)
+        prev = b
+        st = pool.state()
+        g[b] = {k: v[sample] for k, v in st.items()}
     lw, ln = api.fte_ledger(tally)
     torch.cuda.synchronize()
     status = st["status"]
@@ -215,3 +222,23 @@ def test_amr_full_config_ledger():
     absorbed = sum(float(lw[c]) for c in (1, 2, 3, 4))
     assert absorbed + wts[alive].sum() == pytest.approx(float(lw[0]), rel=1e-9)
     assert 0.5 * n_inj * w.n_steps < int(ln[6]) <= n_inj * w.n_steps
+    del st, pool, tally, ws
+    fields = view.cpu().numpy()              # the lattices on the host (ghost values ignored)
+    del view, bg
+    torch.cuda.empty_cache()
+
+    obg = O.amr_background(spec, leaves, fields)
+    Po, _ = O.inject(obg, w.inject, sample.astype(np.uint32))
+    total, prev = 0, 0
+    for b in bounds:
+        O.advance(obg, w.params, Po, prev, b)
+        prev = b
+        ok, e = trajectory_errors(g[b], Po, b, sel=Po["status"] != 5, expanding=True)
+        total += int(ok.sum())
+        if b <= 256:
+            assert ok.sum() >= 300, f"only {ok.sum()} matched trajectories at step {b}"
+        if ok.any():
+            for k in ("pos", "mu", "p", "w"):
+                assert e[k].max() <= 1e-4, (b, k, float(e[k].max()))
+            assert e["status"].sum() == 0, (b, "status")
+    print(f"AMR: {total} (particle, boundary) pairs compared")
