@@ -15,10 +15,13 @@ and the weight ledger are checked over the whole population.  Call boundaries at
 call of 1024 steps launches the same 64-step kernels as these shorter calls, and
 the results do not depend on how the steps are split into calls (tested bitwise
 elsewhere)."""
+import dataclasses
+
 import numpy as np
 import pytest
 
 from fte_inputs import configs
+from fte_inputs.configs import SmoothObserver
 from oracle import oracle as O
 
 from _parity import trajectory_errors
@@ -41,14 +44,19 @@ def _built():
 
 
 @pytest.fixture(scope="module")
-def full_run():
-    import torch
-    from paper_2404_12164_gb300 import api
+def cir_full():
     w = configs.cir_uniform_1e6()
     assert (w.grid.nr, w.grid.nth, w.grid.nph, w.grid.n_snap) == (512, 60, 180, 24)
     assert w.n_particles == 1_000_000 and w.n_steps == 34560
     w.params.sort_every = 64
-    f = configs.build_background(w)
+    return w, configs.build_background(w)
+
+
+@pytest.fixture(scope="module")
+def full_run(cir_full):
+    import torch
+    from paper_2404_12164_gb300 import api
+    w, f = cir_full
     bg = api.Background(w.grid)
     api.fte_load_background(bg, f)
     pool = api.Particles(w.n_particles)
@@ -242,3 +250,112 @@ def test_amr_full_config():
                 assert e[k].max() <= 1e-4, (b, k, float(e[k].max()))
             assert e["status"].sum() == 0, (b, "status")
     print(f"AMR: {total} (particle, boundary) pairs compared")
+
+
+def test_ensemble_full_config_sampled(cir_full):
+    """The 64-set ensemble at its full size (2e7 protons on the full CIR grid, 2160 steps)
+    through the ensemble kernel in its default launch configuration: 8 seeded sets, 128
+    particles each, recomputed by the oracle with their set's parameters and Philox key."""
+    import torch
+    from paper_2404_12164_gb300 import api
+    _, f = cir_full
+    w = configs.cir_ensemble_64()
+    assert w.n_particles == 20_000_000 and len(w.sets) == 64
+    w.params.sort_every = 64
+    bg = api.Background(w.grid)
+    api.fte_load_background(bg, f)
+    pool = api.Particles(w.n_particles)
+    tally = api.Tally(w.observers, n_sets=64)
+    api.fte_tally_reset(tally)
+    api.fte_inject_batched(pool, bg, w.sets, tally)
+    rng = np.random.default_rng(20240420)
+    chosen = np.sort(rng.choice(64, 8, replace=False))
+    starts = np.concatenate([[0], np.cumsum([s.count for s in w.sets])])
+    picks = {int(k): np.sort(rng.choice(w.sets[k].count, 128, replace=False)) for k in chosen}
+    index = np.concatenate([starts[k] + picks[k] for k in picks])
+    bounds = [64, 256, 1024, 2160]
+    ws = api.Workspace()
+    g, prev = {}, 0
+    for b in bounds:
+        api.fte_advance_batched(pool, bg, w.params, w.sets, tally, prev, b, ws)
+        prev = b
+        st = pool.state()
+        g[b] = {key: v[index] for key, v in st.items()}
+    torch.cuda.synchronize()
+    del pool, tally, ws, bg
+    torch.cuda.empty_cache()
+    obg = O.grid_background(w.grid, f)
+    total, pos = 0, 0
+    for k, ids in picks.items():
+        s = w.sets[k]
+        prm = dataclasses.replace(w.params, lambda_par=s.lambda_par, q=s.q, H=s.H, eps=s.eps, seed=s.seed,
+                                  set_id=s.set_id)
+        P, _ = O.inject(obg, s.inject, ids.astype(np.uint32))
+        prev = 0
+        for b in bounds:
+            O.advance(obg, prm, P, prev, b)
+            prev = b
+            gb = {key: v[pos:pos + len(ids)] for key, v in g[b].items()}
+            ok, e = trajectory_errors(gb, P, b, sel=P["status"] != 5, expanding=True)
+            total += int(ok.sum())
+            if ok.any():
+                for key in ("pos", "mu", "p", "w"):
+                    assert e[key].max() <= 1e-4, (k, b, key, float(e[key].max()))
+                assert e["status"].sum() == 0, (k, b, "status")
+        pos += len(ids)
+    print(f"ensemble: {total} (particle, boundary) pairs compared")
+    assert total >= 1000
+
+
+def test_adjoint_full_grid_and_population(cir_full):
+    """The adjoint on the full CIR grid with 1e6 E^-3 protons and the benchmark's launch
+    configuration (checkpoints every 256 steps, reordering every 64), over one 256-step
+    segment with the observable centred in it: on a seeded sample of 512 particles, J_i
+    equals the oracle's and the per-particle gradients equal central differences of the
+    FP64 oracle (same noise) on paths without a divergence event or a 100-fold
+    amplification of the pitch-angle map."""
+    import torch
+    from paper_2404_12164_gb300 import api
+    w, f = cir_full
+    inj = dataclasses.replace(w.inject, energy="powerlaw", e1=0.05, e2=5.0, gamma=3.0)
+    prm = dataclasses.replace(w.params, sort_every=64)
+    obs = SmoothObserver(r_o=1.5, sigma_r=0.2, e_c=0.1, sigma_lnE=0.7, t_c=1280.0, sigma_t=1000.0)
+    n, steps = w.n_particles, 256
+    bg = api.Background(w.grid)
+    api.fte_load_background(bg, f)
+    pool = api.Particles(n)
+    tally = api.Tally([])
+    api.fte_tally_reset(tally)
+    api.fte_inject(pool, bg, inj, n, tally, id_base=0, check_failed=False)
+    adj = api.Adjoint(bg, prm, obs, 0, steps, 256)
+    J = adj.forward(pool)
+    _, pp = adj.reverse(pool, inj, per_particle=True)
+    torch.cuda.synchronize()
+    pp = pp.cpu().numpy()
+    assert float(J) == pytest.approx(pp[:, 0].astype(np.float64).sum(), rel=1e-5)
+    del pool, tally, adj, bg
+    torch.cuda.empty_cache()
+
+    rng = np.random.default_rng(20240421)
+    sample = np.sort(rng.choice(n, 512, replace=False))
+    obg = O.grid_background(w.grid, f)
+
+    def oracle_J(p):
+        P, _ = O.inject(obg, inj, sample.astype(np.uint32))
+        return O.observe(obg, p, P, 0, steps, obs), P
+    Jo, Po = oracle_J(prm)
+    clean = (Po["n_div"] < 0) & (Po["n_sens"] < 0) & (Po["status"] != 5)
+    assert clean.sum() >= 100
+    g = pp[sample]
+    scale = np.abs(Jo).max()
+    assert np.all(np.abs(g[clean, 0] - Jo[clean]) <= 1e-4 * np.abs(Jo[clean]) + 1e-6 * scale)
+    for col, name in ((1, "lambda_par"), (2, "q"), (3, "H")):
+        v0 = getattr(prm, name)
+        h = 1e-6 * v0
+        Jp, _ = oracle_J(dataclasses.replace(prm, **{name: v0 + h}))
+        Jm, _ = oracle_J(dataclasses.replace(prm, **{name: v0 - h}))
+        fd = (Jp - Jm) / (2 * h)
+        gs = np.abs(fd[clean]).max()
+        err = np.abs(g[clean, col] - fd[clean]) / (np.abs(fd[clean]) + 1e-3 * gs)
+        assert np.median(err) < 1e-3, name
+        assert np.percentile(err, 95) < 1e-2, name
