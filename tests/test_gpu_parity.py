@@ -320,3 +320,34 @@ def test_tally_layouts_agree(cir_small):
         Sg, Ss = g["tallies"][o]["S"], s["tallies"][o]["S"]
         assert np.allclose(Sg, Ss, rtol=1e-5, atol=1e-12 * max(Sg.max(), 1e-30))
     assert np.array_equal(g["ledger_n"], s["ledger_n"])
+
+
+def test_maximum_observer_count(parker):
+    """A tally with the maximum number of observers (8) of all four kinds: every
+    observer's occupancy agrees with the oracle's within 3 sigma, and a ninth observer
+    is refused."""
+    from paper_2404_12164_gb300 import api
+    w, f = parker
+    from paper_2404_12164_gb300 import _abi as A
+    assert A.FTE_MAX_OBS == 8
+    obs = [Observer(kind="shell", r=r, dr=0.03, e_lo=0.01, e_hi=1.0, ne=8, t_lo=0.0, t_hi=20000.0, nt=10)
+           for r in (0.2, 0.35, 0.5, 0.8)]
+    obs += [Observer(kind="box", r=0.3, dr=0.05, th=math.pi / 2, dth=0.3, ph=0.3, dph=0.6,
+                     e_lo=0.01, e_hi=1.0, ne=8, t_lo=0.0, t_hi=20000.0, nt=10),
+            Observer(kind="box", r=0.6, dr=0.1, th=math.pi / 2, dth=0.3, ph=6.0, dph=0.6,
+                     e_lo=0.01, e_hi=1.0, ne=8, t_lo=0.0, t_hi=20000.0, nt=10),
+            Observer(kind="slab", r=0.3, dr=0.05, e_lo=0.01, e_hi=1.0, ne=8, t_lo=0.0, t_hi=20000.0, nt=10),
+            Observer(kind="ring", r=0.4, dr=0.05, th=math.pi / 2, dth=0.2, e_lo=0.01, e_hi=1.0, ne=8,
+                     t_lo=0.0, t_hi=20000.0, nt=12)]
+    assert len(obs) == A.FTE_MAX_OBS
+    g = gpu_run(w, f, 2000, observers=obs)
+    o = oracle_run(w, f, 2000, observers=obs)
+    busy = 0
+    for k in range(len(obs)):
+        tg, to = g["tallies"][k], o["tallies"][k]
+        sig = np.sqrt(tg["S2"] + to["S2"])
+        assert np.all(np.abs(tg["S"] - to["S"]) <= 3 * sig + 1e-9 * max(to["S"].max(), 1e-30)), k
+        busy += int(to["C"].sum() > 100)
+    assert busy >= 6
+    with pytest.raises(ValueError):
+        api.Tally(obs + [obs[0]])
