@@ -355,10 +355,15 @@ def run_gpu(args):
     # kernels and the step table, then per launch chunk the step kernel, (with the
     # shared-memory tally) the partial-histogram reduction and (with reordering) the
     # five sort kernels
+    # a pool of at least one wave of threads (at most 3 blocks of 256 per SM) is advanced as
+    # two halves, each with its own reordering and launches (global tally, reordering on)
+    wave = torch.cuda.get_device_properties(local).multi_processor_count * 3 * 256
+    halves = 2 if (w.params.sort_every > 0 and w.params.tally_layout == "global" and n_part >= wave) else 1
+
     def kernels_per_call(s):
         chunk = min(w.params.sort_every, CHUNK) if w.params.sort_every > 0 else CHUNK
         per_chunk = 1 + (1 if w.params.tally_layout == "shared" else 0) + (5 if w.params.sort_every > 0 else 0)
-        return 3 + math.ceil(s / chunk) * per_chunk
+        return 3 + math.ceil(s / chunk) * per_chunk * halves
     launches_per_step = 1 + sum(kernels_per_call(min(CHUNK, n_steps - c)) for c in range(0, n_steps, CHUNK))
     result = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,

@@ -292,7 +292,12 @@ fte_status fte_inject(fte_particles* P, const fte_background* bg, const fte_inje
    t and absorbing particles that leave [r_min, r_max] x [th_min, th_max] (ledger
    slots 1-3).  ws (DEVICE, ws_bytes >= fte_workspace_bytes(device, &bg->grid, t,
    P->count, n_end - n_start)) is scratch; its contents on return are unspecified.
-   Asynchronous on `stream`. */
+   Asynchronous on `stream`.  With the global tally layout, reordering on and at
+   least one wave of threads' worth of particles, the two halves of P are
+   advanced concurrently, one on `stream` and one on a stream the call creates,
+   forks from `stream` and joins back to it before returning (so all work is
+   ordered after earlier and before later work on `stream`); under stream capture
+   the call keeps to `stream`. */
 fte_status fte_advance(fte_particles* P, const fte_background* bg, const fte_params* prm,
                        const fte_tally_buf* t, int64_t n_start, int64_t n_end, void* ws,
                        size_t ws_bytes, void* stream);

@@ -230,6 +230,29 @@ size_t single_smem(int mode, size_t nbins)
     return mode == kModeSingle ? 3 * sizeof(float) * (nbins ? nbins : 1) : 0;
 }
 
+// Reordering scratch of fte_advance: one sort of the whole pool, or, when the pool is
+// advanced as two halves on two streams, one sort per half and a second fetch counter.
+size_t advance_sort_bytes(const GridK& g, unsigned long long n)
+{
+    const unsigned long long h = n / 2;
+    const size_t one = sort_scratch_bytes(g, n);
+    const size_t two = sort_scratch_bytes(g, h) + sort_scratch_bytes(g, n - h) + 256;
+    return one > two ? one : two;
+}
+
+// A second stream and the events that fork it from and join it back to the
+// caller's stream; released when the call returns (the device finishes the work).
+struct SideStream {
+    cudaStream_t s = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+    ~SideStream()
+    {
+        if (fork) cudaEventDestroy(fork);
+        if (join) cudaEventDestroy(join);
+        if (s) cudaStreamDestroy(s);
+    }
+};
+
 fte_status layout(int device, int kperp, int dtype, int pair, int amr, int mode, size_t nbins, long long n_steps,
                   size_t sort_bytes, WsLayout* L)
 {
@@ -388,7 +411,7 @@ size_t fte_workspace_bytes(int device, const fte_grid* g, const fte_tally_buf* t
     fte_background tmp;
     memset(&tmp, 0, sizeof(tmp));
     tmp.grid = *g;
-    const size_t sort_bytes = sort_scratch_bytes(make_gridk(&tmp), n_particles);
+    const size_t sort_bytes = advance_sort_bytes(make_gridk(&tmp), n_particles);
     size_t best = 0;
     for (int dtype = FTE_F32; dtype <= FTE_F16; ++dtype)
         for (int kperp = 0; kperp < 2; ++kperp)
@@ -499,7 +522,7 @@ fte_status fte_advance(fte_particles* P, const fte_background* bg, const fte_par
     const int sorting = prm->sort_every > 0;
     WsLayout L;
     s = layout(device, kperp, bg->grid.dtype, gk.pair, gk.amr > 0, mode, nb, nsteps,
-               sorting ? sort_scratch_bytes(gk, P->count) : 0,
+               sorting ? advance_sort_bytes(gk, P->count) : 0,
                &L);
     if (s != FTE_OK) return s;
     if (ws_bytes < L.total) return fail(FTE_ENOMEM, "workspace has %zu bytes, needs %zu", ws_bytes, L.total);
@@ -568,6 +591,56 @@ fte_status fte_advance(fte_particles* P, const fte_background* bg, const fte_par
     int per_sm = 0;
     FTE_CUDA(advance_occupancy(kperp, bg->grid.dtype, mode, kThreads, bg->grid.layout == FTE_LAYOUT_PAIR, gk.amr > 0,
                                smem, &per_sm), "occupancy");
+
+    // Two halves on two streams: while the last particles of one half's launch run, the
+    // other half's reordering and launch fill the idle SMs (the step kernel launches one
+    // wave of persistent blocks and its end waits for its slowest thread).  Only with the
+    // global tally (no per-block partials), a pool of at least one wave, and outside
+    // stream capture; each particle's result does not depend on it.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    FTE_CUDA(cudaStreamIsCapturing(st, &cap), "capture query");
+    if (sorting && mode == kModeSingleGlobal && P->count >= lanes && cap == cudaStreamCaptureStatusNone) {
+        SideStream side;
+        FTE_CUDA(cudaStreamCreateWithFlags(&side.s, cudaStreamNonBlocking), "stream create");
+        FTE_CUDA(cudaEventCreateWithFlags(&side.fork, cudaEventDisableTiming), "event create");
+        FTE_CUDA(cudaEventCreateWithFlags(&side.join, cudaEventDisableTiming), "event create");
+        AdvanceArgs ah[2] = {a, a};
+        SortArgs sh[2];
+        cudaStream_t hs[2] = {st, side.s};
+        const unsigned long long half = P->count / 2;
+        char* p = w + L.off_sort;
+        for (int k = 0; k < 2; ++k) {
+            const unsigned long long base = k ? half : 0, cnt = k ? P->count - half : half;
+            AdvanceArgs& ak = ah[k];
+            ak.x = P->x + base; ak.y = P->y + base; ak.z = P->z + base; ak.mu = P->mu + base;
+            ak.p = P->p + base; ak.w = P->w + base; ak.id = P->id + base; ak.status = P->status + base;
+            ak.n_particles = cnt;
+            memset(&sh[k], 0, sizeof(SortArgs));
+            sort_carve(gk, cnt, p, &sh[k]);
+            p += sort_scratch_bytes(gk, cnt);
+            sh[k].g = gk;
+            sh[k].x = ak.x; sh[k].y = ak.y; sh[k].z = ak.z; sh[k].mu = ak.mu; sh[k].status = ak.status;
+            sh[k].n = cnt;
+            ak.order = sh[k].order;
+            ak.n_order = sh[k].hist + sh[k].nb;
+        }
+        ah[1].fetch = reinterpret_cast<unsigned long long*>(p);
+        FTE_CUDA(cudaEventRecord(side.fork, st), "fork");
+        FTE_CUDA(cudaStreamWaitEvent(side.s, side.fork, 0), "fork");
+        for (long long c0 = n_start; c0 < n_end; c0 += chunk) {
+            for (int k = 0; k < 2; ++k) {
+                ah[k].n_start = c0;
+                ah[k].n_end = (c0 + chunk < n_end) ? c0 + chunk : n_end;
+                FTE_CUDA(launch_sort(sh[k], hs[k]), "sort launch");
+                FTE_CUDA(cudaMemsetAsync(ah[k].fetch, 0, sizeof(unsigned long long), hs[k]), "fetch reset");
+                FTE_CUDA(launch_advance(ah[k], g_no_batch, kperp, mode, kThreads, blocks, smem, hs[k]),
+                         "step kernel launch");
+            }
+        }
+        FTE_CUDA(cudaEventRecord(side.join, side.s), "join");
+        FTE_CUDA(cudaStreamWaitEvent(st, side.join, 0), "join");
+        return FTE_OK;
+    }
 
     for (long long c0 = n_start; c0 < n_end; c0 += chunk) {
         a.n_start = c0;
