@@ -994,7 +994,7 @@ fte_status ens_run(fte_particles* P, const fte_background* bg, const fte_params*
     const int sorting = prm->sort_every > 0;
     EnsLayout L;
     fte_status s = ens_layout(device, kperp, bg->grid.dtype, gk.pair, cfg.mode, cfg.nt, n_sets, nb, nsteps,
-                              sorting ? sort_scratch_bytes(gk, P->count) : 0, &L);
+                              sorting ? advance_sort_bytes(gk, P->count) : 0, &L);
     if (s != FTE_OK) return s;
     if (ws_bytes < L.total) return fail(FTE_ENOMEM, "workspace has %zu bytes, needs %zu", ws_bytes, L.total);
     char* w = (char*)ws;
@@ -1066,6 +1066,59 @@ fte_status ens_run(fte_particles* P, const fte_background* bg, const fte_params*
     if (blocks < 1) blocks = 1;
     const size_t smem = ens_smem(cfg.mode, n_sets, nb);
     const int reduce_bins = (int)shared_bins(n_sets, nb);
+
+    // two halves of the pool on two streams, as in fte_advance (global tally only); each
+    // half's set boundaries are taken relative to its first entry
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    FTE_CUDA(cudaStreamIsCapturing(st, &cap), "capture query");
+    if (sorting && cfg.mode == kModeGlobal && P->count >= lanes && cap == cudaStreamCaptureStatusNone) {
+        SideStream side;
+        FTE_CUDA(cudaStreamCreateWithFlags(&side.s, cudaStreamNonBlocking), "stream create");
+        FTE_CUDA(cudaEventCreateWithFlags(&side.fork, cudaEventDisableTiming), "event create");
+        FTE_CUDA(cudaEventCreateWithFlags(&side.join, cudaEventDisableTiming), "event create");
+        AdvanceArgs ah[2] = {a, a};
+        BatchArgs bh[2] = {b, b};
+        SortArgs sh[2];
+        cudaStream_t hs[2] = {st, side.s};
+        const unsigned long long half = P->count / 2;
+        char* p = w + L.off_sort;
+        for (int k = 0; k < 2; ++k) {
+            const unsigned long long base = k ? half : 0, cnt = k ? P->count - half : half;
+            AdvanceArgs& ak = ah[k];
+            ak.x = P->x + base; ak.y = P->y + base; ak.z = P->z + base; ak.mu = P->mu + base;
+            ak.p = P->p + base; ak.w = P->w + base; ak.id = P->id + base; ak.status = P->status + base;
+            ak.n_particles = cnt;
+            for (int q = 0; q < n_sets; ++q) {
+                const long long e = (long long)b.end[q] - (long long)base;
+                bh[k].end[q] = e < 0 ? 0ULL : ((unsigned long long)e > cnt ? cnt : (unsigned long long)e);
+            }
+            memset(&sh[k], 0, sizeof(SortArgs));
+            sort_carve(gk, cnt, p, &sh[k]);
+            p += sort_scratch_bytes(gk, cnt);
+            sh[k].g = gk;
+            sh[k].x = ak.x; sh[k].y = ak.y; sh[k].z = ak.z; sh[k].mu = ak.mu; sh[k].status = ak.status;
+            sh[k].n = cnt;
+            ak.order = sh[k].order;
+            ak.n_order = sh[k].hist + sh[k].nb;
+        }
+        ah[1].fetch = reinterpret_cast<unsigned long long*>(p);
+        FTE_CUDA(cudaEventRecord(side.fork, st), "fork");
+        FTE_CUDA(cudaStreamWaitEvent(side.s, side.fork, 0), "fork");
+        for (long long c0 = n_start; c0 < n_end; c0 += cfg.steps) {
+            for (int k = 0; k < 2; ++k) {
+                ah[k].n_start = c0;
+                ah[k].n_end = (c0 + cfg.steps < n_end) ? c0 + cfg.steps : n_end;
+                FTE_CUDA(launch_sort(sh[k], hs[k]), "sort launch");
+                FTE_CUDA(cudaMemsetAsync(ah[k].fetch, 0, sizeof(unsigned long long), hs[k]), "fetch reset");
+                FTE_CUDA(launch_advance(ah[k], bh[k], kperp, cfg.mode, cfg.nt, blocks, smem, hs[k]),
+                         "step kernel launch");
+            }
+        }
+        FTE_CUDA(cudaEventRecord(side.join, side.s), "join");
+        FTE_CUDA(cudaStreamWaitEvent(st, side.join, 0), "join");
+        return FTE_OK;
+    }
+
     for (long long c0 = n_start; c0 < n_end; c0 += cfg.steps) {
         a.n_start = c0;
         a.n_end = (c0 + cfg.steps < n_end) ? c0 + cfg.steps : n_end;
@@ -1137,7 +1190,7 @@ size_t fte_workspace_bytes_batched(int device, const fte_grid* g, const fte_tall
     fte_background tmp;
     memset(&tmp, 0, sizeof(tmp));
     tmp.grid = *g;
-    const size_t sort_bytes = sort_scratch_bytes(make_gridk(&tmp), n_particles);
+    const size_t sort_bytes = advance_sort_bytes(make_gridk(&tmp), n_particles);
     size_t best = 0;
     for (int dtype = FTE_F32; dtype <= FTE_F16; ++dtype)
         for (int kperp = 0; kperp < 2; ++kperp)
