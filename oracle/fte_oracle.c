@@ -910,9 +910,14 @@ static void tally_state(tally_t* T, double x, double y, double z, double p, doub
     }
 }
 
-/* Advance particle P by one step from step index n.  Returns the new status. */
-static int step_one(const or_background* bg, const or_params* prm, double I,
-                    or_particle* P, int64_t n, tally_t* T, double* terms)
+/* Advance particle P by one step from step index n.  Returns the new status.
+   hold (optional): the pitch-angle cosine after the step is *hold instead of the
+   Euler-Maruyama draw (the score form of the gradient holds it; everything else
+   of the step is unchanged).  ms (optional): receives the mean mu + (mudot +
+   dD/dmu) dt and the width sqrt(2 D dt) of the Gaussian pitch-angle increment. */
+static int step_core(const or_background* bg, const or_params* prm, double I,
+                     or_particle* P, int64_t n, tally_t* T, double* terms,
+                     const double* hold, double* ms)
 {
     const double dt = prm->dt;
     const double t = prm->t0 + (double)n * dt;
@@ -944,7 +949,10 @@ static int step_one(const or_background* bg, const or_params* prm, double I,
     /* Eq. 3 and the Ito pitch-angle step */
     double omm = 1.0 - mu * mu;
     double mudot = 0.5 * omm * (v * divb + mu * divv - 3.0 * mu * bbgv - (2.0 / v) * bdvdt);
-    double mu_new = mu + (mudot + dD) * dt + sqrt(2.0 * D * dt) * zn[0];
+    double m_mean = mu + (mudot + dD) * dt;
+    double sig = sqrt(2.0 * D * dt);
+    if (ms) { ms[0] = m_mean; ms[1] = sig; }
+    double mu_new = hold ? *hold : m_mean + sig * zn[0];
     int ev = 0;
     if (mu_new > 1.0 || mu_new < -1.0) ev = 1;           /* reflection */
     if (mu_new > 1.0) mu_new = 2.0 - mu_new;
@@ -1054,6 +1062,12 @@ static int step_one(const or_background* bg, const or_params* prm, double I,
     return st;
 }
 
+static int step_one(const or_background* bg, const or_params* prm, double I,
+                    or_particle* P, int64_t n, tally_t* T, double* terms)
+{
+    return step_core(bg, prm, I, P, n, T, terms, NULL, NULL);
+}
+
 int or_step_terms(const or_background* bg, const or_params* prm, const or_particle* p,
                   int64_t n, double out[32])
 {
@@ -1159,6 +1173,128 @@ int or_observe(const or_background* bg, const or_params* prm, const or_smooth_ob
         J[i] = acc;
     }
     return 0;
+}
+
+/* Density of the pitch-angle cosine after one step (Sec. 2.1: the Ito step adds a
+   Gaussian increment of mean (mudot + dD/dmu) dt and variance 2 D dt; a draw beyond
+   mu = +-1 is reflected back into [-1, 1]): the unreflected value y ~ N(m, s^2)
+   lands at mu1 from y = mu1, 2 - mu1 or -2 - mu1.  Returns the log of the sum of
+   the three Gaussian densities without the constant -ln(2 pi)/2. */
+double or_mu_logpdf(double mu1, double m, double s)
+{
+    const double y[3] = {mu1, 2.0 - mu1, -2.0 - mu1};
+    double e[3], emax = -INFINITY;
+    for (int j = 0; j < 3; ++j) {
+        const double z = (y[j] - m) / s;
+        e[j] = -0.5 * z * z;
+        if (e[j] > emax) emax = e[j];
+    }
+    double sum = 0.0;
+    for (int j = 0; j < 3; ++j) sum += exp(e[j] - emax);
+    return emax + log(sum) - log(s);
+}
+
+/* Gradient of the smooth observable (or_observe) with respect to the pitch-angle
+   parameters, in the score (likelihood-ratio) form for the steps where the jump of
+   Eq. 5's dD/dmu at mu = 0, or the singular quasi-linear drift, makes the
+   Euler-Maruyama map discontinuous, and pathwise elsewhere.
+   A step n is "gated" when the Gaussian increment's mean m lies within `window`
+   widths s of a value that lands at mu = 0 (m = 0, or m = +-2 through the
+   reflection): min(|m|, ||m| - 2|) < window s.  For a perturbed parameter theta', the path
+   is recomputed with the noise of every other step held and, at every gated step,
+   with the base path's mu_{n+1} held, while the observable's terms after step n are
+   weighted by p(mu_{n+1} | state_n(theta'), theta') / p(mu_{n+1} | state_n, theta).
+   Its expectation equals E[J(theta')] for every theta', so its derivative at theta
+   (central differences, step rel * theta_j) estimates dE[J]/dtheta_j without bias.
+   window = 0: no gated steps (the derivative of the realised path).
+   which: bit j requests parameter j = lambda_par, q, H, eps; G[i * 4 + j].
+   flags[i]: bit 0 a gate decision within 1e-4 (relative) of |m| = window s;
+             bit 1 a step starting within 1e-5 of mu = 0 (where the map jumps);
+             bit 2 a perturbed path ended at another step than the base path.
+   P is advanced in place along the base path, as by or_observe. */
+int or_observe_lr(const or_background* bg, const or_params* prm, const or_smooth_obs* K, double window,
+                  or_particle* P, int64_t n, int64_t n_start, int64_t n_end, int which, double rel,
+                  double* J, double* G, int32_t* flags, int n_threads)
+{
+    if (n_threads < 1) n_threads = 1;
+    if (n_end < n_start) return 1;
+    const int64_t ns = n_end - n_start;
+    const double I = or_norm_integral(prm->dmumu, prm->q, prm->H, prm->eps);
+    int rc = 0;
+#ifdef _OPENMP
+#pragma omp parallel num_threads(n_threads)
+#endif
+    {
+        signed char* gate = (signed char*)malloc((size_t)(ns > 0 ? ns : 1));
+        double* hold = (double*)malloc(sizeof(double) * (size_t)(ns > 0 ? ns : 1));
+        double* lp = (double*)malloc(sizeof(double) * (size_t)(ns > 0 ? ns : 1));
+        if (!gate || !hold || !lp) {
+#ifdef _OPENMP
+#pragma omp atomic write
+#endif
+            rc = 2;
+        }
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 16)
+#endif
+        for (int64_t i = 0; i < n; ++i) {
+            if (!gate || !hold || !lp) continue;
+            const or_particle p0 = P[i];
+            or_particle q = p0;
+            int32_t fl = 0;
+            double acc = 0.0, ms[2];
+            int64_t s_end = n_end;
+            for (int64_t s = n_start; s < n_end && q.status == OR_ALIVE; ++s) {
+                const double t = prm->t0 + (double)s * prm->dt;
+                acc += q.w * prm->dt * smooth_kernel(K, q.x, q.y, q.z, q.p, t);
+                if (fabs(q.mu) < 1e-5) fl |= 2;
+                const int st = step_core(bg, prm, I, &q, s, NULL, NULL, NULL, ms);
+                /* distance of the mean from the nearest unreflected value that lands at mu = 0 */
+                const double am = fabs(ms[0]), d0 = fmin(am, fabs(am - 2.0));
+                const double lim = window * ms[1];
+                const int g = d0 < lim;
+                if (window > 0.0 && fabs(d0 - lim) <= 1e-4 * lim) fl |= 1;
+                gate[s - n_start] = (signed char)g;
+                hold[s - n_start] = q.mu;
+                lp[s - n_start] = g ? or_mu_logpdf(q.mu, ms[0], ms[1]) : 0.0;
+                if (st != OR_ALIVE) { s_end = s + 1; break; }
+            }
+            J[i] = acc;
+            for (int j = 0; j < 4; ++j) {
+                if (!(which & (1 << j))) { G[i * 4 + j] = 0.0; continue; }
+                double psi[2];
+                for (int sg = 0; sg < 2; ++sg) {
+                    or_params pp = *prm;
+                    double* th = j == 0 ? &pp.lambda_par : j == 1 ? &pp.q : j == 2 ? &pp.H : &pp.eps;
+                    const double d = rel * *th;
+                    *th += sg ? -d : d;
+                    const double Ip = or_norm_integral(pp.dmumu, pp.q, pp.H, pp.eps);
+                    or_particle r = p0;
+                    double sum = 0.0, logw = 0.0;
+                    int64_t e = n_end;
+                    for (int64_t s = n_start; s < s_end && r.status == OR_ALIVE; ++s) {
+                        const double t = pp.t0 + (double)s * pp.dt;
+                        sum += r.w * pp.dt * smooth_kernel(K, r.x, r.y, r.z, r.p, t) * exp(logw);
+                        const int g = gate[s - n_start];
+                        const int st = step_core(bg, &pp, Ip, &r, s, NULL, NULL, g ? &hold[s - n_start] : NULL, ms);
+                        if (g) logw += or_mu_logpdf(hold[s - n_start], ms[0], ms[1]) - lp[s - n_start];
+                        if (st != OR_ALIVE) { e = s + 1; break; }
+                    }
+                    /* the perturbed path must end where the base path ends */
+                    if ((r.status != OR_ALIVE) != (q.status != OR_ALIVE) || e != s_end) fl |= 4;
+                    psi[sg] = sum;
+                }
+                const double th0 = j == 0 ? prm->lambda_par : j == 1 ? prm->q : j == 2 ? prm->H : prm->eps;
+                G[i * 4 + j] = (psi[0] - psi[1]) / (2.0 * rel * th0);
+            }
+            flags[i] = fl;
+            P[i] = q;
+        }
+        free(gate);
+        free(hold);
+        free(lp);
+    }
+    return rc;
 }
 
 /* Intensity from the occupancy sum (Eq. 7 with j = p^2 f): S / dt_bin is the

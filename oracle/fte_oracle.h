@@ -113,6 +113,17 @@ typedef struct {
 } or_smooth_obs;
 int or_observe(const or_background* bg, const or_params* prm, const or_smooth_obs* K, or_particle* P,
                int64_t n, int64_t n_start, int64_t n_end, double* J, int n_threads);
+/* log density (without -ln(2 pi)/2) of the pitch-angle cosine mu1 after a step whose
+   Gaussian increment has mean m and width s, reflected at mu = +-1 (images 2 - mu1,
+   -2 - mu1) */
+double or_mu_logpdf(double mu1, double m, double s);
+/* hybrid pathwise / score gradient of or_observe's J with respect to the pitch-angle
+   parameters (bit j of `which`: lambda_par, q, H, eps; G[i*4+j]); steps whose Gaussian
+   increment has its mean within `window` widths of mu = 0 enter by the likelihood
+   ratio of the held mu_{n+1}; see fte_oracle.c for flags */
+int or_observe_lr(const or_background* bg, const or_params* prm, const or_smooth_obs* K, double window,
+                  or_particle* P, int64_t n, int64_t n_start, int64_t n_end, int which, double rel,
+                  double* J, double* G, int32_t* flags, int n_threads);
 /* value of padded cell (li, lj, lk) of an AMR leaf (interior cells: the stored record;
    ghost cells: the neighbour value the method defines), fields 0..17 */
 void or_amr_cell(const or_background* bg, int snap, int leaf, int li, int lj, int lk, double out[18]);

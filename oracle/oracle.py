@@ -94,6 +94,11 @@ def lib():
         L.or_intensity.argtypes = [P(ObserverC), C.c_void_p, C.c_void_p]
         L.or_observe.argtypes = [P(Background), P(ParamsC), P(SmoothObsC), C.c_void_p, C.c_int64,
                                  C.c_int64, C.c_int64, C.c_void_p, C.c_int]
+        L.or_mu_logpdf.argtypes = [C.c_double, C.c_double, C.c_double]
+        L.or_mu_logpdf.restype = C.c_double
+        L.or_observe_lr.argtypes = [P(Background), P(ParamsC), P(SmoothObsC), C.c_double, C.c_void_p,
+                                    C.c_int64, C.c_int64, C.c_int64, C.c_int, C.c_double, C.c_void_p,
+                                    C.c_void_p, C.c_void_p, C.c_int]
         L.or_max_threads.restype = C.c_int
         L.or_amr_cell.argtypes = [P(Background), C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                                   P(C.c_double)]
@@ -313,6 +318,40 @@ def observe(bg, params, particles, n_start, n_end, obs, threads=None):
     if rc != 0:
         raise RuntimeError(f"or_observe failed ({rc})")
     return J
+
+
+LR_PARAMS = ("lambda_par", "q", "H", "eps")
+
+
+def mu_logpdf(mu1, m, s):
+    """Log density (without -ln(2 pi)/2) of the pitch-angle cosine after a step whose
+    Gaussian increment has mean m and width s, reflected at +-1."""
+    return lib().or_mu_logpdf(float(mu1), float(m), float(s))
+
+
+def observe_lr(bg, params, particles, n_start, n_end, obs, window, names=("lambda_par",), rel=1e-6,
+               threads=None):
+    """or_observe plus each particle's hybrid pathwise / score gradient of J_i with respect
+    to `names` (a subset of LR_PARAMS): steps whose Gaussian pitch-angle increment has its
+    mean within `window` widths of mu = 0 enter by the likelihood ratio of the held
+    mu_{n+1}.  Returns (J [n], {name: gradient [n]}, flags [n]); particles advance in place."""
+    assert particles.dtype == PARTICLE and particles.flags.c_contiguous
+    L = lib()
+    n = len(particles)
+    J = np.zeros(n)
+    G = np.zeros((n, 4))
+    fl = np.zeros(n, dtype=np.int32)
+    which = 0
+    for nm in names:
+        which |= 1 << LR_PARAMS.index(nm)
+    k = SmoothObsC(obs.r_o, obs.sigma_r, obs.e_c, obs.sigma_lnE, obs.t_c, obs.sigma_t)
+    nthreads = threads or int(os.environ.get("FTE_ORACLE_THREADS", "0")) or L.or_max_threads()
+    rc = L.or_observe_lr(C.byref(bg.c), C.byref(params_c(params)), C.byref(k), float(window),
+                         particles.ctypes.data, n, n_start, n_end, which, float(rel), J.ctypes.data,
+                         G.ctypes.data, fl.ctypes.data, nthreads)
+    if rc != 0:
+        raise RuntimeError(f"or_observe_lr failed ({rc})")
+    return J, {nm: G[:, LR_PARAMS.index(nm)].copy() for nm in names}, fl
 
 
 def convolve(G, dt_bin, src=None):
