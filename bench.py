@@ -218,21 +218,13 @@ def run_gpu(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    def one_step(timed_launches=None):
-        """inject + advance (chunked launches) + tally reduction over ranks."""
+    def one_step():
+        """inject + advance (chunked calls) + tally reduction over ranks."""
         pool.c.count = 0
         api.fte_tally_reset(tally)
         api.fte_inject(pool, bg, w.inject, n_part, tally, id_base=id_base, check_failed=False)
         for c in range(0, n_steps, CHUNK):
-            e = min(c + CHUNK, n_steps)
-            if timed_launches is not None:
-                ev0 = torch.cuda.Event(enable_timing=True)
-                ev1 = torch.cuda.Event(enable_timing=True)
-                ev0.record(stream)
-            api.fte_advance(pool, bg, w.params, tally, c, e, wsp)
-            if timed_launches is not None:
-                ev1.record(stream)
-                timed_launches.append((ev0, ev1))
+            api.fte_advance(pool, bg, w.params, tally, c, min(c + CHUNK, n_steps), wsp)
         pdist.reduce_tally(tally)
 
     def upload():
@@ -246,44 +238,50 @@ def run_gpu(args):
     torch.cuda.synchronize()
 
     def measure(background, steps, warmup, clocks=None):
-        """W warm-up + K timed steps on `background`; returns (ms, kernel ms, launches, steps)."""
+        """W warm-up + K timed steps on `background`; returns (ms, step-kernel launch intervals
+        of this rank, alive particle-steps of this rank).  The library records a CUDA event pair
+        around every step-kernel launch on the stream of that launch (fte_probe_step_timing)."""
         nonlocal bg
         saved, bg = bg, background
         for _ in range(warmup):
             one_step()
-        launches = []
         done = 0
         barrier()
+        api.fte_probe_step_timing(1 << 16)
         if clocks:
             clocks.start()
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
         t0.record(stream)
         for _ in range(steps):
-            one_step(launches)
+            one_step()
             ln = tally.ledger_n.cpu().numpy()
             done += int(ln[6]) // ws
         t1.record(stream)
         barrier()
         if clocks:
             clocks.result = clocks.stop()
+        iv = api.fte_probe_step_intervals(1 << 16)
+        api.fte_probe_step_timing(0)
         bg = saved
         ms = t0.elapsed_time(t1)
-        k_ms = sum(a_.elapsed_time(b_) for a_, b_ in launches)
-        ms, k_ms = pdist.max_over_ranks([ms, k_ms], device="cuda")
-        return ms, k_ms, len(launches), done
+        (ms,) = pdist.max_over_ranks([ms], device="cuda")
+        return ms, iv, done
 
     clocks = Clocks(local)
-    ms, k_ms, n_launch, steps_total = measure(bg, args.steps, args.warmup, clocks)
+    ms, intervals, steps_total = measure(bg, args.steps, args.warmup, clocks)
     cl = clocks.result
     total_steps = steps_total * ws
     value = total_steps / (ms / 1e3)
     S_f32 = api.fte_tally(tally, 0, A.FTE_TALLY_S)
 
-    # tally error: relative standard error of the observer's total occupancy
+    # tally error: relative standard error of the observer's total occupancy, by batch means
+    # over the 32 particle-id classes; the per-step figure sqrt(sum S2) / sum S treats a
+    # particle's consecutive steps inside the observer as independent and understates it
     S = api.fte_tally(tally, 0, A.FTE_TALLY_S)
     S2 = api.fte_tally(tally, 0, A.FTE_TALLY_S2)
-    rel_err = math.sqrt(S2.sum()) / S.sum() if S.sum() > 0 else None
+    _, rel_err = tally.batch_means(0)
+    rel_err_per_step = math.sqrt(S2.sum()) / S.sum() if S.sum() > 0 else None
 
     # end-to-end arm: host buffers through the C ABI ---------------------------
     # The snapshots stream from page-locked host memory into a ring of one slot per
@@ -324,22 +322,23 @@ def run_gpu(args):
     del sstream, ring_bg
     torch.cuda.empty_cache()
 
+    # ceilings of the memory levels that serve the gathers (measured in this run)
+    l1 = l1_probe()
+    l2_gbs = l2_probe()
     # reduced-precision storage forms (same workload, background quantized on the device)
-    peak, peak_kind = _peaks()
     forms = {}
     if not args.no_forms:
         for dt in ("bf16", "f16"):
             bh = api.Background(w.grid, dtype=dt, layout=args.layout)
             api.fte_quantize_background(bh, src)
-            f_ms, f_kms, _, f_steps = measure(bh, args.steps, max(1, args.warmup // 3))
+            f_ms, f_iv, f_steps = measure(bh, args.steps, max(1, args.warmup // 3))
             Sh = api.fte_tally(tally, 0, A.FTE_TALLY_S)
-            f_alg = f_steps * (ALG_BYTES // 2) / (f_kms / 1e3) / 1e9
+            _, f_rel = tally.batch_means(0)
             forms[dt] = {"value": f_steps * ws / (f_ms / 1e3), "unit": UNIT,
                          "speedup_vs_f32": (f_steps / f_ms) / (steps_total / ms),
-                         "roofline": {"achieved": f_alg, "peak": peak, "unit": "GB/s",
-                                      "frac": f_alg / peak,
-                                      "alg_bytes_per_particle_step": ALG_BYTES // 2},
+                         "roofline": roofline_record(f_iv, f_steps, ALG_BYTES // 2, l1, None, None),
                          "tally_total_rel_diff_vs_f32": float(abs(Sh.sum() - S_f32.sum()) / S_f32.sum()),
+                         "tally_rel_err": f_rel,
                          "background_bytes": int(bh.nbytes)}
             del bh
             torch.cuda.empty_cache()
@@ -350,8 +349,7 @@ def run_gpu(args):
         adjoint["note"] = ("first %d steps of the workload, E^-3 injection over 50 keV-5 MeV; bench.py --case "
                            "adjoint runs the full 4 days" % args.adj_slice)
 
-    achieved = total_steps / ws * ALG_BYTES / (k_ms / 1e3) / 1e9
-    l2_gbs = l2_probe()
+    roofline = roofline_record(intervals, total_steps // ws, ALG_BYTES, l1, l2_gbs, measured_traffic(args.layout))
     # our kernels per timed step: inject, and per advance call the two normalisation
     # kernels and the step table, then per launch chunk the step kernel, (with the
     # shared-memory tally) the partial-histogram reduction and (with reordering) the
@@ -376,23 +374,28 @@ def run_gpu(args):
                                "1 au box tally 16x144",
                    "particles_per_gpu": n_part, "steps_per_particle": n_steps, "record_layout": args.layout,
                    "background_bytes": int(bg.nbytes), "l2": "inputs larger than L2 (background %.1f GB)" % (bg.nbytes / 1e9),
-                   "tally_rel_err": rel_err},
+                   "tally_rel_err": rel_err,
+                   "tally_rel_err_method": "relative standard error of the 1 au observer's total occupancy from "
+                                           "32 batch means over particle-id classes (id mod 32)",
+                   "tally_rel_err_per_step": rel_err_per_step,
+                   "tally_rel_err_per_step_note": "sqrt(sum S2)/sum S counts every tallied step as an "
+                                                  "independent event; a particle's consecutive steps in the "
+                                                  "observer are correlated, so it understates the error"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d_bytes),
                 "d2h_bytes_per_step": int(out_host.nbytes + 2 * 8 * A.FTE_LEDGER),
                 "path": "fte_advance_streamed, %d-slot ring, each snapshot copied once per step" % w.grid.n_snap},
         "gpu_launches": launches_per_step * args.steps,
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": measured_traffic(args.layout),
-                     "traffic_source": "profiles/advance_kernel_traffic.json (ncu, same kernel sources)",
-                     "alg_bytes_per_launch": total_steps / ws * ALG_BYTES / n_launch,
-                     "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)",
-                     "kernel": "advance_kernel", "alg_bytes_per_particle_step": ALG_BYTES,
-                     "kernel_ms_total": k_ms, "kernel_launches": n_launch,
-                     "l2_random_sector_gbs": l2_gbs, "frac_of_l2": achieved / l2_gbs},
+        "roofline": roofline,
         "clocks": cl,
         "forms": forms,
         "adjoint": adjoint,
     }
+    if ws == 1 and not args.no_amr:
+        # the block-AMR workload (the largest single-GPU configuration), one GPU only
+        aclk = Clocks(local)
+        result["amr"] = amr_measure(api, args, l1=l1, forms=False, cpu=rank == 0 and not args.no_cpu_baseline,
+                                    clocks=aclk)
+        result["amr"]["clocks"] = aclk.result
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(w, fields, budget_s=args.cpu_budget)
     if rank == 0:
@@ -475,16 +478,16 @@ def run_profile_case(args):
         w = configs.cir_amr_1e7(n_particles=1 << 18, n_steps=256 * args.launches, spec=spec)
         w.params.sort_every = args.sort_every
         bg, leaves = build_amr_background(w, api)
-        if args.layout != "cell":
+        if args.layout != "cell" or args.dtype != "f32":
             cell = bg
-            bg = api.AmrBackground(w.grid, leaves, share=cell, layout=args.layout)
+            bg = api.AmrBackground(w.grid, leaves, dtype=args.dtype, share=cell, layout=args.layout)
             api.fte_quantize_background(bg, cell)
             torch.cuda.synchronize()
             del cell
     else:
         w = configs.scaled(configs.cir_uniform_1e6(), n_snap=2, n_particles=1 << 18)
         w.params.sort_every = args.sort_every
-        bg = device_background(api, w, configs.build_background(w), args.layout)
+        bg = device_background(api, w, configs.build_background(w), args.layout, args.dtype)
     pool = api.Particles(w.n_particles)
     tally = api.Tally(w.observers)
     api.fte_tally_reset(tally)
@@ -494,8 +497,9 @@ def run_profile_case(args):
         api.fte_advance(pool, bg, w.params, tally, 256 * c, 256 * (c + 1), wsp)
     lw, ln = api.fte_ledger(tally)
     torch.cuda.synchronize()
-    print(json.dumps({"case": "profile", "launches": args.launches, "particle_steps": int(ln[6]),
-                      "alg_bytes": int(ln[6]) * ALG_BYTES}))
+    per_step = ALG_BYTES if args.dtype == "f32" else ALG_BYTES // 2
+    print(json.dumps({"case": "profile", "grid": args.grid, "dtype": args.dtype, "launches": args.launches,
+                      "particle_steps": int(ln[6]), "alg_bytes": int(ln[6]) * per_step}))
 
 
 def build_amr_background(w, api, device="cuda"):
@@ -516,14 +520,14 @@ def build_amr_background(w, api, device="cuda"):
     return bg, leaves
 
 
-def run_amr_case(args):
-    """Block-AMR workload (cir_amr_1e7): FP32, BF16 and FP16 storage, one line of JSON."""
+def amr_measure(api, args, l1=None, forms=True, cpu=True, clocks=None):
+    """Block-AMR workload (cir_amr_1e7): FP32 rate with its roofline and batch-means tally
+    errors at the 4 observers, optionally the BF16/FP16 forms and the oracle on a bounded
+    sample; returns a dict."""
     import torch
-    from paper_2404_12164_gb300 import api, build
     from paper_2404_12164_gb300 import _abi as A
-    build.build()
-    torch.cuda.set_device(0)
     w = configs.cir_amr_1e7(n_particles=args.amr_particles, n_steps=args.amr_steps)
+    w.params.sort_every = args.sort_every
     t_gen = time.perf_counter()
     bg, leaves = build_amr_background(w, api)
     t_gen = time.perf_counter() - t_gen
@@ -534,93 +538,129 @@ def run_amr_case(args):
     wsp = api.Workspace()
     wsp.ensure(api.fte_workspace_bytes(bg, tally, n_part, CHUNK))
     alg = ALG_BYTES + 4                  # + the 4-byte finest-level table entry
+    if l1 is None:
+        l1 = l1_probe()
 
-    def one_step(b, launches=None):
+    def one_step(b):
         pool.c.count = 0
         api.fte_tally_reset(tally)
         api.fte_inject(pool, b, w.inject, n_part, tally, check_failed=False)
         for c in range(0, n_steps, CHUNK):
-            e = min(c + CHUNK, n_steps)
-            if launches is not None:
-                ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-                ev[0].record(stream)
-            api.fte_advance(pool, b, w.params, tally, c, e, wsp)
-            if launches is not None:
-                ev[1].record(stream)
-                launches.append(ev)
+            api.fte_advance(pool, b, w.params, tally, c, min(c + CHUNK, n_steps), wsp)
 
-    def measure(b, steps, warmup, clocks=None):
+    def measure(b, steps, warmup, clk=None):
         for _ in range(warmup):
             one_step(b)
         torch.cuda.synchronize()
-        if clocks:
-            clocks.start()
-        launches, done = [], 0
+        api.fte_probe_step_timing(1 << 16)
+        if clk:
+            clk.start()
+        done = 0
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
         t0.record(stream)
         for _ in range(steps):
-            one_step(b, launches)
+            one_step(b)
             done += int(tally.ledger_n.cpu().numpy()[6])
         t1.record(stream)
         torch.cuda.synchronize()
-        if clocks:
-            clocks.result = clocks.stop()
+        if clk:
+            clk.result = clk.stop()
+        iv = api.fte_probe_step_intervals(1 << 16)
+        api.fte_probe_step_timing(0)
         ms = t0.elapsed_time(t1)
-        k_ms = sum(a_.elapsed_time(b_) for a_, b_ in launches)
-        S = np.array([api.fte_tally(tally, o, A.FTE_TALLY_S).sum() for o in range(len(w.observers))])
-        S2 = np.array([api.fte_tally(tally, o, A.FTE_TALLY_S2).sum() for o in range(len(w.observers))])
-        return ms, k_ms, done, S, S2
+        errs = [tally.batch_means(o)[1] for o in range(len(w.observers))]
+        S = np.array([tally.S_class[0, o].sum().item() for o in range(len(w.observers))])
+        return ms, iv, done, S, errs
 
-    peak, peak_kind = _peaks()
-    clocks = Clocks(0)
     layout = getattr(args, "layout", "cell")
     bm = bg
     if layout != "cell":
         bm = api.AmrBackground(w.grid, leaves, share=bg, layout=layout)
         api.fte_quantize_background(bm, bg)
-    ms, k_ms, done, S, S2 = measure(bm, args.steps, args.warmup, clocks)
+    ms, iv, done, S, errs = measure(bm, args.steps, args.warmup, clocks)
     if bm is not bg:
         del bm
         torch.cuda.empty_cache()
-    achieved = done * alg / (k_ms / 1e3) / 1e9
-    forms = {}
-    if not args.no_forms:
+    out_forms = {}
+    if forms:
         for dt in ("bf16", "f16"):
             bh = api.AmrBackground(w.grid, leaves, dtype=dt, share=bg, layout=layout)
             api.fte_quantize_background(bh, bg)
-            f_ms, f_kms, f_done, Sh, S2h = measure(bh, args.steps, max(1, args.warmup // 3))
-            f_alg = f_done * (ALG_BYTES // 2 + 4) / (f_kms / 1e3) / 1e9
-            forms[dt] = {"value": f_done / (f_ms / 1e3), "unit": UNIT,
-                         "speedup_vs_f32": (f_done / f_ms) / (done / ms),
-                         "roofline": {"achieved": f_alg, "peak": peak, "unit": "GB/s", "frac": f_alg / peak,
-                                      "alg_bytes_per_particle_step": ALG_BYTES // 2 + 4},
-                         "tally_total_rel_diff_vs_f32": [float(abs(a - b) / b) if b > 0 else None
-                                                         for a, b in zip(Sh, S)],
-                         "background_bytes": int(bh.nbytes)}
+            f_ms, f_iv, f_done, Sh, f_errs = measure(bh, args.steps, max(1, args.warmup // 3))
+            out_forms[dt] = {"value": f_done / (f_ms / 1e3), "unit": UNIT,
+                             "speedup_vs_f32": (f_done / f_ms) / (done / ms),
+                             "roofline": roofline_record(f_iv, f_done, ALG_BYTES // 2 + 4, l1, None, None),
+                             "tally_total_rel_diff_vs_f32": [float(abs(a - b) / b) if b > 0 else None
+                                                             for a, b in zip(Sh, S)],
+                             "tally_rel_err": f_errs,
+                             "background_bytes": int(bh.nbytes)}
             del bh
             torch.cuda.empty_cache()
     lv = np.bincount(leaves[:, 0], minlength=w.grid.levels)
-    print(json.dumps({
-        "case": "amr", "metric": METRIC, "value": done / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
-        "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+    res = {
+        "value": done / (ms / 1e3), "unit": UNIT, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms / args.steps, "dtype": "f32",
         "config": {"workload": "cir_amr_1e7: synthetic CIR on a log-r 3-level block-AMR grid (16^3 blocks, "
                                "base 32x8x24, refined where |div V| > 6e-5/s), 2 hourly snapshots, "
-                               f"{n_part:.0e} protons E^-3 over 50 keV-5 MeV (1-2 au, 90+-2 deg, w=1/r^2), "
+                               f"{n_part:.0e} protons E^-3 over 50 keV-5 MeV injected over one CIR's spiral band "
+                               "(phi + (r - 0.1 au) Omega/U within +-10 deg of its compression boundary) from "
+                               "0.12 to 2 au at 90+-2 deg, w=1/r^2, "
                                f"QLT q=5/3 H=0.05 lambda_par=0.1 au, dt=2 s x {n_steps}, "
-                               "4 observer boxes 16x144",
+                               "4 observer boxes (0.5, 1, 1.5, 1.8 au) 16x144",
                    "leaves": int(len(leaves)), "leaves_per_level": lv.tolist(), "record_layout": layout,
                    "background_bytes": int(bg.nbytes), "generate_s": t_gen,
-                   "tally_rel_err": [float(math.sqrt(b) / a) if a > 0 else None for a, b in zip(S, S2)]},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None,
-                     "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)",
-                     "kernel": "advance_kernel", "alg_bytes_per_particle_step": alg,
-                     "kernel_ms_total": k_ms},
-        "clocks": clocks.result,
-        "forms": forms,
-    }), flush=True)
+                   "l2": "inputs larger than L2 (background %.1f GB)" % (bg.nbytes / 1e9),
+                   "tally_rel_err": errs,
+                   "tally_rel_err_method": "per observer: relative standard error of the total occupancy from "
+                                           "32 batch means over particle-id classes"},
+        "roofline": roofline_record(iv, done, alg, l1, None, None),
+        "forms": out_forms,
+    }
+    if cpu:
+        res["cpu_baseline"] = amr_cpu_baseline(w, bg, leaves, budget_s=args.cpu_budget / 2)
+    del bg
+    torch.cuda.empty_cache()
+    return res
+
+
+def amr_cpu_baseline(w, bg, leaves, budget_s=10.0):
+    """The FP64 oracle on the host cores over a bounded sample of the AMR workload: the first
+    1e4 particles for as many of the workload's steps as fit the budget (a host copy of the
+    lattices)."""
+    from oracle import oracle as O
+    from fte_inputs.grid import REC
+    spec = w.grid
+    P_ = spec.bsize + 2
+    fields = bg.dev.view(spec.n_snap, len(leaves), P_, P_, P_, REC).cpu().numpy()
+    obg = O.amr_background(spec, leaves, fields)
+    threads = O.lib().or_max_threads()
+    n = 10_000
+    P, led = O.inject(obg, w.inject, np.arange(n, dtype=np.uint32))
+    t = time.perf_counter()
+    O.advance(obg, w.params, P.copy(), 0, 20, threads=threads)
+    per_step = (time.perf_counter() - t) / 20
+    steps = int(max(20, min(w.n_steps, budget_s / max(per_step, 1e-6))))
+    led = O.Ledger()
+    t = time.perf_counter()
+    O.advance(obg, w.params, P, 0, steps, ledger=led, threads=threads)
+    el = time.perf_counter() - t
+    done = int(led.as_dict()["n"][6])
+    return {"value": done / el, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"first {n} of the workload's particles over its first {steps} steps "
+                      f"({done} alive particle-steps, {el:.1f} s)"}
+
+
+def run_amr_case(args):
+    """Block-AMR workload (cir_amr_1e7): FP32, BF16 and FP16 storage, one line of JSON."""
+    import torch
+    from paper_2404_12164_gb300 import api, build
+    build.build()
+    torch.cuda.set_device(0)
+    clocks = Clocks(0)
+    res = amr_measure(api, args, forms=not args.no_forms, cpu=not args.no_cpu_baseline, clocks=clocks)
+    print(json.dumps({"case": "amr", "metric": METRIC, "n_gpus": 1, "higher_is_better": True,
+                      "data": "synthetic", **res, "clocks": clocks.result}), flush=True)
 
 
 def run_ensemble_case(args):
@@ -734,10 +774,21 @@ def run_ensemble_case(args):
 ADJ_OBS = dict(r_o=1.0, sigma_r=0.02, e_c=0.1, sigma_lnE=0.1, t_c=2 * 86400.0, sigma_t=3600.0)
 
 
-def adjoint_times(api, bg, w, n_part, n_steps, K, sort_every, reps=1, fd=False):
+def batch_sigma(x, nb=32):
+    """Standard error of sum(x) over particles from the sums of nb classes of particle index
+    (batch means: particles are independent, so the class sums are independent)."""
+    x = np.asarray(x, dtype=np.float64)
+    s = np.bincount(np.arange(len(x)) % nb, weights=x, minlength=nb)
+    return float(math.sqrt(nb * s.var(ddof=1)))
+
+
+def adjoint_times(api, bg, w, n_part, n_steps, K, sort_every, reps=1, fd=True, fd_names=("lambda_par", "q", "H"),
+                  fd_rel=2e-2):
     """Times of the plain step kernel, of the adjoint's forward pass and of forward + reverse on
-    the same particles (1e6-style power-law injection of the CIR workload); optionally the
-    central difference of dJ/dlambda_par with common random numbers."""
+    the same particles (1e6-style power-law injection of the CIR workload); with `fd` a check of
+    each gradient in fd_names against central differences (fd_rel of the parameter) of the
+    forward pass with common random numbers, both with batch-means standard errors over 32
+    particle-index classes, and the pathwise-only total (score window 0) beside them."""
     import torch
     inj = dataclasses.replace(w.inject, energy="powerlaw", e1=0.05, e2=5.0, gamma=3.0)
     # a run shorter than the observable's time centre looks at its middle instead
@@ -787,18 +838,41 @@ def adjoint_times(api, bg, w, n_part, n_steps, K, sort_every, reps=1, fd=False):
     out = {"particles": n_part, "steps": n_steps, "checkpoint_every": K, "t_c": t_c, "alive_particle_steps": alive_steps,
            "plain_s": t_plain, "adjoint_forward_s": t_fwd, "adjoint_forward_reverse_s": t_adj,
            "adj_over_fwd": t_adj / t_plain, "J": float(adj.out[0]),
-           "grad": dict(zip(api.GRAD_NAMES, adj.out[1:].cpu().numpy().tolist()))}
+           "grad": dict(zip(api.GRAD_NAMES, adj.out[1:].cpu().numpy().tolist())),
+           "estimator": "pathwise, with the steps whose pitch-angle Gaussian reaches mu = 0 in score form "
+                        "(window %s widths)" % ("4" if prm.dmumu != "iso" else "0")}
     if fd:
-        h = 1e-3 * prm.lambda_par
-        Js = []
-        for lam in (prm.lambda_par + h, prm.lambda_par - h):
-            a2 = api.Adjoint(bg, dataclasses.replace(prm, lambda_par=lam), obs, 0, n_steps, K, ws=adj.ws)
+        def per_particle(a):
             inject()
-            Js.append(float(a2.forward(pool)))
-        d = (Js[0] - Js[1]) / (2 * h)
-        g0 = out["grad"]["lambda_par"]
-        out["fd_check"] = {"d_lambda_par_central_difference": d, "adjoint": g0,
-                           "rel_diff": abs(d - g0) / abs(d) if d else None}
+            a.forward(pool)
+            _, pp = a.reverse(pool, inj, per_particle=True)
+            return pp.double().cpu().numpy()
+
+        pp = per_particle(adj)
+        pw = per_particle(api.Adjoint(bg, prm, dataclasses.replace(obs, lr_window=0.0), 0, n_steps, K, ws=adj.ws))
+        checks = {}
+        for nm in fd_names:
+            col = 1 + list(api.GRAD_NAMES).index(nm)
+            v0 = getattr(prm, nm)
+            h = fd_rel * v0
+            Js = []
+            for v in (v0 + h, v0 - h):
+                a2 = api.Adjoint(bg, dataclasses.replace(prm, **{nm: v}), obs, 0, n_steps, K, ws=adj.ws)
+                inject()
+                Js.append(a2.forward(pool, per_particle=True)[1].cpu().numpy())
+            fdp = (Js[0] - Js[1]) / (2 * h)
+            d, sd = float(fdp.sum()), batch_sigma(fdp)
+            g, sg = float(pp[:, col].sum()), batch_sigma(pp[:, col])
+            g0, sg0 = float(pw[:, col].sum()), batch_sigma(pw[:, col])
+            comb = math.sqrt(sd * sd + sg * sg)
+            checks[nm] = {"central_difference": d, "central_difference_sigma": sd, "adjoint": g, "adjoint_sigma": sg,
+                          "rel_diff": abs(d - g) / abs(d) if d else None,
+                          "diff_in_sigma": abs(d - g) / comb if comb > 0 else None,
+                          "pathwise_only": g0, "pathwise_only_sigma": sg0,
+                          "pathwise_only_diff_in_sigma": abs(d - g0) / math.sqrt(sd * sd + sg0 * sg0)
+                          if sd > 0 or sg0 > 0 else None}
+        out["fd_check"] = {"step": f"{fd_rel:g} of each parameter, common random numbers",
+                           "sigma": "batch means over 32 particle-index classes", "params": checks}
     return out
 
 
@@ -807,8 +881,8 @@ def run_adjoint_case(args):
     spectrum over 50 keV - 5 MeV, gradients of the smoothed 1 au intensity (E_c = 100 keV,
     sigma_lnE = 0.1, t_c = 2 d, sigma_t = 1 h, sigma_r = 0.02 au) with respect to lambda_par, q, H
     and the injection index; checkpoints every 256 steps.  Reports the plain step kernel's time,
-    the adjoint's forward + reverse time, their ratio, and a central-difference check of
-    dJ/dlambda_par with common random numbers."""
+    the adjoint's forward + reverse time, their ratio, and central-difference checks of
+    dJ/dlambda_par, dJ/dq and dJ/dH with common random numbers."""
     import torch
     from paper_2404_12164_gb300 import api, build
     build.build()
@@ -829,7 +903,8 @@ def run_adjoint_case(args):
                                  "s": res["adjoint_forward_s"]},
         "adjoint_forward_plus_reverse": {"value": res["alive_particle_steps"] / res["adjoint_forward_reverse_s"],
                                          "s": res["adjoint_forward_reverse_s"]},
-        "adj_over_fwd": res["adj_over_fwd"], "J": res["J"], "grad": res["grad"], "fd_check": res["fd_check"],
+        "adj_over_fwd": res["adj_over_fwd"], "J": res["J"], "grad": res["grad"], "estimator": res["estimator"],
+        "fd_check": res["fd_check"],
     }), flush=True)
 
 
@@ -956,6 +1031,77 @@ def run_stream_case(args):
     }), flush=True)
 
 
+def l1_probe(kib=64, records=4096, reps=5, spreads=(1, 2, 4, 8, 32)):
+    """Delivered GB/s of the transport kernel's record loads (ld.global.nc.v8 x 2 + v2, 72 B
+    per record) from an L1-resident buffer of FP32 cell records, for several numbers of
+    distinct records per warp (`spread`); best of reps each.  Returns {spread: GB/s}."""
+    import torch
+    from paper_2404_12164_gb300 import api
+    from paper_2404_12164_gb300 import _abi as A
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    threads = sms * 2048
+    buf = torch.rand(kib * 1024 // 4, dtype=torch.float32, device="cuda")
+    out = torch.empty(threads, dtype=torch.float32, device="cuda")
+    res = {}
+    for sp in spreads:
+        api.fte_probe_gather_l1(buf, threads, 64, sp, out)
+        best = 0.0
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            api.fte_probe_gather_l1(buf, threads, records, sp, out)
+            e1.record()
+            torch.cuda.synchronize()
+            best = max(best, threads * records * (A.FTE_NFIELD * 4) / (e0.elapsed_time(e1) / 1e3) / 1e9)
+        res[sp] = best
+    return res
+
+
+def union_ms(iv):
+    """Length of the union of [start, end] intervals (ms)."""
+    if len(iv) == 0:
+        return 0.0
+    iv = iv[np.argsort(iv[:, 0])]
+    tot, cs, ce = 0.0, iv[0, 0], iv[0, 1]
+    for s, e in iv[1:]:
+        if s > ce:
+            tot += ce - cs
+            cs, ce = s, e
+        else:
+            ce = max(ce, e)
+    return tot + (ce - cs)
+
+
+def roofline_record(intervals, particle_steps, alg_per_step, l1, l2_gbs, traffic):
+    """Roofline of the step kernel over the timed region from its recorded launches: the
+    algorithmic bytes of all launches over the time the kernel ran (the union of its launch
+    intervals; the two half-pool streams overlap), in units of one launch."""
+    hbm, hbm_kind = _peaks()
+    n = len(intervals)
+    u = union_ms(intervals)
+    alg = particle_steps * alg_per_step
+    achieved = alg / (u / 1e3) / 1e9 if u > 0 else None
+    peak = max(l1.values()) if l1 else None
+    durs = intervals[:, 1] - intervals[:, 0] if n else np.zeros(0)
+    return {"bound": "l1", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak if achieved and peak else None,
+            "traffic": traffic.get("dram_bytes_per_launch") if traffic else None,
+            "traffic_source": traffic.get("source") if traffic else None,
+            "kernel": "advance_kernel", "alg_bytes_per_particle_step": alg_per_step,
+            "alg_bytes_per_launch": alg / n if n else None,
+            "kernel_launches": n, "kernel_ms_total": float(durs.sum()), "kernel_ms_union": u,
+            "kernel_ms_mean_launch": float(durs.mean()) if n else None,
+            "peak_source": "L1 probe of the step kernel's record loads (fte_probe_gather_l1, 64 KiB of records, "
+                           "best over lane spreads), measured in this run",
+            "l1_probe_gbs_by_spread": {str(k): v for k, v in l1.items()},
+            "l1_wavefronts": traffic.get("l1") if traffic else None,
+            "hbm": {"peak": hbm, "peak_source": f"{hbm_kind} hbm_gbs (MEASURED_PEAKS.json)",
+                    "frac": achieved / hbm if achieved else None},
+            "l2_random_sector_gbs": l2_gbs,
+            "frac_of_l2": achieved / l2_gbs if achieved and l2_gbs else None}
+
+
 def l2_probe(mib=64, threads=152 * 2048, loads=256, reps=5):
     """Random 32-byte sector read bandwidth of an L2-resident buffer (GB/s), best of reps."""
     import torch
@@ -990,6 +1136,7 @@ def main():
     ap.add_argument("--amr-steps", type=int, default=1800)
     ap.add_argument("--launches", type=int, default=3)
     ap.add_argument("--grid", default="uniform", choices=["uniform", "amr"], help="grid of --case profile")
+    ap.add_argument("--dtype", default="f32", choices=["f32", "bf16", "f16"], help="storage of --case profile")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
@@ -1000,6 +1147,7 @@ def main():
     ap.add_argument("--layout", default="cell", choices=["cell", "pair"],
                     help="record layout of the device background (pair: a cell and its r-neighbour per record)")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-amr", action="store_true", help="leave the block-AMR workload out of the default line")
     ap.add_argument("--adj-slice", type=int, default=4096, help="steps of the adjoint measurement in the default run")
     ap.add_argument("--sort-every", type=int, default=64,
                     help="steps between spatial reorderings of the alive particles (0: off)")

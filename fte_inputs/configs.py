@@ -65,6 +65,8 @@ class InjectSpec:
     mu0: float = 0.0
     seed: int = 0
     set_id: int = 0
+    spiral: float = 0.0              # box: ph1..ph2 bound the spiral phase phi + spiral (r - spiral_rb)
+    spiral_rb: float = 0.1           # au
 
 
 @dataclass
@@ -117,6 +119,7 @@ class SmoothObserver:
     sigma_lnE: float = 0.1           # natural log
     t_c: float = 2 * 86400.0         # s
     sigma_t: float = 3600.0          # s
+    lr_window: float = -1.0          # gradient estimator: score-form window around mu = 0 (< 0: default)
 
 
 @dataclass
@@ -133,7 +136,10 @@ class Workload:
     sets: Optional[list] = None        # ensembles: EnsembleSet per parameter set
 
 
-def cir_observer_phi(r_obs=1.0, psi_c=1.5 * math.pi, u_kms=500.0, r_b=0.1):
+CIR_PSI_C = 1.5 * math.pi            # spiral phase of the observed CIR's compression boundary
+
+
+def cir_observer_phi(r_obs=1.0, psi_c=CIR_PSI_C, u_kms=500.0, r_b=0.1):
     """Longitude where the CIR whose compression boundary sits at spiral phase psi_c crosses r_obs."""
     return (psi_c - OMEGA_SUN * (r_obs - r_b) / (u_kms * KMS)) % (2 * math.pi)
 
@@ -166,8 +172,13 @@ def cir_amr_1e7(n_particles=10_000_000, n_steps=1800, spec=None):
     from .amr import AmrSpec
     g = spec or AmrSpec(nbr=32, nbt=8, nbp=24, bsize=16, levels=3, radial="log", n_snap=2,
                         periodic=False, t_snap0=0.0, dt_snap=3600.0)
-    inj = InjectSpec(region="box", r1=1.0, r2=2.0, th1=88 * DEG, th2=92 * DEG,
-                     ph1=math.pi, ph2=2 * math.pi, divv_max=0.0, divv_snap=0,
+    # one CIR from 0.12 to 2 au (Sec. 2.3), selected by the spiral region criterion
+    # phi_hat = phi + (r - r_B) Omega / U within +-10 deg of the CIR's compression boundary
+    # (the observers sit on it): the synthetic wind compresses (div V < 0) only beyond
+    # ~0.65 au, so the band stands in for the shock-traced div V < 0 region
+    inj = InjectSpec(region="box", r1=0.12, r2=2.0, th1=88 * DEG, th2=92 * DEG,
+                     ph1=CIR_PSI_C - 10 * DEG, ph2=CIR_PSI_C + 10 * DEG,
+                     spiral=OMEGA_SUN / (500.0 * KMS), spiral_rb=0.1,
                      energy="powerlaw", e1=0.05, e2=5.0, gamma=3.0, weight="r-2", seed=0)
     prm = Params(dmumu="qlt", lambda_par=0.1, q=5.0 / 3.0, H=0.05, dt=2.0, seed=0, sort_every=64)
     t_end = n_steps * prm.dt

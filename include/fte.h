@@ -16,7 +16,10 @@
  *     colatitude, phi longitude in [0, 2 pi).
  *   - Memory: every pointer named "dev" / documented DEVICE is device memory
  *     owned by the caller (the Python binding allocates it with PyTorch).  The
- *     library allocates no device memory and keeps no state between calls.
+ *     library allocates no device memory and keeps no state between calls, with
+ *     one exception: fte_advance_noalloc's statically placed 24 MiB scratch
+ *     array (present on every device that loads the library) and the device
+ *     address of it that the library looks up once per device.
  *     Pointers documented HOST are host memory owned by the caller.
  *   - Streams: `stream` is a cudaStream_t (NULL = legacy default stream).  All
  *     work is enqueued asynchronously on it unless the call says it synchronises.
@@ -39,8 +42,9 @@
 extern "C" {
 #endif
 
-#define FTE_ABI_VERSION 2
+#define FTE_ABI_VERSION 3
 #define FTE_NFIELD 18          /* stored fields per cell */
+#define FTE_NCLASS 32          /* particle-id classes of the observer totals S_class */
 #define FTE_REC 24             /* floats per stored cell record (96 bytes) */
 #define FTE_HREC 32            /* 16-bit values per reduced-precision cell record (64 bytes) */
 #define FTE_HHDR 32            /* floats of the per-field scale header of a reduced-precision background */
@@ -184,7 +188,10 @@ typedef struct fte_particles {
 /* ---------------------------------------------------------------------------
  * Injection (Sec. 2.3, Eq. 7).  region 0: all at the point (r, th, ph); region 1:
  * uniform in volume over r in [r1, r2], cos(theta) between cos th1 and cos th2,
- * phi in [ph1, ph2], optionally accepting only positions whose containing cell
+ * phi in [ph1, ph2] (with spiral != 0: the spiral phase phi_hat = phi + spiral
+ * (r - spiral_rb) in [ph1, ph2], i.e. a band along an Archimedean spiral such as
+ * the CIR region criterion phi_hat = phi + (r - r_B) Omega / U of Sec. 2.3; the
+ * volume element is unchanged), optionally accepting only positions whose containing cell
  * of snapshot `divv_snap` (of a ring background: slot `divv_snap`, which the caller
  * must have filled) has stored div V (dV_x/dx + dV_y/dy + dV_z/dz, summed in
  * float in that order) < divv_max, with at most max_tries attempts per particle.
@@ -201,6 +208,8 @@ typedef struct fte_inject_spec {
     double e0, e1, e2, gamma, mu0;
     uint32_t seed, set_id;
     uint32_t id_base, pad1;
+    double spiral;             /* box: rad per au; phi = phi_hat - spiral (r - spiral_rb) */
+    double spiral_rb;          /* au */
 } fte_inject_spec;
 
 /* ---------------------------------------------------------------------------
@@ -261,12 +270,16 @@ typedef struct fte_tally_buf {
     unsigned long long* C;            /* DEVICE, max(n_sets, 1) * fte_tally_bins() counts */
     double* ledger_w;                 /* DEVICE, FTE_LEDGER doubles */
     unsigned long long* ledger_n;     /* DEVICE, FTE_LEDGER counts */
+    double* S_class;                  /* DEVICE, optional (NULL: not kept): max(n_sets, 1) * n_obs *
+                                         FTE_NCLASS doubles, [set][obs][class]: the sum of w dt over
+                                         the tallied steps of the particles whose id % FTE_NCLASS is
+                                         `class`, for batch-means error estimates of observer totals */
 } fte_tally_buf;
 
 /* Total bins over all observers of one set (0 if the tally description is invalid). */
 size_t fte_tally_bins(const fte_tally_buf* t);
 
-/* Zero S, S2, C of every set and the ledger (asynchronous). */
+/* Zero S, S2, C of every set, S_class (when kept) and the ledger (asynchronous). */
 fte_status fte_tally_reset(const fte_tally_buf* t, void* stream);
 
 /* Scratch (DEVICE) needed by fte_advance on `device` for grid `g`, tally `t`, a
@@ -372,15 +385,23 @@ fte_status fte_stream_load(const fte_background* bg, const void* host_snapshots,
 /* Allocation-free variant of fte_advance (the paper has no counterpart: this is
    an interface for callers that cannot allocate device memory at run time, such
    as a host code whose own allocator owns all of the GPU's memory, or a service
-   that must not call cudaMalloc once running).  Same arguments, results and
-   stream semantics as fte_advance, but without the workspace: the scratch is a
-   24 MiB array that the library places in device memory statically, held by
-   every GPU that loads the library until the process exits.  The first call on
-   a device (with that device current) looks up the array's device address;
-   make that first call before any stream capture.  All calls share the array:
-   calls whose work overlaps on the GPU race on it.  Returns FTE_ENOMEM when the
-   tally's per-block partial histograms (12 bytes per bin) do not fit the array
-   for at least one block per SM (about 13,800 bins on a 152-SM GB300). */
+   that must not call cudaMalloc once running).  Same arguments and stream
+   semantics as fte_advance, but without the workspace: the scratch is a 24 MiB
+   array that the library places in device memory statically, held by every GPU
+   that loads the library until the process exits.  It always tallies through
+   per-block shared-memory histograms (prm->tally_layout must still be a valid
+   value and is otherwise not used) and never reorders the particles
+   (prm->sort_every is not used): particle states, ledger and tally counts equal
+   those of fte_advance with tally_layout = FTE_LAYOUT_SHARED, tally sums up to
+   the order of FP32 partial sums.  The first call on a device (with that device
+   current) looks up the array's device address; make that first call before
+   any stream capture.  That address belongs to the device's primary context: a
+   cudaDeviceReset (or any teardown of that context) invalidates it, after which
+   the process must not call this entry point on that device again.  All calls
+   share the array: calls whose work overlaps on the GPU race on it.  Returns
+   FTE_ENOMEM when the tally's per-block partial histograms (12 bytes per bin) do
+   not fit the array for at least one block per SM (about 13,800 bins on a
+   152-SM GB300). */
 fte_status fte_advance_noalloc(fte_particles* P, const fte_background* bg, const fte_params* prm,
                                const fte_tally_buf* t, int64_t n_start, int64_t n_end, void* stream);
 
@@ -480,12 +501,23 @@ fte_status fte_graph_destroy(fte_graph* g);
  * n = n_start .. n_end-1 of every particle (start-of-step state, t_n = t0 + n dt),
  * K = exp(-(r - r_o)^2 / (2 sigma_r^2)) exp(-ln(E / e_c)^2 / (2 sigma_lnE^2))
  *     exp(-(t - t_c)^2 / (2 sigma_t^2)).
- * Gradients (FTE_NGRAD): dJ/dlambda_par, dJ/dq, dJ/dH, dJ/deps (pathwise, through
- * D_mumu, its mu derivative and the normalisation integral), dJ/dgamma of the
- * injected power law (likelihood ratio of each particle's injected energy).
- * Discrete decisions along a path (cell, reflection, absorption) are held
- * fixed, so the pathwise part is the derivative of the realised paths; paths
- * crossing mu = 0 under the quasi-linear D_mumu see its |mu|^(q-2) drift.
+ * Gradients (FTE_NGRAD): dJ/dlambda_par, dJ/dq, dJ/dH, dJ/deps (through D_mumu,
+ * its mu derivative and the normalisation integral), dJ/dgamma of the injected
+ * power law (likelihood ratio of each particle's injected energy).
+ * Each step's pitch-angle increment is a Gaussian of mean m = mu + (mudot +
+ * dD/dmu) dt and width s = sqrt(2 D dt), reflected at mu = +-1 (Sec. 2.1).  Eq. 5's
+ * dD/dmu jumps at mu = 0 and the quasi-linear one is singular there, so the
+ * derivative of a realised path misses the part of dE[J]/dtheta carried by
+ * paths whose mu passes 0.  Steps whose m lies within lr_window widths of a value
+ * that lands at mu = 0 (min(|m|, ||m| - 2|) < lr_window s) therefore enter in the
+ * score (likelihood-ratio) form: mu' is held and the derivative of the log of its
+ * transition density (with the reflection's images) multiplies the observable
+ * accumulated after the step; every other step is differentiated pathwise with its
+ * Philox noise held.  The estimate is unbiased for the discretised chain up to the
+ * Gaussian tail beyond lr_window widths.  lr_window < 0 selects 4 for Eq. 5 and the
+ * quasi-linear form and 0 (pathwise everywhere) for the isotropic form, whose
+ * coefficients are smooth in mu.  Other discrete decisions (cell, absorption) are
+ * held fixed.
  * Supported: lambda_perp = 0, lambda independent of p (p_ref = 0 or alpha = 0).
  * ------------------------------------------------------------------------- */
 #define FTE_NGRAD 5
@@ -493,6 +525,7 @@ typedef struct fte_smooth_obs {
     double r_o, sigma_r;       /* au */
     double e_c, sigma_lnE;     /* MeV; natural log */
     double t_c, sigma_t;       /* s */
+    double lr_window;          /* widths of the score-form window around mu = 0; < 0: the default */
 } fte_smooth_obs;
 
 /* Scratch (DEVICE) for fte_adjoint_forward/reverse: checkpoints every
@@ -506,10 +539,11 @@ size_t fte_adjoint_workspace_bytes(int device, const fte_grid* g, uint64_t n_par
 
 /* Forward pass: advances P from n_start to n_end exactly as fte_advance would
    (no tally, no ledger), storing checkpoints in ws, and writes J to dev_out[0]
-   (DEVICE, 1 + FTE_NGRAD doubles; the rest is zeroed).  Asynchronous. */
+   (DEVICE, 1 + FTE_NGRAD doubles; the rest is zeroed).  dev_J_particle (DEVICE,
+   optional, P->count doubles): each particle's J_i.  Asynchronous. */
 fte_status fte_adjoint_forward(fte_particles* P, const fte_background* bg, const fte_params* prm,
                                const fte_smooth_obs* obs, int64_t n_start, int64_t n_end, int checkpoint_every,
-                               double* dev_out, void* ws, size_t ws_bytes, void* stream);
+                               double* dev_out, double* dev_J_particle, void* ws, size_t ws_bytes, void* stream);
 
 /* Reverse pass after fte_adjoint_forward with the same P, bg, prm, obs, steps,
    checkpoint interval and ws: writes the FTE_NGRAD gradients to dev_out[1..].
@@ -557,15 +591,6 @@ fte_status fte_tally_convolve(const fte_tally_buf* t, int set, int obs, int kind
 
 /* Copy the ledger to HOST arrays (FTE_LEDGER entries each); synchronises `stream`. */
 fte_status fte_ledger(const fte_tally_buf* t, double* host_w, uint64_t* host_n, void* stream);
-
-/* Measurement helper (the paper has no counterpart): `threads` threads (a
-   multiple of 256) each read `loads` pseudo-random 32-byte sectors of `buf`
-   (DEVICE, 32-byte aligned, `bytes` >= 32) bypassing L1, and write one float
-   each to dev_out (DEVICE, `threads` floats).  Timing it gives the random-sector
-   read bandwidth of the level holding `buf` (L2 when `bytes` fits in L2), the
-   ceiling of a gather served from L2.  Asynchronous on `stream`. */
-fte_status fte_probe_sectors(const void* buf, size_t bytes, int threads, int loads, float* dev_out,
-                             void* stream);
 
 const char* fte_last_error(void);
 const char* fte_status_string(int status);

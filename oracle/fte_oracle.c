@@ -751,6 +751,9 @@ int or_inject(const or_background* bg, const or_inject_spec* sp, const uint32_t*
                 double c1 = cos(sp->th1), c2 = cos(sp->th2);
                 th = acos(c1 + v[1] * (c2 - c1));
                 ph = sp->ph1 + v[2] * (sp->ph2 - sp->ph1);
+                /* a band of spiral phase phi_hat = phi + spiral (r - r_b) (the region
+                   criterion of Sec. 2.3 for one CIR) */
+                if (sp->spiral != 0.0) ph -= sp->spiral * (r - sp->spiral_rb);
                 if (!sp->use_divv || bg->kind != OR_BG_GRID) { ok = 1; break; }
                 /* acceptance decided on the stored cell value of the containing
                    cell, summed in float like the device does */
@@ -833,6 +836,7 @@ typedef struct {
     const int64_t* off;
     double *S, *S2;
     uint64_t *C, *A;
+    double* SC;                  /* optional [n_obs][32]: observer totals by particle id mod 32 */
     double lw[8];
     uint64_t ln[8];
 } tally_t;
@@ -845,10 +849,11 @@ static double wrap_pi(double a)
 }
 
 /* Occupancy tally of the start-of-step state: in observer o, bin (E, t) gains
-   w dt (and (w dt)^2, and one count).  Events within 1e-4 (relative) of an
+   w dt (and (w dt)^2, and one count), and observer o's total for the particle's
+   id class (id mod 32) gains w dt.  Events within 1e-4 (relative) of an
    energy-bin edge or of the observer's boundary are also counted in A. */
 static void tally_state(tally_t* T, double x, double y, double z, double p, double w,
-                        double t, double dt)
+                        double t, double dt, uint32_t id)
 {
     if (!T || T->n_obs == 0) return;
     double r = sqrt(x * x + y * y + z * z);
@@ -905,6 +910,7 @@ static void tally_state(tally_t* T, double x, double y, double z, double p, doub
             T->S[b] += wd;
             T->S2[b] += wd * wd;
             T->C[b] += 1;
+            if (T->SC) T->SC[o * 32 + (int)(id % 32u)] += wd;
         }
         if (amb) T->A[b] += 1;
     }
@@ -1028,7 +1034,7 @@ static int step_core(const or_background* bg, const or_params* prm, double I,
     }
 
     /* tally the start-of-step state */
-    tally_state(T, x, y, z, p, P->w, t, dt);
+    tally_state(T, x, y, z, p, P->w, t, dt, P->id);
 
     P->x = xn[0]; P->y = xn[1]; P->z = xn[2];
     P->mu = mu_new; P->p = p_new;
@@ -1088,7 +1094,7 @@ int or_max_threads(void)
 
 int or_advance(const or_background* bg, const or_params* prm, const or_observer* obs,
                int n_obs, or_particle* P, int64_t n, int64_t n_start, int64_t n_end,
-               double* S, double* S2, uint64_t* C, uint64_t* A, double ledger_w[8],
+               double* S, double* S2, uint64_t* C, uint64_t* A, double* SC, double ledger_w[8],
                uint64_t ledger_n[8], int n_threads)
 {
     if (n_threads < 1) n_threads = 1;
@@ -1103,12 +1109,14 @@ int or_advance(const or_background* bg, const or_params* prm, const or_observer*
     double* tS2 = (double*)calloc((size_t)n_threads * (nb > 0 ? nb : 1), sizeof(double));
     uint64_t* tC = (uint64_t*)calloc((size_t)n_threads * (nb > 0 ? nb : 1), sizeof(uint64_t));
     uint64_t* tA = (uint64_t*)calloc((size_t)n_threads * (nb > 0 ? nb : 1), sizeof(uint64_t));
+    double* tSC = (double*)calloc((size_t)n_threads * (n_obs > 0 ? n_obs : 1) * 32, sizeof(double));
     tally_t* tt = (tally_t*)calloc((size_t)n_threads, sizeof(tally_t));
-    if (!tS || !tS2 || !tC || !tA || !tt) return -2;
+    if (!tS || !tS2 || !tC || !tA || !tSC || !tt) return -2;
     for (int k = 0; k < n_threads; ++k) {
         tt[k].obs = obs; tt[k].n_obs = n_obs; tt[k].off = off;
         tt[k].S = tS + (size_t)k * nb; tt[k].S2 = tS2 + (size_t)k * nb;
         tt[k].C = tC + (size_t)k * nb; tt[k].A = tA + (size_t)k * nb;
+        tt[k].SC = tSC + (size_t)k * (n_obs > 0 ? n_obs : 1) * 32;
     }
 #ifdef _OPENMP
 #pragma omp parallel num_threads(n_threads)
@@ -1136,8 +1144,10 @@ int or_advance(const or_background* bg, const or_params* prm, const or_observer*
             S[b] += tt[k].S[b]; S2[b] += tt[k].S2[b]; C[b] += tt[k].C[b]; A[b] += tt[k].A[b];
         }
         for (int m = 0; m < 8; ++m) { ledger_w[m] += tt[k].lw[m]; ledger_n[m] += tt[k].ln[m]; }
+        if (SC)
+            for (int b = 0; b < n_obs * 32; ++b) SC[b] += tt[k].SC[b];
     }
-    free(tS); free(tS2); free(tC); free(tA); free(tt);
+    free(tS); free(tS2); free(tC); free(tA); free(tSC); free(tt);
     return 0;
 }
 

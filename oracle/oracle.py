@@ -52,7 +52,8 @@ class InjectC(C.Structure):
                 ("pad", C.c_int32), ("divv_max", C.c_double),
                 ("e0", C.c_double), ("e1", C.c_double), ("e2", C.c_double),
                 ("gamma", C.c_double), ("mu0", C.c_double),
-                ("seed", C.c_uint32), ("set_id", C.c_uint32)]
+                ("seed", C.c_uint32), ("set_id", C.c_uint32),
+                ("spiral", C.c_double), ("spiral_rb", C.c_double)]
 
 
 class ObserverC(C.Structure):
@@ -88,7 +89,8 @@ def lib():
                                 P(C.c_double), P(C.c_uint64)]
         L.or_advance.argtypes = [P(Background), P(ParamsC), P(ObserverC), C.c_int, C.c_void_p,
                                  C.c_int64, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p,
-                                 C.c_void_p, C.c_void_p, P(C.c_double), P(C.c_uint64), C.c_int]
+                                 C.c_void_p, C.c_void_p, C.c_void_p, P(C.c_double), P(C.c_uint64),
+                                 C.c_int]
         L.or_step_terms.argtypes = [P(Background), P(ParamsC), C.c_void_p, C.c_int64,
                                     P(C.c_double)]
         L.or_intensity.argtypes = [P(ObserverC), C.c_void_p, C.c_void_p]
@@ -201,6 +203,7 @@ def inject_c(s):
     c.divv_max = 0.0 if s.divv_max is None else s.divv_max
     c.e0, c.e1, c.e2, c.gamma, c.mu0 = s.e0, s.e1, s.e2, s.gamma, s.mu0
     c.seed, c.set_id = s.seed & 0xFFFFFFFF, s.set_id & 0xFFFFFFFF
+    c.spiral, c.spiral_rb = getattr(s, "spiral", 0.0), getattr(s, "spiral_rb", 0.1)
     return c
 
 
@@ -284,6 +287,8 @@ class Tally:
         self.S2 = np.zeros(n)
         self.C = np.zeros(n, dtype=np.uint64)
         self.A = np.zeros(n, dtype=np.uint64)
+        # observer totals by particle id mod 32: [observer][class]
+        self.SC = np.zeros((max(len(self.observers), 1), 32))
         self.oc = (ObserverC * max(len(self.observers), 1))(
             *[observer_c(o) for o in self.observers])
 
@@ -385,7 +390,7 @@ def advance(bg, params, particles, n_start, n_end, tally=None, ledger=None, thre
     rc = L.or_advance(C.byref(bg.c), C.byref(pc), tally.oc, len(tally.observers),
                       particles.ctypes.data, len(particles), n_start, n_end,
                       tally.S.ctypes.data, tally.S2.ctypes.data, tally.C.ctypes.data,
-                      tally.A.ctypes.data, led.w, led.n, nthreads)
+                      tally.A.ctypes.data, tally.SC.ctypes.data, led.w, led.n, nthreads)
     if rc != 0:
         raise RuntimeError(f"or_advance failed ({rc})")
     return tally, led

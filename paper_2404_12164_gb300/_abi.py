@@ -10,6 +10,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libfte_gb300.so")
 
 FTE_NFIELD = 18
+FTE_NCLASS = 32
 FTE_REC = 24
 FTE_HREC = 32
 FTE_HHDR = 32
@@ -56,7 +57,8 @@ class fte_inject_spec(C.Structure):
                 ("pad0", C.c_int32), ("divv_max", C.c_double),
                 ("e0", C.c_double), ("e1", C.c_double), ("e2", C.c_double), ("gamma", C.c_double),
                 ("mu0", C.c_double), ("seed", C.c_uint32), ("set_id", C.c_uint32),
-                ("id_base", C.c_uint32), ("pad1", C.c_uint32)]
+                ("id_base", C.c_uint32), ("pad1", C.c_uint32),
+                ("spiral", C.c_double), ("spiral_rb", C.c_double)]
 
 
 class fte_params(C.Structure):
@@ -80,12 +82,12 @@ class fte_observer(C.Structure):
 class fte_tally_buf(C.Structure):
     _fields_ = [("n_obs", C.c_int32), ("n_sets", C.c_int32), ("obs", fte_observer * FTE_MAX_OBS),
                 ("S", C.c_void_p), ("S2", C.c_void_p), ("C", C.c_void_p),
-                ("ledger_w", C.c_void_p), ("ledger_n", C.c_void_p)]
+                ("ledger_w", C.c_void_p), ("ledger_n", C.c_void_p), ("S_class", C.c_void_p)]
 
 
 class fte_smooth_obs(C.Structure):
     _fields_ = [("r_o", C.c_double), ("sigma_r", C.c_double), ("e_c", C.c_double), ("sigma_lnE", C.c_double),
-                ("t_c", C.c_double), ("sigma_t", C.c_double)]
+                ("t_c", C.c_double), ("sigma_t", C.c_double), ("lr_window", C.c_double)]
 
 
 class fte_set(C.Structure):
@@ -135,8 +137,8 @@ SIGNATURES = {
                                        _P(C.c_double), _P(C.c_int), C.c_void_p]),
     "fte_adjoint_workspace_bytes": (C.c_size_t, [C.c_int, _P(fte_grid), C.c_uint64, C.c_int64, C.c_int]),
     "fte_adjoint_forward": (C.c_int, [_P(fte_particles), _P(fte_background), _P(fte_params), _P(fte_smooth_obs),
-                                      C.c_int64, C.c_int64, C.c_int, C.c_void_p, C.c_void_p, C.c_size_t,
-                                      C.c_void_p]),
+                                      C.c_int64, C.c_int64, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
+                                      C.c_size_t, C.c_void_p]),
     "fte_adjoint_reverse": (C.c_int, [_P(fte_particles), _P(fte_background), _P(fte_params), _P(fte_smooth_obs),
                                       _P(fte_inject_spec), C.c_int64, C.c_int64, C.c_int, C.c_void_p, C.c_void_p,
                                       C.c_void_p, C.c_size_t, C.c_void_p]),
@@ -156,6 +158,10 @@ SIGNATURES = {
     "fte_graph_destroy": (C.c_int, [C.c_void_p]),
     "fte_ledger": (C.c_int, [_P(fte_tally_buf), _P(C.c_double), _P(C.c_uint64), C.c_void_p]),
     "fte_probe_sectors": (C.c_int, [C.c_void_p, C.c_size_t, C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
+    "fte_probe_gather_l1": (C.c_int, [C.c_void_p, C.c_size_t, C.c_int, C.c_int, C.c_int, C.c_void_p,
+                                      C.c_void_p]),
+    "fte_probe_step_timing": (C.c_int, [C.c_int]),
+    "fte_probe_step_intervals": (C.c_int, [C.c_void_p, C.c_int, _P(C.c_int)]),
     "fte_last_error": (C.c_char_p, []),
     "fte_status_string": (C.c_char_p, [C.c_int]),
     "fte_abi_version": (C.c_int, []),

@@ -58,6 +58,7 @@ def inject_c(s, id_base=0):
     c.e0, c.e1, c.e2, c.gamma, c.mu0 = s.e0, s.e1, s.e2, s.gamma, s.mu0
     c.seed, c.set_id = s.seed & 0xFFFFFFFF, s.set_id & 0xFFFFFFFF
     c.id_base = id_base
+    c.spiral, c.spiral_rb = getattr(s, "spiral", 0.0), getattr(s, "spiral_rb", 0.1)
     return c
 
 
@@ -236,6 +237,9 @@ class Tally:
         self.C = torch.zeros(n, dtype=torch.int64, device=device)
         self.ledger_w = torch.zeros(A.FTE_LEDGER, dtype=torch.float64, device=device)
         self.ledger_n = torch.zeros(A.FTE_LEDGER, dtype=torch.int64, device=device)
+        # observer totals by particle-id class: [set][observer][class]
+        self.S_class = torch.zeros((max(self.n_sets, 1), max(len(self.observers), 1), A.FTE_NCLASS),
+                                   dtype=torch.float64, device=device)
         self.out = torch.zeros(max(self.nb + [1]), dtype=torch.float64, device=device)
         c = A.fte_tally_buf()
         c.n_obs = len(self.observers)
@@ -244,7 +248,20 @@ class Tally:
             c.obs[i] = observer_c(o)
         c.S, c.S2, c.C = self.S.data_ptr(), self.S2.data_ptr(), self.C.data_ptr()
         c.ledger_w, c.ledger_n = self.ledger_w.data_ptr(), self.ledger_n.data_ptr()
+        c.S_class = self.S_class.data_ptr()
         self.c = c
+
+    def batch_means(self, obs=0, set=0):
+        """Observer `obs`'s total occupancy (sum of w dt over its tallied steps) and the
+        relative standard error of that total from its FTE_NCLASS particle-id class sums
+        (batch means: the particles are independent, so the class sums are independent
+        estimates of 1/FTE_NCLASS of the total).  Returns (total, rel_err or None)."""
+        c = self.S_class[set, obs].double().cpu().numpy()
+        tot = float(c.sum())
+        if tot <= 0:
+            return tot, None
+        k = len(c)
+        return tot, float((k * c.var(ddof=1)) ** 0.5 / tot)
 
 
 class Workspace:
@@ -316,8 +333,33 @@ def fte_tally(tally, obs, kind=A.FTE_TALLY_S, stream=None):
     return host
 
 
+def fte_probe_gather_l1(buf, threads, records, spread, out, stream=None):
+    """The transport kernel's record loads from the L1-sized device tensor `buf` of FP32
+    cell records (measurement aid, include/fte_probe.h)."""
+    check(A.lib().fte_probe_gather_l1(C.c_void_p(buf.data_ptr()), buf.numel() * buf.element_size(),
+                                      int(threads), int(records), int(spread), C.c_void_p(out.data_ptr()),
+                                      _stream(stream)), "fte_probe_gather_l1")
+
+
+def fte_probe_step_timing(capacity):
+    """Record CUDA events around up to `capacity` step-kernel launches of fte_advance
+    (0: stop; measurement aid, include/fte_probe.h)."""
+    check(A.lib().fte_probe_step_timing(int(capacity)), "fte_probe_step_timing")
+
+
+def fte_probe_step_intervals(capacity=1 << 16):
+    """(start, end) in ms of every recorded step-kernel launch since the last read,
+    relative to the first start (float64 array [n, 2]); synchronises the events."""
+    out = np.zeros(2 * capacity, dtype=np.float64)
+    n = C.c_int(0)
+    check(A.lib().fte_probe_step_intervals(C.c_void_p(out.ctypes.data), int(capacity), C.byref(n)),
+          "fte_probe_step_intervals")
+    return out[:2 * n.value].reshape(-1, 2)
+
+
 def fte_probe_sectors(buf, threads, loads, out, stream=None):
-    """Random 32-byte sector reads of the device tensor `buf` (see include/fte.h)."""
+    """Random 32-byte sector reads of the device tensor `buf` (measurement aid,
+    include/fte_probe.h)."""
     check(A.lib().fte_probe_sectors(C.c_void_p(buf.data_ptr()), buf.numel() * buf.element_size(),
                                     int(threads), int(loads), C.c_void_p(out.data_ptr()),
                                     _stream(stream)), "fte_probe_sectors")
@@ -473,7 +515,8 @@ GRAD_NAMES = ("lambda_par", "q", "H", "eps", "gamma")
 
 
 def smooth_c(o):
-    return A.fte_smooth_obs(o.r_o, o.sigma_r, o.e_c, o.sigma_lnE, o.t_c, o.sigma_t)
+    return A.fte_smooth_obs(o.r_o, o.sigma_r, o.e_c, o.sigma_lnE, o.t_c, o.sigma_t,
+                            float(getattr(o, "lr_window", -1.0)))
 
 
 def fte_adjoint_workspace_bytes(bg, n_particles, n_steps, checkpoint_every, device=None):
@@ -495,15 +538,19 @@ class Adjoint:
         self.ws = ws if ws is not None else Workspace(device)
         self.out = torch.zeros(1 + A.FTE_NGRAD, dtype=torch.float64, device=device)
 
-    def forward(self, pool, stream=None):
-        """Advance `pool` and return J (a 0-d device tensor, valid once the stream reaches it)."""
+    def forward(self, pool, stream=None, per_particle=False):
+        """Advance `pool` and return J (a 0-d device tensor, valid once the stream reaches it);
+        with per_particle also each particle's J_i (float64 device tensor [n])."""
         buf = self.ws.ensure(fte_adjoint_workspace_bytes(self.bg, pool.count, self.n_end - self.n_start, self.K))
+        Ji = torch.zeros(pool.count, dtype=torch.float64, device=buf.device) if per_particle else None
         check(A.lib().fte_adjoint_forward(C.byref(pool.c), C.byref(self.bg.c), C.byref(params_c(self.params)),
                                           C.byref(smooth_c(self.obs)), self.n_start, self.n_end, self.K,
-                                          C.c_void_p(self.out.data_ptr()), C.c_void_p(buf.data_ptr()),
-                                          buf.numel(), _stream(stream)), "fte_adjoint_forward")
+                                          C.c_void_p(self.out.data_ptr()),
+                                          C.c_void_p(Ji.data_ptr()) if Ji is not None else None,
+                                          C.c_void_p(buf.data_ptr()), buf.numel(), _stream(stream)),
+              "fte_adjoint_forward")
         self.n_particles = pool.count
-        return self.out[0]
+        return (self.out[0], Ji) if per_particle else self.out[0]
 
     def reverse(self, pool, inject=None, per_particle=False, stream=None):
         """Gradients of J (device tensor of FTE_NGRAD doubles, in GRAD_NAMES order); with

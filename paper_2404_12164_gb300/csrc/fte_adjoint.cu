@@ -1,9 +1,10 @@
-// Pathwise adjoint of the transport (Sec. 2.1 steps, Sec. 2.4 interpolation):
-// gradients of a smooth observable J = sum_i w_i sum_n dt K(x_n, E_n, t_n)
-// with respect to the pitch-angle-diffusion parameters (lambda_par, q, H, eps),
-// with the Philox noise of every step held fixed, and with respect to the
-// injection spectral index through the likelihood ratio of the injected
-// energies.
+// Adjoint of the transport (Sec. 2.1 steps, Sec. 2.4 interpolation): gradients
+// of a smooth observable J = sum_i w_i sum_n dt K(x_n, E_n, t_n) with respect to
+// the pitch-angle-diffusion parameters (lambda_par, q, H, eps), pathwise with the
+// Philox noise of every step held fixed except at the steps whose pitch-angle
+// Gaussian reaches mu = 0, which enter in the score (likelihood-ratio) form (see
+// step_vjp), and with respect to the injection spectral index through the
+// likelihood ratio of the injected energies.
 //
 // Forward: the run is cut into segments of K steps; every particle stores its
 // state at each segment start (checkpoints).  Reverse: segment by segment from
@@ -168,10 +169,17 @@ __device__ __forceinline__ void dmumu_vjp(const ParamsK& P, float I, float rq, f
 // ---------------------------------------------------------------------------
 // Vector-Jacobian product of one step (lambda_perp = 0): lam holds the adjoint
 // of the state after step n on entry and of the state before it on return.
+// Score form (win > 0): when the pitch-angle Gaussian's mean m lies within win
+// widths s of a value landing at mu = 0, mu' is held instead of differentiated:
+// the derivative of ln p(mu' | m, s) (p the Gaussian with its reflection images
+// 2 - mu', -2 - mu'), times Gto, the observable accumulated after the step, takes
+// the place of the adjoint of mu'; m and s then carry it back to the state and
+// the parameters exactly as the pathwise adjoint would.
 // ---------------------------------------------------------------------------
 template <int DT, int LAY>
 __device__ void step_vjp(const AdvanceArgs& a, float I, float rq, float rh, long long n, uint32_t pid, float x,
-                         float y, float z, float mu, float p, const float* sc, float* lam, float* gth)
+                         float y, float z, float mu, float p, const float* sc, float Gto, float win, float* lam,
+                         float* gth)
 {
     const GridK& g = a.g;
     const ParamsK& P = a.prm;
@@ -243,11 +251,29 @@ __device__ void step_vjp(const AdvanceArgs& a, float I, float rq, float rh, long
     const float pdotb = (P.p_update == 0) ? lam[4] * p * ep_ * dt : lam[4] * p * dt;
     float xb[3] = {xnb[0], xnb[1], xnb[2]};
     const float ub[3] = {xnb[0] * dt, xnb[1] * dt, xnb[2] * dt};
-    const float m1b = lam[3] * fm;
+    // adjoints of the Gaussian's mean (m1b) and of its width times dsigma/dD's z factor (zb)
+    float m1b = lam[3] * fm, zb = m1b * zmu;
+    if (win > 0.f && D > 0.f) {
+        const float mm = mu + (mudot + dD) * dt;
+        const float sg = sqrtf(2.f * D * dt);
+        const float am = fabsf(mm);
+        if (fminf(am, fabsf(am - 2.f)) < win * sg) {
+            const float is = 1.f / sg;
+            const float mc = fminf(fmaxf(m2, -1.f), 1.f);
+            const float z0 = (mc - mm) * is, z1 = (2.f - mc - mm) * is, z2 = (-2.f - mc - mm) * is;
+            const float e0 = z0 * z0, e1 = z1 * z1, e2 = z2 * z2;
+            const float emin = fminf(e0, fminf(e1, e2));
+            const float w0 = __expf(-0.5f * (e0 - emin)), w1 = __expf(-0.5f * (e1 - emin)),
+                        w2 = __expf(-0.5f * (e2 - emin));
+            const float gw = Gto * is / (w0 + w1 + w2);
+            m1b = gw * (w0 * z0 + w1 * z1 + w2 * z2);                       // G d ln p / dm
+            zb = gw * (w0 * (e0 - 1.f) + w1 * (e1 - 1.f) + w2 * (e2 - 1.f));  // G d ln p / ds
+        }
+    }
     float mub = m1b;
     const float mudotb = m1b * dt;
     const float dDb = m1b * dt;
-    const float Db = D > 0.f ? m1b * zmu * dt * rsqrtf(2.f * D * dt) : 0.f;
+    const float Db = D > 0.f ? zb * dt * rsqrtf(2.f * D * dt) : 0.f;
     // u = V + mu v b
     const float ubb = ub[0] * b[0] + ub[1] * b[1] + ub[2] * b[2];
     float Vb[3] = {ub[0], ub[1], ub[2]};
@@ -394,7 +420,7 @@ __global__ void __launch_bounds__(256) adj_forward_kernel(const AdvanceArgs a, c
             const float r = sqrtf(x * x + y * y + z * z);
             J += (double)(w * a.prm.dt * smooth_k(k, r, p, time_arg(k, s), nullptr, nullptr));
             st = step<false, DT, kModeSingle, LAY>(a, a.prm, I, 0, s, pid, x, y, z, mu, p, w, nullptr, nullptr,
-                                              nullptr, sc, noor);
+                                              nullptr, sc, noor, 0);
             if (st != FTE_ALIVE) { ++s; break; }
         }
         // steps taken since the start of the run (a.n_table0), counting the one that ended it
@@ -459,7 +485,7 @@ __global__ void __launch_bounds__(256) adj_replay_kernel(const AdvanceArgs a, co
             sp[0] = x; sp[n] = y; sp[2 * n] = z; sp[3 * n] = mu; sp[4 * n] = p;
             if (s + 1 < e)
                 step<false, DT, kModeSingle, LAY>(a, a.prm, I, 0, s, pid, x, y, z, mu, p, w, nullptr, nullptr, nullptr,
-                                             sc, noor);
+                                             sc, noor, 0);
         }
         if (ce < e) {      // the start of the next chunk
             float* cp = k.carry + i;
@@ -499,27 +525,30 @@ __global__ void __launch_bounds__(256, 2) adj_back_kernel(const AdvanceArgs a, c
         for (int q = 0; q < 5; ++q) lam[q] = k.adj[q * n + i];
 #pragma unroll
         for (int q = 0; q < 4; ++q) gth[q] = k.adj[(5 + q) * n + i];
+        float Gacc = k.adj[9 * n + i];      // observable of the steps after the current one
         const float w = a.w[i];
         const uint32_t pid = a.id[i];
         for (long long s = min(ce, e) - 1; s >= cs; --s) {
             const float* sp = k.scratch + (size_t)(s - n0) * 5 * n + f;
             const float sx = sp[0], sy = sp[n], sz = sp[2 * n], smu = sp[3 * n], spp = sp[4 * n];
-            step_vjp<DT, LAY>(a, I, rq, rh, s, pid, sx, sy, sz, smu, spp, sc, lam, gth);
+            step_vjp<DT, LAY>(a, I, rq, rh, s, pid, sx, sy, sz, smu, spp, sc, Gacc, k.lr_window, lam, gth);
             // the observable's own term at the start-of-step state
             const float r = sqrtf(sx * sx + sy * sy + sz * sz);
             float dKdr, dKdp;
-            smooth_k(k, r, spp, time_arg(k, s), &dKdr, &dKdp);
+            const float Kv = smooth_k(k, r, spp, time_arg(k, s), &dKdr, &dKdp);
             const float fw = w * a.prm.dt;
             lam[0] += fw * dKdr * sx / r;
             lam[1] += fw * dKdr * sy / r;
             lam[2] += fw * dKdr * sz / r;
             lam[4] += fw * dKdp;
+            Gacc += fw * Kv;
         }
         if (!closing) {
 #pragma unroll
             for (int q = 0; q < 5; ++q) k.adj[q * n + i] = lam[q];
 #pragma unroll
             for (int q = 0; q < 4; ++q) k.adj[(5 + q) * n + i] = gth[q];
+            k.adj[9 * n + i] = Gacc;
             continue;
         }
         // first step of the run: injection index by the likelihood ratio of the injected energy

@@ -6,9 +6,13 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <atomic>
+#include <mutex>
 #include <new>
+#include <vector>
 
 #include "fte_kernels.cuh"
+#include "fte_probe.h"
 
 using namespace fte;
 
@@ -201,6 +205,7 @@ void fill_observers(const fte_tally_buf* t, AdvanceArgs* a)
         off += (size_t)ob.ne * ob.nt;
     }
     a->n_obs = t->n_obs;
+    a->cls = t->S_class;
 }
 
 // Layout of the fte_advance workspace.
@@ -242,6 +247,33 @@ size_t advance_sort_bytes(const GridK& g, unsigned long long n)
 
 // A second stream and the events that fork it from and join it back to the
 // caller's stream; released when the call returns (the device finishes the work).
+// Measurement aid (fte_probe_step_timing): a CUDA event before and after every
+// step-kernel launch of fte_advance, recorded on the stream of that launch, while
+// recording is on (and the stream is not being captured).
+struct StepTiming {
+    std::atomic<int> on{0};
+    std::mutex mu;
+    std::vector<cudaEvent_t> ev;    // start, stop of launch i at 2 i, 2 i + 1
+    int used = 0;
+};
+StepTiming g_timing;
+
+cudaError_t launch_advance_timed(const AdvanceArgs& a, int kperp, int mode, int blocks, size_t smem, cudaStream_t s,
+                                 bool capturing)
+{
+    if (!g_timing.on.load(std::memory_order_relaxed) || capturing)
+        return launch_advance(a, g_no_batch, kperp, mode, kThreads, blocks, smem, s);
+    std::lock_guard<std::mutex> lock(g_timing.mu);
+    const bool rec = g_timing.used + 2 <= (int)g_timing.ev.size();
+    if (rec) cudaEventRecord(g_timing.ev[g_timing.used], s);
+    const cudaError_t e = launch_advance(a, g_no_batch, kperp, mode, kThreads, blocks, smem, s);
+    if (rec) {
+        cudaEventRecord(g_timing.ev[g_timing.used + 1], s);
+        g_timing.used += 2;
+    }
+    return e;
+}
+
 struct SideStream {
     cudaStream_t s = nullptr;
     cudaEvent_t fork = nullptr, join = nullptr;
@@ -397,6 +429,9 @@ fte_status fte_tally_reset(const fte_tally_buf* t, void* stream)
         FTE_CUDA(cudaMemsetAsync(t->S2, 0, nb * sizeof(double), st), "memset S2");
         FTE_CUDA(cudaMemsetAsync(t->C, 0, nb * sizeof(unsigned long long), st), "memset C");
     }
+    if (t->S_class && t->n_obs)
+        FTE_CUDA(cudaMemsetAsync(t->S_class, 0, (size_t)(t->n_sets > 1 ? t->n_sets : 1) * t->n_obs * FTE_NCLASS *
+                                 sizeof(double), st), "memset S_class");
     FTE_CUDA(cudaMemsetAsync(t->ledger_w, 0, FTE_LEDGER * sizeof(double), st), "memset ledger");
     FTE_CUDA(cudaMemsetAsync(t->ledger_n, 0, FTE_LEDGER * sizeof(unsigned long long), st), "memset ledger");
     return FTE_OK;
@@ -469,6 +504,7 @@ fte_status fte_inject(fte_particles* P, const fte_background* bg, const fte_inje
     a.ph1 = (float)spec->ph1; a.ph2 = (float)spec->ph2; a.divv_max = (float)spec->divv_max;
     a.e0 = (float)spec->e0; a.e1 = (float)spec->e1; a.e2 = (float)spec->e2; a.gamma = (float)spec->gamma;
     a.mu0 = (float)spec->mu0;
+    a.spiral = (float)spec->spiral; a.spiral_rb = (float)spec->spiral_rb;
     a.seed = spec->seed; a.set_id = spec->set_id; a.id_base = spec->id_base;
     a.offset = P->count; a.n = n;
     a.x = P->x; a.y = P->y; a.z = P->z; a.mu = P->mu; a.p = P->p; a.w = P->w; a.id = P->id; a.status = P->status;
@@ -633,8 +669,7 @@ fte_status fte_advance(fte_particles* P, const fte_background* bg, const fte_par
                 ah[k].n_end = (c0 + chunk < n_end) ? c0 + chunk : n_end;
                 FTE_CUDA(launch_sort(sh[k], hs[k]), "sort launch");
                 FTE_CUDA(cudaMemsetAsync(ah[k].fetch, 0, sizeof(unsigned long long), hs[k]), "fetch reset");
-                FTE_CUDA(launch_advance(ah[k], g_no_batch, kperp, mode, kThreads, blocks, smem, hs[k]),
-                         "step kernel launch");
+                FTE_CUDA(launch_advance_timed(ah[k], kperp, mode, blocks, smem, hs[k], false), "step kernel launch");
             }
         }
         FTE_CUDA(cudaEventRecord(side.join, side.s), "join");
@@ -647,7 +682,8 @@ fte_status fte_advance(fte_particles* P, const fte_background* bg, const fte_par
         a.n_end = (c0 + chunk < n_end) ? c0 + chunk : n_end;
         if (sorting) FTE_CUDA(launch_sort(sa, st), "sort launch");
         FTE_CUDA(cudaMemsetAsync(a.fetch, 0, sizeof(unsigned long long), st), "fetch reset");
-        FTE_CUDA(launch_advance(a, g_no_batch, kperp, mode, kThreads, blocks, smem, st), "step kernel launch");
+        FTE_CUDA(launch_advance_timed(a, kperp, mode, blocks, smem, st, cap != cudaStreamCaptureStatusNone),
+                 "step kernel launch");
         if (nb && mode == kModeSingle)
             FTE_CUDA(launch_reduce(a.part, blocks, (int)nb, t->S, t->S2, t->C, st), "reduce launch");
     }
@@ -727,6 +763,61 @@ fte_status fte_tally_convolve(const fte_tally_buf* t, int set, int obs, int kind
     return copy_out(host_out, dev_out, n, st);
 }
 
+fte_status fte_probe_gather_l1(const void* buf, size_t bytes, int threads, int records, int spread,
+                               float* dev_out, void* stream)
+{
+    if (!buf || !dev_out) return fail(FTE_EINVAL, "NULL pointer");
+    if ((uintptr_t)buf % 32) return fail(FTE_EINVAL, "buffer must be 32-byte aligned");
+    const unsigned long long nrec = bytes / (FTE_REC * sizeof(float));
+    if (nrec < 64) return fail(FTE_EINVAL, "buffer holds %llu records, fewer than 64", nrec);
+    if (spread < 1 || spread > 32) return fail(FTE_EINVAL, "spread must be in [1, 32]");
+    if (threads < 256 || threads % 256 || records < 1)
+        return fail(FTE_EINVAL, "threads must be a multiple of 256, records >= 1");
+    FTE_CUDA(launch_probe_l1((const float*)buf, (unsigned)nrec, threads, records, spread, dev_out,
+                             (cudaStream_t)stream), "probe launch");
+    return FTE_OK;
+}
+
+fte_status fte_probe_step_timing(int capacity)
+{
+    if (capacity < 0 || capacity > (1 << 20)) return fail(FTE_EINVAL, "capacity must be in [0, 2^20]");
+    std::lock_guard<std::mutex> lock(g_timing.mu);
+    g_timing.on.store(0);
+    for (cudaEvent_t e : g_timing.ev) cudaEventDestroy(e);
+    g_timing.ev.clear();
+    g_timing.used = 0;
+    if (capacity == 0) return FTE_OK;
+    g_timing.ev.resize(2 * (size_t)capacity, nullptr);
+    for (auto& e : g_timing.ev) {
+        const cudaError_t r = cudaEventCreate(&e);
+        if (r != cudaSuccess) {
+            for (cudaEvent_t x : g_timing.ev)
+                if (x) cudaEventDestroy(x);
+            g_timing.ev.clear();
+            return cuda_fail(r, "cudaEventCreate");
+        }
+    }
+    g_timing.on.store(1);
+    return FTE_OK;
+}
+
+fte_status fte_probe_step_intervals(double* host_ms, int capacity, int* count)
+{
+    if (!count || (capacity > 0 && !host_ms)) return fail(FTE_EINVAL, "NULL pointer");
+    std::lock_guard<std::mutex> lock(g_timing.mu);
+    const int n = g_timing.used / 2;
+    *count = n;
+    if (n > capacity) return fail(FTE_ENOMEM, "%d launches recorded, room for %d", n, capacity);
+    for (int i = 0; i < 2 * n; ++i) FTE_CUDA(cudaEventSynchronize(g_timing.ev[i]), "event synchronize");
+    for (int i = 0; i < 2 * n; ++i) {
+        float ms = 0.f;
+        FTE_CUDA(cudaEventElapsedTime(&ms, g_timing.ev[0], g_timing.ev[i]), "event elapsed");
+        host_ms[i] = ms;
+    }
+    g_timing.used = 0;
+    return FTE_OK;
+}
+
 fte_status fte_probe_sectors(const void* buf, size_t bytes, int threads, int loads, float* dev_out,
                              void* stream)
 {
@@ -774,7 +865,10 @@ std::mutex g_noalloc_mu;
 void* g_noalloc_ptr[64];
 
 // Device address of the scratch array for the current device, looked up once
-// per device (the host-side name of the array is not a device address).
+// per device (the host-side name of the array is not a device address).  The
+// address belongs to the device's primary context: after cudaDeviceReset (or
+// any teardown of that context) it is no longer valid, and this process must
+// not call fte_advance_noalloc on that device again.
 fte_status noalloc_scratch(int device, char** out)
 {
     if (device < 0 || device >= 64) return fail(FTE_ENOTSUP, "device index %d out of range", device);
@@ -810,6 +904,10 @@ extern "C" fte_status fte_advance_noalloc(fte_particles* P, const fte_background
     if (prm->dmumu == 0 && !(prm->q > 1.0 && prm->q <= 2.0 && prm->H >= 0.0)) return fail(FTE_EINVAL, "need 1 < q <= 2, H >= 0");
     if (prm->dmumu == 1 && !(prm->eps > 0.0)) return fail(FTE_EINVAL, "eps must be > 0");
     if (prm->lambda_perp < 0.0) return fail(FTE_EINVAL, "lambda_perp must be >= 0");
+    // the tally always goes through per-block shared-memory histograms here; other layout
+    // values are refused as fte_advance refuses them
+    if (prm->tally_layout != 0 && prm->tally_layout != FTE_LAYOUT_SHARED && prm->tally_layout != FTE_LAYOUT_GLOBAL)
+        return fail(FTE_EINVAL, "bad tally_layout %d", prm->tally_layout);
     if (!P->x || !P->y || !P->z || !P->mu || !P->p || !P->w || !P->id || !P->status)
         return fail(FTE_EINVAL, "NULL particle array");
 
@@ -1380,6 +1478,9 @@ namespace {
 
 // Steps per reverse-pass launch (the reordering interval of the reverse pass).
 constexpr long long kAdjChunk = 64;
+// Per-particle values carried between reverse launches: state adjoint (5), parameter
+// adjoint (4), observable accumulated after the current step (1).
+constexpr int kAdjRows = 10;
 
 struct AdjLayout {
     size_t off_fetch, off_norm, off_npart, off_normd, off_ndpart, off_table, off_ckpt, off_ndead, off_jpart,
@@ -1419,7 +1520,7 @@ fte_status adj_layout(int device, const fte_grid* g, unsigned long long n, long 
     L->off_ckpt = take((size_t)L->nseg * 5 * nn * sizeof(float));
     L->off_ndead = take(nn * sizeof(int));
     L->off_jpart = take(nn * sizeof(double));
-    L->off_adj = take(9 * nn * sizeof(float));
+    L->off_adj = take(kAdjRows * nn * sizeof(float));
     L->off_scratch = take((size_t)K * 5 * nn * sizeof(float));    // a segment's states, per particle
     L->off_carry = take(5 * nn * sizeof(float));
     const long long nch = sorting ? (K + kAdjChunk - 1) / kAdjChunk : 1;
@@ -1448,6 +1549,7 @@ fte_status adj_check(const fte_particles* P, const fte_background* bg, const fte
     if (prm->p_ref > 0.0 && prm->alpha != 0.0) return fail(FTE_ENOTSUP, "the adjoint needs lambda independent of p");
     if (!(obs->sigma_r > 0.0 && obs->sigma_lnE > 0.0 && obs->sigma_t > 0.0 && obs->e_c > 0.0))
         return fail(FTE_EINVAL, "observable widths and e_c must be > 0");
+    if (!(obs->lr_window <= 1e30)) return fail(FTE_EINVAL, "lr_window must be finite");
     if (K < 1 || K > 65536) return fail(FTE_EINVAL, "checkpoint_every must be in [1, 65536]");
     if (n_end < n_start || n_start < 0) return fail(FTE_EINVAL, "need 0 <= n_start <= n_end");
     if (n_end - n_start > 0x7FFFFFFFll) return fail(FTE_EINVAL, "more than 2^31 - 1 steps");
@@ -1511,6 +1613,7 @@ fte_status adj_args(const fte_particles* P, const fte_background* bg, const fte_
     k->t_c = obs->t_c; k->inv_st = 1.0 / obs->sigma_t; k->t0 = prm->t0; k->dt = prm->dt;
     k->c0 = (float)((prm->t0 - obs->t_c) / obs->sigma_t);
     k->cstep = (float)(prm->dt / obs->sigma_t);
+    k->lr_window = obs->lr_window < 0.0 ? (prm->dmumu == 2 ? 0.f : 4.f) : (float)obs->lr_window;
     return FTE_OK;
 }
 
@@ -1540,7 +1643,7 @@ size_t fte_adjoint_workspace_bytes(int device, const fte_grid* g, uint64_t n_par
 
 fte_status fte_adjoint_forward(fte_particles* P, const fte_background* bg, const fte_params* prm,
                                const fte_smooth_obs* obs, int64_t n_start, int64_t n_end, int checkpoint_every,
-                               double* dev_out, void* ws, size_t ws_bytes, void* stream)
+                               double* dev_out, double* dev_J_particle, void* ws, size_t ws_bytes, void* stream)
 {
     fte_status s = adj_check(P, bg, prm, obs, n_start, n_end, checkpoint_every, ws);
     if (s != FTE_OK) return s;
@@ -1588,6 +1691,9 @@ fte_status fte_adjoint_forward(fte_particles* P, const fte_background* bg, const
             FTE_CUDA(launch_adjoint_forward(a, k, L.fwd_blocks, st), "adjoint forward launch");
         }
     }
+    if (dev_J_particle)
+        FTE_CUDA(cudaMemcpyAsync(dev_J_particle, k.J_part, P->count * sizeof(double), cudaMemcpyDeviceToDevice, st),
+                 "per-particle observable copy");
     return FTE_OK;
 }
 
@@ -1624,7 +1730,7 @@ fte_status fte_adjoint_reverse(const fte_particles* P, const fte_background* bg,
     if (dev_per_particle)
         FTE_CUDA(cudaMemsetAsync(dev_per_particle, 0, P->count * (1 + FTE_NGRAD) * sizeof(float), st),
                  "per-particle reset");
-    FTE_CUDA(cudaMemsetAsync(k.adj, 0, 9 * P->count * sizeof(float), st), "adjoint reset");
+    FTE_CUDA(cudaMemsetAsync(k.adj, 0, kAdjRows * P->count * sizeof(float), st), "adjoint reset");
     const size_t n = P->count;
     SortArgs sa;
     memset(&sa, 0, sizeof(sa));

@@ -1,7 +1,7 @@
 // Injection kernel (Sec. 2.3, Eq. 7): one thread per particle, counter-based
 // draws (tag 1: pitch-angle cosine and energy; tag 2: position attempt a),
-// volume-uniform positions with optional div V < 0 acceptance on the stored
-// cell values, weight 1 or 1/r^2.
+// volume-uniform positions (optionally in a band of spiral phase) with optional
+// div V < 0 acceptance on the stored cell values, weight 1 or 1/r^2.
 #include "fte_kernels.cuh"
 
 namespace fte {
@@ -54,6 +54,7 @@ __global__ void __launch_bounds__(256) inject_kernel(const InjectArgs a)
                 r = cbrtf(r13 + u01(q.x) * (r23 - r13));
                 th = acosf(c1 + u01(q.y) * (c2 - c1));
                 ph = a.ph1 + u01(q.z) * (a.ph2 - a.ph1);
+                if (a.spiral != 0.f) ph -= a.spiral * (r - a.spiral_rb);   // spiral phase -> longitude
                 if (!a.use_divv) { ok = true; break; }
                 const GridK& g = a.g;
                 float phw = fmodf(ph, kTwoPi);

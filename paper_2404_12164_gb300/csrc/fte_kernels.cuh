@@ -49,6 +49,7 @@ struct AdvanceArgs {
     unsigned long long* fetch;    // particle counter for dynamic assignment
     double* ledger_w;
     unsigned long long* ledger_n;
+    double* cls;                  // optional [set][obs][FTE_NCLASS] observer totals by particle-id class
 };
 
 struct SortArgs {
@@ -93,6 +94,7 @@ struct InjectArgs {
     GridK g;
     int n_snap, region, energy, weight, mu_mode, use_divv, divv_snap, max_tries;
     float r, th, ph, r1, r2, th1, th2, ph1, ph2, divv_max, e0, e1, e2, gamma, mu0;
+    float spiral, spiral_rb;      // box: longitude = sampled spiral phase - spiral (r - spiral_rb)
     uint32_t seed, set_id, id_base;
     unsigned long long offset, n;
     float *x, *y, *z, *mu, *p, *w;
@@ -121,7 +123,10 @@ struct AdjK {
     float* scratch;               // [K][5][n]: replayed start-of-step states of the segment, at
                                   // each particle's position in its chunk's order (coalesced)
     float* carry;                 // [5][n]: state at the start of the next chunk, by particle
-    float* adj;                   // [9][n]: state adjoint (5) and parameter adjoint (4) between segments
+    float* adj;                   // [10][n]: state adjoint (5), parameter adjoint (4) and the observable
+                                  // accumulated after the current step (the score terms' weight), between launches
+    float lr_window;              // score form for steps whose pitch-angle mean is within this many widths
+                                  // of a value landing at mu = 0 (0: pathwise everywhere)
     int* n_dead;                  // [n]: steps each particle took (alive at their start)
     double* J_part;               // [n]: each particle's observable
     double* out;                  // [1 + FTE_NGRAD]: J, then the gradients
@@ -181,6 +186,8 @@ cudaError_t launch_amr_table(const GridK& g, int* table, unsigned* status, cudaS
 cudaError_t launch_amr_ghosts(const GridK& g, int n_snap, double r_min, double r_max, double th_min,
                               double th_max, cudaStream_t s);
 // random-sector read probe (fte_probe.cu)
+cudaError_t launch_probe_l1(const float* buf, unsigned nrec, int threads, int records, int spread, float* out,
+                            cudaStream_t s);
 cudaError_t launch_probe(const float* buf, unsigned long long nsec, int threads, int loads, float* out,
                          cudaStream_t s);
 // storage conversion of `nrec` FP32 cell records (r-rows of `row` cells): 16-bit

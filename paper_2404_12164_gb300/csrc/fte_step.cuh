@@ -59,6 +59,15 @@ __device__ __forceinline__ void warp_tally_global(double* S, double* S2, unsigne
     }
 }
 
+// Observer totals by particle-id class (batch means of the occupancy estimator):
+// every tallied step also adds w dt to the total of its observer, set and
+// particle-id class (cbase = set * n_obs).  Tallied steps are a small fraction of
+// all steps, so one FP64 atomic each costs nothing measurable and no registers.
+__device__ __forceinline__ void class_add(const AdvanceArgs& a, int cbase, int o, uint32_t pid, float wdt)
+{
+    atomicAdd(a.cls + ((size_t)(cbase + o) * FTE_NCLASS + (pid % FTE_NCLASS)), (double)wdt);
+}
+
 // One Euler-Maruyama step of Eqs. 2-4 for one particle (Sec. 2.1), with the
 // background interpolated at the start-of-step position and time (Sec. 2.4).
 template <bool KPERP, int DT, int MODE, int LAY>
@@ -66,7 +75,7 @@ __device__ __forceinline__ int step(const AdvanceArgs& a, const ParamsK& prm, fl
                                     long long n, uint32_t pid,
                                     float& x, float& y, float& z, float& mu, float& p, float w,
                                     float* shS, float* shS2, unsigned* shC, const float* sc,
-                                    unsigned long long& noor)
+                                    unsigned long long& noor, int cbase)
 {
     const StepEntry* ep = a.table + (n - a.n_table0);
     StepEntry e;
@@ -193,10 +202,12 @@ __device__ __forceinline__ int step(const AdvanceArgs& a, const ParamsK& prm, fl
                 const float le = logf(energy_of(p) / ob.e_lo) * ob.ne_over_lnratio;
                 int it = __ldg(&ep->it[o]);     // time bin, -1 outside [t_lo, t_hi)
                 if (ob.kind == 3 && it >= 0) it = min((int)(ph * ob.phi_scale), ob.nt - 1);
-                if (le >= 0.f && le < (float)ob.ne && it >= 0)
+                if (le >= 0.f && le < (float)ob.ne && it >= 0) {
                     bin = sbin + ob.off + (int)le * ob.nt + it;
-                else
+                    if (a.cls) class_add(a, cbase, o, pid, w * dt);
+                } else {
                     ++noor;
+                }
             }
             if (global_tally(MODE)) warp_tally_global(a.gS, a.gS2, a.gC, bin, w * dt);
             else warp_tally(shS, shS2, shC, bin, w * dt);
@@ -281,7 +292,8 @@ __global__ void __launch_bounds__(NT, single_set(MODE) ? MINB : 512 / NT) advanc
         if (single_set(MODE)) {
             for (long long n = a.n_start; n < a.n_end; ++n) {
                 ++nsteps;
-                st = step<KPERP, DT, MODE, LAY>(a, a.prm, I0, 0, n, pid, x, y, z, mu, p, w, shS, shS2, shC, sc, noor);
+                st = step<KPERP, DT, MODE, LAY>(a, a.prm, I0, 0, n, pid, x, y, z, mu, p, w, shS, shS2, shC, sc, noor,
+                                                0);
                 if (st != FTE_ALIVE) break;
             }
         } else {
@@ -296,9 +308,11 @@ __global__ void __launch_bounds__(NT, single_set(MODE) ? MINB : 512 / NT) advanc
             prm.set_id = s_set[s].set_id;
             const float I = s_I[s];
             const int sbin = s * a.nbins;
+            const int cbase = s * a.n_obs;
             for (long long n = a.n_start; n < a.n_end; ++n) {
                 ++nsteps;
-                st = step<KPERP, DT, MODE, LAY>(a, prm, I, sbin, n, pid, x, y, z, mu, p, w, shS, shS2, shC, sc, noor);
+                st = step<KPERP, DT, MODE, LAY>(a, prm, I, sbin, n, pid, x, y, z, mu, p, w, shS, shS2, shC, sc, noor,
+                                                cbase);
                 if (st != FTE_ALIVE) break;
             }
         }

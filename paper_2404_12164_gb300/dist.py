@@ -12,11 +12,15 @@ def id_base(rank, n_per_rank):
 
 
 def reduce_tally(tally):
-    """Sum S, S2, C and both ledgers over the ranks, in place (every rank gets the totals).
-    `tally` has tensors S, S2, C, ledger_w, ledger_n (api.Tally or any object with them)."""
+    """Sum S, S2, C, both ledgers and the class totals S_class (when present) over the ranks,
+    in place (every rank gets the totals).  `tally` has tensors S, S2, C, ledger_w, ledger_n
+    (api.Tally or any object with them)."""
     if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
         return tally
-    for t in (tally.S, tally.S2, tally.C, tally.ledger_w, tally.ledger_n):
+    ts = [tally.S, tally.S2, tally.C, tally.ledger_w, tally.ledger_n]
+    if getattr(tally, "S_class", None) is not None:
+        ts.append(tally.S_class)
+    for t in ts:
         dist.all_reduce(t)
     return tally
 

@@ -1,4 +1,4 @@
-"""The C-ABI library loads and exports every entry point include/fte.h declares;
+"""The C-ABI library loads and exports every entry point include/*.h declares;
 host-side argument checks that return before any CUDA call work without a GPU."""
 import ctypes as C
 import math
@@ -8,14 +8,16 @@ import re
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADER = os.path.join(ROOT, "include", "fte.h")
+HEADERS = [os.path.join(ROOT, "include", h) for h in sorted(os.listdir(os.path.join(ROOT, "include")))
+           if h.endswith(".h")]
 
 
 def _declared():
-    src = open(HEADER).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    names = re.findall(r"\b(fte_[a-z_]+)\s*\(", src)
-    return sorted(set(names))
+    names = set()
+    for h in HEADERS:
+        src = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        names.update(re.findall(r"\b(fte_[a-z_0-9]+)\s*\(", src))
+    return sorted(names)
 
 
 @pytest.fixture(scope="module")
@@ -36,7 +38,7 @@ def test_every_declared_symbol_is_exported(L):
 
 
 def test_version_and_status_strings(L):
-    assert L.fte_abi_version() == 2
+    assert L.fte_abi_version() == 3
     assert L.fte_status_string(0) == b"ok"
     assert L.fte_status_string(1) == b"invalid argument"
 
@@ -46,7 +48,9 @@ def test_struct_sizes_match_header_layout():
     assert C.sizeof(A.fte_grid) == 4 * 4 + 4 * 8 + 2 * 4 + 2 * 8 + 6 * 4
     assert C.sizeof(A.fte_observer) == 4 * 4 + 10 * 8
     assert C.sizeof(A.fte_params) == 4 * 4 + 10 * 8 + 4 * 4
-    assert C.sizeof(A.fte_inject_spec) == 4 * 4 + 9 * 8 + 4 * 4 + 6 * 8 + 4 * 4
+    assert C.sizeof(A.fte_inject_spec) == 4 * 4 + 9 * 8 + 4 * 4 + 6 * 8 + 4 * 4 + 2 * 8
+    assert C.sizeof(A.fte_smooth_obs) == 7 * 8
+    assert C.sizeof(A.fte_tally_buf) == 2 * 4 + A.FTE_MAX_OBS * C.sizeof(A.fte_observer) + 6 * 8
 
 
 def test_background_bytes_and_grid_validation(L):

@@ -1,8 +1,9 @@
 """The multi-process path on CPU (gloo, world size 2): each rank advances its own
 batch with disjoint particle ids, the tallies and ledgers are summed over the
 ranks, and the step time is the slowest rank's.  The per-rank work here is the
-FP64 oracle, so the reduced tallies must equal one oracle run over both batches
-(counts exactly, sums to rounding)."""
+FP64 oracle, so the reduced tallies (and the observer totals by particle-id
+class) must equal one oracle run over both batches (counts exactly, sums to
+rounding)."""
 import math
 import os
 import socket
@@ -52,10 +53,12 @@ def _rank_main(rank, world, port, out_dir):
     t.C = torch.tensor(T.C.astype(np.int64))
     t.ledger_w = torch.tensor(np.asarray(L["w"], dtype=np.float64))
     t.ledger_n = torch.tensor(np.asarray(L["n"], dtype=np.int64))
+    t.S_class = torch.tensor(T.SC)
     pdist.reduce_tally(t)
     (slowest,) = pdist.max_over_ranks([10.0 + rank])
     if rank == 0:
         np.savez(os.path.join(out_dir, "reduced.npz"), S=t.S.numpy(), S2=t.S2.numpy(), C=t.C.numpy(),
+                 SC=t.S_class.numpy(),
                  lw=t.ledger_w.numpy(), ln=t.ledger_n.numpy(), slowest=slowest)
     dist.barrier()
     dist.destroy_process_group()
@@ -80,6 +83,8 @@ def test_two_ranks_equal_one_run(tmp_path):
     assert np.array_equal(got["C"], T.C.astype(np.int64))
     assert np.allclose(got["S"], T.S, rtol=1e-12, atol=0)
     assert np.allclose(got["S2"], T.S2, rtol=1e-12, atol=0)
+    # observer totals by particle-id class (batch means of the total) sum over ranks too
+    assert np.allclose(got["SC"], T.SC, rtol=1e-12, atol=0) and T.SC.sum() > 0
     assert np.array_equal(got["ln"], np.asarray(L["n"], dtype=np.int64))
     assert np.allclose(got["lw"], L["w"], rtol=1e-12)
     assert int(got["ln"][0]) == 2 * N_PER_RANK

@@ -1,18 +1,24 @@
-"""Pathwise adjoint on the GPU against the FP64 oracle.
+"""Adjoint on the GPU against the FP64 oracle.
 
 The observable J = sum_i w_i sum_n dt K(r_n, E_n, t_n) (Gaussians in r, ln E, t)
-is a smooth function of each particle's path; with the Philox noise fixed, the
-path is a piecewise-smooth function of (lambda_par, q, H, eps).  Checks:
+is a smooth function of each particle's path.  The gradient is pathwise (Philox
+noise held) except at steps whose pitch-angle Gaussian reaches mu = 0, which
+enter in the score form (mu' held, its transition density differentiated); with
+the default window that is every such step of Eq. 5 and the quasi-linear form and
+none of the isotropic form.  Checks:
 
 * J per particle equals the oracle's (the forward pass is the transport);
-* per-particle gradients equal central finite differences of the FP64 oracle
-  (step 1e-6 relative, same noise) for trajectories the oracle records no
-  divergence event for, for all three D_mumu forms;
+* per-particle gradients equal the FP64 oracle's estimate of the same form
+  (or_observe_lr: central differences of the density-reweighted observable with
+  the same held values and noise) on particles whose GPU and oracle end states
+  agree and whose gate decisions are not within rounding of the window's edge,
+  for all three D_mumu forms;
 * dJ/dgamma equals the finite difference of the likelihood-ratio weights of
   the injected energies (normalisation by numerical quadrature);
-* for the isotropic D_mumu (smooth in mu) the total gradient agrees with
-  central differences of the GPU forward pass with common random numbers; the
-  checkpoint interval changes nothing;
+* for all three forms the total gradient agrees with central differences of the
+  GPU forward pass with common random numbers within their statistical errors
+  (batch means over 32 particle-id classes); the checkpoint interval changes
+  nothing;
 * torch.autograd through SmoothIntensity returns the adjoint gradient.
 """
 import dataclasses
@@ -53,7 +59,7 @@ def cir_small():
 OBS = SmoothObserver(r_o=1.15, sigma_r=0.05, e_c=0.08, sigma_lnE=0.5, t_c=1500.0, sigma_t=1000.0)
 
 
-def _gpu(w, f, prm, n, steps, K=64, per_particle=True):
+def _gpu(w, f, prm, n, steps, K=64, per_particle=True, obs=OBS):
     import torch
     from paper_2404_12164_gb300 import api
     bg = api.Background(w.grid)
@@ -62,7 +68,7 @@ def _gpu(w, f, prm, n, steps, K=64, per_particle=True):
     tally = api.Tally([])
     api.fte_tally_reset(tally)
     api.fte_inject(pool, bg, w.inject, n, tally, id_base=0)
-    adj = api.Adjoint(bg, prm, OBS, 0, steps, K)
+    adj = api.Adjoint(bg, prm, obs, 0, steps, K)
     J = adj.forward(pool)
     g, pp = adj.reverse(pool, w.inject, per_particle=True)
     torch.cuda.synchronize()
@@ -82,32 +88,43 @@ MODELS = [
     ("iso", Params(dmumu="iso", lambda_par=0.1, dt=10.0), ("lambda_par",)),
 ]
 GI = {"lambda_par": 1, "q": 2, "H": 3, "eps": 4}
+WINDOW = {"qlt": 4.0, "paper": 4.0, "iso": 0.0}      # the library's default window per form
+
+
+def _batch_sigma(x, ids, nb=32):
+    """Standard error of sum(x) from the sums over nb classes of particle id."""
+    s = np.bincount(ids % nb, weights=x, minlength=nb)
+    return math.sqrt(nb * s.var(ddof=1))
 
 
 @pytest.mark.parametrize("name,prm,names", MODELS, ids=[m[0] for m in MODELS])
-def test_gradients_match_oracle_finite_differences(cir_small, name, prm, names):
+def test_gradients_match_oracle(cir_small, name, prm, names):
     w, f = cir_small
     n, steps = 4000, 200
-    J, g, pp, _ = _gpu(w, f, prm, n, steps)
-    Jo, Po = _oracle_J(w, f, prm, n, steps)
-    clean = Po["n_div"] < 0
-    print(f"{name}: {clean.sum()} of {n} trajectories without a divergence event")
-    assert clean.sum() >= 400
+    J, g, pp, st = _gpu(w, f, prm, n, steps)
+    bg = O.grid_background(w.grid, f)
+    P, _ = O.inject(bg, w.inject, np.arange(n, dtype=np.uint32))
+    Jo, Go, fl = O.observe_lr(bg, prm, P, 0, steps, OBS, WINDOW[name], names)
+    # trajectories that FP32 and FP64 computed alike: same status, end states within 1e-4, no
+    # 100-fold amplification of mu differences by the pitch-angle map on the way, and no gate
+    # decision, mu = 0 passage or end step within rounding of a decision
+    same = (st["status"] == P["status"]) & (fl == 0) & (P["n_sens"] < 0)
+    for key, tol in (("x", 1e-4), ("y", 1e-4), ("z", 1e-4), ("mu", 1e-4)):
+        same &= np.abs(st[key].astype(np.float64) - P[key]) <= tol
+    same &= np.abs(st["p"].astype(np.float64) - P["p"]) <= 1e-4 * P["p"]
+    print(f"{name}: {same.sum()} of {n} trajectories agree end to end")
+    assert same.sum() >= 0.5 * n
     # the forward observable, particle by particle
     scale = np.abs(Jo).max()
-    assert np.all(np.abs(pp[clean, 0] - Jo[clean]) <= 1e-4 * np.abs(Jo[clean]) + 1e-6 * scale)
+    assert np.all(np.abs(pp[same, 0] - Jo[same]) <= 1e-4 * np.abs(Jo[same]) + 1e-6 * scale)
     assert J == pytest.approx(pp[:, 0].astype(np.float64).sum(), rel=1e-5)
     for nm in names:
-        v0 = getattr(prm, nm)
-        h = 1e-6 * v0
-        Jp, _ = _oracle_J(w, f, dataclasses.replace(prm, **{nm: v0 + h}), n, steps)
-        Jm, _ = _oracle_J(w, f, dataclasses.replace(prm, **{nm: v0 - h}), n, steps)
-        fd = (Jp - Jm) / (2 * h)
+        ref = Go[nm]
         ga = pp[:, GI[nm]].astype(np.float64)
-        gscale = np.abs(fd[clean]).max()
-        err = np.abs(ga[clean] - fd[clean]) / (np.abs(fd[clean]) + 1e-3 * gscale)
+        gscale = np.abs(ref[same]).max()
+        err = np.abs(ga[same] - ref[same]) / (np.abs(ref[same]) + 1e-3 * gscale)
         print(f"{name} d/d{nm}: median rel err {np.median(err):.2e}, 99% {np.percentile(err, 99):.2e}, "
-              f"max {err.max():.2e}, total adjoint {g[GI[nm] - 1]:.6e} vs FD over all {fd.sum():.6e}")
+              f"max {err.max():.2e}; total adjoint {g[GI[nm] - 1]:.6e}, oracle {ref.sum():.6e}")
         assert np.median(err) < 1e-3, nm
         assert np.percentile(err, 95) < 1e-2, nm
 
@@ -158,22 +175,33 @@ def test_spatial_ordering_changes_nothing(cir_small):
     assert np.allclose(g0, g1, rtol=1e-9, atol=0)
 
 
-def test_total_matches_gpu_finite_differences(cir_small):
-    """Sum over many particles against central differences of the GPU forward pass with
-    common random numbers, for the isotropic D_mumu, whose coefficients are smooth in mu.
-    (Eq. 5's drift jumps at mu = 0 and the quasi-linear drift with q < 2 is singular
-    there: paths crossing mu = 0 then add a part to dE[J]/dtheta that no pathwise
-    derivative sees, so for those forms only the per-particle agreement is asserted.)"""
+@pytest.mark.parametrize("name,prm,names", MODELS, ids=[m[0] for m in MODELS])
+def test_total_matches_gpu_finite_differences(cir_small, name, prm, names):
+    """Sum over many particles against central differences (2 % of each parameter) of
+    the GPU forward pass with common random numbers, within 4 combined standard errors
+    (batch means over 32 particle-id classes).  The pathwise-only total (window 0) is
+    printed beside it; the oracle's exact-derivative pins show its bias."""
     w, f = cir_small
-    name, prm, names = MODELS[2]
-    n, steps = 20000, 400
-    J, g, _, _ = _gpu(w, f, prm, n, steps)
-    h = 1e-3 * prm.lambda_par
-    Jp = _gpu(w, f, dataclasses.replace(prm, lambda_par=prm.lambda_par + h), n, steps)[0]
-    Jm = _gpu(w, f, dataclasses.replace(prm, lambda_par=prm.lambda_par - h), n, steps)[0]
-    fd = (Jp - Jm) / (2 * h)
-    print(f"{name} total d/dlambda_par: adjoint {g[0]:.6e}, GPU central difference {fd:.6e}")
-    assert g[0] == pytest.approx(fd, rel=1e-2)
+    n, steps = 40000, 400
+    J, g, pp, st = _gpu(w, f, prm, n, steps)
+    ids = np.arange(n)
+    for nm in names:
+        v0 = getattr(prm, nm)
+        h = 2e-2 * v0
+        Jp = _gpu(w, f, dataclasses.replace(prm, **{nm: v0 + h}), n, steps)[2][:, 0].astype(np.float64)
+        Jm = _gpu(w, f, dataclasses.replace(prm, **{nm: v0 - h}), n, steps)[2][:, 0].astype(np.float64)
+        fd = (Jp - Jm) / (2 * h)
+        ga = pp[:, GI[nm]].astype(np.float64)
+        sa, sf = _batch_sigma(ga, ids), _batch_sigma(fd, ids)
+        band = 4 * math.sqrt(sa * sa + sf * sf)
+        print(f"{name} total d/d{nm}: adjoint {ga.sum():.6e} +- {sa:.2e}, GPU central difference "
+              f"{fd.sum():.6e} +- {sf:.2e}")
+        assert g[GI[nm] - 1] == pytest.approx(ga.sum(), rel=1e-4, abs=1e-6 * abs(ga).sum())
+        assert abs(ga.sum() - fd.sum()) < band, nm
+        if name != "iso":
+            g0 = _gpu(w, f, prm, n, steps, obs=dataclasses.replace(OBS, lr_window=0.0))[2][:, GI[nm]]
+            g0 = g0.astype(np.float64)
+            print(f"{name} total d/d{nm}: pathwise only {g0.sum():.6e} +- {_batch_sigma(g0, ids):.2e}")
 
 
 def test_autograd_function(cir_small):

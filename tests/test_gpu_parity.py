@@ -85,6 +85,25 @@ def test_injection_box_divv(cir_small):
     assert gr["ledger_w"][0] == pytest.approx(orr["ledger_w"][0], rel=1e-5)
 
 
+def test_injection_spiral_band():
+    """The block-AMR workload's injection (a band of spiral phase from 0.12 to 2 au) on a
+    uniform grid of the same wind: positions to 1e-5, mu bit-exact, weights and ledger."""
+    w = configs.scaled(configs.cir_uniform_1e6(), nr=128, nth=30, nph=90, n_snap=2, n_particles=20000)
+    w.inject = configs.cir_amr_1e7().inject
+    f = configs.build_background(w)
+    gr = gpu_run(w, f, 0, chunks=[])
+    orr = oracle_run(w, f, 0, chunks=[])
+    g, o = gr["states"][0], orr["states"][0]
+    assert gr["failed"] == 0
+    r_o = np.sqrt(o["x"] ** 2 + o["y"] ** 2 + o["z"] ** 2)
+    dx = np.sqrt((g["x"] - o["x"]) ** 2 + (g["y"] - o["y"]) ** 2 + (g["z"] - o["z"]) ** 2) / r_o
+    assert dx.max() < 1e-5
+    assert np.abs(g["w"] - o["w"]).max() / o["w"].max() < 1e-5
+    assert np.array_equal(g["mu"], o["mu"].astype(np.float32))
+    assert gr["ledger_w"][0] == pytest.approx(orr["ledger_w"][0], rel=1e-5)
+    assert r_o.min() < 0.2 and r_o.max() > 1.9
+
+
 def test_trajectories_parker_qlt(parker):
     w, f = parker
     chunks = [1, 10, 60, 250, 700]
@@ -151,6 +170,11 @@ def test_counts_exact_for_deterministic_trajectories():
         assert np.all(np.abs(Cg - Co) <= amb), np.abs(Cg - Co).max()
         assert np.array_equal(Cg[amb == 0], Co[amb == 0])
         assert np.abs(Cg - Co).sum() <= 2 * A.sum()
+        # observer totals by particle-id class: the same steps in the same classes (weights are
+        # 1 here, so a class total is dt times its tallied steps), up to the ambiguous events
+        cg, co = g["S_class"][k], o["S_class"][k]
+        assert cg.sum() == pytest.approx(g["tallies"][k]["S"].sum(), rel=1e-6)
+        assert np.abs(cg - co).sum() <= 2 * A.sum() * w.params.dt + 1e-6 * co.sum()
 
 
 def test_tallies_within_three_sigma(parker):
@@ -169,6 +193,14 @@ def test_tallies_within_three_sigma(parker):
     # total occupancy agrees to a few per cent of its own statistical error
     tot_sig = math.sqrt(tg["S2"].sum() + to["S2"].sum())
     assert abs(tg["S"].sum() - to["S"].sum()) < 3 * tot_sig
+    # class totals (batch means): they add up to the total, and the two batch-means errors
+    # of the total, from the same Philox streams, agree
+    cg, co = g["S_class"][0], o["S_class"][0]
+    assert cg.sum() == pytest.approx(tg["S"].sum(), rel=1e-6)
+    bm_g = math.sqrt(32 * cg.var(ddof=1))
+    bm_o = math.sqrt(32 * co.var(ddof=1))
+    assert abs(cg.sum() - co.sum()) < 3 * math.hypot(bm_g, bm_o)
+    assert 0.7 < bm_g / bm_o < 1.4
 
 
 def test_ledger_conservation(cir_small):

@@ -58,6 +58,28 @@ def test_box_volume_uniform_and_weights():
     assert led.as_dict()["w"][0] == pytest.approx(P["w"].sum(), rel=1e-12)
 
 
+def test_spiral_band_volume_uniform():
+    """A box whose longitude range bounds the spiral phase phi_hat = phi + k (r - r_b)
+    (the one-CIR region criterion of Sec. 2.3): r^3, cos(theta) and phi_hat are uniform, so
+    the band is filled uniformly in volume, and at fixed r the longitudes lie on the
+    sheared interval."""
+    bg = O.analytic_background("uniform_b", [5.0])
+    k, rb = 0.8, 0.1
+    spec = InjectSpec(region="box", r1=0.12, r2=2.0, th1=88 * DEG, th2=92 * DEG, ph1=4.5, ph2=4.9,
+                      spiral=k, spiral_rb=rb, weight="r-2", seed=6)
+    P, led = O.inject(bg, spec, np.arange(20000))
+    r, th, ph = _sph(P)
+    assert stats.kstest((r ** 3 - 0.12 ** 3) / (8 - 0.12 ** 3), "uniform").pvalue > 0.01
+    c = (np.cos(th) - math.cos(88 * DEG)) / (math.cos(92 * DEG) - math.cos(88 * DEG))
+    assert stats.kstest(c, "uniform").pvalue > 0.01
+    phat = np.mod(ph + k * (r - rb), 2 * math.pi)
+    assert phat.min() >= 4.5 - 1e-12 and phat.max() <= 4.9 + 1e-12
+    assert stats.kstest((phat - 4.5) / 0.4, "uniform").pvalue > 0.01
+    # the longitudes themselves are not confined to [ph1, ph2]: the band winds with r
+    assert np.mod(ph[r > 1.5], 2 * math.pi).max() < 4.5 - k * (1.5 - rb) + 0.4 + 1e-9
+    assert P["w"] == pytest.approx(1 / r ** 2, rel=1e-12)
+
+
 def test_power_law_energy():
     bg = O.analytic_background("uniform_b", [5.0])
     spec = InjectSpec(region="point", energy="powerlaw", e1=0.05, e2=5.0, gamma=3.0, seed=9)

@@ -40,7 +40,8 @@ def test_noalloc_matches_fte_advance_on_two_calls():
     bg_a, pool_a, tally_a = _setup(api, w, fields, obs)
     bg_b, pool_b, tally_b = _setup(api, w, fields, obs)
     ws = api.Workspace()
-    # the allocation-free call keeps per-block histograms in shared memory: compare with the same layout
+    # the allocation-free call keeps per-block histograms in shared memory and never reorders:
+    # compare with fte_advance in the shared-memory layout (which reorders, changing no result)
     prm = dataclasses.replace(w.params, tally_layout="shared")
     for n0, n1 in ((0, 700), (700, 2300)):          # two calls in a row; the second spans 2 launches
         api.fte_advance(pool_a, bg_a, prm, tally_a, n0, n1, ws)
@@ -70,7 +71,13 @@ def test_noalloc_rejects_oversized_tally():
     build.build()
     w = configs.scaled(configs.parker_1e4(), n_particles=64)
     fields = configs.build_background(w)
-    big = [Observer(ne=16, nt=450), Observer(ne=16, nt=450)]     # 14,400 bins: fit a block, not the array
+    # a tally whose per-block histograms (12 bytes per bin) fit one block's shared memory
+    # (at most 16,384 bins) but not one block per SM in the 24 MiB array
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    nt = (24 * 2 ** 20 // (12 * sms)) // 32 + 1              # two observers of 16 x nt bins
+    if 32 * nt > 16384:
+        pytest.skip(f"{sms} SMs: every tally that fits a block also fits the array")
+    big = [Observer(ne=16, nt=nt), Observer(ne=16, nt=nt)]
     bg, pool, tally = _setup(api, w, fields, big)
     with pytest.raises(A.FteError) as e:
         api.fte_advance_noalloc(pool, bg, w.params, tally, 0, 10)
