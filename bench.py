@@ -485,21 +485,29 @@ def run_profile_case(args):
             torch.cuda.synchronize()
             del cell
     else:
-        w = configs.scaled(configs.cir_uniform_1e6(), n_snap=2, n_particles=1 << 18)
+        w = configs.scaled(configs.cir_uniform_1e6(), n_snap=2, n_particles=args.profile_particles)
         w.params.sort_every = args.sort_every
         bg = device_background(api, w, configs.build_background(w), args.layout, args.dtype)
+    if args.no_obs:
+        w.observers = []
     pool = api.Particles(w.n_particles)
     tally = api.Tally(w.observers)
     api.fte_tally_reset(tally)
     api.fte_inject(pool, bg, w.inject, w.n_particles, tally)
     wsp = api.Workspace()
+    wsp.ensure(api.fte_workspace_bytes(bg, tally, w.n_particles, 256))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
     for c in range(args.launches):
         api.fte_advance(pool, bg, w.params, tally, 256 * c, 256 * (c + 1), wsp)
+    e1.record()
     lw, ln = api.fte_ledger(tally)
     torch.cuda.synchronize()
     per_step = ALG_BYTES if args.dtype == "f32" else ALG_BYTES // 2
     print(json.dumps({"case": "profile", "grid": args.grid, "dtype": args.dtype, "launches": args.launches,
-                      "particle_steps": int(ln[6]), "alg_bytes": int(ln[6]) * per_step}))
+                      "particles": w.n_particles, "observers": len(w.observers),
+                      "particle_steps": int(ln[6]), "alg_bytes": int(ln[6]) * per_step,
+                      "rate": int(ln[6]) / (e0.elapsed_time(e1) / 1e3)}))
 
 
 def build_amr_background(w, api, device="cuda"):
@@ -570,7 +578,7 @@ def amr_measure(api, args, l1=None, forms=True, cpu=True, clocks=None):
         api.fte_probe_step_timing(0)
         ms = t0.elapsed_time(t1)
         errs = [tally.batch_means(o)[1] for o in range(len(w.observers))]
-        S = np.array([tally.S_class[0, o].sum().item() for o in range(len(w.observers))])
+        S = np.array([tally.classes(o).sum() for o in range(len(w.observers))])
         return ms, iv, done, S, errs
 
     layout = getattr(args, "layout", "cell")
@@ -724,6 +732,8 @@ def run_ensemble_case(args):
         return sum(int(tl.ledger_n.cpu().numpy()[6]) for tl in sub_tallies)
     with torch.cuda.stream(side):
         plain_rate, plain_ms = timed(plain_step, plain_count, args.ens_timed, 1)
+    side.synchronize()
+    rel_plain = [e for e in (tl.batch_means(0)[1] for tl in sub_tallies) if e is not None]
     del sub_pools, sub_tallies
     torch.cuda.empty_cache()
 
@@ -747,9 +757,8 @@ def run_ensemble_case(args):
         with g.capture(side):
             batched_step(best)
         graph_rate, graph_ms = timed(lambda: g.launch(side), ensemble_count, args.ens_timed, 1)
-    S = np.array([api.fte_tally_set(tally, k, 0, A.FTE_TALLY_S).sum() for k in range(len(sets))])
-    S2 = np.array([api.fte_tally_set(tally, k, 0, A.FTE_TALLY_S2).sum() for k in range(len(sets))])
-    rel = [float(math.sqrt(b) / a) for a, b in zip(S, S2) if a > 0]
+    # per-set tally errors by batch means over the 32 particle-id classes (graph arm's last step)
+    rel = [e for e in (tally.batch_means(0, set=k)[1] for k in range(len(sets))) if e is not None]
     counts = [s.count for s in sets]
     print(json.dumps({
         "case": "ensemble", "metric": METRIC, "value": graph_rate, "unit": UNIT, "n_gpus": 1,
@@ -761,8 +770,12 @@ def run_ensemble_case(args):
                                "per-set 1 au box tallies 16x144",
                    "sort_every": w.params.sort_every, "record_layout": args.layout,
                    "tally_rel_err_median": float(np.median(rel)) if rel else None,
+                   "tally_rel_err_method": "per set: relative standard error of the 1 au total occupancy from 32 "
+                                           "batch means over particle-id classes; median over the sets with hits",
                    "sets_with_hits": len(rel)},
-        "arms": {"single_set_kernel_set_after_set": {"value": plain_rate, "ms_per_step": plain_ms},
+        "arms": {"single_set_kernel_set_after_set": {"value": plain_rate, "ms_per_step": plain_ms,
+                                                     "tally_rel_err_median": float(np.median(rel_plain))
+                                                     if rel_plain else None},
                  "ensemble_kernel_default_config": {"value": eager_rate, "ms_per_step": eager_ms},
                  "ensemble_kernel_autotuned_graph": {"value": graph_rate, "ms_per_step": graph_ms,
                                                      "config": best}},
@@ -1137,6 +1150,8 @@ def main():
     ap.add_argument("--launches", type=int, default=3)
     ap.add_argument("--grid", default="uniform", choices=["uniform", "amr"], help="grid of --case profile")
     ap.add_argument("--dtype", default="f32", choices=["f32", "bf16", "f16"], help="storage of --case profile")
+    ap.add_argument("--profile-particles", type=int, default=1 << 18, help="particles of --case profile")
+    ap.add_argument("--no-obs", action="store_true", help="--case profile without observers")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)

@@ -44,7 +44,7 @@ extern "C" {
 
 #define FTE_ABI_VERSION 3
 #define FTE_NFIELD 18          /* stored fields per cell */
-#define FTE_NCLASS 32          /* particle-id classes of the observer totals S_class */
+#define FTE_NCLASS 32          /* particle-id classes of the class-resolved tally S_class */
 #define FTE_REC 24             /* floats per stored cell record (96 bytes) */
 #define FTE_HREC 32            /* 16-bit values per reduced-precision cell record (64 bytes) */
 #define FTE_HHDR 32            /* floats of the per-field scale header of a reduced-precision background */
@@ -270,10 +270,10 @@ typedef struct fte_tally_buf {
     unsigned long long* C;            /* DEVICE, max(n_sets, 1) * fte_tally_bins() counts */
     double* ledger_w;                 /* DEVICE, FTE_LEDGER doubles */
     unsigned long long* ledger_n;     /* DEVICE, FTE_LEDGER counts */
-    double* S_class;                  /* DEVICE, optional (NULL: not kept): max(n_sets, 1) * n_obs *
-                                         FTE_NCLASS doubles, [set][obs][class]: the sum of w dt over
-                                         the tallied steps of the particles whose id % FTE_NCLASS is
-                                         `class`, for batch-means error estimates of observer totals */
+    double* S_class;                  /* DEVICE, optional (NULL: not kept): max(n_sets, 1) *
+                                         fte_tally_bins() * FTE_NCLASS doubles, [set][bin][class]: S of
+                                         the bin from the particles whose id % FTE_NCLASS is `class`,
+                                         for batch-means error estimates of bins and observer totals */
 } fte_tally_buf;
 
 /* Total bins over all observers of one set (0 if the tally description is invalid). */

@@ -836,7 +836,7 @@ typedef struct {
     const int64_t* off;
     double *S, *S2;
     uint64_t *C, *A;
-    double* SC;                  /* optional [n_obs][32]: observer totals by particle id mod 32 */
+    double* SC;                  /* optional [bin][32]: S of every bin by particle id mod 32 */
     double lw[8];
     uint64_t ln[8];
 } tally_t;
@@ -849,8 +849,8 @@ static double wrap_pi(double a)
 }
 
 /* Occupancy tally of the start-of-step state: in observer o, bin (E, t) gains
-   w dt (and (w dt)^2, and one count), and observer o's total for the particle's
-   id class (id mod 32) gains w dt.  Events within 1e-4 (relative) of an
+   w dt (and (w dt)^2, and one count), and the bin's total for the particle's id
+   class (id mod 32) gains w dt.  Events within 1e-4 (relative) of an
    energy-bin edge or of the observer's boundary are also counted in A. */
 static void tally_state(tally_t* T, double x, double y, double z, double p, double w,
                         double t, double dt, uint32_t id)
@@ -910,7 +910,7 @@ static void tally_state(tally_t* T, double x, double y, double z, double p, doub
             T->S[b] += wd;
             T->S2[b] += wd * wd;
             T->C[b] += 1;
-            if (T->SC) T->SC[o * 32 + (int)(id % 32u)] += wd;
+            if (T->SC) T->SC[b * 32 + (int)(id % 32u)] += wd;
         }
         if (amb) T->A[b] += 1;
     }
@@ -1109,14 +1109,14 @@ int or_advance(const or_background* bg, const or_params* prm, const or_observer*
     double* tS2 = (double*)calloc((size_t)n_threads * (nb > 0 ? nb : 1), sizeof(double));
     uint64_t* tC = (uint64_t*)calloc((size_t)n_threads * (nb > 0 ? nb : 1), sizeof(uint64_t));
     uint64_t* tA = (uint64_t*)calloc((size_t)n_threads * (nb > 0 ? nb : 1), sizeof(uint64_t));
-    double* tSC = (double*)calloc((size_t)n_threads * (n_obs > 0 ? n_obs : 1) * 32, sizeof(double));
+    double* tSC = (double*)calloc((size_t)n_threads * (nb > 0 ? nb : 1) * 32, sizeof(double));
     tally_t* tt = (tally_t*)calloc((size_t)n_threads, sizeof(tally_t));
     if (!tS || !tS2 || !tC || !tA || !tSC || !tt) return -2;
     for (int k = 0; k < n_threads; ++k) {
         tt[k].obs = obs; tt[k].n_obs = n_obs; tt[k].off = off;
         tt[k].S = tS + (size_t)k * nb; tt[k].S2 = tS2 + (size_t)k * nb;
         tt[k].C = tC + (size_t)k * nb; tt[k].A = tA + (size_t)k * nb;
-        tt[k].SC = tSC + (size_t)k * (n_obs > 0 ? n_obs : 1) * 32;
+        tt[k].SC = tSC + (size_t)k * (nb > 0 ? nb : 1) * 32;
     }
 #ifdef _OPENMP
 #pragma omp parallel num_threads(n_threads)
@@ -1145,7 +1145,7 @@ int or_advance(const or_background* bg, const or_params* prm, const or_observer*
         }
         for (int m = 0; m < 8; ++m) { ledger_w[m] += tt[k].lw[m]; ledger_n[m] += tt[k].ln[m]; }
         if (SC)
-            for (int b = 0; b < n_obs * 32; ++b) SC[b] += tt[k].SC[b];
+            for (int64_t b = 0; b < nb * 32; ++b) SC[b] += tt[k].SC[b];
     }
     free(tS); free(tS2); free(tC); free(tA); free(tSC); free(tt);
     return 0;

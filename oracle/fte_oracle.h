@@ -100,7 +100,7 @@ int or_eval_fields(const or_background* bg, double x, double y, double z, double
                    double out[40]);
 int or_inject(const or_background* bg, const or_inject_spec* spec, const uint32_t* ids,
               int64_t n, or_particle* out, double ledger_w[8], uint64_t ledger_n[8]);
-/* SC (optional, [n_obs][32]): each observer's total w dt by particle id mod 32 */
+/* SC (optional, [bin][32]): the tally S of every bin by particle id mod 32 */
 int or_advance(const or_background* bg, const or_params* prm, const or_observer* obs,
                int n_obs, or_particle* P, int64_t n, int64_t n_start, int64_t n_end,
                double* S, double* S2, uint64_t* C, uint64_t* A, double* SC, double ledger_w[8],

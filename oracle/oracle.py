@@ -287,8 +287,8 @@ class Tally:
         self.S2 = np.zeros(n)
         self.C = np.zeros(n, dtype=np.uint64)
         self.A = np.zeros(n, dtype=np.uint64)
-        # observer totals by particle id mod 32: [observer][class]
-        self.SC = np.zeros((max(len(self.observers), 1), 32))
+        # the tally S by particle id mod 32: [bin][class]
+        self.SC = np.zeros((n, 32))
         self.oc = (ObserverC * max(len(self.observers), 1))(
             *[observer_c(o) for o in self.observers])
 
@@ -296,6 +296,12 @@ class Tally:
         off = sum(self.nb[:o])
         ob = self.observers[o]
         return arr[off:off + self.nb[o]].reshape(ob.ne, ob.nt)
+
+    def classes(self, o):
+        """Observer o's S by particle id mod 32, [ne, nt, 32]."""
+        off = sum(self.nb[:o])
+        ob = self.observers[o]
+        return self.SC[off:off + self.nb[o]].reshape(ob.ne, ob.nt, 32)
 
     def intensity(self, o):
         S = np.ascontiguousarray(self.obs_view(o, self.S))

@@ -237,8 +237,8 @@ class Tally:
         self.C = torch.zeros(n, dtype=torch.int64, device=device)
         self.ledger_w = torch.zeros(A.FTE_LEDGER, dtype=torch.float64, device=device)
         self.ledger_n = torch.zeros(A.FTE_LEDGER, dtype=torch.int64, device=device)
-        # observer totals by particle-id class: [set][observer][class]
-        self.S_class = torch.zeros((max(self.n_sets, 1), max(len(self.observers), 1), A.FTE_NCLASS),
+        # the tally by particle-id class: [set][bin][class]
+        self.S_class = torch.zeros((max(self.n_sets, 1), max(sum(self.nb), 1), A.FTE_NCLASS),
                                    dtype=torch.float64, device=device)
         self.out = torch.zeros(max(self.nb + [1]), dtype=torch.float64, device=device)
         c = A.fte_tally_buf()
@@ -251,12 +251,25 @@ class Tally:
         c.S_class = self.S_class.data_ptr()
         self.c = c
 
+    def classes(self, obs=0, set=0):
+        """Observer `obs`'s bins by particle-id class, float64 numpy [ne, nt, FTE_NCLASS]."""
+        off = sum(self.nb[:obs])
+        ob = self.observers[obs]
+        c = self.S_class[set, off:off + self.nb[obs]].double().cpu().numpy()
+        return c.reshape(ob.ne, ob.nt, A.FTE_NCLASS)
+
+    def batch_sigma(self, obs=0, set=0):
+        """Standard error of every bin of observer `obs` from its FTE_NCLASS particle-id
+        class sums (batch means), float64 numpy [ne, nt]."""
+        c = self.classes(obs, set)
+        return (c.shape[-1] * c.var(axis=-1, ddof=1)) ** 0.5
+
     def batch_means(self, obs=0, set=0):
         """Observer `obs`'s total occupancy (sum of w dt over its tallied steps) and the
         relative standard error of that total from its FTE_NCLASS particle-id class sums
         (batch means: the particles are independent, so the class sums are independent
         estimates of 1/FTE_NCLASS of the total).  Returns (total, rel_err or None)."""
-        c = self.S_class[set, obs].double().cpu().numpy()
+        c = self.classes(obs, set).reshape(-1, A.FTE_NCLASS).sum(axis=0)
         tot = float(c.sum())
         if tot <= 0:
             return tot, None

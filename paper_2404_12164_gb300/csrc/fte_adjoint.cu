@@ -404,6 +404,7 @@ __global__ void __launch_bounds__(256) adj_forward_kernel(const AdvanceArgs a, c
     float* c = k.ckpt + (size_t)k.seg * 5 * n;
     double jsum = 0.0;
     unsigned long long noor = 0;
+    TallyRun nrun{-1, 0u};                 // the adjoint kernels run without observers
     for (;;) {
         const unsigned long long f = atomicAdd(a.fetch, 1ULL);
         if (f >= n_work) break;
@@ -420,7 +421,7 @@ __global__ void __launch_bounds__(256) adj_forward_kernel(const AdvanceArgs a, c
             const float r = sqrtf(x * x + y * y + z * z);
             J += (double)(w * a.prm.dt * smooth_k(k, r, p, time_arg(k, s), nullptr, nullptr));
             st = step<false, DT, kModeSingle, LAY>(a, a.prm, I, 0, s, pid, x, y, z, mu, p, w, nullptr, nullptr,
-                                              nullptr, sc, noor, 0);
+                                              nullptr, sc, noor, nrun);
             if (st != FTE_ALIVE) { ++s; break; }
         }
         // steps taken since the start of the run (a.n_table0), counting the one that ended it
@@ -468,6 +469,7 @@ __global__ void __launch_bounds__(256) adj_replay_kernel(const AdvanceArgs a, co
     const long long cs = k.c_start, ce = k.c_end;
     const float* c = k.ckpt + (size_t)k.seg * 5 * n;
     unsigned long long noor = 0;
+    TallyRun nrun{-1, 0u};                 // the adjoint kernels run without observers
     for (;;) {
         const unsigned long long f = atomicAdd(a.fetch, 1ULL);
         if (f >= n_work) break;
@@ -485,7 +487,7 @@ __global__ void __launch_bounds__(256) adj_replay_kernel(const AdvanceArgs a, co
             sp[0] = x; sp[n] = y; sp[2 * n] = z; sp[3 * n] = mu; sp[4 * n] = p;
             if (s + 1 < e)
                 step<false, DT, kModeSingle, LAY>(a, a.prm, I, 0, s, pid, x, y, z, mu, p, w, nullptr, nullptr, nullptr,
-                                             sc, noor, 0);
+                                             sc, noor, nrun);
         }
         if (ce < e) {      // the start of the next chunk
             float* cp = k.carry + i;

@@ -429,9 +429,8 @@ fte_status fte_tally_reset(const fte_tally_buf* t, void* stream)
         FTE_CUDA(cudaMemsetAsync(t->S2, 0, nb * sizeof(double), st), "memset S2");
         FTE_CUDA(cudaMemsetAsync(t->C, 0, nb * sizeof(unsigned long long), st), "memset C");
     }
-    if (t->S_class && t->n_obs)
-        FTE_CUDA(cudaMemsetAsync(t->S_class, 0, (size_t)(t->n_sets > 1 ? t->n_sets : 1) * t->n_obs * FTE_NCLASS *
-                                 sizeof(double), st), "memset S_class");
+    if (t->S_class && nb)
+        FTE_CUDA(cudaMemsetAsync(t->S_class, 0, nb * FTE_NCLASS * sizeof(double), st), "memset S_class");
     FTE_CUDA(cudaMemsetAsync(t->ledger_w, 0, FTE_LEDGER * sizeof(double), st), "memset ledger");
     FTE_CUDA(cudaMemsetAsync(t->ledger_n, 0, FTE_LEDGER * sizeof(unsigned long long), st), "memset ledger");
     return FTE_OK;

@@ -49,7 +49,7 @@ struct AdvanceArgs {
     unsigned long long* fetch;    // particle counter for dynamic assignment
     double* ledger_w;
     unsigned long long* ledger_n;
-    double* cls;                  // optional [set][obs][FTE_NCLASS] observer totals by particle-id class
+    double* cls;                  // optional [set][bin][FTE_NCLASS]: S by particle-id class
 };
 
 struct SortArgs {

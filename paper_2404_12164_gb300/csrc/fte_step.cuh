@@ -7,65 +7,38 @@
 namespace fte {
 
 // ---------------------------------------------------------------------------
-// Occupancy tally (start-of-step state, w dt per step).  Lanes of a warp that
-// hit the same bin are merged first (__match_any_sync), then one lane per bin
-// adds the merged sums to the block's shared-memory histogram.
+// Occupancy tally (start-of-step state, w dt per step).  A particle's consecutive
+// tallied steps in one bin add up in two registers (its w dt is the same every
+// step) and reach the accumulators once, when the bin changes and when the particle
+// leaves the launch: the steps tallied at one time are concentrated in a few bins
+// (one time bin, a few energy bins), so adding every step there would have tens of
+// thousands of threads contend for a handful of addresses.  The accumulators are
+// the FP64 tally in global memory (global modes) or the block's shared-memory
+// histogram (shared modes); the class-resolved tally (batch means) gains the same
+// sum in the particle's id class.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void warp_tally(float* shS, float* shS2, unsigned* shC, int bin,
-                                           float val)
-{
-    const unsigned m = __activemask();
-    if (!__any_sync(m, bin >= 0)) return;
-    const unsigned grp = __match_any_sync(m, bin);
-    if (bin < 0) return;
-    float s = 0.f, s2 = 0.f;
-    unsigned mm = grp;
-    while (mm) {
-        const int src = __ffs(mm) - 1;
-        mm &= mm - 1;
-        const float v = __shfl_sync(grp, val, src);
-        s += v;
-        s2 += v * v;
-    }
-    if ((int)(threadIdx.x & 31) == __ffs(grp) - 1) {
-        atomicAdd(&shS[bin], s);
-        atomicAdd(&shS2[bin], s2);
-        atomicAdd(&shC[bin], (unsigned)__popc(grp));
-    }
-}
+struct TallyRun {
+    int bin;          // bin of the run of tallied steps, -1 before the first
+    unsigned cnt;     // steps in it not yet added to the accumulators
+};
 
-// The same merge for tallies too large for shared memory (ensembles): one lane
-// per bin adds the merged sums to the FP64 accumulators in global memory.
-__device__ __forceinline__ void warp_tally_global(double* S, double* S2, unsigned long long* C,
-                                                  int bin, float val)
+template <int MODE>
+__device__ __forceinline__ void tally_flush(const AdvanceArgs& a, float* shS, float* shS2, unsigned* shC,
+                                           TallyRun& t, float wdt, uint32_t pid)
 {
-    const unsigned m = __activemask();
-    if (!__any_sync(m, bin >= 0)) return;
-    const unsigned grp = __match_any_sync(m, bin);
-    if (bin < 0) return;
-    float s = 0.f, s2 = 0.f;
-    unsigned mm = grp;
-    while (mm) {
-        const int src = __ffs(mm) - 1;
-        mm &= mm - 1;
-        const float v = __shfl_sync(grp, val, src);
-        s += v;
-        s2 += v * v;
+    if (t.cnt == 0) return;
+    const double d = (double)wdt, c = (double)t.cnt;
+    if (global_tally(MODE)) {
+        atomicAdd(&a.gS[t.bin], d * c);
+        atomicAdd(&a.gS2[t.bin], d * d * c);
+        atomicAdd(&a.gC[t.bin], (unsigned long long)t.cnt);
+    } else {
+        atomicAdd(&shS[t.bin], (float)(d * c));
+        atomicAdd(&shS2[t.bin], (float)(d * d * c));
+        atomicAdd(&shC[t.bin], t.cnt);
     }
-    if ((int)(threadIdx.x & 31) == __ffs(grp) - 1) {
-        atomicAdd(&S[bin], (double)s);
-        atomicAdd(&S2[bin], (double)s2);
-        atomicAdd(&C[bin], (unsigned long long)__popc(grp));
-    }
-}
-
-// Observer totals by particle-id class (batch means of the occupancy estimator):
-// every tallied step also adds w dt to the total of its observer, set and
-// particle-id class (cbase = set * n_obs).  Tallied steps are a small fraction of
-// all steps, so one FP64 atomic each costs nothing measurable and no registers.
-__device__ __forceinline__ void class_add(const AdvanceArgs& a, int cbase, int o, uint32_t pid, float wdt)
-{
-    atomicAdd(a.cls + ((size_t)(cbase + o) * FTE_NCLASS + (pid % FTE_NCLASS)), (double)wdt);
+    if (a.cls) atomicAdd(a.cls + ((size_t)t.bin * FTE_NCLASS + (pid % FTE_NCLASS)), d * c);
+    t.cnt = 0;
 }
 
 // One Euler-Maruyama step of Eqs. 2-4 for one particle (Sec. 2.1), with the
@@ -75,7 +48,7 @@ __device__ __forceinline__ int step(const AdvanceArgs& a, const ParamsK& prm, fl
                                     long long n, uint32_t pid,
                                     float& x, float& y, float& z, float& mu, float& p, float w,
                                     float* shS, float* shS2, unsigned* shC, const float* sc,
-                                    unsigned long long& noor, int cbase)
+                                    unsigned long long& noor, TallyRun& run)
 {
     const StepEntry* ep = a.table + (n - a.n_table0);
     StepEntry e;
@@ -202,15 +175,18 @@ __device__ __forceinline__ int step(const AdvanceArgs& a, const ParamsK& prm, fl
                 const float le = logf(energy_of(p) / ob.e_lo) * ob.ne_over_lnratio;
                 int it = __ldg(&ep->it[o]);     // time bin, -1 outside [t_lo, t_hi)
                 if (ob.kind == 3 && it >= 0) it = min((int)(ph * ob.phi_scale), ob.nt - 1);
-                if (le >= 0.f && le < (float)ob.ne && it >= 0) {
+                if (le >= 0.f && le < (float)ob.ne && it >= 0)
                     bin = sbin + ob.off + (int)le * ob.nt + it;
-                    if (a.cls) class_add(a, cbase, o, pid, w * dt);
-                } else {
+                else
                     ++noor;
-                }
             }
-            if (global_tally(MODE)) warp_tally_global(a.gS, a.gS2, a.gC, bin, w * dt);
-            else warp_tally(shS, shS2, shC, bin, w * dt);
+            if (bin >= 0) {
+                if (bin != run.bin) {
+                    tally_flush<MODE>(a, shS, shS2, shC, run, w * dt, pid);
+                    run.bin = bin;
+                }
+                ++run.cnt;
+            }
         }
     }
 
@@ -289,11 +265,12 @@ __global__ void __launch_bounds__(NT, single_set(MODE) ? MINB : 512 / NT) advanc
         const float w = a.w[i];
         const uint32_t pid = a.id[i];
         int st = FTE_ALIVE;
+        TallyRun run{-1, 0u};
         if (single_set(MODE)) {
             for (long long n = a.n_start; n < a.n_end; ++n) {
                 ++nsteps;
                 st = step<KPERP, DT, MODE, LAY>(a, a.prm, I0, 0, n, pid, x, y, z, mu, p, w, shS, shS2, shC, sc, noor,
-                                                0);
+                                                run);
                 if (st != FTE_ALIVE) break;
             }
         } else {
@@ -308,14 +285,14 @@ __global__ void __launch_bounds__(NT, single_set(MODE) ? MINB : 512 / NT) advanc
             prm.set_id = s_set[s].set_id;
             const float I = s_I[s];
             const int sbin = s * a.nbins;
-            const int cbase = s * a.n_obs;
             for (long long n = a.n_start; n < a.n_end; ++n) {
                 ++nsteps;
                 st = step<KPERP, DT, MODE, LAY>(a, prm, I, sbin, n, pid, x, y, z, mu, p, w, shS, shS2, shC, sc, noor,
-                                                cbase);
+                                                run);
                 if (st != FTE_ALIVE) break;
             }
         }
+        tally_flush<MODE>(a, shS, shS2, shC, run, w * a.prm.dt, pid);
         a.x[i] = x; a.y[i] = y; a.z[i] = z; a.mu[i] = mu; a.p[i] = p;
         if (st != FTE_ALIVE) {
             a.status[i] = (uint8_t)st;

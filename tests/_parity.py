@@ -31,9 +31,11 @@ def gpu_run(w, fields, n_steps, chunks=None, params=None, observers=None, n_part
                         (("S", A.FTE_TALLY_S), ("S2", A.FTE_TALLY_S2), ("C", A.FTE_TALLY_C),
                          ("J", A.FTE_TALLY_INTENSITY))})
     lw, ln = api.fte_ledger(tally)
-    cls = tally.S_class[0].cpu().numpy()
+    # per observer: the bins by particle-id class [ne, nt, 32] and the class totals [32]
+    bins = [tally.classes(o) for o in range(len(obs))]
+    cls = [b.reshape(-1, b.shape[-1]).sum(axis=0) for b in bins]
     torch.cuda.synchronize()
-    return dict(states=states, tallies=tallies, ledger_w=lw, ledger_n=ln, failed=failed, S_class=cls)
+    return dict(states=states, tallies=tallies, ledger_w=lw, ledger_n=ln, failed=failed, S_class=cls, classes=bins)
 
 
 def oracle_run(w, fields, n_steps, chunks=None, params=None, observers=None, n_particles=None,
@@ -55,7 +57,9 @@ def oracle_run(w, fields, n_steps, chunks=None, params=None, observers=None, n_p
         tallies.append(dict(S=T.obs_view(o, T.S), S2=T.obs_view(o, T.S2), C=T.obs_view(o, T.C),
                             A=T.obs_view(o, T.A), J=T.intensity(o)))
     L = led.as_dict()
-    return dict(states=states, tallies=tallies, ledger_w=L["w"], ledger_n=L["n"], S_class=T.SC)
+    bins = [T.classes(o) for o in range(len(obs))]
+    cls = [b.reshape(-1, 32).sum(axis=0) for b in bins]
+    return dict(states=states, tallies=tallies, ledger_w=L["w"], ledger_n=L["n"], S_class=cls, classes=bins)
 
 
 def trajectory_errors(g, o, step, sel=None, expanding=False):

@@ -59,11 +59,14 @@ def cir_small():
 OBS = SmoothObserver(r_o=1.15, sigma_r=0.05, e_c=0.08, sigma_lnE=0.5, t_c=1500.0, sigma_t=1000.0)
 
 
-def _gpu(w, f, prm, n, steps, K=64, per_particle=True, obs=OBS):
+def _gpu(w, f, prm, n, steps, K=64, per_particle=True, obs=OBS, dtype="f32"):
     import torch
     from paper_2404_12164_gb300 import api
     bg = api.Background(w.grid)
     api.fte_load_background(bg, f)
+    if dtype != "f32":
+        b32, bg = bg, api.Background(w.grid, dtype=dtype)
+        api.fte_quantize_background(bg, b32)
     pool = api.Particles(n)
     tally = api.Tally([])
     api.fte_tally_reset(tally)
@@ -127,6 +130,33 @@ def test_gradients_match_oracle(cir_small, name, prm, names):
               f"max {err.max():.2e}; total adjoint {g[GI[nm] - 1]:.6e}, oracle {ref.sum():.6e}")
         assert np.median(err) < 1e-3, nm
         assert np.percentile(err, 95) < 1e-2, nm
+
+
+@pytest.mark.parametrize("dtype", ["bf16", "f16"])
+def test_gradient_storage_error(cir_small, dtype):
+    """Stated error of the gradients on a 16-bit background: the adjoint's totals on BF16 or
+    FP16 storage against the oracle's estimate of the same form on the FP32 fields (same
+    noise, so nearly the same paths), in units of the batch-means error of the per-particle
+    differences, and relative."""
+    w, f = cir_small
+    name, prm, names = MODELS[0]
+    n, steps = 4000, 200
+    _, g, pp, _ = _gpu(w, f, prm, n, steps, dtype=dtype)
+    bg = O.grid_background(w.grid, f)
+    P, _ = O.inject(bg, w.inject, np.arange(n, dtype=np.uint32))
+    Jo, Go, fl = O.observe_lr(bg, prm, P, 0, steps, OBS, WINDOW[name], names)
+    ids = np.arange(n)
+    dJ = pp[:, 0].astype(np.float64) - Jo
+    print(f"{dtype} J: total {pp[:, 0].sum():.6e} vs oracle {Jo.sum():.6e} "
+          f"(rel {dJ.sum() / Jo.sum():+.2e}, {dJ.sum() / _batch_sigma(dJ, ids):+.1f} sigma)")
+    assert abs(dJ.sum()) <= 0.02 * abs(Jo.sum())
+    for nm in names:
+        d = pp[:, GI[nm]].astype(np.float64) - Go[nm]
+        sd = _batch_sigma(d, ids)
+        rel = d.sum() / abs(Go[nm].sum())
+        print(f"{dtype} d/d{nm}: total {pp[:, GI[nm]].sum():.6e} vs oracle {Go[nm].sum():.6e} "
+              f"(rel {rel:+.2e}, {d.sum() / sd:+.1f} sigma of the difference)")
+        assert abs(d.sum()) <= 4 * sd + 0.05 * abs(Go[nm].sum()), nm
 
 
 def test_gamma_gradient_is_likelihood_ratio(cir_small):

@@ -7,8 +7,9 @@ particles are independent, so the totals of the 32 classes id mod 32 are
 independent estimates of 1/32 of the total, and sqrt(32 var(class totals)) is its
 standard error (batch means).
 
-* A particle resting inside an observer puts all its w dt into its own class.
-* The class totals add up to the observer's total.
+* A particle resting inside an observer puts all its w dt into its own class,
+  bin by bin.
+* The class sums of every bin add up to the bin.
 * Over 16 independent seeds of a diffusive workload the batch-means standard
   error predicts the seed-to-seed scatter of the total, while the per-step
   estimate falls short of it by more than a factor of 3.
@@ -36,8 +37,9 @@ def test_resting_particle_fills_its_own_class():
     expect = np.zeros(32)
     expect[7] = (0.5 + 2.0) * 10.0 * 100
     expect[12] = 1.0 * 10.0 * 100
-    assert np.allclose(T.SC[0], expect, rtol=1e-12, atol=0)
-    assert T.SC[0].sum() == pytest.approx(T.S.sum(), rel=1e-12)
+    cls = T.classes(0)
+    assert np.allclose(cls.reshape(-1, 32).sum(axis=0), expect, rtol=1e-12, atol=0)
+    assert np.allclose(cls.sum(axis=-1), T.obs_view(0, T.S), rtol=1e-12, atol=0)
 
 
 def test_batch_means_predicts_seed_to_seed_scatter():
@@ -51,7 +53,7 @@ def test_batch_means_predicts_seed_to_seed_scatter():
         P["mu"] = (np.arange(n) + 0.5) / n * 2 - 1
         P["id"] = np.arange(n)
         T, _ = O.advance(bg, prm, P, 0, steps, tally=O.Tally(obs))
-        c = T.SC[0]
+        c = T.classes(0).reshape(-1, 32).sum(axis=0)
         assert c.sum() == pytest.approx(T.S.sum(), rel=1e-10)
         tot.append(c.sum())
         bm.append(math.sqrt(32 * c.var(ddof=1)))
