@@ -208,6 +208,20 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
     return v;
 }
 
+// Persistent work distribution: lane 0 of the warp claims the next 32 entries of the
+// work list and each lane takes one, after the warp has reconverged (every lane of a
+// warp runs the same fetch loop and leaves it at the same time, so the full-warp
+// barrier always completes).  A per-lane counter would let lanes that reach the fetch
+// at different times (a particle absorbed early, a tally added) take entries far apart
+// in the ordered list, and their loads would then touch more cache lines.
+__device__ __forceinline__ unsigned long long warp_fetch(unsigned long long* counter)
+{
+    __syncwarp();
+    unsigned long long base = 0;
+    if ((threadIdx.x & 31u) == 0) base = atomicAdd(counter, 32ULL);
+    return __shfl_sync(0xffffffffu, base, 0) + (threadIdx.x & 31u);
+}
+
 // Set of pool entry i: the first s with i < end[s] (end holds running totals).
 __device__ __forceinline__ int set_of(const unsigned long long* end, int n_sets, unsigned long long i)
 {
@@ -257,8 +271,11 @@ __global__ void __launch_bounds__(NT, single_set(MODE) ? MINB : 512 / NT) advanc
     const unsigned long long n_work = a.order ? (unsigned long long)__ldg(a.n_order) : a.n_particles;
     unsigned long long nsteps = 0, noor = 0;
     for (;;) {
-        const unsigned long long f = atomicAdd(a.fetch, 1ULL);
-        if (f >= n_work) break;
+        // the warp takes 32 consecutive entries of the (spatially ordered) work list at once,
+        // so that its lanes hold neighbouring particles whatever branches they took before
+        const unsigned long long f = warp_fetch(a.fetch);
+        if (__shfl_sync(0xffffffffu, f, 0) >= n_work) break;
+        if (f >= n_work) continue;
         const unsigned long long i = a.order ? (unsigned long long)__ldg(a.order + f) : f;
         if (!a.order && a.status[i] != FTE_ALIVE) continue;
         float x = a.x[i], y = a.y[i], z = a.z[i], mu = a.mu[i], p = a.p[i];
