@@ -146,8 +146,10 @@ cudaError_t launch_advance(const AdvanceArgs& a, const BatchArgs& b, int kperp, 
 cudaError_t advance_occupancy(int kperp, int dtype, int mode, int nt, int pair, int amr, size_t smem,
                               int* blocks_per_sm);
 // whether the single-set step kernel runs in its 3-blocks-per-SM build: block AMR
-// or 16-bit storage with the global tally and no cross-field diffusion (uniform
-// FP32 grids keep the unconstrained build, which spills under the tighter limit)
+// with the global tally and no cross-field diffusion (its chain of dependent loads,
+// table -> leaf -> records, needs the extra warps); uniform grids keep the
+// unconstrained build in every storage form (under the tighter limit it spills:
+// 16-bit storage measured 1.018x FP32 with it and 1.069x without)
 bool dense_variant(int kperp, int dtype, int mode, int amr);
 // the ensemble variants live in their own translation unit (fte_batched.cu)
 const void* advance_fn_batched(int kperp, int dtype, int mode, int nt, int pair);
