@@ -79,9 +79,11 @@ def kernel_sources_hash():
     return h.hexdigest()
 
 
-def measured_traffic(layout):
-    """DRAM bytes per step-kernel launch from the committed ncu summary, or None when the kernel
-    sources changed since, or the summary is for another record layout."""
+def measured_traffic(layout, dtype="f32"):
+    """The committed ncu record of the step kernel for one storage type (DRAM bytes per alive
+    particle-step of the profile case, and its L1 data-pipe figures), or None when the kernel
+    sources changed since, the record is for another record layout or has no capture of
+    `dtype`."""
     try:
         with open(TRAFFIC_FILE) as f:
             d = json.load(f)
@@ -89,7 +91,11 @@ def measured_traffic(layout):
         return None
     if d.get("sources_sha256") != kernel_sources_hash() or d.get("record_layout") != layout:
         return None
-    return d.get("dram_bytes_per_launch")
+    e = d.get("by_dtype", {}).get(dtype)
+    if not e:
+        return None
+    return {"dram_bytes_per_particle_step": e.get("dram_bytes_per_particle_step"),
+            "source": TRAFFIC_FILE.split(ROOT + os.sep)[-1] + " (" + dtype + ")", "l1": e.get("l1")}
 
 
 def _peaks():
@@ -336,7 +342,8 @@ def run_gpu(args):
             _, f_rel = tally.batch_means(0)
             forms[dt] = {"value": f_steps * ws / (f_ms / 1e3), "unit": UNIT,
                          "speedup_vs_f32": (f_steps / f_ms) / (steps_total / ms),
-                         "roofline": roofline_record(f_iv, f_steps, ALG_BYTES // 2, l1, None, None),
+                         "roofline": roofline_record(f_iv, f_steps, ALG_BYTES // 2, l1, None,
+                                                      measured_traffic(args.layout, dt)),
                          "tally_total_rel_diff_vs_f32": float(abs(Sh.sum() - S_f32.sum()) / S_f32.sum()),
                          "tally_rel_err": f_rel,
                          "background_bytes": int(bh.nbytes)}
@@ -1099,8 +1106,9 @@ def roofline_record(intervals, particle_steps, alg_per_step, l1, l2_gbs, traffic
     durs = intervals[:, 1] - intervals[:, 0] if n else np.zeros(0)
     return {"bound": "l1", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak if achieved and peak else None,
-            "traffic": traffic.get("dram_bytes_per_launch") if traffic else None,
-            "traffic_source": traffic.get("source") if traffic else None,
+            "traffic": traffic["dram_bytes_per_particle_step"] * particle_steps / n if traffic and n else None,
+            "traffic_source": (traffic["source"] + ": DRAM bytes per alive particle-step of the profile case x "
+                               "this run's particle-steps per launch") if traffic else None,
             "kernel": "advance_kernel", "alg_bytes_per_particle_step": alg_per_step,
             "alg_bytes_per_launch": alg / n if n else None,
             "kernel_launches": n, "kernel_ms_total": float(durs.sum()), "kernel_ms_union": u,
