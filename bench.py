@@ -53,6 +53,29 @@ from fte_inputs import configs  # noqa: E402
 METRIC = "FTE particle-steps/s on 1 GB300 at stated tally error; % gather roofline; adj/fwd"
 UNIT = "particle-steps/s"
 ALG_BYTES = 2 * 8 * 18 * 4          # 2 snapshots x 8 corners x 18 fields x 4 B per particle-step
+
+# Error of the 16-bit storage forms against the FP64 oracle on the FP32 fields, per output: the
+# bounds tests/test_gpu_precision.py::test_storage_error_per_output and
+# tests/test_gpu_adjoint.py::test_gradient_storage_error assert (both import this table), and
+# what they measured on GB300 (small CIR grid, 4000 particles).
+STORAGE_ERROR = {
+    "bf16": {"trajectory_p99_at_400_steps": {"pos_rel": 3e-4, "mu": 3e-3, "p_rel": 3e-3},
+             "trajectory_p99_at_400_steps_measured": {"pos_rel": 4.4e-5, "mu": 3.7e-4, "p_rel": 3.9e-4}},
+    "f16": {"trajectory_p99_at_400_steps": {"pos_rel": 3e-5, "mu": 3e-4, "p_rel": 3e-4},
+            "trajectory_p99_at_400_steps_measured": {"pos_rel": 4.5e-6, "mu": 3.9e-5, "p_rel": 4.4e-5}},
+}
+STORAGE_ERROR_COMMON = {
+    "trajectory": "99th percentile over the particles of |16-bit run - FP64 oracle| before the first "
+                  "divergence event (position relative to r, mu absolute, p relative)",
+    "tally_bins": {"max_share_beyond_3_sigma": 0.05, "max_abs_mean_z": 1.0,
+                   "sigma": "batch-means standard error of the bin difference (32 particle-id classes, both sides)"},
+    "ledger": "absorbed counts per face within 4 binomial sigma of the oracle's",
+    "adjoint": {"J_rel": 0.02, "gradient_total_sigma": 4.0, "gradient_total_rel": 0.05,
+                "gradient_total": "|16-bit total - FP32-field oracle total| within gradient_total_sigma batch-means "
+                                  "sigma of the per-particle differences + gradient_total_rel of the oracle total"},
+    "source": "tests/test_gpu_precision.py::test_storage_error_per_output, "
+              "tests/test_gpu_adjoint.py::test_gradient_storage_error",
+}
 CHUNK = 1024                        # steps per advance launch
 
 
@@ -346,6 +369,7 @@ def run_gpu(args):
                                                       measured_traffic(args.layout, dt)),
                          "tally_total_rel_diff_vs_f32": float(abs(Sh.sum() - S_f32.sum()) / S_f32.sum()),
                          "tally_rel_err": f_rel,
+                         "stated_storage_error": dict(STORAGE_ERROR[dt], **STORAGE_ERROR_COMMON),
                          "background_bytes": int(bh.nbytes)}
             del bh
             torch.cuda.empty_cache()

@@ -12,6 +12,7 @@ import math
 import numpy as np
 import pytest
 
+import bench
 from fte_inputs import configs
 from oracle.quantize import quantize
 from tests._parity import oracle_run, trajectory_errors
@@ -129,11 +130,12 @@ def _gpu_half_full(w, fields, dtype, chunks):
 
 
 STORAGE_BOUNDS = {            # stated storage error against the FP64 oracle on FP32 fields
-    # (p99 position rel., p99 mu, p99 p rel.) before the first divergence event, at 400 steps
-    # (measured on GB300: BF16 4.4e-5, 3.7e-4, 3.9e-4; FP16 4.5e-6, 3.9e-5, 4.4e-5)
-    "bf16": (3e-4, 3e-3, 3e-3),
-    "f16": (3e-5, 3e-4, 3e-4),
+    # (p99 position rel., p99 mu, p99 p rel.) before the first divergence event, at 400 steps;
+    # the table bench.py reports in its forms object
+    k: tuple(v["trajectory_p99_at_400_steps"][q] for q in ("pos_rel", "mu", "p_rel"))
+    for k, v in bench.STORAGE_ERROR.items()
 }
+TALLY_BOUNDS = bench.STORAGE_ERROR_COMMON["tally_bins"]
 
 
 @pytest.mark.parametrize("dtype", ["bf16", "f16"])
@@ -168,7 +170,8 @@ def test_storage_error_per_output(cir_small, dtype):
               f"|z| > 3 in {np.mean(np.abs(z) > 3):.3f}, mean z {z.mean():+.2f}; absorbed count differences {led}, "
               f"injected weight rel. diff {abs(lw[0] - o['ledger_w'][0]) / o['ledger_w'][0]:.1e}")
         assert busy.sum() >= 15
-        assert np.mean(np.abs(z) > 3) <= 0.05 and abs(z.mean()) < 1.0, dt_
+        assert np.mean(np.abs(z) > 3) <= TALLY_BOUNDS["max_share_beyond_3_sigma"], dt_
+        assert abs(z.mean()) < TALLY_BOUNDS["max_abs_mean_z"], dt_
         for k in (1, 2, 3):                     # absorbed counts: within 4 binomial sigmas
             assert abs(led[k]) <= 4 * math.sqrt(max(int(o["ledger_n"][k]), 1)) + 2, (dt_, k)
     bp, bm, bq = STORAGE_BOUNDS[dtype]
