@@ -18,30 +18,37 @@ static const void* single_fn(int kperp, int dtype)
                  : (const void*)advance_kernel<false, FTE_F32, MODE, kThreads, LAY>;
 }
 
-// the denser builds (768 threads per SM: at most 85 registers; global tally, no
-// cross-field diffusion)
+// the register-limited builds of block AMR (global tally, no cross-field diffusion):
+// 16-bit records 3 blocks of 256 threads per SM (at most 85 registers), FP32 records
+// 5 blocks of 128 (at most 102)
 constexpr int kDenseBlocks = 768 / kThreads;
+constexpr int kAmr32Threads = 128;
+constexpr int kAmr32Blocks = 5;
 template <int LAY>
 static const void* dense_fn(int dtype)
 {
     if (dtype == FTE_BF16) return (const void*)advance_kernel<false, FTE_BF16, kModeSingleGlobal, kThreads, LAY, kDenseBlocks>;
     if (dtype == FTE_F16) return (const void*)advance_kernel<false, FTE_F16, kModeSingleGlobal, kThreads, LAY, kDenseBlocks>;
-    return (const void*)advance_kernel<false, FTE_F32, kModeSingleGlobal, kThreads, LAY, kDenseBlocks>;
+    return (const void*)advance_kernel<false, FTE_F32, kModeSingleGlobal, kAmr32Threads, LAY, kAmr32Blocks>;
 }
 
-bool dense_variant(int kperp, int dtype, int mode, int amr)
+static bool dense_variant(int kperp, int mode, int amr)
 {
-    (void)dtype;
     return mode == kModeSingleGlobal && !kperp && amr;
 }
 
+int advance_threads(int kperp, int dtype, int mode, int amr)
+{
+    return single_set(mode) && dense_variant(kperp, mode, amr) && dtype == FTE_F32 ? kAmr32Threads : kThreads;
+}
+
 // the single-set kernels come in one variant per record layout (pair: 1) and tally
-// mode, and for dense_variant() in a 3-blocks-per-SM build
+// mode, and for block AMR in a register-limited build
 static const void* advance_fn(int kperp, int dtype, int mode, int nt, int pair, int amr)
 {
     if (!single_set(mode)) return advance_fn_batched(kperp, dtype, mode, nt, pair);
-    if (nt != kThreads) return nullptr;
-    if (dense_variant(kperp, dtype, mode, amr)) return pair ? dense_fn<kLayPair>(dtype) : dense_fn<kLayCell>(dtype);
+    if (nt != advance_threads(kperp, dtype, mode, amr)) return nullptr;
+    if (dense_variant(kperp, mode, amr)) return pair ? dense_fn<kLayPair>(dtype) : dense_fn<kLayCell>(dtype);
     if (mode == kModeSingleGlobal)
         return pair ? single_fn<kModeSingleGlobal, kLayPair>(kperp, dtype)
                     : single_fn<kModeSingleGlobal, kLayCell>(kperp, dtype);

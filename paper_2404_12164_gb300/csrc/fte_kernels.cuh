@@ -47,6 +47,7 @@ struct AdvanceArgs {
     const unsigned* n_order;      // number of entries of `order` (device)
     float* part;                  // per-block partial histograms [grid][3][nbins]
     unsigned long long* fetch;    // particle counter for dynamic assignment
+    unsigned fetch_slots;         // > 0: `fetch` holds that many per-SM range counters
     double* ledger_w;
     unsigned long long* ledger_n;
     double* cls;                  // optional [set][bin][FTE_NCLASS]: S by particle-id class
@@ -139,18 +140,23 @@ struct AdjK {
 };
 
 // launchers (return cudaGetLastError())
-// step kernel of (kperp, dtype, mode, threads per block); nt is 256 for the single-set modes
+// step kernel of (kperp, dtype, mode, threads per block); for the single-set modes nt must
+// be advance_threads() of the same arguments
 cudaError_t launch_advance(const AdvanceArgs& a, const BatchArgs& b, int kperp, int mode, int nt, int blocks,
                            size_t smem, cudaStream_t s);
 // resident blocks per SM of a step kernel (`pair`: record layout of a single-set kernel)
 cudaError_t advance_occupancy(int kperp, int dtype, int mode, int nt, int pair, int amr, size_t smem,
                               int* blocks_per_sm);
-// whether the single-set step kernel runs in its 3-blocks-per-SM build: block AMR
-// with the global tally and no cross-field diffusion (its chain of dependent loads,
-// table -> leaf -> records, needs the extra warps); uniform grids keep the
-// unconstrained build in every storage form (under the tighter limit it spills:
-// 16-bit storage measured 1.018x FP32 with it and 1.069x without)
-bool dense_variant(int kperp, int dtype, int mode, int amr);
+// Builds of the single-set step kernel.  Block AMR with the global tally and no
+// cross-field diffusion (its chain of dependent loads, table -> leaf -> records, needs
+// more resident warps) runs a register-limited build: FP32 records 5 blocks of 128
+// threads per SM (at most 102 registers, 20 warps: 1.997e10 particle-steps/s against
+// 1.912e10 with 24 warps at 85 registers and 1.892e10 with 16 unconstrained), 16-bit
+// records 3 blocks of 256 (85 registers, 24 warps).  Uniform grids keep the
+// unconstrained build of 256 threads in every storage form (under the tighter limits it
+// spills: 16-bit storage measured 1.018x FP32 with the 3-block build and 1.069x without).
+// advance_threads: threads per block of the build that advance_fn selects.
+int advance_threads(int kperp, int dtype, int mode, int amr);
 // the ensemble variants live in their own translation unit (fte_batched.cu)
 const void* advance_fn_batched(int kperp, int dtype, int mode, int nt, int pair);
 cudaError_t launch_advance_batched(const AdvanceArgs& a, const BatchArgs& b, int kperp, int mode, int nt,

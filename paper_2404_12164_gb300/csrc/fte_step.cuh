@@ -222,6 +222,58 @@ __device__ __forceinline__ unsigned long long warp_fetch(unsigned long long* cou
     return __shfl_sync(0xffffffffu, base, 0) + (threadIdx.x & 31u);
 }
 
+// Per-SM ranges of the work list: the list is cut into `slots` equal ranges (at most
+// `slots`, fewer when the device has fewer SM ids) and the warps of the SM with id c
+// take 32 consecutive entries of range c at a time, so that all warps resident on one
+// SM - whatever their block - hold neighbouring particles of the spatially ordered list
+// and share the background records in that SM's L1.  Once its range is used up, a warp
+// takes entries of the following ranges, checking 32 of them per round (one lane each,
+// the counters read from L2): no entry is handed out twice, since each is claimed by the
+// one atomic add on its range's counter, and a warp returns `n` only after it has seen
+// every range used up, so every entry is handed out.  *end receives the end of the range
+// the lane's entry lies in.
+__device__ __forceinline__ unsigned long long warp_fetch_sm(unsigned long long* cnt, unsigned slots,
+                                                            unsigned long long n, unsigned long long* end)
+{
+    __syncwarp();
+    const unsigned lane = threadIdx.x & 31u;
+    unsigned smid, nsmid;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+    asm volatile("mov.u32 %0, %%nsmid;" : "=r"(nsmid));
+    const unsigned ns = nsmid == 0 ? 1u : (nsmid < slots ? nsmid : slots);
+    const unsigned own = smid % ns;
+    unsigned long long base = n, hi = n;
+    if (lane == 0) {
+        const unsigned long long lo = own * n / ns, h = (own + 1ULL) * n / ns;
+        const unsigned long long got = atomicAdd(cnt + own, 32ULL);
+        if (lo + got < h) { base = lo + got; hi = h; }
+    }
+    base = __shfl_sync(0xffffffffu, base, 0);
+    hi = __shfl_sync(0xffffffffu, hi, 0);
+    for (unsigned off = 1; base == n && off < ns; off += 32) {
+        bool avail = false;
+        if (off + lane < ns) {
+            const unsigned c = (own + off + lane) % ns;
+            avail = c * n / ns + __ldcg(cnt + c) < (c + 1ULL) * n / ns;
+        }
+        unsigned m = __ballot_sync(0xffffffffu, avail);
+        while (m != 0u && base == n) {
+            const unsigned j = __ffs(m) - 1;
+            m &= m - 1;
+            if (lane == 0) {
+                const unsigned c = (own + off + j) % ns;
+                const unsigned long long lo = c * n / ns, h = (c + 1ULL) * n / ns;
+                const unsigned long long got = atomicAdd(cnt + c, 32ULL);
+                if (lo + got < h) { base = lo + got; hi = h; }
+            }
+            base = __shfl_sync(0xffffffffu, base, 0);
+            hi = __shfl_sync(0xffffffffu, hi, 0);
+        }
+    }
+    *end = hi;
+    return base == n ? n : base + lane;
+}
+
 // Set of pool entry i: the first s with i < end[s] (end holds running totals).
 __device__ __forceinline__ int set_of(const unsigned long long* end, int n_sets, unsigned long long i)
 {
@@ -273,9 +325,11 @@ __global__ void __launch_bounds__(NT, single_set(MODE) ? MINB : 512 / NT) advanc
     for (;;) {
         // the warp takes 32 consecutive entries of the (spatially ordered) work list at once,
         // so that its lanes hold neighbouring particles whatever branches they took before
-        const unsigned long long f = warp_fetch(a.fetch);
+        unsigned long long fend = n_work;
+        const unsigned long long f = a.fetch_slots ? warp_fetch_sm(a.fetch, a.fetch_slots, n_work, &fend)
+                                                   : warp_fetch(a.fetch);
         if (__shfl_sync(0xffffffffu, f, 0) >= n_work) break;
-        if (f >= n_work) continue;
+        if (f >= fend) continue;
         const unsigned long long i = a.order ? (unsigned long long)__ldg(a.order + f) : f;
         if (!a.order && a.status[i] != FTE_ALIVE) continue;
         float x = a.x[i], y = a.y[i], z = a.z[i], mu = a.mu[i], p = a.p[i];
