@@ -406,9 +406,11 @@ __global__ void __launch_bounds__(256) adj_forward_kernel(const AdvanceArgs a, c
     unsigned long long noor = 0;
     TallyRun nrun{-1, 0u};                 // the adjoint kernels run without observers
     for (;;) {
-        const unsigned long long f = warp_fetch(a.fetch);
+        unsigned long long fend = n_work;
+        const unsigned long long f = a.fetch_slots ? warp_fetch_sm(a.fetch, a.fetch_slots, n_work, &fend)
+                                                   : warp_fetch(a.fetch);
         if (__shfl_sync(0xffffffffu, f, 0) >= n_work) break;
-        if (f >= n_work) continue;
+        if (f >= fend) continue;
         const unsigned long long i = a.order ? (unsigned long long)__ldg(a.order + f) : f;
         if (!a.order && a.status[i] != FTE_ALIVE) continue;
         float x = a.x[i], y = a.y[i], z = a.z[i], mu = a.mu[i], p = a.p[i];
@@ -472,9 +474,11 @@ __global__ void __launch_bounds__(256) adj_replay_kernel(const AdvanceArgs a, co
     unsigned long long noor = 0;
     TallyRun nrun{-1, 0u};                 // the adjoint kernels run without observers
     for (;;) {
-        const unsigned long long f = warp_fetch(a.fetch);
+        unsigned long long fend = n_work;
+        const unsigned long long f = a.fetch_slots ? warp_fetch_sm(a.fetch, a.fetch_slots, n_work, &fend)
+                                                   : warp_fetch(a.fetch);
         if (__shfl_sync(0xffffffffu, f, 0) >= n_work) break;
-        if (f >= n_work) continue;
+        if (f >= fend) continue;
         const unsigned long long i = a.order ? (unsigned long long)__ldg(a.order + f) : f;
         const long long nd = k.n_dead[i];
         if (nd <= cs - a.n_table0) continue;                  // not alive at this chunk's start
@@ -518,9 +522,11 @@ __global__ void __launch_bounds__(256, 2) adj_back_kernel(const AdvanceArgs a, c
 #pragma unroll
     for (int q = 0; q < FTE_NGRAD; ++q) gsum[q] = 0.0;
     for (;;) {
-        const unsigned long long f = warp_fetch(a.fetch);
+        unsigned long long fend = n_work;
+        const unsigned long long f = a.fetch_slots ? warp_fetch_sm(a.fetch, a.fetch_slots, n_work, &fend)
+                                                   : warp_fetch(a.fetch);
         if (__shfl_sync(0xffffffffu, f, 0) >= n_work) break;
-        if (f >= n_work) continue;
+        if (f >= fend) continue;
         const unsigned long long i = a.order ? (unsigned long long)__ldg(a.order + f) : f;
         const long long nd = k.n_dead[i];
         if (nd <= cs - a.n_table0) continue;

@@ -1520,7 +1520,7 @@ fte_status adj_layout(int device, const fte_grid* g, unsigned long long n, long 
     const size_t nn = n ? n : 1;
     size_t off = 0;
     auto take = [&](size_t bytes) { const size_t o = off; off = (off + bytes + 255) & ~(size_t)255; return o; };
-    L->off_fetch = take(64);
+    L->off_fetch = take(kFetchBytes);
     L->off_norm = take(64);
     L->off_npart = take(kNormPartials * sizeof(double));
     L->off_normd = take(64);
@@ -1607,6 +1607,7 @@ fte_status adj_args(const fte_particles* P, const fte_background* bg, const fte_
     a->norm = norm;
     a->nbins = 1;
     a->fetch = (unsigned long long*)(w + L.off_fetch);
+    a->fetch_slots = bg->grid.dtype == FTE_F32 ? kFetchSlots : 0u;
     memset(k, 0, sizeof(*k));
     k->K = K;
     k->ckpt = (float*)(w + L.off_ckpt);
@@ -1696,7 +1697,7 @@ fte_status fte_adjoint_forward(fte_particles* P, const fte_background* bg, const
             a.n_end = c0 + sub < s1 ? c0 + sub : s1;
             k.ckpt_on = c0 == s0;
             if (sorting) FTE_CUDA(launch_sort(sa, st), "sort launch");
-            FTE_CUDA(cudaMemsetAsync(a.fetch, 0, sizeof(unsigned long long), st), "fetch reset");
+            FTE_CUDA(cudaMemsetAsync(a.fetch, 0, kFetchBytes, st), "fetch reset");
             FTE_CUDA(launch_adjoint_forward(a, k, L.fwd_blocks, st), "adjoint forward launch");
         }
     }
@@ -1777,7 +1778,7 @@ fte_status fte_adjoint_reverse(const fte_particles* P, const fte_background* bg,
                 a.order = sa.order;
                 a.n_order = counts + q;
             }
-            FTE_CUDA(cudaMemsetAsync(a.fetch, 0, sizeof(unsigned long long), st), "fetch reset");
+            FTE_CUDA(cudaMemsetAsync(a.fetch, 0, kFetchBytes, st), "fetch reset");
             FTE_CUDA(launch_adjoint_replay(a, k, L.rep_blocks, st), "adjoint replay launch");
         }
         for (long long q = nch - 1; q >= 0; --q) {
@@ -1787,7 +1788,7 @@ fte_status fte_adjoint_reverse(const fte_particles* P, const fte_background* bg,
                 a.order = orders + (size_t)q * n;
                 a.n_order = counts + q;
             }
-            FTE_CUDA(cudaMemsetAsync(a.fetch, 0, sizeof(unsigned long long), st), "fetch reset");
+            FTE_CUDA(cudaMemsetAsync(a.fetch, 0, kFetchBytes, st), "fetch reset");
             FTE_CUDA(launch_adjoint_back(a, k, L.rev_blocks, st), "adjoint backward launch");
         }
     }
