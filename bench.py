@@ -527,6 +527,16 @@ def run_profile_case(args):
         bg = device_background(api, w, configs.build_background(w), args.layout, args.dtype)
     if args.no_obs:
         w.observers = []
+    if args.profile_adjoint:
+        # the adjoint's kernels on the same small case: forward and reverse over the launches'
+        # steps (E^-3 injection, smoothed intensity at the middle of the run), no checks
+        res = adjoint_times(api, bg, w, w.n_particles, 256 * args.launches, args.checkpoint_every,
+                            args.sort_every, fd=False)
+        print(json.dumps({"case": "profile", "grid": args.grid, "dtype": args.dtype, "adjoint": True,
+                          **{k: res[k] for k in ("particles", "steps", "alive_particle_steps", "plain_s",
+                                                 "adjoint_forward_s", "adjoint_forward_reverse_s",
+                                                 "adj_over_fwd")}}))
+        return
     pool = api.Particles(w.n_particles)
     tally = api.Tally(w.observers)
     api.fte_tally_reset(tally)
@@ -1190,6 +1200,8 @@ def main():
     ap.add_argument("--dtype", default="f32", choices=["f32", "bf16", "f16"], help="storage of --case profile")
     ap.add_argument("--profile-particles", type=int, default=1 << 18, help="particles of --case profile")
     ap.add_argument("--no-obs", action="store_true", help="--case profile without observers")
+    ap.add_argument("--profile-adjoint", action="store_true",
+                    help="--case profile: time the adjoint's forward and reverse passes instead")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)

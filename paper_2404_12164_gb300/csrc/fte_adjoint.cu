@@ -446,19 +446,15 @@ __global__ void __launch_bounds__(256) adj_forward_kernel(const AdvanceArgs a, c
 }
 
 // ---------------------------------------------------------------------------
-// Reverse pass, one launch per segment from the last to the first: each
-// particle alive at the segment's start (in spatial order of its checkpoint)
-// loads its adjoints, replays the segment into the thread's scratch
-// (scratch[(kk * 5 + c) * threads + tid]) and walks it backwards.  The launch
-// of the first segment adds the injection-index term and reduces the gradients.
-// ---------------------------------------------------------------------------
 // Reverse pass, in two phases per checkpoint segment, each launched chunk by chunk
 // (chunk [k.c_start, k.c_end), the particles reordered before the chunk's replay):
 // the replay walks the chunk forwards from the checkpoint (or from the state the
 // previous chunk left in k.carry) and stores every start-of-step state at the
 // particle's position f in the chunk's order; the backward phase walks the chunks
 // from the last, in the same order as their replay, and runs the step VJPs over
-// the stored states, carrying the adjoints between launches in k.adj.
+// the stored states, carrying the adjoints between launches in k.adj.  The launch
+// of the run's first chunk adds the injection-index term and reduces the gradients.
+// ---------------------------------------------------------------------------
 template <int DT, int LAY>
 __global__ void __launch_bounds__(256) adj_replay_kernel(const AdvanceArgs a, const AdjK k)
 {
