@@ -366,7 +366,12 @@ fte_status fte_stream_scales(const fte_background* bg, const void* host_snapshot
    sequences: the same snapshot of another period) is not copied again, so a
    ring of n_snap slots over a periodic sequence copies each snapshot once.
    slot_state (HOST, ring entries, caller-owned, -1 = empty before the first
-   call) records the unwrapped snapshot each slot holds and is updated.  ws as for fte_advance with n_steps = the longest run.
+   call) records the unwrapped snapshot each slot holds and is updated.  Consecutive
+   runs are advanced together, one fte_advance call per group of up to 8 runs
+   (ramping 1, 1, 2, 4, 8 from the call's start), as long as a group's snapshots fit
+   the ring with one slot to spare (ring >= 3) and its steps fit ws's time table:
+   ws as for fte_advance with n_steps at least the longest run of the plan
+   (n_end - n_start steps allow full groups).
    Work of earlier calls on either stream is waited for.  EINVAL/ENOMEM for a
    missing or undersized staging buffer.  Asynchronous. */
 fte_status fte_advance_streamed(fte_particles* P, const fte_background* bg, const void* host_snapshots,

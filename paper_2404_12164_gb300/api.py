@@ -677,9 +677,8 @@ class SnapshotStream:
 def fte_advance_streamed(pool, bg, stream_state, params, tally, n_start, n_end, ws=None, stream=None):
     """fte_advance over a ring background, uploading snapshots as the run reaches them."""
     ws = ws if ws is not None else Workspace(bg.dev.device)
-    plan = fte_stream_plan(bg, params, n_start, n_end)
-    longest = int((plan[:, 1] - plan[:, 0]).max()) if len(plan) else 0
-    buf = ws.ensure(fte_workspace_bytes(bg, tally, pool.count, longest, bg.dev.device.index))
+    # a time table for the whole range lets the library advance several runs per call
+    buf = ws.ensure(fte_workspace_bytes(bg, tally, pool.count, n_end - n_start, bg.dev.device.index))
     pc = params_c(params)
     check(A.lib().fte_advance_streamed(C.byref(pool.c), C.byref(bg.c), C.c_void_p(stream_state.host.data_ptr()),
                                        C.byref(pc), C.byref(tally.c), int(n_start), int(n_end),

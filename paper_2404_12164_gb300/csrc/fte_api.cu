@@ -6,7 +6,9 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <atomic>
+#include <functional>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -217,6 +219,7 @@ struct WsLayout {
 
 constexpr int kMaxSmemBins = 16384;    // 3 x 4 B per bin in shared memory
 constexpr long long kChunkSteps = 1024;
+constexpr size_t kStreamGroupRuns = 8;   // snapshot intervals per fte_advance call of a streamed run
 // Work counters of the step kernel: one per SM range (warp_fetch_sm), for up to 1024 SM ids.
 constexpr unsigned kFetchSlots = 1024;
 constexpr size_t kFetchBytes = kFetchSlots * sizeof(unsigned long long);
@@ -1997,8 +2000,8 @@ fte_status fte_advance_streamed(fte_particles* P, const fte_background* bg, cons
     }
     // bring unwrapped snapshot u into its slot (unless already there - for a
     // periodic sequence, the same snapshot of an earlier period counts - or, for a
-    // prefetch, the slot is in use by the current run)
-    auto ensure = [&](int64_t u, int busy0, int busy1, bool prefetch) {
+    // prefetch, the slot is in use by the current group)
+    auto ensure = [&](int64_t u, const std::function<bool(int)>& busy, bool prefetch) {
         if (result != FTE_OK) return;
         const int slot = (int)pmod(u, R);
         if (slot_state[slot] == u) return;
@@ -2006,7 +2009,7 @@ fte_status fte_advance_streamed(fte_particles* P, const fte_background* bg, cons
             slot_state[slot] = u;
             return;
         }
-        if (prefetch && (slot == busy0 || slot == busy1)) return;
+        if (prefetch && busy(slot)) return;
         if (has_freed[slot]) {
             const cudaError_t e = cudaStreamWaitEvent(xs, freed[slot], 0);
             if (e != cudaSuccess) { fail_cuda(e, "copy wait"); return; }
@@ -2017,35 +2020,59 @@ fte_status fte_advance_streamed(fte_particles* P, const fte_background* bg, cons
         has_ready[slot] = 1;
         slot_state[slot] = u;
     };
-    for (size_t k = 0; k < runs.size() && result == FTE_OK; ++k) {
-        const Run& r = runs[k];
-        const bool pair = r.key >= 0;
-        const int64_t u0 = pair ? r.key : -1 - r.key;
-        const int64_t u1 = pair ? r.key + 1 : u0;
-        const int s0 = (int)pmod(u0, R), s1 = (int)pmod(u1, R);
-        ensure(u0, -1, -1, false);
-        ensure(u1, -1, -1, false);
-        // the snapshots after this pair, as far ahead as the slots that this run does not
-        // use allow (R - 2 of them), while this run computes
-        for (int64_t nx = u1 + 1; nx <= u1 + R - 2 && result == FTE_OK; ++nx) {
+    // Consecutive runs are advanced in groups, one fte_advance call each, ramping up as
+    // 1, 1, 2, 4, then kStreamGroupRuns runs per call: every call ends with its two
+    // halves joined and a partial reordering chunk, so one call per snapshot interval
+    // leaves the GPU idle at each interval's end; the ramp lets the first intervals
+    // start as soon as their own snapshots are in.  A group's snapshots must fit the
+    // ring together, leaving one slot to prefetch into (R >= 3), and its steps the
+    // workspace's time table.
+    auto run_lo = [](const Run& r) { return r.key >= 0 ? r.key : -1 - r.key; };
+    auto run_hi = [](const Run& r) { return r.key >= 0 ? r.key + 1 : -1 - r.key; };
+    const int64_t span_max = R >= 3 ? R - 1 : R;
+    int device = 0;
+    if (result == FTE_OK) {
+        const cudaError_t e = cudaGetDevice(&device);
+        if (e != cudaSuccess) fail_cuda(e, "cudaGetDevice");
+    }
+    const size_t ws0 = result == FTE_OK ? fte_workspace_bytes(device, &g, t, P->count, 0) : 0;
+    auto fits = [&](int64_t steps) { return ws0 + (size_t)steps * sizeof(StepEntry) + 256 <= ws_bytes; };
+    size_t k = 0;
+    for (int gi = 0; k < runs.size() && result == FTE_OK; ++gi) {
+        const size_t want = gi < 2 ? 1 : (gi == 2 ? 2 : (gi == 3 ? 4 : kStreamGroupRuns));
+        size_t k1 = k + 1;
+        int64_t ulo = run_lo(runs[k]), uhi = run_hi(runs[k]);
+        while (k1 < runs.size() && k1 - k < want) {
+            const int64_t lo2 = std::min(ulo, run_lo(runs[k1])), hi2 = std::max(uhi, run_hi(runs[k1]));
+            if (hi2 - lo2 + 1 > span_max || !fits(runs[k1].b - runs[k].a)) break;
+            ulo = lo2; uhi = hi2; ++k1;
+        }
+        auto busy = [&](int slot) { return pmod(slot - ulo, R) <= uhi - ulo; };
+        for (int64_t u = ulo; u <= uhi && result == FTE_OK; ++u) ensure(u, busy, false);
+        // the snapshots after this group, as far ahead as the slots that it does not
+        // use allow, while it computes
+        for (int64_t nx = uhi + 1; nx <= uhi + R - 2 && result == FTE_OK; ++nx) {
             if (!g.periodic && nx > g.n_snap - 1) break;
-            ensure(nx, s0, s1, true);
+            ensure(nx, busy, true);
         }
         if (result != FTE_OK) break;
-        for (int sl : {s0, s1}) {
+        for (int64_t u = ulo; u <= uhi; ++u) {
+            const int sl = (int)pmod(u, R);
             if (has_ready[sl]) {
                 const cudaError_t e = cudaStreamWaitEvent(cs, ready[sl], 0);
                 if (e != cudaSuccess) { fail_cuda(e, "compute wait"); break; }
             }
         }
         if (result != FTE_OK) break;
-        const fte_status st = fte_advance(P, bg, prm, t, r.a, r.b, ws, ws_bytes, compute_stream);
+        const fte_status st = fte_advance(P, bg, prm, t, runs[k].a, runs[k1 - 1].b, ws, ws_bytes, compute_stream);
         if (st != FTE_OK) { result = st; break; }
-        for (int sl : {s0, s1}) {
+        for (int64_t u = ulo; u <= uhi; ++u) {
+            const int sl = (int)pmod(u, R);
             const cudaError_t e = cudaEventRecord(freed[sl], cs);
             if (e != cudaSuccess) { fail_cuda(e, "event record"); break; }
             has_freed[sl] = 1;
         }
+        k = k1;
     }
     for (int k = 0; k < R; ++k) {
         if (ready[k]) cudaEventDestroy(ready[k]);
