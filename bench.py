@@ -24,13 +24,15 @@ sample of the same workload.
 The device background uses the cell record layout by default (`--layout pair`
 measures records that hold a cell and its upper r-neighbour, converted on the
 device from the uploaded cell records).  The default
-line also carries the 16-bit storage forms (`forms`) and the adjoint's cost on a
-slice of the workload (`adjoint`).  Other cases, each one
+line also carries the 16-bit storage forms (`forms`), the adjoint's cost on a
+slice of the workload (`adjoint`), the 64-set ensemble (`ensemble`, the same three
+arms as `--case ensemble`) and the block-AMR workload (`amr`).  Other cases, each one
 JSON line: `--case amr` (the CIR on a 39,520-leaf block-AMR grid, 1e7 protons,
 FP32/BF16/FP16), `--case ensemble` (64 parameter sets, 2e7 protons: set after
 set, one ensemble launch, autotuned and graph-captured), `--case adjoint` (the
 full 4-day adjoint with a finite-difference check), `--case profile` (small
-cases for ncu captures).
+cases for ncu captures), `--case slices` (the rate per 1024-step slice of the 4-day run, against
+the number of alive particles).
 """
 import argparse
 import dataclasses
@@ -430,6 +432,12 @@ def run_gpu(args):
         "forms": forms,
         "adjoint": adjoint,
     }
+    if ws == 1 and not args.no_ensemble:
+        # the 64-set ensemble on the same background (one GPU only)
+        eclk = Clocks(local)
+        eclk.start()
+        result["ensemble"] = ensemble_measure(api, args, bg)
+        result["ensemble"]["clocks"] = eclk.stop()
     if ws == 1 and not args.no_amr:
         # the block-AMR workload (the largest single-GPU configuration), one GPU only
         aclk = Clocks(local)
@@ -721,21 +729,77 @@ def run_amr_case(args):
                       "data": "synthetic", **res, "clocks": clocks.result}), flush=True)
 
 
-def run_ensemble_case(args):
-    """Ensemble workload (cir_ensemble_64): 64 parameter sets with uneven counts.  Three arms on
-    the same particles: the single-set kernel run set after set; the ensemble kernel with the
-    default launch configuration; the autotuned configuration replayed as one CUDA graph."""
+def run_slices_case(args):
+    """Rate of the benchmark workload per slice of --slice-steps steps: one pass (inject + 4 days)
+    with CUDA events around each fte_advance call of one slice, after one untimed pass; shows how
+    the rate follows the number of alive particles as absorption empties the pool."""
     import torch
     from paper_2404_12164_gb300 import api, build
-    from paper_2404_12164_gb300 import _abi as A
+    build.build()
+    torch.cuda.set_device(0)
+    w, fields = build_workload()
+    w.params.sort_every = args.sort_every
+    bg = device_background(api, w, fields, args.layout)
+    del fields
+    pool = api.Particles(w.n_particles)
+    tally = api.Tally(w.observers)
+    wsp = api.Workspace()
+    wsp.ensure(api.fte_workspace_bytes(bg, tally, w.n_particles, args.slice_steps))
+    S = args.slice_steps
+
+    def one_pass(record):
+        pool.c.count = 0
+        api.fte_tally_reset(tally)
+        api.fte_inject(pool, bg, w.inject, w.n_particles, tally, check_failed=False)
+        out, prev = [], 0
+        for c in range(0, w.n_steps, S):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            api.fte_advance(pool, bg, w.params, tally, c, min(c + S, w.n_steps), wsp)
+            e1.record()
+            if record:
+                torch.cuda.synchronize()
+                done = int(tally.ledger_n.cpu().numpy()[6])
+                out.append({"first_step": c, "steps": min(S, w.n_steps - c), "particle_steps": done - prev,
+                            "ms": e0.elapsed_time(e1)})
+                prev = done
+        torch.cuda.synchronize()
+        return out
+
+    one_pass(False)
+    sl = one_pass(True)
+    for x in sl:
+        x["alive_mean"] = x["particle_steps"] / x["steps"]
+        x["rate"] = x["particle_steps"] / (x["ms"] / 1e3)
+    tot_ms = sum(x["ms"] for x in sl)
+    print(json.dumps({"case": "slices", "workload": "cir_uniform_1e6", "slice_steps": S,
+                      "rate": sum(x["particle_steps"] for x in sl) / (tot_ms / 1e3),
+                      "note": "rate of the slices' sum; one fte_advance call per slice, so every slice ends "
+                              "with both half-pools joined",
+                      "slices": sl}), flush=True)
+
+
+def run_ensemble_case(args):
+    """Ensemble workload (cir_ensemble_64) on its own: see ensemble_measure."""
+    import torch
+    from paper_2404_12164_gb300 import api, build
     build.build()
     torch.cuda.set_device(0)
     w0, fields = build_workload()
+    bg = device_background(api, w0, fields, args.layout)
+    del fields
+    print(json.dumps(ensemble_measure(api, args, bg)), flush=True)
+
+
+def ensemble_measure(api, args, bg):
+    """Ensemble workload (cir_ensemble_64): 64 parameter sets with uneven counts on the
+    cir_uniform_1e6 background `bg`.  Three arms on the same particles: the single-set kernel run
+    set after set; the ensemble kernel with the default launch configuration; the autotuned
+    configuration replayed as one CUDA graph."""
+    import torch
     w = configs.cir_ensemble_64(n_steps=args.ens_steps)
     w.params.sort_every = args.sort_every
     sets, n_steps, n_tot = w.sets, w.n_steps, w.n_particles
-    bg = device_background(api, w, fields, args.layout)
-    del fields
     side = torch.cuda.Stream()
     pool = api.Particles(n_tot)
     tally = api.Tally(w.observers, n_sets=len(sets))
@@ -810,7 +874,9 @@ def run_ensemble_case(args):
     # per-set tally errors by batch means over the 32 particle-id classes (graph arm's last step)
     rel = [e for e in (tally.batch_means(0, set=k)[1] for k in range(len(sets))) if e is not None]
     counts = [s.count for s in sets]
-    print(json.dumps({
+    del g, pool, tally, ws
+    torch.cuda.empty_cache()
+    return {
         "case": "ensemble", "metric": METRIC, "value": graph_rate, "unit": UNIT, "n_gpus": 1,
         "steps": args.ens_timed, "warmup": 1, "ms_per_step": graph_ms, "higher_is_better": True,
         "dtype": "f32", "data": "synthetic",
@@ -831,7 +897,7 @@ def run_ensemble_case(args):
                                                      "config": best}},
         "speedup_vs_single_set_kernel": graph_rate / plain_rate,
         "autotune": [{"config": c, "rate": r} for c, r in tried],
-    }), flush=True)
+    }
 
 
 ADJ_OBS = dict(r_o=1.0, sigma_r=0.02, e_c=0.1, sigma_lnE=0.1, t_c=2 * 86400.0, sigma_t=3600.0)
@@ -1206,7 +1272,9 @@ def l2_probe(mib=64, threads=152 * 2048, loads=256, reps=5):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--case", default="bench", choices=["bench", "profile", "amr", "ensemble", "adjoint", "stream"])
+    ap.add_argument("--case", default="bench",
+                    choices=["bench", "profile", "amr", "ensemble", "adjoint", "stream", "slices"])
+    ap.add_argument("--slice-steps", type=int, default=1024, help="steps per slice of --case slices")
     ap.add_argument("--ring", type=int, default=3, help="resident snapshot slots of --case stream")
     ap.add_argument("--stream-dtype", default="f32", choices=["f32", "bf16", "f16"],
                     help="storage of the slots (and of the resident comparison) of --case stream")
@@ -1235,6 +1303,8 @@ def main():
                     help="record layout of the device background (pair: a cell and its r-neighbour per record)")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-amr", action="store_true", help="leave the block-AMR workload out of the default line")
+    ap.add_argument("--no-ensemble", action="store_true",
+                    help="leave the 64-set ensemble workload out of the default line")
     ap.add_argument("--adj-slice", type=int, default=4096, help="steps of the adjoint measurement in the default run")
     ap.add_argument("--sort-every", type=int, default=64,
                     help="steps between spatial reorderings of the alive particles (0: off)")
@@ -1245,6 +1315,8 @@ def main():
         run_amr_case(args)
     elif args.case == "ensemble":
         run_ensemble_case(args)
+    elif args.case == "slices":
+        run_slices_case(args)
     elif args.case == "adjoint":
         run_adjoint_case(args)
     elif args.case == "stream":

@@ -661,6 +661,7 @@ fte_status fte_advance(fte_particles* P, const fte_background* bg, const fte_par
             ak.x = P->x + base; ak.y = P->y + base; ak.z = P->z + base; ak.mu = P->mu + base;
             ak.p = P->p + base; ak.w = P->w + base; ak.id = P->id + base; ak.status = P->status + base;
             ak.n_particles = cnt;
+            ak.compact = 1;
             memset(&sh[k], 0, sizeof(SortArgs));
             sort_carve(gk, cnt, p, &sh[k]);
             p += sort_scratch_bytes(gk, cnt);

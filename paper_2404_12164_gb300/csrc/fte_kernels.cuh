@@ -48,6 +48,8 @@ struct AdvanceArgs {
     float* part;                  // per-block partial histograms [grid][3][nbins]
     unsigned long long* fetch;    // particle counter for dynamic assignment
     unsigned fetch_slots;         // > 0: `fetch` holds that many per-SM range counters
+    int compact;                  // one of two half-pools on two streams: a launch with fewer ordered
+                                  // particles than resident threads keeps one per thread (see advance_kernel)
     double* ledger_w;
     unsigned long long* ledger_n;
     double* cls;                  // optional [set][bin][FTE_NCLASS]: S by particle-id class

@@ -321,12 +321,24 @@ __global__ void __launch_bounds__(NT, single_set(MODE) ? MINB : 512 / NT) advanc
 
     const float I0 = single_set(MODE) ? (float)__ldg(a.norm) : 0.f;
     const unsigned long long n_work = a.order ? (unsigned long long)__ldg(a.n_order) : a.n_particles;
+    // A launch of one of two half-pools (on two streams) with fewer alive particles than
+    // resident threads keeps only the blocks that give each thread one particle: the others
+    // leave at once, so that their SM slots go to the other half's launch (a persistent block
+    // holds its slot until its last warp ends).  The blocks that stay take work from one global
+    // counter.  A pool launched alone keeps all blocks: there the freed slots would stay idle.
+    unsigned fetch_slots = a.fetch_slots;
+    if (MODE == kModeSingleGlobal && a.order && a.compact) {
+        if (n_work < (unsigned long long)gridDim.x * NT) {
+            fetch_slots = 0;
+            if (blockIdx.x >= (n_work + NT - 1) / NT) return;
+        }
+    }
     unsigned long long nsteps = 0, noor = 0;
     for (;;) {
         // the warp takes 32 consecutive entries of the (spatially ordered) work list at once,
         // so that its lanes hold neighbouring particles whatever branches they took before
         unsigned long long fend = n_work;
-        const unsigned long long f = a.fetch_slots ? warp_fetch_sm(a.fetch, a.fetch_slots, n_work, &fend)
+        const unsigned long long f = fetch_slots ? warp_fetch_sm(a.fetch, fetch_slots, n_work, &fend)
                                                    : warp_fetch(a.fetch);
         if (__shfl_sync(0xffffffffu, f, 0) >= n_work) break;
         if (f >= fend) continue;
