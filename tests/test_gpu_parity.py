@@ -294,6 +294,27 @@ def test_spatial_reordering_changes_nothing(cir_small):
     assert np.array_equal(a["ledger_n"], b["ledger_n"])
 
 
+def test_half_pools_and_block_compaction_change_nothing():
+    """A reordered pool of more particles than the step kernel has resident threads runs as two
+    halves on two streams, and each half (fewer particles than resident threads) launches on
+    only the blocks that give each thread one particle: states, counts and the ledger equal those
+    of the unordered run on one stream."""
+    import dataclasses
+    import torch
+    w = configs.scaled(configs.cir_uniform_1e6(), nr=128, nth=30, nph=90, n_particles=120_000)
+    f = configs.build_background(w)
+    threads = torch.cuda.get_device_properties(0).multi_processor_count * 512
+    assert threads <= w.n_particles < 2 * threads
+    a = gpu_run(w, f, 300, params=dataclasses.replace(w.params, sort_every=0))
+    b = gpu_run(w, f, 300, params=dataclasses.replace(w.params, sort_every=64))
+    for k in ("x", "y", "z", "mu", "p", "w", "status"):
+        assert np.array_equal(a["states"][300][k], b["states"][300][k]), k
+    assert np.array_equal(a["tallies"][0]["C"], b["tallies"][0]["C"])
+    assert np.allclose(a["tallies"][0]["S"], b["tallies"][0]["S"], rtol=1e-9, atol=1e-12)
+    assert np.array_equal(a["ledger_n"], b["ledger_n"])
+    assert int(a["ledger_n"][6]) > 0
+
+
 def test_checkpoint_resume_is_bit_exact(tmp_path, parker):
     """A run saved to disk after 150 steps and resumed in a fresh pool ends where the
     uninterrupted run ends (every random number depends on (seed, set, step, id) only)."""
