@@ -388,8 +388,9 @@ def run_gpu(args):
     adjoint = None
     if not args.no_adjoint:
         adjoint = adjoint_times(api, bg, w, n_part, args.adj_slice, args.checkpoint_every, args.sort_every)
-        adjoint["note"] = ("first %d steps of the workload, E^-3 injection over 50 keV-5 MeV; bench.py --case "
-                           "adjoint runs the full 4 days" % args.adj_slice)
+        adjoint["note"] = ("first %d of the workload's %d steps, E^-3 injection over 50 keV-5 MeV, smoothed "
+                           "intensity at 1 au (E_c 100 keV, t_c %.0f s)" % (min(args.adj_slice, n_steps), n_steps,
+                                                                          adjoint["t_c"]))
 
     roofline = roofline_record(intervals, total_steps // ws, ALG_BYTES, l1, l2_gbs, measured_traffic(args.layout))
     # our kernels per timed step: inject, and per advance call the two normalisation
@@ -1305,7 +1306,8 @@ def main():
     ap.add_argument("--no-amr", action="store_true", help="leave the block-AMR workload out of the default line")
     ap.add_argument("--no-ensemble", action="store_true",
                     help="leave the 64-set ensemble workload out of the default line")
-    ap.add_argument("--adj-slice", type=int, default=4096, help="steps of the adjoint measurement in the default run")
+    ap.add_argument("--adj-slice", type=int, default=34_560,
+                    help="steps of the adjoint measurement in the default run (default: the whole 4 days)")
     ap.add_argument("--sort-every", type=int, default=64,
                     help="steps between spatial reorderings of the alive particles (0: off)")
     args = ap.parse_args()
