@@ -117,7 +117,7 @@ def measured_traffic(layout, dtype="f32"):
     """The committed ncu record of the step kernel for one storage type (DRAM bytes per alive
     particle-step of the profile case, and its L1 data-pipe figures), or None when the kernel
     sources changed since, the record is for another record layout or has no capture of
-    `dtype`."""
+    `dtype` ("f32", "bf16", "f16" on the uniform grid, "amr_f32" on the block-AMR grid)."""
     try:
         with open(TRAFFIC_FILE) as f:
             d = json.load(f)
@@ -681,7 +681,8 @@ def amr_measure(api, args, l1=None, forms=True, cpu=True, clocks=None):
                    "tally_rel_err": errs,
                    "tally_rel_err_method": "per observer: relative standard error of the total occupancy from "
                                            "32 batch means over particle-id classes"},
-        "roofline": roofline_record(iv, done, alg, l1, None, None),
+        "roofline": roofline_record(iv, done, alg, l1, None,
+                                    measured_traffic(layout, "amr_f32") if layout == "cell" else None),
         "forms": out_forms,
     }
     if cpu:
