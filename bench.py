@@ -224,6 +224,61 @@ def build_workload():
     return w, f
 
 
+def e2e_breakdown(api, pool, ring_bg, sstream, w, tally, wsp, id_base, stream, barrier):
+    """Where the end-to-end step's time goes, from three more steps on the streamed ring:
+    the streamed calls with every snapshot already in its slot (the cost of advancing in
+    snapshot-interval groups, no copy), a step with every snapshot copied (device-timed,
+    without the host's read of the results), and the page-locked host-to-device copy rate
+    of the snapshots with nothing else running.  (An event recorded on the copy stream
+    after the streamed call returns does not mark its last copy: the call enqueues more
+    launches than CUDA's launch queue holds, so it returns near the end of the step.)"""
+    import torch
+
+    def ev():
+        return torch.cuda.Event(enable_timing=True)
+
+    n_part, n_steps = w.n_particles, w.n_steps
+    res = {}
+    # 1. no copies: after a streamed step every slot holds its snapshot (periodic sequence)
+    barrier()
+    a, b = ev(), ev()
+    a.record(stream)
+    pool.c.count = 0
+    api.fte_tally_reset(tally)
+    api.fte_inject(pool, ring_bg, w.inject, n_part, tally, id_base=id_base, check_failed=False)
+    api.fte_advance_streamed(pool, ring_bg, sstream, w.params, tally, 0, n_steps, wsp)
+    b.record(stream)
+    barrier()
+    ms = a.elapsed_time(b)
+    res["streamed_no_copy"] = {"value": int(tally.ledger_n.cpu().numpy()[6]) / (ms / 1e3), "ms": ms}
+    # 2. a step with every snapshot copied
+    a, b = ev(), ev()
+    a.record(stream)
+    pool.c.count = 0
+    sstream.slots[:] = -1
+    api.fte_tally_reset(tally)
+    sstream.load(0)
+    api.fte_inject(pool, ring_bg, w.inject, n_part, tally, id_base=id_base, check_failed=False)
+    api.fte_advance_streamed(pool, ring_bg, sstream, w.params, tally, 0, n_steps, wsp)
+    b.record(stream)
+    barrier()
+    ms = a.elapsed_time(b)
+    res["streamed_with_copies"] = {"value": int(tally.ledger_n.cpu().numpy()[6]) / (ms / 1e3), "ms": ms}
+    # 3. the snapshot copies alone, one after another on the copy stream
+    sstream.slots[:] = -1
+    barrier()
+    a, b = ev(), ev()
+    a.record(sstream.copy_stream)
+    for u in range(w.grid.n_snap):
+        sstream.load(u)
+    b.record(sstream.copy_stream)
+    barrier()
+    ms = a.elapsed_time(b)
+    res["h2d_copies_alone"] = {"gbs": w.grid.n_snap * api.fte_snapshot_bytes(ring_bg) / (ms / 1e3) / 1e9,
+                               "ms": ms}
+    return res
+
+
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
@@ -359,6 +414,7 @@ def run_gpu(args):
     e_s = time.perf_counter() - e0
     (e_s,) = pdist.max_over_ranks([e_s], device="cuda")
     e2e_value = e_steps * ws / e_s
+    e2e_parts = e2e_breakdown(api, pool, ring_bg, sstream, w, tally, wsp, id_base, stream, barrier)
     del sstream, ring_bg
     torch.cuda.empty_cache()
 
@@ -426,7 +482,8 @@ def run_gpu(args):
                                                   "observer are correlated, so it understates the error"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d_bytes),
                 "d2h_bytes_per_step": int(out_host.nbytes + 2 * 8 * A.FTE_LEDGER),
-                "path": "fte_advance_streamed, %d-slot ring, each snapshot copied once per step" % w.grid.n_snap},
+                "path": "fte_advance_streamed, %d-slot ring, each snapshot copied once per step" % w.grid.n_snap,
+                "of_value": e2e_value / value, "breakdown": e2e_parts},
         "gpu_launches": launches_per_step * args.steps,
         "roofline": roofline,
         "clocks": cl,

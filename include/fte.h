@@ -23,9 +23,14 @@
  *     Pointers documented HOST are host memory owned by the caller.
  *   - Streams: `stream` is a cudaStream_t (NULL = legacy default stream).  All
  *     work is enqueued asynchronously on it unless the call says it synchronises.
- *   - Errors: every call returns an fte_status; on failure nothing was enqueued
- *     unless stated, and fte_last_error() returns a message (thread-local, valid
- *     until the next call on the same thread).  No C++ exception crosses the ABI.
+ *   - Errors: every call returns an fte_status, and fte_last_error() returns a
+ *     message (thread-local, valid until the next call on the same thread).  No
+ *     C++ exception crosses the ABI.  Argument errors are found before anything
+ *     is enqueued, so the caller's buffers are unchanged.  A CUDA error returned
+ *     by a launch, copy or event call (FTE_ECUDA) can come after part of the
+ *     call's work was enqueued; that work stays enqueued, a call that forked a
+ *     second stream (fte_advance's half-pools) has not joined it back, and, as
+ *     after any CUDA error, the context may be unusable.
  *   - Random numbers: one Philox4x32-10 block (Salmon et al. 2011) per particle
  *     and step, key (seed, set_id), counter (step, particle id, tag, 0); tag 0
  *     transport, tag 1 injection draw, tag 2 injection position attempt.
