@@ -29,8 +29,9 @@
  *     is enqueued, so the caller's buffers are unchanged.  A CUDA error returned
  *     by a launch, copy or event call (FTE_ECUDA) can come after part of the
  *     call's work was enqueued; that work stays enqueued, a call that forked a
- *     second stream (fte_advance's half-pools) has not joined it back, and, as
- *     after any CUDA error, the context may be unusable.
+ *     second stream (the half-pools of fte_advance and of the adjoint passes) has
+ *     not joined it back, and, as after any CUDA error, the context may be
+ *     unusable.
  *   - Random numbers: one Philox4x32-10 block (Salmon et al. 2011) per particle
  *     and step, key (seed, set_id), counter (step, particle id, tag, 0); tag 0
  *     transport, tag 1 injection draw, tag 2 injection position attempt.
@@ -543,14 +544,21 @@ typedef struct fte_smooth_obs {
    counts and observables, the replay scratch of the reverse pass (the states
    of one segment: checkpoint_every x 20 bytes per particle, e.g. 5.1 GB for
    1e6 particles and 256 steps), the particle orders of its 64-step chunks and
-   the time table.  0 on error. */
+   the time table.  A pool of at least one wave of the forward kernel's threads
+   (reordering on) gets two such regions, one per half of the pool (below).
+   0 on error. */
 size_t fte_adjoint_workspace_bytes(int device, const fte_grid* g, uint64_t n_particles, int64_t n_steps,
                                    int checkpoint_every);
 
 /* Forward pass: advances P from n_start to n_end exactly as fte_advance would
    (no tally, no ledger), storing checkpoints in ws, and writes J to dev_out[0]
    (DEVICE, 1 + FTE_NGRAD doubles; the rest is zeroed).  dev_J_particle (DEVICE,
-   optional, P->count doubles): each particle's J_i.  Asynchronous. */
+   optional, P->count doubles): each particle's J_i.  With reordering on
+   (prm->sort_every > 0), a pool of at least one wave of the forward kernel's
+   threads is advanced as two halves, each in its own region of ws, on `stream`
+   and a second stream forked from and joined back to it (in turn on `stream`
+   while it is being captured); every particle's results are those of one pool.
+   Asynchronous. */
 fte_status fte_adjoint_forward(fte_particles* P, const fte_background* bg, const fte_params* prm,
                                const fte_smooth_obs* obs, int64_t n_start, int64_t n_end, int checkpoint_every,
                                double* dev_out, double* dev_J_particle, void* ws, size_t ws_bytes, void* stream);
@@ -563,7 +571,8 @@ fte_status fte_adjoint_forward(fte_particles* P, const fte_background* bg, const
    spec (HOST, optional): the injection that produced P at n_start; with a power
    law (energy 1) the dJ/dgamma entry is filled, otherwise it is 0.
    dev_per_particle (DEVICE, optional, n x (1 + FTE_NGRAD) floats): each
-   particle's J_i and gradients.  Asynchronous. */
+   particle's J_i and gradients.  The pool is split into the same halves as in
+   the forward pass.  Asynchronous. */
 fte_status fte_adjoint_reverse(const fte_particles* P, const fte_background* bg, const fte_params* prm,
                                const fte_smooth_obs* obs, const fte_inject_spec* spec, int64_t n_start,
                                int64_t n_end, int checkpoint_every, double* dev_out, float* dev_per_particle,

@@ -1631,6 +1631,81 @@ fte_status adj_args(const fte_particles* P, const fte_background* bg, const fte_
     return FTE_OK;
 }
 
+// A pool of at least one wave of the forward kernel's threads is advanced, in both
+// passes, as two halves, each with its own region of the workspace (its own strides,
+// orders, checkpoints and counters), on the caller's stream and a second stream forked
+// from and joined back to it, as fte_advance does with its half-pools: one half's
+// launches fill the SMs that the end of the other half's launches leaves idle.  Every
+// particle's result is unchanged (only the order of the FP64 sums of the totals is
+// not).  The split depends only on the pool, the device and whether reordering is on,
+// so a forward and a reverse pass over the same pool lay out the workspace alike.
+struct AdjPlan {
+    int halves;
+    unsigned long long base[2], cnt[2];
+    AdjLayout L[2];
+    size_t off[2], total;
+};
+
+fte_status adj_plan(int device, const fte_grid* g, unsigned long long n, long long n_steps, int K, bool sorting,
+                    AdjPlan* p)
+{
+    AdjLayout full;
+    fte_status s = adj_layout(device, g, n, n_steps, K, sorting, &full);
+    if (s != FTE_OK) return s;
+    const unsigned long long wave = (unsigned long long)full.fwd_blocks * 256ull;
+    p->base[0] = p->base[1] = 0;
+    p->cnt[1] = 0;
+    p->off[0] = p->off[1] = 0;
+    if (!sorting || n < wave || n < 2) {
+        p->halves = 1;
+        p->cnt[0] = n;
+        p->L[0] = full;
+        p->total = full.total;
+        return FTE_OK;
+    }
+    p->halves = 2;
+    p->cnt[0] = n / 2;
+    p->base[1] = n / 2;
+    p->cnt[1] = n - n / 2;
+    for (int h = 0; h < 2; ++h) {
+        s = adj_layout(device, g, p->cnt[h], n_steps, K, sorting, &p->L[h]);
+        if (s != FTE_OK) return s;
+    }
+    p->off[1] = (p->L[0].total + 255) & ~(size_t)255;
+    p->total = p->off[1] + p->L[1].total;
+    return FTE_OK;
+}
+
+// The particles [base, base + cnt) of P as a pool of their own.
+fte_particles sub_pool(const fte_particles* P, unsigned long long base, unsigned long long cnt)
+{
+    fte_particles h = *P;
+    h.x += base; h.y += base; h.z += base; h.mu += base; h.p += base; h.w += base;
+    h.id += base; h.status += base;
+    h.count = cnt;
+    h.capacity = cnt;
+    return h;
+}
+
+// A second stream that starts after the work already on `st`.
+fte_status fork_side(cudaStream_t st, SideStream* side)
+{
+    FTE_CUDA(cudaStreamCreateWithFlags(&side->s, cudaStreamNonBlocking), "stream create");
+    FTE_CUDA(cudaEventCreateWithFlags(&side->fork, cudaEventDisableTiming), "event create");
+    FTE_CUDA(cudaEventCreateWithFlags(&side->join, cudaEventDisableTiming), "event create");
+    FTE_CUDA(cudaEventRecord(side->fork, st), "fork");
+    FTE_CUDA(cudaStreamWaitEvent(side->s, side->fork, 0), "fork");
+    return FTE_OK;
+}
+
+// `st` waits for everything enqueued on the second stream.
+fte_status join_side(cudaStream_t st, SideStream* side)
+{
+    FTE_CUDA(cudaEventRecord(side->join, side->s), "join");
+    FTE_CUDA(cudaStreamWaitEvent(st, side->join, 0), "join");
+    return FTE_OK;
+}
+
 // Mean ln E of dN/dE ~ E^-gamma on [e1, e2].
 double mean_ln_energy(double e1, double e2, double gamma)
 {
@@ -1650,9 +1725,9 @@ size_t fte_adjoint_workspace_bytes(int device, const fte_grid* g, uint64_t n_par
                                    int checkpoint_every)
 {
     if (check_grid(g) != FTE_OK || n_steps < 0 || checkpoint_every < 1) return 0;
-    AdjLayout L;
-    if (adj_layout(device, g, n_particles, n_steps, checkpoint_every, true, &L) != FTE_OK) return 0;
-    return L.total;
+    AdjPlan plan;
+    if (adj_plan(device, g, n_particles, n_steps, checkpoint_every, true, &plan) != FTE_OK) return 0;
+    return plan.total;
 }
 
 fte_status fte_adjoint_forward(fte_particles* P, const fte_background* bg, const fte_params* prm,
@@ -1665,49 +1740,73 @@ fte_status fte_adjoint_forward(fte_particles* P, const fte_background* bg, const
     int device = 0;
     FTE_CUDA(cudaGetDevice(&device), "cudaGetDevice");
     const bool sorting = prm->sort_every > 0;
-    AdjLayout L;
-    s = adj_layout(device, &bg->grid, P->count, n_end - n_start, checkpoint_every, sorting, &L);
+    AdjPlan plan;
+    s = adj_plan(device, &bg->grid, P->count, n_end - n_start, checkpoint_every, sorting, &plan);
     if (s != FTE_OK) return s;
-    if (ws_bytes < L.total) return fail(FTE_ENOMEM, "workspace has %zu bytes, needs %zu", ws_bytes, L.total);
+    if (ws_bytes < plan.total) return fail(FTE_ENOMEM, "workspace has %zu bytes, needs %zu", ws_bytes, plan.total);
     cudaStream_t st = (cudaStream_t)stream;
     FTE_CUDA(cudaMemsetAsync(dev_out, 0, (1 + FTE_NGRAD) * sizeof(double), st), "output reset");
     if (P->count == 0) return FTE_OK;
-    char* w = (char*)ws;
-    AdvanceArgs a;
-    AdjK k;
-    s = adj_args(P, bg, prm, obs, n_start, n_end, checkpoint_every, w, L, dev_out, true, st, &a, &k);
-    if (s != FTE_OK) return s;
-    FTE_CUDA(cudaMemsetAsync(k.n_dead, 0, P->count * sizeof(int), st), "step count reset");
-    FTE_CUDA(cudaMemsetAsync(k.J_part, 0, P->count * sizeof(double), st), "observable reset");
-    SortArgs sa;
-    memset(&sa, 0, sizeof(sa));
-    if (sorting) {
-        sort_carve(a.g, P->count, w + L.off_sort, &sa);
-        sa.g = a.g;
-        sa.x = P->x; sa.y = P->y; sa.z = P->z; sa.mu = P->mu; sa.status = P->status; sa.n = P->count;
-        a.order = sa.order;
-        a.n_order = sa.hist + sa.nb;
+    // the halves share the caller's stream while it is being captured into a graph
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    FTE_CUDA(cudaStreamIsCapturing(st, &cap), "capture query");
+    const bool forked = plan.halves == 2 && cap == cudaStreamCaptureStatusNone;
+    SideStream side;
+    cudaStream_t hs[2] = {st, st};
+    if (forked) {
+        s = fork_side(st, &side);
+        if (s != FTE_OK) return s;
+        hs[1] = side.s;
+    }
+    const int H = plan.halves;
+    fte_particles ph[2];
+    AdvanceArgs a[2];
+    AdjK k[2];
+    SortArgs sa[2];
+    for (int h = 0; h < H; ++h) {
+        ph[h] = sub_pool(P, plan.base[h], plan.cnt[h]);
+        char* w = (char*)ws + plan.off[h];
+        s = adj_args(&ph[h], bg, prm, obs, n_start, n_end, checkpoint_every, w, plan.L[h], dev_out, true, hs[h],
+                     &a[h], &k[h]);
+        if (s != FTE_OK) return s;
+        FTE_CUDA(cudaMemsetAsync(k[h].n_dead, 0, ph[h].count * sizeof(int), hs[h]), "step count reset");
+        FTE_CUDA(cudaMemsetAsync(k[h].J_part, 0, ph[h].count * sizeof(double), hs[h]), "observable reset");
+        memset(&sa[h], 0, sizeof(SortArgs));
+        if (sorting) {
+            sort_carve(a[h].g, ph[h].count, w + plan.L[h].off_sort, &sa[h]);
+            sa[h].g = a[h].g;
+            sa[h].x = ph[h].x; sa[h].y = ph[h].y; sa[h].z = ph[h].z; sa[h].mu = ph[h].mu;
+            sa[h].status = ph[h].status; sa[h].n = ph[h].count;
+            a[h].order = sa[h].order;
+            a[h].n_order = sa[h].hist + sa[h].nb;
+        }
     }
     // each segment in launches of sort_every steps (reordered before each, as the plain
-    // step kernel is); the first launch of a segment stores its checkpoint
+    // step kernel is); the first launch of a segment stores its checkpoint.  The halves'
+    // launches alternate, so that both streams always have work queued.
     const long long sub = sorting ? (prm->sort_every < checkpoint_every ? prm->sort_every : checkpoint_every)
                                   : checkpoint_every;
-    for (long long seg = 0; seg < L.nseg && n_end > n_start; ++seg) {
-        k.seg = (int)seg;
+    for (long long seg = 0; seg < plan.L[0].nseg && n_end > n_start; ++seg) {
         const long long s0 = n_start + seg * checkpoint_every;
         const long long s1 = s0 + checkpoint_every < n_end ? s0 + checkpoint_every : n_end;
         for (long long c0 = s0; c0 < s1; c0 += sub) {
-            a.n_start = c0;
-            a.n_end = c0 + sub < s1 ? c0 + sub : s1;
-            k.ckpt_on = c0 == s0;
-            if (sorting) FTE_CUDA(launch_sort(sa, st), "sort launch");
-            FTE_CUDA(cudaMemsetAsync(a.fetch, 0, kFetchBytes, st), "fetch reset");
-            FTE_CUDA(launch_adjoint_forward(a, k, L.fwd_blocks, st), "adjoint forward launch");
+            for (int h = 0; h < H; ++h) {
+                k[h].seg = (int)seg;
+                a[h].n_start = c0;
+                a[h].n_end = c0 + sub < s1 ? c0 + sub : s1;
+                k[h].ckpt_on = c0 == s0;
+                if (sorting) FTE_CUDA(launch_sort(sa[h], hs[h]), "sort launch");
+                FTE_CUDA(cudaMemsetAsync(a[h].fetch, 0, kFetchBytes, hs[h]), "fetch reset");
+                FTE_CUDA(launch_adjoint_forward(a[h], k[h], plan.L[h].fwd_blocks, hs[h]), "adjoint forward launch");
+            }
         }
     }
-    if (dev_J_particle)
-        FTE_CUDA(cudaMemcpyAsync(dev_J_particle, k.J_part, P->count * sizeof(double), cudaMemcpyDeviceToDevice, st),
-                 "per-particle observable copy");
+    for (int h = 0; h < H; ++h)
+        if (dev_J_particle)
+            FTE_CUDA(cudaMemcpyAsync(dev_J_particle + plan.base[h], k[h].J_part, ph[h].count * sizeof(double),
+                                     cudaMemcpyDeviceToDevice, hs[h]),
+                     "per-particle observable copy");
+    if (forked) return join_side(st, &side);
     return FTE_OK;
 }
 
@@ -1724,78 +1823,105 @@ fte_status fte_adjoint_reverse(const fte_particles* P, const fte_background* bg,
     int device = 0;
     FTE_CUDA(cudaGetDevice(&device), "cudaGetDevice");
     const bool sorting = prm->sort_every > 0;
-    AdjLayout L;
-    s = adj_layout(device, &bg->grid, P->count, n_end - n_start, checkpoint_every, sorting, &L);
+    AdjPlan plan;
+    s = adj_plan(device, &bg->grid, P->count, n_end - n_start, checkpoint_every, sorting, &plan);
     if (s != FTE_OK) return s;
-    if (ws_bytes < L.total) return fail(FTE_ENOMEM, "workspace has %zu bytes, needs %zu", ws_bytes, L.total);
+    if (ws_bytes < plan.total) return fail(FTE_ENOMEM, "workspace has %zu bytes, needs %zu", ws_bytes, plan.total);
     cudaStream_t st = (cudaStream_t)stream;
     FTE_CUDA(cudaMemsetAsync(dev_out + 1, 0, FTE_NGRAD * sizeof(double), st), "output reset");
     if (P->count == 0) return FTE_OK;
-    char* w = (char*)ws;
-    AdvanceArgs a;
-    AdjK k;
-    s = adj_args(P, bg, prm, obs, n_start, n_end, checkpoint_every, w, L, dev_out, false, st, &a, &k);
-    if (s != FTE_OK) return s;
-    k.per_particle = dev_per_particle;
-    if (spec && spec->energy == 1) {
-        k.score_on = 1;
-        k.mean_lnE = mean_ln_energy(spec->e1, spec->e2, spec->gamma);
+    // the halves share the caller's stream while it is being captured into a graph
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    FTE_CUDA(cudaStreamIsCapturing(st, &cap), "capture query");
+    const bool forked = plan.halves == 2 && cap == cudaStreamCaptureStatusNone;
+    SideStream side;
+    cudaStream_t hs[2] = {st, st};
+    if (forked) {
+        s = fork_side(st, &side);
+        if (s != FTE_OK) return s;
+        hs[1] = side.s;
     }
-    if (dev_per_particle)
-        FTE_CUDA(cudaMemsetAsync(dev_per_particle, 0, P->count * (1 + FTE_NGRAD) * sizeof(float), st),
-                 "per-particle reset");
-    FTE_CUDA(cudaMemsetAsync(k.adj, 0, kAdjRows * P->count * sizeof(float), st), "adjoint reset");
-    const size_t n = P->count;
-    SortArgs sa;
-    memset(&sa, 0, sizeof(sa));
-    if (sorting) {
-        sort_carve(a.g, n, w + L.off_sort, &sa);
-        sa.g = a.g;
-        sa.steps = k.n_dead;
-        sa.n = n;
-        a.order = sa.order;
-        a.n_order = sa.hist + sa.nb;
+    const int H = plan.halves;
+    fte_particles ph[2];
+    AdvanceArgs a[2];
+    AdjK k[2];
+    SortArgs sa[2];
+    uint32_t* orders[2];
+    unsigned* counts[2];
+    for (int h = 0; h < H; ++h) {
+        ph[h] = sub_pool(P, plan.base[h], plan.cnt[h]);
+        char* w = (char*)ws + plan.off[h];
+        s = adj_args(&ph[h], bg, prm, obs, n_start, n_end, checkpoint_every, w, plan.L[h], dev_out, false, hs[h],
+                     &a[h], &k[h]);
+        if (s != FTE_OK) return s;
+        k[h].per_particle = dev_per_particle ? dev_per_particle + plan.base[h] * (1 + FTE_NGRAD) : nullptr;
+        if (spec && spec->energy == 1) {
+            k[h].score_on = 1;
+            k[h].mean_lnE = mean_ln_energy(spec->e1, spec->e2, spec->gamma);
+        }
+        const size_t n = ph[h].count;
+        if (k[h].per_particle)
+            FTE_CUDA(cudaMemsetAsync(k[h].per_particle, 0, n * (1 + FTE_NGRAD) * sizeof(float), hs[h]),
+                     "per-particle reset");
+        FTE_CUDA(cudaMemsetAsync(k[h].adj, 0, kAdjRows * n * sizeof(float), hs[h]), "adjoint reset");
+        memset(&sa[h], 0, sizeof(SortArgs));
+        if (sorting) {
+            sort_carve(a[h].g, n, w + plan.L[h].off_sort, &sa[h]);
+            sa[h].g = a[h].g;
+            sa[h].steps = k[h].n_dead;
+            sa[h].n = n;
+            a[h].order = sa[h].order;
+            a[h].n_order = sa[h].hist + sa[h].nb;
+        }
+        orders[h] = (uint32_t*)(w + plan.L[h].off_orders);
+        counts[h] = (unsigned*)(w + plan.L[h].off_counts);
     }
     // every segment from the last: replay its chunks forwards, then run the VJPs over
     // its chunks backwards; each chunk's particles (those alive at its start) are
-    // reordered by their position there, and its backward launch reuses that order
+    // reordered by their position there, and its backward launch reuses that order.  The
+    // halves' launches alternate, so that both streams always have work queued.
     const long long chunk = sorting ? (kAdjChunk < checkpoint_every ? kAdjChunk : checkpoint_every) : checkpoint_every;
-    uint32_t* orders = (uint32_t*)(w + L.off_orders);
-    unsigned* counts = (unsigned*)(w + L.off_counts);
-    for (long long seg = L.nseg - 1; seg >= 0; --seg) {
-        k.seg = (int)seg;
-        k.last = seg == 0;
+    for (long long seg = plan.L[0].nseg - 1; seg >= 0; --seg) {
         const long long n0 = n_start + seg * checkpoint_every;
         const long long se = n0 + checkpoint_every < n_end ? n0 + checkpoint_every : n_end;
         const long long nch = (se - n0 + chunk - 1) / chunk;
         for (long long q = 0; q < nch; ++q) {
-            k.c_start = n0 + q * chunk;
-            k.c_end = k.c_start + chunk < se ? k.c_start + chunk : se;
-            if (sorting) {
-                const float* c = q == 0 ? k.ckpt + (size_t)seg * 5 * n : k.carry;
-                sa.x = c; sa.y = c + n; sa.z = c + 2 * n; sa.mu = c + 3 * n;
-                sa.steps_min = k.c_start - n_start;
-                sa.order = orders + (size_t)q * n;
-                FTE_CUDA(launch_sort(sa, st), "sort launch");
-                FTE_CUDA(cudaMemcpyAsync(counts + q, sa.hist + sa.nb, sizeof(unsigned), cudaMemcpyDeviceToDevice, st),
-                         "order count");
-                a.order = sa.order;
-                a.n_order = counts + q;
+            for (int h = 0; h < H; ++h) {
+                const size_t n = ph[h].count;
+                k[h].seg = (int)seg;
+                k[h].last = seg == 0;
+                k[h].c_start = n0 + q * chunk;
+                k[h].c_end = k[h].c_start + chunk < se ? k[h].c_start + chunk : se;
+                if (sorting) {
+                    const float* c = q == 0 ? k[h].ckpt + (size_t)seg * 5 * n : k[h].carry;
+                    sa[h].x = c; sa[h].y = c + n; sa[h].z = c + 2 * n; sa[h].mu = c + 3 * n;
+                    sa[h].steps_min = k[h].c_start - n_start;
+                    sa[h].order = orders[h] + (size_t)q * n;
+                    FTE_CUDA(launch_sort(sa[h], hs[h]), "sort launch");
+                    FTE_CUDA(cudaMemcpyAsync(counts[h] + q, sa[h].hist + sa[h].nb, sizeof(unsigned),
+                                             cudaMemcpyDeviceToDevice, hs[h]),
+                             "order count");
+                    a[h].order = sa[h].order;
+                    a[h].n_order = counts[h] + q;
+                }
+                FTE_CUDA(cudaMemsetAsync(a[h].fetch, 0, kFetchBytes, hs[h]), "fetch reset");
+                FTE_CUDA(launch_adjoint_replay(a[h], k[h], plan.L[h].rep_blocks, hs[h]), "adjoint replay launch");
             }
-            FTE_CUDA(cudaMemsetAsync(a.fetch, 0, kFetchBytes, st), "fetch reset");
-            FTE_CUDA(launch_adjoint_replay(a, k, L.rep_blocks, st), "adjoint replay launch");
         }
         for (long long q = nch - 1; q >= 0; --q) {
-            k.c_start = n0 + q * chunk;
-            k.c_end = k.c_start + chunk < se ? k.c_start + chunk : se;
-            if (sorting) {
-                a.order = orders + (size_t)q * n;
-                a.n_order = counts + q;
+            for (int h = 0; h < H; ++h) {
+                k[h].c_start = n0 + q * chunk;
+                k[h].c_end = k[h].c_start + chunk < se ? k[h].c_start + chunk : se;
+                if (sorting) {
+                    a[h].order = orders[h] + (size_t)q * ph[h].count;
+                    a[h].n_order = counts[h] + q;
+                }
+                FTE_CUDA(cudaMemsetAsync(a[h].fetch, 0, kFetchBytes, hs[h]), "fetch reset");
+                FTE_CUDA(launch_adjoint_back(a[h], k[h], plan.L[h].rev_blocks, hs[h]), "adjoint backward launch");
             }
-            FTE_CUDA(cudaMemsetAsync(a.fetch, 0, kFetchBytes, st), "fetch reset");
-            FTE_CUDA(launch_adjoint_back(a, k, L.rev_blocks, st), "adjoint backward launch");
         }
     }
+    if (forked) return join_side(st, &side);
     return FTE_OK;
 }
 

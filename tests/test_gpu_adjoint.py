@@ -207,6 +207,24 @@ def test_spatial_ordering_changes_nothing(cir_small):
     assert np.allclose(g0, g1, rtol=1e-9, atol=0)
 
 
+def test_half_pools_change_nothing(cir_small):
+    """With reordering on, a pool of at least one wave of the forward kernel's threads runs
+    both passes as two halves on two streams, each half with its own workspace region; every
+    particle's end state, J_i and gradients equal those of the single pool in the original
+    order (reordering off), bit for bit, and the totals agree to the order of their FP64 sums."""
+    w, f = cir_small
+    prm = MODELS[0][1]
+    n = 1 << 18                       # more particles than resident forward-kernel threads
+    J0, g0, pp0, s0 = _gpu(w, f, prm, n, 200, K=64)
+    J1, g1, pp1, s1 = _gpu(w, f, dataclasses.replace(prm, sort_every=32), n, 200, K=64)
+    assert np.array_equal(pp0, pp1)
+    for key in ("x", "y", "z", "mu", "p", "status"):
+        assert np.array_equal(s0[key], s1[key]), key
+    assert J1 == pytest.approx(J0, rel=1e-12)
+    assert np.allclose(g0, g1, rtol=1e-9, atol=0)
+    assert (s1["status"] == 0).sum() > n // 2 and np.count_nonzero(pp1[:, 0]) > 1000
+
+
 @pytest.mark.parametrize("name,prm,names", MODELS, ids=[m[0] for m in MODELS])
 def test_total_matches_gpu_finite_differences(cir_small, name, prm, names):
     """Sum over many particles against central differences (2 % of each parameter) of
