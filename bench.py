@@ -264,18 +264,24 @@ def e2e_breakdown(api, pool, ring_bg, sstream, w, tally, wsp, id_base, stream, b
     barrier()
     ms = a.elapsed_time(b)
     res["streamed_with_copies"] = {"value": int(tally.ledger_n.cpu().numpy()[6]) / (ms / 1e3), "ms": ms}
-    # 3. the snapshot copies alone, one after another on the copy stream
+    # 3. the snapshot copies alone, one after another on the copy stream; the host's time to
+    # issue them tells whether the copies ran asynchronously (a copy from memory that is not
+    # page-locked, or one the driver stages, returns only when done and keeps the host from
+    # enqueuing the compute meanwhile)
     sstream.slots[:] = -1
     barrier()
     a, b = ev(), ev()
     a.record(sstream.copy_stream)
+    t0 = time.perf_counter()
     for u in range(w.grid.n_snap):
         sstream.load(u)
+    host_ms = (time.perf_counter() - t0) * 1e3
     b.record(sstream.copy_stream)
     barrier()
     ms = a.elapsed_time(b)
     res["h2d_copies_alone"] = {"gbs": w.grid.n_snap * api.fte_snapshot_bytes(ring_bg) / (ms / 1e3) / 1e9,
-                               "ms": ms}
+                               "ms": ms, "host_issue_ms": host_ms,
+                               "host_buffer_page_locked": bool(sstream.host.is_pinned())}
     return res
 
 
