@@ -225,6 +225,40 @@ def test_half_pools_change_nothing(cir_small):
     assert (s1["status"] == 0).sum() > n // 2 and np.count_nonzero(pp1[:, 0]) > 1000
 
 
+def test_graph_capture_of_both_passes(cir_small):
+    """The injection, the forward and the reverse pass captured in one CUDA graph and replayed
+    twice give the eager run's J and gradients.  The pool is large enough for two halves,
+    which then go in turn on the capturing stream (no second stream inside a capture)."""
+    import torch
+    from paper_2404_12164_gb300 import api
+    w, f = cir_small
+    prm = dataclasses.replace(MODELS[0][1], sort_every=32)
+    n, steps, K = 1 << 18, 200, 64
+    J0, g0, _, _ = _gpu(w, f, prm, n, steps, K=K)
+    bg = api.Background(w.grid)
+    api.fte_load_background(bg, f)
+    pool = api.Particles(n)
+    tally = api.Tally([])
+    adj = api.Adjoint(bg, prm, OBS, 0, steps, K)
+    adj.ws.ensure(api.fte_adjoint_workspace_bytes(bg, n, steps, K))    # no allocation while capturing
+    side = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    g = api.Graph()
+    with torch.cuda.stream(side):
+        with g.capture(side):
+            api.fte_tally_reset(tally, stream=side)
+            api.fte_inject(pool, bg, w.inject, n, tally, id_base=0, check_failed=False, stream=side)
+            adj.forward(pool, stream=side)
+            adj.reverse(pool, w.inject, stream=side)
+        for rep in range(2):
+            adj.out.zero_()
+            g.launch(side)
+            side.synchronize()
+            assert float(adj.out[0]) == pytest.approx(J0, rel=1e-12), rep
+            assert np.allclose(adj.out[1:].cpu().numpy(), g0, rtol=1e-9, atol=0), rep
+    assert J0 > 0 and np.abs(g0[:3]).max() > 0
+
+
 @pytest.mark.parametrize("name,prm,names", MODELS, ids=[m[0] for m in MODELS])
 def test_total_matches_gpu_finite_differences(cir_small, name, prm, names):
     """Sum over many particles against central differences (2 % of each parameter) of
