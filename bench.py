@@ -1106,9 +1106,9 @@ def ring_uploads(plan, R, n_snap, periodic, group_runs=8):
     """Snapshot copies of one streamed step: the injection snapshot, then the library's rule.
     Runs are taken in groups (1, 1, 2, 4, then `group_runs` runs per advance call) whose
     snapshots fit the ring with one slot to spare (R >= 3); each group's snapshots are
-    brought in, then the next R - 2 are prefetched into the slots the group does not use; a
-    slot holding the snapshot (for a periodic sequence, the same snapshot of another period)
-    is not copied again."""
+    brought in, and after its launches the next group's snapshots are prefetched into the
+    slots the group does not use; a slot holding the snapshot (for a periodic sequence, the
+    same snapshot of another period) is not copied again."""
     slots = [-1] * R
     n = 0
 
@@ -1134,8 +1134,9 @@ def ring_uploads(plan, R, n_snap, periodic, group_runs=8):
     ensure(0)
     keys = [int(key) for _, _, key in plan]
     span_max = R - 1 if R >= 3 else R
-    k, gi = 0, 0
+    groups, k = [], 0
     while k < len(keys):
+        gi = len(groups)
         want = 1 if gi < 2 else (2 if gi == 2 else (4 if gi == 3 else group_runs))
         k1, ulo, uhi = k + 1, lo(keys[k]), hi(keys[k])
         while k1 < len(keys) and k1 - k < want:
@@ -1143,14 +1144,18 @@ def ring_uploads(plan, R, n_snap, periodic, group_runs=8):
             if hi2 - lo2 + 1 > span_max:
                 break
             ulo, uhi, k1 = lo2, hi2, k1 + 1
+        groups.append((ulo, uhi))
+        k = k1
+    for gi, (ulo, uhi) in enumerate(groups):
         busy = {u % R for u in range(ulo, uhi + 1)}
         for u in range(ulo, uhi + 1):
             ensure(u)
-        for nx in range(uhi + 1, uhi + R - 1):
-            if not periodic and nx > n_snap - 1:
-                break
-            ensure(nx, busy, True)
-        k, gi = k1, gi + 1
+        if gi + 1 < len(groups):
+            nlo, nhi = groups[gi + 1]
+            for nx in range(max(nlo, uhi + 1), nhi + 1):
+                if not periodic and nx > n_snap - 1:
+                    break
+                ensure(nx, busy, True)
     return n
 
 

@@ -2151,8 +2151,9 @@ fte_status fte_advance_streamed(fte_particles* P, const fte_background* bg, cons
     // 1, 1, 2, 4, then kStreamGroupRuns runs per call: every call ends with its two
     // halves joined and a partial reordering chunk, so one call per snapshot interval
     // leaves the GPU idle at each interval's end; the ramp lets the first intervals
-    // start as soon as their own snapshots are in.  A group's snapshots must fit the
-    // ring together, leaving one slot to prefetch into (R >= 3), and its steps the
+    // start as soon as their own snapshots are in, and lets each group's compute cover
+    // the copies of the next group's snapshots.  A group's snapshots must fit the ring
+    // together, leaving one slot to prefetch into (R >= 3), and its steps the
     // workspace's time table.
     auto run_lo = [](const Run& r) { return r.key >= 0 ? r.key : -1 - r.key; };
     auto run_hi = [](const Run& r) { return r.key >= 0 ? r.key + 1 : -1 - r.key; };
@@ -2164,8 +2165,13 @@ fte_status fte_advance_streamed(fte_particles* P, const fte_background* bg, cons
     }
     const size_t ws0 = result == FTE_OK ? fte_workspace_bytes(device, &g, t, P->count, 0) : 0;
     auto fits = [&](int64_t steps) { return ws0 + (size_t)steps * sizeof(StepEntry) + 256 <= ws_bytes; };
-    size_t k = 0;
-    for (int gi = 0; k < runs.size() && result == FTE_OK; ++gi) {
+    struct Group {
+        size_t k, k1;          // runs [k, k1)
+        int64_t ulo, uhi;      // the unwrapped snapshots they read
+    };
+    std::vector<Group> groups;
+    for (size_t k = 0; k < runs.size();) {
+        const size_t gi = groups.size();
         const size_t want = gi < 2 ? 1 : (gi == 2 ? 2 : (gi == 3 ? 4 : kStreamGroupRuns));
         size_t k1 = k + 1;
         int64_t ulo = run_lo(runs[k]), uhi = run_hi(runs[k]);
@@ -2174,16 +2180,15 @@ fte_status fte_advance_streamed(fte_particles* P, const fte_background* bg, cons
             if (hi2 - lo2 + 1 > span_max || !fits(runs[k1].b - runs[k].a)) break;
             ulo = lo2; uhi = hi2; ++k1;
         }
-        auto busy = [&](int slot) { return pmod(slot - ulo, R) <= uhi - ulo; };
-        for (int64_t u = ulo; u <= uhi && result == FTE_OK; ++u) ensure(u, busy, false);
-        // the snapshots after this group, as far ahead as the slots that it does not
-        // use allow, while it computes
-        for (int64_t nx = uhi + 1; nx <= uhi + R - 2 && result == FTE_OK; ++nx) {
-            if (!g.periodic && nx > g.n_snap - 1) break;
-            ensure(nx, busy, true);
-        }
+        groups.push_back(Group{k, k1, ulo, uhi});
+        k = k1;
+    }
+    for (size_t gi = 0; gi < groups.size() && result == FTE_OK; ++gi) {
+        const Group& G = groups[gi];
+        auto busy = [&](int slot) { return pmod(slot - G.ulo, R) <= G.uhi - G.ulo; };
+        for (int64_t u = G.ulo; u <= G.uhi && result == FTE_OK; ++u) ensure(u, busy, false);
         if (result != FTE_OK) break;
-        for (int64_t u = ulo; u <= uhi; ++u) {
+        for (int64_t u = G.ulo; u <= G.uhi; ++u) {
             const int sl = (int)pmod(u, R);
             if (has_ready[sl]) {
                 const cudaError_t e = cudaStreamWaitEvent(cs, ready[sl], 0);
@@ -2191,15 +2196,24 @@ fte_status fte_advance_streamed(fte_particles* P, const fte_background* bg, cons
             }
         }
         if (result != FTE_OK) break;
-        const fte_status st = fte_advance(P, bg, prm, t, runs[k].a, runs[k1 - 1].b, ws, ws_bytes, compute_stream);
+        const fte_status st = fte_advance(P, bg, prm, t, runs[G.k].a, runs[G.k1 - 1].b, ws, ws_bytes, compute_stream);
         if (st != FTE_OK) { result = st; break; }
-        for (int64_t u = ulo; u <= uhi; ++u) {
+        for (int64_t u = G.ulo; u <= G.uhi; ++u) {
             const int sl = (int)pmod(u, R);
             const cudaError_t e = cudaEventRecord(freed[sl], cs);
             if (e != cudaSuccess) { fail_cuda(e, "event record"); break; }
             has_freed[sl] = 1;
         }
-        k = k1;
+        if (result != FTE_OK || gi + 1 == groups.size()) break;
+        // the next group's snapshots that are not in their slots yet, into the slots that
+        // this group does not use, copied while it computes: issued only now, after this
+        // group's launches, so that even copy calls that hold the host thread until they
+        // are done (where the driver stages them) overlap this group's compute
+        const Group& N = groups[gi + 1];
+        for (int64_t nx = std::max(N.ulo, G.uhi + 1); nx <= N.uhi && result == FTE_OK; ++nx) {
+            if (!g.periodic && nx > g.n_snap - 1) break;
+            ensure(nx, busy, true);
+        }
     }
     for (int k = 0; k < R; ++k) {
         if (ready[k]) cudaEventDestroy(ready[k]);
