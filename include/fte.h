@@ -326,7 +326,8 @@ fte_status fte_advance(fte_particles* P, const fte_background* bg, const fte_par
  * the cost of whole snapshot files): with grid.ring = R > 0 only R snapshots are
  * resident and fte_advance_streamed moves snapshot files from host memory into
  * their slots as the simulated time reaches them, on a copy stream, overlapped
- * with the steps of earlier intervals (R >= 3 prefetches R - 2 snapshots ahead).
+ * with the steps of earlier intervals (R >= 3: each group of intervals prefetches
+ * the next group's snapshots while it computes).
  * ------------------------------------------------------------------------- */
 
 /* Plan of a streamed advance: the steps n_start .. n_end-1 split into runs that
@@ -360,8 +361,7 @@ fte_status fte_stream_scales(const fte_background* bg, const void* host_snapshot
                              size_t staging_bytes, void* stream);
 
 /* fte_advance over a ring background (grid.ring >= 2): for every run of the
-   plan, the snapshots it needs (and, with ring >= 3, the next ring - 2) are copied
-   from host_snapshots (HOST, page-locked for overlap: the n_snap snapshots in
+   plan, the snapshots it needs are copied from host_snapshots (HOST, page-locked for overlap: the n_snap snapshots in
    order, each fte_snapshot_bytes(g) bytes of FP32 cell records) into their slots
    on copy_stream - for a 16-bit or pair-layout ring through `staging` (DEVICE,
    32-byte aligned, fte_stream_staging_bytes(g) bytes; may be NULL when that is
@@ -377,7 +377,10 @@ fte_status fte_stream_scales(const fte_background* bg, const void* host_snapshot
    (ramping 1, 1, 2, 4, 8 from the call's start), as long as a group's snapshots fit
    the ring with one slot to spare (ring >= 3) and its steps fit ws's time table:
    ws as for fte_advance with n_steps at least the longest run of the plan
-   (n_end - n_start steps allow full groups).
+   (n_end - n_start steps allow full groups).  With ring >= 3, once a group's
+   launches are enqueued the next group's snapshots are copied into the slots the
+   group does not use, so that the group's compute covers them (also where a
+   copy call returns only when done).
    Work of earlier calls on either stream is waited for.  EINVAL/ENOMEM for a
    missing or undersized staging buffer.  Asynchronous. */
 fte_status fte_advance_streamed(fte_particles* P, const fte_background* bg, const void* host_snapshots,
