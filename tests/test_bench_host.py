@@ -1,6 +1,7 @@
 """Host-side arithmetic of the benchmark's JSON line (no GPU): the union of launch intervals,
 the roofline record built from them, the DRAM-traffic record that is reported only while the
-step kernel's sources are the ones it was captured from, and the batch-means standard error."""
+step kernel's sources are the ones it was captured from, the batch-means standard error and
+the snapshot copy count of the end-to-end arm."""
 import math
 
 import numpy as np
@@ -65,3 +66,20 @@ def test_batch_means_standard_error():
     rng = np.random.default_rng(0)
     y = rng.normal(0.0, 2.0, size=320_000)
     assert bench.batch_sigma(y) == pytest.approx(math.sqrt(len(y)) * 2.0, rel=0.35)
+
+
+def test_ring_upload_count():
+    """The copy count behind the end-to-end line's h2d_bytes_per_step: with one slot per
+    snapshot of a periodic sequence every snapshot crosses once per step however many periods
+    the run spans; with a smaller ring every unwrapped snapshot the run reaches crosses once
+    (time only moves forward); a non-periodic sequence is copied once, its frozen tail
+    included."""
+    hourly_4d = [(i * 360, (i + 1) * 360, i) for i in range(96)]          # 4 days, 24 snapshots
+    assert bench.ring_uploads(hourly_4d, 24, 24, True) == 24
+    runs = [(i * 60, (i + 1) * 60, i) for i in range(14)]                  # 2.3 periods of 6
+    assert bench.ring_uploads(runs, 6, 6, True) == 6
+    for R in (2, 3, 4):
+        assert bench.ring_uploads(runs, R, 6, True) == 15                  # snapshots 0 .. 14
+    frozen = [(i * 60, (i + 1) * 60, i) for i in range(5)] + [(300, 800, -1 - 5)]
+    for R in (2, 3, 6):
+        assert bench.ring_uploads(frozen, R, 6, False) == 6
