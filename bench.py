@@ -13,7 +13,10 @@ Metric: alive particle-steps per second (whole job, all ranks).
 same step through the C ABI starting from host buffers: the snapshots stream
 from page-locked memory into a ring of one slot per snapshot (each copied once
 per step, overlapped with the steps of earlier intervals), and the tally and
-ledger are read back.
+ledger are read back.  `e2e.breakdown` splits the gap between the two on the box
+that runs it (rank 0's own particles): the streamed calls without copies, a
+device-timed step with them, and the copies alone with the host's time to issue
+them.
 
 Multi-GPU: every rank runs its own batch of 1e6 particles (distinct particle
 ids, weak scaling) and the tallies are summed over ranks after each step.
